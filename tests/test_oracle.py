@@ -1,0 +1,421 @@
+"""Pins for the FP64 CPU oracle: each test checks the oracle against something
+the paper or mathematics fixes, not against itself (CPU only)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1502_02941_gb300 import workloads as W
+from helpers import oracle_direct, oracle_l2, oracle_system, read_golden_sections
+
+# ----------------------------------------------------------------------------
+# quadrature
+# ----------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 8, 12])
+def test_gauss_legendre_matches_library(n):
+    """Oracle Gauss-Legendre (Newton on P_n) equals numpy's leggauss on [0,1]."""
+    t, w = O.gauss_legendre01(n)
+    x, wx = np.polynomial.legendre.leggauss(n)
+    order = np.argsort(t)
+    np.testing.assert_allclose(np.sort(t), 0.5 * (1 + x), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(w[order], 0.5 * wx, rtol=0, atol=1e-15)
+
+
+# ----------------------------------------------------------------------------
+# mesh (Sec. 2.1, Fig. 2)
+# ----------------------------------------------------------------------------
+
+
+def test_fixture_matches_paper_listing():
+    g = read_golden_sections("fig2_initial_mesh.txt")
+    np.testing.assert_array_equal(g["nodes"], W.FIXTURE_NODES)
+    np.testing.assert_array_equal(g["elements"].astype(int) - 1, W.FIXTURE_ELEMS)
+    np.testing.assert_array_equal(g["dirichlet"].astype(int) - 1, W.FIXTURE_DIRICHLET)
+
+
+def test_fixture_skeleton():
+    m = O.make_mesh(W.FIXTURE_NODES, W.FIXTURE_ELEMS, W.FIXTURE_DIRICHLET, np.zeros((0, 2)))
+    assert m.ned == 16 and m.n_bedges == 8 and m.n_interior == 8
+    # interior edges: Ki < Kj, n_e from Ki to Kj points away from Ki's centroid
+    for va, vb, Ki, Kj, typ in m.edges:
+        if Kj < 0:
+            assert typ == 1
+            continue
+        assert Ki < Kj and typ == 0
+        d = m.nodes[vb] - m.nodes[va]
+        n = np.array([d[1], -d[0]])
+        mid = 0.5 * (m.nodes[va] + m.nodes[vb])
+        ci = m.nodes[m.elems[Ki]].mean(0)
+        cj = m.nodes[m.elems[Kj]].mean(0)
+        assert n @ (mid - ci) > 0 and n @ (cj - mid) > 0
+
+
+def _triangle_set(nodes, elems):
+    out = set()
+    for t in elems:
+        pts = [tuple(np.round(nodes[v], 12)) for v in t]
+        # canonical rotation of the counter-clockwise cycle
+        i = pts.index(min(pts))
+        out.add(tuple(pts[i:] + pts[:i]))
+    return out
+
+
+def test_two_refinements_give_config1_mesh():
+    """Two uniform refinements of the printed 8-triangle mesh give the 8x8 "/"
+    split mesh of 128 triangles (Sec. 2.1 refinement loop)."""
+    nodes, elems, dr, ne = W.FIXTURE_NODES, W.FIXTURE_ELEMS, W.FIXTURE_DIRICHLET, np.zeros((0, 2), np.int32)
+    for _ in range(2):
+        nodes, elems, dr, ne = O.refine(nodes, elems, dr, ne)
+    assert elems.shape[0] == 128 and dr.shape[0] == 32
+    s8 = W.structured_mesh(8)
+    assert _triangle_set(nodes, elems) == _triangle_set(s8.nodes, s8.elems)
+    # all counter-clockwise
+    a, b, c = nodes[elems[:, 0]], nodes[elems[:, 1]], nodes[elems[:, 2]]
+    area2 = (b[:, 0] - a[:, 0]) * (c[:, 1] - a[:, 1]) - (b[:, 1] - a[:, 1]) * (c[:, 0] - a[:, 0])
+    assert (area2 > 0).all()
+
+
+@pytest.mark.parametrize("N", [1, 2, 5, 16])
+def test_structured_counts(N):
+    ma = W.structured_mesh(N, neumann_sides=("top",))
+    m = O.make_mesh(ma.nodes, ma.elems, ma.dirichlet, ma.neumann)
+    assert m.ne == 2 * N * N
+    assert m.ned == 3 * N * N + 2 * N
+    assert m.n_interior == 3 * N * N - 2 * N
+    assert m.n_bedges == 4 * N
+    assert (O.boundary_types(m) == 2).sum() == N
+
+
+def test_mesh_errors():
+    ma = W.structured_mesh(2)
+    bad = ma.elems.copy()
+    bad[0] = bad[0, ::-1]
+    with pytest.raises(ValueError, match="counter-clockwise"):
+        O.make_mesh(ma.nodes, bad, ma.dirichlet, ma.neumann)
+    with pytest.raises(ValueError, match="boundary"):
+        O.make_mesh(ma.nodes, ma.elems, ma.dirichlet[:-1], ma.neumann)
+
+
+# ----------------------------------------------------------------------------
+# parameters (Sec. 1, Sec. 4 set_parameter)
+# ----------------------------------------------------------------------------
+
+
+def test_set_parameter_table():
+    rows = np.loadtxt(__import__("os").path.join(__import__("helpers").GOLDEN, "set_parameter.txt"))
+    for method, k, kappa, sigma in rows:
+        s, kap = O.set_parameter(int(method), int(k))
+        assert (s, kap) == (sigma, kappa)
+
+
+def test_dof_formula():
+    assert [O.nbasis(k) for k in (1, 2, 3)] == [3, 6, 10]
+
+
+# ----------------------------------------------------------------------------
+# element integrals against closed forms
+# ----------------------------------------------------------------------------
+
+
+def _one_element(v):
+    nodes = np.array(v, dtype=np.float64)
+    elems = np.array([[0, 1, 2]], np.int32)
+    dirichlet = np.array([[0, 1], [1, 2], [2, 0]], np.int32)
+    return W.MeshArrays(nodes, elems, dirichlet, np.zeros((0, 2), np.int32))
+
+
+def _exact_monomial_integral(v, a, b, xc, yc, h):
+    """Exact integral over the triangle v of ((x-xc)/h)^a ((y-yc)/h)^b, by
+    expanding in reference coordinates and using int r^p s^q = p! q!/(p+q+2)!."""
+    from itertools import product
+    v = np.asarray(v, dtype=np.float64)
+    e1, e2 = v[1] - v[0], v[2] - v[0]
+    det = abs(e1[0] * e2[1] - e1[1] * e2[0])
+    # X = c0 + c1 r + c2 s, Y = d0 + d1 r + d2 s
+    c = np.array([(v[0, 0] - xc) / h, e1[0] / h, e2[0] / h])
+    d = np.array([(v[0, 1] - yc) / h, e1[1] / h, e2[1] / h])
+    # polynomial in r,s as dict (p,q)->coef
+    def pw(coefs, n):
+        poly = {(0, 0): 1.0}
+        for _ in range(n):
+            new = {}
+            for (p, q), val in poly.items():
+                for (dp, dq), cc in (((0, 0), coefs[0]), ((1, 0), coefs[1]), ((0, 1), coefs[2])):
+                    new[(p + dp, q + dq)] = new.get((p + dp, q + dq), 0.0) + val * cc
+            poly = new
+        return poly
+    P1, P2 = pw(c, a), pw(d, b)
+    tot = 0.0
+    for (p1, q1), v1 in P1.items():
+        for (p2, q2), v2 in P2.items():
+            p, q = p1 + p2, q1 + q2
+            tot += v1 * v2 * math.factorial(p) * math.factorial(q) / math.factorial(p + q + 2)
+    return tot * det
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_mass_matrix_exact(k):
+    """R with alpha=1 is the mass matrix of the scaled monomials; compare with
+    exact integrals of monomial products."""
+    v = [[0.1, 0.2], [0.9, 0.35], [0.3, 0.8]]
+    run = oracle_system(_one_element(v), k, 2, W.Problem("z", 0.0, 1.0, (0,) * 6, None, lambda xp, x, y: 0 * x))
+    V = np.array(v)
+    xc, yc = V.mean(0)
+    h = max(np.linalg.norm(V[(i + 1) % 3] - V[i]) for i in range(3))
+    exps = [(a, d - a) for d in range(k + 1) for a in range(d, -1, -1)]
+    M = np.array([[_exact_monomial_integral(v, ai + aj, bi + bj, xc, yc, h) for (aj, bj) in exps]
+                  for (ai, bi) in exps])
+    np.testing.assert_allclose(run.system.R_diag[0], M, rtol=1e-13, atol=1e-15)
+
+
+def test_p1_stiffness_and_mass_closed_form():
+    """P1 element matrices in the barycentric (hat) basis, textbook forms:
+    stiffness |K| grad(lambda_i).grad(lambda_j) = (e_i . e_j)/(4|K|) with e_i
+    the edge opposite vertex i, and mass |K|/12 [[2,1,1],[1,2,1],[1,1,2]]."""
+    v = np.array([[0.1, 0.2], [0.9, 0.35], [0.3, 0.8]])
+    prob = W.Problem("z", 1.0, 1.0, (0,) * 6, None, lambda xp, x, y: 0 * x)
+    run = oracle_system(_one_element(v), 1, 2, prob)
+    # change of basis: lambda_i(x) = sum_m T[m,i] phi_m(x); phi values at the vertices
+    _, phi = O.evaluate(run.mesh, 1, None, [0, 0, 0], v, want_basis=True)   # phi[p, m]
+    T = np.linalg.solve(phi, np.eye(3))                                     # phi @ T = I
+    area = 0.5 * abs((v[1, 0] - v[0, 0]) * (v[2, 1] - v[0, 1]) - (v[1, 1] - v[0, 1]) * (v[2, 0] - v[0, 0]))
+    # grad lambda_i = rot(edge opposite i)/(2|K|)
+    G = np.array([[v[(i + 1) % 3][1] - v[(i + 2) % 3][1], v[(i + 2) % 3][0] - v[(i + 1) % 3][0]] for i in range(3)]) / (2 * area)
+    # volume-only diffusion: assemble with eps=1 but look at the volume part
+    # through D with penalties removed: use a one-element mesh with Neumann
+    # boundary so that no edge term enters D.
+    ma = _one_element(v)
+    ma = W.MeshArrays(ma.nodes, ma.elems, np.zeros((0, 2), np.int32), ma.dirichlet)
+    run_n = oracle_system(ma, 1, 2, prob)
+    S = T.T @ run_n.system.D_diag[0] @ T
+    M = T.T @ run_n.system.R_diag[0] @ T
+    np.testing.assert_allclose(S, area * G @ G.T, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(M, area / 12 * np.array([[2, 1, 1], [1, 2, 1], [1, 1, 2]]), rtol=1e-12)
+
+
+# ----------------------------------------------------------------------------
+# whole assembly: exact reproduction of P_k solutions (consistency)
+# ----------------------------------------------------------------------------
+
+
+def _poly_problem(k, neumann=("right", "top"), eps=0.3, alpha=0.7, b=(0.4, 0.3, -0.2, -0.6, 0.1, 0.5)):
+    a, bb = {1: (1, 0), 2: (1, 1), 3: (2, 1)}[k]
+    return W.Problem("poly", eps, alpha, b, W.polynomial(a, bb), neumann_sides=neumann)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+@pytest.mark.parametrize("method", [1, 2, 3])
+def test_polynomial_reproduction(k, method):
+    """u in P_k with exact data is reproduced by SIPG/NIPG/IIPG with upwinding,
+    affine b, reaction, and Neumann edges that are partly inflow (A-1, A-5, A-6)."""
+    prob = _poly_problem(k)
+    ma = W.perturbed_mesh(4, seed=7, neumann_sides=prob.neumann_sides)
+    run = oracle_system(ma, k, method, prob)
+    x = oracle_direct(run)
+    err, _ = oracle_l2(run, x, prob)
+    assert err < 1e-11
+
+
+@pytest.mark.parametrize("method", [1, 3])
+def test_literal_rhs_sign_breaks_consistency(method):
+    """With the printed RHS term -eps grad v.n gD for NIPG/IIPG the scheme no
+    longer reproduces polynomials: evidence for reading A-1."""
+    prob = _poly_problem(2)
+    ma = W.perturbed_mesh(4, seed=7, neumann_sides=prob.neumann_sides)
+    run = oracle_system(ma, 2, method, prob, literal_rhs=True)
+    err, _ = oracle_l2(run, oracle_direct(run), prob)
+    assert err > 1e-3
+
+
+def test_pure_transport_reproduction():
+    """eps = 0 (no diffusion terms), pure upwind transport + reaction reproduces
+    P_k data through the inflow boundary."""
+    prob = _poly_problem(2, neumann=("right",), eps=0.0, b=(1.0, 0.2, 0.0, 0.5, 0.0, 0.1))
+    ma = W.perturbed_mesh(3, seed=3, neumann_sides=prob.neumann_sides)
+    run = oracle_system(ma, 2, 2, prob)
+    err, _ = oracle_l2(run, oracle_direct(run), prob)
+    assert err < 1e-11
+
+
+# ----------------------------------------------------------------------------
+# structure: symmetry, definiteness, D/C/R split, upwind direction
+# ----------------------------------------------------------------------------
+
+
+def test_sipg_symmetric_positive_definite_config1():
+    c = W.config1()
+    ma = W.structured_mesh(c.N)
+    run = oracle_system(ma, c.k, c.method, c.problem, sigma=c.sigma)
+    A = O.dense_matrix(run.mesh, run.system.A_diag, run.system.A_off)
+    assert np.abs(A - A.T).max() <= 1e-14 * np.abs(A).max()
+    np.linalg.cholesky(A)
+
+
+@pytest.mark.parametrize("method", [1, 3])
+def test_nipg_iipg_not_symmetric(method):
+    ma = W.structured_mesh(2)
+    run = oracle_system(ma, 1, method, W.Problem("z", 1.0, 0.0, (0,) * 6, W.sinsin))
+    A = O.dense_matrix(run.mesh, run.system.A_diag, run.system.A_off)
+    assert np.abs(A - A.T).max() > 1e-3 * np.abs(A).max()
+
+
+def test_dcr_split():
+    ma = W.perturbed_mesh(3, seed=1)
+    prob0 = W.Problem("z", 0.5, 2.0, (0,) * 6, W.sinsin)
+    run = oracle_system(ma, 2, 2, prob0)
+    assert np.abs(run.system.C_diag).max() == 0 and np.abs(run.system.C_off).max() == 0
+    assert np.abs(run.system.R_off).max() == 0
+    prob1 = W.Problem("z", 0.5, 1.0, (0,) * 6, W.sinsin)
+    run1 = oracle_system(ma, 2, 2, prob1)
+    np.testing.assert_allclose(run.system.R_diag, 2.0 * run1.system.R_diag, rtol=1e-15)
+    # mass matrix symmetric positive definite per element
+    for K in range(run1.mesh.ne):
+        np.linalg.cholesky(run1.system.R_diag[K])
+    probb = W.Problem("z", 0.5, 1.0, (1.0, 0, 0, 0.3, 0, 0), W.sinsin)
+    assert np.abs(oracle_system(ma, 2, 2, probb).system.C_off).max() > 0
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_l2_projection(k):
+    """eps = 0, b = 0, alpha = 1: the scheme is the L2 projection, exact for f in P_k."""
+    prob = W.Problem("p", 0.0, 1.0, (0,) * 6, _poly_problem(k).exact)
+    ma = W.perturbed_mesh(3, seed=5)
+    run = oracle_system(ma, k, 2, prob)
+    err, _ = oracle_l2(run, oracle_direct(run), prob)
+    assert err < 1e-12
+
+
+def test_upwind_direction():
+    """eps = 0, b = (1, 0): block (K, L) is nonzero only if L lies upstream of K
+    across their shared edge (b.n_K < 0 there)."""
+    ma = W.structured_mesh(3)
+    prob = W.Problem("t", 0.0, 1.0, (1.0, 0, 0, 0, 0, 0), W.sinsin)
+    run = oracle_system(ma, 1, 2, prob)
+    m = run.mesh
+    for e, (va, vb, Ki, Kj, typ) in enumerate(m.edges):
+        if Kj < 0:
+            continue
+        d = m.nodes[vb] - m.nodes[va]
+        n = np.array([d[1], -d[0]]) / np.linalg.norm(d)     # from Ki to Kj
+        bn = n[0]
+        blk_ij, blk_ji = np.abs(run.system.C_off[e, 0]).max(), np.abs(run.system.C_off[e, 1]).max()
+        if bn < -1e-12:      # flow enters Ki from Kj
+            assert blk_ij > 0 and blk_ji == 0
+        elif bn > 1e-12:     # flow enters Kj from Ki
+            assert blk_ij == 0 and blk_ji > 0
+        else:
+            assert blk_ij == 0 and blk_ji == 0
+        assert np.abs(run.system.D_off[e]).max() == 0        # eps = 0: no IP coupling
+
+
+# ----------------------------------------------------------------------------
+# convergence (optimal SIPG rates)
+# ----------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_sipg_convergence_rate(k):
+    prob = W.Problem("sinsin", 1.0, 0.0, (0,) * 6, W.sinsin)
+    errs = []
+    for N in (4, 8, 16):
+        run = oracle_system(W.structured_mesh(N), k, 2, prob)
+        errs.append(oracle_l2(run, oracle_direct(run), prob)[0])
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert abs(rates[-1] - (k + 1)) < 0.15, rates
+
+
+@pytest.mark.parametrize("method", [1, 3])
+def test_nipg_iipg_convergence(method):
+    prob = W.Problem("sinsin", 1.0, 0.0, (0,) * 6, W.sinsin)
+    for k in (1, 2):
+        errs = []
+        for N in (4, 8, 16):
+            run = oracle_system(W.structured_mesh(N), k, method, prob)
+            errs.append(oracle_l2(run, oracle_direct(run), prob)[0])
+        rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+        assert rates[-1] > k - 0.1, (k, rates)
+
+
+# ----------------------------------------------------------------------------
+# manufactured data (inputs) against finite differences
+# ----------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("name", ["sinsin", "bl", "gauss", "tanh", "poly"])
+def test_manufactured_derivatives(name):
+    ex = {"sinsin": W.sinsin, "bl": W.boundary_layer(0.05), "gauss": W.gaussian_bump,
+          "tanh": W.tanh_layer(0.01), "poly": W.polynomial(2, 1)}[name]
+    rng = np.random.default_rng(0)
+    x, y = rng.uniform(0.1, 0.9, 20), rng.uniform(0.1, 0.9, 20)
+    h = 1e-3
+    u = lambda x, y: ex(np, x, y)[0]
+    d1 = lambda f, x, y, dx, dy: (-f(x + 2 * dx, y + 2 * dy) + 8 * f(x + dx, y + dy) - 8 * f(x - dx, y - dy) + f(x - 2 * dx, y - 2 * dy)) / (12 * h)
+    d2 = lambda f, x, y, dx, dy: (-f(x + 2 * dx, y + 2 * dy) + 16 * f(x + dx, y + dy) - 30 * f(x, y) + 16 * f(x - dx, y - dy) - f(x - 2 * dx, y - 2 * dy)) / (12 * h * h)
+    _, ux, uy, lap = ex(np, x, y)
+    scale = 1 + np.abs(lap).max()
+    np.testing.assert_allclose(ux, d1(u, x, y, h, 0), atol=1e-6 * scale)
+    np.testing.assert_allclose(uy, d1(u, x, y, 0, h), atol=1e-6 * scale)
+    np.testing.assert_allclose(lap, d2(u, x, y, h, 0) + d2(u, x, y, 0, h), atol=1e-4 * scale)
+
+
+def test_tanh_matches_paper_derivative_formulas():
+    """The listing's fexact/fsource write yex_x, yex_y, yex_xx, yex_yy in sech
+    form; check the workload's tanh form against them."""
+    eps = 1e-2
+    rng = np.random.default_rng(1)
+    x, y = rng.uniform(0, 1, 30), rng.uniform(0, 1, 30)
+    s = (2 * x - y - 0.25) / np.sqrt(5 * eps)
+    sech2 = 1 / np.cosh(s) ** 2
+    u, ux, uy, lap = W.tanh_layer(eps)(np, x, y)
+    np.testing.assert_allclose(u, 0.5 * (1 - np.tanh(s)), rtol=1e-14)
+    # absolute tolerances: 1 - tanh^2 and sech^2 differ by cancellation only
+    np.testing.assert_allclose(ux, -1 / np.sqrt(5 * eps) * sech2, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(uy, 0.5 / np.sqrt(5 * eps) * sech2, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(lap, (0.8 / eps + 0.2 / eps) * np.tanh(s) * sech2, rtol=0, atol=1e-11)
+
+
+# ----------------------------------------------------------------------------
+# solvers and post-processing
+# ----------------------------------------------------------------------------
+
+
+def test_dense_solve_matches_numpy():
+    rng = np.random.default_rng(2)
+    A = rng.standard_normal((40, 40)) + 5 * np.eye(40)
+    b = rng.standard_normal(40)
+    np.testing.assert_allclose(O.dense_solve(A, b), np.linalg.solve(A, b), rtol=1e-12)
+
+
+@pytest.mark.parametrize("method", [1, 2])
+def test_gmres_matches_direct(method):
+    c = W.config2(method=method, N=8)
+    run = oracle_system(W.structured_mesh(c.N), c.k, c.method, c.problem)
+    x, its, relres, ok = O.gmres(run.mesh, run.system.A_diag, run.system.A_off, run.system.F, m=20, tol=1e-12)
+    assert ok and relres <= 1e-12 and its > 0
+    xd = oracle_direct(run)
+    assert np.linalg.norm(x - xd) <= 1e-9 * np.linalg.norm(xd)
+    import scipy.sparse.linalg as spla
+    A = O.to_sparse(run.mesh, run.system.A_diag, run.system.A_off)
+    np.testing.assert_allclose(spla.spsolve(A.tocsc(), run.system.F), xd, rtol=1e-9, atol=1e-12)
+
+
+def test_apply_matches_sparse_matvec():
+    prob = _poly_problem(2)
+    ma = W.perturbed_mesh(3, seed=7, neumann_sides=prob.neumann_sides)
+    run = oracle_system(ma, 2, 1, prob)
+    A = O.to_sparse(run.mesh, run.system.A_diag, run.system.A_off)
+    x = np.random.default_rng(0).standard_normal(A.shape[0])
+    np.testing.assert_allclose(O.apply(run.mesh, run.system.A_diag, run.system.A_off, x), A @ x,
+                               rtol=1e-13, atol=1e-13)
+
+
+def test_l2_error_of_zero_solution():
+    """||0 - sin(pi x) sin(pi y)||_L2 = 1/2 on the unit square; h_max = sqrt(2)/N."""
+    prob = W.Problem("sinsin", 1.0, 0.0, (0,) * 6, W.sinsin)
+    run = oracle_system(W.structured_mesh(8), 1, 2, prob)
+    err, hmax = oracle_l2(run, np.zeros(run.mesh.ne * 3), prob)
+    assert abs(err - 0.5) < 1e-9
+    assert abs(hmax - math.sqrt(2) / 8) < 1e-15
