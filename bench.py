@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Benchmark of the DG hot path on one GB300 (or N replicas).
+
+Workload: the 256x256 split-square mesh (131072 triangles), P2 (786432 dofs),
+eps = 1e-6, b = (1,0), alpha = 1, boundary-layer manufactured solution,
+Dirichlet data on all sides; NIPG and SIPG with upwinding; GMRES(50) with
+block-Jacobi preconditioning to relative residual 1e-10 (f64).
+
+One step = for each of NIPG and SIPG: mesh upload + device geometry/adjacency,
+assembly of the block operator and F, block-Jacobi set-up, GMRES solve.  The
+metric is solves/s (2 solves per step).  `value` has the problem data (f, gD,
+gN at the quadrature points) resident in HBM; `e2e` copies them from pinned
+host memory every step and reads the solution back.
+
+Also reported: the f64 operator apply against the HBM roofline (CUDA events,
+same stream), the oracle's CPU time for the same solve (bounded sample), clocks
+sampled during the timed region, and the number of kernels launched.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solves/s to rel-res 1e-10, learned+mixed vs plain FP64 GMRES; apply HBM GB/s"
+WORKLOAD = "cfg2: 256x256 split squares (131072 triangles), P2 (786432 dofs), NIPG+SIPG, eps=1e-6, " \
+           "b=(1,0), alpha=1, boundary-layer u, all Dirichlet, GMRES(50)+block-Jacobi f64 to rel-res 1e-10"
+N_MESH, DEGREE = 256, 2
+METHODS = (1, 2)   # NIPG, SIPG
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"dg_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# roofline inputs
+# ---------------------------------------------------------------------------
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def profile_traffic(name):
+    """dram bytes per launch recorded in profiles/<name>.md ('dram_bytes_per_launch: X')."""
+    p = os.path.join(ROOT, "profiles", name + ".md")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        if line.strip().startswith("dram_bytes_per_launch:"):
+            try:
+                return float(line.split(":", 1)[1].split()[0])
+            except ValueError:
+                return None
+    return None
+
+
+def apply_bytes(ne, n_interior, nb, s_a, s_x):
+    """Algorithmic bytes of one apply: nonzero blocks, x read once, y written once,
+    3 neighbour ids per element."""
+    blocks = ne + 2 * n_interior
+    return blocks * nb * nb * s_a + ne * nb * (s_x + s_x) + 12 * ne
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline (the oracle), bounded sample
+# ---------------------------------------------------------------------------
+def oracle_sample(gpu_its, iters=50):
+    """Time the oracle's assembly + block inverses + `iters` GMRES iterations of
+    each method and scale the per-iteration time to `gpu_its` (iterations the
+    same algorithm needs) -> estimated oracle solves/s."""
+    import numpy as np
+
+    import oracle as O
+    from paper_1502_02941_gb300 import workloads as W
+    total = 0.0
+    detail = []
+    for method, its in zip(METHODS, gpu_its):
+        cfg = W.config2(method=method, N=N_MESH)
+        ma = W.structured_mesh(cfg.N)
+        p = cfg.problem
+        t0 = time.perf_counter()
+        m = O.make_mesh(ma.nodes, ma.elems, ma.dirichlet, ma.neumann)
+        s, kap = O.set_parameter(cfg.method, cfg.k)
+        xq = O.quad_points(m, cfg.k, O.VOLUME)
+        xb = O.quad_points(m, cfg.k, O.BOUNDARY)
+        sysm = O.assemble(m, cfg.k, kap, s, 2 * s, p.eps, p.alpha, p.b, p.f(np, xq[..., 0], xq[..., 1]),
+                          p.gD(np, xb[..., 0], xb[..., 1]), None, split=False)
+        t1 = time.perf_counter()
+        _, done, _, _ = O.gmres(m, sysm.A_diag, sysm.A_off, sysm.F, m=50, tol=1e-10, max_it=iters)
+        t2 = time.perf_counter()
+        per_it = (t2 - t1) / max(done, 1)
+        est = (t1 - t0) + per_it * its
+        total += est
+        detail.append({"method": "NIPG" if method == 1 else "SIPG", "setup_s": round(t1 - t0, 3),
+                       "per_iteration_ms": round(per_it * 1e3, 3), "iterations_scaled_to": its,
+                       "est_solve_s": round(est, 3)})
+    return len(METHODS) / total, detail
+
+
+def oracle_iteration_counts():
+    p = os.path.join(ROOT, "oracle", "cfg2_oracle_solves.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return [s["iterations"] for s in d["solves"]], "oracle full solves (oracle/cfg2_oracle_solves.json)"
+    return None, None
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# ---------------------------------------------------------------------------
+def reference_arm(args, rank):
+    if rank != 0:
+        return
+    its, src = oracle_iteration_counts()
+    if its is None:
+        its, src = [2000, 2000], "assumed 2000 iterations per solve (no oracle record)"
+    for _ in range(args.warmup):
+        oracle_sample(its, iters=10)
+    vals = []
+    t0 = time.perf_counter()
+    details = None
+    for _ in range(args.steps):
+        v, details = oracle_sample(its, iters=20)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    value = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": "per step and method: oracle assembly + block inverses + 20 GMRES "
+                                       f"iterations, per-iteration time scaled to {its} iterations ({src})",
+                             "detail": details},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, rank)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__ as G
+    G.build()
+    from paper_1502_02941_gb300 import dg as D
+    from paper_1502_02941_gb300 import problem
+    from paper_1502_02941_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    h = D.DG(local)
+    cfg0 = W.config2(method=METHODS[0], N=N_MESH)
+    ma = W.structured_mesh(N_MESH)
+    # problem data at the quadrature points (identical for both methods)
+    problem.setup(h, cfg0, mesh=ma, assemble=False)
+    f, gD, gN = problem.problem_data(h, cfg0.problem)
+    info = h.info()
+    dofs = info.dofs
+    x = torch.empty(dofs, dtype=torch.float64, device=dev)
+    p = cfg0.problem
+    f_h = f.cpu().pin_memory(); gD_h = gD.cpu().pin_memory(); gN_h = gN.cpu().pin_memory()
+    x_h = torch.empty(dofs, dtype=torch.float64).pin_memory()
+    h2d = (f_h.numel() + gD_h.numel() + gN_h.numel()) * 8 * len(METHODS) \
+        + (ma.nodes.nbytes + ma.elems.nbytes + ma.dirichlet.nbytes + ma.neumann.nbytes) * len(METHODS)
+    d2h = dofs * 8 * len(METHODS)
+
+    last = {}
+
+    def step(e2e=False):
+        its = []
+        for method in METHODS:
+            if e2e:
+                f.copy_(f_h, non_blocking=True); gD.copy_(gD_h, non_blocking=True); gN.copy_(gN_h, non_blocking=True)
+            h.mesh_upload(ma.nodes, ma.elems, ma.dirichlet, ma.neumann)
+            h.set_params(method=method, degree=DEGREE, sigma_int=0.0, store=D.DG_STORE_F64, gmres_m=50,
+                         tol=1e-10, max_it=20000)
+            h.assemble(p.eps, p.alpha, p.b, f, gD, gN)
+            h.precond_setup()
+            _, sinfo = h.gmres_solve(x=x)
+            its.append(sinfo.iterations)
+            last[method] = (sinfo.iterations, sinfo.relres, sinfo.restarts)
+            if e2e:
+                x_h.copy_(x, non_blocking=True)
+        return its
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def timed(e2e, sampler=None):
+        barrier()
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.start()
+        n0 = h.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step(e2e)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clocks = sampler.stop() if sampler else None
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, h.launch_count() - n0, clocks
+
+    sampler = ClockSampler(local)
+    ms, launches, clocks = timed(False, sampler)
+    ms_e2e, _, _ = timed(True)
+    solves = len(METHODS) * args.steps * world
+    value = solves / (ms / 1e3)
+    e2e_value = solves / (ms_e2e / 1e3)
+    its = [last[m][0] for m in METHODS]
+
+    # ---- roofline of the operator apply (f64), CUDA events on the same stream
+    y = torch.empty_like(x)
+    xr = torch.randn(dofs, dtype=torch.float64, device=dev)
+    for _ in range(3):
+        h.apply(xr, D.DG_F64, y)
+    nrep = 50
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    tot = 0.0
+    for _ in range(nrep):
+        flush.fill_(1.0)
+        a0.record(stream)
+        h.apply(xr, D.DG_F64, y)
+        a1.record(stream)
+        a1.synchronize()
+        tot += a0.elapsed_time(a1)
+    apply_ms = tot / nrep
+    abytes = apply_bytes(info.ne, info.n_interior, info.nb, 8, 8)
+    peak, peak_src = measured_peaks()
+    achieved = abytes / (apply_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_apply<6,double,double,double>", "achieved": achieved,
+                "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": profile_traffic("k_apply_f64_cfg2"),
+                "algorithmic_bytes": abytes, "avg_launch_ms": apply_ms, "peak_source": peak_src + " (hbm_gbs)"}
+
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": N_MESH, "k": DEGREE, "ne": info.ne, "dofs": dofs,
+                       "methods": ["NIPG", "SIPG"], "gmres_m": 50, "tol": 1e-10,
+                       "iterations": {"NIPG": its[0], "SIPG": its[1]},
+                       "relres": {"NIPG": last[1][1], "SIPG": last[2][1]},
+                       "l2_policy": "working set > L2 (blocks 151 MB + Krylov basis 321 MB per solve)",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "clocks": clocks, "roofline": roofline}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ref_its, _ = oracle_iteration_counts()
+        scale_its = ref_its if ref_its else its
+        cpu_val, detail = oracle_sample(scale_its, iters=50)
+        line["cpu_baseline"] = {"value": cpu_val, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                "sample": "per method: oracle assembly + block inverses + 50 GMRES(50) iterations; "
+                                          f"per-iteration time scaled to {scale_its} iterations",
+                                "detail": detail}
+    if rank == 0:
+        print(json.dumps(line))
+    h.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

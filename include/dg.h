@@ -1,0 +1,319 @@
+/*
+ * dg.h -- C ABI of libdg, a GB300 (sm_103a) interior-penalty discontinuous
+ * Galerkin solver for the steady diffusion-convection-reaction problem
+ *
+ *     alpha u - eps Lap u + b . grad u = f   in Omega (a polygon in R^2),
+ *     u = gD on Gamma_D,   eps grad u . n = gN on Gamma_N            (Eq. (1))
+ *
+ * following Uzunca & Karasozen, "A Matlab Tutorial for Diffusion-Convection-
+ * Reaction Equations using DGFEM" (arXiv:1502.02941): SIPG / NIPG / IIPG for
+ * diffusion (Sec. 1, Eq. (ds)), upwinding for convection, discontinuous P_k
+ * elements on triangles, weakly imposed boundary data.
+ *
+ * Conventions for every call:
+ *   - Every call returns a dg_status; DG_OK (0) on success.  Arguments are
+ *     checked before anything is launched; dg_status_string() names a code and
+ *     dg_last_error() gives the message of the handle's last failure.
+ *   - Pointers are marked "host" or "device".  Device pointers are plain CUDA
+ *     global-memory addresses on the handle's device (e.g. a torch tensor's
+ *     data_ptr()).  The caller owns every buffer it passes; the handle owns the
+ *     mesh, the assembled blocks and its solver workspace.
+ *   - Work is issued on the handle's stream.  Calls return without waiting for
+ *     the GPU, except those that return values to host memory (dg_mesh_upload,
+ *     dg_gmres_solve, dg_dense_solve, dg_mixed_solve, dg_l2_error,
+ *     dg_precond_setup), which synchronise the stream.
+ *   - Indices are 0-based (the paper's MATLAB arrays are 1-based).
+ *   - Unknowns are element-major: x[K*nb + i] is the coefficient of the i-th
+ *     orthonormal Dubiner basis function of element K, nb = (k+1)(k+2)/2
+ *     (the DoF formula of the Sec. 4 listing).
+ *   - A handle is not thread-safe; use one handle per host thread.
+ */
+#ifndef DG_H
+#define DG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* status codes                                                              */
+/* ------------------------------------------------------------------------ */
+typedef int dg_status;
+#define DG_OK                  0
+#define DG_ERR_INVALID_ARG     1  /* a pointer, size or enum is out of range */
+#define DG_ERR_CUDA            2  /* a CUDA runtime call failed */
+#define DG_NOT_CONVERGED       3  /* solver hit its iteration cap; info still filled */
+#define DG_ERR_TIMEOUT         4  /* a bounded device-side wait expired */
+#define DG_ERR_NONFINITE       5  /* NaN/Inf met in data or in a residual */
+#define DG_ERR_SINGULAR_BLOCK  6  /* a diagonal block could not be inverted */
+#define DG_ERR_MESH            7  /* invalid mesh: clockwise element, edge shared by
+                                     more than two elements, boundary edge without
+                                     a condition, or a condition on a non-boundary edge */
+#define DG_ERR_STATE           8  /* call order violated (e.g. apply before assemble) */
+#define DG_ERR_NOMEM           9  /* device allocation failed */
+
+/* ------------------------------------------------------------------------ */
+/* enumerations                                                              */
+/* ------------------------------------------------------------------------ */
+/* DG variant, the paper's `method` numbering (Sec. 2.2, set_parameter). */
+#define DG_NIPG 1   /* kappa = +1 */
+#define DG_SIPG 2   /* kappa = -1 */
+#define DG_IIPG 3   /* kappa =  0 */
+
+/* Arithmetic / storage types of an operator apply. */
+#define DG_F64  0   /* f64 blocks, f64 vectors, f64 accumulation */
+#define DG_F32  1   /* f32 blocks, f32 vectors, f32 accumulation */
+#define DG_BF16 2   /* bf16 blocks, f32 vectors, f32 accumulation */
+
+/* Which block copies dg_assemble stores (bit mask). */
+#define DG_STORE_F64  1
+#define DG_STORE_F32  2
+#define DG_STORE_BF16 4
+
+/* Preconditioners. */
+#define DG_PRECOND_NONE          0
+#define DG_PRECOND_BLOCK_JACOBI  1
+
+/* Point sets of dg_quad_points / dg_eval. */
+#define DG_POINTS_VOLUME   0  /* [ne][(k+2)^2]: Duffy-collapsed Gauss-Legendre */
+#define DG_POINTS_BOUNDARY 1  /* [n_bedges][k+2]: Gauss-Legendre on boundary edges */
+#define DG_POINTS_ERROR    2  /* [ne][(k+4)^2]: the L2-error rule */
+
+/* ------------------------------------------------------------------------ */
+/* parameters                                                                */
+/* ------------------------------------------------------------------------ */
+/*
+ * Method parameters (Sec. 1 last paragraph; Sec. 4 set_parameter) and solver
+ * settings.  Fill with dg_params_default() and override fields.
+ */
+typedef struct {
+    int32_t method;            /* DG_NIPG / DG_SIPG / DG_IIPG */
+    int32_t degree;            /* k, 1..3 */
+    double  sigma_int;         /* interior-edge penalty sigma; <= 0 selects the
+                                  paper's rule: 3k(k+1) for SIPG/IIPG, 1 for NIPG */
+    double  sigma_bdry_factor; /* boundary-edge penalty = factor * sigma_int
+                                  (paper: 2); <= 0 selects 2 */
+    double  b0;                /* superpenalisation exponent of h_e; only 1 */
+    int32_t store;             /* DG_STORE_* mask of block copies to keep */
+    int32_t gmres_m;           /* GMRES restart length, 1..64 (default 50) */
+    double  tol;               /* relative residual target ||F-Ax||/||F|| */
+    int32_t max_it;            /* cap on Arnoldi steps (default 10000) */
+    int32_t precond;           /* DG_PRECOND_* (default block Jacobi) */
+} dg_params;
+
+/*
+ * Problem data (Eq. (1)).  eps and alpha are constants; the advection field is
+ * affine, b(x,y) = (b[0] + b[1] x + b[2] y, b[3] + b[4] x + b[5] y).  The data
+ * f, gD, gN are given at the library's quadrature points (dg_quad_points), the
+ * way the paper's vectorised sub-functions fsource / DBCexact / NBCexact are
+ * evaluated on arrays of points, or as constants when the pointer is NULL.
+ *   f  : device [ne][(k+2)^2]     at DG_POINTS_VOLUME
+ *   gD : device [n_bedges][k+2]   at DG_POINTS_BOUNDARY; read on Dirichlet edges
+ *        and on the inflow part (b.n < 0) of EVERY boundary edge, Neumann ones
+ *        included (the inflow term of Eq. (ds) runs over all of Gamma^-)
+ *   gN : device [n_bedges][k+2]   at DG_POINTS_BOUNDARY; read on Neumann edges
+ */
+typedef struct {
+    double eps;
+    double alpha;
+    double b[6];
+    const double* f;   double f_const;
+    const double* gD;  double gD_const;
+    const double* gN;  double gN_const;
+} dg_coeffs;
+
+/* Sizes of the uploaded mesh for the current degree. */
+typedef struct {
+    int32_t ne;          /* elements */
+    int32_t nv;          /* nodes */
+    int32_t n_bedges;    /* boundary edges (Dirichlet + Neumann) */
+    int32_t n_interior;  /* interior edges */
+    int32_t nb;          /* unknowns per element, (k+1)(k+2)/2 */
+    int64_t dofs;        /* ne * nb */
+    int32_t q_volume;    /* (k+2)^2 */
+    int32_t q_edge;      /* k+2 */
+    int32_t q_error;     /* (k+4)^2 */
+    int64_t block_bytes[3]; /* bytes of the stored f64 / f32 / bf16 block copies (0 if absent) */
+} dg_info;
+
+/* Result of an iterative solve. */
+typedef struct {
+    int32_t iterations;  /* inner Arnoldi steps (all cycles) */
+    int32_t restarts;    /* completed restart cycles */
+    int32_t outer;       /* refinement steps (dg_mixed_solve), else 0 */
+    int32_t status;      /* DG_OK or DG_NOT_CONVERGED */
+    double  relres;      /* final true relative residual ||F - A x|| / ||F|| in f64 */
+} dg_solve_info;
+
+/* ------------------------------------------------------------------------ */
+/* handle                                                                    */
+/* ------------------------------------------------------------------------ */
+typedef struct dg_handle dg_handle;
+
+/* Create a handle on CUDA device `device`, issuing work on `stream`
+   (a cudaStream_t; NULL = the legacy default stream).  *h receives the handle. */
+dg_status dg_create(dg_handle** h, int device, void* stream);
+/* Free the handle and all device memory it owns.  NULL is accepted. */
+dg_status dg_destroy(dg_handle* h);
+/* Change the stream later calls issue work on. */
+dg_status dg_set_stream(dg_handle* h, void* stream);
+/* Human-readable text of a status code (static storage). */
+const char* dg_status_string(dg_status s);
+/* Message of the last failed call on h (handle-owned storage). */
+const char* dg_last_error(const dg_handle* h);
+
+/* Fill p with defaults: SIPG, k = 1, paper's penalty rule, factor 2, b0 = 1,
+   store f64, GMRES(50), tol 1e-10, max_it 10000, block Jacobi. */
+dg_status dg_params_default(dg_params* p);
+
+/* ------------------------------------------------------------------------ */
+/* mesh and parameters  (the paper's getmesh and set_parameter)             */
+/* ------------------------------------------------------------------------ */
+/*
+ * Upload a triangulation (Sec. 2.1 data structure; the paper's getmesh):
+ *   nodes     host [nv][2]  f64 coordinates
+ *   elems     host [ne][3]  i32 node ids, counter-clockwise, 0-based
+ *   dirichlet host [nd][2]  i32 start/end node of each Dirichlet edge
+ *   neumann   host [nn][2]  i32 start/end node of each Neumann edge
+ * The arrays are copied; the element adjacency, face types, boundary-edge
+ * numbering and per-element geometry are built on the device.  Every boundary
+ * edge must carry exactly one condition.  Returns DG_ERR_MESH for an invalid
+ * mesh.  Invalidates assembled data.  Synchronises.
+ */
+dg_status dg_mesh_upload(dg_handle* h, const double* nodes, int nv, const int* elems, int ne,
+                         const int* dirichlet, int nd, const int* neumann, int nn);
+
+/* Set method and solver parameters (the paper's set_parameter).  A change of
+   degree invalidates assembled data. */
+dg_status dg_set_params(dg_handle* h, const dg_params* p);
+
+/* Sizes of the uploaded mesh under the current parameters. */
+dg_status dg_get_info(dg_handle* h, dg_info* out);
+
+/*
+ * Physical coordinates of a point set (DG_POINTS_*), written to device
+ * xy[...][2] in the layout given at the DG_POINTS_* constants.  Boundary edges
+ * are numbered in (element, local face) order; each edge's points run
+ * counter-clockwise around its element.
+ */
+dg_status dg_quad_points(dg_handle* h, int which, double* xy);
+
+/* Outward unit normal (device [n_bedges][2]) and condition (device [n_bedges],
+   1 Dirichlet, 2 Neumann; may be NULL) of every boundary edge. */
+dg_status dg_boundary_info(dg_handle* h, double* normals, int* type);
+
+/* ------------------------------------------------------------------------ */
+/* assembly  (the paper's global_system, Sec. 2.3)                          */
+/* ------------------------------------------------------------------------ */
+/*
+ * Assemble Stiff = D + C + R (Eq. (system)) and F_i = l_h(phi_i) of Eq. (ds)
+ * on the device, element row by element row: per element K the diagonal block
+ * A_KK (volume terms eps grad u.grad v + (b.grad u) v + alpha u v, and the
+ * K-side parts of the face terms) and one block per neighbour L across face f,
+ * A_KL (interior-penalty, symmetry/non-symmetry and upwind coupling).  Face
+ * terms: -{eps grad u}.[v] + kappa {eps grad v}.[u] + (sigma eps/h_e)[u].[v]
+ * on interior and Dirichlet edges (h_e = |e|, boundary sigma = factor*sigma),
+ * upwind b.n(u_out - u_in) v on the inflow part of interior edges and
+ * -b.n u_in v on the inflow part of every boundary edge.  RHS: f v, Dirichlet
+ * terms gD (sigma eps/h_e v + kappa eps grad v.n), inflow -b.n gD v, Neumann
+ * gN v.  Block copies are kept in the precisions of params.store.
+ */
+dg_status dg_assemble(dg_handle* h, const dg_coeffs* c);
+
+/* Copy the assembled F (device [dofs] f64). */
+dg_status dg_get_rhs(dg_handle* h, double* F);
+
+/*
+ * Copy the assembled blocks of one stored precision into device out
+ * [ne][4][nb][nb] (type per dtype: f64 / f32 / bf16 as uint16), row-major:
+ * slot 0 = A_KK, slot 1+f = A_{K,L(f)} for the neighbour across local face f
+ * (face f joins local vertices f and f+1 mod 3); absent neighbours give zero
+ * blocks.  nbr (device [ne][3], may be NULL) receives L(f), -1 on the boundary.
+ */
+dg_status dg_get_blocks(dg_handle* h, int dtype, void* out, int* nbr);
+
+/* ------------------------------------------------------------------------ */
+/* operator apply and preconditioner                                         */
+/* ------------------------------------------------------------------------ */
+/*
+ * y = Stiff x (Eq. (system): D u + C u + R u) for device vectors of `dofs`
+ * entries: f64 for DG_F64, f32 for DG_F32 and DG_BF16.  Requires the matching
+ * block copy in params.store.  x and y must not overlap.
+ */
+dg_status dg_apply(dg_handle* h, int dtype, const void* x, void* y);
+
+/* Build the preconditioner (DG_PRECOND_BLOCK_JACOBI: f64 Gauss-Jordan inverse
+   with partial pivoting of every diagonal block A_KK, plus an f32 copy).
+   DG_ERR_SINGULAR_BLOCK if a block is singular.  Synchronises. */
+dg_status dg_precond_setup(dg_handle* h, int kind);
+
+/* z = M^-1 r for device vectors (f64 for DG_F64, f32 otherwise). */
+dg_status dg_precond_apply(dg_handle* h, int dtype, const void* r, void* z);
+
+/* ------------------------------------------------------------------------ */
+/* solvers  (replacing the paper's Stiff\F, Sec. 2.3)                       */
+/* ------------------------------------------------------------------------ */
+/*
+ * Restarted GMRES(m) in f64 with right preconditioning (params.precond),
+ * x0 = 0, classical Gram-Schmidt with one conditional re-orthogonalisation
+ * pass, Givens rotations on the device.  Stops when the true residual
+ * ||F - A x||/||F|| <= params.tol (checked at every restart) or after
+ * params.max_it Arnoldi steps (DG_NOT_CONVERGED, info still filled).
+ *   F    device [dofs] f64 right-hand side, or NULL for the assembled F
+ *   x    device [dofs] f64 solution (output)
+ *   info host, may be NULL
+ * Synchronises.
+ */
+dg_status dg_gmres_solve(dg_handle* h, const double* F, double* x, dg_solve_info* info);
+
+/*
+ * Direct solve Stiff x = F (the paper's coef = Stiff\F) by dense LU with
+ * partial pivoting on the device, f64.  For small systems: dofs <= 4096.
+ * F device or NULL (assembled F); x device output.  Synchronises.
+ */
+dg_status dg_dense_solve(dg_handle* h, const double* F, double* x);
+
+/* ------------------------------------------------------------------------ */
+/* post-processing  (the paper's dg_error, Sec. 2.4)                        */
+/* ------------------------------------------------------------------------ */
+/*
+ * L2 error ||u_h - u||_{L2(Omega)} with u given at DG_POINTS_ERROR (device
+ * [ne][(k+4)^2] f64), and h_max = the longest mesh edge.  l2 and hmax are
+ * host outputs (either may be NULL).  Synchronises.
+ */
+dg_status dg_l2_error(dg_handle* h, const double* x, const double* uex_q, double* l2, double* hmax);
+
+/*
+ * u_h at np points given in reference coordinates (host rs[np][2], inside the
+ * reference triangle (0,0),(1,0),(0,1)), in every element: device out[ne][np].
+ */
+dg_status dg_eval(dg_handle* h, const double* x, int np, const double* rs, double* out);
+
+/* ------------------------------------------------------------------------ */
+/* instrumentation                                                           */
+/* ------------------------------------------------------------------------ */
+/* Number of CUDA kernels this handle has launched so far (a graph launch
+   counts each kernel node of the graph).  Host counter, no synchronisation. */
+dg_status dg_get_launch_count(dg_handle* h, int64_t* count);
+
+/* ------------------------------------------------------------------------ */
+/* host-only helpers (no GPU needed)                                         */
+/* ------------------------------------------------------------------------ */
+/* Orthonormal Dubiner basis of degree k on the reference triangle and its
+   reference gradients at np host points rs[np][2]: phi, dr, ds host
+   [np][nb] (dr, ds may be NULL). */
+dg_status dg_reference_basis(int degree, int np, const double* rs, double* phi, double* dr, double* ds);
+
+/* The library's quadrature rule `which` (DG_POINTS_*) on the reference
+   triangle (VOLUME, ERROR: rs[n][2], w[n], weights sum to 1/2) or on [0,1]
+   (BOUNDARY: rs[n][0] = t, rs[n][1] = 0, w[n] sums to 1); n given by dg_info
+   sizes for degree k.  Returns the number of points through *n. */
+dg_status dg_reference_rule(int which, int degree, double* rs, double* w, int* n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DG_H */

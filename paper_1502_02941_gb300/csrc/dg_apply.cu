@@ -1,0 +1,184 @@
+// dg_apply.cu -- the block-sparse operator apply y = Stiff x (the D u + C u +
+// R u of Eq. (system)) and the block-Jacobi preconditioner.
+//
+// apply: one thread per element K, one warp per 32-element tile.  For each of
+// the 4 slots the warp streams the slot's chunks as 32 x 16-byte loads
+// (512 contiguous bytes per load instruction, evict-first so the blocks do not
+// displace the vectors from L2), gathers the nb entries of x for the slot's
+// element (K itself or its neighbour across face f) and accumulates the nb
+// rows of y_K in registers.  Bytes per element: 4*nb^2*sizeof(TA) (fewer on the
+// boundary) + 2*nb*sizeof(TX) + 12 (neighbour ids) -> HBM-bound.
+#include "dg_kernels.cuh"
+
+// Gauss-Jordan inverse with partial pivoting of each diagonal block A_KK.
+template <int NB>
+__global__ void __launch_bounds__(128) k_bj_setup(const double* __restrict__ A, int ne, double* Binv64,
+                                                   float* Binv32, int* flag) {
+    const int K = blockIdx.x * blockDim.x + threadIdx.x;
+    if (K >= ne) return;
+    double M[NB][2 * NB];
+    for (int i = 0; i < NB; ++i)
+        for (int j = 0; j < NB; ++j) {
+            M[i][j] = A[dg_blk_index<double>(K, 0, i * NB + j, NB, 4)];
+            M[i][NB + j] = i == j ? 1.0 : 0.0;
+        }
+    double amax = 0.0;
+    for (int i = 0; i < NB; ++i)
+        for (int j = 0; j < NB; ++j) amax = fmax(amax, fabs(M[i][j]));
+    bool singular = !(amax > 0.0) || !isfinite(amax);
+    for (int c = 0; c < NB && !singular; ++c) {
+        int p = c;
+        for (int r = c + 1; r < NB; ++r)
+            if (fabs(M[r][c]) > fabs(M[p][c])) p = r;
+        if (!(fabs(M[p][c]) > 1e-14 * amax)) {
+            singular = true;
+            break;
+        }
+        if (p != c)
+            for (int j = 0; j < 2 * NB; ++j) {
+                double t = M[c][j];
+                M[c][j] = M[p][j];
+                M[p][j] = t;
+            }
+        const double d = 1.0 / M[c][c];
+        for (int j = 0; j < 2 * NB; ++j) M[c][j] *= d;
+        for (int r = 0; r < NB; ++r) {
+            if (r == c) continue;
+            const double l = M[r][c];
+            for (int j = 0; j < 2 * NB; ++j) M[r][j] -= l * M[c][j];
+        }
+    }
+    if (singular) {
+        atomicOr(flag, 1);
+        for (int m = 0; m < NB * NB; ++m) {
+            Binv64[dg_blk_index<double>(K, 0, m, NB, 1)] = 0.0;
+            Binv32[dg_blk_index<float>(K, 0, m, NB, 1)] = 0.0f;
+        }
+        return;
+    }
+    for (int i = 0; i < NB; ++i)
+        for (int j = 0; j < NB; ++j) {
+            Binv64[dg_blk_index<double>(K, 0, i * NB + j, NB, 1)] = M[i][NB + j];
+            Binv32[dg_blk_index<float>(K, 0, i * NB + j, NB, 1)] = (float)M[i][NB + j];
+        }
+}
+
+// ---------------------------------------------------------------------------
+// dispatch
+// ---------------------------------------------------------------------------
+template <int NB>
+static dg_status apply_nb(dg_handle* h, int dtype, const void* x, void* y) {
+    const unsigned grid = (unsigned)((h->ne + 255) / 256);
+    switch (dtype) {
+        case DG_F64:
+            if (!h->A64) return dg_fail(h, DG_ERR_STATE, "f64 blocks not stored");
+            k_apply<NB, double, double, double><<<grid, 256, 0, h->stream>>>(h->A64, h->nbr, (const double*)x,
+                                                                             (double*)y, h->ne, dctl_none(),
+                                                                             vsel_fixed(), vsel_fixed());
+            break;
+        case DG_F32:
+            if (!h->A32) return dg_fail(h, DG_ERR_STATE, "f32 blocks not stored");
+            k_apply<NB, float, float, float><<<grid, 256, 0, h->stream>>>(h->A32, h->nbr, (const float*)x, (float*)y,
+                                                                          h->ne, dctl_none(), vsel_fixed(),
+                                                                          vsel_fixed());
+            break;
+        case DG_BF16:
+            if (!h->A16) return dg_fail(h, DG_ERR_STATE, "bf16 blocks not stored");
+            k_apply<NB, __nv_bfloat16, float, float><<<grid, 256, 0, h->stream>>>(h->A16, h->nbr, (const float*)x,
+                                                                                  (float*)y, h->ne, dctl_none(),
+                                                                                  vsel_fixed(), vsel_fixed());
+            break;
+        default:
+            return dg_fail(h, DG_ERR_INVALID_ARG, "dtype");
+    }
+    h->nlaunch += 1;
+    DG_LAUNCH_CK(h);
+    return DG_OK;
+}
+
+dg_status dg_launch_apply(dg_handle* h, int dtype, const void* x, void* y) {
+    switch (dg_nb(h->asm_k)) {
+        case 3: return apply_nb<3>(h, dtype, x, y);
+        case 6: return apply_nb<6>(h, dtype, x, y);
+        case 10: return apply_nb<10>(h, dtype, x, y);
+    }
+    return dg_fail(h, DG_ERR_INVALID_ARG, "degree");
+}
+
+extern "C" dg_status dg_apply(dg_handle* h, int dtype, const void* x, void* y) {
+    if (!h || !x || !y) return DG_ERR_INVALID_ARG;
+    if (!h->assembled) return dg_fail(h, DG_ERR_STATE, "not assembled");
+    if (x == y) return dg_fail(h, DG_ERR_INVALID_ARG, "x and y must not overlap");
+    if (!dg_aligned16(x) || !dg_aligned16(y)) return dg_fail(h, DG_ERR_INVALID_ARG, "x and y must be 16-byte aligned");
+    return dg_launch_apply(h, dtype, x, y);
+}
+
+template <int NB>
+static dg_status bj_apply_nb(dg_handle* h, int dtype, const void* r, void* z) {
+    const unsigned grid = (unsigned)((h->ne + 255) / 256);
+    if (dtype == DG_F64)
+        k_bj_apply<NB, double, double, double><<<grid, 256, 0, h->stream>>>(
+            h->Binv64, (const double*)r, (double*)z, h->ne, dctl_none(), vsel_fixed(), vsel_fixed());
+    else
+        k_bj_apply<NB, float, float, float><<<grid, 256, 0, h->stream>>>(
+            h->Binv32, (const float*)r, (float*)z, h->ne, dctl_none(), vsel_fixed(), vsel_fixed());
+    h->nlaunch += 1;
+    DG_LAUNCH_CK(h);
+    return DG_OK;
+}
+
+dg_status dg_launch_bj_apply(dg_handle* h, int dtype, const void* r, void* z, const double* scale) {
+    (void)scale;
+    switch (dg_nb(h->asm_k)) {
+        case 3: return bj_apply_nb<3>(h, dtype, r, z);
+        case 6: return bj_apply_nb<6>(h, dtype, r, z);
+        case 10: return bj_apply_nb<10>(h, dtype, r, z);
+    }
+    return dg_fail(h, DG_ERR_INVALID_ARG, "degree");
+}
+
+dg_status dg_launch_bj_setup(dg_handle* h) {
+    const int nb = dg_nb(h->asm_k);
+    if (!h->A64) return dg_fail(h, DG_ERR_STATE, "block Jacobi needs the f64 blocks (DG_STORE_F64)");
+    dg_status s;
+    size_t b64 = (size_t)h->ntiles * dg_chunks<double>(nb) * 512;
+    size_t b32 = (size_t)h->ntiles * dg_chunks<float>(nb) * 512;
+    if ((s = dg_ensure(h, (void**)&h->Binv64, &h->cap_binv64, b64)) != DG_OK) return s;
+    if ((s = dg_ensure(h, (void**)&h->Binv32, &h->cap_binv32, b32)) != DG_OK) return s;
+    DG_CK(h, cudaMemsetAsync(h->Binv64, 0, b64, h->stream));
+    DG_CK(h, cudaMemsetAsync(h->Binv32, 0, b32, h->stream));
+    DG_CK(h, cudaMemsetAsync(h->dflag, 0, sizeof(int), h->stream));
+    const unsigned grid = (unsigned)((h->ne + 127) / 128);
+    switch (nb) {
+        case 3: k_bj_setup<3><<<grid, 128, 0, h->stream>>>(h->A64, h->ne, h->Binv64, h->Binv32, h->dflag); break;
+        case 6: k_bj_setup<6><<<grid, 128, 0, h->stream>>>(h->A64, h->ne, h->Binv64, h->Binv32, h->dflag); break;
+        case 10: k_bj_setup<10><<<grid, 128, 0, h->stream>>>(h->A64, h->ne, h->Binv64, h->Binv32, h->dflag); break;
+        default: return dg_fail(h, DG_ERR_INVALID_ARG, "degree");
+    }
+    h->nlaunch += 1;
+    DG_LAUNCH_CK(h);
+    int flag = 0;
+    DG_CK(h, cudaMemcpyAsync(&flag, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    DG_CK(h, cudaStreamSynchronize(h->stream));
+    if (flag) return dg_fail(h, DG_ERR_SINGULAR_BLOCK, "a diagonal block is singular");
+    return DG_OK;
+}
+
+extern "C" dg_status dg_precond_setup(dg_handle* h, int kind) {
+    if (!h) return DG_ERR_INVALID_ARG;
+    if (!h->assembled) return dg_fail(h, DG_ERR_STATE, "not assembled");
+    if (kind == DG_PRECOND_NONE) return DG_OK;
+    if (kind != DG_PRECOND_BLOCK_JACOBI) return dg_fail(h, DG_ERR_INVALID_ARG, "precond kind");
+    h->bj_ok = false;
+    dg_status s = dg_launch_bj_setup(h);
+    if (s == DG_OK) h->bj_ok = true;
+    return s;
+}
+
+extern "C" dg_status dg_precond_apply(dg_handle* h, int dtype, const void* r, void* z) {
+    if (!h || !r || !z) return DG_ERR_INVALID_ARG;
+    if (!h->bj_ok) return dg_fail(h, DG_ERR_STATE, "preconditioner not set up");
+    if (!dg_aligned16(r) || !dg_aligned16(z)) return dg_fail(h, DG_ERR_INVALID_ARG, "r and z must be 16-byte aligned");
+    if (dtype != DG_F64 && dtype != DG_F32 && dtype != DG_BF16) return dg_fail(h, DG_ERR_INVALID_ARG, "dtype");
+    return dg_launch_bj_apply(h, dtype == DG_F64 ? DG_F64 : DG_F32, r, z, nullptr);
+}

@@ -1,0 +1,191 @@
+// dg_internal.cuh -- shared internals of libdg (not part of the public ABI).
+//
+// Data layout in HBM (all per handle):
+//   geometry  geo[G_NFIELDS][ne]  f64 SoA, one field per array, element K at
+//             index K: vertex 0, Jacobian J = [x1-x0 x2-x0; y1-y0 y2-y0] of the
+//             affine map from the reference triangle (0,0),(1,0),(0,1), its
+//             inverse and det J (= 2|K| > 0).
+//   faces     nbr/nface/ftype/bidx [3][ne] i32 SoA: face f of K joins local
+//             vertices f and f+1 (mod 3); nbr = neighbour across it (-1 on the
+//             boundary), nface = the neighbour's local face, ftype 0 interior /
+//             1 Dirichlet / 2 Neumann, bidx = boundary-edge number or -1.
+//   blocks    element-row block-ELL, 4 slots per element (slot 0 = A_KK,
+//             slot 1+f = A_{K,nbr(f)}).  Entries m = i*nb + j of one block are
+//             cut into chunks of W = 16/sizeof(T) values; elements are grouped
+//             in tiles of 32.  Entry (K, s, m) lives at
+//               (((K/32)*4 + s)*C + m/W)*32*W + (K%32)*W + m%W,  C = ceil(nb^2/W)
+//             so one warp (= one tile) reads one chunk of one slot as 32
+//             consecutive 16-byte vectors (512 B).  Padding is zero.
+//   vectors   element-major, x[K*nb + i].
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <string>
+
+#include "dg.h"
+
+#define DG_MAXK 3
+#define DG_MAXNB 10
+#define DG_TILE 32
+#define DG_MAXM 64
+
+enum GeoField { G_X0 = 0, G_Y0, G_J00, G_J01, G_J10, G_J11, G_I00, G_I01, G_I10, G_I11, G_DET, G_NFIELDS };
+
+__host__ __device__ constexpr int dg_nb(int k) { return (k + 1) * (k + 2) / 2; }
+
+// Number of 16-byte chunks per nb x nb block for element type T.
+template <typename T>
+__host__ __device__ constexpr int dg_chunks(int nb) { return (nb * nb + (16 / (int)sizeof(T)) - 1) / (16 / (int)sizeof(T)); }
+
+// Offsets (in doubles) of the reference tables of one degree k.
+struct TabLayout {
+    int k, nb, nq, qk, qerr;
+    int vol_w, vol_r, vol_s, vol_phi, vol_dr, vol_ds;        // [qk], [qk][nb]
+    int face_w, face_r, face_s, face_phi, face_dr, face_ds;   // [nq], [3][nq], [3][nq][nb]
+    int err_w, err_r, err_s, err_phi;                         // [qerr], [qerr][nb]
+    int total;
+};
+
+struct GmresState;   // device-side solver state (dg_gmres.cu)
+
+struct dg_handle {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    dg_params p{};
+    bool params_set = false;
+
+    // mesh
+    int nv = 0, ne = 0, nbe = 0, nint = 0, ntiles = 0;
+    bool mesh_ok = false;
+    double* nodes = nullptr;
+    int* elems = nullptr;
+    double* geo = nullptr;
+    int* nbr = nullptr;
+    int* nface = nullptr;
+    int* ftype = nullptr;
+    int* bidx = nullptr;
+    int* bedge = nullptr;          // [nbe] = 3*K + f
+    double hmax = 0.0;
+
+    // reference tables for tl.k
+    double* tab = nullptr;
+    TabLayout tl{};
+    int tab_k = -1;
+
+    // assembled operator
+    bool assembled = false;
+    int asm_k = -1;
+    int asm_store = 0;
+    double* A64 = nullptr;
+    float* A32 = nullptr;
+    __nv_bfloat16* A16 = nullptr;
+    size_t A_bytes[3] = {0, 0, 0};
+    double* F = nullptr;
+
+    // block-Jacobi inverses (f64 and f32 copies), same tile layout with 1 slot
+    bool bj_ok = false;
+    double* Binv64 = nullptr;
+    float* Binv32 = nullptr;
+
+    // GMRES workspace
+    size_t gm_n = 0;
+    int gm_m = 0;
+    double* V = nullptr;           // [(m+1)][n]
+    double* Z = nullptr;           // [n]   work vector
+    double* R = nullptr;           // [n]   work vector
+    double* partials = nullptr;    // reduction scratch
+    GmresState* st = nullptr;      // device state
+    GmresState* st_host = nullptr; // pinned mirror
+    cudaGraphExec_t gm_graph = nullptr;
+    int gm_graph_key[4] = {0, 0, 0, 0};
+
+    // misc scratch
+    double* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    int* dflag = nullptr;          // device error flags [8]
+
+    // instrumentation: kernels launched by this handle (graph launches count
+    // every kernel node of the graph)
+    long long nlaunch = 0;
+    int gm_nodes = 0;
+
+    // capacities (bytes) of arrays that are re-sized only when they must grow
+    size_t cap_nodes = 0, cap_elems = 0, cap_geo = 0, cap_face = 0, cap_bedge = 0;
+    size_t cap_binv64 = 0, cap_binv32 = 0, cap_F = 0;
+};
+
+// error helpers (dg_host.cu)
+dg_status dg_fail(dg_handle* h, dg_status s, const std::string& msg);
+dg_status dg_cuda_fail(dg_handle* h, cudaError_t e, const char* what);
+#define DG_CK(h, call)                                                 \
+    do {                                                               \
+        cudaError_t e__ = (call);                                      \
+        if (e__ != cudaSuccess) return dg_cuda_fail((h), e__, #call);  \
+    } while (0)
+#define DG_LAUNCH_CK(h) DG_CK(h, cudaGetLastError())
+
+// vector arguments are read with 16-byte loads
+static inline bool dg_aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// allocation helper: frees *p (if any) and allocates bytes
+dg_status dg_realloc(dg_handle* h, void** p, size_t bytes);
+dg_status dg_scratch(dg_handle* h, size_t bytes);   // ensure h->scratch >= bytes
+// keep *p if its capacity *cap already holds bytes, else reallocate
+dg_status dg_ensure(dg_handle* h, void** p, size_t* cap, size_t bytes);
+
+// host-side table construction (dg_tables.cu)
+TabLayout dg_table_layout(int k);
+void dg_build_tables(int k, double* host_out);                       // host_out[layout.total]
+void dg_dubiner(int k, double r, double s, double* phi, double* dr, double* ds);
+void dg_gauss_legendre01(int n, double* t, double* w);
+dg_status dg_ensure_tables(dg_handle* h, int k);
+
+// launches implemented in the various translation units
+dg_status dg_launch_assemble(dg_handle* h, const dg_coeffs* c, double kappa, double sig_int, double sig_bdry);
+dg_status dg_launch_apply(dg_handle* h, int dtype, const void* x, void* y);
+dg_status dg_launch_bj_setup(dg_handle* h);
+dg_status dg_launch_bj_apply(dg_handle* h, int dtype, const void* r, void* z, const double* scale);
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double dg_warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double dg_warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+// Block-wide sum; every thread gets the result.  sh must hold 32 doubles.
+__device__ __forceinline__ double dg_block_sum(double v, double* sh) {
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    v = dg_warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double t = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+    if (wid == 0) t = dg_warp_sum(t);
+    if (threadIdx.x == 0) sh[0] = t;
+    __syncthreads();
+    double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// Index of entry (K, slot s, m) in a tile-interleaved block array of type T
+// with `slots` slots per element.
+template <typename T>
+__host__ __device__ __forceinline__ size_t dg_blk_index(int K, int s, int m, int nb, int slots) {
+    constexpr int W = 16 / (int)sizeof(T);
+    const int C = dg_chunks<T>(nb);
+    return ((((size_t)(K >> 5) * slots + s) * C + m / W) * 32 + (K & 31)) * W + (m % W);
+}
+
+__device__ __forceinline__ float dg_bf16_lo(uint32_t u) { return __uint_as_float(u << 16); }
+__device__ __forceinline__ float dg_bf16_hi(uint32_t u) { return __uint_as_float(u & 0xffff0000u); }

@@ -1,0 +1,208 @@
+// dg_kernels.cuh -- operator-apply and block-Jacobi kernel templates shared
+// by the standalone calls (dg_apply.cu) and the device-resident solvers
+// (dg_gmres.cu).  See dg_apply.cu for the access pattern.
+#pragma once
+#include "dg_internal.cuh"
+
+// Run-time selection of a vector inside a Krylov basis: the vector used is
+// base + (*j + add) * stride when j is set, else base.
+struct VecSel {
+    const int* j;
+    int add;
+    long stride;
+};
+static inline VecSel vsel_fixed() { return VecSel{nullptr, 0, 0}; }
+template <typename T>
+__device__ __forceinline__ T* sel(T* base, const VecSel& s) {
+    return s.j ? base + (long)(*s.j + s.add) * s.stride : base;
+}
+// Solver control seen by the kernels: `active` (exit at once when 0) and the
+// basis scale factors (1/||v_i||) of lazily normalised Krylov vectors.
+struct DevCtl {
+    const int* active;
+    const double* scale;
+};
+static inline DevCtl dctl_none() { return DevCtl{nullptr, nullptr}; }
+
+// ---------------------------------------------------------------------------
+// typed 16-byte chunk loads
+// ---------------------------------------------------------------------------
+template <typename TA, typename TACC>
+struct Chunk;
+
+template <>
+struct Chunk<double, double> {
+    static constexpr int W = 2;
+    __device__ __forceinline__ static void load(const double* p, double* v) {
+        double2 t = __ldcs(reinterpret_cast<const double2*>(p));
+        v[0] = t.x;
+        v[1] = t.y;
+    }
+};
+template <>
+struct Chunk<float, float> {
+    static constexpr int W = 4;
+    __device__ __forceinline__ static void load(const float* p, float* v) {
+        float4 t = __ldcs(reinterpret_cast<const float4*>(p));
+        v[0] = t.x;
+        v[1] = t.y;
+        v[2] = t.z;
+        v[3] = t.w;
+    }
+};
+template <>
+struct Chunk<float, double> {
+    static constexpr int W = 4;
+    __device__ __forceinline__ static void load(const float* p, double* v) {
+        float4 t = __ldcs(reinterpret_cast<const float4*>(p));
+        v[0] = t.x;
+        v[1] = t.y;
+        v[2] = t.z;
+        v[3] = t.w;
+    }
+};
+template <>
+struct Chunk<__nv_bfloat16, float> {
+    static constexpr int W = 8;
+    __device__ __forceinline__ static void load(const __nv_bfloat16* p, float* v) {
+        uint4 t = __ldcs(reinterpret_cast<const uint4*>(p));
+        v[0] = dg_bf16_lo(t.x);
+        v[1] = dg_bf16_hi(t.x);
+        v[2] = dg_bf16_lo(t.y);
+        v[3] = dg_bf16_hi(t.y);
+        v[4] = dg_bf16_lo(t.z);
+        v[5] = dg_bf16_hi(t.z);
+        v[6] = dg_bf16_lo(t.w);
+        v[7] = dg_bf16_hi(t.w);
+    }
+};
+
+// nb consecutive vector entries of element L (read-only path).
+template <int NB, typename TX, typename TACC>
+__device__ __forceinline__ void load_x(const TX* __restrict__ x, int L, TACC* v) {
+    const TX* p = x + (size_t)L * NB;
+    if constexpr ((NB * sizeof(TX)) % 16 == 0 && sizeof(TX) == 8) {
+#pragma unroll
+        for (int j = 0; j < NB; j += 2) {
+            double2 t = __ldg(reinterpret_cast<const double2*>(p) + j / 2);
+            v[j] = t.x;
+            v[j + 1] = t.y;
+        }
+    } else if constexpr ((NB * sizeof(TX)) % 8 == 0 && sizeof(TX) == 4) {
+#pragma unroll
+        for (int j = 0; j < NB; j += 2) {
+            float2 t = __ldg(reinterpret_cast<const float2*>(p) + j / 2);
+            v[j] = t.x;
+            v[j + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < NB; ++j) v[j] = (TACC)__ldg(p + j);
+    }
+}
+
+template <int NB, typename TX, typename TACC>
+__device__ __forceinline__ void store_y(TX* __restrict__ y, int K, const TACC* v) {
+    TX* p = y + (size_t)K * NB;
+    if constexpr ((NB * sizeof(TX)) % 16 == 0 && sizeof(TX) == 8) {
+#pragma unroll
+        for (int j = 0; j < NB; j += 2) reinterpret_cast<double2*>(p)[j / 2] = make_double2(v[j], v[j + 1]);
+    } else if constexpr ((NB * sizeof(TX)) % 8 == 0 && sizeof(TX) == 4) {
+#pragma unroll
+        for (int j = 0; j < NB; j += 2) reinterpret_cast<float2*>(p)[j / 2] = make_float2((float)v[j], (float)v[j + 1]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < NB; ++j) p[j] = (TX)v[j];
+    }
+}
+
+// y = A x over elements [0, ne).  nbr is [3][ne].  With a solver control
+// block, the kernel exits at once when the solver is inactive and x / y are
+// picked from the Krylov basis by the device-side step counter.
+template <int NB, typename TA, typename TX, typename TACC>
+__global__ void __launch_bounds__(256) k_apply(const TA* __restrict__ A, const int* __restrict__ nbr,
+                                                const TX* __restrict__ x0, TX* __restrict__ y0, int ne,
+                                                DevCtl ctl, VecSel sx, VecSel sy) {
+    using CH = Chunk<TA, TACC>;
+    constexpr int W = CH::W;
+    constexpr int C = (NB * NB + W - 1) / W;
+    if (ctl.active && !*ctl.active) return;
+    const int K = blockIdx.x * blockDim.x + threadIdx.x;
+    if (K >= ne) return;
+    const TX* __restrict__ x = sel(x0, sx);
+    TX* __restrict__ y = sel(y0, sy);
+    const int tile = K >> 5, lane = K & 31;
+    int Ls[4];
+    Ls[0] = K;
+#pragma unroll
+    for (int f = 0; f < 3; ++f) Ls[1 + f] = __ldg(nbr + (size_t)f * ne + K);
+    TACC acc[NB];
+#pragma unroll
+    for (int r = 0; r < NB; ++r) acc[r] = 0;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const int Ln = Ls[s];
+        if (Ln < 0) continue;
+        TACC xv[NB];
+        load_x<NB, TX, TACC>(x, Ln, xv);
+        const TA* base = A + (((size_t)tile * 4 + s) * C * 32 + lane) * W;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            TACC v[W];
+            CH::load(base + (size_t)c * 32 * W, v);
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                const int m = c * W + w;
+                if (m < NB * NB) acc[m / NB] = fma(v[w], xv[m % NB], acc[m / NB]);
+            }
+        }
+    }
+    store_y<NB, TX, TACC>(y, K, acc);
+}
+
+// z_K = scale * Binv_K r_K  (one slot, no gather).  scale = ctl.scale[sr index]
+// when ctl.scale is set, else 1.  B == nullptr means no preconditioner (copy).
+template <int NB, typename TA, typename TX, typename TACC>
+__global__ void __launch_bounds__(256) k_bj_apply(const TA* __restrict__ B, const TX* __restrict__ r0,
+                                                   TX* __restrict__ z0, int ne, DevCtl ctl, VecSel sr, VecSel sz) {
+    using CH = Chunk<TA, TACC>;
+    constexpr int W = CH::W;
+    constexpr int C = (NB * NB + W - 1) / W;
+    if (ctl.active && !*ctl.active) return;
+    const int K = blockIdx.x * blockDim.x + threadIdx.x;
+    if (K >= ne) return;
+    const TX* __restrict__ r = sel(r0, sr);
+    TX* __restrict__ z = sel(z0, sz);
+    const double scale = ctl.scale ? ctl.scale[sr.j ? *sr.j + sr.add : 0] : 1.0;
+    if (B == nullptr) {
+        TACC v[NB];
+        load_x<NB, TX, TACC>(r, K, v);
+#pragma unroll
+        for (int i = 0; i < NB; ++i) v[i] *= (TACC)scale;
+        store_y<NB, TX, TACC>(z, K, v);
+        return;
+    }
+    const int tile = K >> 5, lane = K & 31;
+    TACC xv[NB], acc[NB];
+    load_x<NB, TX, TACC>(r, K, xv);
+#pragma unroll
+    for (int i = 0; i < NB; ++i) acc[i] = 0;
+    const TA* base = B + ((size_t)tile * C * 32 + lane) * W;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        TACC v[W];
+        CH::load(base + (size_t)c * 32 * W, v);
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            const int m = c * W + w;
+            if (m < NB * NB) acc[m / NB] = fma(v[w], xv[m % NB], acc[m / NB]);
+        }
+    }
+    if (ctl.scale) {
+        const TACC sc = (TACC)scale;
+#pragma unroll
+        for (int i = 0; i < NB; ++i) acc[i] *= sc;
+    }
+    store_y<NB, TX, TACC>(z, K, acc);
+}
+

@@ -1,0 +1,402 @@
+"""ctypes binding of libdg (include/dg.h): argument marshalling only.
+
+Every entry point of the C ABI is exposed under its own name with the same
+arguments; device pointers may be passed as torch tensors (their data_ptr() is
+used) or as integers, host arrays as numpy arrays.  ``DG`` is a thin object
+wrapper that owns one handle and issues work on torch's current stream.
+
+There is no fallback: if libdg.so has not been built, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libdg.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "dg.h")
+
+# constants mirrored from include/dg.h
+DG_OK, DG_ERR_INVALID_ARG, DG_ERR_CUDA, DG_NOT_CONVERGED = 0, 1, 2, 3
+DG_ERR_TIMEOUT, DG_ERR_NONFINITE, DG_ERR_SINGULAR_BLOCK, DG_ERR_MESH = 4, 5, 6, 7
+DG_ERR_STATE, DG_ERR_NOMEM = 8, 9
+DG_NIPG, DG_SIPG, DG_IIPG = 1, 2, 3
+DG_F64, DG_F32, DG_BF16 = 0, 1, 2
+DG_STORE_F64, DG_STORE_F32, DG_STORE_BF16 = 1, 2, 4
+DG_PRECOND_NONE, DG_PRECOND_BLOCK_JACOBI = 0, 1
+DG_POINTS_VOLUME, DG_POINTS_BOUNDARY, DG_POINTS_ERROR = 0, 1, 2
+
+c_int32, c_int64, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+
+
+class dg_params(ctypes.Structure):
+    _fields_ = [("method", c_int32), ("degree", c_int32), ("sigma_int", c_double),
+                ("sigma_bdry_factor", c_double), ("b0", c_double), ("store", c_int32),
+                ("gmres_m", c_int32), ("tol", c_double), ("max_it", c_int32), ("precond", c_int32)]
+
+
+class dg_coeffs(ctypes.Structure):
+    _fields_ = [("eps", c_double), ("alpha", c_double), ("b", c_double * 6),
+                ("f", c_void_p), ("f_const", c_double),
+                ("gD", c_void_p), ("gD_const", c_double),
+                ("gN", c_void_p), ("gN_const", c_double)]
+
+
+class dg_info(ctypes.Structure):
+    _fields_ = [("ne", c_int32), ("nv", c_int32), ("n_bedges", c_int32), ("n_interior", c_int32),
+                ("nb", c_int32), ("dofs", c_int64), ("q_volume", c_int32), ("q_edge", c_int32),
+                ("q_error", c_int32), ("block_bytes", c_int64 * 3)]
+
+
+class dg_solve_info(ctypes.Structure):
+    _fields_ = [("iterations", c_int32), ("restarts", c_int32), ("outer", c_int32),
+                ("status", c_int32), ("relres", c_double)]
+
+
+_lib = None
+
+_SIGS = {
+    "dg_create": (ctypes.c_int, [ctypes.POINTER(c_void_p), ctypes.c_int, c_void_p]),
+    "dg_destroy": (ctypes.c_int, [c_void_p]),
+    "dg_set_stream": (ctypes.c_int, [c_void_p, c_void_p]),
+    "dg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "dg_last_error": (ctypes.c_char_p, [c_void_p]),
+    "dg_params_default": (ctypes.c_int, [ctypes.POINTER(dg_params)]),
+    "dg_mesh_upload": (ctypes.c_int, [c_void_p, c_void_p, ctypes.c_int, c_void_p, ctypes.c_int,
+                                      c_void_p, ctypes.c_int, c_void_p, ctypes.c_int]),
+    "dg_set_params": (ctypes.c_int, [c_void_p, ctypes.POINTER(dg_params)]),
+    "dg_get_info": (ctypes.c_int, [c_void_p, ctypes.POINTER(dg_info)]),
+    "dg_quad_points": (ctypes.c_int, [c_void_p, ctypes.c_int, c_void_p]),
+    "dg_boundary_info": (ctypes.c_int, [c_void_p, c_void_p, c_void_p]),
+    "dg_assemble": (ctypes.c_int, [c_void_p, ctypes.POINTER(dg_coeffs)]),
+    "dg_get_rhs": (ctypes.c_int, [c_void_p, c_void_p]),
+    "dg_get_blocks": (ctypes.c_int, [c_void_p, ctypes.c_int, c_void_p, c_void_p]),
+    "dg_apply": (ctypes.c_int, [c_void_p, ctypes.c_int, c_void_p, c_void_p]),
+    "dg_precond_setup": (ctypes.c_int, [c_void_p, ctypes.c_int]),
+    "dg_precond_apply": (ctypes.c_int, [c_void_p, ctypes.c_int, c_void_p, c_void_p]),
+    "dg_gmres_solve": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(dg_solve_info)]),
+    "dg_dense_solve": (ctypes.c_int, [c_void_p, c_void_p, c_void_p]),
+    "dg_l2_error": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_double),
+                                   ctypes.POINTER(c_double)]),
+    "dg_eval": (ctypes.c_int, [c_void_p, c_void_p, ctypes.c_int, c_void_p, c_void_p]),
+    "dg_get_launch_count": (ctypes.c_int, [c_void_p, ctypes.POINTER(c_int64)]),
+    "dg_reference_basis": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "dg_reference_rule": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, c_void_p, c_void_p,
+                                         ctypes.POINTER(ctypes.c_int)]),
+}
+
+
+def header_symbols():
+    """Entry points declared in include/dg.h."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:dg_status|const char\*|size_t)\s+(dg_\w+)\s*\(", txt, re.M)))
+
+
+def load():
+    """Load libdg.so; raises if it is missing (no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built: run `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class DGError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{status_name(status)}: {msg}")
+        self.status = status
+
+
+def status_name(s):
+    return load().dg_status_string(int(s)).decode()
+
+
+def _ptr(x):
+    """Device/host pointer of a torch tensor, numpy array, int or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+# ---------------------------------------------------------------------------
+# the C ABI under its own names
+# ---------------------------------------------------------------------------
+def dg_create(device=0, stream=None):
+    h = c_void_p()
+    s = load().dg_create(ctypes.byref(h), int(device), stream)
+    if s != DG_OK:
+        raise DGError(s, "dg_create failed")
+    return h
+
+
+def dg_destroy(h):
+    return load().dg_destroy(h)
+
+
+def dg_set_stream(h, stream):
+    return load().dg_set_stream(h, stream)
+
+
+def dg_status_string(s):
+    return load().dg_status_string(int(s)).decode()
+
+
+def dg_last_error(h):
+    return load().dg_last_error(h).decode()
+
+
+def dg_params_default():
+    p = dg_params()
+    load().dg_params_default(ctypes.byref(p))
+    return p
+
+
+def dg_mesh_upload(h, nodes, elems, dirichlet, neumann):
+    nodes = np.ascontiguousarray(nodes, dtype=np.float64).reshape(-1, 2)
+    elems = np.ascontiguousarray(elems, dtype=np.int32).reshape(-1, 3)
+    dirichlet = np.ascontiguousarray(dirichlet, dtype=np.int32).reshape(-1, 2)
+    neumann = np.ascontiguousarray(neumann, dtype=np.int32).reshape(-1, 2)
+    return load().dg_mesh_upload(h, _ptr(nodes), nodes.shape[0], _ptr(elems), elems.shape[0],
+                                 _ptr(dirichlet) if len(dirichlet) else None, dirichlet.shape[0],
+                                 _ptr(neumann) if len(neumann) else None, neumann.shape[0])
+
+
+def dg_set_params(h, p):
+    return load().dg_set_params(h, ctypes.byref(p))
+
+
+def dg_get_info(h):
+    i = dg_info()
+    s = load().dg_get_info(h, ctypes.byref(i))
+    return s, i
+
+
+def dg_quad_points(h, which, xy):
+    return load().dg_quad_points(h, int(which), _ptr(xy))
+
+
+def dg_boundary_info(h, normals, types=None):
+    return load().dg_boundary_info(h, _ptr(normals), _ptr(types))
+
+
+def dg_assemble(h, c):
+    return load().dg_assemble(h, ctypes.byref(c))
+
+
+def dg_get_rhs(h, F):
+    return load().dg_get_rhs(h, _ptr(F))
+
+
+def dg_get_blocks(h, dtype, out, nbr=None):
+    return load().dg_get_blocks(h, int(dtype), _ptr(out), _ptr(nbr))
+
+
+def dg_apply(h, dtype, x, y):
+    return load().dg_apply(h, int(dtype), _ptr(x), _ptr(y))
+
+
+def dg_precond_setup(h, kind):
+    return load().dg_precond_setup(h, int(kind))
+
+
+def dg_precond_apply(h, dtype, r, z):
+    return load().dg_precond_apply(h, int(dtype), _ptr(r), _ptr(z))
+
+
+def dg_gmres_solve(h, F, x, info=None):
+    return load().dg_gmres_solve(h, _ptr(F), _ptr(x), ctypes.byref(info) if info is not None else None)
+
+
+def dg_dense_solve(h, F, x):
+    return load().dg_dense_solve(h, _ptr(F), _ptr(x))
+
+
+def dg_l2_error(h, x, uex_q):
+    l2, hmax = c_double(), c_double()
+    s = load().dg_l2_error(h, _ptr(x), _ptr(uex_q), ctypes.byref(l2), ctypes.byref(hmax))
+    return s, l2.value, hmax.value
+
+
+def dg_eval(h, x, rs, out):
+    rs = np.ascontiguousarray(rs, dtype=np.float64).reshape(-1, 2)
+    return load().dg_eval(h, _ptr(x), rs.shape[0], _ptr(rs), _ptr(out))
+
+
+def dg_get_launch_count(h):
+    c = c_int64()
+    s = load().dg_get_launch_count(h, ctypes.byref(c))
+    return s, c.value
+
+
+def dg_reference_basis(degree, rs):
+    rs = np.ascontiguousarray(rs, dtype=np.float64).reshape(-1, 2)
+    nb = (degree + 1) * (degree + 2) // 2
+    phi = np.zeros((rs.shape[0], nb)); dr = np.zeros_like(phi); ds = np.zeros_like(phi)
+    s = load().dg_reference_basis(int(degree), rs.shape[0], _ptr(rs), _ptr(phi), _ptr(dr), _ptr(ds))
+    if s != DG_OK:
+        raise DGError(s, "dg_reference_basis")
+    return phi, dr, ds
+
+
+def dg_reference_rule(which, degree):
+    n = ctypes.c_int()
+    load().dg_reference_rule(int(which), int(degree), None, None, ctypes.byref(n))
+    rs = np.zeros((n.value, 2)); w = np.zeros(n.value)
+    s = load().dg_reference_rule(int(which), int(degree), _ptr(rs), _ptr(w), ctypes.byref(n))
+    if s != DG_OK:
+        raise DGError(s, "dg_reference_rule")
+    return rs, w
+
+
+# ---------------------------------------------------------------------------
+# object wrapper
+# ---------------------------------------------------------------------------
+class DG:
+    """One libdg handle on a CUDA device; work goes to torch's current stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device("cuda", device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device).cuda_stream
+        self.h = dg_create(device, stream)
+        self.params = dg_params_default()
+
+    def close(self):
+        if self.h is not None:
+            dg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, s):
+        if s != DG_OK:
+            raise DGError(s, dg_last_error(self.h))
+
+    # -- set-up -------------------------------------------------------------
+    def mesh_upload(self, nodes, elems, dirichlet, neumann):
+        self.check(dg_mesh_upload(self.h, nodes, elems, dirichlet, neumann))
+
+    def set_params(self, **kw):
+        for k, v in kw.items():
+            setattr(self.params, k, v)
+        self.check(dg_set_params(self.h, self.params))
+
+    def info(self):
+        s, i = dg_get_info(self.h)
+        self.check(s)
+        return i
+
+    def _empty(self, shape, dtype=None):
+        return self.torch.empty(shape, dtype=dtype or self.torch.float64, device=self.device)
+
+    def quad_points(self, which):
+        i = self.info()
+        shape = {DG_POINTS_VOLUME: (i.ne, i.q_volume, 2), DG_POINTS_BOUNDARY: (i.n_bedges, i.q_edge, 2),
+                 DG_POINTS_ERROR: (i.ne, i.q_error, 2)}[which]
+        out = self._empty(shape)
+        self.check(dg_quad_points(self.h, which, out))
+        return out
+
+    def boundary_info(self):
+        i = self.info()
+        n = self._empty((i.n_bedges, 2))
+        t = self._empty((i.n_bedges,), self.torch.int32)
+        self.check(dg_boundary_info(self.h, n, t))
+        return n, t
+
+    def assemble(self, eps, alpha, b, f=None, gD=None, gN=None, f_const=0.0, gD_const=0.0, gN_const=0.0):
+        c = dg_coeffs()
+        c.eps, c.alpha = float(eps), float(alpha)
+        for t in range(6):
+            c.b[t] = float(b[t])
+        self._keep = (f, gD, gN)
+        c.f, c.gD, c.gN = _ptr(f), _ptr(gD), _ptr(gN)
+        c.f_const, c.gD_const, c.gN_const = float(f_const), float(gD_const), float(gN_const)
+        self.check(dg_assemble(self.h, c))
+
+    def rhs(self):
+        i = self.info()
+        F = self._empty((i.dofs,))
+        self.check(dg_get_rhs(self.h, F))
+        return F
+
+    def blocks(self, dtype=DG_F64):
+        import torch
+        i = self.info()
+        td = {DG_F64: torch.float64, DG_F32: torch.float32, DG_BF16: torch.bfloat16}[dtype]
+        out = self._empty((i.ne, 4, i.nb, i.nb), td)
+        nbr = self._empty((i.ne, 3), torch.int32)
+        self.check(dg_get_blocks(self.h, dtype, out, nbr))
+        return out, nbr
+
+    # -- operators ------------------------------------------------------------
+    def apply(self, x, dtype=DG_F64, y=None):
+        y = self.torch.empty_like(x) if y is None else y
+        self.check(dg_apply(self.h, dtype, x, y))
+        return y
+
+    def precond_setup(self, kind=DG_PRECOND_BLOCK_JACOBI):
+        self.check(dg_precond_setup(self.h, kind))
+
+    def precond_apply(self, r, dtype=DG_F64, z=None):
+        z = self.torch.empty_like(r) if z is None else z
+        self.check(dg_precond_apply(self.h, dtype, r, z))
+        return z
+
+    # -- solvers --------------------------------------------------------------
+    def gmres_solve(self, F=None, x=None, raise_on_nonconv=True):
+        i = self.info()
+        x = self._empty((i.dofs,)) if x is None else x
+        info = dg_solve_info()
+        s = dg_gmres_solve(self.h, F, x, info)
+        if s != DG_OK and not (s == DG_NOT_CONVERGED and not raise_on_nonconv):
+            self.check(s)
+        return x, info
+
+    def dense_solve(self, F=None):
+        i = self.info()
+        x = self._empty((i.dofs,))
+        self.check(dg_dense_solve(self.h, F, x))
+        return x
+
+    def l2_error(self, x, uex_q):
+        s, l2, hmax = dg_l2_error(self.h, x, uex_q)
+        self.check(s)
+        return l2, hmax
+
+    def launch_count(self):
+        s, c = dg_get_launch_count(self.h)
+        self.check(s)
+        return c
+
+    def eval(self, x, rs):
+        rs = np.ascontiguousarray(rs, dtype=np.float64).reshape(-1, 2)
+        out = self._empty((self.info().ne, rs.shape[0]))
+        self.check(dg_eval(self.h, x, rs, out))
+        return out

@@ -1,0 +1,45 @@
+"""Set up a workload (paper_1502_02941_gb300.workloads.Config) on a DG handle.
+
+Problem data f, gD, gN are evaluated at the library's own quadrature points on
+the device (the role of the paper's vectorised sub-functions fsource, DBCexact
+and NBCexact); everything else is a call into libdg.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import dg as D
+from . import workloads as W
+
+
+def mesh_for(cfg: W.Config) -> W.MeshArrays:
+    return W.structured_mesh(cfg.N, cfg.problem.neumann_sides)
+
+
+def problem_data(h: D.DG, prob: W.Problem):
+    """f at the volume points, gD / gN at the boundary points (device tensors)."""
+    torch = h.torch
+    xq = h.quad_points(D.DG_POINTS_VOLUME)
+    f = prob.f(torch, xq[..., 0], xq[..., 1]).contiguous()
+    xb = h.quad_points(D.DG_POINTS_BOUNDARY)
+    nrm, _ = h.boundary_info()
+    gD = prob.gD(torch, xb[..., 0], xb[..., 1]).contiguous()
+    gN = prob.gN(torch, xb[..., 0], xb[..., 1], nrm[:, None, 0], nrm[:, None, 1]).contiguous()
+    return f, gD, gN
+
+
+def setup(h: D.DG, cfg: W.Config, store=D.DG_STORE_F64, mesh: W.MeshArrays | None = None,
+          assemble: bool = True, **params):
+    ma = mesh if mesh is not None else mesh_for(cfg)
+    h.mesh_upload(ma.nodes, ma.elems, ma.dirichlet, ma.neumann)
+    h.set_params(method=cfg.method, degree=cfg.k, sigma_int=float(cfg.sigma or 0.0), store=store, **params)
+    data = problem_data(h, cfg.problem)
+    if assemble:
+        p = cfg.problem
+        h.assemble(p.eps, p.alpha, p.b, *data)
+    return ma, data
+
+
+def exact_at_error_points(h: D.DG, prob: W.Problem):
+    xe = h.quad_points(D.DG_POINTS_ERROR)
+    return prob.u(h.torch, xe[..., 0], xe[..., 1]).contiguous()

@@ -1,0 +1,97 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports
+every entry point include/dg.h declares, and its host-only helpers (reference
+basis and quadrature) are right."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1502_02941_gb300 import dg as D
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as g
+    g.build()
+    return D.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    syms = D.header_symbols()
+    assert len(syms) >= 20
+    missing = [s for s in syms if not hasattr(lib, s)]
+    assert not missing, missing
+    # the binding wraps every declared entry point under the same name
+    assert set(syms) <= set(D._SIGS)
+    for s in syms:
+        assert callable(getattr(D, s))
+
+
+def test_status_strings(lib):
+    for code in range(10):
+        assert D.dg_status_string(code).startswith("DG_")
+    assert "unknown" in D.dg_status_string(99)
+
+
+def test_params_default(lib):
+    p = D.dg_params_default()
+    assert (p.method, p.degree, p.gmres_m, p.max_it, p.precond) == (D.DG_SIPG, 1, 50, 10000, 1)
+    assert p.sigma_bdry_factor == 2.0 and p.b0 == 1.0 and p.tol == 1e-10
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(D.DGError):
+        D.dg_create(0)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_reference_basis_orthonormal(lib, k):
+    """int_T phi_i phi_j = delta_ij on the reference triangle (area 1/2), with the
+    library's own volume rule, which is exact for degree 2k."""
+    rs, w = D.dg_reference_rule(D.DG_POINTS_VOLUME, k)
+    assert abs(w.sum() - 0.5) < 1e-15 and len(w) == (k + 2) ** 2
+    phi, _, _ = D.dg_reference_basis(k, rs)
+    M = phi.T @ (w[:, None] * phi)
+    np.testing.assert_allclose(M, np.eye(phi.shape[1]), atol=1e-13)
+    # spans P_k: monomials r^a s^b are reproduced by projection
+    for a in range(k + 1):
+        for b in range(k + 1 - a):
+            f = rs[:, 0] ** a * rs[:, 1] ** b
+            c = phi.T @ (w * f)
+            np.testing.assert_allclose(phi @ c, f, atol=1e-12)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_reference_basis_gradients(lib, k):
+    rng = np.random.default_rng(k)
+    r = rng.uniform(0.05, 0.6, 20)
+    s = rng.uniform(0.05, 0.3, 20)
+    rs = np.stack([r, s], 1)
+    phi, dr, ds = D.dg_reference_basis(k, rs)
+    h = 1e-6
+    fr = (D.dg_reference_basis(k, rs + [h, 0])[0] - D.dg_reference_basis(k, rs - [h, 0])[0]) / (2 * h)
+    fs = (D.dg_reference_basis(k, rs + [0, h])[0] - D.dg_reference_basis(k, rs - [0, h])[0]) / (2 * h)
+    np.testing.assert_allclose(dr, fr, atol=1e-7)
+    np.testing.assert_allclose(ds, fs, atol=1e-7)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_reference_rules(lib, k):
+    t, w = D.dg_reference_rule(D.DG_POINTS_BOUNDARY, k)
+    x, wx = np.polynomial.legendre.leggauss(k + 2)
+    np.testing.assert_allclose(t[:, 0], 0.5 * (x + 1), atol=1e-15)
+    np.testing.assert_allclose(w, 0.5 * wx, atol=1e-15)
+    # the L2-error rule integrates r^a s^b exactly to degree 2k+6
+    rs, w = D.dg_reference_rule(D.DG_POINTS_ERROR, k)
+    for a in range(2 * k + 7):
+        for b in range(2 * k + 7 - a):
+            exact = math.factorial(a) * math.factorial(b) / math.factorial(a + b + 2)
+            assert abs((w * rs[:, 0] ** a * rs[:, 1] ** b).sum() - exact) < 1e-15
+
+
+def test_invalid_arguments(lib):
+    with pytest.raises(D.DGError):
+        D.dg_reference_basis(7, np.zeros((1, 2)))
