@@ -292,6 +292,24 @@ dg_status dg_l2_error(dg_handle* h, const double* x, const double* uex_q, double
  */
 dg_status dg_eval(dg_handle* h, const double* x, int np, const double* rs, double* out);
 
+/*
+ * dg_l2_error without any device allocation.  Same inputs, outputs and result
+ * as dg_l2_error (the paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory, e.g. when another allocator owns
+ * all of it or a timing-critical loop must not enter the driver's allocator).
+ * Its reduction scratch is a fixed array inside the library (16385 doubles per
+ * GPU, kept until the process exits), which limits the mesh to 4,194,304
+ * elements (DG_ERR_INVALID_ARG beyond).  The handle's reference tables must
+ * already exist: call dg_quad_points, dg_boundary_info or dg_assemble once
+ * for the current degree first (DG_ERR_STATE otherwise).  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the array: calls whose GPU work overlaps (other streams or handles on
+ * the same device) race on it and must be serialised by the caller.
+ * Synchronises the handle's stream.
+ */
+dg_status dg_l2_error_noalloc(dg_handle* h, const double* x, const double* uex_q, double* l2, double* hmax);
+
 /* ------------------------------------------------------------------------ */
 /* instrumentation                                                           */
 /* ------------------------------------------------------------------------ */

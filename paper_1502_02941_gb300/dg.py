@@ -82,6 +82,8 @@ _SIGS = {
     "dg_l2_error": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_double),
                                    ctypes.POINTER(c_double)]),
     "dg_eval": (ctypes.c_int, [c_void_p, c_void_p, ctypes.c_int, c_void_p, c_void_p]),
+    "dg_l2_error_noalloc": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_double),
+                                           ctypes.POINTER(c_double)]),
     "dg_get_launch_count": (ctypes.c_int, [c_void_p, ctypes.POINTER(c_int64)]),
     "dg_reference_basis": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
     "dg_reference_rule": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, c_void_p, c_void_p,
@@ -234,6 +236,13 @@ def dg_dense_solve(h, F, x):
 def dg_l2_error(h, x, uex_q):
     l2, hmax = c_double(), c_double()
     s = load().dg_l2_error(h, _ptr(x), _ptr(uex_q), ctypes.byref(l2), ctypes.byref(hmax))
+    return s, l2.value, hmax.value
+
+
+def dg_l2_error_noalloc(h, x, uex_q):
+    """dg_l2_error through the allocation-free entry point (see include/dg.h)."""
+    l2, hmax = c_double(), c_double()
+    s = load().dg_l2_error_noalloc(h, _ptr(x), _ptr(uex_q), ctypes.byref(l2), ctypes.byref(hmax))
     return s, l2.value, hmax.value
 
 
