@@ -270,6 +270,26 @@ dg_status dg_precond_apply(dg_handle* h, int dtype, const void* r, void* z);
 dg_status dg_gmres_solve(dg_handle* h, const double* F, double* x, dg_solve_info* info);
 
 /*
+ * Mixed-precision solve by iterative refinement.  The outer loop computes the
+ * true residual r = F - A x with the f64 blocks (f64 arithmetic) and stops when
+ * ||r||/||F|| <= params.tol.  Each correction solves A_lo d = r/||r||
+ * approximately with restarted GMRES(inner_m) on f32 vectors, using the f32
+ * (inner_dtype DG_F32) or bf16 (DG_BF16) block copy with f32 accumulation and
+ * the block-Jacobi inverses (computed in f64, applied in f32), to relative
+ * residual inner_tol; dot products accumulate in f64 beyond per-thread
+ * compensated f32 partial sums, Hessenberg/Givens in f64.  Then x += ||r|| d in
+ * f64.  Needs DG_STORE_F64 and the inner copy in params.store.
+ *   inner_m   1..64;  inner_tol in (0,1);  max_outer >= 1 corrections
+ *   F device [dofs] f64 or NULL (assembled F); x device [dofs] f64 output
+ *   info: iterations = inner Arnoldi steps in total, outer = corrections,
+ *         relres = final f64 relative residual.
+ * DG_NOT_CONVERGED after max_outer corrections or params.max_it inner steps.
+ * Synchronises.
+ */
+dg_status dg_mixed_solve(dg_handle* h, int inner_dtype, int inner_m, double inner_tol, int max_outer,
+                         const double* F, double* x, dg_solve_info* info);
+
+/*
  * Direct solve Stiff x = F (the paper's coef = Stiff\F) by dense LU with
  * partial pivoting on the device, f64.  For small systems: dofs <= 4096.
  * F device or NULL (assembled F); x device output.  Synchronises.

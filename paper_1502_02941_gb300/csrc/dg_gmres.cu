@@ -2,19 +2,23 @@
 // (Saad & Schultz 1986), replacing the paper's direct solve Stiff\F.
 //
 // Every step of the iteration runs in kernels on the handle's stream; the
-// host only launches one captured CUDA graph per restart cycle and reads a
-// small status header when the cycle ends.  One Arnoldi step j:
-//   Z       = s_j M^-1 V_j                 (block-Jacobi apply, lazily scaled)
-//   V_{j+1} = A Z                          (operator apply)
-//   h_d     = s_d <V_d, V_{j+1}>, d <= j, and ||V_{j+1}||^2  (one fused multi-dot pass)
-//   V_{j+1} -= sum_d h_d s_d V_d, ||V_{j+1}||^2               (one update pass)
-//   [if the norm fell below 0.7 of its value before: a second classical
-//    Gram-Schmidt pass ("twice is enough")]
-//   Hessenberg column, Givens rotations, residual estimate   (one thread)
-// Basis vectors are stored unnormalised with s_i = 1/||V_i|| so no separate
-// normalisation pass is needed.  All Hessenberg/Givens arithmetic is f64.
-// At the end of a cycle: y = H^-1 g (one thread), U = sum y_i s_i V_i,
-// x += M^-1 U, r = F - A x, and the true residual decides convergence.
+// host launches one captured CUDA graph per restart cycle and reads a small
+// status header when the cycle ends.  One Arnoldi step j is 4 kernels:
+//   1. Z       = s_j M^-1 V_j                       (block-Jacobi apply)
+//   2. V_{j+1} = A Z                                (operator apply)
+//   3. r_d     = <V_d, V_{j+1}>, d <= j+1           (one multi-dot pass; d = j+1
+//                                                    is ||V_{j+1}||^2)
+//   4. V_{j+1} -= sum_d s_d^2 r_d V_d, ||V_{j+1}||^2 (one update pass)
+// plus, only when the norm fell below 0.7 of its value before the update, a
+// second classical Gram-Schmidt pass (kernels 3-4 again; otherwise they exit at
+// once).  Reductions finish inside the reducing kernel: the last block to
+// arrive (threadfence + arrival counter, no waiting) sums the per-block
+// partials in a fixed order and runs the control step -- Hessenberg column,
+// Givens rotations, residual estimate, convergence / re-orthogonalisation
+// decisions -- so results are deterministic.  Basis vectors are stored
+// unnormalised with s_i = 1/||V_i||.  Hessenberg and Givens arithmetic is f64.
+// End of a cycle: y = H^-1 g, U = sum y_i s_i V_i, x += M^-1 U, r = F - A x,
+// and the true residual decides convergence.
 #include <math.h>
 #include <string.h>
 
@@ -31,7 +35,7 @@ struct GmresState {  // header fields first: the first GM_HDR bytes go to the ho
     int pending;     // the cycle has a correction to add to x
     int nonfinite;   // NaN/Inf met
     int m, max_it;
-    int pad_;
+    unsigned int arrive;  // last-block arrival counter
     double tol, bnorm, relres, wn2_before;
     double scale[DG_MAXM + 2];
     double hcol[DG_MAXM + 2];
@@ -40,54 +44,79 @@ struct GmresState {  // header fields first: the first GM_HDR bytes go to the ho
     double cs[DG_MAXM], sn[DG_MAXM], g[DG_MAXM + 1], y[DG_MAXM];
 };
 
-#define GM_G 4   // dots per block in the multi-dot kernel
-#define GM_HDR 96  // bytes of GmresState copied back to the host (through relres)
+#define GM_HDR 96     // bytes of GmresState copied back to the host (through relres)
+#define GM_TX 32      // multi-dot block: 32 vector entries x 32 dot groups
+#define GM_TY 32
+#define GM_DPT ((DG_MAXM + 2 + GM_TY - 1) / GM_TY)   // dots per thread
 
 // ---------------------------------------------------------------------------
-// reduction helper: 4 block sums at once (blockDim.x == 256)
+// helpers
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void block_sum4(double* v, double (*sh)[8]) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int g = 0; g < GM_G; ++g) v[g] = dg_warp_sum(v[g]);
-    if (lane == 0)
-#pragma unroll
-        for (int g = 0; g < GM_G; ++g) sh[g][wid] = v[g];
-    __syncthreads();
-    if (wid == 0) {
-#pragma unroll
-        for (int g = 0; g < GM_G; ++g) {
-            double t = lane < 8 ? sh[g][lane] : 0.0;
-            v[g] = dg_warp_sum(t);
-        }
+// Per-thread accumulation: f64 vectors accumulate in f64; f32 vectors in f32
+// with Kahan compensation (the block/grid reduction is always f64).
+template <typename TV>
+struct Acc {
+    double s = 0.0;
+    __device__ __forceinline__ void fma(double a, double b) { s = ::fma(a, b, s); }
+    __device__ __forceinline__ double get() const { return s; }
+};
+template <>
+struct Acc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void fma(float a, float b) {
+        const float y = a * b - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
     }
+    __device__ __forceinline__ double get() const { return (double)s - (double)c; }
+};
+
+// Returns true in exactly one block: the last to arrive.  All partial results
+// written before the call by any block are visible to that block (read them
+// with __ldcg).  The counter is reset for the next kernel.
+__device__ __forceinline__ bool last_block(unsigned int* counter) {
+    __shared__ int amlast;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        const unsigned int nblk = gridDim.x * gridDim.y;
+        const unsigned int t = atomicAdd(counter, 1u);
+        amlast = (t == nblk - 1) ? 1 : 0;
+        if (amlast) *counter = 0u;
+    }
+    __syncthreads();
+    return amlast != 0;
 }
 
-// x = 0, V_0 = F, partial ||F||^2
+// Sum cnt partials with all threads of a 1-D block; every thread gets it.
+__device__ double sum_partials(const double* p, int cnt, double* sh) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) s += __ldcg(p + i);
+    return dg_block_sum(s, sh);
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+// x = 0, V_0 = F; last block: ||F||, state initialisation.
 template <typename TV>
 __global__ void __launch_bounds__(256) k_gm_init(const TV* __restrict__ F, TV* __restrict__ x, TV* __restrict__ V0,
-                                                  long n, double* partials) {
-    __shared__ double sh[GM_G][8];
-    double v[GM_G] = {0, 0, 0, 0};
+                                                  long n, GmresState* st, double* partials, int m, int max_it,
+                                                  double tol) {
+    __shared__ double sh[32];
+    Acc<TV> a;
     for (long l = (long)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (long)gridDim.x * blockDim.x) {
         const TV f = F[l];
         x[l] = (TV)0;
         V0[l] = f;
-        v[0] += (double)f * (double)f;
+        a.fma(f, f);
     }
-    block_sum4(v, sh);
-    if (threadIdx.x == 0) partials[blockIdx.x] = v[0];
-}
-
-__device__ double reduce_partials(const double* p, int cnt, double* sh) {
-    double s = 0.0;
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) s += p[i];
-    return dg_block_sum(s, sh);
-}
-
-__global__ void k_gm_ctl_init(GmresState* st, const double* partials, int gx, int m, int max_it, double tol) {
-    __shared__ double sh[32];
-    const double b2 = reduce_partials(partials, gx, sh);
+    const double v = dg_block_sum(a.get(), sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = v;
+    if (!last_block(&st->arrive)) return;
+    const double b2 = sum_partials(partials, gridDim.x, sh);
     if (threadIdx.x != 0) return;
     st->m = m;
     st->max_it = max_it;
@@ -100,15 +129,15 @@ __global__ void k_gm_ctl_init(GmresState* st, const double* partials, int gx, in
     st->j = 0;
     const double bn = sqrt(b2);
     st->bnorm = bn;
+    st->converged = 0;
     if (!isfinite(bn)) {
         st->nonfinite = 1;
         st->done = 1;
         st->active = 0;
-        st->converged = 0;
         st->relres = bn;
         return;
     }
-    if (bn == 0.0) {
+    if (bn == 0.0 || tol >= 1.0) {
         st->done = 1;
         st->converged = 1;
         st->active = 0;
@@ -116,54 +145,73 @@ __global__ void k_gm_ctl_init(GmresState* st, const double* partials, int gx, in
         return;
     }
     st->relres = 1.0;
-    st->converged = 0;
-    st->done = tol >= 1.0 ? 1 : 0;
-    st->converged = st->done;
-    st->active = st->done ? 0 : 1;
+    st->done = 0;
+    st->active = 1;
     for (int i = 0; i <= m; ++i) st->g[i] = 0.0;
     st->g[0] = bn;
     st->scale[0] = 1.0 / bn;
 }
 
-// Multi-dot: raw r_d = <V_d, V_{j+1}> for d <= j (pass 1 also d = j+1: the norm).
+// Multi-dot r_d = <V_d, V_{j+1}>, d <= dlast (pass 1: dlast = j+1, the last
+// one being the squared norm; pass 2: dlast = j).  One 1024-thread block per
+// SM, block (32, 32): lanes run over 32 consecutive entries, warp ty over the
+// dots d = ty, ty + 32, ...; four chunks per loop trip keep ~10 loads in
+// flight per thread.  Last block: all threads reduce the per-block partials
+// (16 threads per dot, independent loads), then h_d = s_d r_d into hcol and the
+// update coefficients s_d h_d.
 template <typename TV>
-__global__ void __launch_bounds__(256) k_gm_dots(const TV* __restrict__ V, long n, const GmresState* st,
-                                                  double* partials, int gx, int pass) {
+__global__ void __launch_bounds__(GM_TX* GM_TY) k_gm_dots(const TV* __restrict__ V, long n, GmresState* st,
+                                                         double* partials, int pass) {
     if (!st->active || (pass == 2 && !st->reorth)) return;
     const int j = st->j;
     const int dlast = pass == 1 ? j + 1 : j;
-    const int d0 = blockIdx.y * GM_G;
-    if (d0 > dlast) return;
-    __shared__ double sh[GM_G][8];
+    const int tx = threadIdx.x, ty = threadIdx.y;
     const TV* __restrict__ w = V + (long)(j + 1) * n;
-    const TV* vp[GM_G];
+    Acc<TV> acc[GM_DPT];
+    const long nchunk = (n + GM_TX - 1) / GM_TX;
+    const long step = gridDim.x;
+    for (long c = blockIdx.x; c < nchunk; c += 4 * step) {
+        TV wl[4];
 #pragma unroll
-    for (int g = 0; g < GM_G; ++g) vp[g] = V + (long)min(d0 + g, j + 1) * n;
-    double v[GM_G] = {0, 0, 0, 0};
-    for (long l = (long)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (long)gx * blockDim.x) {
-        const double wl = (double)w[l];
+        for (int u = 0; u < 4; ++u) {
+            const long l = (c + u * step) * GM_TX + tx;
+            wl[u] = l < n ? w[l] : (TV)0;
+        }
 #pragma unroll
-        for (int g = 0; g < GM_G; ++g)
-            if (d0 + g <= dlast) v[g] += (double)vp[g][l] * wl;
+        for (int k = 0; k < GM_DPT; ++k) {
+            const int d = ty + GM_TY * k;
+            if (d <= dlast) {
+                TV v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const long l = (c + u * step) * GM_TX + tx;
+                    v[u] = l < n ? V[(long)d * n + l] : (TV)0;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[k].fma(v[u], wl[u]);
+            }
+        }
     }
-    block_sum4(v, sh);
-    if (threadIdx.x == 0)
+    const int gx = gridDim.x;
 #pragma unroll
-        for (int g = 0; g < GM_G; ++g)
-            if (d0 + g <= dlast) partials[(long)(d0 + g) * gx + blockIdx.x] = v[g];
-}
-
-// One warp per dot: warp w sums partials of d = w, w+32, ... (blockDim 1024).
-__global__ void k_gm_ctl_dots(GmresState* st, const double* partials, int gx, int pass) {
-    if (!st->active || (pass == 2 && !st->reorth)) return;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int j = st->j;
-    const int dlast = pass == 1 ? j + 1 : j;
-    for (int d = wid; d <= dlast; d += nw) {
+    for (int k = 0; k < GM_DPT; ++k) {
+        const int d = ty + GM_TY * k;
+        const double v = dg_warp_sum(acc[k].get());
+        if (tx == 0 && d <= dlast) partials[(long)d * gx + blockIdx.x] = v;
+    }
+    if (!last_block(&st->arrive)) return;
+    // 16 threads per dot: thread t sums partials t%16, t%16+16, ... of dot t/16
+    const int t = ty * GM_TX + tx;
+    for (int d0 = 0; d0 <= dlast; d0 += (GM_TX * GM_TY) / 16) {
+        const int d = d0 + t / 16;
         double r = 0.0;
-        for (int i = lane; i < gx; i += 32) r += partials[(long)d * gx + i];
-        r = dg_warp_sum(r);
-        if (lane == 0) {
+        if (d <= dlast) {
+#pragma unroll 4
+            for (int b = t % 16; b < gx; b += 16) r += __ldcg(partials + (long)d * gx + b);
+        }
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+        if ((t % 16) == 0 && d <= dlast) {
             if (d == j + 1) {
                 st->wn2_before = r;
             } else {
@@ -175,90 +223,110 @@ __global__ void k_gm_ctl_dots(GmresState* st, const double* partials, int gx, in
     }
 }
 
-// V_{j+1} -= sum_{d<=j} coef_d V_d ; partial ||V_{j+1}||^2
-template <typename TV>
-__global__ void __launch_bounds__(256) k_gm_update(TV* V, long n, const GmresState* st,
-                                                    double* partials, int pass) {
-    if (!st->active || (pass == 2 && !st->reorth)) return;
-    __shared__ double c[DG_MAXM + 2];
-    __shared__ double sh[GM_G][8];
+// Givens / Hessenberg step for column j; runs in thread 0 of the last block
+// with the column and the previous rotations staged in shared memory.
+__device__ void gm_finish_column(GmresState* st, double wn, const double* hc, const double* cs, const double* sn) {
     const int j = st->j;
-    for (int d = threadIdx.x; d <= j; d += blockDim.x) c[d] = st->coef[d];
-    __syncthreads();
-    TV* w = V + (long)(j + 1) * n;   // aliases V: no __restrict__
-    double v[GM_G] = {0, 0, 0, 0};
-    for (long l = (long)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (long)gridDim.x * blockDim.x) {
-        double acc = (double)w[l];
-        int d = 0;
-        for (; d + 4 <= j + 1; d += 4) {
-            const double a0 = (double)V[(long)d * n + l], a1 = (double)V[(long)(d + 1) * n + l];
-            const double a2 = (double)V[(long)(d + 2) * n + l], a3 = (double)V[(long)(d + 3) * n + l];
-            acc -= c[d] * a0 + c[d + 1] * a1 + c[d + 2] * a2 + c[d + 3] * a3;
-        }
-        for (; d <= j; ++d) acc -= c[d] * (double)V[(long)d * n + l];
-        const TV out = (TV)acc;
-        w[l] = out;
-        v[0] += (double)out * (double)out;
-    }
-    block_sum4(v, sh);
-    if (threadIdx.x == 0) partials[blockIdx.x] = v[0];
-}
-
-// Norm, re-orthogonalisation decision, Hessenberg column, Givens rotation.
-__global__ void k_gm_ctl_update(GmresState* st, const double* partials, int gx, int pass) {
-    if (!st->active || (pass == 2 && !st->reorth)) return;
-    __shared__ double sh[32];
-    const double wn2 = reduce_partials(partials, gx, sh);
-    if (threadIdx.x != 0) return;
-    const int j = st->j;
-    const double wn = sqrt(wn2);
-    if (pass == 1 && wn < 0.7 * sqrt(st->wn2_before)) {
-        st->reorth = 1;
-        return;
-    }
-    st->reorth = 0;
     const int LD = DG_MAXM + 1;
     double* Hc = st->H + (long)j * LD;
-    for (int i = 0; i <= j; ++i) Hc[i] = st->hcol[i];
-    Hc[j + 1] = wn;
+    double a = hc[0];
     for (int i = 0; i < j; ++i) {
-        const double t1 = st->cs[i] * Hc[i] + st->sn[i] * Hc[i + 1];
-        const double t2 = -st->sn[i] * Hc[i] + st->cs[i] * Hc[i + 1];
-        Hc[i] = t1;
-        Hc[i + 1] = t2;
+        const double b = hc[i + 1];
+        Hc[i] = cs[i] * a + sn[i] * b;
+        a = -sn[i] * a + cs[i] * b;
     }
-    const double a = Hc[j], b = Hc[j + 1];
+    const double b = wn;
     const double r = hypot(a, b);
     const double c = r == 0.0 ? 1.0 : a / r, s = r == 0.0 ? 0.0 : b / r;
     st->cs[j] = c;
     st->sn[j] = s;
     Hc[j] = r;
     Hc[j + 1] = 0.0;
-    st->g[j + 1] = -s * st->g[j];
-    st->g[j] = c * st->g[j];
+    const double gj = st->g[j];
+    st->g[j + 1] = -s * gj;
+    st->g[j] = c * gj;
     st->scale[j + 1] = wn > 0.0 ? 1.0 / wn : 0.0;
     st->its += 1;
     st->j = j + 1;
     st->pending = 1;
     const bool bad = !isfinite(wn) || !isfinite(r);
     if (bad) st->nonfinite = 1;
-    const double est = fabs(st->g[j + 1]);
+    const double est = fabs(s * gj);
     const bool breakdown = !(wn > 1e-300) || !(r > 0.0);
     if (bad || est <= st->tol * st->bnorm || j + 1 >= st->m || st->its >= st->max_it || breakdown) st->active = 0;
 }
 
-// y = H(0:jj,0:jj)^-1 g(0:jj); coef_i = y_i s_i
-__global__ void k_gm_ctl_solve(GmresState* st) {
-    if (threadIdx.x != 0 || !st->pending) return;
+// V_{j+1} -= sum_{d<=j} coef_d V_d ; ||V_{j+1}||^2.  Last block: norm,
+// re-orthogonalisation decision, Hessenberg/Givens step.
+template <typename TV>
+__global__ void __launch_bounds__(256) k_gm_update(TV* V, long n, GmresState* st, double* partials, int pass) {
+    if (!st->active || (pass == 2 && !st->reorth)) return;
+    __shared__ TV c[DG_MAXM + 2];
+    __shared__ double sh[32];
+    __shared__ double hc[DG_MAXM + 2], css[DG_MAXM], sns[DG_MAXM];
+    const int j = st->j;
+    for (int d = threadIdx.x; d <= j; d += blockDim.x) c[d] = (TV)st->coef[d];
+    __syncthreads();
+    TV* w = V + (long)(j + 1) * n;   // aliases V: no __restrict__
+    Acc<TV> nrm;
+    for (long l = (long)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (long)gridDim.x * blockDim.x) {
+        TV acc = w[l];
+        int d = 0;
+        for (; d + 8 <= j + 1; d += 8) {
+            TV v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = V[(long)(d + u) * n + l];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc = ::fma(-c[d + u], v[u], acc);
+        }
+        for (; d <= j; ++d) acc = ::fma(-c[d], V[(long)d * n + l], acc);
+        w[l] = acc;
+        nrm.fma(acc, acc);
+    }
+    const double v = dg_block_sum(nrm.get(), sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = v;
+    if (!last_block(&st->arrive)) return;
+    const double wn2 = sum_partials(partials, gridDim.x, sh);
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+        hc[i] = st->hcol[i];
+        if (i < j) {
+            css[i] = st->cs[i];
+            sns[i] = st->sn[i];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const double wn = sqrt(wn2);
+    if (pass == 1 && wn < 0.7 * sqrt(st->wn2_before)) {
+        st->reorth = 1;
+        return;
+    }
+    st->reorth = 0;
+    gm_finish_column(st, wn, hc, css, sns);
+}
+
+// y = H(0:jj,0:jj)^-1 g(0:jj) by column-oriented back substitution in shared
+// memory; coef_i = y_i s_i.
+__global__ void __launch_bounds__(256) k_gm_solve(GmresState* st) {
+    if (!st->pending) return;
+    __shared__ double Hs[(DG_MAXM + 1) * DG_MAXM];
+    __shared__ double gs[DG_MAXM + 1];
     const int jj = st->j;
     const int LD = DG_MAXM + 1;
+    for (int t = threadIdx.x; t < jj * LD; t += blockDim.x) Hs[t] = st->H[t];
+    for (int t = threadIdx.x; t < jj; t += blockDim.x) gs[t] = st->g[t];
+    __syncthreads();
     for (int i = jj - 1; i >= 0; --i) {
-        double s = st->g[i];
-        for (int l = i + 1; l < jj; ++l) s -= st->H[(long)l * LD + i] * st->y[l];
-        const double d = st->H[(long)i * LD + i];
-        st->y[i] = d != 0.0 ? s / d : 0.0;
+        const double d = Hs[(long)i * LD + i];
+        const double yi = d != 0.0 ? gs[i] / d : 0.0;
+        __syncthreads();
+        for (int l = threadIdx.x; l < i; l += blockDim.x) gs[l] -= Hs[(long)i * LD + l] * yi;
+        if (threadIdx.x == 0) {
+            st->y[i] = yi;
+            st->coef[i] = yi * st->scale[i];
+        }
+        __syncthreads();
     }
-    for (int i = 0; i < jj; ++i) st->coef[i] = st->y[i] * st->scale[i];
 }
 
 // U = sum_{i<jj} coef_i V_i
@@ -272,7 +340,13 @@ __global__ void __launch_bounds__(256) k_gm_combine(const TV* __restrict__ V, lo
     __syncthreads();
     for (long l = (long)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (long)gridDim.x * blockDim.x) {
         double acc = 0.0;
-        for (int d = 0; d < jj; ++d) acc += c[d] * (double)V[(long)d * n + l];
+        int d = 0;
+        for (; d + 4 <= jj; d += 4) {
+            const double a0 = (double)V[(long)d * n + l], a1 = (double)V[(long)(d + 1) * n + l];
+            const double a2 = (double)V[(long)(d + 2) * n + l], a3 = (double)V[(long)(d + 3) * n + l];
+            acc += c[d] * a0 + c[d + 1] * a1 + c[d + 2] * a2 + c[d + 3] * a3;
+        }
+        for (; d < jj; ++d) acc += c[d] * (double)V[(long)d * n + l];
         U[l] = (TV)acc;
     }
 }
@@ -282,31 +356,25 @@ __global__ void __launch_bounds__(256) k_gm_axpy(TV* __restrict__ x, const TV* _
                                                   const GmresState* st) {
     if (!st->pending) return;
     for (long l = (long)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (long)gridDim.x * blockDim.x)
-        x[l] = (TV)((double)x[l] + (double)z[l]);
+        x[l] = x[l] + z[l];
 }
 
-// V_0 = F - AX ; partial norm
+// V_0 = F - AX, ||V_0||; last block: restart decision.
 template <typename TV>
 __global__ void __launch_bounds__(256) k_gm_resid(const TV* __restrict__ F, const TV* __restrict__ AX,
-                                                   TV* __restrict__ V0, long n, const GmresState* st,
-                                                   double* partials) {
-    if (!st->pending) return;
-    __shared__ double sh[GM_G][8];
-    double v[GM_G] = {0, 0, 0, 0};
-    for (long l = (long)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (long)gridDim.x * blockDim.x) {
-        const double r = (double)F[l] - (double)AX[l];
-        const TV rv = (TV)r;
-        V0[l] = rv;
-        v[0] += (double)rv * (double)rv;
-    }
-    block_sum4(v, sh);
-    if (threadIdx.x == 0) partials[blockIdx.x] = v[0];
-}
-
-__global__ void k_gm_ctl_restart(GmresState* st, const double* partials, int gx) {
+                                                   TV* __restrict__ V0, long n, GmresState* st, double* partials) {
     if (!st->pending) return;
     __shared__ double sh[32];
-    const double r2 = reduce_partials(partials, gx, sh);
+    Acc<TV> a;
+    for (long l = (long)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (long)gridDim.x * blockDim.x) {
+        const TV rv = F[l] - AX[l];
+        V0[l] = rv;
+        a.fma(rv, rv);
+    }
+    const double v = dg_block_sum(a.get(), sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = v;
+    if (!last_block(&st->arrive)) return;
+    const double r2 = sum_partials(partials, gridDim.x, sh);
     if (threadIdx.x != 0) return;
     const double beta = sqrt(r2);
     st->pending = 0;
@@ -350,126 +418,119 @@ static void launch_bj(dg_handle* h, const TB* B, const TV* r, TV* z, DevCtl ctl,
     k_bj_apply<NB, TB, TV, TV><<<grid, 256, 0, h->stream>>>(B, r, z, h->ne, ctl, sr, sz);
 }
 
-struct GmSetup {
-    long n;
-    int m;
-    int gx;
-};
-
 // One restart cycle: m Arnoldi steps, the correction and the true residual.
+// Returns the number of kernels enqueued.
 template <int NB, typename TA, typename TB, typename TV>
-static int enqueue_cycle(dg_handle* h, const GmSetup& S, const TA* A, const TB* B, const TV* F, TV* x) {
-    TV* V = (TV*)h->V;
-    TV* Z = (TV*)h->Z;
-    TV* R = (TV*)h->R;
-    GmresState* st = h->st;
-    const long n = S.n;
-    const int gx = S.gx;
-    const int gy = (S.m + 2 + GM_G - 1) / GM_G;
-    const dim3 gdots(gx, gy);
+static int enqueue_cycle(dg_handle* h, GmresWork& W, const TA* A, const TB* B, const TV* F, TV* x) {
+    TV* V = (TV*)W.V;
+    TV* Z = (TV*)W.Z;
+    TV* R = (TV*)W.R;
+    GmresState* st = W.st;
+    const long n = (long)W.n;
+    const int gx = W.gx;
+    const dim3 bdots(GM_TX, GM_TY);
+    const int gdots = W.gsm;
     DevCtl step{&st->active, st->scale};
     DevCtl step_noscale{&st->active, nullptr};
     VecSel vj{&st->j, 0, n}, vj1{&st->j, 1, n};
-    for (int it = 0; it < S.m; ++it) {
+    for (int it = 0; it < W.m; ++it) {
         launch_bj<NB, TB, TV>(h, B, V, Z, step, vj, vsel_fixed());
         launch_apply<NB, TA, TV>(h, A, Z, V, step_noscale, vsel_fixed(), vj1);
         for (int pass = 1; pass <= 2; ++pass) {
-            k_gm_dots<TV><<<gdots, 256, 0, h->stream>>>(V, n, st, h->partials, gx, pass);
-            k_gm_ctl_dots<<<1, 1024, 0, h->stream>>>(st, h->partials, gx, pass);
-            k_gm_update<TV><<<gx, 256, 0, h->stream>>>(V, n, st, h->partials, pass);
-            k_gm_ctl_update<<<1, 256, 0, h->stream>>>(st, h->partials, gx, pass);
+            k_gm_dots<TV><<<gdots, bdots, 0, h->stream>>>(V, n, st, W.partials, pass);
+            k_gm_update<TV><<<gx, 256, 0, h->stream>>>(V, n, st, W.partials, pass);
         }
     }
     DevCtl pend{&st->pending, nullptr};
-    k_gm_ctl_solve<<<1, 32, 0, h->stream>>>(st);
+    k_gm_solve<<<1, 256, 0, h->stream>>>(st);
     k_gm_combine<TV><<<gx, 256, 0, h->stream>>>(V, n, st, R);
     launch_bj<NB, TB, TV>(h, B, R, Z, pend, vsel_fixed(), vsel_fixed());
     k_gm_axpy<TV><<<gx, 256, 0, h->stream>>>(x, Z, n, st);
     launch_apply<NB, TA, TV>(h, A, x, R, pend, vsel_fixed(), vsel_fixed());
-    k_gm_resid<TV><<<gx, 256, 0, h->stream>>>(F, R, V, n, st, h->partials);
-    k_gm_ctl_restart<<<1, 256, 0, h->stream>>>(st, h->partials, gx);
-    // status header to pinned host memory
-    cudaMemcpyAsync(h->st_host, st, GM_HDR, cudaMemcpyDeviceToHost, h->stream);
-    return 10 * S.m + 7;   // kernels enqueued
+    k_gm_resid<TV><<<gx, 256, 0, h->stream>>>(F, R, V, n, st, W.partials);
+    cudaMemcpyAsync(W.st_host, st, GM_HDR, cudaMemcpyDeviceToHost, h->stream);
+    return 6 * W.m + 6;
 }
 
-static dg_status ensure_workspace(dg_handle* h, long n, int m, size_t elem) {
-    const size_t need_v = (size_t)(m + 2) * n * elem;
+void dg_gmres_free(GmresWork* w) {
+    void* ptrs[] = {w->V, w->Z, w->R, w->partials, w->st};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (w->st_host) cudaFreeHost(w->st_host);
+    if (w->graph) cudaGraphExecDestroy(w->graph);
+    *w = GmresWork();
+}
+
+static dg_status ensure_workspace(dg_handle* h, GmresWork& W, long n, int m, size_t elem) {
     dg_status s;
-    if (h->gm_n != (size_t)n || h->gm_m != m || !h->V) {
-        if ((s = dg_realloc(h, (void**)&h->V, need_v)) != DG_OK) return s;
-        if ((s = dg_realloc(h, (void**)&h->Z, (size_t)n * 8)) != DG_OK) return s;
-        if ((s = dg_realloc(h, (void**)&h->R, (size_t)n * 8)) != DG_OK) return s;
-        h->gm_n = n;
-        h->gm_m = m;
-        if (h->gm_graph) {
-            cudaGraphExecDestroy(h->gm_graph);
-            h->gm_graph = nullptr;
+    if (W.n != (size_t)n || W.m != m || W.elem != elem || !W.V) {
+        if ((s = dg_realloc(h, &W.V, (size_t)(m + 2) * n * elem)) != DG_OK) return s;
+        if ((s = dg_realloc(h, &W.Z, (size_t)n * elem)) != DG_OK) return s;
+        if ((s = dg_realloc(h, &W.R, (size_t)n * elem)) != DG_OK) return s;
+        W.n = n;
+        W.m = m;
+        W.elem = elem;
+        if (W.graph) {
+            cudaGraphExecDestroy(W.graph);
+            W.graph = nullptr;
         }
     }
-    if (!h->partials)
-        if ((s = dg_realloc(h, (void**)&h->partials, sizeof(double) * (DG_MAXM + 2) * 4096)) != DG_OK) return s;
-    if (!h->st)
-        if ((s = dg_realloc(h, (void**)&h->st, sizeof(GmresState))) != DG_OK) return s;
-    if (!h->st_host) DG_CK(h, cudaMallocHost((void**)&h->st_host, sizeof(GmresState)));
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    long want = 4L * sms, cap = (n + 255) / 256;
+    W.gx = (int)(want < cap ? want : (cap < 1 ? 1 : cap));
+    W.gsm = (int)((long)sms < (n + 1023) / 1024 ? sms : ((n + 1023) / 1024 < 1 ? 1 : (n + 1023) / 1024));
+    if (!W.partials)
+        if ((s = dg_realloc(h, (void**)&W.partials, sizeof(double) * (DG_MAXM + 2) * 4096)) != DG_OK) return s;
+    if (!W.st) {
+        if ((s = dg_realloc(h, (void**)&W.st, sizeof(GmresState))) != DG_OK) return s;
+        DG_CK(h, cudaMemsetAsync(W.st, 0, sizeof(GmresState), h->stream));
+    }
+    if (!W.st_host) DG_CK(h, cudaMallocHost((void**)&W.st_host, sizeof(GmresState)));
     return DG_OK;
 }
 
-static int grid_x(dg_handle* h, long n) {
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-    long want = (long)sms * 4;
-    long cap = (n + 255) / 256;
-    long g = want < cap ? want : cap;
-    if (g < 1) g = 1;
-    if (g > 4096) g = 4096;
-    return (int)g;
-}
-
+// Run restarted GMRES(m) to `tol` on (A, M = B) from x0 = 0.
 template <int NB, typename TA, typename TB, typename TV>
-static dg_status gmres_run(dg_handle* h, const TA* A, const TB* B, const TV* F, TV* x, dg_solve_info* info) {
+static dg_status gmres_run(dg_handle* h, GmresWork& W, const TA* A, const TB* B, const TV* F, TV* x, int m,
+                           double tol, int max_it, dg_solve_info* info) {
     const long n = (long)h->ne * NB;
-    const int m = h->p.gmres_m;
-    dg_status s = ensure_workspace(h, n, m, sizeof(TV));
+    dg_status s = ensure_workspace(h, W, n, m, sizeof(TV));
     if (s != DG_OK) return s;
-    GmSetup S{n, m, grid_x(h, n)};
-    // initialise
-    k_gm_init<TV><<<S.gx, 256, 0, h->stream>>>(F, x, (TV*)h->V, n, h->partials);
-    k_gm_ctl_init<<<1, 256, 0, h->stream>>>(h->st, h->partials, S.gx, m, h->p.max_it, h->p.tol);
-    h->nlaunch += 2;
+    k_gm_init<TV><<<W.gx, 256, 0, h->stream>>>(F, x, (TV*)W.V, n, W.st, W.partials, m, max_it, tol);
+    h->nlaunch += 1;
     DG_LAUNCH_CK(h);
-    DG_CK(h, cudaMemcpyAsync(h->st_host, h->st, GM_HDR, cudaMemcpyDeviceToHost, h->stream));
+    DG_CK(h, cudaMemcpyAsync(W.st_host, W.st, GM_HDR, cudaMemcpyDeviceToHost, h->stream));
     DG_CK(h, cudaStreamSynchronize(h->stream));
-    // capture one cycle into a graph keyed on the buffers it touches
-    const int key[4] = {(int)(((uintptr_t)x) & 0x7fffffff), (int)(((uintptr_t)F) & 0x7fffffff),
-                        (int)(((uintptr_t)A) & 0x7fffffff), (int)(((uintptr_t)B) & 0x7fffffff) ^ m};
-    if (h->gm_graph && memcmp(key, h->gm_graph_key, sizeof(key)) != 0) {
-        cudaGraphExecDestroy(h->gm_graph);
-        h->gm_graph = nullptr;
+    const uintptr_t key[6] = {(uintptr_t)x, (uintptr_t)F, (uintptr_t)A, (uintptr_t)B, (uintptr_t)m,
+                              (uintptr_t)h->stream};
+    if (W.graph && memcmp(key, W.key, sizeof(key)) != 0) {
+        cudaGraphExecDestroy(W.graph);
+        W.graph = nullptr;
     }
     const bool use_graph = h->stream != nullptr;  // capture needs a non-legacy stream
-    if (use_graph && !h->gm_graph) {
+    if (use_graph && !W.graph && !W.st_host->done) {
         cudaGraph_t g;
         DG_CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-        h->gm_nodes = enqueue_cycle<NB, TA, TB, TV>(h, S, A, B, F, x);
+        W.nodes = enqueue_cycle<NB, TA, TB, TV>(h, W, A, B, F, x);
         DG_CK(h, cudaStreamEndCapture(h->stream, &g));
-        cudaError_t e = cudaGraphInstantiate(&h->gm_graph, g, 0);
+        cudaError_t e = cudaGraphInstantiate(&W.graph, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return dg_cuda_fail(h, e, "cudaGraphInstantiate");
-        memcpy(h->gm_graph_key, key, sizeof(key));
+        memcpy(W.key, key, sizeof(key));
     }
-    const int max_cycles = h->p.max_it + 2;
-    for (int c = 0; c < max_cycles && !h->st_host->done; ++c) {
+    const int max_cycles = max_it + 2;
+    for (int c = 0; c < max_cycles && !W.st_host->done; ++c) {
         if (use_graph) {
-            DG_CK(h, cudaGraphLaunch(h->gm_graph, h->stream));
-            h->nlaunch += h->gm_nodes;
+            DG_CK(h, cudaGraphLaunch(W.graph, h->stream));
+            h->nlaunch += W.nodes;
         } else {
-            h->nlaunch += enqueue_cycle<NB, TA, TB, TV>(h, S, A, B, F, x);
+            h->nlaunch += enqueue_cycle<NB, TA, TB, TV>(h, W, A, B, F, x);
         }
         DG_LAUNCH_CK(h);
         DG_CK(h, cudaStreamSynchronize(h->stream));
     }
-    GmresState* hs = h->st_host;
+    GmresState* hs = W.st_host;
     if (info) {
         info->iterations = hs->its;
         info->restarts = hs->cycles;
@@ -485,7 +546,8 @@ static dg_status gmres_run(dg_handle* h, const TA* A, const TB* B, const TV* F, 
 template <int NB>
 static dg_status gmres_f64(dg_handle* h, const double* F, double* x, dg_solve_info* info) {
     const double* B = h->p.precond == DG_PRECOND_BLOCK_JACOBI ? h->Binv64 : nullptr;
-    return gmres_run<NB, double, double, double>(h, h->A64, B, F, x, info);
+    return gmres_run<NB, double, double, double>(h, h->gw[0], h->A64, B, F, x, h->p.gmres_m, h->p.tol,
+                                                 h->p.max_it, info);
 }
 
 extern "C" dg_status dg_gmres_solve(dg_handle* h, const double* F, double* x, dg_solve_info* info) {
@@ -504,5 +566,141 @@ extern "C" dg_status dg_gmres_solve(dg_handle* h, const double* F, double* x, dg
         case 6: return gmres_f64<6>(h, F, x, info);
         case 10: return gmres_f64<10>(h, F, x, info);
     }
+    return dg_fail(h, DG_ERR_INVALID_ARG, "degree");
+}
+
+// ---------------------------------------------------------------------------
+// mixed-precision iterative refinement
+// ---------------------------------------------------------------------------
+// Outer loop in f64:  r = F - A64 x,  stop when ||r||/||F|| <= tol;
+// inner solve in f32: A_lo d = r/||r|| by restarted GMRES(m_in) on the f32 or
+// bf16 block copy with the f32 block-Jacobi inverses, to relative residual
+// inner_tol;  x += ||r|| d  (f64).
+struct MixState {
+    double bnorm, rnorm, relres;
+    unsigned int arrive;
+    int first;
+};
+
+__global__ void __launch_bounds__(256) k_mx_resid(const double* __restrict__ F, const double* __restrict__ AX,
+                                                   double* __restrict__ r, long n, MixState* ms, double* partials) {
+    __shared__ double sh[32];
+    double a = 0.0;
+    for (long l = (long)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (long)gridDim.x * blockDim.x) {
+        const double v = F[l] - AX[l];
+        r[l] = v;
+        a = fma(v, v, a);
+    }
+    const double v = dg_block_sum(a, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = v;
+    if (!last_block(&ms->arrive)) return;
+    const double r2 = sum_partials(partials, gridDim.x, sh);
+    if (threadIdx.x != 0) return;
+    ms->rnorm = sqrt(r2);
+    if (ms->first) {
+        ms->bnorm = ms->rnorm;   // x = 0 on the first pass: r = F
+        ms->first = 0;
+    }
+    ms->relres = ms->bnorm > 0.0 ? ms->rnorm / ms->bnorm : 0.0;
+}
+
+__global__ void __launch_bounds__(256) k_mx_scale(const double* __restrict__ r, float* __restrict__ r32, long n,
+                                                   const MixState* ms) {
+    const double s = ms->rnorm > 0.0 ? 1.0 / ms->rnorm : 0.0;
+    for (long l = (long)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (long)gridDim.x * blockDim.x)
+        r32[l] = (float)(r[l] * s);
+}
+
+__global__ void __launch_bounds__(256) k_mx_update(double* __restrict__ x, const float* __restrict__ d, long n,
+                                                    const MixState* ms) {
+    const double s = ms->rnorm;
+    for (long l = (long)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (long)gridDim.x * blockDim.x)
+        x[l] = fma(s, (double)d[l], x[l]);
+}
+
+template <int NB, typename TA>
+static dg_status mixed_run(dg_handle* h, const TA* Alo, const double* F, double* x, int inner_m, double inner_tol,
+                           int max_outer, dg_solve_info* info) {
+    const long n = (long)h->ne * NB;
+    dg_status s;
+    const size_t need = (size_t)n * (8 + 8 + 4 + 4) + sizeof(MixState) + 256;
+    if ((s = dg_ensure(h, &h->mx_buf, &h->cap_mx, need)) != DG_OK) return s;
+    double* r64 = (double*)h->mx_buf;
+    double* ax = r64 + n;
+    float* r32 = (float*)(ax + n);
+    float* d32 = r32 + n;
+    MixState* ms = (MixState*)(((uintptr_t)(d32 + n) + 255) & ~(uintptr_t)255);
+    GmresWork& W = h->gw[0];   // reuse its partials buffer for the outer reductions
+    if ((s = ensure_workspace(h, W, n, h->p.gmres_m, sizeof(double))) != DG_OK) return s;
+    MixState init{0.0, 0.0, 1.0, 0u, 1};
+    MixState hm{};
+    DG_CK(h, cudaMemcpyAsync(ms, &init, sizeof(MixState), cudaMemcpyHostToDevice, h->stream));
+    DG_CK(h, cudaMemsetAsync(x, 0, sizeof(double) * n, h->stream));
+    const float* B32 = h->p.precond == DG_PRECOND_BLOCK_JACOBI ? h->Binv32 : nullptr;
+    int inner_total = 0, outer = 0;
+    const int gx = W.gx;
+    bool converged = false;
+    for (;;) {
+        launch_apply<NB, double, double>(h, h->A64, x, ax, dctl_none(), vsel_fixed(), vsel_fixed());
+        k_mx_resid<<<gx, 256, 0, h->stream>>>(F, ax, r64, n, ms, W.partials);
+        h->nlaunch += 2;
+        DG_LAUNCH_CK(h);
+        DG_CK(h, cudaMemcpyAsync(&hm, ms, sizeof(MixState), cudaMemcpyDeviceToHost, h->stream));
+        DG_CK(h, cudaStreamSynchronize(h->stream));
+        if (!isfinite(hm.relres)) return dg_fail(h, DG_ERR_NONFINITE, "NaN/Inf in the refinement residual");
+        if (hm.relres <= h->p.tol) { converged = true; break; }
+        if (outer >= max_outer || inner_total >= h->p.max_it) break;
+        k_mx_scale<<<gx, 256, 0, h->stream>>>(r64, r32, n, ms);
+        h->nlaunch += 1;
+        DG_LAUNCH_CK(h);
+        dg_solve_info in{};
+        s = gmres_run<NB, TA, float, float>(h, h->gw[1], Alo, B32, r32, d32, inner_m, inner_tol,
+                                             h->p.max_it - inner_total, &in);
+        if (s != DG_OK && s != DG_NOT_CONVERGED) return s;
+        inner_total += in.iterations;
+        k_mx_update<<<gx, 256, 0, h->stream>>>(x, d32, n, ms);
+        h->nlaunch += 1;
+        DG_LAUNCH_CK(h);
+        ++outer;
+    }
+    if (info) {
+        info->iterations = inner_total;
+        info->restarts = 0;
+        info->outer = outer;
+        info->relres = hm.relres;
+        info->status = converged ? DG_OK : DG_NOT_CONVERGED;
+    }
+    h->err.clear();
+    if (!converged) return dg_fail(h, DG_NOT_CONVERGED, "mixed-precision refinement did not reach the tolerance");
+    return DG_OK;
+}
+
+extern "C" dg_status dg_mixed_solve(dg_handle* h, int inner_dtype, int inner_m, double inner_tol, int max_outer,
+                                    const double* F, double* x, dg_solve_info* info) {
+    if (!h || !x) return DG_ERR_INVALID_ARG;
+    if (!h->assembled) return dg_fail(h, DG_ERR_STATE, "not assembled");
+    if (!h->A64) return dg_fail(h, DG_ERR_STATE, "the f64 blocks are needed for the outer residual");
+    if (inner_dtype != DG_F32 && inner_dtype != DG_BF16) return dg_fail(h, DG_ERR_INVALID_ARG, "inner_dtype");
+    if (inner_dtype == DG_F32 && !h->A32) return dg_fail(h, DG_ERR_STATE, "f32 blocks not stored");
+    if (inner_dtype == DG_BF16 && !h->A16) return dg_fail(h, DG_ERR_STATE, "bf16 blocks not stored");
+    if (inner_m < 1 || inner_m > DG_MAXM || !(inner_tol > 0.0 && inner_tol < 1.0) || max_outer < 1)
+        return dg_fail(h, DG_ERR_INVALID_ARG, "inner_m / inner_tol / max_outer");
+    if (h->p.precond == DG_PRECOND_BLOCK_JACOBI && !h->bj_ok) {
+        dg_status s = dg_precond_setup(h, DG_PRECOND_BLOCK_JACOBI);
+        if (s != DG_OK) return s;
+    }
+    DG_CK(h, cudaSetDevice(h->device));
+    if (!F) F = h->F;
+    if (!dg_aligned16(F) || !dg_aligned16(x)) return dg_fail(h, DG_ERR_INVALID_ARG, "F and x must be 16-byte aligned");
+    const int nb = dg_nb(h->asm_k);
+#define DG_MIX(NBV)                                                                                          \
+    if (nb == NBV)                                                                                           \
+        return inner_dtype == DG_F32                                                                         \
+                   ? mixed_run<NBV, float>(h, h->A32, F, x, inner_m, inner_tol, max_outer, info)             \
+                   : mixed_run<NBV, __nv_bfloat16>(h, h->A16, F, x, inner_m, inner_tol, max_outer, info);
+    DG_MIX(3)
+    DG_MIX(6)
+    DG_MIX(10)
+#undef DG_MIX
     return dg_fail(h, DG_ERR_INVALID_ARG, "degree");
 }

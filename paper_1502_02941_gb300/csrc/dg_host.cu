@@ -54,12 +54,10 @@ dg_status dg_scratch(dg_handle* h, size_t bytes) {
 
 static void free_all(dg_handle* h) {
     void* ptrs[] = {h->nodes, h->elems, h->geo, h->nbr, h->nface, h->ftype, h->bidx, h->bedge, h->tab,
-                    h->A64, h->A32, h->A16, h->F, h->Binv64, h->Binv32, h->V, h->Z, h->R,
-                    h->partials, h->st, h->scratch, h->dflag};
+                    h->A64, h->A32, h->A16, h->F, h->Binv64, h->Binv32, h->scratch, h->dflag, h->mx_buf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
-    if (h->st_host) cudaFreeHost(h->st_host);
-    if (h->gm_graph) cudaGraphExecDestroy(h->gm_graph);
+    for (GmresWork& w : h->gw) dg_gmres_free(&w);
 }
 
 extern "C" const char* dg_status_string(dg_status s) {
@@ -129,10 +127,11 @@ extern "C" dg_status dg_destroy(dg_handle* h) {
 extern "C" dg_status dg_set_stream(dg_handle* h, void* stream) {
     if (!h) return DG_ERR_INVALID_ARG;
     h->stream = (cudaStream_t)stream;
-    if (h->gm_graph) {
-        cudaGraphExecDestroy(h->gm_graph);
-        h->gm_graph = nullptr;
-    }
+    for (GmresWork& w : h->gw)
+        if (w.graph) {
+            cudaGraphExecDestroy(w.graph);
+            w.graph = nullptr;
+        }
     return DG_OK;
 }
 

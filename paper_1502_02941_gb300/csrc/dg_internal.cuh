@@ -50,6 +50,24 @@ struct TabLayout {
 
 struct GmresState;   // device-side solver state (dg_gmres.cu)
 
+// Workspace of one restarted-GMRES solver instance (vectors of `elem` bytes).
+struct GmresWork {
+    size_t n = 0;
+    int m = 0;
+    size_t elem = 0;
+    void* V = nullptr;             // [(m+2)][n] Krylov basis, unnormalised
+    void* Z = nullptr;             // [n] preconditioned vector / correction
+    void* R = nullptr;             // [n] work vector
+    double* partials = nullptr;    // per-block reduction scratch
+    GmresState* st = nullptr;      // device state
+    GmresState* st_host = nullptr; // pinned mirror of the state header
+    cudaGraphExec_t graph = nullptr;
+    uintptr_t key[6] = {0, 0, 0, 0, 0, 0};
+    int nodes = 0;
+    int gx = 0;    // grid of the 1-D vector kernels (4 blocks of 256 per SM)
+    int gsm = 0;   // grid of the multi-dot kernel (one 1024-thread block per SM)
+};
+
 struct dg_handle {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -90,17 +108,9 @@ struct dg_handle {
     double* Binv64 = nullptr;
     float* Binv32 = nullptr;
 
-    // GMRES workspace
-    size_t gm_n = 0;
-    int gm_m = 0;
-    double* V = nullptr;           // [(m+1)][n]
-    double* Z = nullptr;           // [n]   work vector
-    double* R = nullptr;           // [n]   work vector
-    double* partials = nullptr;    // reduction scratch
-    GmresState* st = nullptr;      // device state
-    GmresState* st_host = nullptr; // pinned mirror
-    cudaGraphExec_t gm_graph = nullptr;
-    int gm_graph_key[4] = {0, 0, 0, 0};
+    // GMRES workspaces: [0] the f64 solver, [1] the f32 inner solver of the
+    // mixed-precision refinement
+    GmresWork gw[2];
 
     // misc scratch
     double* scratch = nullptr;
@@ -110,11 +120,14 @@ struct dg_handle {
     // instrumentation: kernels launched by this handle (graph launches count
     // every kernel node of the graph)
     long long nlaunch = 0;
-    int gm_nodes = 0;
 
     // capacities (bytes) of arrays that are re-sized only when they must grow
     size_t cap_nodes = 0, cap_elems = 0, cap_geo = 0, cap_face = 0, cap_bedge = 0;
     size_t cap_binv64 = 0, cap_binv32 = 0, cap_F = 0;
+
+    // mixed-precision refinement buffers (r64, A x, r32, d32, state)
+    void* mx_buf = nullptr;
+    size_t cap_mx = 0;
 };
 
 // error helpers (dg_host.cu)
@@ -148,6 +161,7 @@ dg_status dg_launch_assemble(dg_handle* h, const dg_coeffs* c, double kappa, dou
 dg_status dg_launch_apply(dg_handle* h, int dtype, const void* x, void* y);
 dg_status dg_launch_bj_setup(dg_handle* h);
 dg_status dg_launch_bj_apply(dg_handle* h, int dtype, const void* r, void* z, const double* scale);
+void dg_gmres_free(GmresWork* w);
 
 // ---------------------------------------------------------------------------
 // device helpers

@@ -329,3 +329,29 @@ def test_nonfinite_data_reported():
         h.gmres_solve()
     assert e.value.status == D.DG_ERR_NONFINITE
     h.close()
+
+
+# ----------------------------------------------------------------------------
+# mixed-precision refinement
+# ----------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("inner", ["f32", "bf16"])
+def test_mixed_refinement_reaches_f64_tolerance(inner):
+    """bf16/f32 inner solves with f64 refinement reach rel-res 1e-10, measured
+    by the oracle's own f64 operator (reading A-12)."""
+    cfg = W.config3(N=12)
+    ma = W.structured_mesh(cfg.N, cfg.problem.neumann_sides)
+    store = D.DG_STORE_F64 | (D.DG_STORE_F32 if inner == "f32" else D.DG_STORE_BF16)
+    h = gpu_setup(ma, cfg.k, cfg.method, cfg.problem, store=store, tol=1e-10)
+    dt = D.DG_F32 if inner == "f32" else D.DG_BF16
+    xg, info = h.mixed_solve(dt, inner_m=30, inner_tol=1e-4 if inner == "f32" else 1e-2, max_outer=40)
+    assert info.status == D.DG_OK and info.relres <= 1e-10 and info.outer >= 1
+    run = oracle_run(ma, cfg.k, cfg.method, cfg.problem)
+    T = basis_change(run, ma, cfg.k)
+    assert rel_residual_oracle(run, T, _np(xg)) <= 1e-10 * 1.5
+    # same solution as the f64 GMRES path, as functions
+    x64, _ = h.gmres_solve()
+    xo = x_to_oracle(T, _np(x64))
+    assert np.abs(x_to_oracle(T, _np(xg)) - xo).max() <= 1e-7 * np.abs(xo).max()
+    h.close()
