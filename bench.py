@@ -34,6 +34,7 @@ WORKLOAD = "cfg2: 256x256 split squares (131072 triangles), P2 (786432 dofs), NI
            "b=(1,0), alpha=1, boundary-layer u, all Dirichlet, GMRES(50)+block-Jacobi f64 to rel-res 1e-10"
 N_MESH, DEGREE = 256, 2
 METHODS = (1, 2)   # NIPG, SIPG
+SMS, SM_MAX_GHZ, FP64_FMA_PER_CLK_SM = 152, 2.07, 2   # GB300: FP64 is 1/64 of FP32 per SM
 
 
 def parse():
@@ -297,30 +298,90 @@ def main():
     e2e_value = solves / (ms_e2e / 1e3)
     its = [last[m][0] for m in METHODS]
 
-    # ---- roofline of the operator apply (f64), CUDA events on the same stream
-    y = torch.empty_like(x)
-    xr = torch.randn(dofs, dtype=torch.float64, device=dev)
-    for _ in range(3):
-        h.apply(xr, D.DG_F64, y)
-    nrep = 50
-    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # ---- mixed precision on the same workload: bf16 / f32 inner GMRES with f64 refinement
+    def mixed_steps(inner, nsteps):
+        store = D.DG_STORE_F64 | (D.DG_STORE_BF16 if inner == D.DG_BF16 else D.DG_STORE_F32)
+        tol_in = 1e-2 if inner == D.DG_BF16 else 1e-4
+        res = {}
+        for method in METHODS:
+            h.mesh_upload(ma.nodes, ma.elems, ma.dirichlet, ma.neumann)
+            h.set_params(method=method, degree=DEGREE, sigma_int=0.0, store=store, gmres_m=50, tol=1e-10,
+                         max_it=20000)
+            h.assemble(p.eps, p.alpha, p.b, f, gD, gN)
+            h.precond_setup()
+            _, si = h.mixed_solve(inner, inner_m=50, inner_tol=tol_in, max_outer=60, x=x, raise_on_nonconv=False)
+            res[method] = si
+        return res
+
+    mixed = {}
+    for name, inner in (("bf16", D.DG_BF16), ("f32", D.DG_F32)):
+        mixed_steps(inner, 1)   # warm-up (graph capture, workspaces)
+        torch.cuda.synchronize()
+        m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        m0.record(stream)
+        for _ in range(args.steps):
+            res = mixed_steps(inner, args.steps)
+        m1.record(stream)
+        torch.cuda.synchronize()
+        mms = m0.elapsed_time(m1)
+        mixed[name] = {"solves_per_s": len(METHODS) * args.steps / (mms / 1e3),
+                       "ms_per_solve": mms / (len(METHODS) * args.steps),
+                       "inner_iterations": {"NIPG": res[1].iterations, "SIPG": res[2].iterations},
+                       "outer": {"NIPG": res[1].outer, "SIPG": res[2].outer},
+                       "relres_f64": {"NIPG": res[1].relres, "SIPG": res[2].relres},
+                       "converged": all(r.status == 0 for r in res.values()),
+                       "speedup_vs_f64": (len(METHODS) * args.steps / (mms / 1e3)) / value}
+
+    # ---- kernel timings with CUDA events on the launching stream
+    h.mesh_upload(ma.nodes, ma.elems, ma.dirichlet, ma.neumann)
+    h.set_params(method=2, degree=DEGREE, sigma_int=0.0, store=D.DG_STORE_F64 | D.DG_STORE_F32 | D.DG_STORE_BF16,
+                 gmres_m=50, tol=1e-10, max_it=20000)
+    h.assemble(p.eps, p.alpha, p.b, f, gD, gN)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
-    tot = 0.0
-    for _ in range(nrep):
-        flush.fill_(1.0)
-        a0.record(stream)
-        h.apply(xr, D.DG_F64, y)
-        a1.record(stream)
-        a1.synchronize()
-        tot += a0.elapsed_time(a1)
-    apply_ms = tot / nrep
-    abytes = apply_bytes(info.ne, info.n_interior, info.nb, 8, 8)
+
+    def time_apply(dt, reps=30):
+        td = torch.float64 if dt == D.DG_F64 else torch.float32
+        xr = torch.randn(dofs, dtype=td, device=dev)
+        yr = torch.empty_like(xr)
+        for _ in range(3):
+            h.apply(xr, dt, yr)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        for _ in range(reps):
+            flush.fill_(1.0)
+            a0.record(stream)
+            h.apply(xr, dt, yr)
+            a1.record(stream)
+            a1.synchronize()
+            tot += a0.elapsed_time(a1)
+        return tot / reps
+
     peak, peak_src = measured_peaks()
-    achieved = abytes / (apply_ms / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "k_apply<6,double,double,double>", "achieved": achieved,
-                "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": profile_traffic("k_apply_f64_cfg2"),
-                "algorithmic_bytes": abytes, "avg_launch_ms": apply_ms, "peak_source": peak_src + " (hbm_gbs)"}
+    apply = {}
+    for name, dt, sa, sx in (("f64", D.DG_F64, 8, 8), ("f32", D.DG_F32, 4, 4), ("bf16", D.DG_BF16, 2, 4)):
+        ams = time_apply(dt)
+        abytes = apply_bytes(info.ne, info.n_interior, info.nb, sa, sx)
+        apply[name] = {"ms": ams, "bytes": abytes, "GBps": abytes / (ams / 1e3) / 1e9,
+                       "frac_hbm": abytes / (ams / 1e3) / 1e9 / peak}
+    apply["f64"]["fma_per_apply"] = (info.ne + 2 * info.n_interior) * info.nb * info.nb
+    jmid = 25
+    dots_ms = h.profile_kernel(D.DG_PROF_DOTS, D.DG_F64, jmid)
+    upd_ms = h.profile_kernel(D.DG_PROF_UPDATE, D.DG_F64, jmid)
+    fp64_peak_tflops = FP64_FMA_PER_CLK_SM * 2 * SMS * SM_MAX_GHZ * 1e9 / 1e12
+    dots_flops = 2.0 * (jmid + 2) * dofs
+    upd_flops = 2.0 * (jmid + 1) * dofs
+    roofline = {"bound": "alu", "kernel": f"k_gm_dots<double> (Arnoldi multi-dot, step j={jmid}, the largest "
+                                          "share of the f64 GMRES step)",
+                "achieved": dots_flops / (dots_ms / 1e3) / 1e12, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                "frac": dots_flops / (dots_ms / 1e3) / 1e12 / fp64_peak_tflops,
+                "traffic": profile_traffic("k_gm_dots_f64_cfg2"),
+                "algorithmic_flops": dots_flops, "algorithmic_bytes": 8.0 * (jmid + 2) * dofs,
+                "avg_launch_ms": dots_ms,
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (f64 FMA probe measured "
+                               "1.19 TFLOP/s); HBM peak for the applies is measured hbm_gbs"}
+    kernels = {"k_gm_update<double>": {"ms": upd_ms, "TFLOPs": upd_flops / (upd_ms / 1e3) / 1e12,
+                                       "GBps": 8.0 * (jmid + 3) * dofs / (upd_ms / 1e3) / 1e9},
+               "k_apply": apply}
 
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -332,7 +393,8 @@ def main():
                        "l2_policy": "working set > L2 (blocks 151 MB + Krylov basis 321 MB per solve)",
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches, "clocks": clocks, "roofline": roofline}
+            "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
+            "mixed": mixed, "kernels": kernels, "hbm_peak_GBps": peak}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ref_its, _ = oracle_iteration_counts()
         scale_its = ref_its if ref_its else its

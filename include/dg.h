@@ -297,6 +297,48 @@ dg_status dg_mixed_solve(dg_handle* h, int inner_dtype, int inner_m, double inne
 dg_status dg_dense_solve(dg_handle* h, const double* F, double* x);
 
 /* ------------------------------------------------------------------------ */
+/* batches of independent instances                                          */
+/* ------------------------------------------------------------------------ */
+/*
+ * Declare a batch.  The uploaded mesh (dg_mesh_upload) is the concatenation of
+ * n_inst independent meshes: instance i owns elements [elem_start[i],
+ * elem_start[i+1]) (host [n_inst+1], from 0 to ne); no edge may join two
+ * instances (DG_ERR_MESH).  coeffs host [n_inst][8] = eps, alpha, b[0..5] of
+ * each instance (Eq. (1)); degree, method and penalties come from the params
+ * and are shared.  After this call dg_assemble assembles every instance with
+ * its own coefficients in one pass (the eps/alpha/b of dg_coeffs are ignored;
+ * f, gD, gN are read as usual over the whole concatenated mesh).
+ */
+dg_status dg_batch_setup(dg_handle* h, int n_inst, const int* elem_start, const double* coeffs);
+
+/* Leave batch mode (dg_assemble uses dg_coeffs again). */
+dg_status dg_batch_clear(dg_handle* h);
+
+/* Choose the work-item size of the batched reductions (unknowns per item,
+   from 2048 to 32768) by timing the batched multi-dot on the assembled batch;
+   the choice is kept in the handle and returned in *tile.  Synchronises. */
+dg_status dg_batch_autotune(dg_handle* h, int* tile);
+
+/* Set the work-item size directly (256..2^20), or 0 for the default 4096. */
+dg_status dg_batch_set_tile(dg_handle* h, int tile);
+
+/*
+ * Solve every instance of the batch.  inner_dtype DG_F64: restarted GMRES
+ * (params.gmres_m) in f64 per instance, all instances advancing together with
+ * per-instance reductions, Hessenberg/Givens and convergence.  DG_F32 /
+ * DG_BF16: per-instance f64 iterative refinement (as dg_mixed_solve) around a
+ * batched GMRES(inner_m) on f32 vectors with the f32 / bf16 block copy.
+ * Each instance stops when its own ||F_i - A_i x_i|| / ||F_i|| <= params.tol.
+ *   F device [dofs] f64 or NULL (assembled F); x device [dofs] f64 output;
+ *   its, relres, status: host [n_inst] or NULL -- Arnoldi steps (inner steps
+ *   summed over corrections), final f64 relative residual, DG_OK /
+ *   DG_NOT_CONVERGED per instance.
+ * Returns DG_NOT_CONVERGED if any instance missed the tolerance.  Synchronises.
+ */
+dg_status dg_batch_solve(dg_handle* h, int inner_dtype, int inner_m, double inner_tol, int max_outer,
+                         const double* F, double* x, int* its, double* relres, int* status);
+
+/* ------------------------------------------------------------------------ */
 /* post-processing  (the paper's dg_error, Sec. 2.4)                        */
 /* ------------------------------------------------------------------------ */
 /*
@@ -333,6 +375,18 @@ dg_status dg_l2_error_noalloc(dg_handle* h, const double* x, const double* uex_q
 /* ------------------------------------------------------------------------ */
 /* instrumentation                                                           */
 /* ------------------------------------------------------------------------ */
+/*
+ * Average device time (CUDA events on the handle's stream) of one solver
+ * kernel run in isolation on the handle's GMRES workspace, for roofline
+ * accounting: which = DG_PROF_DOTS (the multi-dot of an Arnoldi step) or
+ * DG_PROF_UPDATE (its Gram-Schmidt update), at step `param` = j (0 <= j <
+ * gmres_m), for dtype DG_F64 (f64 vectors) or DG_F32 (f32 vectors), averaged
+ * over reps launches.  Overwrites the workspace.  Synchronises.
+ */
+#define DG_PROF_DOTS   1
+#define DG_PROF_UPDATE 2
+dg_status dg_profile_kernel(dg_handle* h, int which, int dtype, int param, int reps, double* avg_ms);
+
 /* Number of CUDA kernels this handle has launched so far (a graph launch
    counts each kernel node of the graph).  Host counter, no synchronisation. */
 dg_status dg_get_launch_count(dg_handle* h, int64_t* count);

@@ -1,0 +1,80 @@
+"""Command-line solve of one workload through libdg.
+
+    python -m paper_1502_02941_gb300.cli --config 2 --N 256 --method 2 --solver gmres
+    python -m paper_1502_02941_gb300.cli --config 3 --N 64 --solver mixed-bf16
+
+Prints one JSON line with sizes, iterations, relative residual, L2 error (when
+the workload has an exact solution) and wall time of the solve.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3])
+    ap.add_argument("--N", type=int, default=None)
+    ap.add_argument("--method", type=int, default=None, help="1 NIPG, 2 SIPG, 3 IIPG")
+    ap.add_argument("--solver", default="gmres", choices=["gmres", "dense", "mixed-bf16", "mixed-f32"])
+    ap.add_argument("--m", type=int, default=50)
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--max-it", type=int, default=20000)
+    ap.add_argument("--repeat", type=int, default=1)
+    a = ap.parse_args(argv)
+
+    import torch
+
+    from . import dg as D
+    from . import problem
+    from . import workloads as W
+
+    if a.config == 1:
+        cfg = W.config1()
+    elif a.config == 2:
+        cfg = W.config2(method=a.method or 2, N=a.N or 256)
+    else:
+        cfg = W.config3(N=a.N or 512)
+    if a.N and a.config == 1:
+        cfg.N = a.N
+    if a.method:
+        cfg.method = a.method
+    store = D.DG_STORE_F64
+    if a.solver == "mixed-bf16":
+        store |= D.DG_STORE_BF16
+    elif a.solver == "mixed-f32":
+        store |= D.DG_STORE_F32
+    h = D.DG(0)
+    problem.setup(h, cfg, store=store, gmres_m=a.m, tol=a.tol, max_it=a.max_it)
+    h.precond_setup()
+    info = h.info()
+    out = {}
+    for _ in range(a.repeat):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if a.solver == "dense":
+            x = h.dense_solve()
+            si = None
+        elif a.solver == "gmres":
+            x, si = h.gmres_solve(raise_on_nonconv=False)
+        else:
+            dt = D.DG_BF16 if a.solver == "mixed-bf16" else D.DG_F32
+            x, si = h.mixed_solve(dt, inner_m=a.m, inner_tol=1e-2 if dt == D.DG_BF16 else 1e-4, max_outer=60,
+                                  raise_on_nonconv=False)
+        torch.cuda.synchronize()
+        out["seconds"] = time.perf_counter() - t0
+    if si is not None:
+        out.update(iterations=si.iterations, outer=si.outer, relres=si.relres, status=D.status_name(si.status))
+    if cfg.problem.exact is not None:
+        l2, hmax = h.l2_error(x, problem.exact_at_error_points(h, cfg.problem))
+        out.update(l2_error=l2, h_max=hmax)
+    out.update(config=a.config, N=cfg.N, k=cfg.k, method=cfg.method, ne=info.ne, dofs=info.dofs,
+               solver=a.solver)
+    print(json.dumps(out))
+    h.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -10,16 +10,17 @@
 // boundary) + 2*nb*sizeof(TX) + 12 (neighbour ids) -> HBM-bound.
 #include "dg_kernels.cuh"
 
-// Gauss-Jordan inverse with partial pivoting of each diagonal block A_KK.
-template <int NB>
-__global__ void __launch_bounds__(128) k_bj_setup(const double* __restrict__ A, int ne, double* Binv64,
+// Gauss-Jordan inverse with partial pivoting (in f64) of each diagonal block
+// A_KK read from the block copy of type TA; Binv64 may be NULL.
+template <int NB, typename TA>
+__global__ void __launch_bounds__(128) k_bj_setup(const TA* __restrict__ A, int ne, double* Binv64,
                                                    float* Binv32, int* flag) {
     const int K = blockIdx.x * blockDim.x + threadIdx.x;
     if (K >= ne) return;
     double M[NB][2 * NB];
     for (int i = 0; i < NB; ++i)
         for (int j = 0; j < NB; ++j) {
-            M[i][j] = A[dg_blk_index<double>(K, 0, i * NB + j, NB, 4)];
+            M[i][j] = (double)A[dg_blk_index<TA>(K, 0, i * NB + j, NB, 4)];
             M[i][NB + j] = i == j ? 1.0 : 0.0;
         }
     double amax = 0.0;
@@ -51,14 +52,14 @@ __global__ void __launch_bounds__(128) k_bj_setup(const double* __restrict__ A, 
     if (singular) {
         atomicOr(flag, 1);
         for (int m = 0; m < NB * NB; ++m) {
-            Binv64[dg_blk_index<double>(K, 0, m, NB, 1)] = 0.0;
+            if (Binv64) Binv64[dg_blk_index<double>(K, 0, m, NB, 1)] = 0.0;
             Binv32[dg_blk_index<float>(K, 0, m, NB, 1)] = 0.0f;
         }
         return;
     }
     for (int i = 0; i < NB; ++i)
         for (int j = 0; j < NB; ++j) {
-            Binv64[dg_blk_index<double>(K, 0, i * NB + j, NB, 1)] = M[i][NB + j];
+            if (Binv64) Binv64[dg_blk_index<double>(K, 0, i * NB + j, NB, 1)] = M[i][NB + j];
             Binv32[dg_blk_index<float>(K, 0, i * NB + j, NB, 1)] = (float)M[i][NB + j];
         }
 }
@@ -149,13 +150,30 @@ dg_status dg_launch_bj_setup(dg_handle* h) {
     DG_CK(h, cudaMemsetAsync(h->Binv32, 0, b32, h->stream));
     DG_CK(h, cudaMemsetAsync(h->dflag, 0, sizeof(int), h->stream));
     const unsigned grid = (unsigned)((h->ne + 127) / 128);
+    // with a bf16 copy stored, the bf16 inner solves get the inverses of the
+    // bf16 diagonal blocks themselves (M^-1 A_bf16 has identity diagonal blocks)
+    float* B16 = nullptr;
+    if (h->A16) {
+        if ((s = dg_ensure(h, (void**)&h->Binv16, &h->cap_binv16, b32)) != DG_OK) return s;
+        DG_CK(h, cudaMemsetAsync(h->Binv16, 0, b32, h->stream));
+        B16 = h->Binv16;
+    }
     switch (nb) {
-        case 3: k_bj_setup<3><<<grid, 128, 0, h->stream>>>(h->A64, h->ne, h->Binv64, h->Binv32, h->dflag); break;
-        case 6: k_bj_setup<6><<<grid, 128, 0, h->stream>>>(h->A64, h->ne, h->Binv64, h->Binv32, h->dflag); break;
-        case 10: k_bj_setup<10><<<grid, 128, 0, h->stream>>>(h->A64, h->ne, h->Binv64, h->Binv32, h->dflag); break;
+        case 3:
+            k_bj_setup<3, double><<<grid, 128, 0, h->stream>>>(h->A64, h->ne, h->Binv64, h->Binv32, h->dflag);
+            if (B16) k_bj_setup<3, __nv_bfloat16><<<grid, 128, 0, h->stream>>>(h->A16, h->ne, nullptr, B16, h->dflag);
+            break;
+        case 6:
+            k_bj_setup<6, double><<<grid, 128, 0, h->stream>>>(h->A64, h->ne, h->Binv64, h->Binv32, h->dflag);
+            if (B16) k_bj_setup<6, __nv_bfloat16><<<grid, 128, 0, h->stream>>>(h->A16, h->ne, nullptr, B16, h->dflag);
+            break;
+        case 10:
+            k_bj_setup<10, double><<<grid, 128, 0, h->stream>>>(h->A64, h->ne, h->Binv64, h->Binv32, h->dflag);
+            if (B16) k_bj_setup<10, __nv_bfloat16><<<grid, 128, 0, h->stream>>>(h->A16, h->ne, nullptr, B16, h->dflag);
+            break;
         default: return dg_fail(h, DG_ERR_INVALID_ARG, "degree");
     }
-    h->nlaunch += 1;
+    h->nlaunch += B16 ? 2 : 1;
     DG_LAUNCH_CK(h);
     int flag = 0;
     DG_CK(h, cudaMemcpyAsync(&flag, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));

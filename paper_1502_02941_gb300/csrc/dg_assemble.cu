@@ -37,6 +37,10 @@ struct AsmArgs {
     double* A64;
     float* A32;
     __nv_bfloat16* A16;
+    // per-instance coefficients of a batch (NULL for one instance): element K
+    // uses icoef[DG_ICOEF * inst[K] + ...] = eps, alpha, b[6], sigma_int, sigma_bdry
+    const int* inst;
+    const double* icoef;
     // RHS data
     const double* f;
     double f_const;
@@ -88,7 +92,19 @@ __global__ void __launch_bounds__(256) k_assemble(const AsmArgs a) {
         const double i00 = gload(a.geo, G_I00, ne, K), i01 = gload(a.geo, G_I01, ne, K);
         const double i10 = gload(a.geo, G_I10, ne, K), i11 = gload(a.geo, G_I11, ne, K);
         const double det = gload(a.geo, G_DET, ne, K);
-        const double eps = a.eps, alpha = a.alpha;
+        double eps = a.eps, alpha = a.alpha, sig_int = a.sig_int, sig_bdry = a.sig_bdry;
+        double bc[6];
+#pragma unroll
+        for (int t = 0; t < 6; ++t) bc[t] = a.b[t];
+        if (a.inst) {
+            const double* c = a.icoef + (size_t)DG_ICOEF * a.inst[K];
+            eps = c[0];
+            alpha = c[1];
+#pragma unroll
+            for (int t = 0; t < 6; ++t) bc[t] = c[2 + t];
+            sig_int = c[8];
+            sig_bdry = c[9];
+        }
 
         // ---- volume integrals ------------------------------------------------
         const double* vw = sm + L.vol_w;
@@ -108,8 +124,8 @@ __global__ void __launch_bounds__(256) k_assemble(const AsmArgs a) {
             const double gxj = i00 * drj + i10 * dsj, gyj = i01 * drj + i11 * dsj;
             const double x = x0 + j00 * vr[q] + j01 * vs[q];
             const double y = y0 + j10 * vr[q] + j11 * vs[q];
-            const double bx = a.b[0] + a.b[1] * x + a.b[2] * y;
-            const double by = a.b[3] + a.b[4] * x + a.b[5] * y;
+            const double bx = bc[0] + bc[1] * x + bc[2] * y;
+            const double by = bc[3] + bc[4] * x + bc[5] * y;
             acc += w * (eps * (gxj * gxi + gyj * gyi) + (bx * gxj + by * gyj) * pi + alpha * pj * pi);
         }
 
@@ -138,7 +154,7 @@ __global__ void __launch_bounds__(256) k_assemble(const AsmArgs a) {
                 li10 = gload(a.geo, G_I10, ne, Ln);
                 li11 = gload(a.geo, G_I11, ne, Ln);
             }
-            const double sig = type == 0 ? a.sig_int : a.sig_bdry;
+            const double sig = type == 0 ? sig_int : sig_bdry;
             double self = 0.0, cross = 0.0;
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
@@ -149,7 +165,7 @@ __global__ void __launch_bounds__(256) k_assemble(const AsmArgs a) {
                 const double gjn = (i00 * fdr[o + j] + i10 * fds[o + j]) * nx + (i01 * fdr[o + j] + i11 * fds[o + j]) * ny;
                 const double x = x0 + j00 * fr[f * NQ + q] + j01 * fs[f * NQ + q];
                 const double y = y0 + j10 * fr[f * NQ + q] + j11 * fs[f * NQ + q];
-                const double bn = (a.b[0] + a.b[1] * x + a.b[2] * y) * nx + (a.b[3] + a.b[4] * x + a.b[5] * y) * ny;
+                const double bn = (bc[0] + bc[1] * x + bc[2] * y) * nx + (bc[3] + bc[4] * x + bc[5] * y) * ny;
                 const double up = bn < 0.0 ? bn : 0.0;
                 if (type == 0) {
                     const int oo = (nf * NQ + (NQ - 1 - q)) * NB;   // same point seen from L
@@ -214,6 +230,17 @@ __global__ void __launch_bounds__(256) k_rhs(const AsmArgs a) {
     const double i00 = gload(a.geo, G_I00, ne, K), i01 = gload(a.geo, G_I01, ne, K);
     const double i10 = gload(a.geo, G_I10, ne, K), i11 = gload(a.geo, G_I11, ne, K);
     const double det = gload(a.geo, G_DET, ne, K);
+    double eps = a.eps, sig_bdry = a.sig_bdry;
+    double bc[6];
+#pragma unroll
+    for (int t = 0; t < 6; ++t) bc[t] = a.b[t];
+    if (a.inst) {
+        const double* c = a.icoef + (size_t)DG_ICOEF * a.inst[K];
+        eps = c[0];
+#pragma unroll
+        for (int t = 0; t < 6; ++t) bc[t] = c[2 + t];
+        sig_bdry = c[9];
+    }
     double acc = 0.0;
     for (int q = 0; q < QK; ++q) {
         const double fv = a.f ? __ldg(a.f + (size_t)K * QK + q) : a.f_const;
@@ -237,10 +264,10 @@ __global__ void __launch_bounds__(256) k_rhs(const AsmArgs a) {
                                (i01 * sm[L.face_dr + o] + i11 * sm[L.face_ds + o]) * ny;
             const double x = x0 + j00 * sm[L.face_r + f * NQ + q] + j01 * sm[L.face_s + f * NQ + q];
             const double y = y0 + j10 * sm[L.face_r + f * NQ + q] + j11 * sm[L.face_s + f * NQ + q];
-            const double bn = (a.b[0] + a.b[1] * x + a.b[2] * y) * nx + (a.b[3] + a.b[4] * x + a.b[5] * y) * ny;
+            const double bn = (bc[0] + bc[1] * x + bc[2] * y) * nx + (bc[3] + bc[4] * x + bc[5] * y) * ny;
             const double up = bn < 0.0 ? bn : 0.0;
             const double gD = a.gD ? __ldg(a.gD + (size_t)b * NQ + q) : a.gD_const;
-            if (type == 1) acc += w * gD * (a.sig_bdry * a.eps / he * pi + a.kappa * a.eps * gin);
+            if (type == 1) acc += w * gD * (sig_bdry * eps / he * pi + a.kappa * eps * gin);
             acc -= w * up * gD * pi;
             if (type == 2) {
                 const double gN = a.gN ? __ldg(a.gN + (size_t)b * NQ + q) : a.gN_const;
@@ -279,6 +306,8 @@ dg_status dg_launch_assemble(dg_handle* h, const dg_coeffs* c, double kappa, dou
     a.gN = c->gN;
     a.gN_const = c->gN_const;
     a.F = h->F;
+    a.inst = h->b_inst_active ? h->b_inst : nullptr;
+    a.icoef = h->b_inst_active ? h->b_icoef : nullptr;
     const size_t smem = sizeof(double) * h->tl.err_w;
     const long warps_a = (long)h->ntiles * nb * nb;
     const long warps_r = (long)h->ntiles * nb;

@@ -1,0 +1,940 @@
+// dg_batch.cu -- many independent instances of the DG problem solved together.
+//
+// The uploaded mesh is the concatenation of the instances' meshes (disjoint,
+// each instance a contiguous range of elements), so assembly, the operator
+// apply and the block-Jacobi apply run as single launches over all elements,
+// with per-element instance ids selecting each instance's coefficients and
+// skipping the elements of instances that are already done.  The Krylov
+// reductions are segmented: the unknowns are cut into work items of `tile`
+// entries that never straddle two instances; a persistent grid walks the item
+// list, each item leaves one partial per dot, and the last item of an instance
+// to arrive (per-instance arrival counter, no waiting) reduces that
+// instance's partials in a fixed order and runs the instance's Hessenberg /
+// Givens step.  All active instances take Arnoldi step j together and restart
+// together every m steps; an instance that meets its tolerance drops out.
+// One restart cycle is captured in a CUDA graph; the host reads the number of
+// still-active instances between cycles.
+//
+// Mixed precision (inner_dtype DG_F32 / DG_BF16): per-instance f64 iterative
+// refinement, r = F - A64 x, inner batched GMRES on f32 vectors for
+// A_lo d = r/||r||, x += ||r|| d; instances whose f64 relative residual meets
+// the tolerance leave the refinement.  inner_dtype DG_F64: one batched f64
+// GMRES on A64 x = F.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <type_traits>
+#include <vector>
+
+#include "dg_kernels.cuh"
+
+struct BState {
+    int its, converged, done, reorth, pending, nonfinite, cycles, j;
+    unsigned int arrive;
+    int m, max_it, pad_;
+    double tol, bnorm, relres, wn2_before;
+    double scale[DG_MAXM + 2];
+    double hcol[DG_MAXM + 2];
+    double coef[DG_MAXM + 2];
+    double H[(DG_MAXM + 1) * DG_MAXM];
+    double cs[DG_MAXM], sn[DG_MAXM], g[DG_MAXM + 1], y[DG_MAXM];
+};
+
+// per-instance refinement state
+struct BOuter {
+    double bnorm, rnorm, relres;
+    unsigned int arrive;
+    int first;
+};
+
+struct BatchDev {
+    BState* bst;          // [nI]
+    BOuter* bo;           // [nI]
+    int* iactive;         // [nI] Arnoldi step active
+    int* ipending;        // [nI] cycle has a correction
+    int* iparticipate;    // [nI] takes part in the current inner solve
+    int* iouter;          // [nI] refinement still running
+    double* iscale;       // [nI] scale of the current basis vector
+    int* item_inst;       // [nit]
+    int* item_lo;         // [nit] first unknown
+    int* item_hi;         // [nit] one past the last unknown
+    int* inst_item_lo;    // [nI]
+    int* inst_item_hi;    // [nI]
+    double* partials;     // [nit][DG_MAXM+2]
+    int* jglob;           // current Arnoldi step of all active instances
+    int* counters;        // [4]: active instances, nonfinite, outer-active
+    int nI, nit;
+};
+
+#define B_TX 32
+#define B_TY 32
+#define B_DPT ((DG_MAXM + 2 + B_TY - 1) / B_TY)
+
+template <typename TV>
+struct BAcc {
+    double s = 0.0;
+    __device__ __forceinline__ void fma(double a, double b) { s = ::fma(a, b, s); }
+    __device__ __forceinline__ double get() const { return s; }
+};
+template <>
+struct BAcc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void fma(float a, float b) {
+        const float y = a * b - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double get() const { return (double)s - (double)c; }
+};
+
+// Per-instance arrival: true in the block that processed the instance's last
+// item.  Partials written before the call are visible to it (read with __ldcg).
+__device__ __forceinline__ bool inst_last(unsigned int* counter, int nitems) {
+    __shared__ int amlast;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        const unsigned int t = atomicAdd(counter, 1u);
+        amlast = (t == (unsigned)nitems - 1) ? 1 : 0;
+        if (amlast) *counter = 0u;
+    }
+    __syncthreads();
+    return amlast != 0;
+}
+
+__device__ __forceinline__ double block_sum_1d(double v, double* sh) { return dg_block_sum(v, sh); }
+
+// Sum partials[item][col] over the instance's items with all threads of a 1-D block.
+__device__ double inst_sum(const BatchDev& B, int inst, int col, double* sh) {
+    double s = 0.0;
+    for (int it = B.inst_item_lo[inst] + threadIdx.x; it < B.inst_item_hi[inst]; it += blockDim.x)
+        s += __ldcg(B.partials + (long)it * (DG_MAXM + 2) + col);
+    return dg_block_sum(s, sh);
+}
+
+// ---------------------------------------------------------------------------
+// inner batched GMRES kernels
+// ---------------------------------------------------------------------------
+// x = 0, V_0 = F on every item; last item of an instance: ||F||, state init.
+template <typename TV>
+__global__ void __launch_bounds__(256) k_b_init(const TV* __restrict__ F, TV* __restrict__ x, TV* __restrict__ V0,
+                                                 BatchDev B, int m, int max_it, double tol) {
+    __shared__ double sh[32];
+    for (int it = blockIdx.x; it < B.nit; it += gridDim.x) {
+        const int inst = B.item_inst[it];
+        double a = 0.0;
+        for (int l = B.item_lo[it] + threadIdx.x; l < B.item_hi[it]; l += blockDim.x) {
+            const TV f = F[l];
+            x[l] = (TV)0;
+            V0[l] = f;
+            a = ::fma((double)f, (double)f, a);
+        }
+        a = dg_block_sum(a, sh);
+        if (threadIdx.x == 0) B.partials[(long)it * (DG_MAXM + 2)] = a;
+        if (!inst_last(&B.bst[inst].arrive, B.inst_item_hi[inst] - B.inst_item_lo[inst])) continue;
+        const double b2 = inst_sum(B, inst, 0, sh);
+        if (threadIdx.x == 0) {
+            BState* st = B.bst + inst;
+            st->m = m;
+            st->max_it = max_it;
+            st->tol = tol;
+            st->its = 0;
+            st->cycles = 0;
+            st->reorth = 0;
+            st->pending = 0;
+            st->nonfinite = 0;
+            st->j = 0;
+            st->converged = 0;
+            const double bn = sqrt(b2);
+            st->bnorm = bn;
+            st->relres = 1.0;
+            int act = B.iparticipate[inst];
+            if (!isfinite(bn)) {
+                st->nonfinite = 1;
+                act = 0;
+                atomicAdd(B.counters + 1, 1);
+            } else if (bn == 0.0 || tol >= 1.0) {
+                st->converged = 1;
+                st->relres = 0.0;
+                act = 0;
+            }
+            st->done = act ? 0 : 1;
+            B.iactive[inst] = act;
+            B.ipending[inst] = 0;
+            for (int i = 0; i <= m; ++i) st->g[i] = 0.0;
+            st->g[0] = bn;
+            st->scale[0] = bn > 0.0 ? 1.0 / bn : 0.0;
+            B.iscale[inst] = st->scale[0];
+        }
+        __syncthreads();
+    }
+}
+
+// Segmented multi-dot: per item, r_d = <V_d, V_{j+1}> over the item's range.
+template <typename TV>
+__global__ void __launch_bounds__(B_TX* B_TY) k_b_dots(const TV* __restrict__ V, long ld, BatchDev B, int pass) {
+    const int j = *B.jglob;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int t = ty * B_TX + tx;
+    for (int it = blockIdx.x; it < B.nit; it += gridDim.x) {
+        const int inst = B.item_inst[it];
+        BState* st = B.bst + inst;
+        if (!B.iactive[inst] || (pass == 2 && !st->reorth)) continue;
+        const int dlast = pass == 1 ? j + 1 : j;
+        const TV* __restrict__ w = V + (long)(j + 1) * ld;
+        BAcc<TV> acc[B_DPT];
+        const int lo = B.item_lo[it], hi = B.item_hi[it];
+        for (int l = lo + tx; l < hi; l += B_TX) {
+            const TV wl = w[l];
+#pragma unroll
+            for (int k = 0; k < B_DPT; ++k) {
+                const int d = ty + B_TY * k;
+                if (d <= dlast) acc[k].fma(V[(long)d * ld + l], wl);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < B_DPT; ++k) {
+            const int d = ty + B_TY * k;
+            const double v = dg_warp_sum(acc[k].get());
+            if (tx == 0 && d <= dlast) B.partials[(long)it * (DG_MAXM + 2) + d] = v;
+        }
+        if (!inst_last(&st->arrive, B.inst_item_hi[inst] - B.inst_item_lo[inst])) continue;
+        // 16 threads per dot over the instance's items
+        const int ilo = B.inst_item_lo[inst], ihi = B.inst_item_hi[inst];
+        for (int d0 = 0; d0 <= dlast; d0 += (B_TX * B_TY) / 16) {
+            const int d = d0 + t / 16;
+            double r = 0.0;
+            if (d <= dlast)
+                for (int i2 = ilo + t % 16; i2 < ihi; i2 += 16) r += __ldcg(B.partials + (long)i2 * (DG_MAXM + 2) + d);
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+            if ((t % 16) == 0 && d <= dlast) {
+                if (d == j + 1) {
+                    st->wn2_before = r;
+                } else {
+                    const double hd = st->scale[d] * r;
+                    st->hcol[d] = pass == 1 ? hd : st->hcol[d] + hd;
+                    st->coef[d] = hd * st->scale[d];
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__device__ void b_finish_column(BatchDev& B, int inst, int j, double wn, const double* hc, const double* cs,
+                                const double* sn) {
+    BState* st = B.bst + inst;
+    const int LD = DG_MAXM + 1;
+    double* Hc = st->H + (long)j * LD;
+    double a = hc[0];
+    for (int i = 0; i < j; ++i) {
+        const double b = hc[i + 1];
+        Hc[i] = cs[i] * a + sn[i] * b;
+        a = -sn[i] * a + cs[i] * b;
+    }
+    const double r = hypot(a, wn);
+    const double c = r == 0.0 ? 1.0 : a / r, s = r == 0.0 ? 0.0 : wn / r;
+    st->cs[j] = c;
+    st->sn[j] = s;
+    Hc[j] = r;
+    Hc[j + 1] = 0.0;
+    const double gj = st->g[j];
+    st->g[j + 1] = -s * gj;
+    st->g[j] = c * gj;
+    st->scale[j + 1] = wn > 0.0 ? 1.0 / wn : 0.0;
+    B.iscale[inst] = st->scale[j + 1];
+    st->its += 1;
+    st->j = j + 1;
+    st->pending = 1;
+    B.ipending[inst] = 1;
+    const bool bad = !isfinite(wn) || !isfinite(r);
+    if (bad) st->nonfinite = 1;
+    const double est = fabs(s * gj);
+    const bool breakdown = !(wn > 1e-300) || !(r > 0.0);
+    if (bad || est <= st->tol * st->bnorm || j + 1 >= st->m || st->its >= st->max_it || breakdown)
+        B.iactive[inst] = 0;
+}
+
+// Segmented update: V_{j+1} -= sum_d coef_d V_d on each item; norm; last item
+// of the instance: re-orthogonalisation decision or Hessenberg/Givens step.
+template <typename TV>
+__global__ void __launch_bounds__(256) k_b_update(TV* V, long ld, BatchDev B, int pass) {
+    const int j = *B.jglob;
+    __shared__ TV c[DG_MAXM + 2];
+    __shared__ double sh[32];
+    __shared__ double hc[DG_MAXM + 2], css[DG_MAXM], sns[DG_MAXM];
+    for (int it = blockIdx.x; it < B.nit; it += gridDim.x) {
+        const int inst = B.item_inst[it];
+        BState* st = B.bst + inst;
+        if (!B.iactive[inst] || (pass == 2 && !st->reorth)) continue;
+        __syncthreads();
+        for (int d = threadIdx.x; d <= j; d += blockDim.x) c[d] = (TV)st->coef[d];
+        __syncthreads();
+        TV* w = V + (long)(j + 1) * ld;
+        double nrm = 0.0;
+        for (int l = B.item_lo[it] + threadIdx.x; l < B.item_hi[it]; l += blockDim.x) {
+            TV acc = w[l];
+            int d = 0;
+            for (; d + 4 <= j + 1; d += 4) {
+                const TV v0 = V[(long)d * ld + l], v1 = V[(long)(d + 1) * ld + l];
+                const TV v2 = V[(long)(d + 2) * ld + l], v3 = V[(long)(d + 3) * ld + l];
+                acc = ::fma(-c[d], v0, acc);
+                acc = ::fma(-c[d + 1], v1, acc);
+                acc = ::fma(-c[d + 2], v2, acc);
+                acc = ::fma(-c[d + 3], v3, acc);
+            }
+            for (; d <= j; ++d) acc = ::fma(-c[d], V[(long)d * ld + l], acc);
+            w[l] = acc;
+            nrm = ::fma((double)acc, (double)acc, nrm);
+        }
+        nrm = dg_block_sum(nrm, sh);
+        if (threadIdx.x == 0) B.partials[(long)it * (DG_MAXM + 2)] = nrm;
+        if (!inst_last(&st->arrive, B.inst_item_hi[inst] - B.inst_item_lo[inst])) continue;
+        const double wn2 = inst_sum(B, inst, 0, sh);
+        for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+            hc[i] = st->hcol[i];
+            if (i < j) {
+                css[i] = st->cs[i];
+                sns[i] = st->sn[i];
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const double wn = sqrt(wn2);
+            if (pass == 1 && wn < 0.7 * sqrt(st->wn2_before)) {
+                st->reorth = 1;
+            } else {
+                st->reorth = 0;
+                b_finish_column(B, inst, j, wn, hc, css, sns);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_b_step(BatchDev B) {
+    if (threadIdx.x == 0) *B.jglob += 1;
+}
+
+// y = H^-1 g per pending instance (one block per instance)
+__global__ void __launch_bounds__(256) k_b_solve(BatchDev B) {
+    const int inst = blockIdx.x;
+    if (!B.ipending[inst]) return;
+    BState* st = B.bst + inst;
+    __shared__ double gs[DG_MAXM + 1];
+    const int jj = st->j;
+    const int LD = DG_MAXM + 1;
+    for (int t = threadIdx.x; t < jj; t += blockDim.x) gs[t] = st->g[t];
+    __syncthreads();
+    for (int i = jj - 1; i >= 0; --i) {
+        const double d = st->H[(long)i * LD + i];
+        const double yi = d != 0.0 ? gs[i] / d : 0.0;
+        __syncthreads();
+        for (int l = threadIdx.x; l < i; l += blockDim.x) gs[l] -= st->H[(long)i * LD + l] * yi;
+        if (threadIdx.x == 0) {
+            st->y[i] = yi;
+            st->coef[i] = yi * st->scale[i];
+        }
+        __syncthreads();
+    }
+}
+
+// U = sum_{i<jj} coef_i V_i on the items of pending instances
+template <typename TV>
+__global__ void __launch_bounds__(256) k_b_combine(const TV* __restrict__ V, long ld, BatchDev B, TV* __restrict__ U) {
+    __shared__ TV c[DG_MAXM + 2];
+    for (int it = blockIdx.x; it < B.nit; it += gridDim.x) {
+        const int inst = B.item_inst[it];
+        if (!B.ipending[inst]) continue;
+        const BState* st = B.bst + inst;
+        const int jj = st->j;
+        __syncthreads();
+        for (int d = threadIdx.x; d < jj; d += blockDim.x) c[d] = (TV)st->coef[d];
+        __syncthreads();
+        for (int l = B.item_lo[it] + threadIdx.x; l < B.item_hi[it]; l += blockDim.x) {
+            TV acc = (TV)0;
+            for (int d = 0; d < jj; ++d) acc = ::fma(c[d], V[(long)d * ld + l], acc);
+            U[l] = acc;
+        }
+    }
+}
+
+template <typename TV>
+__global__ void __launch_bounds__(256) k_b_axpy(TV* __restrict__ x, const TV* __restrict__ z, BatchDev B) {
+    for (int it = blockIdx.x; it < B.nit; it += gridDim.x) {
+        if (!B.ipending[B.item_inst[it]]) continue;
+        for (int l = B.item_lo[it] + threadIdx.x; l < B.item_hi[it]; l += blockDim.x) x[l] = x[l] + z[l];
+    }
+}
+
+// V_0 = F - AX on pending instances; last item: restart decision.
+template <typename TV>
+__global__ void __launch_bounds__(256) k_b_resid(const TV* __restrict__ F, const TV* __restrict__ AX,
+                                                  TV* __restrict__ V0, BatchDev B) {
+    __shared__ double sh[32];
+    for (int it = blockIdx.x; it < B.nit; it += gridDim.x) {
+        const int inst = B.item_inst[it];
+        if (!B.ipending[inst]) continue;
+        double a = 0.0;
+        for (int l = B.item_lo[it] + threadIdx.x; l < B.item_hi[it]; l += blockDim.x) {
+            const TV rv = F[l] - AX[l];
+            V0[l] = rv;
+            a = ::fma((double)rv, (double)rv, a);
+        }
+        a = dg_block_sum(a, sh);
+        if (threadIdx.x == 0) B.partials[(long)it * (DG_MAXM + 2)] = a;
+        BState* st = B.bst + inst;
+        if (!inst_last(&st->arrive, B.inst_item_hi[inst] - B.inst_item_lo[inst])) continue;
+        const double r2 = inst_sum(B, inst, 0, sh);
+        if (threadIdx.x == 0) {
+            const double beta = sqrt(r2);
+            st->pending = 0;
+            B.ipending[inst] = 0;
+            st->cycles += 1;
+            st->relres = beta / st->bnorm;
+            st->j = 0;
+            int act = 1;
+            if (!isfinite(beta) || st->nonfinite) {
+                st->nonfinite = 1;
+                atomicAdd(B.counters + 1, 1);
+                act = 0;
+            } else if (st->relres <= st->tol) {
+                st->converged = 1;
+                act = 0;
+            } else if (st->its >= st->max_it) {
+                act = 0;
+            }
+            st->done = act ? 0 : 1;
+            B.iactive[inst] = act;
+            if (act) {
+                for (int i = 0; i <= st->m; ++i) st->g[i] = 0.0;
+                st->g[0] = beta;
+                st->scale[0] = 1.0 / beta;
+                B.iscale[inst] = st->scale[0];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// j = 0 for the next cycle; count instances still active
+__global__ void k_b_cycle_end(BatchDev B) {
+    __shared__ double sh[32];
+    double c = 0.0;
+    for (int i = threadIdx.x; i < B.nI; i += blockDim.x) c += B.iactive[i];
+    c = dg_block_sum(c, sh);
+    if (threadIdx.x == 0) {
+        *B.jglob = 0;
+        B.counters[0] = (int)c;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// f64 refinement kernels
+// ---------------------------------------------------------------------------
+// r = F - AX on instances still refining; last item: ||r||, relres, flags.
+__global__ void __launch_bounds__(256) k_bo_resid(const double* __restrict__ F, const double* __restrict__ AX,
+                                                   double* __restrict__ r, BatchDev B, double tol) {
+    __shared__ double sh[32];
+    for (int it = blockIdx.x; it < B.nit; it += gridDim.x) {
+        const int inst = B.item_inst[it];
+        if (!B.iouter[inst]) continue;
+        double a = 0.0;
+        for (int l = B.item_lo[it] + threadIdx.x; l < B.item_hi[it]; l += blockDim.x) {
+            const double v = F[l] - AX[l];
+            r[l] = v;
+            a = ::fma(v, v, a);
+        }
+        a = dg_block_sum(a, sh);
+        if (threadIdx.x == 0) B.partials[(long)it * (DG_MAXM + 2)] = a;
+        BOuter* o = B.bo + inst;
+        if (!inst_last(&o->arrive, B.inst_item_hi[inst] - B.inst_item_lo[inst])) continue;
+        const double r2 = inst_sum(B, inst, 0, sh);
+        if (threadIdx.x == 0) {
+            o->rnorm = sqrt(r2);
+            if (o->first) {
+                o->bnorm = o->rnorm;
+                o->first = 0;
+            }
+            o->relres = o->bnorm > 0.0 ? o->rnorm / o->bnorm : 0.0;
+            const bool fin = isfinite(o->relres);
+            if (!fin) atomicAdd(B.counters + 1, 1);
+            const int go = (fin && o->relres > tol) ? 1 : 0;
+            B.iouter[inst] = go;
+            B.iparticipate[inst] = go;
+            if (go) atomicAdd(B.counters + 2, 1);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) k_bo_scale(const double* __restrict__ r, float* __restrict__ r32, BatchDev B) {
+    for (int it = blockIdx.x; it < B.nit; it += gridDim.x) {
+        const int inst = B.item_inst[it];
+        if (!B.iouter[inst]) continue;
+        const double s = 1.0 / B.bo[inst].rnorm;
+        for (int l = B.item_lo[it] + threadIdx.x; l < B.item_hi[it]; l += blockDim.x) r32[l] = (float)(r[l] * s);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_bo_update(double* __restrict__ x, const float* __restrict__ d, BatchDev B) {
+    for (int it = blockIdx.x; it < B.nit; it += gridDim.x) {
+        const int inst = B.item_inst[it];
+        if (!B.iouter[inst]) continue;
+        const double s = B.bo[inst].rnorm;
+        for (int l = B.item_lo[it] + threadIdx.x; l < B.item_hi[it]; l += blockDim.x) x[l] = ::fma(s, (double)d[l], x[l]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct BatchHostLayout {
+    size_t off_bst, off_bo, off_iactive, off_ipending, off_ipart, off_iouter, off_iscale, off_item_inst, off_item_lo,
+        off_item_hi, off_iilo, off_iihi, off_partials, off_jglob, off_counters, total;
+};
+
+static BatchHostLayout batch_layout(int nI, int nit) {
+    BatchHostLayout L{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t r = o;
+        o = (o + bytes + 255) & ~(size_t)255;
+        return r;
+    };
+    L.off_bst = take(sizeof(BState) * nI);
+    L.off_bo = take(sizeof(BOuter) * nI);
+    L.off_iactive = take(sizeof(int) * nI);
+    L.off_ipending = take(sizeof(int) * nI);
+    L.off_ipart = take(sizeof(int) * nI);
+    L.off_iouter = take(sizeof(int) * nI);
+    L.off_iscale = take(sizeof(double) * nI);
+    L.off_item_inst = take(sizeof(int) * nit);
+    L.off_item_lo = take(sizeof(int) * nit);
+    L.off_item_hi = take(sizeof(int) * nit);
+    L.off_iilo = take(sizeof(int) * nI);
+    L.off_iihi = take(sizeof(int) * nI);
+    L.off_partials = take(sizeof(double) * (size_t)nit * (DG_MAXM + 2));
+    L.off_jglob = take(sizeof(int));
+    L.off_counters = take(sizeof(int) * 4);
+    L.total = o;
+    return L;
+}
+
+extern "C" dg_status dg_batch_setup(dg_handle* h, int n_inst, const int* elem_start, const double* coeffs) {
+    if (!h || n_inst < 1 || !elem_start || !coeffs) return DG_ERR_INVALID_ARG;
+    if (!h->mesh_ok) return dg_fail(h, DG_ERR_STATE, "upload the concatenated mesh first");
+    if (elem_start[0] != 0 || elem_start[n_inst] != h->ne)
+        return dg_fail(h, DG_ERR_INVALID_ARG, "elem_start must run from 0 to ne");
+    for (int i = 0; i < n_inst; ++i)
+        if (elem_start[i + 1] <= elem_start[i]) return dg_fail(h, DG_ERR_INVALID_ARG, "empty or unordered instance");
+    DG_CK(h, cudaSetDevice(h->device));
+    dg_status s;
+    if ((s = dg_realloc(h, (void**)&h->b_inst, sizeof(int) * h->ne)) != DG_OK) return s;
+    if ((s = dg_realloc(h, (void**)&h->b_icoef, sizeof(double) * DG_ICOEF * n_inst)) != DG_OK) return s;
+    std::vector<int> inst(h->ne);
+    for (int i = 0; i < n_inst; ++i)
+        for (int K = elem_start[i]; K < elem_start[i + 1]; ++K) inst[K] = i;
+    // the instances must not touch: no face may join two instances
+    std::vector<int> nbr(3 * (size_t)h->ne);
+    DG_CK(h, cudaMemcpy(nbr.data(), h->nbr, sizeof(int) * 3 * (size_t)h->ne, cudaMemcpyDeviceToHost));
+    for (int f = 0; f < 3; ++f)
+        for (int K = 0; K < h->ne; ++K) {
+            const int L = nbr[(size_t)f * h->ne + K];
+            if (L >= 0 && inst[L] != inst[K]) return dg_fail(h, DG_ERR_MESH, "two instances share an edge");
+        }
+    // per-instance coefficients: eps, alpha, b[6] from the caller; penalties from params
+    const int k = h->p.degree;
+    const double sig = h->p.sigma_int > 0.0 ? h->p.sigma_int : (h->p.method == DG_NIPG ? 1.0 : 3.0 * k * (k + 1));
+    const double fac = h->p.sigma_bdry_factor > 0.0 ? h->p.sigma_bdry_factor : 2.0;
+    std::vector<double> ic((size_t)DG_ICOEF * n_inst);
+    for (int i = 0; i < n_inst; ++i) {
+        for (int t = 0; t < 8; ++t) ic[(size_t)DG_ICOEF * i + t] = coeffs[8 * i + t];
+        if (!(ic[(size_t)DG_ICOEF * i] >= 0.0)) return dg_fail(h, DG_ERR_INVALID_ARG, "eps must be >= 0");
+        ic[(size_t)DG_ICOEF * i + 8] = sig;
+        ic[(size_t)DG_ICOEF * i + 9] = fac * sig;
+    }
+    DG_CK(h, cudaMemcpy(h->b_inst, inst.data(), sizeof(int) * h->ne, cudaMemcpyHostToDevice));
+    DG_CK(h, cudaMemcpy(h->b_icoef, ic.data(), sizeof(double) * ic.size(), cudaMemcpyHostToDevice));
+    free(h->b_elem_start);
+    h->b_elem_start = (int*)malloc(sizeof(int) * (n_inst + 1));
+    memcpy(h->b_elem_start, elem_start, sizeof(int) * (n_inst + 1));
+    h->b_n = n_inst;
+    h->b_inst_active = true;
+    h->assembled = false;
+    h->bj_ok = false;
+    if (h->b_graph) {
+        cudaGraphExecDestroy(h->b_graph);
+        h->b_graph = nullptr;
+    }
+    return DG_OK;
+}
+
+extern "C" dg_status dg_batch_clear(dg_handle* h) {
+    if (!h) return DG_ERR_INVALID_ARG;
+    h->b_inst_active = false;
+    h->b_n = 0;
+    h->assembled = false;
+    return DG_OK;
+}
+
+// Build the item list for degree nb and tile size; returns the layout.
+static dg_status batch_tables(dg_handle* h, int nb, int tile, BatchDev& B, BatchHostLayout& L) {
+    std::vector<int> iinst, ilo, ihi, iilo(h->b_n), iihi(h->b_n);
+    for (int i = 0; i < h->b_n; ++i) {
+        const long lo = (long)h->b_elem_start[i] * nb, hi = (long)h->b_elem_start[i + 1] * nb;
+        iilo[i] = (int)iinst.size();
+        for (long a = lo; a < hi; a += tile) {
+            iinst.push_back(i);
+            ilo.push_back((int)a);
+            ihi.push_back((int)std::min(hi, a + (long)tile));
+        }
+        iihi[i] = (int)iinst.size();
+    }
+    const int nit = (int)iinst.size();
+    L = batch_layout(h->b_n, nit);
+    dg_status s;
+    if ((s = dg_ensure(h, &h->b_dev, &h->cap_bdev, L.total)) != DG_OK) return s;
+    char* base = (char*)h->b_dev;
+    B.bst = (BState*)(base + L.off_bst);
+    B.bo = (BOuter*)(base + L.off_bo);
+    B.iactive = (int*)(base + L.off_iactive);
+    B.ipending = (int*)(base + L.off_ipending);
+    B.iparticipate = (int*)(base + L.off_ipart);
+    B.iouter = (int*)(base + L.off_iouter);
+    B.iscale = (double*)(base + L.off_iscale);
+    B.item_inst = (int*)(base + L.off_item_inst);
+    B.item_lo = (int*)(base + L.off_item_lo);
+    B.item_hi = (int*)(base + L.off_item_hi);
+    B.inst_item_lo = (int*)(base + L.off_iilo);
+    B.inst_item_hi = (int*)(base + L.off_iihi);
+    B.partials = (double*)(base + L.off_partials);
+    B.jglob = (int*)(base + L.off_jglob);
+    B.counters = (int*)(base + L.off_counters);
+    B.nI = h->b_n;
+    B.nit = nit;
+    DG_CK(h, cudaMemsetAsync(h->b_dev, 0, L.total, h->stream));
+    DG_CK(h, cudaMemcpyAsync(B.item_inst, iinst.data(), sizeof(int) * nit, cudaMemcpyHostToDevice, h->stream));
+    DG_CK(h, cudaMemcpyAsync(B.item_lo, ilo.data(), sizeof(int) * nit, cudaMemcpyHostToDevice, h->stream));
+    DG_CK(h, cudaMemcpyAsync(B.item_hi, ihi.data(), sizeof(int) * nit, cudaMemcpyHostToDevice, h->stream));
+    DG_CK(h, cudaMemcpyAsync(B.inst_item_lo, iilo.data(), sizeof(int) * h->b_n, cudaMemcpyHostToDevice, h->stream));
+    DG_CK(h, cudaMemcpyAsync(B.inst_item_hi, iihi.data(), sizeof(int) * h->b_n, cudaMemcpyHostToDevice, h->stream));
+    DG_CK(h, cudaStreamSynchronize(h->stream));
+    return DG_OK;
+}
+
+struct BatchRun {
+    BatchDev B;
+    void* V;
+    void* Z;
+    void* R;
+    long ld;
+    int m;
+    int gsm, gx;
+};
+
+template <int NB, typename TA, typename TB, typename TV>
+static int b_enqueue_cycle(dg_handle* h, const BatchRun& Rn, const TA* A, const TB* Binv, const TV* F, TV* x) {
+    const BatchDev& B = Rn.B;
+    TV* V = (TV*)Rn.V;
+    TV* Z = (TV*)Rn.Z;
+    TV* R = (TV*)Rn.R;
+    const unsigned ge = (unsigned)((h->ne + 255) / 256);
+    DevCtl step{nullptr, nullptr, h->b_inst, B.iactive, B.iscale};
+    DevCtl pend{nullptr, nullptr, h->b_inst, B.ipending, nullptr};
+    VecSel vj{B.jglob, 0, Rn.ld}, vj1{B.jglob, 1, Rn.ld};
+    int n = 0;
+    for (int it = 0; it < Rn.m; ++it) {
+        k_bj_apply<NB, TB, TV, TV><<<ge, 256, 0, h->stream>>>(Binv, V, Z, h->ne, step, vj, vsel_fixed());
+        k_apply<NB, TA, TV, TV><<<ge, 256, 0, h->stream>>>(A, h->nbr, Z, V, h->ne, DevCtl{nullptr, nullptr, h->b_inst,
+                                                                                        B.iactive, nullptr},
+                                                          vsel_fixed(), vj1);
+        for (int pass = 1; pass <= 2; ++pass) {
+            k_b_dots<TV><<<Rn.gsm, dim3(B_TX, B_TY), 0, h->stream>>>(V, Rn.ld, B, pass);
+            k_b_update<TV><<<Rn.gx, 256, 0, h->stream>>>(V, Rn.ld, B, pass);
+        }
+        k_b_step<<<1, 32, 0, h->stream>>>(B);
+        n += 7;
+    }
+    k_b_solve<<<B.nI, 256, 0, h->stream>>>(B);
+    k_b_combine<TV><<<Rn.gx, 256, 0, h->stream>>>(V, Rn.ld, B, R);
+    k_bj_apply<NB, TB, TV, TV><<<ge, 256, 0, h->stream>>>(Binv, R, Z, h->ne, pend, vsel_fixed(), vsel_fixed());
+    k_b_axpy<TV><<<Rn.gx, 256, 0, h->stream>>>(x, Z, B);
+    k_apply<NB, TA, TV, TV><<<ge, 256, 0, h->stream>>>(A, h->nbr, x, R, h->ne, pend, vsel_fixed(), vsel_fixed());
+    k_b_resid<TV><<<Rn.gx, 256, 0, h->stream>>>(F, R, V, B);
+    k_b_cycle_end<<<1, 1024, 0, h->stream>>>(B);
+    return n + 7;
+}
+
+template <int NB, typename TA, typename TB, typename TV>
+static dg_status b_gmres(dg_handle* h, BatchRun& Rn, const TA* A, const TB* Binv, const TV* F, TV* x, double tol,
+                         int max_it, int* counters_host) {
+    const BatchDev& B = Rn.B;
+    k_b_init<TV><<<Rn.gx, 256, 0, h->stream>>>(F, x, (TV*)Rn.V, B, Rn.m, max_it, tol);
+    DG_CK(h, cudaMemsetAsync(B.jglob, 0, sizeof(int), h->stream));
+    k_b_cycle_end<<<1, 1024, 0, h->stream>>>(B);
+    h->nlaunch += 2;
+    DG_LAUNCH_CK(h);
+    const uintptr_t key[8] = {(uintptr_t)A, (uintptr_t)Binv, (uintptr_t)F, (uintptr_t)x, (uintptr_t)Rn.V,
+                              (uintptr_t)B.bst, (uintptr_t)Rn.m | ((uintptr_t)sizeof(TV) << 16), (uintptr_t)h->stream};
+    if (h->b_graph && memcmp(key, h->b_key, sizeof(key)) != 0) {
+        cudaGraphExecDestroy(h->b_graph);
+        h->b_graph = nullptr;
+    }
+    if (!h->b_graph) {
+        cudaGraph_t g;
+        DG_CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        h->b_nodes = b_enqueue_cycle<NB, TA, TB, TV>(h, Rn, A, Binv, F, x);
+        cudaMemcpyAsync(counters_host, B.counters, sizeof(int) * 4, cudaMemcpyDeviceToHost, h->stream);
+        DG_CK(h, cudaStreamEndCapture(h->stream, &g));
+        cudaError_t e = cudaGraphInstantiate(&h->b_graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return dg_cuda_fail(h, e, "cudaGraphInstantiate (batch)");
+        memcpy(h->b_key, key, sizeof(key));
+    }
+    DG_CK(h, cudaMemcpyAsync(counters_host, B.counters, sizeof(int) * 4, cudaMemcpyDeviceToHost, h->stream));
+    DG_CK(h, cudaStreamSynchronize(h->stream));
+    const int max_cycles = max_it + 2;
+    for (int c = 0; c < max_cycles && counters_host[0] > 0; ++c) {
+        DG_CK(h, cudaGraphLaunch(h->b_graph, h->stream));
+        h->nlaunch += h->b_nodes;
+        DG_CK(h, cudaStreamSynchronize(h->stream));
+    }
+    return DG_OK;
+}
+
+template <int NB, typename TA, typename TB>
+static dg_status batch_solve_t(dg_handle* h, int inner_dtype, const TA* Alo, const TB* Binv, int inner_m,
+                               double inner_tol, int max_outer, const double* F, double* x, int* its_out,
+                               double* relres_out, int* status_out) {
+    const long n = (long)h->ne * NB;
+    const long ld = (n + 63) / 64 * 64;
+    BatchRun Rn{};
+    BatchHostLayout L;
+    const int tile = h->b_tile > 0 ? h->b_tile : 4096;
+    dg_status s = batch_tables(h, NB, tile, Rn.B, L);
+    if (s != DG_OK) return s;
+    const bool f64 = inner_dtype == DG_F64;
+    const size_t elem = f64 ? 8 : 4;
+    // vectors: V (m+2) x ld, Z, R (ld); refinement: r64, ax (n f64), rin, din (ld f32)
+    const size_t vbytes = ((size_t)(inner_m + 2) * ld + 2 * ld) * elem + (f64 ? 0 : (2 * n * 8 + 2 * ld * 4)) + 1024;
+    if ((s = dg_ensure(h, &h->mx_buf, &h->cap_mx, vbytes)) != DG_OK) return s;
+    char* vb = (char*)h->mx_buf;
+    Rn.V = vb;
+    Rn.Z = vb + (size_t)(inner_m + 2) * ld * elem;
+    Rn.R = (char*)Rn.Z + ld * elem;
+    double* r64 = (double*)((char*)Rn.R + ld * elem);
+    double* ax = r64 + n;
+    float* rin = (float*)(ax + n);
+    float* din = rin + ld;
+    DG_CK(h, cudaMemsetAsync(h->mx_buf, 0, vbytes, h->stream));
+    Rn.ld = ld;
+    Rn.m = inner_m;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    Rn.gsm = sms;
+    Rn.gx = 4 * sms;
+    dg_status result = DG_OK;
+    if (!h->b_host) {
+        DG_CK(h, cudaMallocHost(&h->b_host, 64));
+        h->cap_bhost = 64;
+    }
+    int* cnt = (int*)h->b_host;   // pinned: the captured cycle copies the counters here
+    const BatchDev& B = Rn.B;
+    std::vector<BState> hst;
+    std::vector<BOuter> hbo;
+    int outer = 0;
+    if constexpr (std::is_same<TA, double>::value) {
+        // all instances take part in one batched f64 GMRES
+        std::vector<int> one(h->b_n, 1);
+        DG_CK(h, cudaMemcpyAsync(B.iparticipate, one.data(), sizeof(int) * h->b_n, cudaMemcpyHostToDevice, h->stream));
+        s = b_gmres<NB, double, double, double>(h, Rn, Alo, Binv, F, x, h->p.tol, h->p.max_it, cnt);
+        if (s != DG_OK) result = s;
+        (void)r64; (void)ax; (void)rin; (void)din; (void)inner_tol; (void)max_outer;
+    } else {
+        // f64 refinement around the f32 inner batched GMRES
+        std::vector<BOuter> bo0(h->b_n);
+        for (auto& o : bo0) o = BOuter{0.0, 0.0, 1.0, 0u, 1};
+        std::vector<int> one(h->b_n, 1);
+        DG_CK(h, cudaMemcpyAsync(B.bo, bo0.data(), sizeof(BOuter) * h->b_n, cudaMemcpyHostToDevice, h->stream));
+        DG_CK(h, cudaMemcpyAsync(B.iouter, one.data(), sizeof(int) * h->b_n, cudaMemcpyHostToDevice, h->stream));
+        DG_CK(h, cudaMemsetAsync(x, 0, sizeof(double) * n, h->stream));
+        const unsigned ge = (unsigned)((h->ne + 255) / 256);
+        int inner_total = 0;
+        for (;;) {
+            DevCtl oc{nullptr, nullptr, h->b_inst, B.iouter, nullptr};
+            k_apply<NB, double, double, double><<<ge, 256, 0, h->stream>>>(h->A64, h->nbr, x, ax, h->ne, oc,
+                                                                           vsel_fixed(), vsel_fixed());
+            DG_CK(h, cudaMemsetAsync(B.counters + 2, 0, sizeof(int), h->stream));
+            k_bo_resid<<<Rn.gx, 256, 0, h->stream>>>(F, ax, r64, B, h->p.tol);
+            h->nlaunch += 2;
+            DG_LAUNCH_CK(h);
+            DG_CK(h, cudaMemcpyAsync(cnt, B.counters, sizeof(int) * 4, cudaMemcpyDeviceToHost, h->stream));
+            DG_CK(h, cudaStreamSynchronize(h->stream));
+            if (cnt[2] == 0 || outer >= max_outer || inner_total >= h->p.max_it) break;
+            k_bo_scale<<<Rn.gx, 256, 0, h->stream>>>(r64, rin, B);
+            h->nlaunch += 1;
+            s = b_gmres<NB, TA, TB, float>(h, Rn, Alo, Binv, rin, din, inner_tol, h->p.max_it - inner_total, cnt);
+            if (s != DG_OK) {
+                result = s;
+                break;
+            }
+            // inner iterations of this correction: max over instances
+            hst.resize(h->b_n);
+            DG_CK(h, cudaMemcpyAsync(hst.data(), B.bst, sizeof(BState) * h->b_n, cudaMemcpyDeviceToHost, h->stream));
+            k_bo_update<<<Rn.gx, 256, 0, h->stream>>>(x, din, B);
+            h->nlaunch += 1;
+            DG_LAUNCH_CK(h);
+            DG_CK(h, cudaStreamSynchronize(h->stream));
+            int mx = 0;
+            for (auto& st : hst) mx = std::max(mx, st.its);
+            inner_total += mx;
+            if (its_out)
+                for (int i = 0; i < h->b_n; ++i) its_out[i] = (outer == 0 ? 0 : its_out[i]) + hst[i].its;
+            ++outer;
+        }
+    }
+    // per-instance results
+    hst.resize(h->b_n);
+    hbo.resize(h->b_n);
+    DG_CK(h, cudaMemcpyAsync(hst.data(), B.bst, sizeof(BState) * h->b_n, cudaMemcpyDeviceToHost, h->stream));
+    DG_CK(h, cudaMemcpyAsync(hbo.data(), B.bo, sizeof(BOuter) * h->b_n, cudaMemcpyDeviceToHost, h->stream));
+    DG_CK(h, cudaStreamSynchronize(h->stream));
+    int nconv = 0;
+    for (int i = 0; i < h->b_n; ++i) {
+        const double rr = f64 ? hst[i].relres : hbo[i].relres;
+        const bool ok = rr <= h->p.tol;
+        nconv += ok;
+        if (f64 && its_out) its_out[i] = hst[i].its;
+        if (!f64 && its_out && outer == 0) its_out[i] = 0;
+        if (relres_out) relres_out[i] = rr;
+        if (status_out) status_out[i] = ok ? DG_OK : DG_NOT_CONVERGED;
+    }
+    if (result != DG_OK) return result;
+    if (nconv < h->b_n)
+        return dg_fail(h, DG_NOT_CONVERGED, std::to_string(h->b_n - nconv) + " instances did not converge");
+    return DG_OK;
+}
+
+extern "C" dg_status dg_batch_solve(dg_handle* h, int inner_dtype, int inner_m, double inner_tol, int max_outer,
+                                    const double* F, double* x, int* its, double* relres, int* status) {
+    if (!h || !x) return DG_ERR_INVALID_ARG;
+    if (!h->b_inst_active || h->b_n < 1) return dg_fail(h, DG_ERR_STATE, "no batch set up");
+    if (!h->assembled) return dg_fail(h, DG_ERR_STATE, "not assembled");
+    if (!h->A64) return dg_fail(h, DG_ERR_STATE, "the f64 blocks are required");
+    if (inner_m < 1 || inner_m > DG_MAXM || !(inner_tol > 0.0 && inner_tol < 1.0) || max_outer < 1)
+        return dg_fail(h, DG_ERR_INVALID_ARG, "inner_m / inner_tol / max_outer");
+    if (inner_dtype == DG_F32 && !h->A32) return dg_fail(h, DG_ERR_STATE, "f32 blocks not stored");
+    if (inner_dtype == DG_BF16 && !h->A16) return dg_fail(h, DG_ERR_STATE, "bf16 blocks not stored");
+    if (inner_dtype != DG_F64 && inner_dtype != DG_F32 && inner_dtype != DG_BF16)
+        return dg_fail(h, DG_ERR_INVALID_ARG, "inner_dtype");
+    if (h->p.precond == DG_PRECOND_BLOCK_JACOBI && !h->bj_ok) {
+        dg_status s = dg_precond_setup(h, DG_PRECOND_BLOCK_JACOBI);
+        if (s != DG_OK) return s;
+    }
+    DG_CK(h, cudaSetDevice(h->device));
+    if (!F) F = h->F;
+    const bool pj = h->p.precond == DG_PRECOND_BLOCK_JACOBI;
+    const int nb = dg_nb(h->asm_k);
+#define DG_BATCH(NBV)                                                                                             \
+    if (nb == NBV) {                                                                                              \
+        if (inner_dtype == DG_F64)                                                                                \
+            return batch_solve_t<NBV, double, double>(h, inner_dtype, h->A64, pj ? h->Binv64 : nullptr, h->p.gmres_m, \
+                                                      inner_tol, max_outer, F, x, its, relres, status);           \
+        if (inner_dtype == DG_F32)                                                                                \
+            return batch_solve_t<NBV, float, float>(h, inner_dtype, h->A32, pj ? h->Binv32 : nullptr, inner_m,    \
+                                                    inner_tol, max_outer, F, x, its, relres, status);             \
+        return batch_solve_t<NBV, __nv_bfloat16, float>(h, inner_dtype, h->A16, pj ? h->Binv16 : nullptr, inner_m, \
+                                                        inner_tol, max_outer, F, x, its, relres, status);         \
+    }
+    DG_BATCH(3)
+    DG_BATCH(6)
+    DG_BATCH(10)
+#undef DG_BATCH
+    return dg_fail(h, DG_ERR_INVALID_ARG, "degree");
+}
+
+extern "C" dg_status dg_batch_set_tile(dg_handle* h, int tile) {
+    if (!h || tile < 0 || (tile > 0 && (tile < 256 || tile > (1 << 20)))) return DG_ERR_INVALID_ARG;
+    h->b_tile = tile;
+    if (h->b_graph) {
+        cudaGraphExecDestroy(h->b_graph);
+        h->b_graph = nullptr;
+    }
+    return DG_OK;
+}
+
+// Synthetic state for timing: every instance active at step j.
+__global__ void k_b_prof_state(BatchDev B, int j) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B.nI; i += gridDim.x * blockDim.x) {
+        BState* st = B.bst + i;
+        for (int d = 0; d <= j + 1; ++d) {
+            st->scale[d] = 1.0;
+            st->coef[d] = 1e-3;
+            st->hcol[d] = 1e-3;
+        }
+        st->reorth = 0;
+        st->arrive = 0;
+        B.iactive[i] = 1;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *B.jglob = j;
+}
+
+// Choose the work-item size (unknowns per item) of the segmented reductions by
+// timing the batched multi-dot on this batch for each candidate; the result is
+// kept in the handle and returned through *tile.
+extern "C" dg_status dg_batch_autotune(dg_handle* h, int* tile) {
+    if (!h || !tile) return DG_ERR_INVALID_ARG;
+    if (!h->b_inst_active || !h->assembled) return dg_fail(h, DG_ERR_STATE, "set up and assemble a batch first");
+    DG_CK(h, cudaSetDevice(h->device));
+    const int nb = dg_nb(h->asm_k);
+    const long n = (long)h->ne * nb;
+    const long ld = (n + 63) / 64 * 64;
+    const int m = 50, j = 25;
+    const size_t vbytes = (size_t)(m + 2) * ld * 4 + 1024;
+    dg_status s;
+    if ((s = dg_ensure(h, &h->mx_buf, &h->cap_mx, vbytes)) != DG_OK) return s;
+    DG_CK(h, cudaMemsetAsync(h->mx_buf, 0, vbytes, h->stream));
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    const int cands[] = {2048, 4096, 8192, 16384, 32768};
+    double best = 1e30;
+    int best_tile = 4096;
+    cudaEvent_t e0, e1;
+    DG_CK(h, cudaEventCreate(&e0));
+    DG_CK(h, cudaEventCreate(&e1));
+    for (int tcand : cands) {
+        BatchDev B{};
+        BatchHostLayout L;
+        if ((s = batch_tables(h, nb, tcand, B, L)) != DG_OK) return s;
+        double tot = 0.0;
+        for (int r = 0; r < 4; ++r) {
+            k_b_prof_state<<<(h->b_n + 255) / 256, 256, 0, h->stream>>>(B, j);
+            DG_CK(h, cudaEventRecord(e0, h->stream));
+            k_b_dots<float><<<sms, dim3(B_TX, B_TY), 0, h->stream>>>((const float*)h->mx_buf, ld, B, 1);
+            DG_CK(h, cudaEventRecord(e1, h->stream));
+            DG_CK(h, cudaEventSynchronize(e1));
+            float ms = 0.f;
+            DG_CK(h, cudaEventElapsedTime(&ms, e0, e1));
+            if (r > 0) tot += ms;
+        }
+        h->nlaunch += 8;
+        if (tot < best) {
+            best = tot;
+            best_tile = tcand;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->b_tile = best_tile;
+    if (h->b_graph) {
+        cudaGraphExecDestroy(h->b_graph);
+        h->b_graph = nullptr;
+    }
+    *tile = best_tile;
+    return DG_OK;
+}

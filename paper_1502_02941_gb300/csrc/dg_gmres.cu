@@ -72,6 +72,30 @@ struct Acc<float> {
     __device__ __forceinline__ double get() const { return (double)s - (double)c; }
 };
 
+// 16-byte vector of basis entries.  Basis vectors have a padded leading
+// dimension (a multiple of 64 entries) and zero padding, so every vector is
+// 16-byte aligned and the kernels below may run over whole 16-byte vectors.
+template <typename TV>
+struct Vec;
+template <>
+struct Vec<double> {
+    using T = double2;
+    static constexpr int W = 2;
+    __device__ __forceinline__ static double get(const T& v, int i) { return i == 0 ? v.x : v.y; }
+    __device__ __forceinline__ static void set(T& v, int i, double a) { if (i == 0) v.x = a; else v.y = a; }
+};
+template <>
+struct Vec<float> {
+    using T = float4;
+    static constexpr int W = 4;
+    __device__ __forceinline__ static float get(const T& v, int i) {
+        return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+    }
+    __device__ __forceinline__ static void set(T& v, int i, float a) {
+        if (i == 0) v.x = a; else if (i == 1) v.y = a; else if (i == 2) v.z = a; else v.w = a;
+    }
+};
+
 // Returns true in exactly one block: the last to arrive.  All partial results
 // written before the call by any block are visible to that block (read them
 // with __ldcg).  The counter is reset for the next kernel.
@@ -160,35 +184,46 @@ __global__ void __launch_bounds__(256) k_gm_init(const TV* __restrict__ F, TV* _
 // (16 threads per dot, independent loads), then h_d = s_d r_d into hcol and the
 // update coefficients s_d h_d.
 template <typename TV>
-__global__ void __launch_bounds__(GM_TX* GM_TY) k_gm_dots(const TV* __restrict__ V, long n, GmresState* st,
-                                                         double* partials, int pass) {
+__global__ void __launch_bounds__(GM_TX* GM_TY) k_gm_dots(const TV* __restrict__ V, long ld, long nvec,
+                                                         GmresState* st, double* partials, int pass) {
     if (!st->active || (pass == 2 && !st->reorth)) return;
+    using VT = typename Vec<TV>::T;
+    constexpr int W = Vec<TV>::W;
     const int j = st->j;
     const int dlast = pass == 1 ? j + 1 : j;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const TV* __restrict__ w = V + (long)(j + 1) * n;
+    const VT* __restrict__ w = reinterpret_cast<const VT*>(V + (long)(j + 1) * ld);
     Acc<TV> acc[GM_DPT];
-    const long nchunk = (n + GM_TX - 1) / GM_TX;
+    const long nchunk = (nvec + GM_TX - 1) / GM_TX;
     const long step = gridDim.x;
     for (long c = blockIdx.x; c < nchunk; c += 4 * step) {
-        TV wl[4];
+        VT wv[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const long l = (c + u * step) * GM_TX + tx;
-            wl[u] = l < n ? w[l] : (TV)0;
+            const long q = (c + u * step) * GM_TX + tx;
+            if (q < nvec) wv[u] = w[q];
+            else
+#pragma unroll
+                for (int i = 0; i < W; ++i) Vec<TV>::set(wv[u], i, (TV)0);
         }
 #pragma unroll
         for (int k = 0; k < GM_DPT; ++k) {
             const int d = ty + GM_TY * k;
             if (d <= dlast) {
-                TV v[4];
+                const VT* __restrict__ vd = reinterpret_cast<const VT*>(V + (long)d * ld);
+                VT v[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const long l = (c + u * step) * GM_TX + tx;
-                    v[u] = l < n ? V[(long)d * n + l] : (TV)0;
+                    const long q = (c + u * step) * GM_TX + tx;
+                    if (q < nvec) v[u] = vd[q];
+                    else
+#pragma unroll
+                        for (int i = 0; i < W; ++i) Vec<TV>::set(v[u], i, (TV)0);
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) acc[k].fma(v[u], wl[u]);
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int i = 0; i < W; ++i) acc[k].fma(Vec<TV>::get(v[u], i), Vec<TV>::get(wv[u], i));
             }
         }
     }
@@ -259,29 +294,40 @@ __device__ void gm_finish_column(GmresState* st, double wn, const double* hc, co
 // V_{j+1} -= sum_{d<=j} coef_d V_d ; ||V_{j+1}||^2.  Last block: norm,
 // re-orthogonalisation decision, Hessenberg/Givens step.
 template <typename TV>
-__global__ void __launch_bounds__(256) k_gm_update(TV* V, long n, GmresState* st, double* partials, int pass) {
+__global__ void __launch_bounds__(256) k_gm_update(TV* V, long ld, long nvec, GmresState* st, double* partials,
+                                                    int pass) {
     if (!st->active || (pass == 2 && !st->reorth)) return;
+    using VT = typename Vec<TV>::T;
+    constexpr int W = Vec<TV>::W;
     __shared__ TV c[DG_MAXM + 2];
     __shared__ double sh[32];
     __shared__ double hc[DG_MAXM + 2], css[DG_MAXM], sns[DG_MAXM];
     const int j = st->j;
     for (int d = threadIdx.x; d <= j; d += blockDim.x) c[d] = (TV)st->coef[d];
     __syncthreads();
-    TV* w = V + (long)(j + 1) * n;   // aliases V: no __restrict__
+    VT* w = reinterpret_cast<VT*>(V + (long)(j + 1) * ld);   // aliases V: no __restrict__
     Acc<TV> nrm;
-    for (long l = (long)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (long)gridDim.x * blockDim.x) {
-        TV acc = w[l];
+    for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < nvec; q += (long)gridDim.x * blockDim.x) {
+        VT acc = w[q];
         int d = 0;
-        for (; d + 8 <= j + 1; d += 8) {
-            TV v[8];
+        for (; d + 4 <= j + 1; d += 4) {
+            VT v[4];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = V[(long)(d + u) * n + l];
+            for (int u = 0; u < 4; ++u) v[u] = reinterpret_cast<const VT*>(V + (long)(d + u) * ld)[q];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) acc = ::fma(-c[d + u], v[u], acc);
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int i = 0; i < W; ++i)
+                    Vec<TV>::set(acc, i, ::fma(-c[d + u], Vec<TV>::get(v[u], i), Vec<TV>::get(acc, i)));
         }
-        for (; d <= j; ++d) acc = ::fma(-c[d], V[(long)d * n + l], acc);
-        w[l] = acc;
-        nrm.fma(acc, acc);
+        for (; d <= j; ++d) {
+            const VT v = reinterpret_cast<const VT*>(V + (long)d * ld)[q];
+#pragma unroll
+            for (int i = 0; i < W; ++i) Vec<TV>::set(acc, i, ::fma(-c[d], Vec<TV>::get(v, i), Vec<TV>::get(acc, i)));
+        }
+        w[q] = acc;
+#pragma unroll
+        for (int i = 0; i < W; ++i) nrm.fma(Vec<TV>::get(acc, i), Vec<TV>::get(acc, i));
     }
     const double v = dg_block_sum(nrm.get(), sh);
     if (threadIdx.x == 0) partials[blockIdx.x] = v;
@@ -329,25 +375,27 @@ __global__ void __launch_bounds__(256) k_gm_solve(GmresState* st) {
     }
 }
 
-// U = sum_{i<jj} coef_i V_i
+// U = sum_{i<jj} coef_i V_i  (U has the basis' zero padding too)
 template <typename TV>
-__global__ void __launch_bounds__(256) k_gm_combine(const TV* __restrict__ V, long n, const GmresState* st,
-                                                     TV* __restrict__ U) {
+__global__ void __launch_bounds__(256) k_gm_combine(const TV* __restrict__ V, long ld, long nvec,
+                                                     const GmresState* st, TV* __restrict__ U) {
     if (!st->pending) return;
-    __shared__ double c[DG_MAXM + 2];
+    using VT = typename Vec<TV>::T;
+    constexpr int W = Vec<TV>::W;
+    __shared__ TV c[DG_MAXM + 2];
     const int jj = st->j;
-    for (int d = threadIdx.x; d < jj; d += blockDim.x) c[d] = st->coef[d];
+    for (int d = threadIdx.x; d < jj; d += blockDim.x) c[d] = (TV)st->coef[d];
     __syncthreads();
-    for (long l = (long)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (long)gridDim.x * blockDim.x) {
-        double acc = 0.0;
-        int d = 0;
-        for (; d + 4 <= jj; d += 4) {
-            const double a0 = (double)V[(long)d * n + l], a1 = (double)V[(long)(d + 1) * n + l];
-            const double a2 = (double)V[(long)(d + 2) * n + l], a3 = (double)V[(long)(d + 3) * n + l];
-            acc += c[d] * a0 + c[d + 1] * a1 + c[d + 2] * a2 + c[d + 3] * a3;
+    for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < nvec; q += (long)gridDim.x * blockDim.x) {
+        VT acc;
+#pragma unroll
+        for (int i = 0; i < W; ++i) Vec<TV>::set(acc, i, (TV)0);
+        for (int d = 0; d < jj; ++d) {
+            const VT v = reinterpret_cast<const VT*>(V + (long)d * ld)[q];
+#pragma unroll
+            for (int i = 0; i < W; ++i) Vec<TV>::set(acc, i, ::fma(c[d], Vec<TV>::get(v, i), Vec<TV>::get(acc, i)));
         }
-        for (; d < jj; ++d) acc += c[d] * (double)V[(long)d * n + l];
-        U[l] = (TV)acc;
+        reinterpret_cast<VT*>(U)[q] = acc;
     }
 }
 
@@ -427,23 +475,25 @@ static int enqueue_cycle(dg_handle* h, GmresWork& W, const TA* A, const TB* B, c
     TV* R = (TV*)W.R;
     GmresState* st = W.st;
     const long n = (long)W.n;
+    const long ld = (long)W.ld;
+    const long nvec = ld / Vec<TV>::W;
     const int gx = W.gx;
     const dim3 bdots(GM_TX, GM_TY);
     const int gdots = W.gsm;
     DevCtl step{&st->active, st->scale};
     DevCtl step_noscale{&st->active, nullptr};
-    VecSel vj{&st->j, 0, n}, vj1{&st->j, 1, n};
+    VecSel vj{&st->j, 0, ld}, vj1{&st->j, 1, ld};
     for (int it = 0; it < W.m; ++it) {
         launch_bj<NB, TB, TV>(h, B, V, Z, step, vj, vsel_fixed());
         launch_apply<NB, TA, TV>(h, A, Z, V, step_noscale, vsel_fixed(), vj1);
         for (int pass = 1; pass <= 2; ++pass) {
-            k_gm_dots<TV><<<gdots, bdots, 0, h->stream>>>(V, n, st, W.partials, pass);
-            k_gm_update<TV><<<gx, 256, 0, h->stream>>>(V, n, st, W.partials, pass);
+            k_gm_dots<TV><<<gdots, bdots, 0, h->stream>>>(V, ld, nvec, st, W.partials, pass);
+            k_gm_update<TV><<<gx, 256, 0, h->stream>>>(V, ld, nvec, st, W.partials, pass);
         }
     }
     DevCtl pend{&st->pending, nullptr};
     k_gm_solve<<<1, 256, 0, h->stream>>>(st);
-    k_gm_combine<TV><<<gx, 256, 0, h->stream>>>(V, n, st, R);
+    k_gm_combine<TV><<<gx, 256, 0, h->stream>>>(V, ld, nvec, st, R);
     launch_bj<NB, TB, TV>(h, B, R, Z, pend, vsel_fixed(), vsel_fixed());
     k_gm_axpy<TV><<<gx, 256, 0, h->stream>>>(x, Z, n, st);
     launch_apply<NB, TA, TV>(h, A, x, R, pend, vsel_fixed(), vsel_fixed());
@@ -464,9 +514,15 @@ void dg_gmres_free(GmresWork* w) {
 static dg_status ensure_workspace(dg_handle* h, GmresWork& W, long n, int m, size_t elem) {
     dg_status s;
     if (W.n != (size_t)n || W.m != m || W.elem != elem || !W.V) {
-        if ((s = dg_realloc(h, &W.V, (size_t)(m + 2) * n * elem)) != DG_OK) return s;
-        if ((s = dg_realloc(h, &W.Z, (size_t)n * elem)) != DG_OK) return s;
-        if ((s = dg_realloc(h, &W.R, (size_t)n * elem)) != DG_OK) return s;
+        const size_t ld = ((size_t)n + 63) / 64 * 64;
+        if ((s = dg_realloc(h, &W.V, (size_t)(m + 2) * ld * elem)) != DG_OK) return s;
+        if ((s = dg_realloc(h, &W.Z, ld * elem)) != DG_OK) return s;
+        if ((s = dg_realloc(h, &W.R, ld * elem)) != DG_OK) return s;
+        // zero padding: no kernel writes a nonzero beyond entry n of a vector
+        DG_CK(h, cudaMemsetAsync(W.V, 0, (size_t)(m + 2) * ld * elem, h->stream));
+        DG_CK(h, cudaMemsetAsync(W.Z, 0, ld * elem, h->stream));
+        DG_CK(h, cudaMemsetAsync(W.R, 0, ld * elem, h->stream));
+        W.ld = ld;
         W.n = n;
         W.m = m;
         W.elem = elem;
@@ -636,7 +692,8 @@ static dg_status mixed_run(dg_handle* h, const TA* Alo, const double* F, double*
     MixState hm{};
     DG_CK(h, cudaMemcpyAsync(ms, &init, sizeof(MixState), cudaMemcpyHostToDevice, h->stream));
     DG_CK(h, cudaMemsetAsync(x, 0, sizeof(double) * n, h->stream));
-    const float* B32 = h->p.precond == DG_PRECOND_BLOCK_JACOBI ? h->Binv32 : nullptr;
+    const bool lo16 = sizeof(TA) == 2;
+    const float* B32 = h->p.precond == DG_PRECOND_BLOCK_JACOBI ? (lo16 ? h->Binv16 : h->Binv32) : nullptr;
     int inner_total = 0, outer = 0;
     const int gx = W.gx;
     bool converged = false;
@@ -702,5 +759,92 @@ extern "C" dg_status dg_mixed_solve(dg_handle* h, int inner_dtype, int inner_m, 
     DG_MIX(6)
     DG_MIX(10)
 #undef DG_MIX
+    return dg_fail(h, DG_ERR_INVALID_ARG, "degree");
+}
+
+// ---------------------------------------------------------------------------
+// kernel timing (instrumentation)
+// ---------------------------------------------------------------------------
+// A synthetic Arnoldi state: step j active, unit scales, coefficients 1e-3.
+__global__ void k_prof_state(GmresState* st, int j, int m) {
+    if (threadIdx.x != 0) return;
+    st->active = 1;
+    st->j = j;
+    st->reorth = 0;
+    st->m = m;
+    st->its = 0;
+    st->max_it = 1 << 30;
+    st->tol = 0.0;
+    st->bnorm = 1.0;
+    st->wn2_before = 0.0;
+    st->arrive = 0;
+    for (int i = 0; i <= m + 1; ++i) {
+        st->scale[i] = 1.0;
+        st->hcol[i] = 1e-3;
+        st->coef[i] = 1e-3;
+    }
+    for (int i = 0; i <= m; ++i) st->g[i] = i == 0 ? 1.0 : 0.0;
+    for (int i = 0; i < m; ++i) {
+        st->cs[i] = 1.0;
+        st->sn[i] = 0.0;
+    }
+}
+
+template <typename TV>
+__global__ void k_prof_fill(TV* V, size_t nv, size_t n, size_t ld) {
+    for (size_t l = (size_t)blockIdx.x * blockDim.x + threadIdx.x; l < nv * ld; l += (size_t)gridDim.x * blockDim.x)
+        V[l] = (l % ld) < n ? (TV)(1.0 + 1e-3 * (double)(l % 977)) : (TV)0;
+}
+
+template <int NB, typename TV>
+static dg_status profile_arnoldi(dg_handle* h, int which, int j, int reps, double* avg_ms) {
+    GmresWork& W = h->gw[sizeof(TV) == 8 ? 0 : 1];
+    const long n = (long)h->ne * NB;
+    const int m = h->p.gmres_m;
+    if (j < 0 || j >= m) return dg_fail(h, DG_ERR_INVALID_ARG, "j must be in [0, gmres_m)");
+    dg_status s = ensure_workspace(h, W, n, m, sizeof(TV));
+    if (s != DG_OK) return s;
+    k_prof_fill<TV><<<1024, 256, 0, h->stream>>>((TV*)W.V, (size_t)(m + 2), (size_t)n, W.ld);
+    cudaEvent_t e0, e1;
+    DG_CK(h, cudaEventCreate(&e0));
+    DG_CK(h, cudaEventCreate(&e1));
+    double tot = 0.0;
+    for (int r = 0; r < reps; ++r) {
+        k_prof_state<<<1, 32, 0, h->stream>>>(W.st, j, m);
+        DG_CK(h, cudaEventRecord(e0, h->stream));
+        const long nvec = (long)W.ld / Vec<TV>::W;
+        if (which == DG_PROF_DOTS)
+            k_gm_dots<TV><<<W.gsm, dim3(GM_TX, GM_TY), 0, h->stream>>>((const TV*)W.V, (long)W.ld, nvec, W.st,
+                                                                         W.partials, 1);
+        else
+            k_gm_update<TV><<<W.gx, 256, 0, h->stream>>>((TV*)W.V, (long)W.ld, nvec, W.st, W.partials, 1);
+        DG_CK(h, cudaEventRecord(e1, h->stream));
+        DG_CK(h, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        DG_CK(h, cudaEventElapsedTime(&ms, e0, e1));
+        tot += ms;
+    }
+    h->nlaunch += 3 * reps + 1;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *avg_ms = tot / reps;
+    return DG_OK;
+}
+
+extern "C" dg_status dg_profile_kernel(dg_handle* h, int which, int dtype, int param, int reps, double* avg_ms) {
+    if (!h || !avg_ms || reps < 1) return DG_ERR_INVALID_ARG;
+    if (!h->assembled) return dg_fail(h, DG_ERR_STATE, "not assembled");
+    if (which != DG_PROF_DOTS && which != DG_PROF_UPDATE) return dg_fail(h, DG_ERR_INVALID_ARG, "which");
+    if (dtype != DG_F64 && dtype != DG_F32) return dg_fail(h, DG_ERR_INVALID_ARG, "dtype");
+    DG_CK(h, cudaSetDevice(h->device));
+    const int nb = dg_nb(h->asm_k);
+#define DG_PROF(NBV)                                                                           \
+    if (nb == NBV)                                                                             \
+        return dtype == DG_F64 ? profile_arnoldi<NBV, double>(h, which, param, reps, avg_ms)   \
+                               : profile_arnoldi<NBV, float>(h, which, param, reps, avg_ms);
+    DG_PROF(3)
+    DG_PROF(6)
+    DG_PROF(10)
+#undef DG_PROF
     return dg_fail(h, DG_ERR_INVALID_ARG, "degree");
 }

@@ -54,10 +54,15 @@ dg_status dg_scratch(dg_handle* h, size_t bytes) {
 
 static void free_all(dg_handle* h) {
     void* ptrs[] = {h->nodes, h->elems, h->geo, h->nbr, h->nface, h->ftype, h->bidx, h->bedge, h->tab,
-                    h->A64, h->A32, h->A16, h->F, h->Binv64, h->Binv32, h->scratch, h->dflag, h->mx_buf};
+                    h->A64, h->A32, h->A16, h->F, h->Binv64, h->Binv32, h->Binv16, h->scratch, h->dflag, h->mx_buf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (GmresWork& w : h->gw) dg_gmres_free(&w);
+    for (void* p : {(void*)h->b_inst, (void*)h->b_icoef, h->b_dev})
+        if (p) cudaFree(p);
+    if (h->b_host) cudaFreeHost(h->b_host);
+    if (h->b_graph) cudaGraphExecDestroy(h->b_graph);
+    free(h->b_elem_start);
 }
 
 extern "C" const char* dg_status_string(dg_status s) {

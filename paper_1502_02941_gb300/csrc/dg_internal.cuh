@@ -30,6 +30,7 @@
 #define DG_MAXNB 10
 #define DG_TILE 32
 #define DG_MAXM 64
+#define DG_ICOEF 10   // per-instance coefficients: eps, alpha, b[6], sigma_int, sigma_bdry
 
 enum GeoField { G_X0 = 0, G_Y0, G_J00, G_J01, G_J10, G_J11, G_I00, G_I01, G_I10, G_I11, G_DET, G_NFIELDS };
 
@@ -53,6 +54,7 @@ struct GmresState;   // device-side solver state (dg_gmres.cu)
 // Workspace of one restarted-GMRES solver instance (vectors of `elem` bytes).
 struct GmresWork {
     size_t n = 0;
+    size_t ld = 0;                 // leading dimension of the basis (n rounded up to 64)
     int m = 0;
     size_t elem = 0;
     void* V = nullptr;             // [(m+2)][n] Krylov basis, unnormalised
@@ -107,6 +109,7 @@ struct dg_handle {
     bool bj_ok = false;
     double* Binv64 = nullptr;
     float* Binv32 = nullptr;
+    float* Binv16 = nullptr;       // inverses of the bf16 diagonal blocks (f32)
 
     // GMRES workspaces: [0] the f64 solver, [1] the f32 inner solver of the
     // mixed-precision refinement
@@ -123,7 +126,22 @@ struct dg_handle {
 
     // capacities (bytes) of arrays that are re-sized only when they must grow
     size_t cap_nodes = 0, cap_elems = 0, cap_geo = 0, cap_face = 0, cap_bedge = 0;
-    size_t cap_binv64 = 0, cap_binv32 = 0, cap_F = 0;
+    size_t cap_binv64 = 0, cap_binv32 = 0, cap_binv16 = 0, cap_F = 0;
+
+    // batch of independent instances (dg_batch.cu)
+    bool b_inst_active = false;    // assembly reads per-instance coefficients
+    int b_n = 0;                   // instances
+    int* b_inst = nullptr;         // [ne] instance of each element
+    double* b_icoef = nullptr;     // [b_n][DG_ICOEF]
+    int* b_elem_start = nullptr;   // host copy [b_n+1]
+    void* b_dev = nullptr;         // device solver state and tables
+    size_t cap_bdev = 0;
+    void* b_host = nullptr;        // pinned host mirror of per-instance results
+    size_t cap_bhost = 0;
+    int b_tile = 0;                // dofs per work item (autotuned)
+    cudaGraphExec_t b_graph = nullptr;
+    uintptr_t b_key[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int b_nodes = 0;
 
     // mixed-precision refinement buffers (r64, A x, r32, d32, state)
     void* mx_buf = nullptr;

@@ -17,10 +17,16 @@ __device__ __forceinline__ T* sel(T* base, const VecSel& s) {
     return s.j ? base + (long)(*s.j + s.add) * s.stride : base;
 }
 // Solver control seen by the kernels: `active` (exit at once when 0) and the
-// basis scale factors (1/||v_i||) of lazily normalised Krylov vectors.
+// basis scale factors (1/||v_i||) of lazily normalised Krylov vectors.  For a
+// batch of independent instances, `inst` maps an element to its instance and
+// `iactive` / `iscale` hold per-instance flags and current scale factors: an
+// element of an inactive instance is skipped.
 struct DevCtl {
     const int* active;
     const double* scale;
+    const int* inst = nullptr;
+    const int* iactive = nullptr;
+    const double* iscale = nullptr;
 };
 static inline DevCtl dctl_none() { return DevCtl{nullptr, nullptr}; }
 
@@ -129,6 +135,7 @@ __global__ void __launch_bounds__(256) k_apply(const TA* __restrict__ A, const i
     if (ctl.active && !*ctl.active) return;
     const int K = blockIdx.x * blockDim.x + threadIdx.x;
     if (K >= ne) return;
+    if (ctl.inst && !ctl.iactive[ctl.inst[K]]) return;
     const TX* __restrict__ x = sel(x0, sx);
     TX* __restrict__ y = sel(y0, sy);
     const int tile = K >> 5, lane = K & 31;
@@ -171,9 +178,11 @@ __global__ void __launch_bounds__(256) k_bj_apply(const TA* __restrict__ B, cons
     if (ctl.active && !*ctl.active) return;
     const int K = blockIdx.x * blockDim.x + threadIdx.x;
     if (K >= ne) return;
+    if (ctl.inst && !ctl.iactive[ctl.inst[K]]) return;
     const TX* __restrict__ r = sel(r0, sr);
     TX* __restrict__ z = sel(z0, sz);
-    const double scale = ctl.scale ? ctl.scale[sr.j ? *sr.j + sr.add : 0] : 1.0;
+    const double scale = ctl.inst ? (ctl.iscale ? ctl.iscale[ctl.inst[K]] : 1.0)
+                                  : (ctl.scale ? ctl.scale[sr.j ? *sr.j + sr.add : 0] : 1.0);
     if (B == nullptr) {
         TACC v[NB];
         load_x<NB, TX, TACC>(r, K, v);
@@ -198,7 +207,7 @@ __global__ void __launch_bounds__(256) k_bj_apply(const TA* __restrict__ B, cons
             if (m < NB * NB) acc[m / NB] = fma(v[w], xv[m % NB], acc[m / NB]);
         }
     }
-    if (ctl.scale) {
+    if (ctl.scale || ctl.iscale) {
         const TACC sc = (TACC)scale;
 #pragma unroll
         for (int i = 0; i < NB; ++i) acc[i] *= sc;

@@ -28,6 +28,7 @@ DG_F64, DG_F32, DG_BF16 = 0, 1, 2
 DG_STORE_F64, DG_STORE_F32, DG_STORE_BF16 = 1, 2, 4
 DG_PRECOND_NONE, DG_PRECOND_BLOCK_JACOBI = 0, 1
 DG_POINTS_VOLUME, DG_POINTS_BOUNDARY, DG_POINTS_ERROR = 0, 1, 2
+DG_PROF_DOTS, DG_PROF_UPDATE = 1, 2
 
 c_int32, c_int64, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
 
@@ -86,6 +87,14 @@ _SIGS = {
     "dg_eval": (ctypes.c_int, [c_void_p, c_void_p, ctypes.c_int, c_void_p, c_void_p]),
     "dg_l2_error_noalloc": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_double),
                                            ctypes.POINTER(c_double)]),
+    "dg_profile_kernel": (ctypes.c_int, [c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.POINTER(c_double)]),
+    "dg_batch_setup": (ctypes.c_int, [c_void_p, ctypes.c_int, c_void_p, c_void_p]),
+    "dg_batch_clear": (ctypes.c_int, [c_void_p]),
+    "dg_batch_autotune": (ctypes.c_int, [c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    "dg_batch_set_tile": (ctypes.c_int, [c_void_p, ctypes.c_int]),
+    "dg_batch_solve": (ctypes.c_int, [c_void_p, ctypes.c_int, ctypes.c_int, c_double, ctypes.c_int, c_void_p,
+                                      c_void_p, c_void_p, c_void_p, c_void_p]),
     "dg_get_launch_count": (ctypes.c_int, [c_void_p, ctypes.POINTER(c_int64)]),
     "dg_reference_basis": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
     "dg_reference_rule": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, c_void_p, c_void_p,
@@ -258,6 +267,37 @@ def dg_eval(h, x, rs, out):
     return load().dg_eval(h, _ptr(x), rs.shape[0], _ptr(rs), _ptr(out))
 
 
+def dg_profile_kernel(h, which, dtype, param, reps):
+    ms = c_double()
+    s = load().dg_profile_kernel(h, int(which), int(dtype), int(param), int(reps), ctypes.byref(ms))
+    return s, ms.value
+
+
+def dg_batch_setup(h, elem_start, coeffs):
+    elem_start = np.ascontiguousarray(elem_start, dtype=np.int32).reshape(-1)
+    coeffs = np.ascontiguousarray(coeffs, dtype=np.float64).reshape(-1, 8)
+    return load().dg_batch_setup(h, elem_start.shape[0] - 1, _ptr(elem_start), _ptr(coeffs))
+
+
+def dg_batch_clear(h):
+    return load().dg_batch_clear(h)
+
+
+def dg_batch_autotune(h):
+    t = ctypes.c_int()
+    s = load().dg_batch_autotune(h, ctypes.byref(t))
+    return s, t.value
+
+
+def dg_batch_set_tile(h, tile):
+    return load().dg_batch_set_tile(h, int(tile))
+
+
+def dg_batch_solve(h, inner_dtype, inner_m, inner_tol, max_outer, F, x, its=None, relres=None, status=None):
+    return load().dg_batch_solve(h, int(inner_dtype), int(inner_m), float(inner_tol), int(max_outer), _ptr(F),
+                                 _ptr(x), _ptr(its), _ptr(relres), _ptr(status))
+
+
 def dg_get_launch_count(h):
     c = c_int64()
     s = load().dg_get_launch_count(h, ctypes.byref(c))
@@ -415,6 +455,34 @@ class DG:
         s, l2, hmax = dg_l2_error(self.h, x, uex_q)
         self.check(s)
         return l2, hmax
+
+    def profile_kernel(self, which, dtype, j, reps=20):
+        s, ms = dg_profile_kernel(self.h, which, dtype, j, reps)
+        self.check(s)
+        return ms
+
+    def batch_setup(self, elem_start, coeffs):
+        self.check(dg_batch_setup(self.h, elem_start, coeffs))
+        self.batch_n = len(elem_start) - 1
+
+    def batch_clear(self):
+        self.check(dg_batch_clear(self.h))
+
+    def batch_autotune(self):
+        s, t = dg_batch_autotune(self.h)
+        self.check(s)
+        return t
+
+    def batch_solve(self, inner_dtype=DG_F32, inner_m=30, inner_tol=1e-4, max_outer=30, F=None, x=None,
+                    raise_on_nonconv=True):
+        i = self.info()
+        x = self._empty((i.dofs,)) if x is None else x
+        n = self.batch_n
+        its = np.zeros(n, np.int32); rr = np.zeros(n); st = np.zeros(n, np.int32)
+        s = dg_batch_solve(self.h, inner_dtype, inner_m, inner_tol, max_outer, F, x, its, rr, st)
+        if s != DG_OK and not (s == DG_NOT_CONVERGED and not raise_on_nonconv):
+            self.check(s)
+        return x, its, rr, st
 
     def launch_count(self):
         s, c = dg_get_launch_count(self.h)

@@ -40,6 +40,24 @@ def setup(h: D.DG, cfg: W.Config, store=D.DG_STORE_F64, mesh: W.MeshArrays | Non
     return ma, data
 
 
+def setup_batch(h: D.DG, cfgs, ma: W.MeshArrays, elem_start, coeffs, store=D.DG_STORE_F64, **params):
+    """Upload a concatenated batch mesh, declare the instances, evaluate each
+    instance's f at its own volume points (gD = gN = 0: homogeneous Dirichlet
+    data on every instance) and assemble all instances in one pass."""
+    torch = h.torch
+    h.mesh_upload(ma.nodes, ma.elems, ma.dirichlet, ma.neumann)
+    k = cfgs[0].k
+    h.set_params(method=cfgs[0].method, degree=k, sigma_int=0.0, store=store, **params)
+    h.batch_setup(elem_start, coeffs)
+    xq = h.quad_points(D.DG_POINTS_VOLUME)
+    f = torch.empty(xq.shape[:2], dtype=torch.float64, device=xq.device)
+    for i, c in enumerate(cfgs):
+        a, b = int(elem_start[i]), int(elem_start[i + 1])
+        f[a:b] = c.problem.f(torch, xq[a:b, :, 0], xq[a:b, :, 1])
+    h.assemble(0.0, 0.0, (0,) * 6, f.contiguous(), None, None)
+    return f
+
+
 def exact_at_error_points(h: D.DG, prob: W.Problem):
     xe = h.quad_points(D.DG_POINTS_ERROR)
     return prob.u(h.torch, xe[..., 0], xe[..., 1]).contiguous()

@@ -267,3 +267,39 @@ def random_instance(config_id: int, instance: int, N_range=(16, 128), k_choices=
     prob = Problem("gaussians", eps, alpha, (s * np.cos(theta), 0, 0, s * np.sin(theta), 0, 0),
                    None, gaussians_source([tuple(c) for c in centres], list(widths)))
     return Config(f"cfg{config_id}_inst{instance}", N, k, 2, prob)
+
+
+def concat_meshes(meshes):
+    """Concatenate independent meshes into one (node and element ids offset);
+    returns the MeshArrays and elem_start [len+1] (instance i owns elements
+    elem_start[i]..elem_start[i+1]-1)."""
+    nodes, elems, dirs, neus, starts = [], [], [], [], [0]
+    off = 0
+    for m in meshes:
+        nodes.append(m.nodes)
+        elems.append(m.elems + off)
+        dirs.append(m.dirichlet + off)
+        neus.append(m.neumann + off)
+        off += m.nodes.shape[0]
+        starts.append(starts[-1] + m.elems.shape[0])
+    return (MeshArrays(np.concatenate(nodes), np.concatenate(elems).astype(np.int32),
+                       np.concatenate(dirs).astype(np.int32),
+                       np.concatenate(neus).astype(np.int32) if neus else np.zeros((0, 2), np.int32)),
+            np.array(starts, np.int32))
+
+
+def batch(config_id: int, n_inst: int, k: int | None = None, N_fixed: int | None = None, N_range=(16, 128)):
+    """Instances of the batched (config_id 4) or learned (config_id 5) workload
+    with degree k (instances of the other degree are skipped, so that one batch
+    shares k), their concatenated mesh, elem_start and coefficient table."""
+    cfgs, i = [], 0
+    while len(cfgs) < n_inst:
+        c = random_instance(config_id, i, N_range=N_range, N_fixed=N_fixed)
+        i += 1
+        if k is not None and c.k != k:
+            continue
+        cfgs.append(c)
+    meshes = [structured_mesh(c.N) for c in cfgs]
+    ma, starts = concat_meshes(meshes)
+    coeffs = np.array([[c.problem.eps, c.problem.alpha, *c.problem.b] for c in cfgs])
+    return cfgs, ma, starts, coeffs

@@ -1,0 +1,65 @@
+"""Batched solves of independent instances (per-instance reductions and
+convergence) against single-instance solves and the oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1502_02941_gb300 import dg as D
+from paper_1502_02941_gb300 import problem
+from paper_1502_02941_gb300 import workloads as W
+from gpu_helpers import basis_change, rel_residual_oracle
+from helpers import oracle_system
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("inner", ["f64", "f32"])
+def test_batch_matches_single_instance_solves(k, inner):
+    cfgs, ma, starts, coeffs = W.batch(4, 5, k=k, N_range=(3, 7))
+    h = D.DG(0)
+    store = D.DG_STORE_F64 | (D.DG_STORE_F32 if inner == "f32" else 0)
+    problem.setup_batch(h, cfgs, ma, starts, coeffs, store=store, tol=1e-11, gmres_m=20)
+    h.precond_setup()
+    dt = D.DG_F64 if inner == "f64" else D.DG_F32
+    x, its, rr, st = h.batch_solve(dt, inner_m=20, inner_tol=1e-5, max_outer=30)
+    assert (st == 0).all() and (rr <= 1e-11).all() and (its > 0).all()
+    xb = _np(x)
+    nb = O.nbasis(k)
+    for i, c in enumerate(cfgs):
+        a, b = starts[i] * nb, starts[i + 1] * nb
+        mi = W.structured_mesh(c.N)
+        # oracle: residual of this instance's GPU solution with the oracle operator
+        run = oracle_system(mi, c.k, c.method, c.problem)
+        T = basis_change(run, mi, c.k)
+        assert rel_residual_oracle(run, T, xb[a:b]) <= 1e-10
+        # single-instance GPU solve of the same instance
+        hs = D.DG(0)
+        problem.setup(hs, c, mesh=mi, tol=1e-11, gmres_m=20)
+        xs, _ = hs.gmres_solve()
+        xs = _np(xs)
+        assert np.abs(xs - xb[a:b]).max() <= 1e-8 * np.abs(xs).max()
+        hs.close()
+    h.close()
+
+
+def test_batch_autotune_and_rejects_touching_instances():
+    cfgs, ma, starts, coeffs = W.batch(4, 4, k=1, N_range=(3, 5))
+    h = D.DG(0)
+    problem.setup_batch(h, cfgs, ma, starts, coeffs)
+    tile = h.batch_autotune()
+    assert tile in (2048, 4096, 8192, 16384, 32768)
+    x, its, rr, st = h.batch_solve(D.DG_F64, raise_on_nonconv=False)
+    assert (st == 0).all()
+    # one mesh declared as two instances: they share edges
+    m = W.structured_mesh(4)
+    h.mesh_upload(m.nodes, m.elems, m.dirichlet, m.neumann)
+    with pytest.raises(D.DGError) as e:
+        h.batch_setup(np.array([0, 10, m.ne], np.int32), np.zeros((2, 8)))
+    assert e.value.status == D.DG_ERR_MESH
+    h.close()
