@@ -158,6 +158,13 @@ typedef struct dg_handle dg_handle;
 dg_status dg_create(dg_handle** h, int device, void* stream);
 /* Free the handle and all device memory it owns.  NULL is accepted. */
 dg_status dg_destroy(dg_handle* h);
+/* Create / destroy a CUDA stream that is ordered with the legacy default
+   stream (created without cudaStreamNonBlocking), for callers whose own work
+   runs on the legacy stream: unlike the legacy stream it can be captured into
+   the solver's CUDA graphs. */
+dg_status dg_stream_create(int device, void** stream);
+dg_status dg_stream_destroy(void* stream);
+
 /* Change the stream later calls issue work on. */
 dg_status dg_set_stream(dg_handle* h, void* stream);
 /* Human-readable text of a status code (static storage). */

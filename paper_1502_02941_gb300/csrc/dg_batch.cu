@@ -43,9 +43,11 @@ struct BState {
 
 // per-instance refinement state
 struct BOuter {
-    double bnorm, rnorm, relres;
+    double bnorm, rnorm, relres, best;
     unsigned int arrive;
     int first;
+    int used;   // inner Arnoldi steps spent on this instance
+    int ran;    // an inner solve ran since the last residual
 };
 
 struct BatchDev {
@@ -438,7 +440,7 @@ __global__ void k_b_cycle_end(BatchDev B) {
 // ---------------------------------------------------------------------------
 // r = F - AX on instances still refining; last item: ||r||, relres, flags.
 __global__ void __launch_bounds__(256) k_bo_resid(const double* __restrict__ F, const double* __restrict__ AX,
-                                                   double* __restrict__ r, BatchDev B, double tol) {
+                                                   double* __restrict__ r, BatchDev B, double tol, int max_it) {
     __shared__ double sh[32];
     for (int it = blockIdx.x; it < B.nit; it += gridDim.x) {
         const int inst = B.item_inst[it];
@@ -458,15 +460,27 @@ __global__ void __launch_bounds__(256) k_bo_resid(const double* __restrict__ F, 
             o->rnorm = sqrt(r2);
             if (o->first) {
                 o->bnorm = o->rnorm;
+                o->best = 1.0;
                 o->first = 0;
+            }
+            if (o->ran) {
+                o->used += B.bst[inst].its;
+                o->ran = 0;
             }
             o->relres = o->bnorm > 0.0 ? o->rnorm / o->bnorm : 0.0;
             const bool fin = isfinite(o->relres);
             if (!fin) atomicAdd(B.counters + 1, 1);
-            const int go = (fin && o->relres > tol) ? 1 : 0;
+            // stop refining on convergence, an exhausted step budget, or growth
+            // of the residual (the low-precision operator is too far off)
+            const bool diverging = o->relres > 2.0 * o->best;
+            if (o->relres < o->best) o->best = o->relres;
+            const int go = (fin && o->relres > tol && o->used < max_it && !diverging) ? 1 : 0;
             B.iouter[inst] = go;
             B.iparticipate[inst] = go;
-            if (go) atomicAdd(B.counters + 2, 1);
+            if (go) {
+                o->ran = 1;
+                atomicAdd(B.counters + 2, 1);
+            }
         }
         __syncthreads();
     }
@@ -685,7 +699,8 @@ static dg_status b_gmres(dg_handle* h, BatchRun& Rn, const TA* A, const TB* Binv
         cudaGraphExecDestroy(h->b_graph);
         h->b_graph = nullptr;
     }
-    if (!h->b_graph) {
+    const bool use_graph = h->stream != nullptr;   // capture needs a non-legacy stream
+    if (use_graph && !h->b_graph) {
         cudaGraph_t g;
         DG_CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
         h->b_nodes = b_enqueue_cycle<NB, TA, TB, TV>(h, Rn, A, Binv, F, x);
@@ -700,8 +715,14 @@ static dg_status b_gmres(dg_handle* h, BatchRun& Rn, const TA* A, const TB* Binv
     DG_CK(h, cudaStreamSynchronize(h->stream));
     const int max_cycles = max_it + 2;
     for (int c = 0; c < max_cycles && counters_host[0] > 0; ++c) {
-        DG_CK(h, cudaGraphLaunch(h->b_graph, h->stream));
-        h->nlaunch += h->b_nodes;
+        if (use_graph) {
+            DG_CK(h, cudaGraphLaunch(h->b_graph, h->stream));
+            h->nlaunch += h->b_nodes;
+        } else {
+            h->nlaunch += b_enqueue_cycle<NB, TA, TB, TV>(h, Rn, A, Binv, F, x);
+            DG_CK(h, cudaMemcpyAsync(counters_host, B.counters, sizeof(int) * 4, cudaMemcpyDeviceToHost, h->stream));
+        }
+        DG_LAUNCH_CK(h);
         DG_CK(h, cudaStreamSynchronize(h->stream));
     }
     return DG_OK;
@@ -758,43 +779,33 @@ static dg_status batch_solve_t(dg_handle* h, int inner_dtype, const TA* Alo, con
     } else {
         // f64 refinement around the f32 inner batched GMRES
         std::vector<BOuter> bo0(h->b_n);
-        for (auto& o : bo0) o = BOuter{0.0, 0.0, 1.0, 0u, 1};
+        for (auto& o : bo0) o = BOuter{0.0, 0.0, 1.0, 1.0, 0u, 1, 0, 0};
         std::vector<int> one(h->b_n, 1);
         DG_CK(h, cudaMemcpyAsync(B.bo, bo0.data(), sizeof(BOuter) * h->b_n, cudaMemcpyHostToDevice, h->stream));
         DG_CK(h, cudaMemcpyAsync(B.iouter, one.data(), sizeof(int) * h->b_n, cudaMemcpyHostToDevice, h->stream));
         DG_CK(h, cudaMemsetAsync(x, 0, sizeof(double) * n, h->stream));
         const unsigned ge = (unsigned)((h->ne + 255) / 256);
-        int inner_total = 0;
         for (;;) {
             DevCtl oc{nullptr, nullptr, h->b_inst, B.iouter, nullptr};
             k_apply<NB, double, double, double><<<ge, 256, 0, h->stream>>>(h->A64, h->nbr, x, ax, h->ne, oc,
                                                                            vsel_fixed(), vsel_fixed());
             DG_CK(h, cudaMemsetAsync(B.counters + 2, 0, sizeof(int), h->stream));
-            k_bo_resid<<<Rn.gx, 256, 0, h->stream>>>(F, ax, r64, B, h->p.tol);
+            k_bo_resid<<<Rn.gx, 256, 0, h->stream>>>(F, ax, r64, B, h->p.tol, h->p.max_it);
             h->nlaunch += 2;
             DG_LAUNCH_CK(h);
             DG_CK(h, cudaMemcpyAsync(cnt, B.counters, sizeof(int) * 4, cudaMemcpyDeviceToHost, h->stream));
             DG_CK(h, cudaStreamSynchronize(h->stream));
-            if (cnt[2] == 0 || outer >= max_outer || inner_total >= h->p.max_it) break;
+            if (cnt[2] == 0 || outer >= max_outer) break;
             k_bo_scale<<<Rn.gx, 256, 0, h->stream>>>(r64, rin, B);
             h->nlaunch += 1;
-            s = b_gmres<NB, TA, TB, float>(h, Rn, Alo, Binv, rin, din, inner_tol, h->p.max_it - inner_total, cnt);
+            s = b_gmres<NB, TA, TB, float>(h, Rn, Alo, Binv, rin, din, inner_tol, h->p.max_it, cnt);
             if (s != DG_OK) {
                 result = s;
                 break;
             }
-            // inner iterations of this correction: max over instances
-            hst.resize(h->b_n);
-            DG_CK(h, cudaMemcpyAsync(hst.data(), B.bst, sizeof(BState) * h->b_n, cudaMemcpyDeviceToHost, h->stream));
             k_bo_update<<<Rn.gx, 256, 0, h->stream>>>(x, din, B);
             h->nlaunch += 1;
             DG_LAUNCH_CK(h);
-            DG_CK(h, cudaStreamSynchronize(h->stream));
-            int mx = 0;
-            for (auto& st : hst) mx = std::max(mx, st.its);
-            inner_total += mx;
-            if (its_out)
-                for (int i = 0; i < h->b_n; ++i) its_out[i] = (outer == 0 ? 0 : its_out[i]) + hst[i].its;
             ++outer;
         }
     }
@@ -809,8 +820,7 @@ static dg_status batch_solve_t(dg_handle* h, int inner_dtype, const TA* Alo, con
         const double rr = f64 ? hst[i].relres : hbo[i].relres;
         const bool ok = rr <= h->p.tol;
         nconv += ok;
-        if (f64 && its_out) its_out[i] = hst[i].its;
-        if (!f64 && its_out && outer == 0) its_out[i] = 0;
+        if (its_out) its_out[i] = f64 ? hst[i].its : hbo[i].used;
         if (relres_out) relres_out[i] = rr;
         if (status_out) status_out[i] = ok ? DG_OK : DG_NOT_CONVERGED;
     }

@@ -646,3 +646,17 @@ extern "C" dg_status dg_get_launch_count(dg_handle* h, int64_t* count) {
     *count = h->nlaunch;
     return DG_OK;
 }
+
+extern "C" dg_status dg_stream_create(int device, void** stream) {
+    if (!stream) return DG_ERR_INVALID_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return DG_ERR_CUDA;
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreate(&st) != cudaSuccess) return DG_ERR_CUDA;   // blocking w.r.t. the legacy stream
+    *stream = (void*)st;
+    return DG_OK;
+}
+
+extern "C" dg_status dg_stream_destroy(void* stream) {
+    if (!stream) return DG_ERR_INVALID_ARG;
+    return cudaStreamDestroy((cudaStream_t)stream) == cudaSuccess ? DG_OK : DG_ERR_CUDA;
+}

@@ -63,6 +63,8 @@ _SIGS = {
     "dg_create": (ctypes.c_int, [ctypes.POINTER(c_void_p), ctypes.c_int, c_void_p]),
     "dg_destroy": (ctypes.c_int, [c_void_p]),
     "dg_set_stream": (ctypes.c_int, [c_void_p, c_void_p]),
+    "dg_stream_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(c_void_p)]),
+    "dg_stream_destroy": (ctypes.c_int, [c_void_p]),
     "dg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "dg_last_error": (ctypes.c_char_p, [c_void_p]),
     "dg_params_default": (ctypes.c_int, [ctypes.POINTER(dg_params)]),
@@ -168,6 +170,18 @@ def dg_destroy(h):
 
 def dg_set_stream(h, stream):
     return load().dg_set_stream(h, stream)
+
+
+def dg_stream_create(device=0):
+    st = c_void_p()
+    s = load().dg_stream_create(int(device), ctypes.byref(st))
+    if s != DG_OK:
+        raise DGError(s, "dg_stream_create failed")
+    return st.value
+
+
+def dg_stream_destroy(stream):
+    return load().dg_stream_destroy(stream)
 
 
 def dg_status_string(s):
@@ -334,8 +348,16 @@ class DG:
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device)
+        self._own_stream = None
         if stream is None:
-            stream = torch.cuda.current_stream(self.device).cuda_stream
+            cur = torch.cuda.current_stream(self.device)
+            if cur.cuda_stream == 0:
+                # the legacy default stream cannot be captured into CUDA graphs:
+                # use a stream of our own that is ordered with the legacy one
+                self._own_stream = dg_stream_create(device)
+                stream = self._own_stream
+            else:
+                stream = cur.cuda_stream
         self.h = dg_create(device, stream)
         self.params = dg_params_default()
 
@@ -343,6 +365,9 @@ class DG:
         if self.h is not None:
             dg_destroy(self.h)
             self.h = None
+        if self._own_stream is not None:
+            dg_stream_destroy(self._own_stream)
+            self._own_stream = None
 
     def __del__(self):
         try:
