@@ -76,6 +76,7 @@ typedef int dg_status;
 /* Preconditioners. */
 #define DG_PRECOND_NONE          0
 #define DG_PRECOND_BLOCK_JACOBI  1
+#define DG_PRECOND_MLP           2   /* block Jacobi + learned element-local correction (flexible GMRES) */
 
 /* Point sets of dg_quad_points / dg_eval. */
 #define DG_POINTS_VOLUME   0  /* [ne][(k+2)^2]: Duffy-collapsed Gauss-Legendre */
@@ -344,6 +345,46 @@ dg_status dg_batch_set_tile(dg_handle* h, int tile);
  */
 dg_status dg_batch_solve(dg_handle* h, int inner_dtype, int inner_m, double inner_tol, int max_outer,
                          const double* F, double* x, int* its, double* relres, int* status);
+
+/* ------------------------------------------------------------------------ */
+/* learned right preconditioner (not in the paper; layered on its method)    */
+/* ------------------------------------------------------------------------ */
+/*
+ * An element-local MLP corrects block Jacobi: for element K with face
+ * neighbours L0..L2 and residual r, with s = sqrt(sum of r^2 over K and its
+ * neighbours / (4 nb)),
+ *   x   = [r_K, r_L0, r_L1, r_L2]/s ++ [log10(eps)/6 + 1, b_x, b_y, alpha]  (din = 4nb+4),
+ *   y   = W4 relu(W3 relu(W2 relu(W1 x + b1) + b2) + b3) + b4   (width 128),
+ *   z_K = (M_BJ^-1 r)_K + s y_K.
+ * The network is nonlinear, so params.precond = DG_PRECOND_MLP makes
+ * dg_gmres_solve / dg_batch_solve run flexible GMRES; if two consecutive
+ * restart cycles cut the true residual by less than 10% the correction is
+ * switched off and block Jacobi finishes the solve (info.outer = -1 then).
+ * Parameters: one flat f32 vector W1 [128][din], b1, W2 [128][128], b2, W3,
+ * b3, W4 [nb][128], b4 (row-major); inference uses them rounded to bf16 on the
+ * tensor cores with f32 accumulation, training uses the same bf16-rounded
+ * values in f32 GEMMs and updates f32 master weights with Adam.
+ */
+dg_status dg_mlp_num_params(int degree, int64_t* n);
+/* Initialise the weights for params.degree (uniform He-style, counter-based hash of seed). */
+dg_status dg_mlp_init(dg_handle* h, uint64_t seed);
+/* Host copies of the f32 master weights (n = dg_mlp_num_params). */
+dg_status dg_mlp_set_weights(dg_handle* h, const float* theta, int64_t n);
+dg_status dg_mlp_get_weights(dg_handle* h, float* theta, int64_t n);
+/* Append one training row per element from a solve: r = F - A xk, e = xstar - xk
+   (device [dofs] f64; F NULL = the assembled F); target (e_K - (M_BJ^-1 r)_K)/s. */
+dg_status dg_mlp_collect(dg_handle* h, const double* F, const double* xstar, const double* xk);
+dg_status dg_mlp_num_rows(dg_handle* h, int64_t* rows);
+dg_status dg_mlp_get_rows(dg_handle* h, float* X, float* T, int64_t max_rows);   /* host outputs */
+dg_status dg_mlp_clear_data(dg_handle* h);
+/* Adam on random mini-batches of the collected rows: `steps` updates of
+   batch_rows rows each, learning rate lr; loss host [steps] or NULL.  Synchronises. */
+dg_status dg_mlp_train(dg_handle* h, int steps, int batch_rows, float lr, uint64_t seed, float* loss);
+/* Loss (mean 0.5|y-t|^2) and gradient at the current weights on caller rows
+   X device [rows][din], T device [rows][nb] (f32); loss, grad host. */
+dg_status dg_mlp_loss_grad(dg_handle* h, const float* X, const float* T, int rows, double* loss, float* grad);
+/* Tensor-core forward pass y on caller feature rows: X device [rows][din], Y device [rows][nb] (f32). */
+dg_status dg_mlp_forward(dg_handle* h, const float* X, int rows, float* Y);
 
 /* ------------------------------------------------------------------------ */
 /* post-processing  (the paper's dg_error, Sec. 2.4)                        */

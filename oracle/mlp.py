@@ -1,0 +1,115 @@
+"""FP64 oracle of the element-local MLP preconditioner (test infrastructure only).
+
+The network is not in the paper; it is the learned right preconditioner layered
+on the paper's method.  Plain numpy, FP64, written from the definitions:
+
+  features of element K (din = 4*nb + 4):
+      s   = sqrt(sum of r^2 over K and its face neighbours / (4*nb)) + 1e-30
+      x   = [r_K, r_L0, r_L1, r_L2] / s            (zeros for a missing neighbour)
+            + [log10(max(eps,1e-12))/6 + 1, b_x, b_y, alpha]
+  network g:  h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), h3 = relu(W3 h2 + b3),
+              y  = W4 h3 + b4                       (width 128, y has nb entries)
+  preconditioner:  z_K = (M_BJ^-1 r)_K + s * y_K
+  training target for a pair (r, e = A^-1 r):  t_K = (e_K - (M_BJ^-1 r)_K) / s
+  loss = mean over rows of 0.5 * |y - t|^2, Adam (beta1 0.9, beta2 0.999,
+  eps 1e-8, bias-corrected).
+
+Parameters are one flat vector: W1 (128 x din, row-major), b1, W2, b2, W3, b3,
+W4 (nb x 128), b4.
+"""
+import numpy as np
+
+WIDTH = 128
+
+
+def din_of(nb):
+    return 4 * nb + 4
+
+
+def sizes(nb):
+    d = din_of(nb)
+    return [(WIDTH, d), (WIDTH,), (WIDTH, WIDTH), (WIDTH,), (WIDTH, WIDTH), (WIDTH,), (nb, WIDTH), (nb,)]
+
+
+def n_params(nb):
+    return int(sum(np.prod(s) for s in sizes(nb)))
+
+
+def unpack(theta, nb):
+    out, o = [], 0
+    for s in sizes(nb):
+        n = int(np.prod(s))
+        out.append(theta[o:o + n].reshape(s))
+        o += n
+    return out
+
+
+def features(r, nbr, nb, coef):
+    """r [ne*nb]; nbr [ne,3] (-1 = none); coef [ne,4] = (eps, bx, by, alpha).
+    Returns X [ne, din] and s [ne]."""
+    ne = nbr.shape[0]
+    R = r.reshape(ne, nb)
+    P = np.zeros((ne, 4, nb))
+    P[:, 0] = R
+    for f in range(3):
+        ok = nbr[:, f] >= 0
+        P[ok, 1 + f] = R[nbr[ok, f]]
+    s = np.sqrt((P ** 2).sum(axis=(1, 2)) / (4 * nb)) + 1e-30
+    X = np.zeros((ne, din_of(nb)))
+    X[:, :4 * nb] = P.reshape(ne, -1) / s[:, None]
+    X[:, 4 * nb + 0] = np.log10(np.maximum(coef[:, 0], 1e-12)) / 6 + 1
+    X[:, 4 * nb + 1] = coef[:, 1]
+    X[:, 4 * nb + 2] = coef[:, 2]
+    X[:, 4 * nb + 3] = coef[:, 3]
+    return X, s
+
+
+def forward(theta, X, nb):
+    W1, b1, W2, b2, W3, b3, W4, b4 = unpack(theta, nb)
+    a1 = X @ W1.T + b1
+    h1 = np.maximum(a1, 0)
+    a2 = h1 @ W2.T + b2
+    h2 = np.maximum(a2, 0)
+    a3 = h2 @ W3.T + b3
+    h3 = np.maximum(a3, 0)
+    y = h3 @ W4.T + b4
+    return y, (X, a1, h1, a2, h2, a3, h3)
+
+
+def loss_and_grad(theta, X, T, nb):
+    """Mean over rows of 0.5|y - t|^2 and its gradient (backpropagation)."""
+    W1, b1, W2, b2, W3, b3, W4, b4 = unpack(theta, nb)
+    y, (X, a1, h1, a2, h2, a3, h3) = forward(theta, X, nb)
+    n = X.shape[0]
+    d = (y - T) / n
+    loss = 0.5 * ((y - T) ** 2).sum() / n
+    gW4 = d.T @ h3
+    gb4 = d.sum(0)
+    d3 = (d @ W4) * (a3 > 0)
+    gW3 = d3.T @ h2
+    gb3 = d3.sum(0)
+    d2 = (d3 @ W3) * (a2 > 0)
+    gW2 = d2.T @ h1
+    gb2 = d2.sum(0)
+    d1 = (d2 @ W2) * (a1 > 0)
+    gW1 = d1.T @ X
+    gb1 = d1.sum(0)
+    g = np.concatenate([a.ravel() for a in (gW1, gb1, gW2, gb2, gW3, gb3, gW4, gb4)])
+    return loss, g
+
+
+def adam_step(theta, g, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (step counts from 1); returns new theta, m, v."""
+    m = b1 * m + (1 - b1) * g
+    v = b2 * v + (1 - b2) * g * g
+    mh = m / (1 - b1 ** step)
+    vh = v / (1 - b2 ** step)
+    return theta - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def bf16_round(a):
+    """Round to bfloat16 (nearest, ties to even) and back to float64."""
+    a32 = np.asarray(a, dtype=np.float32)
+    u = a32.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)

@@ -10,6 +10,9 @@
 // boundary) + 2*nb*sizeof(TX) + 12 (neighbour ids) -> HBM-bound.
 #include "dg_kernels.cuh"
 
+template <typename TV>
+dg_status dg_mlp_correct(dg_handle* h, const TV* r, TV* z, DevCtl ctl, VecSel sr, VecSel sz, const int* iuse);
+
 // Gauss-Jordan inverse with partial pivoting (in f64) of each diagonal block
 // A_KK read from the block copy of type TA; Binv64 may be NULL.
 template <int NB, typename TA>
@@ -186,7 +189,9 @@ extern "C" dg_status dg_precond_setup(dg_handle* h, int kind) {
     if (!h) return DG_ERR_INVALID_ARG;
     if (!h->assembled) return dg_fail(h, DG_ERR_STATE, "not assembled");
     if (kind == DG_PRECOND_NONE) return DG_OK;
-    if (kind != DG_PRECOND_BLOCK_JACOBI) return dg_fail(h, DG_ERR_INVALID_ARG, "precond kind");
+    if (kind != DG_PRECOND_BLOCK_JACOBI && kind != DG_PRECOND_MLP) return dg_fail(h, DG_ERR_INVALID_ARG, "precond kind");
+    if (kind == DG_PRECOND_MLP && (!h->mlp.packed || h->mlp.nb != dg_nb(h->asm_k)))
+        return dg_fail(h, DG_ERR_STATE, "MLP preconditioner: dg_mlp_init / dg_mlp_set_weights for this degree first");
     h->bj_ok = false;
     dg_status s = dg_launch_bj_setup(h);
     if (s == DG_OK) h->bj_ok = true;
@@ -198,5 +203,11 @@ extern "C" dg_status dg_precond_apply(dg_handle* h, int dtype, const void* r, vo
     if (!h->bj_ok) return dg_fail(h, DG_ERR_STATE, "preconditioner not set up");
     if (!dg_aligned16(r) || !dg_aligned16(z)) return dg_fail(h, DG_ERR_INVALID_ARG, "r and z must be 16-byte aligned");
     if (dtype != DG_F64 && dtype != DG_F32 && dtype != DG_BF16) return dg_fail(h, DG_ERR_INVALID_ARG, "dtype");
-    return dg_launch_bj_apply(h, dtype == DG_F64 ? DG_F64 : DG_F32, r, z, nullptr);
+    dg_status s = dg_launch_bj_apply(h, dtype == DG_F64 ? DG_F64 : DG_F32, r, z, nullptr);
+    if (s != DG_OK || h->p.precond != DG_PRECOND_MLP || !h->mlp.packed) return s;
+    const int one = 1;
+    DG_CK(h, cudaMemcpyAsync(h->mlp.on, &one, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    if (dtype == DG_F64)
+        return dg_mlp_correct<double>(h, (const double*)r, (double*)z, dctl_none(), vsel_fixed(), vsel_fixed(), nullptr);
+    return dg_mlp_correct<float>(h, (const float*)r, (float*)z, dctl_none(), vsel_fixed(), vsel_fixed(), nullptr);
 }

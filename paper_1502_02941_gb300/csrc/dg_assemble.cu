@@ -365,5 +365,8 @@ extern "C" dg_status dg_assemble(dg_handle* h, const dg_coeffs* c) {
     h->assembled = true;
     h->asm_k = k;
     h->asm_store = h->p.store;
+    h->mlp.coef[0] = c->eps;
+    h->mlp.coef[1] = c->alpha;
+    for (int t = 0; t < 6; ++t) h->mlp.coef[2 + t] = c->b[t];
     return DG_OK;
 }

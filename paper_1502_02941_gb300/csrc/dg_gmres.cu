@@ -24,6 +24,9 @@
 
 #include "dg_kernels.cuh"
 
+template <typename TV>
+dg_status dg_mlp_correct(dg_handle* h, const TV* r, TV* z, DevCtl ctl, VecSel sr, VecSel sz, const int* iuse);
+
 struct GmresState {  // header fields first: the first GM_HDR bytes go to the host
     int active;      // Arnoldi steps proceed while 1
     int j;           // steps completed in the current cycle
@@ -353,7 +356,7 @@ __global__ void __launch_bounds__(256) k_gm_update(TV* V, long ld, long nvec, Gm
 
 // y = H(0:jj,0:jj)^-1 g(0:jj) by column-oriented back substitution in shared
 // memory; coef_i = y_i s_i.
-__global__ void __launch_bounds__(256) k_gm_solve(GmresState* st) {
+__global__ void __launch_bounds__(256) k_gm_solve(GmresState* st, int flexible) {
     if (!st->pending) return;
     __shared__ double Hs[(DG_MAXM + 1) * DG_MAXM];
     __shared__ double gs[DG_MAXM + 1];
@@ -369,7 +372,8 @@ __global__ void __launch_bounds__(256) k_gm_solve(GmresState* st) {
         for (int l = threadIdx.x; l < i; l += blockDim.x) gs[l] -= Hs[(long)i * LD + l] * yi;
         if (threadIdx.x == 0) {
             st->y[i] = yi;
-            st->coef[i] = yi * st->scale[i];
+            // fixed preconditioner: x += M^-1 sum y_i s_i V_i;  flexible: x += sum y_i Z_i
+            st->coef[i] = flexible ? yi : yi * st->scale[i];
         }
         __syncthreads();
     }
@@ -469,10 +473,11 @@ static void launch_bj(dg_handle* h, const TB* B, const TV* r, TV* z, DevCtl ctl,
 // One restart cycle: m Arnoldi steps, the correction and the true residual.
 // Returns the number of kernels enqueued.
 template <int NB, typename TA, typename TB, typename TV>
-static int enqueue_cycle(dg_handle* h, GmresWork& W, const TA* A, const TB* B, const TV* F, TV* x) {
+static int enqueue_cycle(dg_handle* h, GmresWork& W, const TA* A, const TB* B, const TV* F, TV* x, bool flex) {
     TV* V = (TV*)W.V;
     TV* Z = (TV*)W.Z;
     TV* R = (TV*)W.R;
+    TV* Zb = (TV*)W.Zb;
     GmresState* st = W.st;
     const long n = (long)W.n;
     const long ld = (long)W.ld;
@@ -483,27 +488,42 @@ static int enqueue_cycle(dg_handle* h, GmresWork& W, const TA* A, const TB* B, c
     DevCtl step{&st->active, st->scale};
     DevCtl step_noscale{&st->active, nullptr};
     VecSel vj{&st->j, 0, ld}, vj1{&st->j, 1, ld};
+    int extra = 0;
     for (int it = 0; it < W.m; ++it) {
-        launch_bj<NB, TB, TV>(h, B, V, Z, step, vj, vsel_fixed());
-        launch_apply<NB, TA, TV>(h, A, Z, V, step_noscale, vsel_fixed(), vj1);
+        if (flex) {
+            // Z_j = s_j M_BJ^-1 V_j + MLP correction, kept for the update of x
+            VecSel zj{&st->j, 0, ld};
+            launch_bj<NB, TB, TV>(h, B, V, Zb, step, vj, zj);
+            dg_mlp_correct<TV>(h, V, Zb, step, vj, zj, nullptr);
+            launch_apply<NB, TA, TV>(h, A, Zb, V, step_noscale, zj, vj1);
+            ++extra;
+        } else {
+            launch_bj<NB, TB, TV>(h, B, V, Z, step, vj, vsel_fixed());
+            launch_apply<NB, TA, TV>(h, A, Z, V, step_noscale, vsel_fixed(), vj1);
+        }
         for (int pass = 1; pass <= 2; ++pass) {
             k_gm_dots<TV><<<gdots, bdots, 0, h->stream>>>(V, ld, nvec, st, W.partials, pass);
             k_gm_update<TV><<<gx, 256, 0, h->stream>>>(V, ld, nvec, st, W.partials, pass);
         }
     }
     DevCtl pend{&st->pending, nullptr};
-    k_gm_solve<<<1, 256, 0, h->stream>>>(st);
-    k_gm_combine<TV><<<gx, 256, 0, h->stream>>>(V, ld, nvec, st, R);
-    launch_bj<NB, TB, TV>(h, B, R, Z, pend, vsel_fixed(), vsel_fixed());
-    k_gm_axpy<TV><<<gx, 256, 0, h->stream>>>(x, Z, n, st);
+    k_gm_solve<<<1, 256, 0, h->stream>>>(st, flex ? 1 : 0);
+    if (flex) {
+        k_gm_combine<TV><<<gx, 256, 0, h->stream>>>(Zb, ld, nvec, st, R);
+        k_gm_axpy<TV><<<gx, 256, 0, h->stream>>>(x, R, n, st);
+    } else {
+        k_gm_combine<TV><<<gx, 256, 0, h->stream>>>(V, ld, nvec, st, R);
+        launch_bj<NB, TB, TV>(h, B, R, Z, pend, vsel_fixed(), vsel_fixed());
+        k_gm_axpy<TV><<<gx, 256, 0, h->stream>>>(x, Z, n, st);
+    }
     launch_apply<NB, TA, TV>(h, A, x, R, pend, vsel_fixed(), vsel_fixed());
     k_gm_resid<TV><<<gx, 256, 0, h->stream>>>(F, R, V, n, st, W.partials);
     cudaMemcpyAsync(W.st_host, st, GM_HDR, cudaMemcpyDeviceToHost, h->stream);
-    return 6 * W.m + 6;
+    return 6 * W.m + 6 + extra - (flex ? 1 : 0);
 }
 
 void dg_gmres_free(GmresWork* w) {
-    void* ptrs[] = {w->V, w->Z, w->R, w->partials, w->st};
+    void* ptrs[] = {w->V, w->Z, w->R, w->Zb, w->partials, w->st};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (w->st_host) cudaFreeHost(w->st_host);
@@ -522,6 +542,10 @@ static dg_status ensure_workspace(dg_handle* h, GmresWork& W, long n, int m, siz
         DG_CK(h, cudaMemsetAsync(W.V, 0, (size_t)(m + 2) * ld * elem, h->stream));
         DG_CK(h, cudaMemsetAsync(W.Z, 0, ld * elem, h->stream));
         DG_CK(h, cudaMemsetAsync(W.R, 0, ld * elem, h->stream));
+        if (W.Zb) {
+            cudaFree(W.Zb);
+            W.Zb = nullptr;
+        }
         W.ld = ld;
         W.n = n;
         W.m = m;
@@ -549,17 +573,21 @@ static dg_status ensure_workspace(dg_handle* h, GmresWork& W, long n, int m, siz
 // Run restarted GMRES(m) to `tol` on (A, M = B) from x0 = 0.
 template <int NB, typename TA, typename TB, typename TV>
 static dg_status gmres_run(dg_handle* h, GmresWork& W, const TA* A, const TB* B, const TV* F, TV* x, int m,
-                           double tol, int max_it, dg_solve_info* info) {
+                           double tol, int max_it, dg_solve_info* info, bool flex = false) {
     const long n = (long)h->ne * NB;
     dg_status s = ensure_workspace(h, W, n, m, sizeof(TV));
     if (s != DG_OK) return s;
+    if (flex && !W.Zb) {
+        if ((s = dg_realloc(h, &W.Zb, (size_t)(m + 1) * W.ld * sizeof(TV))) != DG_OK) return s;
+        DG_CK(h, cudaMemsetAsync(W.Zb, 0, (size_t)(m + 1) * W.ld * sizeof(TV), h->stream));
+    }
     k_gm_init<TV><<<W.gx, 256, 0, h->stream>>>(F, x, (TV*)W.V, n, W.st, W.partials, m, max_it, tol);
     h->nlaunch += 1;
     DG_LAUNCH_CK(h);
     DG_CK(h, cudaMemcpyAsync(W.st_host, W.st, GM_HDR, cudaMemcpyDeviceToHost, h->stream));
     DG_CK(h, cudaStreamSynchronize(h->stream));
-    const uintptr_t key[6] = {(uintptr_t)x, (uintptr_t)F, (uintptr_t)A, (uintptr_t)B, (uintptr_t)m,
-                              (uintptr_t)h->stream};
+    const uintptr_t key[6] = {(uintptr_t)x, (uintptr_t)F, (uintptr_t)A, (uintptr_t)B,
+                              (uintptr_t)m | ((uintptr_t)flex << 20), (uintptr_t)h->stream};
     if (W.graph && memcmp(key, W.key, sizeof(key)) != 0) {
         cudaGraphExecDestroy(W.graph);
         W.graph = nullptr;
@@ -568,7 +596,7 @@ static dg_status gmres_run(dg_handle* h, GmresWork& W, const TA* A, const TB* B,
     if (use_graph && !W.graph && !W.st_host->done) {
         cudaGraph_t g;
         DG_CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-        W.nodes = enqueue_cycle<NB, TA, TB, TV>(h, W, A, B, F, x);
+        W.nodes = enqueue_cycle<NB, TA, TB, TV>(h, W, A, B, F, x, flex);
         DG_CK(h, cudaStreamEndCapture(h->stream, &g));
         cudaError_t e = cudaGraphInstantiate(&W.graph, g, 0);
         cudaGraphDestroy(g);
@@ -576,21 +604,36 @@ static dg_status gmres_run(dg_handle* h, GmresWork& W, const TA* A, const TB* B,
         memcpy(W.key, key, sizeof(key));
     }
     const int max_cycles = max_it + 2;
+    double prev = 1.0;
+    int stalls = 0;
     for (int c = 0; c < max_cycles && !W.st_host->done; ++c) {
         if (use_graph) {
             DG_CK(h, cudaGraphLaunch(W.graph, h->stream));
             h->nlaunch += W.nodes;
         } else {
-            h->nlaunch += enqueue_cycle<NB, TA, TB, TV>(h, W, A, B, F, x);
+            h->nlaunch += enqueue_cycle<NB, TA, TB, TV>(h, W, A, B, F, x, flex);
         }
         DG_LAUNCH_CK(h);
         DG_CK(h, cudaStreamSynchronize(h->stream));
+        if (flex && h->mlp.on) {
+            // learned preconditioner fallback: two cycles in a row that cut the
+            // true residual by less than 10% switch the correction off (block
+            // Jacobi alone; FGMRES stays valid with a fixed preconditioner)
+            const double rr = W.st_host->relres;
+            stalls = (rr > 0.9 * prev) ? stalls + 1 : 0;
+            prev = rr;
+            if (stalls >= 2 && !h->mlp_fallback) {
+                const int zero = 0;
+                DG_CK(h, cudaMemcpyAsync(h->mlp.on, &zero, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+                h->mlp_fallback = true;
+            }
+        }
     }
     GmresState* hs = W.st_host;
     if (info) {
         info->iterations = hs->its;
         info->restarts = hs->cycles;
-        info->outer = 0;
+        info->outer = flex && h->mlp_fallback ? -1 : 0;
         info->relres = hs->relres;
         info->status = hs->converged ? DG_OK : DG_NOT_CONVERGED;
     }
@@ -601,19 +644,27 @@ static dg_status gmres_run(dg_handle* h, GmresWork& W, const TA* A, const TB* B,
 
 template <int NB>
 static dg_status gmres_f64(dg_handle* h, const double* F, double* x, dg_solve_info* info) {
-    const double* B = h->p.precond == DG_PRECOND_BLOCK_JACOBI ? h->Binv64 : nullptr;
+    const bool mlp = h->p.precond == DG_PRECOND_MLP;
+    const double* B = h->p.precond != DG_PRECOND_NONE ? h->Binv64 : nullptr;
+    h->mlp_fallback = false;
+    if (mlp) {
+        const int one = 1;
+        DG_CK(h, cudaMemcpyAsync(h->mlp.on, &one, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    }
     return gmres_run<NB, double, double, double>(h, h->gw[0], h->A64, B, F, x, h->p.gmres_m, h->p.tol,
-                                                 h->p.max_it, info);
+                                                 h->p.max_it, info, mlp);
 }
 
 extern "C" dg_status dg_gmres_solve(dg_handle* h, const double* F, double* x, dg_solve_info* info) {
     if (!h || !x) return DG_ERR_INVALID_ARG;
     if (!h->assembled) return dg_fail(h, DG_ERR_STATE, "not assembled");
     if (!h->A64) return dg_fail(h, DG_ERR_STATE, "f64 blocks not stored");
-    if (h->p.precond == DG_PRECOND_BLOCK_JACOBI && !h->bj_ok) {
+    if (h->p.precond != DG_PRECOND_NONE && !h->bj_ok) {
         dg_status s = dg_precond_setup(h, DG_PRECOND_BLOCK_JACOBI);
         if (s != DG_OK) return s;
     }
+    if (h->p.precond == DG_PRECOND_MLP && (!h->mlp.packed || h->mlp.nb != dg_nb(h->asm_k)))
+        return dg_fail(h, DG_ERR_STATE, "MLP preconditioner: dg_mlp_init / dg_mlp_set_weights for this degree first");
     DG_CK(h, cudaSetDevice(h->device));
     if (!F) F = h->F;
     if (!dg_aligned16(F) || !dg_aligned16(x)) return dg_fail(h, DG_ERR_INVALID_ARG, "F and x must be 16-byte aligned");

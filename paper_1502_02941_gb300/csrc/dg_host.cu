@@ -58,6 +58,12 @@ static void free_all(dg_handle* h) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (GmresWork& w : h->gw) dg_gmres_free(&w);
+    {
+        MlpState& S = h->mlp;
+        for (void* p : {(void*)S.theta, (void*)S.wr, (void*)S.m, (void*)S.v, (void*)S.grad, (void*)S.wbf,
+                        (void*)S.bias, (void*)S.X, (void*)S.T, (void*)S.ws, (void*)S.on})
+            if (p) cudaFree(p);
+    }
     for (void* p : {(void*)h->b_inst, (void*)h->b_icoef, h->b_dev})
         if (p) cudaFree(p);
     if (h->b_host) cudaFreeHost(h->b_host);
@@ -148,7 +154,7 @@ extern "C" dg_status dg_set_params(dg_handle* h, const dg_params* p) {
     if ((p->store & 7) == 0 || (p->store & ~7)) return dg_fail(h, DG_ERR_INVALID_ARG, "store mask");
     if (p->gmres_m < 1 || p->gmres_m > DG_MAXM) return dg_fail(h, DG_ERR_INVALID_ARG, "gmres_m must be 1..64");
     if (!(p->tol > 0.0) || p->max_it < 1) return dg_fail(h, DG_ERR_INVALID_ARG, "tol/max_it");
-    if (p->precond != DG_PRECOND_NONE && p->precond != DG_PRECOND_BLOCK_JACOBI)
+    if (p->precond != DG_PRECOND_NONE && p->precond != DG_PRECOND_BLOCK_JACOBI && p->precond != DG_PRECOND_MLP)
         return dg_fail(h, DG_ERR_INVALID_ARG, "precond");
     if (p->degree != h->p.degree || p->store != h->p.store) {
         h->assembled = false;

@@ -51,6 +51,32 @@ struct TabLayout {
 
 struct GmresState;   // device-side solver state (dg_gmres.cu)
 
+#define DG_MLP_WIDTH 128
+#define DG_MLP_NOUTP 16      // output rows of the packed last layer (nb <= 10, zero padded)
+
+// Element-local MLP right preconditioner (dg_mlp.cu).
+struct MlpState {
+    int nb = 0, din = 0, dinp = 0;   // unknowns per element, input width, input width padded to 16
+    long P = 0;                      // parameters
+    float* theta = nullptr;          // f32 master weights (flat: W1,b1,W2,b2,W3,b3,W4,b4)
+    float* wr = nullptr;             // the same rounded to bf16 (values used by training)
+    float* m = nullptr;
+    float* v = nullptr;
+    float* grad = nullptr;
+    int step = 0;
+    bool ready = false;
+    __nv_bfloat16* wbf = nullptr;    // packed inference weights W1p|W2p|W3p|W4p
+    float* bias = nullptr;           // packed biases b1|b2|b3|b4p
+    bool packed = false;
+    float* X = nullptr;              // training rows [cap][din]
+    float* T = nullptr;              // training targets [cap][nb]
+    long rows = 0, cap = 0;
+    float* ws = nullptr;             // training workspace
+    size_t ws_cap = 0;
+    int* on = nullptr;               // device flag: MLP correction enabled
+    double coef[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // single-instance eps, alpha, b[6] of the last assembly
+};
+
 // Workspace of one restarted-GMRES solver instance (vectors of `elem` bytes).
 struct GmresWork {
     size_t n = 0;
@@ -60,6 +86,7 @@ struct GmresWork {
     void* V = nullptr;             // [(m+2)][n] Krylov basis, unnormalised
     void* Z = nullptr;             // [n] preconditioned vector / correction
     void* R = nullptr;             // [n] work vector
+    void* Zb = nullptr;            // [(m+1)][ld] preconditioned directions (flexible GMRES)
     double* partials = nullptr;    // per-block reduction scratch
     GmresState* st = nullptr;      // device state
     GmresState* st_host = nullptr; // pinned mirror of the state header
@@ -142,6 +169,9 @@ struct dg_handle {
     cudaGraphExec_t b_graph = nullptr;
     uintptr_t b_key[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     int b_nodes = 0;
+
+    MlpState mlp;
+    bool mlp_fallback = false;     // the last flexible solve switched the MLP off
 
     // mixed-precision refinement buffers (r64, A x, r32, d32, state)
     void* mx_buf = nullptr;

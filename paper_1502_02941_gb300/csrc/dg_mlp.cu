@@ -1,0 +1,811 @@
+// dg_mlp.cu -- the learned element-local right preconditioner.
+//
+// Not part of the paper's method: a small network layered on it.  For element
+// K with face neighbours L0..L2 and residual r:
+//   s   = sqrt(sum of r^2 over K, L0, L1, L2 / (4 nb)),
+//   x   = [r_K, r_L0, r_L1, r_L2] / s  ++  [log10(eps)/6 + 1, b_x, b_y, alpha]
+//         (zeros for a missing neighbour; b at the element centroid),
+//   y   = W4 relu(W3 relu(W2 relu(W1 x + b1) + b2) + b3) + b4   (width 128),
+//   z_K = (M_BJ^-1 r)_K + s y_K.
+// Training pairs (r, e = A^-1 r) come from the method's own f64 solves
+// (r = F - A x_k, e = x* - x_k); the target is t_K = (e_K - (M_BJ^-1 r)_K)/s
+// and the loss the mean of |y - t|^2 / 2, minimised by Adam.  The f32 master
+// weights are rounded to bf16 for every forward/backward pass, so the trained
+// network is the one deployed; training runs as f32 GEMMs on CUDA cores,
+// inference as a fused tensor-core kernel (bf16 mma, f32 accumulate) with the
+// packed weights resident in shared memory of a persistent grid.
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "dg_kernels.cuh"
+
+#define MW DG_MLP_WIDTH
+
+// ---------------------------------------------------------------------------
+// parameter layout
+// ---------------------------------------------------------------------------
+struct MlpOff {
+    long W1, b1, W2, b2, W3, b3, W4, b4, P;
+};
+static MlpOff mlp_off(int nb) {
+    const int din = 4 * nb + 4;
+    MlpOff o;
+    long p = 0;
+    o.W1 = p; p += (long)MW * din;
+    o.b1 = p; p += MW;
+    o.W2 = p; p += (long)MW * MW;
+    o.b2 = p; p += MW;
+    o.W3 = p; p += (long)MW * MW;
+    o.b3 = p; p += MW;
+    o.W4 = p; p += (long)nb * MW;
+    o.b4 = p; p += nb;
+    o.P = p;
+    return o;
+}
+
+extern "C" dg_status dg_mlp_num_params(int degree, int64_t* n) {
+    if (degree < 1 || degree > DG_MAXK || !n) return DG_ERR_INVALID_ARG;
+    *n = mlp_off(dg_nb(degree)).P;
+    return DG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float bf16r(float a) { return __bfloat162float(__float2bfloat16_rn(a)); }
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// uniform in [-a, a) from a counter-based hash
+__global__ void k_mlp_init(float* theta, long P, MlpOff o, int din, int nb, unsigned long long seed) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (long)gridDim.x * blockDim.x) {
+        float bound = 0.f;
+        if (i < o.b1) bound = sqrtf(6.f / din);
+        else if (i >= o.W2 && i < o.b2) bound = sqrtf(6.f / MW);
+        else if (i >= o.W3 && i < o.b3) bound = sqrtf(6.f / MW);
+        else if (i >= o.W4 && i < o.b4) bound = 0.1f * sqrtf(3.f / MW);   // small output layer: start near BJ
+        const unsigned long long z = mix64(seed ^ (unsigned long long)i * 0x632BE59BD9B4E019ull);
+        const float u = (float)((z >> 40) * (1.0 / 16777216.0));   // [0,1)
+        theta[i] = bound * (2.f * u - 1.f);
+    }
+}
+
+__global__ void k_mlp_round(const float* __restrict__ theta, float* __restrict__ wr, long P) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (long)gridDim.x * blockDim.x)
+        wr[i] = bf16r(theta[i]);
+}
+
+// Adam (bias-corrected); refreshes the bf16-rounded working copy.
+__global__ void k_mlp_adam(float* theta, const float* __restrict__ g, float* m, float* v, float* wr, long P, float lr,
+                           float c1, float c2) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = 0.9f * m[i] + 0.1f * gi;
+        const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float th = theta[i] - lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
+        theta[i] = th;
+        wr[i] = bf16r(th);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// f32 tiled GEMM for training:  C[MxN] = op(A)[MxK] op(B)[KxN]  (+ epilogue)
+//   TA: A stored [K][M] (op = transpose) else [M][K];  TB: B stored [N][K] else [K][N]
+//   epilogue: + bias[n]; relu; * (mask[m][n] > 0)
+// ---------------------------------------------------------------------------
+#define GT 64
+#define GK 16
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) k_sgemm(int M, int N, int K, const float* __restrict__ A, int lda,
+                                                const float* __restrict__ B, int ldb, float* __restrict__ C, int ldc,
+                                                const float* __restrict__ bias, int relu, const float* __restrict__ mask,
+                                                int ldm) {
+    __shared__ float As[GK][GT + 1];
+    __shared__ float Bs[GK][GT + 1];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += GK) {
+        for (int t = threadIdx.x; t < GK * GT; t += 256) {
+            const int kk = t / GT, mm = t % GT;
+            const int gm = m0 + mm, gk = k0 + kk;
+            float a = 0.f;
+            if (gm < M && gk < K) a = TA ? A[(long)gk * lda + gm] : A[(long)gm * lda + gk];
+            As[kk][mm] = a;
+            const int gn = n0 + mm;
+            float b = 0.f;
+            if (gn < N && gk < K) b = TB ? B[(long)gn * ldb + gk] : B[(long)gk * ldb + gn];
+            Bs[kk][mm] = b;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GK; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                a[i] = As[kk][ty * 4 + i];
+                b[i] = Bs[kk][tx * 4 + i];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int jn = 0; jn < 4; ++jn) acc[i][jn] = fmaf(a[i], b[jn], acc[i][jn]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jn = 0; jn < 4; ++jn) {
+            const int gm = m0 + ty * 4 + i, gn = n0 + tx * 4 + jn;
+            if (gm >= M || gn >= N) continue;
+            float c = acc[i][jn];
+            if (bias) c += bias[gn];
+            if (relu) c = fmaxf(c, 0.f);
+            if (mask && !(mask[(long)gm * ldm + gn] > 0.f)) c = 0.f;
+            C[(long)gm * ldc + gn] = c;
+        }
+}
+
+template <bool TA, bool TB>
+static void sgemm(cudaStream_t s, int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C,
+                  int ldc, const float* bias = nullptr, int relu = 0, const float* mask = nullptr, int ldm = 0) {
+    dim3 grid((N + GT - 1) / GT, (M + GT - 1) / GT);
+    k_sgemm<TA, TB><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, relu, mask, ldm);
+}
+
+// column sums of D [rows][n] into out[n]
+__global__ void k_colsum(const float* __restrict__ D, int rows, int n, float* __restrict__ out) {
+    const int c = blockIdx.x;
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) s += D[(long)r * n + c];
+    s = dg_block_sum(s, sh);
+    if (threadIdx.x == 0) out[c] = (float)s;
+}
+
+// D = (Y - T) / rows; loss = sum 0.5 (Y - T)^2 / rows
+__global__ void k_mlp_lossd(const float* __restrict__ Y, const float* __restrict__ T, float* __restrict__ D, long cnt,
+                            int rows, double* loss) {
+    __shared__ double sh[32];
+    double a = 0.0;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (long)gridDim.x * blockDim.x) {
+        const float d = Y[i] - T[i];
+        D[i] = d / rows;
+        a += 0.5 * (double)d * (double)d;
+    }
+    a = dg_block_sum(a, sh);
+    if (threadIdx.x == 0) atomicAdd(loss, a / rows);
+}
+
+// gather rows idx of X / T into contiguous batches
+__global__ void k_mlp_gather(const float* __restrict__ X, const float* __restrict__ T, int din, int nb, long nrows,
+                             int B, unsigned long long seed, int step, float* __restrict__ Xb, float* __restrict__ Tb) {
+    for (int r = blockIdx.x; r < B; r += gridDim.x) {
+        const unsigned long long z = mix64(seed ^ ((unsigned long long)step << 32) ^ (unsigned long long)r);
+        const long src = (long)(z % (unsigned long long)nrows);
+        for (int c = threadIdx.x; c < din; c += blockDim.x) Xb[(long)r * din + c] = X[src * din + c];
+        for (int c = threadIdx.x; c < nb; c += blockDim.x) Tb[(long)r * nb + c] = T[src * nb + c];
+    }
+}
+
+// Loss and gradient of the network (weights wr) on rows Xb/Tb (device).  ws
+// holds H1,H2,H3 [B][128], Y/D [B][nb], dH [B][128] x 2.
+static void mlp_loss_grad(cudaStream_t st, const MlpState& S, const MlpOff& o, const float* Xb, const float* Tb,
+                          int B, float* ws, float* grad, double* loss_dev) {
+    const int din = S.din, nb = S.nb;
+    const float* W = S.wr;
+    float* H1 = ws;
+    float* H2 = H1 + (long)B * MW;
+    float* H3 = H2 + (long)B * MW;
+    float* Y = H3 + (long)B * MW;
+    float* D = Y + (long)B * 16;
+    float* G1 = D + (long)B * 16;
+    float* G2 = G1 + (long)B * MW;
+    // forward
+    sgemm<false, true>(st, B, MW, din, Xb, din, W + o.W1, din, H1, MW, W + o.b1, 1);
+    sgemm<false, true>(st, B, MW, MW, H1, MW, W + o.W2, MW, H2, MW, W + o.b2, 1);
+    sgemm<false, true>(st, B, MW, MW, H2, MW, W + o.W3, MW, H3, MW, W + o.b3, 1);
+    sgemm<false, true>(st, B, nb, MW, H3, MW, W + o.W4, MW, Y, nb, W + o.b4, 0);
+    k_mlp_lossd<<<64, 256, 0, st>>>(Y, Tb, D, (long)B * nb, B, loss_dev);
+    // backward
+    sgemm<true, false>(st, nb, MW, B, D, nb, H3, MW, grad + o.W4, MW);          // gW4 = D^T H3
+    k_colsum<<<nb, 256, 0, st>>>(D, B, nb, grad + o.b4);
+    sgemm<false, false>(st, B, MW, nb, D, nb, W + o.W4, MW, G1, MW, nullptr, 0, H3, MW);   // dH3
+    sgemm<true, false>(st, MW, MW, B, G1, MW, H2, MW, grad + o.W3, MW);          // gW3 = dH3^T H2
+    k_colsum<<<MW, 256, 0, st>>>(G1, B, MW, grad + o.b3);
+    sgemm<false, false>(st, B, MW, MW, G1, MW, W + o.W3, MW, G2, MW, nullptr, 0, H2, MW);  // dH2
+    sgemm<true, false>(st, MW, MW, B, G2, MW, H1, MW, grad + o.W2, MW);          // gW2
+    k_colsum<<<MW, 256, 0, st>>>(G2, B, MW, grad + o.b2);
+    sgemm<false, false>(st, B, MW, MW, G2, MW, W + o.W2, MW, G1, MW, nullptr, 0, H1, MW);  // dH1
+    sgemm<true, false>(st, MW, din, B, G1, MW, Xb, din, grad + o.W1, din);       // gW1
+    k_colsum<<<MW, 256, 0, st>>>(G1, B, MW, grad + o.b1);
+}
+
+static size_t mlp_ws_floats(int B) { return (size_t)B * (5 * MW + 32); }
+
+// ---------------------------------------------------------------------------
+// features and training rows
+// ---------------------------------------------------------------------------
+// coefficient features of element K: eps, bx, by, alpha at the centroid
+__device__ __forceinline__ void elem_coef(int K, int ne, const double* __restrict__ geo, const int* inst,
+                                          const double* icoef, const double* scoef, float* out) {
+    const double* c = inst ? icoef + (size_t)DG_ICOEF * inst[K] : scoef;
+    const double x = geo[G_X0 * (size_t)ne + K] + (geo[G_J00 * (size_t)ne + K] + geo[G_J01 * (size_t)ne + K]) / 3.0;
+    const double y = geo[G_Y0 * (size_t)ne + K] + (geo[G_J10 * (size_t)ne + K] + geo[G_J11 * (size_t)ne + K]) / 3.0;
+    out[0] = (float)(log10(fmax(c[0], 1e-12)) / 6.0 + 1.0);
+    out[1] = (float)(c[2] + c[3] * x + c[4] * y);
+    out[2] = (float)(c[5] + c[6] * x + c[7] * y);
+    out[3] = (float)c[1];
+}
+
+struct CoefSrc {
+    const double* geo;
+    const int* inst;
+    const double* icoef;
+    double scoef[8];
+};
+
+// One training row per element: X = features(r), T = (e - zbj)/s.
+template <int NB>
+__global__ void k_mlp_rows(const double* __restrict__ r, const double* __restrict__ e, const double* __restrict__ zbj,
+                           const int* __restrict__ nbr, int ne, CoefSrc cs, float* __restrict__ X,
+                           float* __restrict__ T) {
+    const int K = blockIdx.x * blockDim.x + threadIdx.x;
+    if (K >= ne) return;
+    constexpr int DIN = 4 * NB + 4;
+    double p[4][NB];
+    double ss = 0.0;
+    for (int sl = 0; sl < 4; ++sl) {
+        const int L = sl == 0 ? K : nbr[(size_t)(sl - 1) * ne + K];
+        for (int i = 0; i < NB; ++i) {
+            p[sl][i] = L >= 0 ? r[(size_t)L * NB + i] : 0.0;
+            ss += p[sl][i] * p[sl][i];
+        }
+    }
+    const double s = sqrt(ss / (4 * NB)) + 1e-30;
+    float* x = X + (size_t)K * DIN;
+    for (int sl = 0; sl < 4; ++sl)
+        for (int i = 0; i < NB; ++i) x[sl * NB + i] = (float)(p[sl][i] / s);
+    elem_coef(K, ne, cs.geo, cs.inst, cs.icoef, cs.scoef, x + 4 * NB);
+    for (int i = 0; i < NB; ++i) T[(size_t)K * NB + i] = (float)((e[(size_t)K * NB + i] - zbj[(size_t)K * NB + i]) / s);
+}
+
+__global__ void k_sub(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ c, long n) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        c[i] = a[i] - b[i];
+}
+
+// ---------------------------------------------------------------------------
+// packed bf16 inference weights
+// ---------------------------------------------------------------------------
+struct MlpPack {
+    long W1, W2, W3, W4, total;   // offsets in bf16 elements
+    int dinp;
+};
+static MlpPack mlp_pack_layout(int din) {
+    MlpPack p;
+    p.dinp = (din + 15) / 16 * 16;
+    p.W1 = 0;
+    p.W2 = p.W1 + (long)MW * p.dinp;
+    p.W3 = p.W2 + (long)MW * MW;
+    p.W4 = p.W3 + (long)MW * MW;
+    p.total = p.W4 + (long)DG_MLP_NOUTP * MW;
+    return p;
+}
+
+__global__ void k_mlp_pack(const float* __restrict__ theta, MlpOff o, MlpPack pk, int din, int nb,
+                           __nv_bfloat16* __restrict__ wbf, float* __restrict__ bias) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < pk.total; i += (long)gridDim.x * blockDim.x) {
+        float v = 0.f;
+        if (i < pk.W2) {
+            const long n = i / pk.dinp, k = i % pk.dinp;
+            v = k < din ? theta[o.W1 + n * din + k] : 0.f;
+        } else if (i < pk.W3) {
+            v = theta[o.W2 + (i - pk.W2)];
+        } else if (i < pk.W4) {
+            v = theta[o.W3 + (i - pk.W3)];
+        } else {
+            const long n = (i - pk.W4) / MW, k = (i - pk.W4) % MW;
+            v = n < nb ? theta[o.W4 + n * MW + k] : 0.f;
+        }
+        wbf[i] = __float2bfloat16_rn(v);
+    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 3 * MW + DG_MLP_NOUTP; i += gridDim.x * blockDim.x) {
+        float v;
+        if (i < MW) v = theta[o.b1 + i];
+        else if (i < 2 * MW) v = theta[o.b2 + i - MW];
+        else if (i < 3 * MW) v = theta[o.b3 + i - 2 * MW];
+        else v = (i - 3 * MW) < nb ? theta[o.b4 + i - 3 * MW] : 0.f;
+        bias[i] = bf16r(v);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// fused tensor-core inference
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint32_t* b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// One warp: rows r0..r0+15 of act [rows][ACT_LD] (bf16) times W [N][K] (bf16,
+// row stride K): acc[nt][4] for N/8 n-tiles.
+template <int NT, int KSTEPS>
+__device__ __forceinline__ void warp_layer(const __nv_bfloat16* act, int act_ld, int r0, const __nv_bfloat16* W,
+                                           int wld, float (*acc)[4]) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+#pragma unroll
+    for (int ks = 0; ks < KSTEPS; ++ks) {
+        const int k0 = ks * 16;
+        uint32_t a[4];
+        a[0] = *reinterpret_cast<const uint32_t*>(act + (r0 + g) * act_ld + k0 + 2 * t);
+        a[1] = *reinterpret_cast<const uint32_t*>(act + (r0 + g + 8) * act_ld + k0 + 2 * t);
+        a[2] = *reinterpret_cast<const uint32_t*>(act + (r0 + g) * act_ld + k0 + 2 * t + 8);
+        a[3] = *reinterpret_cast<const uint32_t*>(act + (r0 + g + 8) * act_ld + k0 + 2 * t + 8);
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+            uint32_t b[2];
+            b[0] = *reinterpret_cast<const uint32_t*>(W + (nt * 8 + g) * wld + k0 + 2 * t);
+            b[1] = *reinterpret_cast<const uint32_t*>(W + (nt * 8 + g) * wld + k0 + 2 * t + 8);
+            mma_bf16(acc[nt], a, b);
+        }
+    }
+}
+
+// bias + relu, write back as bf16 into the warp's rows of act
+template <int NT>
+__device__ __forceinline__ void warp_store_relu(__nv_bfloat16* act, int act_ld, int r0, const float* b,
+                                                float (*acc)[4]) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    __syncwarp();
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+        const int c = nt * 8 + 2 * t;
+        const float b0 = b[c], b1 = b[c + 1];
+        *reinterpret_cast<uint32_t*>(act + (r0 + g) * act_ld + c) =
+            pack_bf16(fmaxf(acc[nt][0] + b0, 0.f), fmaxf(acc[nt][1] + b1, 0.f));
+        *reinterpret_cast<uint32_t*>(act + (r0 + g + 8) * act_ld + c) =
+            pack_bf16(fmaxf(acc[nt][2] + b0, 0.f), fmaxf(acc[nt][3] + b1, 0.f));
+    }
+    __syncwarp();
+}
+
+#define MLP_ROWS 128
+#define MLP_ACT_LD (MW + 8)    // padded row stride (bf16) of the activation tile
+
+struct MlpRun {
+    const __nv_bfloat16* wbf;
+    const float* bias;
+    MlpPack pk;
+    CoefSrc cs;
+    const int* on;            // global enable flag (NULL = on)
+    const int* iuse;          // per-instance enable flags (batch) or NULL
+};
+
+// z_K += scale * s_K * y_K for every element (r, z vectors of type TV, selected
+// through the solver control exactly like the block-Jacobi apply).  Also used
+// with Xin != NULL: y for precomputed feature rows (parity tests).
+template <int NB, typename TV>
+__global__ void __launch_bounds__(256, 1) k_mlp_apply(const TV* __restrict__ r0p, TV* __restrict__ z0p,
+                                                       const int* __restrict__ nbr, int ne, MlpRun R, DevCtl ctl,
+                                                       VecSel sr, VecSel sz, const float* __restrict__ Xin,
+                                                       float* __restrict__ Yout) {
+    if (ctl.active && !*ctl.active) return;
+    if (R.on && !*R.on) return;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    constexpr int DIN = 4 * NB + 4;
+    const int dinp = R.pk.dinp;
+    __nv_bfloat16* sW = reinterpret_cast<__nv_bfloat16*>(smraw);
+    float* sb = reinterpret_cast<float*>(smraw + sizeof(__nv_bfloat16) * R.pk.total);
+    __nv_bfloat16* act = reinterpret_cast<__nv_bfloat16*>(sb + 3 * MW + DG_MLP_NOUTP);
+    float* ss = reinterpret_cast<float*>(act + MLP_ROWS * MLP_ACT_LD);
+    int* sk = reinterpret_cast<int*>(ss + MLP_ROWS);
+    // weights and biases once per CTA (persistent grid)
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(R.wbf);
+        uint4* dst = reinterpret_cast<uint4*>(sW);
+        for (long i = threadIdx.x; i < R.pk.total / 8; i += blockDim.x) dst[i] = src[i];
+        for (int i = threadIdx.x; i < 3 * MW + DG_MLP_NOUTP; i += blockDim.x) sb[i] = R.bias[i];
+    }
+    const TV* __restrict__ r = Xin ? nullptr : sel(r0p, sr);
+    TV* __restrict__ z = Xin ? nullptr : sel(z0p, sz);
+    const int ntile = (ne + MLP_ROWS - 1) / MLP_ROWS;
+    const int warp = threadIdx.x >> 5;
+    for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+        __syncthreads();
+        // ---- features (one thread per element)
+        if (threadIdx.x < MLP_ROWS) {
+            const int row = threadIdx.x;
+            const int K = tile * MLP_ROWS + row;
+            __nv_bfloat16* x = act + row * MLP_ACT_LD;
+            bool live = K < ne;
+            if (live && ctl.inst) live = ctl.iactive[ctl.inst[K]] && (!R.iuse || R.iuse[ctl.inst[K]]);
+            float s = 0.f;
+            if (live && Xin) {
+                for (int c = 0; c < dinp; ++c) x[c] = __float2bfloat16_rn(c < DIN ? Xin[(size_t)K * DIN + c] : 0.f);
+                s = 1.f;
+            } else if (live) {
+                double p[4][NB];
+                double sq = 0.0;
+#pragma unroll
+                for (int sl = 0; sl < 4; ++sl) {
+                    const int L = sl == 0 ? K : nbr[(size_t)(sl - 1) * ne + K];
+#pragma unroll
+                    for (int i = 0; i < NB; ++i) {
+                        p[sl][i] = L >= 0 ? (double)r[(size_t)L * NB + i] : 0.0;
+                        sq += p[sl][i] * p[sl][i];
+                    }
+                }
+                const double sd = sqrt(sq / (4 * NB)) + 1e-30;
+#pragma unroll
+                for (int sl = 0; sl < 4; ++sl)
+#pragma unroll
+                    for (int i = 0; i < NB; ++i) x[sl * NB + i] = __float2bfloat16_rn((float)(p[sl][i] / sd));
+                float cf[4];
+                elem_coef(K, ne, R.cs.geo, R.cs.inst, R.cs.icoef, R.cs.scoef, cf);
+                for (int c = 0; c < 4; ++c) x[4 * NB + c] = __float2bfloat16_rn(cf[c]);
+                for (int c = DIN; c < dinp; ++c) x[c] = __float2bfloat16_rn(0.f);
+                double sc = 1.0;
+                if (ctl.inst) sc = ctl.iscale ? ctl.iscale[ctl.inst[K]] : 1.0;
+                else if (ctl.scale) sc = ctl.scale[sr.j ? *sr.j + sr.add : 0];
+                s = (float)(sd * sc);
+            } else {
+                for (int c = 0; c < dinp; ++c) x[c] = __float2bfloat16_rn(0.f);
+            }
+            ss[row] = s;
+            sk[row] = live ? K : -1;
+        }
+        __syncthreads();
+        // ---- four layers, warp w owns rows 16w .. 16w+15
+        const int r0 = warp * 16;
+        float acc[16][4];
+        if (dinp == 16) warp_layer<16, 1>(act, MLP_ACT_LD, r0, sW + R.pk.W1, dinp, acc);
+        else if (dinp == 32) warp_layer<16, 2>(act, MLP_ACT_LD, r0, sW + R.pk.W1, dinp, acc);
+        else warp_layer<16, 3>(act, MLP_ACT_LD, r0, sW + R.pk.W1, dinp, acc);
+        warp_store_relu<16>(act, MLP_ACT_LD, r0, sb, acc);
+        warp_layer<16, 8>(act, MLP_ACT_LD, r0, sW + R.pk.W2, MW, acc);
+        warp_store_relu<16>(act, MLP_ACT_LD, r0, sb + MW, acc);
+        warp_layer<16, 8>(act, MLP_ACT_LD, r0, sW + R.pk.W3, MW, acc);
+        warp_store_relu<16>(act, MLP_ACT_LD, r0, sb + 2 * MW, acc);
+        float out[2][4];
+        warp_layer<2, 8>(act, MLP_ACT_LD, r0, sW + R.pk.W4, MW, out);
+        // ---- z_K += s y_K
+        const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int hrow = 0; hrow < 2; ++hrow)
+#pragma unroll
+                for (int cc = 0; cc < 2; ++cc) {
+                    const int row = r0 + g + 8 * hrow;
+                    const int col = nt * 8 + 2 * t + cc;
+                    const int K = sk[row];
+                    if (K < 0 || col >= NB) continue;
+                    const float y = out[nt][2 * hrow + cc] + sb[3 * MW + col];
+                    if (Yout) Yout[(size_t)K * NB + col] = y;
+                    else z[(size_t)K * NB + col] = (TV)((double)z[(size_t)K * NB + col] + (double)ss[row] * (double)y);
+                }
+    }
+}
+
+static size_t mlp_smem(const MlpPack& pk) {
+    return sizeof(__nv_bfloat16) * pk.total + sizeof(float) * (3 * MW + DG_MLP_NOUTP) +
+           sizeof(__nv_bfloat16) * MLP_ROWS * MLP_ACT_LD + sizeof(float) * MLP_ROWS + sizeof(int) * MLP_ROWS;
+}
+
+template <int NB, typename TV>
+static dg_status launch_mlp(dg_handle* h, const TV* r, TV* z, DevCtl ctl, VecSel sr, VecSel sz, const int* iuse,
+                            const float* Xin, float* Yout, int ne) {
+    MlpState& S = h->mlp;
+    MlpRun R;
+    R.wbf = S.wbf;
+    R.bias = S.bias;
+    R.pk = mlp_pack_layout(S.din);
+    R.cs.geo = h->geo;
+    R.cs.inst = h->b_inst_active ? h->b_inst : nullptr;
+    R.cs.icoef = h->b_inst_active ? h->b_icoef : nullptr;
+    for (int t = 0; t < 8; ++t) R.cs.scoef[t] = S.coef[t];
+    R.on = Xin ? nullptr : S.on;
+    R.iuse = iuse;
+    const size_t smem = mlp_smem(R.pk);
+    static thread_local int configured[DG_MAXK + 1][2] = {};
+    int& cfg = configured[dg_nb(1) == NB ? 1 : (dg_nb(2) == NB ? 2 : 3)][sizeof(TV) == 8 ? 1 : 0];
+    if (!cfg) {
+        DG_CK(h, cudaFuncSetAttribute(k_mlp_apply<NB, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        cfg = 1;
+    }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    const int ntile = (ne + MLP_ROWS - 1) / MLP_ROWS;
+    const int grid = ntile < sms ? ntile : sms;
+    k_mlp_apply<NB, TV><<<grid, 256, smem, h->stream>>>(r, z, h->nbr, ne, R, ctl, sr, sz, Xin, Yout);
+    h->nlaunch += 1;
+    return DG_OK;
+}
+
+// Entry used by the solvers (dg_gmres.cu / dg_batch.cu): z += MLP correction of r.
+template <typename TV>
+dg_status dg_mlp_correct(dg_handle* h, const TV* r, TV* z, DevCtl ctl, VecSel sr, VecSel sz, const int* iuse) {
+    switch (h->mlp.nb) {
+        case 3: return launch_mlp<3, TV>(h, r, z, ctl, sr, sz, iuse, nullptr, nullptr, h->ne);
+        case 6: return launch_mlp<6, TV>(h, r, z, ctl, sr, sz, iuse, nullptr, nullptr, h->ne);
+        case 10: return launch_mlp<10, TV>(h, r, z, ctl, sr, sz, iuse, nullptr, nullptr, h->ne);
+    }
+    return dg_fail(h, DG_ERR_STATE, "MLP not initialised for this degree");
+}
+template dg_status dg_mlp_correct<double>(dg_handle*, const double*, double*, DevCtl, VecSel, VecSel, const int*);
+template dg_status dg_mlp_correct<float>(dg_handle*, const float*, float*, DevCtl, VecSel, VecSel, const int*);
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+static dg_status mlp_alloc(dg_handle* h, int nb) {
+    MlpState& S = h->mlp;
+    if (S.nb == nb && S.theta) return DG_OK;
+    const MlpOff o = mlp_off(nb);
+    S.nb = nb;
+    S.din = 4 * nb + 4;
+    S.dinp = (S.din + 15) / 16 * 16;
+    S.P = o.P;
+    dg_status s;
+    for (float** p : {&S.theta, &S.wr, &S.m, &S.v, &S.grad})
+        if ((s = dg_realloc(h, (void**)p, sizeof(float) * o.P)) != DG_OK) return s;
+    const MlpPack pk = mlp_pack_layout(S.din);
+    if ((s = dg_realloc(h, (void**)&S.wbf, sizeof(__nv_bfloat16) * pk.total)) != DG_OK) return s;
+    if ((s = dg_realloc(h, (void**)&S.bias, sizeof(float) * (3 * MW + DG_MLP_NOUTP))) != DG_OK) return s;
+    if (!S.on) {
+        if ((s = dg_realloc(h, (void**)&S.on, sizeof(int))) != DG_OK) return s;
+    }
+    S.ready = false;
+    S.packed = false;
+    S.step = 0;
+    S.rows = 0;
+    return DG_OK;
+}
+
+static dg_status mlp_refresh(dg_handle* h) {
+    MlpState& S = h->mlp;
+    const MlpOff o = mlp_off(S.nb);
+    k_mlp_round<<<256, 256, 0, h->stream>>>(S.theta, S.wr, S.P);
+    const MlpPack pk = mlp_pack_layout(S.din);
+    k_mlp_pack<<<256, 256, 0, h->stream>>>(S.theta, o, pk, S.din, S.nb, S.wbf, S.bias);
+    const int one = 1;
+    DG_CK(h, cudaMemcpyAsync(S.on, &one, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    h->nlaunch += 2;
+    DG_LAUNCH_CK(h);
+    DG_CK(h, cudaStreamSynchronize(h->stream));
+    S.ready = true;
+    S.packed = true;
+    return DG_OK;
+}
+
+extern "C" dg_status dg_mlp_init(dg_handle* h, uint64_t seed) {
+    if (!h) return DG_ERR_INVALID_ARG;
+    DG_CK(h, cudaSetDevice(h->device));
+    const int nb = dg_nb(h->p.degree);
+    dg_status s = mlp_alloc(h, nb);
+    if (s != DG_OK) return s;
+    MlpState& S = h->mlp;
+    const MlpOff o = mlp_off(nb);
+    k_mlp_init<<<256, 256, 0, h->stream>>>(S.theta, S.P, o, S.din, nb, (unsigned long long)seed);
+    DG_CK(h, cudaMemsetAsync(S.m, 0, sizeof(float) * S.P, h->stream));
+    DG_CK(h, cudaMemsetAsync(S.v, 0, sizeof(float) * S.P, h->stream));
+    h->nlaunch += 1;
+    DG_LAUNCH_CK(h);
+    S.step = 0;
+    return mlp_refresh(h);
+}
+
+extern "C" dg_status dg_mlp_set_weights(dg_handle* h, const float* theta, int64_t n) {
+    if (!h || !theta) return DG_ERR_INVALID_ARG;
+    DG_CK(h, cudaSetDevice(h->device));
+    const int nb = dg_nb(h->p.degree);
+    dg_status s = mlp_alloc(h, nb);
+    if (s != DG_OK) return s;
+    if (n != h->mlp.P) return dg_fail(h, DG_ERR_INVALID_ARG, "parameter count does not match the degree");
+    DG_CK(h, cudaMemcpyAsync(h->mlp.theta, theta, sizeof(float) * n, cudaMemcpyHostToDevice, h->stream));
+    DG_CK(h, cudaMemsetAsync(h->mlp.m, 0, sizeof(float) * n, h->stream));
+    DG_CK(h, cudaMemsetAsync(h->mlp.v, 0, sizeof(float) * n, h->stream));
+    h->mlp.step = 0;
+    return mlp_refresh(h);
+}
+
+extern "C" dg_status dg_mlp_get_weights(dg_handle* h, float* theta, int64_t n) {
+    if (!h || !theta) return DG_ERR_INVALID_ARG;
+    if (!h->mlp.ready) return dg_fail(h, DG_ERR_STATE, "MLP not initialised");
+    if (n != h->mlp.P) return dg_fail(h, DG_ERR_INVALID_ARG, "parameter count");
+    DG_CK(h, cudaMemcpyAsync(theta, h->mlp.theta, sizeof(float) * n, cudaMemcpyDeviceToHost, h->stream));
+    DG_CK(h, cudaStreamSynchronize(h->stream));
+    return DG_OK;
+}
+
+extern "C" dg_status dg_mlp_clear_data(dg_handle* h) {
+    if (!h) return DG_ERR_INVALID_ARG;
+    h->mlp.rows = 0;
+    return DG_OK;
+}
+
+extern "C" dg_status dg_mlp_collect(dg_handle* h, const double* F, const double* xstar, const double* xk) {
+    if (!h || !xstar || !xk) return DG_ERR_INVALID_ARG;
+    if (!h->assembled || !h->A64) return dg_fail(h, DG_ERR_STATE, "assemble with f64 blocks first");
+    MlpState& S = h->mlp;
+    if (!S.ready || S.nb != dg_nb(h->asm_k)) return dg_fail(h, DG_ERR_STATE, "dg_mlp_init first (same degree)");
+    if (!h->bj_ok) {
+        dg_status s = dg_precond_setup(h, DG_PRECOND_BLOCK_JACOBI);
+        if (s != DG_OK) return s;
+    }
+    DG_CK(h, cudaSetDevice(h->device));
+    if (!F) F = h->F;
+    const int nb = S.nb;
+    const long n = (long)h->ne * nb;
+    // grow the row store
+    const long need = S.rows + h->ne;
+    if (need > S.cap) {
+        long cap = S.cap ? S.cap : 65536;
+        while (cap < need) cap *= 2;
+        float *X = nullptr, *T = nullptr;
+        if (cudaMalloc(&X, sizeof(float) * cap * S.din) != cudaSuccess) return dg_fail(h, DG_ERR_NOMEM, "rows");
+        if (cudaMalloc(&T, sizeof(float) * cap * nb) != cudaSuccess) {
+            cudaFree(X);
+            return dg_fail(h, DG_ERR_NOMEM, "rows");
+        }
+        if (S.rows) {
+            DG_CK(h, cudaMemcpyAsync(X, S.X, sizeof(float) * S.rows * S.din, cudaMemcpyDeviceToDevice, h->stream));
+            DG_CK(h, cudaMemcpyAsync(T, S.T, sizeof(float) * S.rows * nb, cudaMemcpyDeviceToDevice, h->stream));
+        }
+        DG_CK(h, cudaStreamSynchronize(h->stream));
+        cudaFree(S.X);
+        cudaFree(S.T);
+        S.X = X;
+        S.T = T;
+        S.cap = cap;
+    }
+    dg_status s = dg_scratch(h, sizeof(double) * 3 * n);
+    if (s != DG_OK) return s;
+    double* r = h->scratch;
+    double* e = r + n;
+    double* zb = e + n;
+    // r = F - A xk, e = x* - xk, zb = M_BJ^-1 r
+    if ((s = dg_launch_apply(h, DG_F64, xk, zb)) != DG_OK) return s;
+    k_sub<<<512, 256, 0, h->stream>>>(F, zb, r, n);
+    k_sub<<<512, 256, 0, h->stream>>>(xstar, xk, e, n);
+    if ((s = dg_launch_bj_apply(h, DG_F64, r, zb, nullptr)) != DG_OK) return s;
+    CoefSrc cs;
+    cs.geo = h->geo;
+    cs.inst = h->b_inst_active ? h->b_inst : nullptr;
+    cs.icoef = h->b_inst_active ? h->b_icoef : nullptr;
+    for (int t = 0; t < 8; ++t) cs.scoef[t] = S.coef[t];
+    float* X = S.X + S.rows * S.din;
+    float* T = S.T + S.rows * nb;
+    const unsigned grid = (unsigned)((h->ne + 127) / 128);
+    switch (nb) {
+        case 3: k_mlp_rows<3><<<grid, 128, 0, h->stream>>>(r, e, zb, h->nbr, h->ne, cs, X, T); break;
+        case 6: k_mlp_rows<6><<<grid, 128, 0, h->stream>>>(r, e, zb, h->nbr, h->ne, cs, X, T); break;
+        case 10: k_mlp_rows<10><<<grid, 128, 0, h->stream>>>(r, e, zb, h->nbr, h->ne, cs, X, T); break;
+    }
+    h->nlaunch += 3;
+    DG_LAUNCH_CK(h);
+    DG_CK(h, cudaStreamSynchronize(h->stream));
+    S.rows += h->ne;
+    return DG_OK;
+}
+
+extern "C" dg_status dg_mlp_num_rows(dg_handle* h, int64_t* rows) {
+    if (!h || !rows) return DG_ERR_INVALID_ARG;
+    *rows = h->mlp.rows;
+    return DG_OK;
+}
+
+static dg_status mlp_ws(dg_handle* h, int B) {
+    MlpState& S = h->mlp;
+    const size_t need = sizeof(float) * (mlp_ws_floats(B) + (size_t)B * (S.din + S.nb)) + sizeof(double) * 4;
+    if (S.ws_cap >= need) return DG_OK;
+    dg_status s = dg_realloc(h, (void**)&S.ws, need);
+    S.ws_cap = s == DG_OK ? need : 0;
+    return s;
+}
+
+extern "C" dg_status dg_mlp_train(dg_handle* h, int steps, int batch_rows, float lr, uint64_t seed, float* loss) {
+    if (!h || steps < 1 || batch_rows < 1 || !(lr > 0.f)) return DG_ERR_INVALID_ARG;
+    MlpState& S = h->mlp;
+    if (!S.ready) return dg_fail(h, DG_ERR_STATE, "dg_mlp_init first");
+    if (S.rows < 1) return dg_fail(h, DG_ERR_STATE, "no training rows (dg_mlp_collect)");
+    DG_CK(h, cudaSetDevice(h->device));
+    dg_status s = mlp_ws(h, batch_rows);
+    if (s != DG_OK) return s;
+    const MlpOff o = mlp_off(S.nb);
+    float* ws = S.ws;
+    float* Xb = ws + mlp_ws_floats(batch_rows);
+    float* Tb = Xb + (size_t)batch_rows * S.din;
+    double* lossd = reinterpret_cast<double*>(Tb + (size_t)batch_rows * S.nb + 2);
+    lossd = reinterpret_cast<double*>(((uintptr_t)lossd + 7) & ~(uintptr_t)7);
+    std::vector<double> hl(steps);
+    for (int it = 0; it < steps; ++it) {
+        k_mlp_gather<<<256, 64, 0, h->stream>>>(S.X, S.T, S.din, S.nb, S.rows, batch_rows, seed, S.step + it, Xb, Tb);
+        DG_CK(h, cudaMemsetAsync(lossd, 0, sizeof(double), h->stream));
+        mlp_loss_grad(h->stream, S, o, Xb, Tb, batch_rows, ws, S.grad, lossd);
+        ++S.step;
+        const float c1 = 1.f - powf(0.9f, (float)S.step), c2 = 1.f - powf(0.999f, (float)S.step);
+        k_mlp_adam<<<512, 256, 0, h->stream>>>(S.theta, S.grad, S.m, S.v, S.wr, S.P, lr, c1, c2);
+        h->nlaunch += 20;
+        if (loss) DG_CK(h, cudaMemcpyAsync(&hl[it], lossd, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    }
+    DG_LAUNCH_CK(h);
+    DG_CK(h, cudaStreamSynchronize(h->stream));
+    if (loss)
+        for (int it = 0; it < steps; ++it) loss[it] = (float)hl[it];
+    return mlp_refresh(h);
+}
+
+// Loss and gradient at the current weights on caller rows (device X [rows][din],
+// T [rows][nb] f32); host outputs.
+extern "C" dg_status dg_mlp_loss_grad(dg_handle* h, const float* X, const float* T, int rows, double* loss,
+                                      float* grad) {
+    if (!h || !X || !T || rows < 1) return DG_ERR_INVALID_ARG;
+    MlpState& S = h->mlp;
+    if (!S.ready) return dg_fail(h, DG_ERR_STATE, "dg_mlp_init first");
+    DG_CK(h, cudaSetDevice(h->device));
+    dg_status s = mlp_ws(h, rows);
+    if (s != DG_OK) return s;
+    const MlpOff o = mlp_off(S.nb);
+    float* ws = S.ws;
+    double* lossd = reinterpret_cast<double*>(((uintptr_t)(ws + mlp_ws_floats(rows) + (size_t)rows * (S.din + S.nb)) + 7) &
+                                              ~(uintptr_t)7);
+    DG_CK(h, cudaMemsetAsync(lossd, 0, sizeof(double), h->stream));
+    mlp_loss_grad(h->stream, S, o, X, T, rows, ws, S.grad, lossd);
+    h->nlaunch += 18;
+    DG_LAUNCH_CK(h);
+    if (loss) DG_CK(h, cudaMemcpyAsync(loss, lossd, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (grad) DG_CK(h, cudaMemcpyAsync(grad, S.grad, sizeof(float) * S.P, cudaMemcpyDeviceToHost, h->stream));
+    DG_CK(h, cudaStreamSynchronize(h->stream));
+    return DG_OK;
+}
+
+// Tensor-core forward on caller feature rows: Y [rows][nb] (device f32).
+extern "C" dg_status dg_mlp_forward(dg_handle* h, const float* X, int rows, float* Y) {
+    if (!h || !X || !Y || rows < 1) return DG_ERR_INVALID_ARG;
+    MlpState& S = h->mlp;
+    if (!S.packed) return dg_fail(h, DG_ERR_STATE, "dg_mlp_init first");
+    DG_CK(h, cudaSetDevice(h->device));
+    dg_status s;
+    switch (S.nb) {
+        case 3: s = launch_mlp<3, float>(h, nullptr, nullptr, dctl_none(), vsel_fixed(), vsel_fixed(), nullptr, X, Y, rows); break;
+        case 6: s = launch_mlp<6, float>(h, nullptr, nullptr, dctl_none(), vsel_fixed(), vsel_fixed(), nullptr, X, Y, rows); break;
+        case 10: s = launch_mlp<10, float>(h, nullptr, nullptr, dctl_none(), vsel_fixed(), vsel_fixed(), nullptr, X, Y, rows); break;
+        default: return dg_fail(h, DG_ERR_STATE, "degree");
+    }
+    if (s != DG_OK) return s;
+    DG_LAUNCH_CK(h);
+    return DG_OK;
+}
+
+// Copy collected rows to the host (first `max_rows`).
+extern "C" dg_status dg_mlp_get_rows(dg_handle* h, float* X, float* T, int64_t max_rows) {
+    if (!h || max_rows < 0) return DG_ERR_INVALID_ARG;
+    MlpState& S = h->mlp;
+    const long n = max_rows < S.rows ? max_rows : S.rows;
+    if (X && n) DG_CK(h, cudaMemcpyAsync(X, S.X, sizeof(float) * n * S.din, cudaMemcpyDeviceToHost, h->stream));
+    if (T && n) DG_CK(h, cudaMemcpyAsync(T, S.T, sizeof(float) * n * S.nb, cudaMemcpyDeviceToHost, h->stream));
+    DG_CK(h, cudaStreamSynchronize(h->stream));
+    return DG_OK;
+}

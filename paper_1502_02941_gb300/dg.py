@@ -26,7 +26,7 @@ DG_ERR_STATE, DG_ERR_NOMEM = 8, 9
 DG_NIPG, DG_SIPG, DG_IIPG = 1, 2, 3
 DG_F64, DG_F32, DG_BF16 = 0, 1, 2
 DG_STORE_F64, DG_STORE_F32, DG_STORE_BF16 = 1, 2, 4
-DG_PRECOND_NONE, DG_PRECOND_BLOCK_JACOBI = 0, 1
+DG_PRECOND_NONE, DG_PRECOND_BLOCK_JACOBI, DG_PRECOND_MLP = 0, 1, 2
 DG_POINTS_VOLUME, DG_POINTS_BOUNDARY, DG_POINTS_ERROR = 0, 1, 2
 DG_PROF_DOTS, DG_PROF_UPDATE = 1, 2
 
@@ -97,6 +97,18 @@ _SIGS = {
     "dg_batch_set_tile": (ctypes.c_int, [c_void_p, ctypes.c_int]),
     "dg_batch_solve": (ctypes.c_int, [c_void_p, ctypes.c_int, ctypes.c_int, c_double, ctypes.c_int, c_void_p,
                                       c_void_p, c_void_p, c_void_p, c_void_p]),
+    "dg_mlp_num_params": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(c_int64)]),
+    "dg_mlp_init": (ctypes.c_int, [c_void_p, ctypes.c_uint64]),
+    "dg_mlp_set_weights": (ctypes.c_int, [c_void_p, c_void_p, c_int64]),
+    "dg_mlp_get_weights": (ctypes.c_int, [c_void_p, c_void_p, c_int64]),
+    "dg_mlp_collect": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "dg_mlp_num_rows": (ctypes.c_int, [c_void_p, ctypes.POINTER(c_int64)]),
+    "dg_mlp_get_rows": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_int64]),
+    "dg_mlp_clear_data": (ctypes.c_int, [c_void_p]),
+    "dg_mlp_train": (ctypes.c_int, [c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_uint64, c_void_p]),
+    "dg_mlp_loss_grad": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, ctypes.c_int, ctypes.POINTER(c_double),
+                                        c_void_p]),
+    "dg_mlp_forward": (ctypes.c_int, [c_void_p, c_void_p, ctypes.c_int, c_void_p]),
     "dg_get_launch_count": (ctypes.c_int, [c_void_p, ctypes.POINTER(c_int64)]),
     "dg_reference_basis": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
     "dg_reference_rule": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, c_void_p, c_void_p,
@@ -312,6 +324,61 @@ def dg_batch_solve(h, inner_dtype, inner_m, inner_tol, max_outer, F, x, its=None
                                  _ptr(x), _ptr(its), _ptr(relres), _ptr(status))
 
 
+def dg_mlp_num_params(degree):
+    n = c_int64()
+    s = load().dg_mlp_num_params(int(degree), ctypes.byref(n))
+    if s != DG_OK:
+        raise DGError(s, "dg_mlp_num_params")
+    return n.value
+
+
+def dg_mlp_init(h, seed):
+    return load().dg_mlp_init(h, int(seed))
+
+
+def dg_mlp_set_weights(h, theta):
+    theta = np.ascontiguousarray(theta, dtype=np.float32)
+    return load().dg_mlp_set_weights(h, _ptr(theta), theta.size)
+
+
+def dg_mlp_get_weights(h, n):
+    out = np.zeros(n, np.float32)
+    s = load().dg_mlp_get_weights(h, _ptr(out), n)
+    return s, out
+
+
+def dg_mlp_collect(h, F, xstar, xk):
+    return load().dg_mlp_collect(h, _ptr(F), _ptr(xstar), _ptr(xk))
+
+
+def dg_mlp_num_rows(h):
+    n = c_int64()
+    s = load().dg_mlp_num_rows(h, ctypes.byref(n))
+    return s, n.value
+
+
+def dg_mlp_get_rows(h, X, T, max_rows):
+    return load().dg_mlp_get_rows(h, _ptr(X), _ptr(T), int(max_rows))
+
+
+def dg_mlp_clear_data(h):
+    return load().dg_mlp_clear_data(h)
+
+
+def dg_mlp_train(h, steps, batch_rows, lr, seed, loss=None):
+    return load().dg_mlp_train(h, int(steps), int(batch_rows), float(lr), int(seed), _ptr(loss))
+
+
+def dg_mlp_loss_grad(h, X, T, rows, grad=None):
+    loss = c_double()
+    s = load().dg_mlp_loss_grad(h, _ptr(X), _ptr(T), int(rows), ctypes.byref(loss), _ptr(grad))
+    return s, loss.value
+
+
+def dg_mlp_forward(h, X, rows, Y):
+    return load().dg_mlp_forward(h, _ptr(X), int(rows), _ptr(Y))
+
+
 def dg_get_launch_count(h):
     c = c_int64()
     s = load().dg_get_launch_count(h, ctypes.byref(c))
@@ -508,6 +575,31 @@ class DG:
         if s != DG_OK and not (s == DG_NOT_CONVERGED and not raise_on_nonconv):
             self.check(s)
         return x, its, rr, st
+
+    # -- learned preconditioner -------------------------------------------------
+    def mlp_init(self, seed=0):
+        self.check(dg_mlp_init(self.h, seed))
+
+    def mlp_set_weights(self, theta):
+        self.check(dg_mlp_set_weights(self.h, theta))
+
+    def mlp_get_weights(self):
+        s, th = dg_mlp_get_weights(self.h, dg_mlp_num_params(self.params.degree))
+        self.check(s)
+        return th
+
+    def mlp_collect(self, xstar, xk, F=None):
+        self.check(dg_mlp_collect(self.h, F, xstar, xk))
+
+    def mlp_rows(self):
+        s, n = dg_mlp_num_rows(self.h)
+        self.check(s)
+        return n
+
+    def mlp_train(self, steps, batch_rows=4096, lr=1e-3, seed=0):
+        loss = np.zeros(steps, np.float32)
+        self.check(dg_mlp_train(self.h, steps, batch_rows, lr, seed, loss))
+        return loss
 
     def launch_count(self):
         s, c = dg_get_launch_count(self.h)

@@ -419,3 +419,58 @@ def test_l2_error_of_zero_solution():
     err, hmax = oracle_l2(run, np.zeros(run.mesh.ne * 3), prob)
     assert abs(err - 0.5) < 1e-9
     assert abs(hmax - math.sqrt(2) / 8) < 1e-15
+
+
+# ----------------------------------------------------------------------------
+# MLP preconditioner oracle (FP64): gradients, Adam, features
+# ----------------------------------------------------------------------------
+
+
+def test_mlp_gradient_matches_finite_differences():
+    from oracle import mlp as M
+    nb = 3
+    rng = np.random.default_rng(0)
+    theta = rng.standard_normal(M.n_params(nb)) * 0.2
+    X = rng.standard_normal((7, M.din_of(nb)))
+    T = rng.standard_normal((7, nb))
+    loss, g = M.loss_and_grad(theta, X, T, nb)
+    idx = rng.choice(theta.size, 40, replace=False)
+    h = 1e-6
+    for i in idx:
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd = (M.loss_and_grad(tp, X, T, nb)[0] - M.loss_and_grad(tm, X, T, nb)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * (1 + abs(g[i]))
+
+
+def test_mlp_adam_step_by_hand():
+    from oracle import mlp as M
+    th = np.array([1.0, -2.0]); g = np.array([0.5, -0.25])
+    t1, m, v = M.adam_step(th, g, np.zeros(2), np.zeros(2), 1, lr=0.1)
+    # first step: m_hat = g, v_hat = g^2 -> update = lr * sign(g) (up to eps)
+    np.testing.assert_allclose(t1, th - 0.1 * np.sign(g), atol=1e-7)
+
+
+def test_mlp_features_scale_invariant():
+    from oracle import mlp as M
+    rng = np.random.default_rng(1)
+    nbr = np.array([[1, -1, 2], [0, 2, -1], [1, 0, -1]])
+    r = rng.standard_normal(9)
+    coef = np.array([[1e-3, 0.3, -0.2, 0.5]] * 3)
+    X1, s1 = M.features(r, nbr, 3, coef)
+    X2, s2 = M.features(7.5 * r, nbr, 3, coef)
+    np.testing.assert_allclose(X1, X2, rtol=1e-13)
+    np.testing.assert_allclose(s2, 7.5 * s1, rtol=1e-13)
+    # element 0: face 0 -> element 1, face 1 -> none, face 2 -> element 2
+    np.testing.assert_allclose(X1[0, 3:6], r[3:6] / s1[0])
+    assert np.all(X1[0, 6:9] == 0)
+    np.testing.assert_allclose(X1[0, 9:12], r[6:9] / s1[0])
+    np.testing.assert_allclose(s1[0], np.sqrt((r[0:9] ** 2).sum() / 12))
+
+
+def test_bf16_rounding():
+    from oracle import mlp as M
+    import torch
+    a = np.random.default_rng(2).standard_normal(1000) * 10
+    np.testing.assert_array_equal(M.bf16_round(a), torch.tensor(a, dtype=torch.float32).to(torch.bfloat16).double().numpy())
