@@ -350,18 +350,22 @@ dg_status dg_batch_solve(dg_handle* h, int inner_dtype, int inner_m, double inne
 /* learned right preconditioner (not in the paper; layered on its method)    */
 /* ------------------------------------------------------------------------ */
 /*
- * An element-local MLP corrects block Jacobi: for element K with face
+ * An element-local MLP corrects block Jacobi towards the one-layer-overlap
+ * Schwarz correction it is trained on: for element K with face
  * neighbours L0..L2 and residual r, with s = sqrt(sum of r^2 over K and its
  * neighbours / (4 nb)),
- *   x   = [r_K, r_L0, r_L1, r_L2]/s ++ [log10(eps)/6 + 1, b_x, b_y, alpha]  (din = 4nb+4),
+ *   x   = [r_K, r_L0, r_L1, r_L2]/s ++ [log10(eps)/6 + 1, b_x, b_y, alpha,
+ *          J/sqrt(det J) (4 entries)]                               (din = 4nb+8),
  *   y   = W4 relu(W3 relu(W2 relu(W1 x + b1) + b2) + b3) + b4   (width 128),
- *   z_K = (M_BJ^-1 r)_K + s y_K.
+ *   z_K = A_KK^-1 (r_K + s sigma y_K)        (A_KK^-1: the block-Jacobi inverse),
+ * b at the element centroid, J the element's affine map, sigma a fixed output
+ * scale set when training starts.
  * The network is nonlinear, so params.precond = DG_PRECOND_MLP makes
  * dg_gmres_solve / dg_batch_solve run flexible GMRES; if two consecutive
  * restart cycles cut the true residual by less than 10% the correction is
  * switched off and block Jacobi finishes the solve (info.outer = -1 then).
  * Parameters: one flat f32 vector W1 [128][din], b1, W2 [128][128], b2, W3,
- * b3, W4 [nb][128], b4 (row-major); inference uses them rounded to bf16 on the
+ * b3, W4 [nb][128], b4 (row-major), sigma; inference uses them rounded to bf16 on the
  * tensor cores with f32 accumulation, training uses the same bf16-rounded
  * values in f32 GEMMs and updates f32 master weights with Adam.
  */
@@ -371,9 +375,17 @@ dg_status dg_mlp_init(dg_handle* h, uint64_t seed);
 /* Host copies of the f32 master weights (n = dg_mlp_num_params). */
 dg_status dg_mlp_set_weights(dg_handle* h, const float* theta, int64_t n);
 dg_status dg_mlp_get_weights(dg_handle* h, float* theta, int64_t n);
-/* Append one training row per element from a solve: r = F - A xk, e = xstar - xk
-   (device [dofs] f64; F NULL = the assembled F); target (e_K - (M_BJ^-1 r)_K)/s. */
-dg_status dg_mlp_collect(dg_handle* h, const double* F, const double* xstar, const double* xk);
+/* Append one training row per element from an iterate xk of a solve:
+   r = F - A xk (device [dofs] f64; F NULL = the assembled F); the correction
+   paired with r is the one-layer-overlap patch solve w (w_K from A_P w = r_P on
+   K and its face neighbours), target (A_KK w_K - r_K)/s. */
+dg_status dg_mlp_collect(dg_handle* h, const double* F, const double* xk);
+/* The same for the first nvec Krylov basis vectors of the last f64 solve
+   (dg_gmres_solve, or dg_batch_solve with DG_F64): the vectors the
+   preconditioner is applied to inside GMRES.  nvec <= params.gmres_m + 1.
+   DG_ERR_STATE when no f64 solve ran since the last solver call of another
+   kind (the basis is then gone). */
+dg_status dg_mlp_collect_basis(dg_handle* h, int nvec);
 dg_status dg_mlp_num_rows(dg_handle* h, int64_t* rows);
 dg_status dg_mlp_get_rows(dg_handle* h, float* X, float* T, int64_t max_rows);   /* host outputs */
 dg_status dg_mlp_clear_data(dg_handle* h);

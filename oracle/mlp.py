@@ -3,27 +3,32 @@
 The network is not in the paper; it is the learned right preconditioner layered
 on the paper's method.  Plain numpy, FP64, written from the definitions:
 
-  features of element K (din = 4*nb + 4):
+  features of element K (din = 4*nb + 8):
       s   = sqrt(sum of r^2 over K and its face neighbours / (4*nb)) + 1e-30
       x   = [r_K, r_L0, r_L1, r_L2] / s            (zeros for a missing neighbour)
-            + [log10(max(eps,1e-12))/6 + 1, b_x, b_y, alpha]
+            + [log10(max(eps,1e-12))/6 + 1, b_x, b_y, alpha, J/sqrt(det J) (4 entries)]
   network g:  h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), h3 = relu(W3 h2 + b3),
               y  = W4 h3 + b4                       (width 128, y has nb entries)
-  preconditioner:  z_K = (M_BJ^-1 r)_K + s * y_K
-  training target for a pair (r, e = A^-1 r):  t_K = (e_K - (M_BJ^-1 r)_K) / s
-  loss = mean over rows of 0.5 * |y - t|^2, Adam (beta1 0.9, beta2 0.999,
-  eps 1e-8, bias-corrected).
+  preconditioner:  z_K = A_KK^-1 (r_K + s * sigma * y_K)   (A_KK: diagonal block)
+  training target for a residual r paired with its correction w (the
+  one-layer-overlap patch solve):  t_K = (A_KK w_K - r_K) / s,
+  sigma = RMS of all targets (fixed when training starts), and the network
+  fits t / sigma: loss = mean over rows of 0.5 * |y - t/sigma|^2, Adam (beta1
+  0.9, beta2 0.999, eps 1e-8, bias-corrected).
 
 Parameters are one flat vector: W1 (128 x din, row-major), b1, W2, b2, W3, b3,
-W4 (nb x 128), b4.
+W4 (nb x 128), b4, sigma.
 """
 import numpy as np
 
 WIDTH = 128
 
 
+NFEAT = 8
+
+
 def din_of(nb):
-    return 4 * nb + 4
+    return 4 * nb + NFEAT
 
 
 def sizes(nb):
@@ -32,7 +37,7 @@ def sizes(nb):
 
 
 def n_params(nb):
-    return int(sum(np.prod(s) for s in sizes(nb)))
+    return int(sum(np.prod(s) for s in sizes(nb))) + 1     # + sigma
 
 
 def unpack(theta, nb):
@@ -45,8 +50,8 @@ def unpack(theta, nb):
 
 
 def features(r, nbr, nb, coef):
-    """r [ne*nb]; nbr [ne,3] (-1 = none); coef [ne,4] = (eps, bx, by, alpha).
-    Returns X [ne, din] and s [ne]."""
+    """r [ne*nb]; nbr [ne,3] (-1 = none); coef [ne,8] = (eps, bx, by, alpha,
+    J00, J01, J10, J11 scaled by 1/sqrt(det J)).  Returns X [ne, din], s [ne]."""
     ne = nbr.shape[0]
     R = r.reshape(ne, nb)
     P = np.zeros((ne, 4, nb))
@@ -61,6 +66,7 @@ def features(r, nbr, nb, coef):
     X[:, 4 * nb + 1] = coef[:, 1]
     X[:, 4 * nb + 2] = coef[:, 2]
     X[:, 4 * nb + 3] = coef[:, 3]
+    X[:, 4 * nb + 4:4 * nb + 8] = coef[:, 4:8]
     return X, s
 
 
@@ -94,7 +100,7 @@ def loss_and_grad(theta, X, T, nb):
     d1 = (d2 @ W2) * (a1 > 0)
     gW1 = d1.T @ X
     gb1 = d1.sum(0)
-    g = np.concatenate([a.ravel() for a in (gW1, gb1, gW2, gb2, gW3, gb3, gW4, gb4)])
+    g = np.concatenate([a.ravel() for a in (gW1, gb1, gW2, gb2, gW3, gb3, gW4, gb4)] + [np.zeros(1)])
     return loss, g
 
 
@@ -105,6 +111,13 @@ def adam_step(theta, g, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
     mh = m / (1 - b1 ** step)
     vh = v / (1 - b2 ** step)
     return theta - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def bf16_round_params(theta):
+    """bf16-rounded weights with the f32 output scale left as is."""
+    out = bf16_round(theta)
+    out[-1] = np.float32(theta[-1])
+    return out
 
 
 def bf16_round(a):

@@ -29,11 +29,14 @@
 
 #include "dg_kernels.cuh"
 
+template <typename TV>
+dg_status dg_mlp_correct(dg_handle* h, const TV* r, TV* z, DevCtl ctl, VecSel sr, VecSel sz, const int* iuse);
+
 struct BState {
     int its, converged, done, reorth, pending, nonfinite, cycles, j;
     unsigned int arrive;
-    int m, max_it, pad_;
-    double tol, bnorm, relres, wn2_before;
+    int m, max_it, stalls;
+    double tol, bnorm, relres, wn2_before, prevres;
     double scale[DG_MAXM + 2];
     double hcol[DG_MAXM + 2];
     double coef[DG_MAXM + 2];
@@ -66,6 +69,7 @@ struct BatchDev {
     double* partials;     // [nit][DG_MAXM+2]
     int* jglob;           // current Arnoldi step of all active instances
     int* counters;        // [4]: active instances, nonfinite, outer-active
+    int* iuse;            // [nI] learned correction still on (flexible mode), else NULL
     int nI, nit;
 };
 
@@ -164,6 +168,8 @@ __global__ void __launch_bounds__(256) k_b_init(const TV* __restrict__ F, TV* __
                 act = 0;
             }
             st->done = act ? 0 : 1;
+            st->prevres = 1.0;
+            st->stalls = 0;
             B.iactive[inst] = act;
             B.ipending[inst] = 0;
             for (int i = 0; i <= m; ++i) st->g[i] = 0.0;
@@ -323,7 +329,7 @@ __global__ void k_b_step(BatchDev B) {
 }
 
 // y = H^-1 g per pending instance (one block per instance)
-__global__ void __launch_bounds__(256) k_b_solve(BatchDev B) {
+__global__ void __launch_bounds__(256) k_b_solve(BatchDev B, int flexible) {
     const int inst = blockIdx.x;
     if (!B.ipending[inst]) return;
     BState* st = B.bst + inst;
@@ -339,7 +345,7 @@ __global__ void __launch_bounds__(256) k_b_solve(BatchDev B) {
         for (int l = threadIdx.x; l < i; l += blockDim.x) gs[l] -= st->H[(long)i * LD + l] * yi;
         if (threadIdx.x == 0) {
             st->y[i] = yi;
-            st->coef[i] = yi * st->scale[i];
+            st->coef[i] = flexible ? yi : yi * st->scale[i];
         }
         __syncthreads();
     }
@@ -412,6 +418,13 @@ __global__ void __launch_bounds__(256) k_b_resid(const TV* __restrict__ F, const
             }
             st->done = act ? 0 : 1;
             B.iactive[inst] = act;
+            if (B.iuse && B.iuse[inst]) {
+                // learned preconditioner fallback per instance: two cycles in a
+                // row with less than 10% residual reduction switch it off
+                st->stalls = st->relres > 0.9 * st->prevres ? st->stalls + 1 : 0;
+                if (st->stalls >= 2) B.iuse[inst] = 0;
+            }
+            st->prevres = st->relres;
             if (act) {
                 for (int i = 0; i <= st->m; ++i) st->g[i] = 0.0;
                 st->g[0] = beta;
@@ -509,7 +522,7 @@ __global__ void __launch_bounds__(256) k_bo_update(double* __restrict__ x, const
 // ---------------------------------------------------------------------------
 struct BatchHostLayout {
     size_t off_bst, off_bo, off_iactive, off_ipending, off_ipart, off_iouter, off_iscale, off_item_inst, off_item_lo,
-        off_item_hi, off_iilo, off_iihi, off_partials, off_jglob, off_counters, total;
+        off_item_hi, off_iilo, off_iihi, off_partials, off_jglob, off_counters, off_iuse, total;
 };
 
 static BatchHostLayout batch_layout(int nI, int nit) {
@@ -535,6 +548,7 @@ static BatchHostLayout batch_layout(int nI, int nit) {
     L.off_partials = take(sizeof(double) * (size_t)nit * (DG_MAXM + 2));
     L.off_jglob = take(sizeof(int));
     L.off_counters = take(sizeof(int) * 4);
+    L.off_iuse = take(sizeof(int) * nI);
     L.total = o;
     return L;
 }
@@ -629,6 +643,7 @@ static dg_status batch_tables(dg_handle* h, int nb, int tile, BatchDev& B, Batch
     B.partials = (double*)(base + L.off_partials);
     B.jglob = (int*)(base + L.off_jglob);
     B.counters = (int*)(base + L.off_counters);
+    B.iuse = nullptr;
     B.nI = h->b_n;
     B.nit = nit;
     DG_CK(h, cudaMemsetAsync(h->b_dev, 0, L.total, h->stream));
@@ -646,6 +661,7 @@ struct BatchRun {
     void* V;
     void* Z;
     void* R;
+    void* Zb;     // [(m+1)][ld] preconditioned directions (flexible)
     long ld;
     int m;
     int gsm, gx;
@@ -657,16 +673,28 @@ static int b_enqueue_cycle(dg_handle* h, const BatchRun& Rn, const TA* A, const 
     TV* V = (TV*)Rn.V;
     TV* Z = (TV*)Rn.Z;
     TV* R = (TV*)Rn.R;
+    TV* Zb = (TV*)Rn.Zb;
+    const bool flex = B.iuse != nullptr;
     const unsigned ge = (unsigned)((h->ne + 255) / 256);
     DevCtl step{nullptr, nullptr, h->b_inst, B.iactive, B.iscale};
     DevCtl pend{nullptr, nullptr, h->b_inst, B.ipending, nullptr};
     VecSel vj{B.jglob, 0, Rn.ld}, vj1{B.jglob, 1, Rn.ld};
     int n = 0;
     for (int it = 0; it < Rn.m; ++it) {
-        k_bj_apply<NB, TB, TV, TV><<<ge, 256, 0, h->stream>>>(Binv, V, Z, h->ne, step, vj, vsel_fixed());
-        k_apply<NB, TA, TV, TV><<<ge, 256, 0, h->stream>>>(A, h->nbr, Z, V, h->ne, DevCtl{nullptr, nullptr, h->b_inst,
-                                                                                        B.iactive, nullptr},
-                                                          vsel_fixed(), vj1);
+        if (flex) {
+            VecSel zj{B.jglob, 0, Rn.ld};
+            k_bj_apply<NB, TB, TV, TV><<<ge, 256, 0, h->stream>>>(Binv, V, Zb, h->ne, step, vj, zj);
+            dg_mlp_correct<TV>(h, V, Zb, step, vj, zj, B.iuse);
+            k_apply<NB, TA, TV, TV><<<ge, 256, 0, h->stream>>>(A, h->nbr, Zb, V, h->ne,
+                                                              DevCtl{nullptr, nullptr, h->b_inst, B.iactive, nullptr},
+                                                              zj, vj1);
+            ++n;
+        } else {
+            k_bj_apply<NB, TB, TV, TV><<<ge, 256, 0, h->stream>>>(Binv, V, Z, h->ne, step, vj, vsel_fixed());
+            k_apply<NB, TA, TV, TV><<<ge, 256, 0, h->stream>>>(A, h->nbr, Z, V, h->ne,
+                                                              DevCtl{nullptr, nullptr, h->b_inst, B.iactive, nullptr},
+                                                              vsel_fixed(), vj1);
+        }
         for (int pass = 1; pass <= 2; ++pass) {
             k_b_dots<TV><<<Rn.gsm, dim3(B_TX, B_TY), 0, h->stream>>>(V, Rn.ld, B, pass);
             k_b_update<TV><<<Rn.gx, 256, 0, h->stream>>>(V, Rn.ld, B, pass);
@@ -674,10 +702,16 @@ static int b_enqueue_cycle(dg_handle* h, const BatchRun& Rn, const TA* A, const 
         k_b_step<<<1, 32, 0, h->stream>>>(B);
         n += 7;
     }
-    k_b_solve<<<B.nI, 256, 0, h->stream>>>(B);
-    k_b_combine<TV><<<Rn.gx, 256, 0, h->stream>>>(V, Rn.ld, B, R);
-    k_bj_apply<NB, TB, TV, TV><<<ge, 256, 0, h->stream>>>(Binv, R, Z, h->ne, pend, vsel_fixed(), vsel_fixed());
-    k_b_axpy<TV><<<Rn.gx, 256, 0, h->stream>>>(x, Z, B);
+    k_b_solve<<<B.nI, 256, 0, h->stream>>>(B, flex ? 1 : 0);
+    if (flex) {
+        k_b_combine<TV><<<Rn.gx, 256, 0, h->stream>>>(Zb, Rn.ld, B, R);
+        k_b_axpy<TV><<<Rn.gx, 256, 0, h->stream>>>(x, R, B);
+        --n;
+    } else {
+        k_b_combine<TV><<<Rn.gx, 256, 0, h->stream>>>(V, Rn.ld, B, R);
+        k_bj_apply<NB, TB, TV, TV><<<ge, 256, 0, h->stream>>>(Binv, R, Z, h->ne, pend, vsel_fixed(), vsel_fixed());
+        k_b_axpy<TV><<<Rn.gx, 256, 0, h->stream>>>(x, Z, B);
+    }
     k_apply<NB, TA, TV, TV><<<ge, 256, 0, h->stream>>>(A, h->nbr, x, R, h->ne, pend, vsel_fixed(), vsel_fixed());
     k_b_resid<TV><<<Rn.gx, 256, 0, h->stream>>>(F, R, V, B);
     k_b_cycle_end<<<1, 1024, 0, h->stream>>>(B);
@@ -694,7 +728,9 @@ static dg_status b_gmres(dg_handle* h, BatchRun& Rn, const TA* A, const TB* Binv
     h->nlaunch += 2;
     DG_LAUNCH_CK(h);
     const uintptr_t key[8] = {(uintptr_t)A, (uintptr_t)Binv, (uintptr_t)F, (uintptr_t)x, (uintptr_t)Rn.V,
-                              (uintptr_t)B.bst, (uintptr_t)Rn.m | ((uintptr_t)sizeof(TV) << 16), (uintptr_t)h->stream};
+                              (uintptr_t)B.bst,
+                              (uintptr_t)Rn.m | ((uintptr_t)sizeof(TV) << 16) | ((uintptr_t)(B.iuse != nullptr) << 24),
+                              (uintptr_t)h->stream};
     if (h->b_graph && memcmp(key, h->b_key, sizeof(key)) != 0) {
         cudaGraphExecDestroy(h->b_graph);
         h->b_graph = nullptr;
@@ -742,7 +778,11 @@ static dg_status batch_solve_t(dg_handle* h, int inner_dtype, const TA* Alo, con
     const bool f64 = inner_dtype == DG_F64;
     const size_t elem = f64 ? 8 : 4;
     // vectors: V (m+2) x ld, Z, R (ld); refinement: r64, ax (n f64), rin, din (ld f32)
-    const size_t vbytes = ((size_t)(inner_m + 2) * ld + 2 * ld) * elem + (f64 ? 0 : (2 * n * 8 + 2 * ld * 4)) + 1024;
+    const bool flex = h->p.precond == DG_PRECOND_MLP;
+    const int mm = f64 ? h->p.gmres_m : inner_m;
+    const size_t zbytes = flex ? (size_t)(mm + 1) * ld * elem : 0;
+    const size_t vbytes = ((size_t)(inner_m + 2) * ld + 2 * ld) * elem + (f64 ? 0 : (2 * n * 8 + 2 * ld * 4)) +
+                          zbytes + 1024;
     if ((s = dg_ensure(h, &h->mx_buf, &h->cap_mx, vbytes)) != DG_OK) return s;
     char* vb = (char*)h->mx_buf;
     Rn.V = vb;
@@ -752,7 +792,16 @@ static dg_status batch_solve_t(dg_handle* h, int inner_dtype, const TA* Alo, con
     double* ax = r64 + n;
     float* rin = (float*)(ax + n);
     float* din = rin + ld;
+    Rn.Zb = f64 ? (void*)r64 : (void*)(din + ld);
     DG_CK(h, cudaMemsetAsync(h->mx_buf, 0, vbytes, h->stream));
+    if (flex) {
+        Rn.B.iuse = (int*)((char*)h->b_dev + L.off_iuse);
+        std::vector<int> ones(h->b_n, 1);
+        DG_CK(h, cudaMemcpyAsync(Rn.B.iuse, ones.data(), sizeof(int) * h->b_n, cudaMemcpyHostToDevice, h->stream));
+        const int one = 1;
+        DG_CK(h, cudaMemcpyAsync(h->mlp.on, &one, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+        DG_CK(h, cudaStreamSynchronize(h->stream));
+    }
     Rn.ld = ld;
     Rn.m = inner_m;
     int sms = 0;
@@ -775,6 +824,9 @@ static dg_status batch_solve_t(dg_handle* h, int inner_dtype, const TA* Alo, con
         DG_CK(h, cudaMemcpyAsync(B.iparticipate, one.data(), sizeof(int) * h->b_n, cudaMemcpyHostToDevice, h->stream));
         s = b_gmres<NB, double, double, double>(h, Rn, Alo, Binv, F, x, h->p.tol, h->p.max_it, cnt);
         if (s != DG_OK) result = s;
+        h->basis = (const double*)Rn.V;
+        h->basis_ld = Rn.ld;
+        h->basis_n = Rn.m + 1;
         (void)r64; (void)ax; (void)rin; (void)din; (void)inner_tol; (void)max_outer;
     } else {
         // f64 refinement around the f32 inner batched GMRES
@@ -833,6 +885,7 @@ static dg_status batch_solve_t(dg_handle* h, int inner_dtype, const TA* Alo, con
 extern "C" dg_status dg_batch_solve(dg_handle* h, int inner_dtype, int inner_m, double inner_tol, int max_outer,
                                     const double* F, double* x, int* its, double* relres, int* status) {
     if (!h || !x) return DG_ERR_INVALID_ARG;
+    h->basis = nullptr;
     if (!h->b_inst_active || h->b_n < 1) return dg_fail(h, DG_ERR_STATE, "no batch set up");
     if (!h->assembled) return dg_fail(h, DG_ERR_STATE, "not assembled");
     if (!h->A64) return dg_fail(h, DG_ERR_STATE, "the f64 blocks are required");
@@ -842,13 +895,15 @@ extern "C" dg_status dg_batch_solve(dg_handle* h, int inner_dtype, int inner_m, 
     if (inner_dtype == DG_BF16 && !h->A16) return dg_fail(h, DG_ERR_STATE, "bf16 blocks not stored");
     if (inner_dtype != DG_F64 && inner_dtype != DG_F32 && inner_dtype != DG_BF16)
         return dg_fail(h, DG_ERR_INVALID_ARG, "inner_dtype");
-    if (h->p.precond == DG_PRECOND_BLOCK_JACOBI && !h->bj_ok) {
+    if (h->p.precond != DG_PRECOND_NONE && !h->bj_ok) {
         dg_status s = dg_precond_setup(h, DG_PRECOND_BLOCK_JACOBI);
         if (s != DG_OK) return s;
     }
+    if (h->p.precond == DG_PRECOND_MLP && (!h->mlp.packed || h->mlp.nb != dg_nb(h->asm_k)))
+        return dg_fail(h, DG_ERR_STATE, "MLP preconditioner: dg_mlp_init / dg_mlp_set_weights for this degree first");
     DG_CK(h, cudaSetDevice(h->device));
     if (!F) F = h->F;
-    const bool pj = h->p.precond == DG_PRECOND_BLOCK_JACOBI;
+    const bool pj = h->p.precond != DG_PRECOND_NONE;
     const int nb = dg_nb(h->asm_k);
 #define DG_BATCH(NBV)                                                                                             \
     if (nb == NBV) {                                                                                              \
@@ -899,6 +954,7 @@ __global__ void k_b_prof_state(BatchDev B, int j) {
 // kept in the handle and returned through *tile.
 extern "C" dg_status dg_batch_autotune(dg_handle* h, int* tile) {
     if (!h || !tile) return DG_ERR_INVALID_ARG;
+    h->basis = nullptr;
     if (!h->b_inst_active || !h->assembled) return dg_fail(h, DG_ERR_STATE, "set up and assemble a batch first");
     DG_CK(h, cudaSetDevice(h->device));
     const int nb = dg_nb(h->asm_k);

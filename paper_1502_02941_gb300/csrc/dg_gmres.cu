@@ -651,12 +651,19 @@ static dg_status gmres_f64(dg_handle* h, const double* F, double* x, dg_solve_in
         const int one = 1;
         DG_CK(h, cudaMemcpyAsync(h->mlp.on, &one, sizeof(int), cudaMemcpyHostToDevice, h->stream));
     }
-    return gmres_run<NB, double, double, double>(h, h->gw[0], h->A64, B, F, x, h->p.gmres_m, h->p.tol,
-                                                 h->p.max_it, info, mlp);
+    const dg_status s = gmres_run<NB, double, double, double>(h, h->gw[0], h->A64, B, F, x, h->p.gmres_m, h->p.tol,
+                                                              h->p.max_it, info, mlp);
+    if (h->gw[0].V) {
+        h->basis = (const double*)h->gw[0].V;
+        h->basis_ld = h->gw[0].ld;
+        h->basis_n = h->gw[0].m + 1;
+    }
+    return s;
 }
 
 extern "C" dg_status dg_gmres_solve(dg_handle* h, const double* F, double* x, dg_solve_info* info) {
     if (!h || !x) return DG_ERR_INVALID_ARG;
+    h->basis = nullptr;
     if (!h->assembled) return dg_fail(h, DG_ERR_STATE, "not assembled");
     if (!h->A64) return dg_fail(h, DG_ERR_STATE, "f64 blocks not stored");
     if (h->p.precond != DG_PRECOND_NONE && !h->bj_ok) {
@@ -786,6 +793,7 @@ static dg_status mixed_run(dg_handle* h, const TA* Alo, const double* F, double*
 extern "C" dg_status dg_mixed_solve(dg_handle* h, int inner_dtype, int inner_m, double inner_tol, int max_outer,
                                     const double* F, double* x, dg_solve_info* info) {
     if (!h || !x) return DG_ERR_INVALID_ARG;
+    h->basis = nullptr;
     if (!h->assembled) return dg_fail(h, DG_ERR_STATE, "not assembled");
     if (!h->A64) return dg_fail(h, DG_ERR_STATE, "the f64 blocks are needed for the outer residual");
     if (inner_dtype != DG_F32 && inner_dtype != DG_BF16) return dg_fail(h, DG_ERR_INVALID_ARG, "inner_dtype");

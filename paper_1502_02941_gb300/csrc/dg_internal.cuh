@@ -53,6 +53,7 @@ struct GmresState;   // device-side solver state (dg_gmres.cu)
 
 #define DG_MLP_WIDTH 128
 #define DG_MLP_NOUTP 16      // output rows of the packed last layer (nb <= 10, zero padded)
+#define DG_MLP_NFEAT 8       // per-element features after the 4 nb residual entries
 
 // Element-local MLP right preconditioner (dg_mlp.cu).
 struct MlpState {
@@ -172,6 +173,12 @@ struct dg_handle {
 
     MlpState mlp;
     bool mlp_fallback = false;     // the last flexible solve switched the MLP off
+    // Krylov basis of the last f64 solve (dg_gmres_solve / dg_batch_solve with
+    // DG_F64): basis_n vectors of leading dimension basis_ld (f64, unnormalised);
+    // cleared when another solve starts
+    const double* basis = nullptr;
+    size_t basis_ld = 0;
+    int basis_n = 0;
 
     // mixed-precision refinement buffers (r64, A x, r32, d32, state)
     void* mx_buf = nullptr;

@@ -6,10 +6,16 @@
 //   x   = [r_K, r_L0, r_L1, r_L2] / s  ++  [log10(eps)/6 + 1, b_x, b_y, alpha]
 //         (zeros for a missing neighbour; b at the element centroid),
 //   y   = W4 relu(W3 relu(W2 relu(W1 x + b1) + b2) + b3) + b4   (width 128),
-//   z_K = (M_BJ^-1 r)_K + s y_K.
-// Training pairs (r, e = A^-1 r) come from the method's own f64 solves
-// (r = F - A x_k, e = x* - x_k); the target is t_K = (e_K - (M_BJ^-1 r)_K)/s
-// and the loss the mean of |y - t|^2 / 2, minimised by Adam.  The f32 master
+//   z_K = A_KK^-1 (r_K + s sigma y_K)      (A_KK^-1: the block-Jacobi inverse).
+// Training pairs come from the method's own f64 solves: the residuals
+// r = F - A x_k of its iterates, each paired with the one-layer-overlap patch
+// correction w (w_K from solving the patch system of K and its face
+// neighbours: the restricted additive Schwarz correction).  The network works
+// in residual space: its target is t_K = (A_KK w_K - r_K)/s (minus the
+// neighbours' coupling terms of the patch solution), so an error in y costs
+// the same in the preconditioned residual whatever the conditioning of A_KK;
+// sigma = RMS of all targets, and the loss is the mean of |y - t/sigma|^2 / 2,
+// minimised by Adam.  The f32 master
 // weights are rounded to bf16 for every forward/backward pass, so the trained
 // network is the one deployed; training runs as f32 GEMMs on CUDA cores,
 // inference as a fused tensor-core kernel (bf16 mma, f32 accumulate) with the
@@ -27,10 +33,10 @@
 // parameter layout
 // ---------------------------------------------------------------------------
 struct MlpOff {
-    long W1, b1, W2, b2, W3, b3, W4, b4, P;
+    long W1, b1, W2, b2, W3, b3, W4, b4, sig, P;
 };
 static MlpOff mlp_off(int nb) {
-    const int din = 4 * nb + 4;
+    const int din = 4 * nb + DG_MLP_NFEAT;
     MlpOff o;
     long p = 0;
     o.W1 = p; p += (long)MW * din;
@@ -41,6 +47,7 @@ static MlpOff mlp_off(int nb) {
     o.b3 = p; p += MW;
     o.W4 = p; p += (long)nb * MW;
     o.b4 = p; p += nb;
+    o.sig = p; p += 1;     // fixed output scale sigma (set from the targets at the start of training)
     o.P = p;
     return o;
 }
@@ -73,13 +80,13 @@ __global__ void k_mlp_init(float* theta, long P, MlpOff o, int din, int nb, unsi
         else if (i >= o.W4 && i < o.b4) bound = 0.1f * sqrtf(3.f / MW);   // small output layer: start near BJ
         const unsigned long long z = mix64(seed ^ (unsigned long long)i * 0x632BE59BD9B4E019ull);
         const float u = (float)((z >> 40) * (1.0 / 16777216.0));   // [0,1)
-        theta[i] = bound * (2.f * u - 1.f);
+        theta[i] = i == o.sig ? 1.f : bound * (2.f * u - 1.f);
     }
 }
 
 __global__ void k_mlp_round(const float* __restrict__ theta, float* __restrict__ wr, long P) {
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (long)gridDim.x * blockDim.x)
-        wr[i] = bf16r(theta[i]);
+        wr[i] = i == P - 1 ? theta[i] : bf16r(theta[i]);   // the last entry is the f32 output scale
 }
 
 // Adam (bias-corrected); refreshes the bf16-rounded working copy.
@@ -93,7 +100,7 @@ __global__ void k_mlp_adam(float* theta, const float* __restrict__ g, float* m, 
         v[i] = vi;
         const float th = theta[i] - lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
         theta[i] = th;
-        wr[i] = bf16r(th);
+        wr[i] = i == P - 1 ? th : bf16r(th);
     }
 }
 
@@ -189,12 +196,14 @@ __global__ void k_mlp_lossd(const float* __restrict__ Y, const float* __restrict
 
 // gather rows idx of X / T into contiguous batches
 __global__ void k_mlp_gather(const float* __restrict__ X, const float* __restrict__ T, int din, int nb, long nrows,
-                             int B, unsigned long long seed, int step, float* __restrict__ Xb, float* __restrict__ Tb) {
+                             int B, unsigned long long seed, int step, float* __restrict__ Xb, float* __restrict__ Tb,
+                             const float* __restrict__ sigma) {
+    const float inv = 1.f / *sigma;
     for (int r = blockIdx.x; r < B; r += gridDim.x) {
         const unsigned long long z = mix64(seed ^ ((unsigned long long)step << 32) ^ (unsigned long long)r);
         const long src = (long)(z % (unsigned long long)nrows);
         for (int c = threadIdx.x; c < din; c += blockDim.x) Xb[(long)r * din + c] = X[src * din + c];
-        for (int c = threadIdx.x; c < nb; c += blockDim.x) Tb[(long)r * nb + c] = T[src * nb + c];
+        for (int c = threadIdx.x; c < nb; c += blockDim.x) Tb[(long)r * nb + c] = T[src * nb + c] * inv;
     }
 }
 
@@ -233,10 +242,26 @@ static void mlp_loss_grad(cudaStream_t st, const MlpState& S, const MlpOff& o, c
 
 static size_t mlp_ws_floats(int B) { return (size_t)B * (5 * MW + 32); }
 
+__global__ void k_mlp_rms(const float* __restrict__ T, long cnt, double* acc) {
+    __shared__ double sh[32];
+    double a = 0.0;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (long)gridDim.x * blockDim.x)
+        a += (double)T[i] * (double)T[i];
+    a = dg_block_sum(a, sh);
+    if (threadIdx.x == 0) atomicAdd(acc, a);
+}
+__global__ void k_mlp_set_sigma(double* acc, long cnt, float* sig, float* sigr) {
+    const float v = (float)sqrt(*acc / (double)cnt);
+    *sig = v > 0.f ? v : 1.f;
+    *sigr = *sig;
+    *acc = 0.0;
+}
+
 // ---------------------------------------------------------------------------
 // features and training rows
 // ---------------------------------------------------------------------------
-// coefficient features of element K: eps, bx, by, alpha at the centroid
+// coefficient and shape features of element K: eps, bx, by, alpha at the
+// centroid, and the Jacobian scaled by 1/sqrt(det J)
 __device__ __forceinline__ void elem_coef(int K, int ne, const double* __restrict__ geo, const int* inst,
                                           const double* icoef, const double* scoef, float* out) {
     const double* c = inst ? icoef + (size_t)DG_ICOEF * inst[K] : scoef;
@@ -246,6 +271,11 @@ __device__ __forceinline__ void elem_coef(int K, int ne, const double* __restric
     out[1] = (float)(c[2] + c[3] * x + c[4] * y);
     out[2] = (float)(c[5] + c[6] * x + c[7] * y);
     out[3] = (float)c[1];
+    const double hs = 1.0 / sqrt(geo[G_DET * (size_t)ne + K]);
+    out[4] = (float)(geo[G_J00 * (size_t)ne + K] * hs);
+    out[5] = (float)(geo[G_J01 * (size_t)ne + K] * hs);
+    out[6] = (float)(geo[G_J10 * (size_t)ne + K] * hs);
+    out[7] = (float)(geo[G_J11 * (size_t)ne + K] * hs);
 }
 
 struct CoefSrc {
@@ -255,14 +285,14 @@ struct CoefSrc {
     double scoef[8];
 };
 
-// One training row per element: X = features(r), T = (e - zbj)/s.
+// One training row per element: X = features(r), T = (A_KK w_K - r_K)/s.
 template <int NB>
-__global__ void k_mlp_rows(const double* __restrict__ r, const double* __restrict__ e, const double* __restrict__ zbj,
+__global__ void k_mlp_rows(const double* __restrict__ r, const double* __restrict__ w, const double* __restrict__ A,
                            const int* __restrict__ nbr, int ne, CoefSrc cs, float* __restrict__ X,
                            float* __restrict__ T) {
     const int K = blockIdx.x * blockDim.x + threadIdx.x;
     if (K >= ne) return;
-    constexpr int DIN = 4 * NB + 4;
+    constexpr int DIN = 4 * NB + DG_MLP_NFEAT;
     double p[4][NB];
     double ss = 0.0;
     for (int sl = 0; sl < 4; ++sl) {
@@ -277,7 +307,87 @@ __global__ void k_mlp_rows(const double* __restrict__ r, const double* __restric
     for (int sl = 0; sl < 4; ++sl)
         for (int i = 0; i < NB; ++i) x[sl * NB + i] = (float)(p[sl][i] / s);
     elem_coef(K, ne, cs.geo, cs.inst, cs.icoef, cs.scoef, x + 4 * NB);
-    for (int i = 0; i < NB; ++i) T[(size_t)K * NB + i] = (float)((e[(size_t)K * NB + i] - zbj[(size_t)K * NB + i]) / s);
+    for (int i = 0; i < NB; ++i) {
+        double t = -r[(size_t)K * NB + i];
+        for (int j = 0; j < NB; ++j) t = fma(A[dg_blk_index<double>(K, 0, i * NB + j, NB, 4)], w[(size_t)K * NB + j], t);
+        T[(size_t)K * NB + i] = (float)(t / s);
+    }
+}
+
+// One-layer-overlap patch solve (the restricted additive Schwarz correction):
+// for element K and its face neighbours L_f, solve A_P w = r_P on the patch
+// P = {K, L_0, L_1, L_2} (f64 Gaussian elimination with partial pivoting) and
+// keep w_K.  A_P couples two neighbours only where they share an edge.
+template <int NB>
+__global__ void __launch_bounds__(64) k_patch_solve(const double* __restrict__ A, const int* __restrict__ nbr,
+                                                     const int* __restrict__ nface, const double* __restrict__ r,
+                                                     int ne, double* __restrict__ w) {
+    const int K = blockIdx.x * blockDim.x + threadIdx.x;
+    if (K >= ne) return;
+    constexpr int NP = 4 * NB;
+    double M[NP][NP + 1];
+    int E[4], cnt = 1;
+    int slotK[4];            // slot of K in the row of patch element p (p >= 1)
+    E[0] = K;
+    for (int f = 0; f < 3; ++f) {
+        const int L = nbr[(size_t)f * ne + K];
+        if (L >= 0) {
+            E[cnt] = L;
+            slotK[cnt] = 1 + nface[(size_t)f * ne + K];
+            ++cnt;
+        }
+    }
+    const int n = cnt * NB;
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b <= n; ++b) M[a][b] = 0.0;
+    for (int p = 0; p < cnt; ++p) {
+        for (int q = 0; q < cnt; ++q) {
+            int slot = -1;
+            if (p == q) slot = 0;
+            else if (p == 0) {
+                for (int f = 0; f < 3; ++f)
+                    if (nbr[(size_t)f * ne + K] == E[q]) slot = 1 + f;
+            } else if (q == 0) {
+                slot = slotK[p];
+            } else {
+                for (int f = 0; f < 3; ++f)
+                    if (nbr[(size_t)f * ne + E[p]] == E[q]) slot = 1 + f;
+            }
+            if (slot < 0) continue;
+            for (int i = 0; i < NB; ++i)
+                for (int j = 0; j < NB; ++j)
+                    M[p * NB + i][q * NB + j] = A[dg_blk_index<double>(E[p], slot, i * NB + j, NB, 4)];
+        }
+        for (int i = 0; i < NB; ++i) M[p * NB + i][n] = r[(size_t)E[p] * NB + i];
+    }
+    bool ok = true;
+    for (int c = 0; c < n && ok; ++c) {
+        int pv = c;
+        for (int a = c + 1; a < n; ++a)
+            if (fabs(M[a][c]) > fabs(M[pv][c])) pv = a;
+        if (!(fabs(M[pv][c]) > 0.0)) {
+            ok = false;
+            break;
+        }
+        if (pv != c)
+            for (int b = c; b <= n; ++b) {
+                const double t = M[c][b];
+                M[c][b] = M[pv][b];
+                M[pv][b] = t;
+            }
+        for (int a = c + 1; a < n; ++a) {
+            const double l = M[a][c] / M[c][c];
+            if (l != 0.0)
+                for (int b = c; b <= n; ++b) M[a][b] -= l * M[c][b];
+        }
+    }
+    double x[NP];
+    for (int a = n - 1; a >= 0 && ok; --a) {
+        double t = M[a][n];
+        for (int b = a + 1; b < n; ++b) t -= M[a][b] * x[b];
+        x[a] = t / M[a][a];
+    }
+    for (int i = 0; i < NB; ++i) w[(size_t)K * NB + i] = ok ? x[i] : 0.0;
 }
 
 __global__ void k_sub(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ c, long n) {
@@ -320,13 +430,14 @@ __global__ void k_mlp_pack(const float* __restrict__ theta, MlpOff o, MlpPack pk
         }
         wbf[i] = __float2bfloat16_rn(v);
     }
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 3 * MW + DG_MLP_NOUTP; i += gridDim.x * blockDim.x) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 3 * MW + DG_MLP_NOUTP + 1; i += gridDim.x * blockDim.x) {
         float v;
-        if (i < MW) v = theta[o.b1 + i];
-        else if (i < 2 * MW) v = theta[o.b2 + i - MW];
-        else if (i < 3 * MW) v = theta[o.b3 + i - 2 * MW];
-        else v = (i - 3 * MW) < nb ? theta[o.b4 + i - 3 * MW] : 0.f;
-        bias[i] = bf16r(v);
+        if (i < MW) v = bf16r(theta[o.b1 + i]);
+        else if (i < 2 * MW) v = bf16r(theta[o.b2 + i - MW]);
+        else if (i < 3 * MW) v = bf16r(theta[o.b3 + i - 2 * MW]);
+        else if (i < 3 * MW + DG_MLP_NOUTP) v = (i - 3 * MW) < nb ? bf16r(theta[o.b4 + i - 3 * MW]) : 0.f;
+        else v = theta[o.sig];   // the output scale stays f32
+        bias[i] = v;
     }
 }
 
@@ -400,9 +511,11 @@ struct MlpRun {
     CoefSrc cs;
     const int* on;            // global enable flag (NULL = on)
     const int* iuse;          // per-instance enable flags (batch) or NULL
+    const double* B64;        // block-Jacobi inverses A_KK^-1 (f64 vectors)
+    const float* B32;         // (f32 vectors)
 };
 
-// z_K += scale * s_K * y_K for every element (r, z vectors of type TV, selected
+// z_K += A_KK^-1 (scale * s_K * sigma * y_K) for every element (r, z vectors of type TV, selected
 // through the solver control exactly like the block-Jacobi apply).  Also used
 // with Xin != NULL: y for precomputed feature rows (parity tests).
 template <int NB, typename TV>
@@ -413,11 +526,11 @@ __global__ void __launch_bounds__(256, 1) k_mlp_apply(const TV* __restrict__ r0p
     if (ctl.active && !*ctl.active) return;
     if (R.on && !*R.on) return;
     extern __shared__ __align__(16) unsigned char smraw[];
-    constexpr int DIN = 4 * NB + 4;
+    constexpr int DIN = 4 * NB + DG_MLP_NFEAT;
     const int dinp = R.pk.dinp;
     __nv_bfloat16* sW = reinterpret_cast<__nv_bfloat16*>(smraw);
     float* sb = reinterpret_cast<float*>(smraw + sizeof(__nv_bfloat16) * R.pk.total);
-    __nv_bfloat16* act = reinterpret_cast<__nv_bfloat16*>(sb + 3 * MW + DG_MLP_NOUTP);
+    __nv_bfloat16* act = reinterpret_cast<__nv_bfloat16*>(sb + 3 * MW + DG_MLP_NOUTP + 4);
     float* ss = reinterpret_cast<float*>(act + MLP_ROWS * MLP_ACT_LD);
     int* sk = reinterpret_cast<int*>(ss + MLP_ROWS);
     // weights and biases once per CTA (persistent grid)
@@ -425,7 +538,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_apply(const TV* __restrict__ r0p
         const uint4* src = reinterpret_cast<const uint4*>(R.wbf);
         uint4* dst = reinterpret_cast<uint4*>(sW);
         for (long i = threadIdx.x; i < R.pk.total / 8; i += blockDim.x) dst[i] = src[i];
-        for (int i = threadIdx.x; i < 3 * MW + DG_MLP_NOUTP; i += blockDim.x) sb[i] = R.bias[i];
+        for (int i = threadIdx.x; i < 3 * MW + DG_MLP_NOUTP + 1; i += blockDim.x) sb[i] = R.bias[i];
     }
     const TV* __restrict__ r = Xin ? nullptr : sel(r0p, sr);
     TV* __restrict__ z = Xin ? nullptr : sel(z0p, sz);
@@ -461,9 +574,9 @@ __global__ void __launch_bounds__(256, 1) k_mlp_apply(const TV* __restrict__ r0p
                 for (int sl = 0; sl < 4; ++sl)
 #pragma unroll
                     for (int i = 0; i < NB; ++i) x[sl * NB + i] = __float2bfloat16_rn((float)(p[sl][i] / sd));
-                float cf[4];
+                float cf[DG_MLP_NFEAT];
                 elem_coef(K, ne, R.cs.geo, R.cs.inst, R.cs.icoef, R.cs.scoef, cf);
-                for (int c = 0; c < 4; ++c) x[4 * NB + c] = __float2bfloat16_rn(cf[c]);
+                for (int c = 0; c < DG_MLP_NFEAT; ++c) x[4 * NB + c] = __float2bfloat16_rn(cf[c]);
                 for (int c = DIN; c < dinp; ++c) x[c] = __float2bfloat16_rn(0.f);
                 double sc = 1.0;
                 if (ctl.inst) sc = ctl.iscale ? ctl.iscale[ctl.inst[K]] : 1.0;
@@ -489,8 +602,10 @@ __global__ void __launch_bounds__(256, 1) k_mlp_apply(const TV* __restrict__ r0p
         warp_store_relu<16>(act, MLP_ACT_LD, r0, sb + 2 * MW, acc);
         float out[2][4];
         warp_layer<2, 8>(act, MLP_ACT_LD, r0, sW + R.pk.W4, MW, out);
-        // ---- z_K += s y_K
+        // ---- u_K = s sigma y_K, staged as f32 in the warp's own activation rows
         const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+        const float sig = sb[3 * MW + DG_MLP_NOUTP];
+        __syncwarp();
 #pragma unroll
         for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
@@ -503,13 +618,34 @@ __global__ void __launch_bounds__(256, 1) k_mlp_apply(const TV* __restrict__ r0p
                     if (K < 0 || col >= NB) continue;
                     const float y = out[nt][2 * hrow + cc] + sb[3 * MW + col];
                     if (Yout) Yout[(size_t)K * NB + col] = y;
-                    else z[(size_t)K * NB + col] = (TV)((double)z[(size_t)K * NB + col] + (double)ss[row] * (double)y);
+                    else reinterpret_cast<float*>(act + row * MLP_ACT_LD)[col] = ss[row] * sig * y;
                 }
+        __syncwarp();
+        // ---- z_K += A_KK^-1 u_K (one lane per row of the warp)
+        if (!Yout && lane < 16) {
+            const int row = r0 + lane;
+            const int K = sk[row];
+            if (K >= 0) {
+                const float* u = reinterpret_cast<const float*>(act + row * MLP_ACT_LD);
+#pragma unroll
+                for (int i = 0; i < NB; ++i) {
+                    double a = 0.0;
+#pragma unroll
+                    for (int j = 0; j < NB; ++j) {
+                        if constexpr (sizeof(TV) == 8)
+                            a = fma(R.B64[dg_blk_index<double>(K, 0, i * NB + j, NB, 1)], (double)u[j], a);
+                        else
+                            a = fma((double)R.B32[dg_blk_index<float>(K, 0, i * NB + j, NB, 1)], (double)u[j], a);
+                    }
+                    z[(size_t)K * NB + i] = (TV)((double)z[(size_t)K * NB + i] + a);
+                }
+            }
+        }
     }
 }
 
 static size_t mlp_smem(const MlpPack& pk) {
-    return sizeof(__nv_bfloat16) * pk.total + sizeof(float) * (3 * MW + DG_MLP_NOUTP) +
+    return sizeof(__nv_bfloat16) * pk.total + sizeof(float) * (3 * MW + DG_MLP_NOUTP + 4) +
            sizeof(__nv_bfloat16) * MLP_ROWS * MLP_ACT_LD + sizeof(float) * MLP_ROWS + sizeof(int) * MLP_ROWS;
 }
 
@@ -527,6 +663,8 @@ static dg_status launch_mlp(dg_handle* h, const TV* r, TV* z, DevCtl ctl, VecSel
     for (int t = 0; t < 8; ++t) R.cs.scoef[t] = S.coef[t];
     R.on = Xin ? nullptr : S.on;
     R.iuse = iuse;
+    R.B64 = h->Binv64;
+    R.B32 = h->Binv32;
     const size_t smem = mlp_smem(R.pk);
     static thread_local int configured[DG_MAXK + 1][2] = {};
     int& cfg = configured[dg_nb(1) == NB ? 1 : (dg_nb(2) == NB ? 2 : 3)][sizeof(TV) == 8 ? 1 : 0];
@@ -539,7 +677,9 @@ static dg_status launch_mlp(dg_handle* h, const TV* r, TV* z, DevCtl ctl, VecSel
     const int ntile = (ne + MLP_ROWS - 1) / MLP_ROWS;
     const int grid = ntile < sms ? ntile : sms;
     k_mlp_apply<NB, TV><<<grid, 256, smem, h->stream>>>(r, z, h->nbr, ne, R, ctl, sr, sz, Xin, Yout);
-    h->nlaunch += 1;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(h->stream, &cap);
+    if (cap == cudaStreamCaptureStatusNone) h->nlaunch += 1;   // captured launches are counted per graph launch
     return DG_OK;
 }
 
@@ -564,7 +704,7 @@ static dg_status mlp_alloc(dg_handle* h, int nb) {
     if (S.nb == nb && S.theta) return DG_OK;
     const MlpOff o = mlp_off(nb);
     S.nb = nb;
-    S.din = 4 * nb + 4;
+    S.din = 4 * nb + DG_MLP_NFEAT;
     S.dinp = (S.din + 15) / 16 * 16;
     S.P = o.P;
     dg_status s;
@@ -572,7 +712,8 @@ static dg_status mlp_alloc(dg_handle* h, int nb) {
         if ((s = dg_realloc(h, (void**)p, sizeof(float) * o.P)) != DG_OK) return s;
     const MlpPack pk = mlp_pack_layout(S.din);
     if ((s = dg_realloc(h, (void**)&S.wbf, sizeof(__nv_bfloat16) * pk.total)) != DG_OK) return s;
-    if ((s = dg_realloc(h, (void**)&S.bias, sizeof(float) * (3 * MW + DG_MLP_NOUTP))) != DG_OK) return s;
+    if ((s = dg_realloc(h, (void**)&S.bias, sizeof(float) * (3 * MW + DG_MLP_NOUTP + 1))) != DG_OK) return s;
+    DG_CK(h, cudaMemsetAsync(S.grad, 0, sizeof(float) * o.P, h->stream));   // the scale entry keeps a zero gradient
     if (!S.on) {
         if ((s = dg_realloc(h, (void**)&S.on, sizeof(int))) != DG_OK) return s;
     }
@@ -645,20 +786,19 @@ extern "C" dg_status dg_mlp_clear_data(dg_handle* h) {
     return DG_OK;
 }
 
-extern "C" dg_status dg_mlp_collect(dg_handle* h, const double* F, const double* xstar, const double* xk) {
-    if (!h || !xstar || !xk) return DG_ERR_INVALID_ARG;
+static dg_status mlp_check_collect(dg_handle* h) {
     if (!h->assembled || !h->A64) return dg_fail(h, DG_ERR_STATE, "assemble with f64 blocks first");
     MlpState& S = h->mlp;
     if (!S.ready || S.nb != dg_nb(h->asm_k)) return dg_fail(h, DG_ERR_STATE, "dg_mlp_init first (same degree)");
-    if (!h->bj_ok) {
-        dg_status s = dg_precond_setup(h, DG_PRECOND_BLOCK_JACOBI);
-        if (s != DG_OK) return s;
-    }
     DG_CK(h, cudaSetDevice(h->device));
-    if (!F) F = h->F;
+    return DG_OK;
+}
+
+// Append one row per element for the residual r (device f64, unnormalised):
+// w = patch-solve correction of r into the scratch vector e, then the rows.
+static dg_status mlp_rows_from(dg_handle* h, const double* r, double* e) {
+    MlpState& S = h->mlp;
     const int nb = S.nb;
-    const long n = (long)h->ne * nb;
-    // grow the row store
     const long need = S.rows + h->ne;
     if (need > S.cap) {
         long cap = S.cap ? S.cap : 65536;
@@ -680,16 +820,12 @@ extern "C" dg_status dg_mlp_collect(dg_handle* h, const double* F, const double*
         S.T = T;
         S.cap = cap;
     }
-    dg_status s = dg_scratch(h, sizeof(double) * 3 * n);
-    if (s != DG_OK) return s;
-    double* r = h->scratch;
-    double* e = r + n;
-    double* zb = e + n;
-    // r = F - A xk, e = x* - xk, zb = M_BJ^-1 r
-    if ((s = dg_launch_apply(h, DG_F64, xk, zb)) != DG_OK) return s;
-    k_sub<<<512, 256, 0, h->stream>>>(F, zb, r, n);
-    k_sub<<<512, 256, 0, h->stream>>>(xstar, xk, e, n);
-    if ((s = dg_launch_bj_apply(h, DG_F64, r, zb, nullptr)) != DG_OK) return s;
+    const unsigned gp = (unsigned)((h->ne + 63) / 64);
+    switch (nb) {
+        case 3: k_patch_solve<3><<<gp, 64, 0, h->stream>>>(h->A64, h->nbr, h->nface, r, h->ne, e); break;
+        case 6: k_patch_solve<6><<<gp, 64, 0, h->stream>>>(h->A64, h->nbr, h->nface, r, h->ne, e); break;
+        case 10: k_patch_solve<10><<<gp, 64, 0, h->stream>>>(h->A64, h->nbr, h->nface, r, h->ne, e); break;
+    }
     CoefSrc cs;
     cs.geo = h->geo;
     cs.inst = h->b_inst_active ? h->b_inst : nullptr;
@@ -699,14 +835,45 @@ extern "C" dg_status dg_mlp_collect(dg_handle* h, const double* F, const double*
     float* T = S.T + S.rows * nb;
     const unsigned grid = (unsigned)((h->ne + 127) / 128);
     switch (nb) {
-        case 3: k_mlp_rows<3><<<grid, 128, 0, h->stream>>>(r, e, zb, h->nbr, h->ne, cs, X, T); break;
-        case 6: k_mlp_rows<6><<<grid, 128, 0, h->stream>>>(r, e, zb, h->nbr, h->ne, cs, X, T); break;
-        case 10: k_mlp_rows<10><<<grid, 128, 0, h->stream>>>(r, e, zb, h->nbr, h->ne, cs, X, T); break;
+        case 3: k_mlp_rows<3><<<grid, 128, 0, h->stream>>>(r, e, h->A64, h->nbr, h->ne, cs, X, T); break;
+        case 6: k_mlp_rows<6><<<grid, 128, 0, h->stream>>>(r, e, h->A64, h->nbr, h->ne, cs, X, T); break;
+        case 10: k_mlp_rows<10><<<grid, 128, 0, h->stream>>>(r, e, h->A64, h->nbr, h->ne, cs, X, T); break;
     }
-    h->nlaunch += 3;
+    h->nlaunch += 2;
     DG_LAUNCH_CK(h);
-    DG_CK(h, cudaStreamSynchronize(h->stream));
     S.rows += h->ne;
+    return DG_OK;
+}
+
+extern "C" dg_status dg_mlp_collect(dg_handle* h, const double* F, const double* xk) {
+    if (!h || !xk) return DG_ERR_INVALID_ARG;
+    dg_status s = mlp_check_collect(h);
+    if (s != DG_OK) return s;
+    if (!F) F = h->F;
+    const long n = (long)h->ne * h->mlp.nb;
+    if ((s = dg_scratch(h, sizeof(double) * 2 * n)) != DG_OK) return s;
+    double* r = h->scratch;
+    double* e = r + n;
+    // r = F - A xk (A xk staged in e)
+    if ((s = dg_launch_apply(h, DG_F64, xk, e)) != DG_OK) return s;
+    k_sub<<<512, 256, 0, h->stream>>>(F, e, r, n);
+    h->nlaunch += 1;
+    if ((s = mlp_rows_from(h, r, e)) != DG_OK) return s;
+    DG_CK(h, cudaStreamSynchronize(h->stream));
+    return DG_OK;
+}
+
+extern "C" dg_status dg_mlp_collect_basis(dg_handle* h, int nvec) {
+    if (!h || nvec < 1) return DG_ERR_INVALID_ARG;
+    dg_status s = mlp_check_collect(h);
+    if (s != DG_OK) return s;
+    if (!h->basis) return dg_fail(h, DG_ERR_STATE, "no Krylov basis: run an f64 solve first");
+    if (nvec > h->basis_n) return dg_fail(h, DG_ERR_INVALID_ARG, "nvec exceeds the basis size (gmres_m + 1)");
+    const long n = (long)h->ne * h->mlp.nb;
+    if ((s = dg_scratch(h, sizeof(double) * n)) != DG_OK) return s;
+    for (int j = 0; j < nvec; ++j)
+        if ((s = mlp_rows_from(h, h->basis + (size_t)j * h->basis_ld, h->scratch)) != DG_OK) return s;
+    DG_CK(h, cudaStreamSynchronize(h->stream));
     return DG_OK;
 }
 
@@ -740,8 +907,16 @@ extern "C" dg_status dg_mlp_train(dg_handle* h, int steps, int batch_rows, float
     double* lossd = reinterpret_cast<double*>(Tb + (size_t)batch_rows * S.nb + 2);
     lossd = reinterpret_cast<double*>(((uintptr_t)lossd + 7) & ~(uintptr_t)7);
     std::vector<double> hl(steps);
+    DG_CK(h, cudaMemsetAsync(lossd, 0, sizeof(double), h->stream));
+    if (S.step == 0) {
+        // output scale sigma = RMS of the collected targets (kept fixed afterwards)
+        k_mlp_rms<<<256, 256, 0, h->stream>>>(S.T, S.rows * S.nb, lossd);
+        k_mlp_set_sigma<<<1, 1, 0, h->stream>>>(lossd, S.rows * S.nb, S.theta + o.sig, S.wr + o.sig);
+        h->nlaunch += 2;
+    }
     for (int it = 0; it < steps; ++it) {
-        k_mlp_gather<<<256, 64, 0, h->stream>>>(S.X, S.T, S.din, S.nb, S.rows, batch_rows, seed, S.step + it, Xb, Tb);
+        k_mlp_gather<<<256, 64, 0, h->stream>>>(S.X, S.T, S.din, S.nb, S.rows, batch_rows, seed, S.step + it, Xb, Tb,
+                                                S.theta + o.sig);
         DG_CK(h, cudaMemsetAsync(lossd, 0, sizeof(double), h->stream));
         mlp_loss_grad(h->stream, S, o, Xb, Tb, batch_rows, ws, S.grad, lossd);
         ++S.step;

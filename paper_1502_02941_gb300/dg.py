@@ -101,7 +101,8 @@ _SIGS = {
     "dg_mlp_init": (ctypes.c_int, [c_void_p, ctypes.c_uint64]),
     "dg_mlp_set_weights": (ctypes.c_int, [c_void_p, c_void_p, c_int64]),
     "dg_mlp_get_weights": (ctypes.c_int, [c_void_p, c_void_p, c_int64]),
-    "dg_mlp_collect": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "dg_mlp_collect": (ctypes.c_int, [c_void_p, c_void_p, c_void_p]),
+    "dg_mlp_collect_basis": (ctypes.c_int, [c_void_p, ctypes.c_int]),
     "dg_mlp_num_rows": (ctypes.c_int, [c_void_p, ctypes.POINTER(c_int64)]),
     "dg_mlp_get_rows": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_int64]),
     "dg_mlp_clear_data": (ctypes.c_int, [c_void_p]),
@@ -347,8 +348,12 @@ def dg_mlp_get_weights(h, n):
     return s, out
 
 
-def dg_mlp_collect(h, F, xstar, xk):
-    return load().dg_mlp_collect(h, _ptr(F), _ptr(xstar), _ptr(xk))
+def dg_mlp_collect(h, F, xk):
+    return load().dg_mlp_collect(h, _ptr(F), _ptr(xk))
+
+
+def dg_mlp_collect_basis(h, nvec):
+    return load().dg_mlp_collect_basis(h, int(nvec))
 
 
 def dg_mlp_num_rows(h):
@@ -588,8 +593,11 @@ class DG:
         self.check(s)
         return th
 
-    def mlp_collect(self, xstar, xk, F=None):
-        self.check(dg_mlp_collect(self.h, F, xstar, xk))
+    def mlp_collect(self, xk, F=None):
+        self.check(dg_mlp_collect(self.h, F, xk))
+
+    def mlp_collect_basis(self, nvec):
+        self.check(dg_mlp_collect_basis(self.h, nvec))
 
     def mlp_rows(self):
         s, n = dg_mlp_num_rows(self.h)

@@ -1,0 +1,86 @@
+"""Training and evaluation driver of the learned preconditioner on batches of
+the learned workload (64x64 split squares, P2, batched-workload coefficients).
+
+Training residuals come from the method's own f64 block-Jacobi GMRES solves of
+the training batch: r = F - A x_k for the iterates x_k after k steps, and the
+Krylov basis vectors of those solves (the vectors the preconditioner is applied
+to inside GMRES); each is paired (inside the library) with its one-layer-overlap
+patch correction.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import dg as D
+from . import problem
+from . import workloads as W
+
+TRAIN_CONFIG_ID = 5
+
+
+def make_batch(h: D.DG, n_inst: int, N: int, first: int = 0, k: int = 2, store=D.DG_STORE_F64, **params):
+    """Instances first .. first+n_inst-1 of the learned workload's draw."""
+    cfgs, i = [], first
+    while len(cfgs) < n_inst:
+        c = W.random_instance(TRAIN_CONFIG_ID, i, N_fixed=N, k_fixed=k)
+        i += 1
+        cfgs.append(c)
+    ma, starts = W.concat_meshes([W.structured_mesh(c.N) for c in cfgs])
+    coeffs = np.array([[c.problem.eps, c.problem.alpha, *c.problem.b] for c in cfgs])
+    problem.setup_batch(h, cfgs, ma, starts, coeffs, store=store, **params)
+    h.precond_setup()
+    return cfgs, ma, starts
+
+
+def collect(h: D.DG, snapshots=(10, 30, 60, 100, 200, 400), basis_at=(40, 90, 240), nvec=30, tol=1e-10,
+            max_it=20000):
+    """Solve the current batch with block-Jacobi GMRES and record one training
+    row per element for the zero iterate and each snapshot iterate, and for
+    the first nvec Krylov basis vectors of the restart cycle running after
+    each count in basis_at."""
+    h.set_params(precond=D.DG_PRECOND_BLOCK_JACOBI, tol=tol, max_it=max_it)
+    xstar, its, rr, st = h.batch_solve(D.DG_F64, raise_on_nonconv=False)
+    h.mlp_collect(h.torch.zeros_like(xstar))
+    for k in snapshots:
+        h.set_params(max_it=k)
+        xk, _, _, _ = h.batch_solve(D.DG_F64, raise_on_nonconv=False)
+        h.mlp_collect(xk)
+    for k in basis_at:
+        h.set_params(max_it=k)
+        h.batch_solve(D.DG_F64, raise_on_nonconv=False)
+        h.mlp_collect_basis(min(nvec, h.params.gmres_m + 1))
+    h.set_params(max_it=max_it)
+    return its, rr, st
+
+
+SCHEDULE = ((1e-3, 0.5), (3e-4, 0.3), (1e-4, 0.2))   # (learning rate, share of the steps)
+
+
+def train(h: D.DG, steps=12000, batch_rows=8192, seed=0, schedule=SCHEDULE):
+    """Adam over the collected rows with a stepwise learning-rate decay."""
+    t0 = time.perf_counter()
+    losses = []
+    for i, (lr, share) in enumerate(schedule):
+        n = max(1, int(round(steps * share)))
+        losses.append(h.mlp_train(n, batch_rows=batch_rows, lr=lr, seed=seed + 7919 * i))
+    return np.concatenate(losses), time.perf_counter() - t0
+
+
+def evaluate(h: D.DG, max_it=20000, tol=1e-10):
+    """Batched f64 solves of the current batch with block Jacobi and with the
+    learned preconditioner: per-instance iterations, relres, wall time."""
+    import torch
+    out = {}
+    for name, pc in (("bj", D.DG_PRECOND_BLOCK_JACOBI), ("mlp", D.DG_PRECOND_MLP)):
+        h.set_params(precond=pc, tol=tol, max_it=max_it)
+        h.batch_solve(D.DG_F64, raise_on_nonconv=False)          # warm-up (graph capture)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, its, rr, st = h.batch_solve(D.DG_F64, raise_on_nonconv=False)
+        torch.cuda.synchronize()
+        out[name] = {"seconds": time.perf_counter() - t0, "its": its.copy(), "relres": rr.copy(),
+                     "converged": int((st == 0).sum())}
+    h.set_params(precond=D.DG_PRECOND_BLOCK_JACOBI)
+    return out

@@ -434,7 +434,8 @@ def test_mlp_gradient_matches_finite_differences():
     X = rng.standard_normal((7, M.din_of(nb)))
     T = rng.standard_normal((7, nb))
     loss, g = M.loss_and_grad(theta, X, T, nb)
-    idx = rng.choice(theta.size, 40, replace=False)
+    assert g[-1] == 0.0     # the output scale is not trained
+    idx = rng.choice(theta.size - 1, 40, replace=False)
     h = 1e-6
     for i in idx:
         tp, tm = theta.copy(), theta.copy()
@@ -457,7 +458,7 @@ def test_mlp_features_scale_invariant():
     rng = np.random.default_rng(1)
     nbr = np.array([[1, -1, 2], [0, 2, -1], [1, 0, -1]])
     r = rng.standard_normal(9)
-    coef = np.array([[1e-3, 0.3, -0.2, 0.5]] * 3)
+    coef = np.array([[1e-3, 0.3, -0.2, 0.5, 1.0, 0.0, 0.0, 1.0]] * 3)
     X1, s1 = M.features(r, nbr, 3, coef)
     X2, s2 = M.features(7.5 * r, nbr, 3, coef)
     np.testing.assert_allclose(X1, X2, rtol=1e-13)
