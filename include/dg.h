@@ -284,7 +284,9 @@ dg_status dg_gmres_solve(dg_handle* h, const double* F, double* x, dg_solve_info
  * approximately with restarted GMRES(inner_m) on f32 vectors, using the f32
  * (inner_dtype DG_F32) or bf16 (DG_BF16) block copy with f32 accumulation and
  * the block-Jacobi inverses (computed in f64, applied in f32), to relative
- * residual inner_tol; dot products accumulate in f64 beyond per-thread
+ * residual inner_tol or for at most 8 restart cycles (8 inner_m steps: past
+ * that the f32 iteration sits at its accuracy floor and a fresh f64 residual
+ * serves better); dot products accumulate in f64 beyond per-thread
  * compensated f32 partial sums, Hessenberg/Givens in f64.  Then x += ||r|| d in
  * f64.  Needs DG_STORE_F64 and the inner copy in params.store.
  *   inner_m   1..64;  inner_tol in (0,1);  max_outer >= 1 corrections

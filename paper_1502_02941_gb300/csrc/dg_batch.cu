@@ -850,7 +850,9 @@ static dg_status batch_solve_t(dg_handle* h, int inner_dtype, const TA* Alo, con
             if (cnt[2] == 0 || outer >= max_outer) break;
             k_bo_scale<<<Rn.gx, 256, 0, h->stream>>>(r64, rin, B);
             h->nlaunch += 1;
-            s = b_gmres<NB, TA, TB, float>(h, Rn, Alo, Binv, rin, din, inner_tol, h->p.max_it, cnt);
+            // inner solves stop at inner_tol or after DG_INNER_CYCLES restart cycles
+            s = b_gmres<NB, TA, TB, float>(h, Rn, Alo, Binv, rin, din, inner_tol,
+                                           std::min(h->p.max_it, DG_INNER_CYCLES * inner_m), cnt);
             if (s != DG_OK) {
                 result = s;
                 break;

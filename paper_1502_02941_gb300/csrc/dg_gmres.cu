@@ -22,6 +22,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
+
 #include "dg_kernels.cuh"
 
 template <typename TV>
@@ -769,8 +771,11 @@ static dg_status mixed_run(dg_handle* h, const TA* Alo, const double* F, double*
         h->nlaunch += 1;
         DG_LAUNCH_CK(h);
         dg_solve_info in{};
-        s = gmres_run<NB, TA, float, float>(h, h->gw[1], Alo, B32, r32, d32, inner_m, inner_tol,
-                                             h->p.max_it - inner_total, &in);
+        // each inner solve stops at inner_tol or after DG_INNER_CYCLES restart
+        // cycles: past that the low-precision GMRES is at its accuracy floor
+        // and a fresh f64 residual serves better than more inner steps
+        const int cap = std::min(h->p.max_it - inner_total, DG_INNER_CYCLES * inner_m);
+        s = gmres_run<NB, TA, float, float>(h, h->gw[1], Alo, B32, r32, d32, inner_m, inner_tol, cap, &in);
         if (s != DG_OK && s != DG_NOT_CONVERGED) return s;
         inner_total += in.iterations;
         k_mx_update<<<gx, 256, 0, h->stream>>>(x, d32, n, ms);

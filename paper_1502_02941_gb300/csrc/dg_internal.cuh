@@ -51,6 +51,7 @@ struct TabLayout {
 
 struct GmresState;   // device-side solver state (dg_gmres.cu)
 
+#define DG_INNER_CYCLES 8    // restart cycles per inner solve of the mixed-precision refinement
 #define DG_MLP_WIDTH 128
 #define DG_MLP_NOUTP 16      // output rows of the packed last layer (nb <= 10, zero padded)
 #define DG_MLP_NFEAT 8       // per-element features after the 4 nb residual entries
