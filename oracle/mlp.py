@@ -113,6 +113,41 @@ def adam_step(theta, g, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
     return theta - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
+def patch_correction(Ablk, nbr, r, nb):
+    """One-layer-overlap patch correction w (the restricted additive Schwarz
+    correction that the training targets are built from): for each element K,
+    solve A_P w_P = r_P on the patch P = {K and its face neighbours} and keep
+    w_K.  Ablk [ne,4,nb,nb]: slot 0 the diagonal block, slot 1+f the block
+    coupling K to nbr[K,f]; nbr [ne,3] (-1 = no neighbour).  Dense numpy solve
+    per patch."""
+    ne = Ablk.shape[0]
+    R = np.asarray(r, dtype=np.float64).reshape(ne, nb)
+    w = np.zeros((ne, nb))
+    for K in range(ne):
+        E = [K] + [int(L) for L in nbr[K] if L >= 0]
+        n = len(E) * nb
+        AP = np.zeros((n, n))
+        for p, Ep in enumerate(E):
+            for q, Eq in enumerate(E):
+                if p == q:
+                    blk = Ablk[Ep, 0]
+                else:
+                    sl = [f for f in range(3) if nbr[Ep, f] == Eq]
+                    if not sl:
+                        continue
+                    blk = Ablk[Ep, 1 + sl[0]]
+                AP[p * nb:(p + 1) * nb, q * nb:(q + 1) * nb] = blk
+        w[K] = np.linalg.solve(AP, np.concatenate([R[e] for e in E]))[:nb]
+    return w.reshape(-1)
+
+
+def target(Ablk, nbr, r, nb, s):
+    """Training target t_K = (A_KK w_K - r_K) / s_K for the residual r."""
+    ne = Ablk.shape[0]
+    w = patch_correction(Ablk, nbr, r, nb).reshape(ne, nb)
+    return (np.einsum("kij,kj->ki", Ablk[:, 0], w) - np.asarray(r).reshape(ne, nb)) / s[:, None]
+
+
 def bf16_round_params(theta):
     """bf16-rounded weights with the f32 output scale left as is."""
     out = bf16_round(theta)

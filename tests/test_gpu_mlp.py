@@ -74,30 +74,6 @@ def test_tensor_core_forward_matches_oracle(k):
     h.close()
 
 
-def _patch_correction(A, nbr, r, nb):
-    """w_K of the one-layer-overlap patch solve, from the GPU's blocks (numpy)."""
-    ne = A.shape[0]
-    R = r.reshape(ne, nb)
-    w = np.zeros((ne, nb))
-    for K in range(ne):
-        E = [K] + [int(L) for L in nbr[K] if L >= 0]
-        n = len(E) * nb
-        M_ = np.zeros((n, n))
-        rhs = np.concatenate([R[e] for e in E])
-        for p, Ep in enumerate(E):
-            for q, Eq in enumerate(E):
-                if p == q:
-                    blk = A[Ep, 0]
-                else:
-                    sl = [f for f in range(3) if nbr[Ep, f] == Eq]
-                    if not sl:
-                        continue
-                    blk = A[Ep, 1 + sl[0]]
-                M_[p * nb:(p + 1) * nb, q * nb:(q + 1) * nb] = blk
-        w[K] = np.linalg.solve(M_, rhs)[:nb]
-    return w.reshape(-1)
-
-
 def test_feature_rows_match_oracle():
     h, cfg = _handle(2, N=5)
     h.mlp_init(seed=3)
@@ -128,8 +104,7 @@ def test_feature_rows_match_oracle():
     geo_c[:, 3] = p.alpha
     Xo, so = M.features(F, nbr, nb, geo_c)
     np.testing.assert_allclose(X, Xo, rtol=2e-6, atol=2e-6)
-    wp = _patch_correction(A, nbr, F, nb).reshape(info.ne, nb)
-    To = (np.einsum("kij,kj->ki", A[:, 0], wp) - F.reshape(info.ne, nb)) / so[:, None]
+    To = M.target(A, nbr, F, nb, so)
     np.testing.assert_allclose(T, To, rtol=1e-5, atol=1e-5 * np.abs(To).max())
     h.close()
 

@@ -470,6 +470,52 @@ def test_mlp_features_scale_invariant():
     np.testing.assert_allclose(s1[0], np.sqrt((r[0:9] ** 2).sum() / 12))
 
 
+def _four_triangle_system():
+    """A central triangle with one neighbour across each edge (all outer edges
+    Dirichlet), SIPG P1 with convection and reaction: the patch of the centre
+    is the whole mesh."""
+    nodes = np.array([[0, 0], [1, 0], [0.5, 0.8], [0.5, -0.6], [1.2, 0.7], [-0.2, 0.7]], float)
+    elems = np.array([[0, 1, 2], [0, 3, 1], [1, 4, 2], [2, 5, 0]])
+    dirichlet = np.array([[0, 3], [3, 1], [1, 4], [4, 2], [2, 5], [5, 0]])
+    mesh = O.make_mesh(nodes, elems, dirichlet, np.zeros((0, 2), int))
+    k, nb = 1, 3
+    si, kap = O.set_parameter(O.SIPG, k)
+    fq = np.zeros((mesh.ne, (k + 2) ** 2))
+    S = O.assemble(mesh, k, kap, si, 2 * si, 1e-2, 1.0, (1.0, 0, 0, 0.5, 0, 0), fq, None, None, split=False)
+    A = O.to_sparse(mesh, S.A_diag, S.A_off).toarray()
+    nbr = -np.ones((mesh.ne, 3), int)
+    Ablk = np.zeros((mesh.ne, 4, nb, nb))
+    Ablk[:, 0] = S.A_diag
+    for e in range(mesh.ned):
+        Ki, Kj = mesh.edges[e, 2], mesh.edges[e, 3]
+        if Kj < 0:
+            continue
+        for K, L, blk in ((Ki, Kj, S.A_off[e, 0]), (Kj, Ki, S.A_off[e, 1])):
+            f = int(np.argmax(nbr[K] < 0))
+            nbr[K, f] = L
+            Ablk[K, 1 + f] = blk
+    return A, Ablk, nbr, nb
+
+
+def test_patch_correction_is_the_local_solve():
+    """Centre: its patch is the whole mesh, so w_0 = (A^-1 r)_0.  An outer
+    element: its patch is itself and the centre, a 2-block system."""
+    from oracle import mlp as M
+    A, Ablk, nbr, nb = _four_triangle_system()
+    r = np.random.default_rng(5).standard_normal(4 * nb)
+    w = M.patch_correction(Ablk, nbr, r, nb)
+    np.testing.assert_allclose(w[:nb], np.linalg.solve(A, r)[:nb], rtol=1e-12, atol=1e-12)
+    idx = np.r_[nb:2 * nb, 0:nb]            # element 1 first, then the centre
+    w1 = np.linalg.solve(A[np.ix_(idx, idx)], r[idx])[:nb]
+    np.testing.assert_allclose(w[nb:2 * nb], w1, rtol=1e-12, atol=1e-12)
+    # target of the centre: row K of A_P w_P = r_P gives A_KK w_K - r_K =
+    # -sum_L A_KL (w_P)_L, and here w_P is the full solve
+    x = np.linalg.solve(A, r).reshape(4, nb)
+    t = M.target(Ablk, nbr, r, nb, np.full(4, 2.0))
+    coupling = sum(Ablk[0, 1 + f] @ x[nbr[0, f]] for f in range(3))
+    np.testing.assert_allclose(t[0], -coupling / 2.0, rtol=1e-10, atol=1e-12)
+
+
 def test_bf16_rounding():
     from oracle import mlp as M
     import torch
