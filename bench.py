@@ -384,39 +384,43 @@ def main():
     e2e_value = solves / (ms_e2e / 1e3)
     its = [last[m][0] for m in METHODS]
 
-    # ---- mixed precision on the same workload: bf16 / f32 inner GMRES with f64 refinement
-    def mixed_steps(inner, nsteps):
+    # ---- mixed precision on the same workload: plain f64 refinement around f32
+    # inner GMRES, and f64 FGMRES around f32 / bf16 inner GMRES (GMRES-based
+    # refinement; plain refinement around bf16 stalls on this workload)
+    def mixed_steps(kind, inner):
         store = D.DG_STORE_F64 | (D.DG_STORE_BF16 if inner == D.DG_BF16 else D.DG_STORE_F32)
         tol_in = 1e-2 if inner == D.DG_BF16 else 1e-4
-        # bf16 blocks stall the refinement near relres 0.9 on this workload
-        # (cond(A) u_bf16 > 1): a smaller inner-step budget bounds the time spent
-        budget = 4000 if inner == D.DG_BF16 else 20000
         res = {}
         for method in METHODS:
             h.mesh_upload(ma.nodes, ma.elems, ma.dirichlet, ma.neumann)
             h.set_params(method=method, degree=DEGREE, sigma_int=0.0, store=store, gmres_m=50, tol=1e-10,
-                         max_it=budget)
+                         max_it=20000)
             h.assemble(p.eps, p.alpha, p.b, f, gD, gN)
             h.precond_setup()
-            _, si = h.mixed_solve(inner, inner_m=50, inner_tol=tol_in, max_outer=60, x=x, raise_on_nonconv=False)
+            if kind == "ir":
+                _, si = h.mixed_solve(inner, inner_m=50, inner_tol=tol_in, max_outer=60, x=x, raise_on_nonconv=False)
+            else:
+                _, si = h.gmres_ir_solve(inner, inner_m=50, inner_tol=tol_in, max_outer=300, x=x,
+                                         raise_on_nonconv=False)
             res[method] = si
         return res
 
     mixed = {}
-    for name, inner in (("bf16", D.DG_BF16), ("f32", D.DG_F32)):
-        mixed_steps(inner, 1)   # warm-up (graph capture, workspaces)
+    for name, kind, inner in (("f32", "ir", D.DG_F32), ("f32_gmres_ir", "gir", D.DG_F32),
+                              ("bf16_gmres_ir", "gir", D.DG_BF16)):
+        mixed_steps(kind, inner)   # warm-up (graph capture, workspaces)
         torch.cuda.synchronize()
         m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         m0.record(stream)
         for _ in range(args.steps):
-            res = mixed_steps(inner, args.steps)
+            res = mixed_steps(kind, inner)
         m1.record(stream)
         torch.cuda.synchronize()
         mms = m0.elapsed_time(m1)
-        mixed[name] = {"solves_per_s": len(METHODS) * args.steps / (mms / 1e3),
+        mixed[name] = {"refinement": "f64 residual correction" if kind == "ir" else "f64 FGMRES outer",
+                       "solves_per_s": len(METHODS) * args.steps / (mms / 1e3),
                        "ms_per_solve": mms / (len(METHODS) * args.steps),
                        "inner_iterations": {"NIPG": res[1].iterations, "SIPG": res[2].iterations},
-                       "inner_step_budget": 4000 if name == "bf16" else 20000,
                        "outer": {"NIPG": res[1].outer, "SIPG": res[2].outer},
                        "relres_f64": {"NIPG": res[1].relres, "SIPG": res[2].relres},
                        "converged": all(r.status == 0 for r in res.values()),
@@ -447,6 +451,23 @@ def main():
         return tot / reps
 
     peak, peak_src = measured_peaks()
+    # assembly (volume + face integrals + F) alone, f64 blocks and f64+f32+bf16
+    assembly = {}
+    for name, store in (("f64", D.DG_STORE_F64), ("f64_f32_bf16", D.DG_STORE_F64 | D.DG_STORE_F32 | D.DG_STORE_BF16)):
+        h.set_params(store=store)
+        h.assemble(p.eps, p.alpha, p.b, f, gD, gN)
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        a0.record(stream)
+        for _ in range(reps):
+            h.assemble(p.eps, p.alpha, p.b, f, gD, gN)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ams = a0.elapsed_time(a1) / reps
+        written = info.ne * 4 * info.nb * info.nb * (8 + (6 if name != "f64" else 0))
+        assembly[name] = {"ms": ams, "elements_per_s": info.ne / (ams / 1e3), "bytes_written": written,
+                          "GBps_written": written / (ams / 1e3) / 1e9}
     apply = {}
     for name, dt, sa, sx in (("f64", D.DG_F64, 8, 8), ("f32", D.DG_F32, 4, 4), ("bf16", D.DG_BF16, 2, 4)):
         ams = time_apply(dt)
@@ -484,7 +505,7 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
-            "mixed": mixed, "kernels": kernels, "hbm_peak_GBps": peak}
+            "mixed": mixed, "assembly": assembly, "kernels": kernels, "hbm_peak_GBps": peak}
     if not args.no_extras:
         line["batched"] = batched_section(local, stream, args.batch_instances)
         line["learned"] = learned_section(local, stream, args.learned_instances, args.learned_steps)

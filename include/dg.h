@@ -300,6 +300,24 @@ dg_status dg_mixed_solve(dg_handle* h, int inner_dtype, int inner_m, double inne
                          const double* F, double* x, dg_solve_info* info);
 
 /*
+ * GMRES-based mixed-precision refinement: flexible GMRES(params.gmres_m) in f64
+ * on the f64 blocks (f64 vectors, orthogonalisation and Givens), whose
+ * preconditioner z = A_lo^-1 v is the low-precision solve of dg_mixed_solve
+ * (f32 GMRES(inner_m) with block Jacobi on the f32 / bf16 copy, to inner_tol or
+ * 8 restart cycles).  Where plain refinement stalls because cond(A) times the
+ * unit roundoff of the inner copy is near or above 1 (bf16 on
+ * convection-dominated operators), the outer Krylov method still converges.
+ * Same arguments as dg_mixed_solve; max_outer caps the outer FGMRES steps
+ * (one inner solve each), params.max_it the inner steps in total.
+ *   info: iterations = inner Arnoldi steps in total, outer = outer FGMRES steps,
+ *         restarts = outer restart cycles, relres = final f64 relative residual.
+ * params.precond must be DG_PRECOND_BLOCK_JACOBI or DG_PRECOND_NONE (for the
+ * inner solve).  DG_NOT_CONVERGED when a cap is reached.  Synchronises.
+ */
+dg_status dg_gmres_ir_solve(dg_handle* h, int inner_dtype, int inner_m, double inner_tol, int max_outer,
+                            const double* F, double* x, dg_solve_info* info);
+
+/*
  * Direct solve Stiff x = F (the paper's coef = Stiff\F) by dense LU with
  * partial pivoting on the device, f64.  For small systems: dofs <= 4096.
  * F device or NULL (assembled F); x device output.  Synchronises.

@@ -827,6 +827,143 @@ extern "C" dg_status dg_mixed_solve(dg_handle* h, int inner_dtype, int inner_m, 
 }
 
 // ---------------------------------------------------------------------------
+// GMRES-based refinement: f64 flexible GMRES on A64 whose preconditioner is
+// the low-precision inner solve (three-precision refinement in the sense of
+// Carson & Higham): z_j = s_j A_lo^-1 V_j, with A_lo^-1 the f32 GMRES(inner_m)
+// on the f32 / bf16 blocks to inner_tol or DG_INNER_CYCLES cycles.  Unlike
+// plain refinement it converges when cond(A) u_lo is near or above 1.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_ir_down(const double* __restrict__ v, float* __restrict__ r, long n) {
+    for (long l = (long)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (long)gridDim.x * blockDim.x)
+        r[l] = (float)v[l];
+}
+
+__global__ void __launch_bounds__(256) k_ir_up(const float* __restrict__ d, double* __restrict__ z, long n,
+                                                const double* __restrict__ scale) {
+    const double s = *scale;
+    for (long l = (long)blockIdx.x * blockDim.x + threadIdx.x; l < n; l += (long)gridDim.x * blockDim.x)
+        z[l] = s * (double)d[l];
+}
+
+template <int NB, typename TA>
+static dg_status gmres_ir_run(dg_handle* h, const TA* Alo, const double* F, double* x, int inner_m, double inner_tol,
+                              int max_outer, dg_solve_info* info) {
+    const long n = (long)h->ne * NB;
+    const int m = h->p.gmres_m;
+    GmresWork& W = h->gw[0];
+    dg_status s = ensure_workspace(h, W, n, m, sizeof(double));
+    if (s != DG_OK) return s;
+    if (!W.Zb) {
+        if ((s = dg_realloc(h, &W.Zb, (size_t)(m + 1) * W.ld * sizeof(double))) != DG_OK) return s;
+        DG_CK(h, cudaMemsetAsync(W.Zb, 0, (size_t)(m + 1) * W.ld * sizeof(double), h->stream));
+    }
+    const size_t ld = W.ld;
+    const size_t need = 2 * ld * sizeof(float) + 256;
+    if ((s = dg_ensure(h, &h->mx_buf, &h->cap_mx, need)) != DG_OK) return s;
+    float* r32 = (float*)h->mx_buf;
+    float* d32 = r32 + ld;
+    DG_CK(h, cudaMemsetAsync(h->mx_buf, 0, need, h->stream));
+    const bool lo16 = sizeof(TA) == 2;
+    const float* B32 = h->p.precond == DG_PRECOND_BLOCK_JACOBI ? (lo16 ? h->Binv16 : h->Binv32) : nullptr;
+    double* V = (double*)W.V;
+    double* Zb = (double*)W.Zb;
+    double* R = (double*)W.R;
+    GmresState* st = W.st;
+    GmresState* hs = W.st_host;
+    const long nvec = (long)W.ld / Vec<double>::W;
+    const int gx = W.gx;
+    k_gm_init<double><<<gx, 256, 0, h->stream>>>(F, x, V, n, st, W.partials, m, max_outer, h->p.tol);
+    h->nlaunch += 1;
+    DG_LAUNCH_CK(h);
+    DG_CK(h, cudaMemcpyAsync(hs, st, GM_HDR, cudaMemcpyDeviceToHost, h->stream));
+    DG_CK(h, cudaStreamSynchronize(h->stream));
+    int inner_total = 0;
+    const DevCtl act{&st->active, nullptr};
+    const DevCtl pend{&st->pending, nullptr};
+    while (!hs->done) {
+        while (hs->active) {
+            const int j = hs->j;
+            if (inner_total >= h->p.max_it) break;
+            // z_j = s_j A_lo^-1 V_j
+            k_ir_down<<<gx, 256, 0, h->stream>>>(V + (size_t)j * ld, r32, n);
+            h->nlaunch += 1;
+            dg_solve_info in{};
+            const int cap = std::min(h->p.max_it - inner_total, DG_INNER_CYCLES * inner_m);
+            s = gmres_run<NB, TA, float, float>(h, h->gw[1], Alo, B32, r32, d32, inner_m, inner_tol, cap, &in);
+            if (s != DG_OK && s != DG_NOT_CONVERGED) return s;
+            inner_total += in.iterations;
+            k_ir_up<<<gx, 256, 0, h->stream>>>(d32, Zb + (size_t)j * ld, n, st->scale + j);
+            // V_{j+1} = A64 z_j, orthogonalised against V_0..V_j; Givens step
+            launch_apply<NB, double, double>(h, h->A64, Zb + (size_t)j * ld, V + (size_t)(j + 1) * ld, act,
+                                             vsel_fixed(), vsel_fixed());
+            for (int pass = 1; pass <= 2; ++pass) {
+                k_gm_dots<double><<<W.gsm, dim3(GM_TX, GM_TY), 0, h->stream>>>(V, (long)ld, nvec, st, W.partials,
+                                                                               pass);
+                k_gm_update<double><<<gx, 256, 0, h->stream>>>(V, (long)ld, nvec, st, W.partials, pass);
+            }
+            h->nlaunch += 6;
+            DG_LAUNCH_CK(h);
+            DG_CK(h, cudaMemcpyAsync(hs, st, GM_HDR, cudaMemcpyDeviceToHost, h->stream));
+            DG_CK(h, cudaStreamSynchronize(h->stream));
+        }
+        // x += Z y; true residual; restart decision
+        k_gm_solve<<<1, 256, 0, h->stream>>>(st, 1);
+        k_gm_combine<double><<<gx, 256, 0, h->stream>>>(Zb, (long)ld, nvec, st, R);
+        k_gm_axpy<double><<<gx, 256, 0, h->stream>>>(x, R, n, st);
+        launch_apply<NB, double, double>(h, h->A64, x, R, pend, vsel_fixed(), vsel_fixed());
+        k_gm_resid<double><<<gx, 256, 0, h->stream>>>(F, R, V, n, st, W.partials);
+        h->nlaunch += 5;
+        DG_LAUNCH_CK(h);
+        DG_CK(h, cudaMemcpyAsync(hs, st, GM_HDR, cudaMemcpyDeviceToHost, h->stream));
+        DG_CK(h, cudaStreamSynchronize(h->stream));
+        if (inner_total >= h->p.max_it) break;
+    }
+    if (info) {
+        info->iterations = inner_total;
+        info->restarts = hs->cycles;
+        info->outer = hs->its;
+        info->relres = hs->relres;
+        info->status = hs->converged ? DG_OK : DG_NOT_CONVERGED;
+    }
+    h->err.clear();
+    if (hs->nonfinite) return dg_fail(h, DG_ERR_NONFINITE, "NaN/Inf in the outer FGMRES");
+    if (!hs->converged) return dg_fail(h, DG_NOT_CONVERGED, "GMRES-based refinement did not reach the tolerance");
+    return DG_OK;
+}
+
+extern "C" dg_status dg_gmres_ir_solve(dg_handle* h, int inner_dtype, int inner_m, double inner_tol, int max_outer,
+                                       const double* F, double* x, dg_solve_info* info) {
+    if (!h || !x) return DG_ERR_INVALID_ARG;
+    h->basis = nullptr;
+    if (!h->assembled) return dg_fail(h, DG_ERR_STATE, "not assembled");
+    if (!h->A64) return dg_fail(h, DG_ERR_STATE, "the f64 blocks are needed for the outer FGMRES");
+    if (inner_dtype != DG_F32 && inner_dtype != DG_BF16) return dg_fail(h, DG_ERR_INVALID_ARG, "inner_dtype");
+    if (inner_dtype == DG_F32 && !h->A32) return dg_fail(h, DG_ERR_STATE, "f32 blocks not stored");
+    if (inner_dtype == DG_BF16 && !h->A16) return dg_fail(h, DG_ERR_STATE, "bf16 blocks not stored");
+    if (inner_m < 1 || inner_m > DG_MAXM || !(inner_tol > 0.0 && inner_tol < 1.0) || max_outer < 1)
+        return dg_fail(h, DG_ERR_INVALID_ARG, "inner_m / inner_tol / max_outer");
+    if (h->p.precond == DG_PRECOND_MLP) return dg_fail(h, DG_ERR_INVALID_ARG, "the inner solve takes block Jacobi or none");
+    if (h->p.precond == DG_PRECOND_BLOCK_JACOBI && !h->bj_ok) {
+        dg_status s = dg_precond_setup(h, DG_PRECOND_BLOCK_JACOBI);
+        if (s != DG_OK) return s;
+    }
+    DG_CK(h, cudaSetDevice(h->device));
+    if (!F) F = h->F;
+    if (!dg_aligned16(F) || !dg_aligned16(x)) return dg_fail(h, DG_ERR_INVALID_ARG, "F and x must be 16-byte aligned");
+    const int nb = dg_nb(h->asm_k);
+#define DG_GIR(NBV)                                                                                          \
+    if (nb == NBV)                                                                                           \
+        return inner_dtype == DG_F32                                                                         \
+                   ? gmres_ir_run<NBV, float>(h, h->A32, F, x, inner_m, inner_tol, max_outer, info)          \
+                   : gmres_ir_run<NBV, __nv_bfloat16>(h, h->A16, F, x, inner_m, inner_tol, max_outer, info);
+    DG_GIR(3)
+    DG_GIR(6)
+    DG_GIR(10)
+#undef DG_GIR
+    return dg_fail(h, DG_ERR_INVALID_ARG, "degree");
+}
+
+// ---------------------------------------------------------------------------
 // kernel timing (instrumentation)
 // ---------------------------------------------------------------------------
 // A synthetic Arnoldi state: step j active, unit scales, coefficients 1e-3.

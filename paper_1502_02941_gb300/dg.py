@@ -84,6 +84,8 @@ _SIGS = {
     "dg_dense_solve": (ctypes.c_int, [c_void_p, c_void_p, c_void_p]),
     "dg_mixed_solve": (ctypes.c_int, [c_void_p, ctypes.c_int, ctypes.c_int, c_double, ctypes.c_int, c_void_p,
                                       c_void_p, ctypes.POINTER(dg_solve_info)]),
+    "dg_gmres_ir_solve": (ctypes.c_int, [c_void_p, ctypes.c_int, ctypes.c_int, c_double, ctypes.c_int, c_void_p,
+                                         c_void_p, ctypes.POINTER(dg_solve_info)]),
     "dg_l2_error": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_double),
                                    ctypes.POINTER(c_double)]),
     "dg_eval": (ctypes.c_int, [c_void_p, c_void_p, ctypes.c_int, c_void_p, c_void_p]),
@@ -270,6 +272,11 @@ def dg_gmres_solve(h, F, x, info=None):
 def dg_mixed_solve(h, inner_dtype, inner_m, inner_tol, max_outer, F, x, info=None):
     return load().dg_mixed_solve(h, int(inner_dtype), int(inner_m), float(inner_tol), int(max_outer), _ptr(F),
                                  _ptr(x), ctypes.byref(info) if info is not None else None)
+
+
+def dg_gmres_ir_solve(h, inner_dtype, inner_m, inner_tol, max_outer, F, x, info=None):
+    return load().dg_gmres_ir_solve(h, int(inner_dtype), int(inner_m), float(inner_tol), int(max_outer), _ptr(F),
+                                    _ptr(x), ctypes.byref(info) if info is not None else None)
 
 
 def dg_dense_solve(h, F, x):
@@ -538,6 +545,16 @@ class DG:
         x = self._empty((i.dofs,)) if x is None else x
         info = dg_solve_info()
         s = dg_mixed_solve(self.h, inner_dtype, inner_m, inner_tol, max_outer, F, x, info)
+        if s != DG_OK and not (s == DG_NOT_CONVERGED and not raise_on_nonconv):
+            self.check(s)
+        return x, info
+
+    def gmres_ir_solve(self, inner_dtype=DG_BF16, inner_m=50, inner_tol=1e-2, max_outer=200, F=None, x=None,
+                       raise_on_nonconv=True):
+        i = self.info()
+        x = self._empty((i.dofs,)) if x is None else x
+        info = dg_solve_info()
+        s = dg_gmres_ir_solve(self.h, inner_dtype, inner_m, inner_tol, max_outer, F, x, info)
         if s != DG_OK and not (s == DG_NOT_CONVERGED and not raise_on_nonconv):
             self.check(s)
         return x, info

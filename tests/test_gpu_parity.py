@@ -355,3 +355,40 @@ def test_mixed_refinement_reaches_f64_tolerance(inner):
     xo = x_to_oracle(T, _np(x64))
     assert np.abs(x_to_oracle(T, _np(xg)) - xo).max() <= 1e-7 * np.abs(xo).max()
     h.close()
+
+
+@pytest.mark.parametrize("inner", ["f32", "bf16"])
+def test_gmres_refinement_reaches_f64_tolerance(inner):
+    """Outer f64 FGMRES with the low-precision solve as preconditioner reaches
+    rel-res 1e-10, measured by the oracle's own f64 operator (reading A-12)."""
+    cfg = W.config3(N=12)
+    ma = W.structured_mesh(cfg.N, cfg.problem.neumann_sides)
+    store = D.DG_STORE_F64 | (D.DG_STORE_F32 if inner == "f32" else D.DG_STORE_BF16)
+    h = gpu_setup(ma, cfg.k, cfg.method, cfg.problem, store=store, tol=1e-10)
+    dt = D.DG_F32 if inner == "f32" else D.DG_BF16
+    xg, info = h.gmres_ir_solve(dt, inner_m=30, inner_tol=1e-4 if inner == "f32" else 1e-2, max_outer=100)
+    assert info.status == D.DG_OK and info.relres <= 1e-10 and info.outer >= 1
+    run = oracle_run(ma, cfg.k, cfg.method, cfg.problem)
+    T = basis_change(run, ma, cfg.k)
+    assert rel_residual_oracle(run, T, _np(xg)) <= 1e-10 * 1.5
+    h.close()
+
+
+def test_gmres_refinement_converges_where_bf16_refinement_stalls():
+    """The 256x256 boundary-layer workload at eps = 1e-6 (P2, SIPG): plain
+    refinement around bf16 inner solves stalls (cond(A) u_bf16 > 1); the f64
+    FGMRES outer loop around the same inner solves reaches 1e-10.  The final
+    residual is re-measured here with the f64 apply."""
+    cfg = W.config2(method=2, N=256)
+    ma = W.structured_mesh(cfg.N)
+    h = gpu_setup(ma, cfg.k, cfg.method, cfg.problem, store=D.DG_STORE_F64 | D.DG_STORE_BF16, tol=1e-10,
+                  max_it=4000)
+    _, plain = h.mixed_solve(D.DG_BF16, inner_m=50, inner_tol=1e-2, max_outer=10, raise_on_nonconv=False)
+    assert plain.status == D.DG_NOT_CONVERGED and plain.relres > 1e-3
+    h.set_params(max_it=20000)
+    xg, info = h.gmres_ir_solve(D.DG_BF16, inner_m=50, inner_tol=1e-2, max_outer=200)
+    assert info.status == D.DG_OK and info.relres <= 1e-10
+    F = h.rhs()
+    rr = (torch.linalg.norm(F - h.apply(xg)) / torch.linalg.norm(F)).item()
+    assert rr <= 1.5e-10
+    h.close()
