@@ -2,6 +2,7 @@
 
     python -m paper_1502_02941_gb300.cli --config 2 --N 256 --method 2 --solver gmres
     python -m paper_1502_02941_gb300.cli --config 3 --N 64 --solver mixed-bf16
+    python -m paper_1502_02941_gb300.cli --config 3 --solver gmres-ir-f32 --max-it 400000
 
 Prints one JSON line with sizes, iterations, relative residual, L2 error (when
 the workload has an exact solution) and wall time of the solve.
@@ -18,7 +19,8 @@ def main(argv=None):
     ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3])
     ap.add_argument("--N", type=int, default=None)
     ap.add_argument("--method", type=int, default=None, help="1 NIPG, 2 SIPG, 3 IIPG")
-    ap.add_argument("--solver", default="gmres", choices=["gmres", "dense", "mixed-bf16", "mixed-f32"])
+    ap.add_argument("--solver", default="gmres",
+                    choices=["gmres", "dense", "mixed-bf16", "mixed-f32", "gmres-ir-bf16", "gmres-ir-f32"])
     ap.add_argument("--m", type=int, default=50)
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--max-it", type=int, default=20000)
@@ -42,9 +44,9 @@ def main(argv=None):
     if a.method:
         cfg.method = a.method
     store = D.DG_STORE_F64
-    if a.solver == "mixed-bf16":
+    if a.solver.endswith("bf16"):
         store |= D.DG_STORE_BF16
-    elif a.solver == "mixed-f32":
+    elif a.solver.endswith("f32"):
         store |= D.DG_STORE_F32
     h = D.DG(0)
     problem.setup(h, cfg, store=store, gmres_m=a.m, tol=a.tol, max_it=a.max_it)
@@ -59,10 +61,14 @@ def main(argv=None):
             si = None
         elif a.solver == "gmres":
             x, si = h.gmres_solve(raise_on_nonconv=False)
-        else:
+        elif a.solver.startswith("mixed"):
             dt = D.DG_BF16 if a.solver == "mixed-bf16" else D.DG_F32
             x, si = h.mixed_solve(dt, inner_m=a.m, inner_tol=1e-2 if dt == D.DG_BF16 else 1e-4, max_outer=60,
                                   raise_on_nonconv=False)
+        else:
+            dt = D.DG_BF16 if a.solver == "gmres-ir-bf16" else D.DG_F32
+            x, si = h.gmres_ir_solve(dt, inner_m=a.m, inner_tol=1e-2 if dt == D.DG_BF16 else 1e-4, max_outer=5000,
+                                     raise_on_nonconv=False)
         torch.cuda.synchronize()
         out["seconds"] = time.perf_counter() - t0
     if si is not None:
