@@ -1,12 +1,13 @@
 // dg_assemble.cu -- element-row ("owner computes") assembly of Stiff = D+C+R
 // and of F (Eq. (ds), (dgscheme), (system) of Uzunca & Karasozen).
 //
-// Mapping: one warp per (tile of 32 elements, block entry m = i*nb + j); the
-// 32 lanes are the 32 elements of the tile.  Every lane of a warp therefore
-// reads the same basis-table entries (shared-memory broadcast), reads its
-// element's geometry with coalesced SoA loads and writes entry m of its four
-// blocks into the tile-interleaved block-ELL layout (16-byte stride between
-// lanes).  Each block entry is written exactly once: no atomics, no races.
+// Mapping: one CTA per tile of 32 elements.  With affine elements each block
+// entry is a short sum of per-element factors times reference-element
+// contraction matrices (built once per degree, staged in shared memory), plus
+// the upwind terms, which are evaluated pointwise at the face points because
+// min(b.n, 0) is not polynomial.  Lanes of a warp are the 32 elements of the
+// tile, so every table read is a shared-memory broadcast; each block entry is
+// written exactly once (no atomics, no races).
 //
 // Per element K, test function phi_i on K, trial phi_j (on K or on the
 // neighbour L across face f), outward normal n of K, face weight w|e|:
@@ -64,146 +65,219 @@ __device__ __forceinline__ void stage_tables(const double* __restrict__ tab, con
     __syncthreads();
 }
 
+// Per-element factors of the reference contractions (see dg_tables.cu):
+// 10 volume factors, then per face f: sA_r, sA_s (trial gradient . n on the
+// test function), sB_r, sB_s (test gradient . n on the trial function), sC
+// (penalty), xA_r, xA_s, xB_r, xB_s, xC (the same for the neighbour block),
+// xU (1 on interior faces), u_q = -w_q |e| min(b.n, 0) at the face points.
+template <int NQ>
+struct CoefIdx {
+    static constexpr int FACE = 11 + NQ;
+    static constexpr int N = 10 + 3 * FACE;
+};
+
+// Factors of the reference contractions, one thread per (element, part):
+// part 0 the volume factors, parts 1..3 the factors of face part-1.  Written
+// to the SoA array fac [CoefIdx::N][ne] (and the neighbour's face to nfo [3][ne]).
 template <int K_DEG>
-__global__ void __launch_bounds__(256) k_assemble(const AsmArgs a) {
+__global__ void __launch_bounds__(256) k_asm_factors(const AsmArgs a, double* __restrict__ fac, int* __restrict__ nfo) {
+    constexpr int NQ = K_DEG + 2;
+    using CI = CoefIdx<NQ>;
+    const int ne = a.ne;
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 4L * ne) return;
+    const int part = (int)(t / ne), K = (int)(t - (long)part * ne);
+    const TabLayout& L = a.L;
+    const double* fw = a.tab + L.face_w;
+    const double* fr = a.tab + L.face_r;
+    const double* fs = a.tab + L.face_s;
+    const size_t sne = (size_t)ne;
+    double* c = fac + K;               // c[idx * ne]
+    {
+        {
+            const double x0 = gload(a.geo, G_X0, ne, K), y0 = gload(a.geo, G_Y0, ne, K);
+            const double j00 = gload(a.geo, G_J00, ne, K), j01 = gload(a.geo, G_J01, ne, K);
+            const double j10 = gload(a.geo, G_J10, ne, K), j11 = gload(a.geo, G_J11, ne, K);
+            const double i00 = gload(a.geo, G_I00, ne, K), i01 = gload(a.geo, G_I01, ne, K);
+            const double i10 = gload(a.geo, G_I10, ne, K), i11 = gload(a.geo, G_I11, ne, K);
+            const double det = gload(a.geo, G_DET, ne, K);
+            double eps = a.eps, alpha = a.alpha, sig_int = a.sig_int, sig_bdry = a.sig_bdry;
+            double bc[6];
+#pragma unroll
+            for (int t = 0; t < 6; ++t) bc[t] = a.b[t];
+            if (a.inst) {
+                const double* ci = a.icoef + (size_t)DG_ICOEF * a.inst[K];
+                eps = ci[0];
+                alpha = ci[1];
+#pragma unroll
+                for (int t = 0; t < 6; ++t) bc[t] = ci[2 + t];
+                sig_int = ci[8];
+                sig_bdry = ci[9];
+            }
+            if (part == 0) {
+                // diffusion: grad phi_j . grad phi_i = sum_ab G_ab d_a phi_j d_b phi_i, G = Jinv Jinv^T
+                c[0 * sne] = eps * det * (i00 * i00 + i01 * i01);
+                c[1 * sne] = eps * det * (i00 * i10 + i01 * i11);
+                c[2 * sne] = eps * det * (i10 * i10 + i11 * i11);
+                // convection: b(x(r,s)) affine in (r, s); beta_a = sum_c Jinv[a][c] b_c
+                const double bx0 = bc[0] + bc[1] * x0 + bc[2] * y0, bxr = bc[1] * j00 + bc[2] * j10,
+                             bxs = bc[1] * j01 + bc[2] * j11;
+                const double by0 = bc[3] + bc[4] * x0 + bc[5] * y0, byr = bc[4] * j00 + bc[5] * j10,
+                             bys = bc[4] * j01 + bc[5] * j11;
+                c[3 * sne] = det * (i00 * bx0 + i01 * by0);
+                c[4 * sne] = det * (i00 * bxr + i01 * byr);
+                c[5 * sne] = det * (i00 * bxs + i01 * bys);
+                c[6 * sne] = det * (i10 * bx0 + i11 * by0);
+                c[7 * sne] = det * (i10 * bxr + i11 * byr);
+                c[8 * sne] = det * (i10 * bxs + i11 * bys);
+                c[9 * sne] = alpha * det;
+            } else {
+                const int f = part - 1;
+                const double dV[3][2] = {{1.0, 0.0}, {-1.0, 1.0}, {0.0, -1.0}};
+                const int type = __ldg(a.ftype + (size_t)f * ne + K);
+                const int Ln = __ldg(a.nbr + (size_t)f * ne + K);
+                const int nf = type == 0 ? __ldg(a.nface + (size_t)f * ne + K) : 0;
+                const double tx = j00 * dV[f][0] + j01 * dV[f][1];
+                const double ty = j10 * dV[f][0] + j11 * dV[f][1];
+                const double len = sqrt(tx * tx + ty * ty);
+                const double nx = ty / len, ny = -tx / len;   // h_e = |e|, b0 = 1
+                const double nu_r = i00 * nx + i01 * ny, nu_s = i10 * nx + i11 * ny;
+                const double fac1 = type == 0 ? -0.5 : (type == 1 ? -1.0 : 0.0);
+                const double fac2 = type == 0 ? 0.5 : (type == 1 ? 1.0 : 0.0);
+                const double sig = type == 0 ? sig_int : (type == 1 ? sig_bdry : 0.0);
+                double* cf = c + (10 + f * CI::FACE) * sne;
+                cf[0 * sne] = fac1 * eps * len * nu_r;
+                cf[1 * sne] = fac1 * eps * len * nu_s;
+                cf[2 * sne] = fac2 * a.kappa * eps * len * nu_r;
+                cf[3 * sne] = fac2 * a.kappa * eps * len * nu_s;
+                cf[4 * sne] = sig * eps;
+                double lnr = 0.0, lns = 0.0;
+                if (type == 0) {
+                    const double li00 = gload(a.geo, G_I00, ne, Ln), li01 = gload(a.geo, G_I01, ne, Ln);
+                    const double li10 = gload(a.geo, G_I10, ne, Ln), li11 = gload(a.geo, G_I11, ne, Ln);
+                    lnr = li00 * nx + li01 * ny;
+                    lns = li10 * nx + li11 * ny;
+                }
+                const double in = type == 0 ? 1.0 : 0.0;
+                cf[5 * sne] = -0.5 * in * eps * len * lnr;
+                cf[6 * sne] = -0.5 * in * eps * len * lns;
+                cf[7 * sne] = -0.5 * in * a.kappa * eps * len * nu_r;
+                cf[8 * sne] = -0.5 * in * a.kappa * eps * len * nu_s;
+                cf[9 * sne] = -in * sig_int * eps;
+                cf[10 * sne] = in;
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    const double x = x0 + j00 * fr[f * NQ + q] + j01 * fs[f * NQ + q];
+                    const double y = y0 + j10 * fr[f * NQ + q] + j11 * fs[f * NQ + q];
+                    const double bn = (bc[0] + bc[1] * x + bc[2] * y) * nx + (bc[3] + bc[4] * x + bc[5] * y) * ny;
+                    const double up = bn < 0.0 ? bn : 0.0;
+                    cf[(11 + q) * sne] = -fw[q] * len * up;
+                }
+                nfo[(size_t)f * ne + K] = nf;
+            }
+        }
+    }
+}
+
+// Element-row assembly: one CTA per tile of 32 elements; the tile's factors
+// are staged in shared memory, then warp w computes block entries m = w, w + 8,
+// ... of the four blocks of its 32 elements (lane = element) as sums of factor
+// x reference matrix (shared-memory broadcasts) plus the pointwise upwind sums,
+// and writes them into the tile-interleaved block-ELL copies.  Each entry is
+// written once.
+template <int K_DEG>
+__global__ void __launch_bounds__(256) k_assemble(const AsmArgs a, const double* __restrict__ fac,
+                                                  const int* __restrict__ nfo) {
     constexpr int NB = dg_nb(K_DEG);
     constexpr int NQ = K_DEG + 2;
-    constexpr int QK = NQ * NQ;
     constexpr int NB2 = NB * NB;
+    using CI = CoefIdx<NQ>;
+    constexpr int NCT = DG_NCT * NB2;
+    constexpr int NFB = NQ + 6 * NQ + 3 * NQ * NB;   // face_w, face_r, face_s, face_phi
     extern __shared__ double sm[];
+    double* sct = sm;                  // contraction matrices
+    double* sfb = sct + NCT;           // face rule + basis at face points
+    double* scf = sfb + NFB;           // factors [CI::N][32]
+    int* snf = reinterpret_cast<int*>(scf + CI::N * 32);   // neighbour's face [3][32]
     const TabLayout& L = a.L;
-    stage_tables<K_DEG>(a.tab, L, sm);
-
-    const int lane = threadIdx.x & 31;
-    const long gw = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int ntiles = (a.ne + 31) >> 5;
-    if (gw >= (long)ntiles * NB2) return;
-    const int tile = (int)(gw / NB2);
-    const int m = (int)(gw - (long)tile * NB2);
-    const int i = m / NB, j = m - (m / NB) * NB;
-    const int K = tile * 32 + lane;
+    for (int t = threadIdx.x; t < NCT; t += blockDim.x) sct[t] = a.tab[L.ct + t];
+    for (int t = threadIdx.x; t < NFB; t += blockDim.x) sfb[t] = a.tab[L.face_w + t];
     const int ne = a.ne;
+    const int tile = blockIdx.x;
+    for (int t = threadIdx.x; t < CI::N * 32; t += blockDim.x) {
+        const int idx = t >> 5, K = tile * 32 + (t & 31);
+        scf[t] = K < ne ? fac[(size_t)idx * ne + K] : 0.0;
+    }
+    if (threadIdx.x < 96) {
+        const int f = threadIdx.x >> 5, K = tile * 32 + (threadIdx.x & 31);
+        snf[threadIdx.x] = K < ne ? nfo[(size_t)f * ne + K] : 0;
+    }
+    const double* fp = sfb + 7 * NQ;
+    __syncthreads();
 
-    double out[4] = {0.0, 0.0, 0.0, 0.0};
-    if (K < ne) {
-        const double x0 = gload(a.geo, G_X0, ne, K), y0 = gload(a.geo, G_Y0, ne, K);
-        const double j00 = gload(a.geo, G_J00, ne, K), j01 = gload(a.geo, G_J01, ne, K);
-        const double j10 = gload(a.geo, G_J10, ne, K), j11 = gload(a.geo, G_J11, ne, K);
-        const double i00 = gload(a.geo, G_I00, ne, K), i01 = gload(a.geo, G_I01, ne, K);
-        const double i10 = gload(a.geo, G_I10, ne, K), i11 = gload(a.geo, G_I11, ne, K);
-        const double det = gload(a.geo, G_DET, ne, K);
-        double eps = a.eps, alpha = a.alpha, sig_int = a.sig_int, sig_bdry = a.sig_bdry;
-        double bc[6];
-#pragma unroll
-        for (int t = 0; t < 6; ++t) bc[t] = a.b[t];
-        if (a.inst) {
-            const double* c = a.icoef + (size_t)DG_ICOEF * a.inst[K];
-            eps = c[0];
-            alpha = c[1];
-#pragma unroll
-            for (int t = 0; t < 6; ++t) bc[t] = c[2 + t];
-            sig_int = c[8];
-            sig_bdry = c[9];
-        }
-
-        // ---- volume integrals ------------------------------------------------
-        const double* vw = sm + L.vol_w;
-        const double* vr = sm + L.vol_r;
-        const double* vs = sm + L.vol_s;
-        const double* vp = sm + L.vol_phi;
-        const double* vdr = sm + L.vol_dr;
-        const double* vds = sm + L.vol_ds;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int K = tile * 32 + lane;
+    const double* c = scf + lane;
+    for (int m = warp; m < NB2; m += 8) {
+        const int i = m / NB, j = m - (m / NB) * NB;
+        const int mt = j * NB + i;
+        double out[4];
         double acc = 0.0;
-#pragma unroll 4
-        for (int q = 0; q < QK; ++q) {
-            const double w = vw[q] * det;
-            const double pi = vp[q * NB + i], pj = vp[q * NB + j];
-            const double dri = vdr[q * NB + i], dsi = vds[q * NB + i];
-            const double drj = vdr[q * NB + j], dsj = vds[q * NB + j];
-            const double gxi = i00 * dri + i10 * dsi, gyi = i01 * dri + i11 * dsi;
-            const double gxj = i00 * drj + i10 * dsj, gyj = i01 * drj + i11 * dsj;
-            const double x = x0 + j00 * vr[q] + j01 * vs[q];
-            const double y = y0 + j10 * vr[q] + j11 * vs[q];
-            const double bx = bc[0] + bc[1] * x + bc[2] * y;
-            const double by = bc[3] + bc[4] * x + bc[5] * y;
-            acc += w * (eps * (gxj * gxi + gyj * gyi) + (bx * gxj + by * gyj) * pi + alpha * pj * pi);
-        }
-
-        // ---- face integrals ----------------------------------------------------
-        const double* fw = sm + L.face_w;
-        const double* fr = sm + L.face_r;
-        const double* fs = sm + L.face_s;
-        const double* fp = sm + L.face_phi;
-        const double* fdr = sm + L.face_dr;
-        const double* fds = sm + L.face_ds;
-        const double dV[3][2] = {{1.0, 0.0}, {-1.0, 1.0}, {0.0, -1.0}};
 #pragma unroll
+        for (int t = 0; t < DG_NCT_VOL; ++t) acc = fma(c[t * 32], sct[t * NB2 + m], acc);
+        out[1] = out[2] = out[3] = 0.0;
+#pragma unroll 1
         for (int f = 0; f < 3; ++f) {
-            const int type = __ldg(a.ftype + (size_t)f * ne + K);
-            const int Ln = __ldg(a.nbr + (size_t)f * ne + K);
-            const int nf = __ldg(a.nface + (size_t)f * ne + K);
-            const double tx = j00 * dV[f][0] + j01 * dV[f][1];
-            const double ty = j10 * dV[f][0] + j11 * dV[f][1];
-            const double len = sqrt(tx * tx + ty * ty);
-            const double nx = ty / len, ny = -tx / len;
-            const double he = len;  // h_e = |e|, b0 = 1
-            double li00 = 0, li01 = 0, li10 = 0, li11 = 0;
-            if (type == 0) {
-                li00 = gload(a.geo, G_I00, ne, Ln);
-                li01 = gload(a.geo, G_I01, ne, Ln);
-                li10 = gload(a.geo, G_I10, ne, Ln);
-                li11 = gload(a.geo, G_I11, ne, Ln);
-            }
-            const double sig = type == 0 ? sig_int : sig_bdry;
-            double self = 0.0, cross = 0.0;
+            const double* cf = c + (10 + f * CI::FACE) * 32;
+            const double* E = sct + (DG_NCT_VOL + DG_NCT_SELF * f) * NB2;
+            acc = fma(cf[0 * 32], E[m], acc);
+            acc = fma(cf[1 * 32], E[NB2 + m], acc);
+            acc = fma(cf[2 * 32], E[mt], acc);
+            acc = fma(cf[3 * 32], E[NB2 + mt], acc);
+            acc = fma(cf[4 * 32], E[2 * NB2 + m], acc);
+            const int nf = snf[f * 32 + lane];
+            const double* X = sct + (DG_NCT_VOL + 3 * DG_NCT_SELF + DG_NCT_CROSS * (3 * f + nf)) * NB2;
+            double cr = cf[5 * 32] * X[m];
+            cr = fma(cf[6 * 32], X[NB2 + m], cr);
+            cr = fma(cf[7 * 32], X[2 * NB2 + m], cr);
+            cr = fma(cf[8 * 32], X[3 * NB2 + m], cr);
+            cr = fma(cf[9 * 32], X[4 * NB2 + m], cr);
+            double us = 0.0, ux = 0.0;
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
-                const double w = fw[q] * len;
-                const int o = (f * NQ + q) * NB;
-                const double pi = fp[o + i], pj = fp[o + j];
-                const double gin = (i00 * fdr[o + i] + i10 * fds[o + i]) * nx + (i01 * fdr[o + i] + i11 * fds[o + i]) * ny;
-                const double gjn = (i00 * fdr[o + j] + i10 * fds[o + j]) * nx + (i01 * fdr[o + j] + i11 * fds[o + j]) * ny;
-                const double x = x0 + j00 * fr[f * NQ + q] + j01 * fs[f * NQ + q];
-                const double y = y0 + j10 * fr[f * NQ + q] + j11 * fs[f * NQ + q];
-                const double bn = (bc[0] + bc[1] * x + bc[2] * y) * nx + (bc[3] + bc[4] * x + bc[5] * y) * ny;
-                const double up = bn < 0.0 ? bn : 0.0;
-                if (type == 0) {
-                    const int oo = (nf * NQ + (NQ - 1 - q)) * NB;   // same point seen from L
-                    const double psj = fp[oo + j];
-                    const double gpj = (li00 * fdr[oo + j] + li10 * fds[oo + j]) * nx +
-                                       (li01 * fdr[oo + j] + li11 * fds[oo + j]) * ny;
-                    self += w * (-0.5 * eps * gjn * pi + 0.5 * a.kappa * eps * gin * pj +
-                                 sig * eps / he * pj * pi - up * pj * pi);
-                    cross += w * (-0.5 * eps * gpj * pi - 0.5 * a.kappa * eps * gin * psj -
-                                  sig * eps / he * psj * pi + up * psj * pi);
-                } else if (type == 1) {
-                    self += w * (-eps * gjn * pi + a.kappa * eps * gin * pj + sig * eps / he * pj * pi - up * pj * pi);
-                } else {
-                    self += w * (-up * pj * pi);
-                }
+                const double uq = cf[(11 + q) * 32];
+                const double pi = fp[(f * NQ + q) * NB + i];
+                us = fma(uq * pi, fp[(f * NQ + q) * NB + j], us);
+                ux = fma(uq * pi, fp[(nf * NQ + NQ - 1 - q) * NB + j], ux);
             }
-            acc += self;
-            out[1 + f] = cross;
+            acc += us;
+            const double xo = fma(-cf[10 * 32], ux, cr);
+            if (f == 0) out[1] = xo;
+            else if (f == 1) out[2] = xo;
+            else out[3] = xo;
         }
         out[0] = acc;
-    }
-    // write entry m of the 4 blocks (zeros for padding lanes K >= ne)
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-        if (a.A64) a.A64[dg_blk_index<double>(K, s, m, NB, 4)] = out[s];
-        if (a.A32) a.A32[dg_blk_index<float>(K, s, m, NB, 4)] = (float)out[s];
-        if (a.A16) a.A16[dg_blk_index<__nv_bfloat16>(K, s, m, NB, 4)] = __double2bfloat16(out[s]);
-    }
-    // the last entry also clears the chunk padding after nb^2
-    if (m == NB2 - 1) {
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            if (a.A64) for (int mm = NB2; mm < dg_chunks<double>(NB) * 2; ++mm) a.A64[dg_blk_index<double>(K, s, mm, NB, 4)] = 0.0;
-            if (a.A32) for (int mm = NB2; mm < dg_chunks<float>(NB) * 4; ++mm) a.A32[dg_blk_index<float>(K, s, mm, NB, 4)] = 0.0f;
-            if (a.A16) for (int mm = NB2; mm < dg_chunks<__nv_bfloat16>(NB) * 8; ++mm)
-                a.A16[dg_blk_index<__nv_bfloat16>(K, s, mm, NB, 4)] = __double2bfloat16(0.0);
+        for (int s2 = 0; s2 < 4; ++s2) {
+            if (a.A64) a.A64[dg_blk_index<double>(K, s2, m, NB, 4)] = out[s2];
+            if (a.A32) a.A32[dg_blk_index<float>(K, s2, m, NB, 4)] = (float)out[s2];
+            if (a.A16) a.A16[dg_blk_index<__nv_bfloat16>(K, s2, m, NB, 4)] = __double2bfloat16(out[s2]);
         }
     }
+    // chunk padding after nb^2: warp s clears slot s
+    if (warp < 4) {
+        const int s2 = warp;
+        if (a.A64) for (int mm = NB2; mm < dg_chunks<double>(NB) * 2; ++mm) a.A64[dg_blk_index<double>(K, s2, mm, NB, 4)] = 0.0;
+        if (a.A32) for (int mm = NB2; mm < dg_chunks<float>(NB) * 4; ++mm) a.A32[dg_blk_index<float>(K, s2, mm, NB, 4)] = 0.0f;
+        if (a.A16) for (int mm = NB2; mm < dg_chunks<__nv_bfloat16>(NB) * 8; ++mm)
+            a.A16[dg_blk_index<__nv_bfloat16>(K, s2, mm, NB, 4)] = __double2bfloat16(0.0);
+    }
+}
+
+template <int K_DEG>
+static size_t assemble_smem() {  // shared memory of k_assemble
+    constexpr int NB = dg_nb(K_DEG), NQ = K_DEG + 2;
+    return sizeof(double) * (DG_NCT * NB * NB + 7 * NQ + 3 * NQ * NB + CoefIdx<NQ>::N * 32) + sizeof(int) * 96;
 }
 
 // F_K[i]: one warp per (tile, i), lanes = elements.
@@ -309,26 +383,38 @@ dg_status dg_launch_assemble(dg_handle* h, const dg_coeffs* c, double kappa, dou
     a.inst = h->b_inst_active ? h->b_inst : nullptr;
     a.icoef = h->b_inst_active ? h->b_icoef : nullptr;
     const size_t smem = sizeof(double) * h->tl.err_w;
-    const long warps_a = (long)h->ntiles * nb * nb;
     const long warps_r = (long)h->ntiles * nb;
-    const unsigned ga = (unsigned)((warps_a + 7) / 8), gr = (unsigned)((warps_r + 7) / 8);
+    const unsigned ga = (unsigned)h->ntiles, gr = (unsigned)((warps_r + 7) / 8);
+    const unsigned gf = (unsigned)((4L * h->ne + 255) / 256);
+    // factor scratch: [CoefIdx::N][ne] f64 + [3][ne] int
+    const int ncoef = 10 + 3 * (11 + k + 2);
+    dg_status s = dg_scratch(h, sizeof(double) * (size_t)ncoef * h->ne + sizeof(int) * 3 * (size_t)h->ne + 16);
+    if (s != DG_OK) return s;
+    double* fac = h->scratch;
+    int* nfo = reinterpret_cast<int*>(fac + (size_t)ncoef * h->ne);
     switch (k) {
         case 1:
-            k_assemble<1><<<ga, 256, smem, h->stream>>>(a);
+            DG_CK(h, cudaFuncSetAttribute(k_assemble<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)assemble_smem<1>()));
+            k_asm_factors<1><<<gf, 256, 0, h->stream>>>(a, fac, nfo);
+            k_assemble<1><<<ga, 256, assemble_smem<1>(), h->stream>>>(a, fac, nfo);
             k_rhs<1><<<gr, 256, smem, h->stream>>>(a);
             break;
         case 2:
-            k_assemble<2><<<ga, 256, smem, h->stream>>>(a);
+            DG_CK(h, cudaFuncSetAttribute(k_assemble<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)assemble_smem<2>()));
+            k_asm_factors<2><<<gf, 256, 0, h->stream>>>(a, fac, nfo);
+            k_assemble<2><<<ga, 256, assemble_smem<2>(), h->stream>>>(a, fac, nfo);
             k_rhs<2><<<gr, 256, smem, h->stream>>>(a);
             break;
         case 3:
-            k_assemble<3><<<ga, 256, smem, h->stream>>>(a);
+            DG_CK(h, cudaFuncSetAttribute(k_assemble<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)assemble_smem<3>()));
+            k_asm_factors<3><<<gf, 256, 0, h->stream>>>(a, fac, nfo);
+            k_assemble<3><<<ga, 256, assemble_smem<3>(), h->stream>>>(a, fac, nfo);
             k_rhs<3><<<gr, 256, smem, h->stream>>>(a);
             break;
         default:
             return dg_fail(h, DG_ERR_INVALID_ARG, "degree");
     }
-    h->nlaunch += 2;
+    h->nlaunch += 3;
     DG_LAUNCH_CK(h);
     return DG_OK;
 }

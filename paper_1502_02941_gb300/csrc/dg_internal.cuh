@@ -46,8 +46,18 @@ struct TabLayout {
     int vol_w, vol_r, vol_s, vol_phi, vol_dr, vol_ds;        // [qk], [qk][nb]
     int face_w, face_r, face_s, face_phi, face_dr, face_ds;   // [nq], [3][nq], [3][nq][nb]
     int err_w, err_r, err_s, err_phi;                         // [qerr], [qerr][nb]
+    int ct;      // DG_NCT reference contraction matrices [nb][nb] (dg_tables.cu)
     int total;
 };
+
+// Reference contraction matrices (each [nb][nb], entry [i][j], i test, j trial):
+// 10 volume (S_rr, S_rs + S_sr, S_ss, C_r1, C_rr, C_rs, C_s1, C_sr, C_ss, M),
+// then per face f: E_fr, E_fs, M_f, then per face pair (f, nf): X_r, X_s, Y_r,
+// Y_s, Z.  See dg_tables.cu for their definitions.
+#define DG_NCT_VOL 10
+#define DG_NCT_SELF 3
+#define DG_NCT_CROSS 5
+#define DG_NCT (DG_NCT_VOL + 3 * DG_NCT_SELF + 9 * DG_NCT_CROSS)
 
 struct GmresState;   // device-side solver state (dg_gmres.cu)
 

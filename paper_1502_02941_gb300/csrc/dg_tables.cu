@@ -128,8 +128,68 @@ TabLayout dg_table_layout(int k) {
     L.err_r = o; o += L.qerr;
     L.err_s = o; o += L.qerr;
     L.err_phi = o; o += L.qerr * L.nb;
+    L.ct = o; o += DG_NCT * L.nb * L.nb;
     L.total = o;
     return L;
+}
+
+// Reference contraction matrices of the element-row assembly.  With affine
+// elements every integrand of Eq. (ds) is a reference-element integral times
+// per-element factors: for grad phi = J^-T grad^ phi^ the diffusion term
+// needs S_ab[i][j] = sum_q w_q d_a phi_j d_b phi_i (a, b in {r, s}); the
+// convection term with b affine in x, hence in (r, s), needs C_am[i][j] =
+// sum_q w_q mu_m d_a phi_j phi_i with mu in {1, r, s}; the reaction term the
+// mass matrix M.  On face f (Gauss points q, weights w_q of [0,1]):
+// E_fa[i][j] = sum_q w_q d_a phi_j phi_i and M_f, and for the neighbour's
+// basis seen at the same points (its face nf, points in reverse order, psi):
+// X_a = sum w d_a psi_j phi_i, Y_a = sum w d_a phi_i psi_j, Z = sum w psi_j phi_i.
+static void dg_build_contractions(const TabLayout& L, double* T) {
+    const int nb = L.nb, nq = L.nq, nb2 = nb * nb;
+    double* C = T + L.ct;
+    auto vphi = [&](int q, int i) { return T[L.vol_phi + q * nb + i]; };
+    auto vd = [&](int a, int q, int i) { return T[(a == 0 ? L.vol_dr : L.vol_ds) + q * nb + i]; };
+    auto fphi = [&](int f, int q, int i) { return T[L.face_phi + (f * nq + q) * nb + i]; };
+    auto fd = [&](int a, int f, int q, int i) { return T[(a == 0 ? L.face_dr : L.face_ds) + (f * nq + q) * nb + i]; };
+    for (int i = 0; i < nb; ++i)
+        for (int j = 0; j < nb; ++j) {
+            const int m = i * nb + j;
+            double v[DG_NCT_VOL] = {0};
+            for (int q = 0; q < L.qk; ++q) {
+                const double w = T[L.vol_w + q], r = T[L.vol_r + q], s = T[L.vol_s + q];
+                v[0] += w * vd(0, q, j) * vd(0, q, i);
+                v[1] += w * (vd(0, q, j) * vd(1, q, i) + vd(1, q, j) * vd(0, q, i));
+                v[2] += w * vd(1, q, j) * vd(1, q, i);
+                const double mu[3] = {1.0, r, s};
+                for (int a = 0; a < 2; ++a)
+                    for (int t = 0; t < 3; ++t) v[3 + 3 * a + t] += w * mu[t] * vd(a, q, j) * vphi(q, i);
+                v[9] += w * vphi(q, j) * vphi(q, i);
+            }
+            for (int t = 0; t < DG_NCT_VOL; ++t) C[t * nb2 + m] = v[t];
+            for (int f = 0; f < 3; ++f) {
+                double e[DG_NCT_SELF] = {0};
+                for (int q = 0; q < nq; ++q) {
+                    const double w = T[L.face_w + q];
+                    e[0] += w * fd(0, f, q, j) * fphi(f, q, i);
+                    e[1] += w * fd(1, f, q, j) * fphi(f, q, i);
+                    e[2] += w * fphi(f, q, j) * fphi(f, q, i);
+                }
+                for (int t = 0; t < DG_NCT_SELF; ++t) C[(DG_NCT_VOL + DG_NCT_SELF * f + t) * nb2 + m] = e[t];
+                for (int nf = 0; nf < 3; ++nf) {
+                    double x[DG_NCT_CROSS] = {0};
+                    for (int q = 0; q < nq; ++q) {
+                        const double w = T[L.face_w + q];
+                        const int qq = nq - 1 - q;
+                        x[0] += w * fd(0, nf, qq, j) * fphi(f, q, i);
+                        x[1] += w * fd(1, nf, qq, j) * fphi(f, q, i);
+                        x[2] += w * fd(0, f, q, i) * fphi(nf, qq, j);
+                        x[3] += w * fd(1, f, q, i) * fphi(nf, qq, j);
+                        x[4] += w * fphi(nf, qq, j) * fphi(f, q, i);
+                    }
+                    const int base = DG_NCT_VOL + 3 * DG_NCT_SELF + DG_NCT_CROSS * (3 * f + nf);
+                    for (int t = 0; t < DG_NCT_CROSS; ++t) C[(base + t) * nb2 + m] = x[t];
+                }
+            }
+        }
 }
 
 // Duffy-collapsed rule: r = u (1 - v), s = v, weight wu wv (1 - v).
@@ -170,6 +230,7 @@ void dg_build_tables(int k, double* T) {
     duffy(k + 4, T + L.err_r, T + L.err_s, T + L.err_w);
     for (int q = 0; q < L.qerr; ++q)
         dg_dubiner(k, T[L.err_r + q], T[L.err_s + q], T + L.err_phi + q * L.nb, nullptr, nullptr);
+    dg_build_contractions(L, T);
 }
 
 dg_status dg_ensure_tables(dg_handle* h, int k) {
