@@ -41,6 +41,7 @@ struct GmresState {  // header fields first: the first GM_HDR bytes go to the ho
     int nonfinite;   // NaN/Inf met
     int m, max_it;
     unsigned int arrive;  // last-block arrival counter
+    int jw;          // column being orthogonalised (read by the update kernel)
     double tol, bnorm, relres, wn2_before;
     double scale[DG_MAXM + 2];
     double hcol[DG_MAXM + 2];
@@ -180,6 +181,39 @@ __global__ void __launch_bounds__(256) k_gm_init(const TV* __restrict__ F, TV* _
     st->g[0] = bn;
     st->scale[0] = 1.0 / bn;
 }
+// Givens / Hessenberg step for column j; runs in thread 0 of the last block
+// with the column and the previous rotations staged in shared memory.
+__device__ void gm_finish_column(GmresState* st, double wn, const double* hc, const double* cs, const double* sn) {
+    const int j = st->j;
+    const int LD = DG_MAXM + 1;
+    double* Hc = st->H + (long)j * LD;
+    double a = hc[0];
+    for (int i = 0; i < j; ++i) {
+        const double b = hc[i + 1];
+        Hc[i] = cs[i] * a + sn[i] * b;
+        a = -sn[i] * a + cs[i] * b;
+    }
+    const double b = wn;
+    const double r = hypot(a, b);
+    const double c = r == 0.0 ? 1.0 : a / r, s = r == 0.0 ? 0.0 : b / r;
+    st->cs[j] = c;
+    st->sn[j] = s;
+    Hc[j] = r;
+    Hc[j + 1] = 0.0;
+    const double gj = st->g[j];
+    st->g[j + 1] = -s * gj;
+    st->g[j] = c * gj;
+    st->scale[j + 1] = wn > 0.0 ? 1.0 / wn : 0.0;
+    st->its += 1;
+    st->j = j + 1;
+    st->pending = 1;
+    const bool bad = !isfinite(wn) || !isfinite(r);
+    if (bad) st->nonfinite = 1;
+    const double est = fabs(s * gj);
+    const bool breakdown = !(wn > 1e-300) || !(r > 0.0);
+    if (bad || est <= st->tol * st->bnorm || j + 1 >= st->m || st->its >= st->max_it || breakdown) st->active = 0;
+}
+
 
 // Multi-dot r_d = <V_d, V_{j+1}>, d <= dlast (pass 1: dlast = j+1, the last
 // one being the squared norm; pass 2: dlast = j).  One 1024-thread block per
@@ -195,7 +229,7 @@ __global__ void __launch_bounds__(GM_TX* GM_TY) k_gm_dots(const TV* __restrict__
     using VT = typename Vec<TV>::T;
     constexpr int W = Vec<TV>::W;
     const int j = st->j;
-    const int dlast = pass == 1 ? j + 1 : j;
+    const int dlast = j + 1;            // V_0..V_j and w itself
     const int tx = threadIdx.x, ty = threadIdx.y;
     const VT* __restrict__ w = reinterpret_cast<const VT*>(V + (long)(j + 1) * ld);
     Acc<TV> acc[GM_DPT];
@@ -241,6 +275,7 @@ __global__ void __launch_bounds__(GM_TX* GM_TY) k_gm_dots(const TV* __restrict__
     }
     if (!last_block(&st->arrive)) return;
     // 16 threads per dot: thread t sums partials t%16, t%16+16, ... of dot t/16
+    __shared__ double hp[DG_MAXM + 2], hc[DG_MAXM + 2], css[DG_MAXM], sns[DG_MAXM];
     const int t = ty * GM_TX + tx;
     for (int d0 = 0; d0 <= dlast; d0 += (GM_TX * GM_TY) / 16) {
         const int d = d0 + t / 16;
@@ -253,65 +288,52 @@ __global__ void __launch_bounds__(GM_TX* GM_TY) k_gm_dots(const TV* __restrict__
         for (int o = 8; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
         if ((t % 16) == 0 && d <= dlast) {
             if (d == j + 1) {
-                st->wn2_before = r;
+                hp[d] = r;                    // ||w||^2
             } else {
                 const double hd = st->scale[d] * r;
-                st->hcol[d] = pass == 1 ? hd : st->hcol[d] + hd;
+                hp[d] = hd;
+                const double h = pass == 1 ? hd : st->hcol[d] + hd;
+                st->hcol[d] = h;
+                hc[d] = h;
                 st->coef[d] = hd * st->scale[d];
             }
         }
     }
-}
-
-// Givens / Hessenberg step for column j; runs in thread 0 of the last block
-// with the column and the previous rotations staged in shared memory.
-__device__ void gm_finish_column(GmresState* st, double wn, const double* hc, const double* cs, const double* sn) {
-    const int j = st->j;
-    const int LD = DG_MAXM + 1;
-    double* Hc = st->H + (long)j * LD;
-    double a = hc[0];
-    for (int i = 0; i < j; ++i) {
-        const double b = hc[i + 1];
-        Hc[i] = cs[i] * a + sn[i] * b;
-        a = -sn[i] * a + cs[i] * b;
+    for (int i = t; i < j; i += GM_TX * GM_TY) {
+        css[i] = st->cs[i];
+        sns[i] = st->sn[i];
     }
-    const double b = wn;
-    const double r = hypot(a, b);
-    const double c = r == 0.0 ? 1.0 : a / r, s = r == 0.0 ? 0.0 : b / r;
-    st->cs[j] = c;
-    st->sn[j] = s;
-    Hc[j] = r;
-    Hc[j + 1] = 0.0;
-    const double gj = st->g[j];
-    st->g[j + 1] = -s * gj;
-    st->g[j] = c * gj;
-    st->scale[j + 1] = wn > 0.0 ? 1.0 / wn : 0.0;
-    st->its += 1;
-    st->j = j + 1;
-    st->pending = 1;
-    const bool bad = !isfinite(wn) || !isfinite(r);
-    if (bad) st->nonfinite = 1;
-    const double est = fabs(s * gj);
-    const bool breakdown = !(wn > 1e-300) || !(r > 0.0);
-    if (bad || est <= st->tol * st->bnorm || j + 1 >= st->m || st->its >= st->max_it || breakdown) st->active = 0;
+    __syncthreads();
+    if (t != 0) return;
+    // norm of w - sum h_d v_d without another pass: ||w||^2 - sum h_d^2 (the
+    // v_d are orthonormal).  Accepted when at least 0.49 ||w||^2 remains (at
+    // most a factor 2 of cancellation); otherwise a second Gram-Schmidt pass
+    // runs and its own self-dot gives the norm exactly.
+    const double w2 = hp[j + 1];
+    double s2 = 0.0;
+    for (int d = 0; d <= j; ++d) s2 = fma(hp[d], hp[d], s2);
+    const double rest = w2 - s2;
+    st->jw = j;
+    if (pass == 1) {
+        const bool again = !(rest >= 0.49 * w2);
+        st->reorth = again ? 1 : 0;
+        if (again) return;
+    }
+    gm_finish_column(st, sqrt(rest > 0.0 ? rest : 0.0), hc, css, sns);
 }
 
-// V_{j+1} -= sum_{d<=j} coef_d V_d ; ||V_{j+1}||^2.  Last block: norm,
-// re-orthogonalisation decision, Hessenberg/Givens step.
+// V_{j+1} -= sum_{d<=j} coef_d V_d for the column j = jw the multi-dot kernel
+// prepared (its tail already took the Givens step, or asked for a second pass).
 template <typename TV>
-__global__ void __launch_bounds__(256) k_gm_update(TV* V, long ld, long nvec, GmresState* st, double* partials,
-                                                    int pass) {
+__global__ void __launch_bounds__(256) k_gm_update(TV* V, long ld, long nvec, GmresState* st, int pass) {
     if (!st->active || (pass == 2 && !st->reorth)) return;
     using VT = typename Vec<TV>::T;
     constexpr int W = Vec<TV>::W;
     __shared__ TV c[DG_MAXM + 2];
-    __shared__ double sh[32];
-    __shared__ double hc[DG_MAXM + 2], css[DG_MAXM], sns[DG_MAXM];
-    const int j = st->j;
+    const int j = st->jw;
     for (int d = threadIdx.x; d <= j; d += blockDim.x) c[d] = (TV)st->coef[d];
     __syncthreads();
     VT* w = reinterpret_cast<VT*>(V + (long)(j + 1) * ld);   // aliases V: no __restrict__
-    Acc<TV> nrm;
     for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < nvec; q += (long)gridDim.x * blockDim.x) {
         VT acc = w[q];
         int d = 0;
@@ -331,29 +353,7 @@ __global__ void __launch_bounds__(256) k_gm_update(TV* V, long ld, long nvec, Gm
             for (int i = 0; i < W; ++i) Vec<TV>::set(acc, i, ::fma(-c[d], Vec<TV>::get(v, i), Vec<TV>::get(acc, i)));
         }
         w[q] = acc;
-#pragma unroll
-        for (int i = 0; i < W; ++i) nrm.fma(Vec<TV>::get(acc, i), Vec<TV>::get(acc, i));
     }
-    const double v = dg_block_sum(nrm.get(), sh);
-    if (threadIdx.x == 0) partials[blockIdx.x] = v;
-    if (!last_block(&st->arrive)) return;
-    const double wn2 = sum_partials(partials, gridDim.x, sh);
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-        hc[i] = st->hcol[i];
-        if (i < j) {
-            css[i] = st->cs[i];
-            sns[i] = st->sn[i];
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x != 0) return;
-    const double wn = sqrt(wn2);
-    if (pass == 1 && wn < 0.7 * sqrt(st->wn2_before)) {
-        st->reorth = 1;
-        return;
-    }
-    st->reorth = 0;
-    gm_finish_column(st, wn, hc, css, sns);
 }
 
 // y = H(0:jj,0:jj)^-1 g(0:jj) by column-oriented back substitution in shared
@@ -505,7 +505,7 @@ static int enqueue_cycle(dg_handle* h, GmresWork& W, const TA* A, const TB* B, c
         }
         for (int pass = 1; pass <= 2; ++pass) {
             k_gm_dots<TV><<<gdots, bdots, 0, h->stream>>>(V, ld, nvec, st, W.partials, pass);
-            k_gm_update<TV><<<gx, 256, 0, h->stream>>>(V, ld, nvec, st, W.partials, pass);
+            k_gm_update<TV><<<gx, 256, 0, h->stream>>>(V, ld, nvec, st, pass);
         }
     }
     DevCtl pend{&st->pending, nullptr};
@@ -899,7 +899,7 @@ static dg_status gmres_ir_run(dg_handle* h, const TA* Alo, const double* F, doub
             for (int pass = 1; pass <= 2; ++pass) {
                 k_gm_dots<double><<<W.gsm, dim3(GM_TX, GM_TY), 0, h->stream>>>(V, (long)ld, nvec, st, W.partials,
                                                                                pass);
-                k_gm_update<double><<<gx, 256, 0, h->stream>>>(V, (long)ld, nvec, st, W.partials, pass);
+                k_gm_update<double><<<gx, 256, 0, h->stream>>>(V, (long)ld, nvec, st, pass);
             }
             h->nlaunch += 6;
             DG_LAUNCH_CK(h);
@@ -979,6 +979,7 @@ __global__ void k_prof_state(GmresState* st, int j, int m) {
     st->bnorm = 1.0;
     st->wn2_before = 0.0;
     st->arrive = 0;
+    st->jw = j;
     for (int i = 0; i <= m + 1; ++i) {
         st->scale[i] = 1.0;
         st->hcol[i] = 1e-3;
@@ -1018,7 +1019,7 @@ static dg_status profile_arnoldi(dg_handle* h, int which, int j, int reps, doubl
             k_gm_dots<TV><<<W.gsm, dim3(GM_TX, GM_TY), 0, h->stream>>>((const TV*)W.V, (long)W.ld, nvec, W.st,
                                                                          W.partials, 1);
         else
-            k_gm_update<TV><<<W.gx, 256, 0, h->stream>>>((TV*)W.V, (long)W.ld, nvec, W.st, W.partials, 1);
+            k_gm_update<TV><<<W.gx, 256, 0, h->stream>>>((TV*)W.V, (long)W.ld, nvec, W.st, 1);
         DG_CK(h, cudaEventRecord(e1, h->stream));
         DG_CK(h, cudaEventSynchronize(e1));
         float ms = 0.f;
