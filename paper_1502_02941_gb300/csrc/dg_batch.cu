@@ -181,58 +181,6 @@ __global__ void __launch_bounds__(256) k_b_init(const TV* __restrict__ F, TV* __
     }
 }
 
-// Segmented multi-dot: per item, r_d = <V_d, V_{j+1}> over the item's range.
-template <typename TV>
-__global__ void __launch_bounds__(B_TX* B_TY) k_b_dots(const TV* __restrict__ V, long ld, BatchDev B, int pass) {
-    const int j = *B.jglob;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int t = ty * B_TX + tx;
-    for (int it = blockIdx.x; it < B.nit; it += gridDim.x) {
-        const int inst = B.item_inst[it];
-        BState* st = B.bst + inst;
-        if (!B.iactive[inst] || (pass == 2 && !st->reorth)) continue;
-        const int dlast = pass == 1 ? j + 1 : j;
-        const TV* __restrict__ w = V + (long)(j + 1) * ld;
-        BAcc<TV> acc[B_DPT];
-        const int lo = B.item_lo[it], hi = B.item_hi[it];
-        for (int l = lo + tx; l < hi; l += B_TX) {
-            const TV wl = w[l];
-#pragma unroll
-            for (int k = 0; k < B_DPT; ++k) {
-                const int d = ty + B_TY * k;
-                if (d <= dlast) acc[k].fma(V[(long)d * ld + l], wl);
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < B_DPT; ++k) {
-            const int d = ty + B_TY * k;
-            const double v = dg_warp_sum(acc[k].get());
-            if (tx == 0 && d <= dlast) B.partials[(long)it * (DG_MAXM + 2) + d] = v;
-        }
-        if (!inst_last(&st->arrive, B.inst_item_hi[inst] - B.inst_item_lo[inst])) continue;
-        // 16 threads per dot over the instance's items
-        const int ilo = B.inst_item_lo[inst], ihi = B.inst_item_hi[inst];
-        for (int d0 = 0; d0 <= dlast; d0 += (B_TX * B_TY) / 16) {
-            const int d = d0 + t / 16;
-            double r = 0.0;
-            if (d <= dlast)
-                for (int i2 = ilo + t % 16; i2 < ihi; i2 += 16) r += __ldcg(B.partials + (long)i2 * (DG_MAXM + 2) + d);
-#pragma unroll
-            for (int o = 8; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
-            if ((t % 16) == 0 && d <= dlast) {
-                if (d == j + 1) {
-                    st->wn2_before = r;
-                } else {
-                    const double hd = st->scale[d] * r;
-                    st->hcol[d] = pass == 1 ? hd : st->hcol[d] + hd;
-                    st->coef[d] = hd * st->scale[d];
-                }
-            }
-        }
-        __syncthreads();
-    }
-}
-
 __device__ void b_finish_column(BatchDev& B, int inst, int j, double wn, const double* hc, const double* cs,
                                 const double* sn) {
     BState* st = B.bst + inst;
@@ -267,14 +215,89 @@ __device__ void b_finish_column(BatchDev& B, int inst, int j, double wn, const d
         B.iactive[inst] = 0;
 }
 
-// Segmented update: V_{j+1} -= sum_d coef_d V_d on each item; norm; last item
-// of the instance: re-orthogonalisation decision or Hessenberg/Givens step.
+// Segmented multi-dot: per item, r_d = <V_d, V_{j+1}> over the item's range,
+// d = 0..j+1 (the last one is ||w||^2).  Last item of an instance: h_d, the
+// norm ||w||^2 - sum h_d^2 and either the Givens step or a request for a
+// second Gram-Schmidt pass (less than 0.49 ||w||^2 left), as in dg_gmres.cu.
+template <typename TV>
+__global__ void __launch_bounds__(B_TX* B_TY) k_b_dots(const TV* __restrict__ V, long ld, BatchDev B, int pass) {
+    const int j = *B.jglob;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int t = ty * B_TX + tx;
+    __shared__ double hp[DG_MAXM + 2], hc[DG_MAXM + 2], css[DG_MAXM], sns[DG_MAXM];
+    for (int it = blockIdx.x; it < B.nit; it += gridDim.x) {
+        const int inst = B.item_inst[it];
+        BState* st = B.bst + inst;
+        if (!B.iactive[inst] || (pass == 2 && !st->reorth)) continue;
+        const int dlast = j + 1;
+        const TV* __restrict__ w = V + (long)(j + 1) * ld;
+        BAcc<TV> acc[B_DPT];
+        const int lo = B.item_lo[it], hi = B.item_hi[it];
+        for (int l = lo + tx; l < hi; l += B_TX) {
+            const TV wl = w[l];
+#pragma unroll
+            for (int k = 0; k < B_DPT; ++k) {
+                const int d = ty + B_TY * k;
+                if (d <= dlast) acc[k].fma(V[(long)d * ld + l], wl);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < B_DPT; ++k) {
+            const int d = ty + B_TY * k;
+            const double v = dg_warp_sum(acc[k].get());
+            if (tx == 0 && d <= dlast) B.partials[(long)it * (DG_MAXM + 2) + d] = v;
+        }
+        if (!inst_last(&st->arrive, B.inst_item_hi[inst] - B.inst_item_lo[inst])) continue;
+        // 16 threads per dot over the instance's items
+        const int ilo = B.inst_item_lo[inst], ihi = B.inst_item_hi[inst];
+        for (int d0 = 0; d0 <= dlast; d0 += (B_TX * B_TY) / 16) {
+            const int d = d0 + t / 16;
+            double r = 0.0;
+            if (d <= dlast)
+                for (int i2 = ilo + t % 16; i2 < ihi; i2 += 16) r += __ldcg(B.partials + (long)i2 * (DG_MAXM + 2) + d);
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+            if ((t % 16) == 0 && d <= dlast) {
+                if (d == j + 1) {
+                    hp[d] = r;
+                } else {
+                    const double hd = st->scale[d] * r;
+                    hp[d] = hd;
+                    const double h = pass == 1 ? hd : st->hcol[d] + hd;
+                    st->hcol[d] = h;
+                    hc[d] = h;
+                    st->coef[d] = hd * st->scale[d];
+                }
+            }
+        }
+        for (int i = t; i < j; i += B_TX * B_TY) {
+            css[i] = st->cs[i];
+            sns[i] = st->sn[i];
+        }
+        __syncthreads();
+        if (t == 0) {
+            const double w2 = hp[j + 1];
+            double s2 = 0.0;
+            for (int d = 0; d <= j; ++d) s2 = ::fma(hp[d], hp[d], s2);
+            const double rest = w2 - s2;
+            bool ready = true;
+            if (pass == 1) {
+                const bool again = !(rest >= 0.49 * w2);
+                st->reorth = again ? 1 : 0;
+                ready = !again;
+            }
+            if (ready) b_finish_column(B, inst, j, sqrt(rest > 0.0 ? rest : 0.0), hc, css, sns);
+        }
+        __syncthreads();
+    }
+}
+
+// Segmented update: V_{j+1} -= sum_d coef_d V_d on each item (the multi-dot
+// kernel already took the Givens step or asked for a second pass).
 template <typename TV>
 __global__ void __launch_bounds__(256) k_b_update(TV* V, long ld, BatchDev B, int pass) {
     const int j = *B.jglob;
     __shared__ TV c[DG_MAXM + 2];
-    __shared__ double sh[32];
-    __shared__ double hc[DG_MAXM + 2], css[DG_MAXM], sns[DG_MAXM];
     for (int it = blockIdx.x; it < B.nit; it += gridDim.x) {
         const int inst = B.item_inst[it];
         BState* st = B.bst + inst;
@@ -283,7 +306,6 @@ __global__ void __launch_bounds__(256) k_b_update(TV* V, long ld, BatchDev B, in
         for (int d = threadIdx.x; d <= j; d += blockDim.x) c[d] = (TV)st->coef[d];
         __syncthreads();
         TV* w = V + (long)(j + 1) * ld;
-        double nrm = 0.0;
         for (int l = B.item_lo[it] + threadIdx.x; l < B.item_hi[it]; l += blockDim.x) {
             TV acc = w[l];
             int d = 0;
@@ -297,30 +319,7 @@ __global__ void __launch_bounds__(256) k_b_update(TV* V, long ld, BatchDev B, in
             }
             for (; d <= j; ++d) acc = ::fma(-c[d], V[(long)d * ld + l], acc);
             w[l] = acc;
-            nrm = ::fma((double)acc, (double)acc, nrm);
         }
-        nrm = dg_block_sum(nrm, sh);
-        if (threadIdx.x == 0) B.partials[(long)it * (DG_MAXM + 2)] = nrm;
-        if (!inst_last(&st->arrive, B.inst_item_hi[inst] - B.inst_item_lo[inst])) continue;
-        const double wn2 = inst_sum(B, inst, 0, sh);
-        for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-            hc[i] = st->hcol[i];
-            if (i < j) {
-                css[i] = st->cs[i];
-                sns[i] = st->sn[i];
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const double wn = sqrt(wn2);
-            if (pass == 1 && wn < 0.7 * sqrt(st->wn2_before)) {
-                st->reorth = 1;
-            } else {
-                st->reorth = 0;
-                b_finish_column(B, inst, j, wn, hc, css, sns);
-            }
-        }
-        __syncthreads();
     }
 }
 

@@ -392,3 +392,28 @@ def test_gmres_refinement_converges_where_bf16_refinement_stalls():
     rr = (torch.linalg.norm(F - h.apply(xg)) / torch.linalg.norm(F)).item()
     assert rr <= 1.5e-10
     h.close()
+
+
+@pytest.mark.parametrize("solver", ["f64", "batch"])
+def test_gmres_lucky_breakdown_on_block_diagonal_operator(solver):
+    """eps = 0, b = 0: the operator is alpha times the block-diagonal mass
+    matrix, block Jacobi inverts it exactly, so GMRES stops after one Arnoldi
+    step through the breakdown path (the orthogonalised vector vanishes) with
+    x = A^-1 F, the L2 projection of f / alpha."""
+    prob = W.Problem("react", 0.0, 2.0, (0,) * 6, W.sinsin)
+    ma = W.perturbed_mesh(6, seed=4)
+    h = gpu_setup(ma, 2, 2, prob, tol=1e-12)
+    h.precond_setup()
+    xb = h.precond_apply(h.rhs(), D.DG_F64)
+    if solver == "f64":
+        x, info = h.gmres_solve()
+        its, st = info.iterations, info.status
+    else:
+        h.batch_setup(np.array([0, ma.ne], np.int32), np.array([[0.0, 2.0, 0, 0, 0, 0, 0, 0]]))
+        h.assemble(0.0, 2.0, (0,) * 6, *problem.problem_data(h, prob))
+        h.precond_setup()
+        x, its_a, rr, st_a = h.batch_solve(D.DG_F64)
+        its, st = int(its_a[0]), int(st_a[0])
+    assert st == D.DG_OK and its == 1
+    np.testing.assert_allclose(_np(x), _np(xb), rtol=1e-12, atol=1e-14 * np.abs(_np(xb)).max())
+    h.close()
