@@ -234,8 +234,15 @@ __global__ void __launch_bounds__(GM_TX* GM_TY) k_gm_dots(const TV* __restrict__
     const VT* __restrict__ w = reinterpret_cast<const VT*>(V + (long)(j + 1) * ld);
     Acc<TV> acc[GM_DPT];
     const long nchunk = (nvec + GM_TX - 1) / GM_TX;
-    const long step = gridDim.x;
-    for (long c = blockIdx.x; c < nchunk; c += 4 * step) {
+    // with at most 16 dots, nsub = 32 / ncol warps share each dot (interleaved
+    // chunks), so every warp streams whatever the step j
+    const int ncol = dlast + 1;
+    const int nsub = ncol <= GM_TY / 2 ? GM_TY / ncol : 1;
+    const int dsel = nsub > 1 ? ty % ncol : ty;
+    const int sub = nsub > 1 ? ty / ncol : 0;
+    const bool live = ty < ncol * nsub || nsub == 1;
+    const long step = (long)gridDim.x * nsub;
+    for (long c = blockIdx.x + (long)sub * gridDim.x; live && c < nchunk; c += 4 * step) {
         VT wv[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -247,7 +254,7 @@ __global__ void __launch_bounds__(GM_TX* GM_TY) k_gm_dots(const TV* __restrict__
         }
 #pragma unroll
         for (int k = 0; k < GM_DPT; ++k) {
-            const int d = ty + GM_TY * k;
+            const int d = dsel + GM_TY * k;
             if (d <= dlast) {
                 const VT* __restrict__ vd = reinterpret_cast<const VT*>(V + (long)d * ld);
                 VT v[4];
@@ -267,11 +274,24 @@ __global__ void __launch_bounds__(GM_TX* GM_TY) k_gm_dots(const TV* __restrict__
         }
     }
     const int gx = gridDim.x;
+    if (nsub > 1) {
+        __shared__ double ws[GM_TY];
+        const double v = dg_warp_sum(acc[0].get());
+        if (tx == 0) ws[ty] = live ? v : 0.0;
+        __syncthreads();
+        const int t0 = ty * GM_TX + tx;
+        if (t0 < ncol) {
+            double r = 0.0;
+            for (int u = 0; u < nsub; ++u) r += ws[t0 + u * ncol];
+            partials[(long)t0 * gx + blockIdx.x] = r;
+        }
+    } else {
 #pragma unroll
-    for (int k = 0; k < GM_DPT; ++k) {
-        const int d = ty + GM_TY * k;
-        const double v = dg_warp_sum(acc[k].get());
-        if (tx == 0 && d <= dlast) partials[(long)d * gx + blockIdx.x] = v;
+        for (int k = 0; k < GM_DPT; ++k) {
+            const int d = ty + GM_TY * k;
+            const double v = dg_warp_sum(acc[k].get());
+            if (tx == 0 && d <= dlast) partials[(long)d * gx + blockIdx.x] = v;
+        }
     }
     if (!last_block(&st->arrive)) return;
     // 16 threads per dot: thread t sums partials t%16, t%16+16, ... of dot t/16
