@@ -67,6 +67,65 @@ __global__ void __launch_bounds__(128) k_bj_setup(const TA* __restrict__ A, int 
         }
 }
 
+// Block (K, slot s) of A M^-1: A_{K,s} Binv_L with L = K (s = 0) or the
+// neighbour across face s-1, in f64; zero for a missing neighbour.  One thread
+// per (element, slot); writes the requested copies.
+template <int NB>
+__global__ void __launch_bounds__(128) k_ahat_setup(const double* __restrict__ A, const double* __restrict__ Binv,
+                                                     const int* __restrict__ nbr, int ne, double* Ah64, float* Ah32,
+                                                     __nv_bfloat16* Ah16) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 4L * ne) return;
+    const int K = (int)(t >> 2), s = (int)(t & 3);
+    const int L = s == 0 ? K : __ldg(nbr + (size_t)(s - 1) * ne + K);
+    double a[NB][NB], b[NB][NB];
+    for (int i = 0; i < NB; ++i)
+        for (int j = 0; j < NB; ++j) {
+            a[i][j] = L >= 0 ? A[dg_blk_index<double>(K, s, i * NB + j, NB, 4)] : 0.0;
+            b[i][j] = L >= 0 ? Binv[dg_blk_index<double>(L, 0, i * NB + j, NB, 1)] : 0.0;
+        }
+    for (int i = 0; i < NB; ++i)
+        for (int j = 0; j < NB; ++j) {
+            double c = 0.0;
+            for (int l = 0; l < NB; ++l) c = fma(a[i][l], b[l][j], c);
+            const int m = i * NB + j;
+            if (Ah64) Ah64[dg_blk_index<double>(K, s, m, NB, 4)] = c;
+            if (Ah32) Ah32[dg_blk_index<float>(K, s, m, NB, 4)] = (float)c;
+            if (Ah16) Ah16[dg_blk_index<__nv_bfloat16>(K, s, m, NB, 4)] = __double2bfloat16(c);
+        }
+}
+
+// A M^-1 for every stored precision (after the f64 inverses exist).  The
+// arrays are cleared first, so chunk padding and padding lanes stay zero.
+static dg_status ahat_setup(dg_handle* h) {
+    const int nb = dg_nb(h->asm_k);
+    const size_t per = (size_t)h->ntiles * 4 * 16 * 32;   // bytes per chunk row x chunks below
+    size_t need[3] = {0, 0, 0};
+    if (h->A64) need[0] = per * dg_chunks<double>(nb);
+    if (h->A32) need[1] = per * dg_chunks<float>(nb);
+    // no bf16 copy: the bf16 inner solves keep block Jacobi on the bf16 blocks,
+    // whose true residual they are checked against
+    void** ptrs[3] = {(void**)&h->Ah64, (void**)&h->Ah32, (void**)&h->Ah16};
+    dg_status s;
+    for (int t = 0; t < 3; ++t) {
+        if (need[t] != h->Ah_bytes[t]) {
+            if ((s = dg_realloc(h, ptrs[t], need[t])) != DG_OK) return s;
+            h->Ah_bytes[t] = need[t];
+        }
+        if (need[t]) DG_CK(h, cudaMemsetAsync(*ptrs[t], 0, need[t], h->stream));
+    }
+    const unsigned g = (unsigned)((4L * h->ne + 127) / 128);
+    switch (nb) {
+        case 3: k_ahat_setup<3><<<g, 128, 0, h->stream>>>(h->A64, h->Binv64, h->nbr, h->ne, h->Ah64, h->Ah32, h->Ah16); break;
+        case 6: k_ahat_setup<6><<<g, 128, 0, h->stream>>>(h->A64, h->Binv64, h->nbr, h->ne, h->Ah64, h->Ah32, h->Ah16); break;
+        case 10: k_ahat_setup<10><<<g, 128, 0, h->stream>>>(h->A64, h->Binv64, h->nbr, h->ne, h->Ah64, h->Ah32, h->Ah16); break;
+        default: return dg_fail(h, DG_ERR_INVALID_ARG, "degree");
+    }
+    h->nlaunch += 1;
+    DG_LAUNCH_CK(h);
+    return DG_OK;
+}
+
 // ---------------------------------------------------------------------------
 // dispatch
 // ---------------------------------------------------------------------------
@@ -182,7 +241,7 @@ dg_status dg_launch_bj_setup(dg_handle* h) {
     DG_CK(h, cudaMemcpyAsync(&flag, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     DG_CK(h, cudaStreamSynchronize(h->stream));
     if (flag) return dg_fail(h, DG_ERR_SINGULAR_BLOCK, "a diagonal block is singular");
-    return DG_OK;
+    return ahat_setup(h);
 }
 
 extern "C" dg_status dg_precond_setup(dg_handle* h, int kind) {

@@ -495,7 +495,8 @@ static void launch_bj(dg_handle* h, const TB* B, const TV* r, TV* z, DevCtl ctl,
 // One restart cycle: m Arnoldi steps, the correction and the true residual.
 // Returns the number of kernels enqueued.
 template <int NB, typename TA, typename TB, typename TV>
-static int enqueue_cycle(dg_handle* h, GmresWork& W, const TA* A, const TB* B, const TV* F, TV* x, bool flex) {
+static int enqueue_cycle(dg_handle* h, GmresWork& W, const TA* A, const TB* B, const TV* F, TV* x, bool flex,
+                         const TA* Ah) {
     TV* V = (TV*)W.V;
     TV* Z = (TV*)W.Z;
     TV* R = (TV*)W.R;
@@ -519,6 +520,10 @@ static int enqueue_cycle(dg_handle* h, GmresWork& W, const TA* A, const TB* B, c
             dg_mlp_correct<TV>(h, V, Zb, step, vj, zj, nullptr);
             launch_apply<NB, TA, TV>(h, A, Zb, V, step_noscale, zj, vj1);
             ++extra;
+        } else if (Ah) {
+            // V_{j+1} = s_j (A M^-1) V_j: one apply of the precomputed operator
+            launch_apply<NB, TA, TV>(h, Ah, V, V, step, vj, vj1);
+            --extra;
         } else {
             launch_bj<NB, TB, TV>(h, B, V, Z, step, vj, vsel_fixed());
             launch_apply<NB, TA, TV>(h, A, Z, V, step_noscale, vsel_fixed(), vj1);
@@ -592,10 +597,19 @@ static dg_status ensure_workspace(dg_handle* h, GmresWork& W, long n, int m, siz
     return DG_OK;
 }
 
-// Run restarted GMRES(m) to `tol` on (A, M = B) from x0 = 0.
+// The precomputed A M^-1 of the block copy of type T (NULL if not stored).
+template <typename T>
+static const T* ahat_of(const dg_handle* h) {
+    if constexpr (sizeof(T) == 8) return h->Ah64;
+    else if constexpr (sizeof(T) == 4) return h->Ah32;
+    else return nullptr;
+}
+
+// Run restarted GMRES(m) to `tol` on (A, M = B) from x0 = 0; with Ah = A M^-1
+// given (block Jacobi), each Arnoldi step is one apply of Ah.
 template <int NB, typename TA, typename TB, typename TV>
 static dg_status gmres_run(dg_handle* h, GmresWork& W, const TA* A, const TB* B, const TV* F, TV* x, int m,
-                           double tol, int max_it, dg_solve_info* info, bool flex = false) {
+                           double tol, int max_it, dg_solve_info* info, bool flex = false, const TA* Ah = nullptr) {
     const long n = (long)h->ne * NB;
     dg_status s = ensure_workspace(h, W, n, m, sizeof(TV));
     if (s != DG_OK) return s;
@@ -608,8 +622,9 @@ static dg_status gmres_run(dg_handle* h, GmresWork& W, const TA* A, const TB* B,
     DG_LAUNCH_CK(h);
     DG_CK(h, cudaMemcpyAsync(W.st_host, W.st, GM_HDR, cudaMemcpyDeviceToHost, h->stream));
     DG_CK(h, cudaStreamSynchronize(h->stream));
-    const uintptr_t key[6] = {(uintptr_t)x, (uintptr_t)F, (uintptr_t)A, (uintptr_t)B,
-                              (uintptr_t)m | ((uintptr_t)flex << 20), (uintptr_t)h->stream};
+    if (flex || !B) Ah = nullptr;
+    const uintptr_t key[7] = {(uintptr_t)x, (uintptr_t)F, (uintptr_t)A, (uintptr_t)B,
+                              (uintptr_t)m | ((uintptr_t)flex << 20), (uintptr_t)h->stream, (uintptr_t)Ah};
     if (W.graph && memcmp(key, W.key, sizeof(key)) != 0) {
         cudaGraphExecDestroy(W.graph);
         W.graph = nullptr;
@@ -618,7 +633,7 @@ static dg_status gmres_run(dg_handle* h, GmresWork& W, const TA* A, const TB* B,
     if (use_graph && !W.graph && !W.st_host->done) {
         cudaGraph_t g;
         DG_CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-        W.nodes = enqueue_cycle<NB, TA, TB, TV>(h, W, A, B, F, x, flex);
+        W.nodes = enqueue_cycle<NB, TA, TB, TV>(h, W, A, B, F, x, flex, Ah);
         DG_CK(h, cudaStreamEndCapture(h->stream, &g));
         cudaError_t e = cudaGraphInstantiate(&W.graph, g, 0);
         cudaGraphDestroy(g);
@@ -633,7 +648,7 @@ static dg_status gmres_run(dg_handle* h, GmresWork& W, const TA* A, const TB* B,
             DG_CK(h, cudaGraphLaunch(W.graph, h->stream));
             h->nlaunch += W.nodes;
         } else {
-            h->nlaunch += enqueue_cycle<NB, TA, TB, TV>(h, W, A, B, F, x, flex);
+            h->nlaunch += enqueue_cycle<NB, TA, TB, TV>(h, W, A, B, F, x, flex, Ah);
         }
         DG_LAUNCH_CK(h);
         DG_CK(h, cudaStreamSynchronize(h->stream));
@@ -674,7 +689,7 @@ static dg_status gmres_f64(dg_handle* h, const double* F, double* x, dg_solve_in
         DG_CK(h, cudaMemcpyAsync(h->mlp.on, &one, sizeof(int), cudaMemcpyHostToDevice, h->stream));
     }
     const dg_status s = gmres_run<NB, double, double, double>(h, h->gw[0], h->A64, B, F, x, h->p.gmres_m, h->p.tol,
-                                                              h->p.max_it, info, mlp);
+                                                              h->p.max_it, info, mlp, h->Ah64);
     if (h->gw[0].V) {
         h->basis = (const double*)h->gw[0].V;
         h->basis_ld = h->gw[0].ld;
@@ -795,7 +810,8 @@ static dg_status mixed_run(dg_handle* h, const TA* Alo, const double* F, double*
         // cycles: past that the low-precision GMRES is at its accuracy floor
         // and a fresh f64 residual serves better than more inner steps
         const int cap = std::min(h->p.max_it - inner_total, DG_INNER_CYCLES * inner_m);
-        s = gmres_run<NB, TA, float, float>(h, h->gw[1], Alo, B32, r32, d32, inner_m, inner_tol, cap, &in);
+        s = gmres_run<NB, TA, float, float>(h, h->gw[1], Alo, B32, r32, d32, inner_m, inner_tol, cap, &in, false,
+                                                ahat_of<TA>(h));
         if (s != DG_OK && s != DG_NOT_CONVERGED) return s;
         inner_total += in.iterations;
         k_mx_update<<<gx, 256, 0, h->stream>>>(x, d32, n, ms);
@@ -909,7 +925,8 @@ static dg_status gmres_ir_run(dg_handle* h, const TA* Alo, const double* F, doub
             h->nlaunch += 1;
             dg_solve_info in{};
             const int cap = std::min(h->p.max_it - inner_total, DG_INNER_CYCLES * inner_m);
-            s = gmres_run<NB, TA, float, float>(h, h->gw[1], Alo, B32, r32, d32, inner_m, inner_tol, cap, &in);
+            s = gmres_run<NB, TA, float, float>(h, h->gw[1], Alo, B32, r32, d32, inner_m, inner_tol, cap, &in, false,
+                                                ahat_of<TA>(h));
             if (s != DG_OK && s != DG_NOT_CONVERGED) return s;
             inner_total += in.iterations;
             k_ir_up<<<gx, 256, 0, h->stream>>>(d32, Zb + (size_t)j * ld, n, st->scale + j);

@@ -103,7 +103,7 @@ struct GmresWork {
     GmresState* st = nullptr;      // device state
     GmresState* st_host = nullptr; // pinned mirror of the state header
     cudaGraphExec_t graph = nullptr;
-    uintptr_t key[6] = {0, 0, 0, 0, 0, 0};
+    uintptr_t key[7] = {0, 0, 0, 0, 0, 0};
     int nodes = 0;
     int gx = 0;    // grid of the 1-D vector kernels (4 blocks of 256 per SM)
     int gsm = 0;   // grid of the multi-dot kernel (one 1024-thread block per SM)
@@ -149,6 +149,13 @@ struct dg_handle {
     double* Binv64 = nullptr;
     float* Binv32 = nullptr;
     float* Binv16 = nullptr;       // inverses of the bf16 diagonal blocks (f32)
+    // the right-preconditioned operator A M_BJ^-1 (block-ELL, 4 slots: block
+    // (K, L) = A_KL A_LL^-1, computed in f64), f64 and f32 copies (Ah16 stays
+    // NULL): a GMRES step with block Jacobi is then one apply
+    double* Ah64 = nullptr;
+    float* Ah32 = nullptr;
+    __nv_bfloat16* Ah16 = nullptr;
+    size_t Ah_bytes[3] = {0, 0, 0};
 
     // GMRES workspaces: [0] the f64 solver, [1] the f32 inner solver of the
     // mixed-precision refinement

@@ -124,7 +124,9 @@ __device__ __forceinline__ void store_y(TX* __restrict__ y, int K, const TACC* v
 
 // y = A x over elements [0, ne).  nbr is [3][ne].  With a solver control
 // block, the kernel exits at once when the solver is inactive and x / y are
-// picked from the Krylov basis by the device-side step counter.
+// picked from the Krylov basis by the device-side step counter; with
+// ctl.scale set, y is multiplied by the scale factor of the selected x (the
+// lazily normalised basis vector).
 template <int NB, typename TA, typename TX, typename TACC>
 __global__ void __launch_bounds__(256) k_apply(const TA* __restrict__ A, const int* __restrict__ nbr,
                                                 const TX* __restrict__ x0, TX* __restrict__ y0, int ne,
@@ -163,6 +165,11 @@ __global__ void __launch_bounds__(256) k_apply(const TA* __restrict__ A, const i
                 if (m < NB * NB) acc[m / NB] = fma(v[w], xv[m % NB], acc[m / NB]);
             }
         }
+    }
+    if (ctl.scale && !ctl.inst) {
+        const TACC sc = (TACC)ctl.scale[sx.j ? *sx.j + sx.add : 0];
+#pragma unroll
+        for (int r = 0; r < NB; ++r) acc[r] *= sc;
     }
     store_y<NB, TX, TACC>(y, K, acc);
 }
