@@ -687,7 +687,8 @@ struct BatchRun {
 };
 
 template <int NB, typename TA, typename TB, typename TV>
-static int b_enqueue_cycle(dg_handle* h, const BatchRun& Rn, const TA* A, const TB* Binv, const TV* F, TV* x) {
+static int b_enqueue_cycle(dg_handle* h, const BatchRun& Rn, const TA* A, const TB* Binv, const TV* F, TV* x,
+                           const TA* Ah) {
     const BatchDev& B = Rn.B;
     TV* V = (TV*)Rn.V;
     TV* Z = (TV*)Rn.Z;
@@ -708,6 +709,10 @@ static int b_enqueue_cycle(dg_handle* h, const BatchRun& Rn, const TA* A, const 
                                                               DevCtl{nullptr, nullptr, h->b_inst, B.iactive, nullptr},
                                                               zj, vj1);
             ++n;
+        } else if (Ah) {
+            // V_{j+1} = s_j (A M^-1) V_j with the precomputed operator
+            k_apply<NB, TA, TV, TV><<<ge, 256, 0, h->stream>>>(Ah, h->nbr, V, V + Rn.ld, h->ne, step, vj, vj);
+            --n;
         } else {
             k_bj_apply<NB, TB, TV, TV><<<ge, 256, 0, h->stream>>>(Binv, V, Z, h->ne, step, vj, vsel_fixed());
             k_apply<NB, TA, TV, TV><<<ge, 256, 0, h->stream>>>(A, h->nbr, Z, V, h->ne,
@@ -740,16 +745,22 @@ static int b_enqueue_cycle(dg_handle* h, const BatchRun& Rn, const TA* A, const 
 template <int NB, typename TA, typename TB, typename TV>
 static dg_status b_gmres(dg_handle* h, BatchRun& Rn, const TA* A, const TB* Binv, const TV* F, TV* x, double tol,
                          int max_it, int* counters_host) {
+    // A M^-1 precomputed by the block-Jacobi set-up (f64 / f32 copies)
+    const TA* Ah = nullptr;
+    if (Binv && Rn.B.iuse == nullptr) {
+        if constexpr (sizeof(TA) == 8) Ah = h->Ah64;
+        else if constexpr (sizeof(TA) == 4) Ah = h->Ah32;
+    }
     const BatchDev& B = Rn.B;
     k_b_init<TV><<<Rn.gx, 256, 0, h->stream>>>(F, x, (TV*)Rn.V, B, Rn.m, max_it, tol);
     DG_CK(h, cudaMemsetAsync(B.jglob, 0, sizeof(int), h->stream));
     k_b_cycle_end<<<1, 1024, 0, h->stream>>>(B);
     h->nlaunch += 2;
     DG_LAUNCH_CK(h);
-    const uintptr_t key[8] = {(uintptr_t)A, (uintptr_t)Binv, (uintptr_t)F, (uintptr_t)x, (uintptr_t)Rn.V,
+    const uintptr_t key[9] = {(uintptr_t)A, (uintptr_t)Binv, (uintptr_t)F, (uintptr_t)x, (uintptr_t)Rn.V,
                               (uintptr_t)B.bst,
                               (uintptr_t)Rn.m | ((uintptr_t)sizeof(TV) << 16) | ((uintptr_t)(B.iuse != nullptr) << 24),
-                              (uintptr_t)h->stream};
+                              (uintptr_t)h->stream, (uintptr_t)Ah};
     if (h->b_graph && memcmp(key, h->b_key, sizeof(key)) != 0) {
         cudaGraphExecDestroy(h->b_graph);
         h->b_graph = nullptr;
@@ -758,7 +769,7 @@ static dg_status b_gmres(dg_handle* h, BatchRun& Rn, const TA* A, const TB* Binv
     if (use_graph && !h->b_graph) {
         cudaGraph_t g;
         DG_CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-        h->b_nodes = b_enqueue_cycle<NB, TA, TB, TV>(h, Rn, A, Binv, F, x);
+        h->b_nodes = b_enqueue_cycle<NB, TA, TB, TV>(h, Rn, A, Binv, F, x, Ah);
         cudaMemcpyAsync(counters_host, B.counters, sizeof(int) * 4, cudaMemcpyDeviceToHost, h->stream);
         DG_CK(h, cudaStreamEndCapture(h->stream, &g));
         cudaError_t e = cudaGraphInstantiate(&h->b_graph, g, 0);
@@ -774,7 +785,7 @@ static dg_status b_gmres(dg_handle* h, BatchRun& Rn, const TA* A, const TB* Binv
             DG_CK(h, cudaGraphLaunch(h->b_graph, h->stream));
             h->nlaunch += h->b_nodes;
         } else {
-            h->nlaunch += b_enqueue_cycle<NB, TA, TB, TV>(h, Rn, A, Binv, F, x);
+            h->nlaunch += b_enqueue_cycle<NB, TA, TB, TV>(h, Rn, A, Binv, F, x, Ah);
             DG_CK(h, cudaMemcpyAsync(counters_host, B.counters, sizeof(int) * 4, cudaMemcpyDeviceToHost, h->stream));
         }
         DG_LAUNCH_CK(h);

@@ -522,7 +522,7 @@ static int enqueue_cycle(dg_handle* h, GmresWork& W, const TA* A, const TB* B, c
             ++extra;
         } else if (Ah) {
             // V_{j+1} = s_j (A M^-1) V_j: one apply of the precomputed operator
-            launch_apply<NB, TA, TV>(h, Ah, V, V, step, vj, vj1);
+            launch_apply<NB, TA, TV>(h, Ah, V, V + ld, step, vj, vj);
             --extra;
         } else {
             launch_bj<NB, TB, TV>(h, B, V, Z, step, vj, vsel_fixed());

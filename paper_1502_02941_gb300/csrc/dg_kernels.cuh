@@ -126,7 +126,7 @@ __device__ __forceinline__ void store_y(TX* __restrict__ y, int K, const TACC* v
 // block, the kernel exits at once when the solver is inactive and x / y are
 // picked from the Krylov basis by the device-side step counter; with
 // ctl.scale set, y is multiplied by the scale factor of the selected x (the
-// lazily normalised basis vector).
+// lazily normalised basis vector; per instance through ctl.iscale in a batch).
 template <int NB, typename TA, typename TX, typename TACC>
 __global__ void __launch_bounds__(256) k_apply(const TA* __restrict__ A, const int* __restrict__ nbr,
                                                 const TX* __restrict__ x0, TX* __restrict__ y0, int ne,
@@ -166,8 +166,8 @@ __global__ void __launch_bounds__(256) k_apply(const TA* __restrict__ A, const i
             }
         }
     }
-    if (ctl.scale && !ctl.inst) {
-        const TACC sc = (TACC)ctl.scale[sx.j ? *sx.j + sx.add : 0];
+    if ((ctl.scale && !ctl.inst) || (ctl.inst && ctl.iscale)) {
+        const TACC sc = (TACC)(ctl.inst ? ctl.iscale[ctl.inst[K]] : ctl.scale[sx.j ? *sx.j + sx.add : 0]);
 #pragma unroll
         for (int r = 0; r < NB; ++r) acc[r] *= sc;
     }
