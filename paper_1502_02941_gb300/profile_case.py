@@ -3,11 +3,15 @@ profilers (a small, self-contained case: ~0.6 GB on the device).
 
     python -m paper_1502_02941_gb300.profile_case --kernel dots --j 25 --reps 3
     python -m paper_1502_02941_gb300.profile_case --kernel apply64 --reps 3
+    python -m paper_1502_02941_gb300.profile_case --kernel step --reps 1
 
 dots / update: the Arnoldi multi-dot / update kernel of f64 (or --f32) GMRES at
 step j on a synthetic basis (dg_profile_kernel); apply64 / apply32 / apply16:
-the block-sparse operator apply on the f64 / f32 / bf16 block copy.  Prints the
-average CUDA-event time per launch as one JSON line.
+the block-sparse operator apply on the f64 / f32 / bf16 block copy; assemble:
+one assembly; step: the benchmark's step (mesh upload, assembly, block-Jacobi
+set-up and f64 GMRES(50) to 1e-10 for NIPG and SIPG) after one untimed step,
+inside an NVTX range "timed_steps".  Prints the average CUDA-event time per
+launch (per step) as one JSON line.
 """
 from __future__ import annotations
 
@@ -17,7 +21,8 @@ import json
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kernel", required=True, choices=["dots", "update", "apply64", "apply32", "apply16"])
+    ap.add_argument("--kernel", required=True,
+                    choices=["dots", "update", "apply64", "apply32", "apply16", "assemble", "step"])
     ap.add_argument("--j", type=int, default=25)
     ap.add_argument("--f32", action="store_true", help="f32 Arnoldi kernels (dots / update)")
     ap.add_argument("--reps", type=int, default=3)
@@ -32,10 +37,51 @@ def main(argv=None):
 
     cfg = W.config2(method=2, N=a.N)
     h = D.DG(0)
+    if a.kernel == "step":
+        ma = W.structured_mesh(a.N)
+        problem.setup(h, cfg, mesh=ma, assemble=False)
+        f, gD, gN = problem.problem_data(h, cfg.problem)
+        p = cfg.problem
+        x = torch.empty(h.info().dofs, dtype=torch.float64, device="cuda")
+
+        def step():
+            for method in (1, 2):
+                h.mesh_upload(ma.nodes, ma.elems, ma.dirichlet, ma.neumann)
+                h.set_params(method=method, degree=2, sigma_int=0.0, store=D.DG_STORE_F64, gmres_m=50, tol=1e-10,
+                             max_it=20000)
+                h.assemble(p.eps, p.alpha, p.b, f, gD, gN)
+                h.precond_setup()
+                h.gmres_solve(x=x)
+
+        step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("timed_steps")
+        e0.record()
+        for _ in range(a.reps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"kernel": "step", "N": a.N, "ms": e0.elapsed_time(e1) / a.reps}))
+        h.close()
+        return
     problem.setup(h, cfg, store=D.DG_STORE_F64 | D.DG_STORE_F32 | D.DG_STORE_BF16, gmres_m=50)
     info = h.info()
     out = {"kernel": a.kernel, "N": a.N, "ne": info.ne, "dofs": info.dofs}
-    if a.kernel in ("dots", "update"):
+    if a.kernel == "assemble":
+        p = cfg.problem
+        data = problem.problem_data(h, p)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        for _ in range(a.reps):
+            e0.record()
+            h.assemble(p.eps, p.alpha, p.b, *data)
+            e1.record()
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        out["ms"] = tot / a.reps
+    elif a.kernel in ("dots", "update"):
         which = D.DG_PROF_DOTS if a.kernel == "dots" else D.DG_PROF_UPDATE
         out["j"] = a.j
         out["ms"] = h.profile_kernel(which, D.DG_F32 if a.f32 else D.DG_F64, a.j, reps=a.reps)
