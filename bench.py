@@ -480,6 +480,33 @@ def main():
         apply[name] = {"ms": ams, "bytes": abytes, "GBps": abytes / (ams / 1e3) / 1e9,
                        "frac_hbm": abytes / (ams / 1e3) / 1e9 / peak}
     apply["f64"]["fma_per_apply"] = (info.ne + 2 * info.n_interior) * info.nb * info.nb
+    # the same kernels on the 512x512 P3 operator (5.24 M unknowns), large enough
+    # that launch and tail latency no longer hide the bandwidth
+    h3 = D.DG(local)
+    cfg3 = W.config3(N=512)
+    problem.setup(h3, cfg3, store=D.DG_STORE_F64 | D.DG_STORE_F32 | D.DG_STORE_BF16)
+    i3 = h3.info()
+    apply_p3 = {}
+    for name, dt, sa, sx in (("f64", D.DG_F64, 8, 8), ("f32", D.DG_F32, 4, 4), ("bf16", D.DG_BF16, 2, 4)):
+        td = torch.float64 if dt == D.DG_F64 else torch.float32
+        xr = torch.randn(i3.dofs, dtype=td, device=dev)
+        yr = torch.empty_like(xr)
+        for _ in range(3):
+            h3.apply(xr, dt, yr)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        for _ in range(20):
+            flush.fill_(1.0)
+            a0.record(stream)
+            h3.apply(xr, dt, yr)
+            a1.record(stream)
+            a1.synchronize()
+            tot += a0.elapsed_time(a1)
+        ams = tot / 20
+        abytes = apply_bytes(i3.ne, i3.n_interior, i3.nb, sa, sx)
+        apply_p3[name] = {"ms": ams, "bytes": abytes, "GBps": abytes / (ams / 1e3) / 1e9,
+                          "frac_hbm": abytes / (ams / 1e3) / 1e9 / peak}
+    h3.close()
     jmid = 25
     dots_ms = h.profile_kernel(D.DG_PROF_DOTS, D.DG_F64, jmid)
     upd_ms = h.profile_kernel(D.DG_PROF_UPDATE, D.DG_F64, jmid)
@@ -497,7 +524,7 @@ def main():
                                "1.19 TFLOP/s); HBM peak for the applies is measured hbm_gbs"}
     kernels = {"k_gm_update<double>": {"ms": upd_ms, "TFLOPs": upd_flops / (upd_ms / 1e3) / 1e12,
                                        "GBps": 8.0 * (jmid + 3) * dofs / (upd_ms / 1e3) / 1e9},
-               "k_apply": apply}
+               "k_apply": apply, "k_apply_512x512_P3": apply_p3}
 
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
