@@ -184,7 +184,9 @@ __global__ void __launch_bounds__(256) k_gm_init(const TV* __restrict__ F, TV* _
 // Givens / Hessenberg step for column j; runs in thread 0 of the last block
 // with the column and the previous rotations staged in shared memory.
 __device__ void gm_finish_column(GmresState* st, double wn, const double* hc, const double* cs, const double* sn) {
-    const int j = st->j;
+    // state read up front: the stores into H below may alias it for the compiler
+    const int j = st->j, m = st->m, its = st->its + 1, max_it = st->max_it;
+    const double gj = st->g[j], tolb = st->tol * st->bnorm;
     const int LD = DG_MAXM + 1;
     double* Hc = st->H + (long)j * LD;
     double a = hc[0];
@@ -193,25 +195,24 @@ __device__ void gm_finish_column(GmresState* st, double wn, const double* hc, co
         Hc[i] = cs[i] * a + sn[i] * b;
         a = -sn[i] * a + cs[i] * b;
     }
-    const double b = wn;
-    const double r = hypot(a, b);
-    const double c = r == 0.0 ? 1.0 : a / r, s = r == 0.0 ? 0.0 : b / r;
+    const double r = hypot(a, wn);
+    const double ir = r == 0.0 ? 0.0 : 1.0 / r;
+    const double c = r == 0.0 ? 1.0 : a * ir, s = wn * ir;
     st->cs[j] = c;
     st->sn[j] = s;
     Hc[j] = r;
     Hc[j + 1] = 0.0;
-    const double gj = st->g[j];
     st->g[j + 1] = -s * gj;
     st->g[j] = c * gj;
     st->scale[j + 1] = wn > 0.0 ? 1.0 / wn : 0.0;
-    st->its += 1;
+    st->its = its;
     st->j = j + 1;
     st->pending = 1;
     const bool bad = !isfinite(wn) || !isfinite(r);
     if (bad) st->nonfinite = 1;
     const double est = fabs(s * gj);
     const bool breakdown = !(wn > 1e-300) || !(r > 0.0);
-    if (bad || est <= st->tol * st->bnorm || j + 1 >= st->m || st->its >= st->max_it || breakdown) st->active = 0;
+    if (bad || est <= tolb || j + 1 >= m || its >= max_it || breakdown) st->active = 0;
 }
 
 
@@ -324,14 +325,16 @@ __global__ void __launch_bounds__(GM_TX* GM_TY) k_gm_dots(const TV* __restrict__
         sns[i] = st->sn[i];
     }
     __syncthreads();
-    if (t != 0) return;
+    if (t >= 32) return;
     // norm of w - sum h_d v_d without another pass: ||w||^2 - sum h_d^2 (the
     // v_d are orthonormal).  Accepted when at least 0.49 ||w||^2 remains (at
     // most a factor 2 of cancellation); otherwise a second Gram-Schmidt pass
     // runs and its own self-dot gives the norm exactly.
-    const double w2 = hp[j + 1];
     double s2 = 0.0;
-    for (int d = 0; d <= j; ++d) s2 = fma(hp[d], hp[d], s2);
+    for (int d = t; d <= j; d += 32) s2 = fma(hp[d], hp[d], s2);
+    s2 = dg_warp_sum(s2);
+    if (t != 0) return;
+    const double w2 = hp[j + 1];
     const double rest = w2 - s2;
     st->jw = j;
     if (pass == 1) {
