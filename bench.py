@@ -471,8 +471,13 @@ def main():
         torch.cuda.synchronize()
         ams = a0.elapsed_time(a1) / reps
         written = info.ne * 4 * info.nb * info.nb * (8 + (6 if name != "f64" else 0))
+        # f64 pipe operations of the entry kernel: per entry of the 4 blocks, 10 volume
+        # terms + per face 11 factor terms and 3 per upwind point (k + 2 points)
+        ops = info.ne * info.nb * info.nb * (43 + 9 * (DEGREE + 2))
+        fp64_ops_peak = SMS * FP64_FMA_PER_CLK_SM * SM_MAX_GHZ * 1e9
         assembly[name] = {"ms": ams, "elements_per_s": info.ne / (ams / 1e3), "bytes_written": written,
-                          "GBps_written": written / (ams / 1e3) / 1e9}
+                          "GBps_written": written / (ams / 1e3) / 1e9, "fp64_ops": ops,
+                          "frac_fp64_peak": ops / (ams / 1e3) / fp64_ops_peak}
     apply = {}
     for name, dt, sa, sx in (("f64", D.DG_F64, 8, 8), ("f32", D.DG_F32, 4, 4), ("bf16", D.DG_BF16, 2, 4)):
         ams = time_apply(dt)
