@@ -19,7 +19,7 @@ def _run(*args):
 def test_cli_dense_solve_of_the_8x8_workload():
     out = _run("paper_1502_02941_gb300.cli", "--config", "1", "--solver", "dense")
     assert out["ne"] == 128 and out["dofs"] == 384
-    assert 0 < out["l2_error"] < 1e-2
+    assert 0 < out["l2_error"] < 5e-2
 
 
 @pytest.mark.parametrize("solver", ["gmres", "mixed-f32", "gmres-ir-bf16"])
