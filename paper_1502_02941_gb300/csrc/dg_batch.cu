@@ -184,9 +184,6 @@ __global__ void __launch_bounds__(256) k_b_init(const TV* __restrict__ F, TV* __
 __device__ void b_finish_column(BatchDev& B, int inst, int j, double wn, const double* hc, const double* cs,
                                 const double* sn) {
     BState* st = B.bst + inst;
-    // state read up front: the stores into H below may alias it for the compiler
-    const int m = st->m, its = st->its + 1, max_it = st->max_it;
-    const double gj = st->g[j], tolb = st->tol * st->bnorm;
     const int LD = DG_MAXM + 1;
     double* Hc = st->H + (long)j * LD;
     double a = hc[0];
@@ -196,17 +193,17 @@ __device__ void b_finish_column(BatchDev& B, int inst, int j, double wn, const d
         a = -sn[i] * a + cs[i] * b;
     }
     const double r = hypot(a, wn);
-    const double ir = r == 0.0 ? 0.0 : 1.0 / r;
-    const double c = r == 0.0 ? 1.0 : a * ir, s = wn * ir;
+    const double c = r == 0.0 ? 1.0 : a / r, s = r == 0.0 ? 0.0 : wn / r;
     st->cs[j] = c;
     st->sn[j] = s;
     Hc[j] = r;
     Hc[j + 1] = 0.0;
+    const double gj = st->g[j];
     st->g[j + 1] = -s * gj;
     st->g[j] = c * gj;
     st->scale[j + 1] = wn > 0.0 ? 1.0 / wn : 0.0;
     B.iscale[inst] = st->scale[j + 1];
-    st->its = its;
+    st->its += 1;
     st->j = j + 1;
     st->pending = 1;
     B.ipending[inst] = 1;
@@ -214,7 +211,7 @@ __device__ void b_finish_column(BatchDev& B, int inst, int j, double wn, const d
     if (bad) st->nonfinite = 1;
     const double est = fabs(s * gj);
     const bool breakdown = !(wn > 1e-300) || !(r > 0.0);
-    if (bad || est <= tolb || j + 1 >= m || its >= max_it || breakdown)
+    if (bad || est <= st->tol * st->bnorm || j + 1 >= st->m || st->its >= st->max_it || breakdown)
         B.iactive[inst] = 0;
 }
 
@@ -298,13 +295,10 @@ __global__ void __launch_bounds__(B_TX* B_TY) k_b_dots(const TV* __restrict__ V,
             sns[i] = st->sn[i];
         }
         __syncthreads();
-        double s2 = 0.0;
-        if (t < 32) {
-            for (int d = t; d <= j; d += 32) s2 = ::fma(hp[d], hp[d], s2);
-            s2 = dg_warp_sum(s2);
-        }
         if (t == 0) {
             const double w2 = hp[j + 1];
+            double s2 = 0.0;
+            for (int d = 0; d <= j; ++d) s2 = ::fma(hp[d], hp[d], s2);
             const double rest = w2 - s2;
             bool ready = true;
             if (pass == 1) {
