@@ -42,6 +42,8 @@ struct GmresState {  // header fields first: the first GM_HDR bytes go to the ho
     int m, max_it;
     unsigned int arrive;  // last-block arrival counter
     int jw;          // column being orthogonalised (read by the update kernel)
+    int colready;    // the column's norm is known; the update kernel takes the Givens step
+    double wn_fin;   // that norm
     double tol, bnorm, relres, wn2_before;
     double scale[DG_MAXM + 2];
     double hcol[DG_MAXM + 2];
@@ -154,6 +156,7 @@ __global__ void __launch_bounds__(256) k_gm_init(const TV* __restrict__ F, TV* _
     st->its = 0;
     st->cycles = 0;
     st->reorth = 0;
+    st->colready = 0;
     st->pending = 0;
     st->nonfinite = 0;
     st->j = 0;
@@ -296,7 +299,7 @@ __global__ void __launch_bounds__(GM_TX* GM_TY) k_gm_dots(const TV* __restrict__
     }
     if (!last_block(&st->arrive)) return;
     // 16 threads per dot: thread t sums partials t%16, t%16+16, ... of dot t/16
-    __shared__ double hp[DG_MAXM + 2], hc[DG_MAXM + 2], css[DG_MAXM], sns[DG_MAXM];
+    __shared__ double hp[DG_MAXM + 2];
     const int t = ty * GM_TX + tx;
     for (int d0 = 0; d0 <= dlast; d0 += (GM_TX * GM_TY) / 16) {
         const int d = d0 + t / 16;
@@ -313,16 +316,10 @@ __global__ void __launch_bounds__(GM_TX* GM_TY) k_gm_dots(const TV* __restrict__
             } else {
                 const double hd = st->scale[d] * r;
                 hp[d] = hd;
-                const double h = pass == 1 ? hd : st->hcol[d] + hd;
-                st->hcol[d] = h;
-                hc[d] = h;
+                st->hcol[d] = pass == 1 ? hd : st->hcol[d] + hd;
                 st->coef[d] = hd * st->scale[d];
             }
         }
-    }
-    for (int i = t; i < j; i += GM_TX * GM_TY) {
-        css[i] = st->cs[i];
-        sns[i] = st->sn[i];
     }
     __syncthreads();
     if (t >= 32) return;
@@ -342,13 +339,34 @@ __global__ void __launch_bounds__(GM_TX* GM_TY) k_gm_dots(const TV* __restrict__
         st->reorth = again ? 1 : 0;
         if (again) return;
     }
-    gm_finish_column(st, sqrt(rest > 0.0 ? rest : 0.0), hc, css, sns);
+    st->wn_fin = sqrt(rest > 0.0 ? rest : 0.0);
+    st->colready = 1;
 }
 
 // V_{j+1} -= sum_{d<=j} coef_d V_d for the column j = jw the multi-dot kernel
-// prepared (its tail already took the Givens step, or asked for a second pass).
+// prepared.  Block 0 (dispatched first) takes the Givens step of the column
+// when the multi-dot tail marked it ready, in parallel with the update (the
+// update does not need it; the next step does).
 template <typename TV>
 __global__ void __launch_bounds__(256) k_gm_update(TV* V, long ld, long nvec, GmresState* st, int pass) {
+    if (blockIdx.x == 0) {
+        __shared__ double hc[DG_MAXM + 2], css[DG_MAXM], sns[DG_MAXM];
+        if (!st->colready) return;
+        const int jc = st->jw;
+        for (int i = threadIdx.x; i <= jc; i += blockDim.x) {
+            hc[i] = st->hcol[i];
+            if (i < jc) {
+                css[i] = st->cs[i];
+                sns[i] = st->sn[i];
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            st->colready = 0;
+            gm_finish_column(st, st->wn_fin, hc, css, sns);
+        }
+        return;
+    }
     if (!st->active || (pass == 2 && !st->reorth)) return;
     using VT = typename Vec<TV>::T;
     constexpr int W = Vec<TV>::W;
@@ -357,7 +375,8 @@ __global__ void __launch_bounds__(256) k_gm_update(TV* V, long ld, long nvec, Gm
     for (int d = threadIdx.x; d <= j; d += blockDim.x) c[d] = (TV)st->coef[d];
     __syncthreads();
     VT* w = reinterpret_cast<VT*>(V + (long)(j + 1) * ld);   // aliases V: no __restrict__
-    for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < nvec; q += (long)gridDim.x * blockDim.x) {
+    const long nthr = (long)(gridDim.x - 1) * blockDim.x;   // block 0 is the control block
+    for (long q = (long)(blockIdx.x - 1) * blockDim.x + threadIdx.x; q < nvec; q += nthr) {
         VT acc = w[q];
         int d = 0;
         for (; d + 4 <= j + 1; d += 4) {
@@ -533,7 +552,7 @@ static int enqueue_cycle(dg_handle* h, GmresWork& W, const TA* A, const TB* B, c
         }
         for (int pass = 1; pass <= 2; ++pass) {
             k_gm_dots<TV><<<gdots, bdots, 0, h->stream>>>(V, ld, nvec, st, W.partials, pass);
-            k_gm_update<TV><<<gx, 256, 0, h->stream>>>(V, ld, nvec, st, pass);
+            k_gm_update<TV><<<gx + 1, 256, 0, h->stream>>>(V, ld, nvec, st, pass);
         }
     }
     DevCtl pend{&st->pending, nullptr};
@@ -939,7 +958,7 @@ static dg_status gmres_ir_run(dg_handle* h, const TA* Alo, const double* F, doub
             for (int pass = 1; pass <= 2; ++pass) {
                 k_gm_dots<double><<<W.gsm, dim3(GM_TX, GM_TY), 0, h->stream>>>(V, (long)ld, nvec, st, W.partials,
                                                                                pass);
-                k_gm_update<double><<<gx, 256, 0, h->stream>>>(V, (long)ld, nvec, st, pass);
+                k_gm_update<double><<<gx + 1, 256, 0, h->stream>>>(V, (long)ld, nvec, st, pass);
             }
             h->nlaunch += 6;
             DG_LAUNCH_CK(h);
@@ -1020,6 +1039,7 @@ __global__ void k_prof_state(GmresState* st, int j, int m) {
     st->wn2_before = 0.0;
     st->arrive = 0;
     st->jw = j;
+    st->colready = 0;
     for (int i = 0; i <= m + 1; ++i) {
         st->scale[i] = 1.0;
         st->hcol[i] = 1e-3;
@@ -1059,7 +1079,7 @@ static dg_status profile_arnoldi(dg_handle* h, int which, int j, int reps, doubl
             k_gm_dots<TV><<<W.gsm, dim3(GM_TX, GM_TY), 0, h->stream>>>((const TV*)W.V, (long)W.ld, nvec, W.st,
                                                                          W.partials, 1);
         else
-            k_gm_update<TV><<<W.gx, 256, 0, h->stream>>>((TV*)W.V, (long)W.ld, nvec, W.st, 1);
+            k_gm_update<TV><<<W.gx + 1, 256, 0, h->stream>>>((TV*)W.V, (long)W.ld, nvec, W.st, 1);
         DG_CK(h, cudaEventRecord(e1, h->stream));
         DG_CK(h, cudaEventSynchronize(e1));
         float ms = 0.f;
