@@ -111,13 +111,19 @@ def test_feature_rows_match_oracle():
 
 def test_flexible_gmres_with_mlp_converges():
     """A randomly initialised network is a poor but valid preconditioner:
-    flexible GMRES still reaches the tolerance (oracle-independent check of the
-    f64 residual), falling back to block Jacobi if it stalls."""
+    flexible GMRES still reaches the tolerance, falling back to block Jacobi if
+    it stalls; the residual is re-measured with the oracle's own f64 operator
+    (reading A-12)."""
+    from gpu_helpers import basis_change, oracle_run, rel_residual_oracle
     h, cfg = _handle(2, N=8)
     h.mlp_init(seed=1)
     h.set_params(precond=D.DG_PRECOND_MLP)
     x, info = h.gmres_solve()
     assert info.status == D.DG_OK and info.relres <= 1e-11
+    ma = problem.mesh_for(cfg)
+    run = oracle_run(ma, cfg.k, cfg.method, cfg.problem)
+    T = basis_change(run, ma, cfg.k)
+    assert rel_residual_oracle(run, T, _np(x)) <= 1e-10
     h.set_params(precond=D.DG_PRECOND_BLOCK_JACOBI)
     xb, ib = h.gmres_solve()
     assert np.abs(_np(x) - _np(xb)).max() <= 1e-8 * np.abs(_np(xb)).max()
