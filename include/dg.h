@@ -254,8 +254,11 @@ dg_status dg_get_blocks(dg_handle* h, int dtype, void* out, int* nbr);
 dg_status dg_apply(dg_handle* h, int dtype, const void* x, void* y);
 
 /* Build the preconditioner (DG_PRECOND_BLOCK_JACOBI: f64 Gauss-Jordan inverse
-   with partial pivoting of every diagonal block A_KK, plus an f32 copy).
-   DG_ERR_SINGULAR_BLOCK if a block is singular.  Synchronises. */
+   with partial pivoting of every diagonal block A_KK, plus an f32 copy, and the
+   right-preconditioned operator A M^-1 (blocks A_KL A_LL^-1 formed in f64,
+   stored for each of the f64 / f32 block copies) that the solvers apply in one
+   pass per Arnoldi step).  DG_ERR_SINGULAR_BLOCK if a block is singular.
+   Synchronises. */
 dg_status dg_precond_setup(dg_handle* h, int kind);
 
 /* z = M^-1 r for device vectors (f64 for DG_F64, f32 otherwise). */
@@ -266,8 +269,10 @@ dg_status dg_precond_apply(dg_handle* h, int dtype, const void* r, void* z);
 /* ------------------------------------------------------------------------ */
 /*
  * Restarted GMRES(m) in f64 with right preconditioning (params.precond),
- * x0 = 0, classical Gram-Schmidt with one conditional re-orthogonalisation
- * pass, Givens rotations on the device.  Stops when the true residual
+ * x0 = 0, classical Gram-Schmidt with the norm taken as ||w||^2 - sum h_d^2 in
+ * the same reduction and one conditional re-orthogonalisation pass (when less
+ * than 0.49 ||w||^2 remains), Givens rotations on the device; one CUDA graph
+ * per restart cycle on a non-default stream.  Stops when the true residual
  * ||F - A x||/||F|| <= params.tol (checked at every restart) or after
  * params.max_it Arnoldi steps (DG_NOT_CONVERGED, info still filled).
  *   F    device [dofs] f64 right-hand side, or NULL for the assembled F

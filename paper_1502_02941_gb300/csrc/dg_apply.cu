@@ -69,11 +69,10 @@ __global__ void __launch_bounds__(128) k_bj_setup(const TA* __restrict__ A, int 
 
 // Block (K, slot s) of A M^-1: A_{K,s} Binv_L with L = K (s = 0) or the
 // neighbour across face s-1, in f64; zero for a missing neighbour.  One thread
-// per (element, slot); writes the requested copies.
+// per (element, slot); writes the f64 and / or f32 copy.
 template <int NB>
 __global__ void __launch_bounds__(128) k_ahat_setup(const double* __restrict__ A, const double* __restrict__ Binv,
-                                                     const int* __restrict__ nbr, int ne, double* Ah64, float* Ah32,
-                                                     __nv_bfloat16* Ah16) {
+                                                     const int* __restrict__ nbr, int ne, double* Ah64, float* Ah32) {
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 4L * ne) return;
     const int K = (int)(t >> 2), s = (int)(t & 3);
@@ -91,7 +90,6 @@ __global__ void __launch_bounds__(128) k_ahat_setup(const double* __restrict__ A
             const int m = i * NB + j;
             if (Ah64) Ah64[dg_blk_index<double>(K, s, m, NB, 4)] = c;
             if (Ah32) Ah32[dg_blk_index<float>(K, s, m, NB, 4)] = (float)c;
-            if (Ah16) Ah16[dg_blk_index<__nv_bfloat16>(K, s, m, NB, 4)] = __double2bfloat16(c);
         }
 }
 
@@ -100,14 +98,14 @@ __global__ void __launch_bounds__(128) k_ahat_setup(const double* __restrict__ A
 static dg_status ahat_setup(dg_handle* h) {
     const int nb = dg_nb(h->asm_k);
     const size_t per = (size_t)h->ntiles * 4 * 16 * 32;   // bytes per chunk row x chunks below
-    size_t need[3] = {0, 0, 0};
-    if (h->A64) need[0] = per * dg_chunks<double>(nb);
-    if (h->A32) need[1] = per * dg_chunks<float>(nb);
     // no bf16 copy: the bf16 inner solves keep block Jacobi on the bf16 blocks,
     // whose true residual they are checked against
-    void** ptrs[3] = {(void**)&h->Ah64, (void**)&h->Ah32, (void**)&h->Ah16};
+    size_t need[2] = {0, 0};
+    if (h->A64) need[0] = per * dg_chunks<double>(nb);
+    if (h->A32) need[1] = per * dg_chunks<float>(nb);
+    void** ptrs[2] = {(void**)&h->Ah64, (void**)&h->Ah32};
     dg_status s;
-    for (int t = 0; t < 3; ++t) {
+    for (int t = 0; t < 2; ++t) {
         if (need[t] != h->Ah_bytes[t]) {
             if ((s = dg_realloc(h, ptrs[t], need[t])) != DG_OK) return s;
             h->Ah_bytes[t] = need[t];
@@ -116,9 +114,9 @@ static dg_status ahat_setup(dg_handle* h) {
     }
     const unsigned g = (unsigned)((4L * h->ne + 127) / 128);
     switch (nb) {
-        case 3: k_ahat_setup<3><<<g, 128, 0, h->stream>>>(h->A64, h->Binv64, h->nbr, h->ne, h->Ah64, h->Ah32, h->Ah16); break;
-        case 6: k_ahat_setup<6><<<g, 128, 0, h->stream>>>(h->A64, h->Binv64, h->nbr, h->ne, h->Ah64, h->Ah32, h->Ah16); break;
-        case 10: k_ahat_setup<10><<<g, 128, 0, h->stream>>>(h->A64, h->Binv64, h->nbr, h->ne, h->Ah64, h->Ah32, h->Ah16); break;
+        case 3: k_ahat_setup<3><<<g, 128, 0, h->stream>>>(h->A64, h->Binv64, h->nbr, h->ne, h->Ah64, h->Ah32); break;
+        case 6: k_ahat_setup<6><<<g, 128, 0, h->stream>>>(h->A64, h->Binv64, h->nbr, h->ne, h->Ah64, h->Ah32); break;
+        case 10: k_ahat_setup<10><<<g, 128, 0, h->stream>>>(h->A64, h->Binv64, h->nbr, h->ne, h->Ah64, h->Ah32); break;
         default: return dg_fail(h, DG_ERR_INVALID_ARG, "degree");
     }
     h->nlaunch += 1;

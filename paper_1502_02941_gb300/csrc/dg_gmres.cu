@@ -44,7 +44,7 @@ struct GmresState {  // header fields first: the first GM_HDR bytes go to the ho
     int jw;          // column being orthogonalised (read by the update kernel)
     int colready;    // the column's norm is known; the update kernel takes the Givens step
     double wn_fin;   // that norm
-    double tol, bnorm, relres, wn2_before;
+    double tol, bnorm, relres;
     double scale[DG_MAXM + 2];
     double hcol[DG_MAXM + 2];
     double coef[DG_MAXM + 2];
@@ -1036,7 +1036,6 @@ __global__ void k_prof_state(GmresState* st, int j, int m) {
     st->max_it = 1 << 30;
     st->tol = 0.0;
     st->bnorm = 1.0;
-    st->wn2_before = 0.0;
     st->arrive = 0;
     st->jw = j;
     st->colready = 0;

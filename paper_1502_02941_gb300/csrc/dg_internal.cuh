@@ -150,12 +150,11 @@ struct dg_handle {
     float* Binv32 = nullptr;
     float* Binv16 = nullptr;       // inverses of the bf16 diagonal blocks (f32)
     // the right-preconditioned operator A M_BJ^-1 (block-ELL, 4 slots: block
-    // (K, L) = A_KL A_LL^-1, computed in f64), f64 and f32 copies (Ah16 stays
-    // NULL): a GMRES step with block Jacobi is then one apply
+    // (K, L) = A_KL A_LL^-1, computed in f64), f64 and f32 copies: a GMRES
+    // step with block Jacobi is then one apply
     double* Ah64 = nullptr;
     float* Ah32 = nullptr;
-    __nv_bfloat16* Ah16 = nullptr;
-    size_t Ah_bytes[3] = {0, 0, 0};
+    size_t Ah_bytes[2] = {0, 0};
 
     // GMRES workspaces: [0] the f64 solver, [1] the f32 inner solver of the
     // mixed-precision refinement
