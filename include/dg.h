@@ -77,6 +77,7 @@ typedef int dg_status;
 #define DG_PRECOND_NONE          0
 #define DG_PRECOND_BLOCK_JACOBI  1
 #define DG_PRECOND_MLP           2   /* block Jacobi + learned element-local correction (flexible GMRES) */
+#define DG_PRECOND_SCHWARZ       3   /* one-layer-overlap restricted additive Schwarz (exact patch solves) */
 
 /* Point sets of dg_quad_points / dg_eval. */
 #define DG_POINTS_VOLUME   0  /* [ne][(k+2)^2]: Duffy-collapsed Gauss-Legendre */
@@ -257,8 +258,12 @@ dg_status dg_apply(dg_handle* h, int dtype, const void* x, void* y);
    with partial pivoting of every diagonal block A_KK, plus an f32 copy, and the
    right-preconditioned operator A M^-1 (blocks A_KL A_LL^-1 formed in f64,
    stored for each of the f64 / f32 block copies) that the solvers apply in one
-   pass per Arnoldi step).  DG_ERR_SINGULAR_BLOCK if a block is singular.
-   Synchronises. */
+   pass per Arnoldi step).  DG_PRECOND_SCHWARZ additionally forms, for every
+   element K, the rows of K in the inverse of its patch matrix A_P (K and its
+   face neighbours, f64 Gaussian elimination with partial pivoting): the
+   preconditioner z_K = (A_P^-1 r_P)_K is then one block-sparse apply with the
+   sparsity of A (f64 and f32 copies).  DG_ERR_SINGULAR_BLOCK if a diagonal
+   block or a patch matrix is singular.  Synchronises. */
 dg_status dg_precond_setup(dg_handle* h, int kind);
 
 /* z = M^-1 r for device vectors (f64 for DG_F64, f32 otherwise). */
@@ -288,7 +293,8 @@ dg_status dg_gmres_solve(dg_handle* h, const double* F, double* x, dg_solve_info
  * ||r||/||F|| <= params.tol.  Each correction solves A_lo d = r/||r||
  * approximately with restarted GMRES(inner_m) on f32 vectors, using the f32
  * (inner_dtype DG_F32) or bf16 (DG_BF16) block copy with f32 accumulation and
- * the block-Jacobi inverses (computed in f64, applied in f32), to relative
+ * the params.precond preconditioner (block Jacobi: the f64 inverses applied in
+ * f32; Schwarz: the f32 copy of the patch-inverse rows), to relative
  * residual inner_tol or for at most 8 restart cycles (8 inner_m steps: past
  * that the f32 iteration sits at its accuracy floor and a fresh f64 residual
  * serves better); dot products accumulate in f64 beyond per-thread
@@ -316,8 +322,8 @@ dg_status dg_mixed_solve(dg_handle* h, int inner_dtype, int inner_m, double inne
  * (one inner solve each), params.max_it the inner steps in total.
  *   info: iterations = inner Arnoldi steps in total, outer = outer FGMRES steps,
  *         restarts = outer restart cycles, relres = final f64 relative residual.
- * params.precond must be DG_PRECOND_BLOCK_JACOBI or DG_PRECOND_NONE (for the
- * inner solve).  DG_NOT_CONVERGED when a cap is reached.  Synchronises.
+ * params.precond must be DG_PRECOND_BLOCK_JACOBI, DG_PRECOND_SCHWARZ or
+ * DG_PRECOND_NONE (for the inner solve).  DG_NOT_CONVERGED when a cap is reached.  Synchronises.
  */
 dg_status dg_gmres_ir_solve(dg_handle* h, int inner_dtype, int inner_m, double inner_tol, int max_outer,
                             const double* F, double* x, dg_solve_info* info);

@@ -124,6 +124,130 @@ static dg_status ahat_setup(dg_handle* h) {
     return DG_OK;
 }
 
+// Restricted additive Schwarz with one layer of overlap: for element K with
+// face neighbours L_f, P = {K, L_f} and A_P the patch matrix (A's blocks
+// between patch elements; neighbours couple only where they share a face).
+// Row block K of A_P^-1 (NB x |P| NB) is stored in the 4 slots of K (slot 1+f
+// multiplies r_{L_f}), so z = G r is one apply.  The rows come from solving
+// A_P^T y_i = e_i (i over K's NB unknowns) by Gaussian elimination with
+// partial pivoting in f64, one thread per element.
+template <int NB>
+__global__ void __launch_bounds__(64) k_ras_setup(const double* __restrict__ A, const int* __restrict__ nbr,
+                                                   const int* __restrict__ nface, int ne, double* G64, float* G32,
+                                                   int* flag) {
+    const int K = blockIdx.x * blockDim.x + threadIdx.x;
+    if (K >= ne) return;
+    constexpr int NP = 4 * NB;
+    double M[NP][NP + NB];
+    int E[4], slotK[4], slotOf[4], cnt = 1;
+    E[0] = K;
+    slotOf[0] = 0;
+    slotK[0] = 0;
+    for (int f = 0; f < 3; ++f) {
+        const int L = nbr[(size_t)f * ne + K];
+        if (L >= 0) {
+            E[cnt] = L;
+            slotOf[cnt] = 1 + f;
+            slotK[cnt] = 1 + nface[(size_t)f * ne + K];
+            ++cnt;
+        }
+    }
+    const int n = cnt * NB;
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n + NB; ++b) M[a][b] = 0.0;
+    // M = A_P^T | [e_0 .. e_{NB-1}]
+    for (int p = 0; p < cnt; ++p)
+        for (int q = 0; q < cnt; ++q) {
+            int slot = -1;
+            if (p == q) slot = 0;
+            else if (p == 0) slot = slotOf[q];
+            else if (q == 0) slot = slotK[p];
+            else
+                for (int f = 0; f < 3; ++f)
+                    if (nbr[(size_t)f * ne + E[p]] == E[q]) slot = 1 + f;
+            if (slot < 0) continue;
+            for (int i = 0; i < NB; ++i)
+                for (int j = 0; j < NB; ++j)
+                    M[q * NB + j][p * NB + i] = A[dg_blk_index<double>(E[p], slot, i * NB + j, NB, 4)];
+        }
+    for (int i = 0; i < NB; ++i) M[i][n + i] = 1.0;
+    double amax = 0.0;
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b) amax = fmax(amax, fabs(M[a][b]));
+    bool ok = amax > 0.0 && isfinite(amax);
+    for (int c = 0; c < n && ok; ++c) {
+        int pv = c;
+        for (int a = c + 1; a < n; ++a)
+            if (fabs(M[a][c]) > fabs(M[pv][c])) pv = a;
+        if (!(fabs(M[pv][c]) > 1e-14 * amax)) {
+            ok = false;
+            break;
+        }
+        if (pv != c)
+            for (int b = c; b < n + NB; ++b) {
+                const double t = M[c][b];
+                M[c][b] = M[pv][b];
+                M[pv][b] = t;
+            }
+        const double inv = 1.0 / M[c][c];
+        for (int a = c + 1; a < n; ++a) {
+            const double l = M[a][c] * inv;
+            if (l != 0.0)
+                for (int b = c; b < n + NB; ++b) M[a][b] = fma(-l, M[c][b], M[a][b]);
+        }
+    }
+    if (!ok) {
+        atomicOr(flag, 2);
+        return;
+    }
+    // back substitution for the NB right-hand sides (solutions overwrite them)
+    for (int i = 0; i < NB; ++i)
+        for (int a = n - 1; a >= 0; --a) {
+            double t = M[a][n + i];
+            for (int b = a + 1; b < n; ++b) t = fma(-M[a][b], M[b][n + i], t);
+            M[a][n + i] = t / M[a][a];
+        }
+    // row i of K's block row: G_{K, slot(p)}[i][j] = y_i[p NB + j]
+    for (int p = 0; p < cnt; ++p)
+        for (int i = 0; i < NB; ++i)
+            for (int j = 0; j < NB; ++j) {
+                const double g = M[p * NB + j][n + i];
+                const int m = i * NB + j;
+                if (G64) G64[dg_blk_index<double>(K, slotOf[p], m, NB, 4)] = g;
+                if (G32) G32[dg_blk_index<float>(K, slotOf[p], m, NB, 4)] = (float)g;
+            }
+}
+
+static dg_status ras_setup(dg_handle* h) {
+    const int nb = dg_nb(h->asm_k);
+    const size_t per = (size_t)h->ntiles * 4 * 16 * 32;
+    size_t need[2] = {per * dg_chunks<double>(nb), per * dg_chunks<float>(nb)};
+    void** ptrs[2] = {(void**)&h->G64, (void**)&h->G32};
+    dg_status s;
+    for (int t = 0; t < 2; ++t) {
+        if (need[t] != h->G_bytes[t]) {
+            if ((s = dg_realloc(h, ptrs[t], need[t])) != DG_OK) return s;
+            h->G_bytes[t] = need[t];
+        }
+        DG_CK(h, cudaMemsetAsync(*ptrs[t], 0, need[t], h->stream));
+    }
+    DG_CK(h, cudaMemsetAsync(h->dflag, 0, sizeof(int), h->stream));
+    const unsigned g = (unsigned)((h->ne + 63) / 64);
+    switch (nb) {
+        case 3: k_ras_setup<3><<<g, 64, 0, h->stream>>>(h->A64, h->nbr, h->nface, h->ne, h->G64, h->G32, h->dflag); break;
+        case 6: k_ras_setup<6><<<g, 64, 0, h->stream>>>(h->A64, h->nbr, h->nface, h->ne, h->G64, h->G32, h->dflag); break;
+        case 10: k_ras_setup<10><<<g, 64, 0, h->stream>>>(h->A64, h->nbr, h->nface, h->ne, h->G64, h->G32, h->dflag); break;
+        default: return dg_fail(h, DG_ERR_INVALID_ARG, "degree");
+    }
+    h->nlaunch += 1;
+    DG_LAUNCH_CK(h);
+    int flag = 0;
+    DG_CK(h, cudaMemcpyAsync(&flag, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    DG_CK(h, cudaStreamSynchronize(h->stream));
+    if (flag) return dg_fail(h, DG_ERR_SINGULAR_BLOCK, "a patch matrix is singular");
+    return DG_OK;
+}
+
 // ---------------------------------------------------------------------------
 // dispatch
 // ---------------------------------------------------------------------------
@@ -246,12 +370,19 @@ extern "C" dg_status dg_precond_setup(dg_handle* h, int kind) {
     if (!h) return DG_ERR_INVALID_ARG;
     if (!h->assembled) return dg_fail(h, DG_ERR_STATE, "not assembled");
     if (kind == DG_PRECOND_NONE) return DG_OK;
-    if (kind != DG_PRECOND_BLOCK_JACOBI && kind != DG_PRECOND_MLP) return dg_fail(h, DG_ERR_INVALID_ARG, "precond kind");
+    if (kind != DG_PRECOND_BLOCK_JACOBI && kind != DG_PRECOND_MLP && kind != DG_PRECOND_SCHWARZ)
+        return dg_fail(h, DG_ERR_INVALID_ARG, "precond kind");
     if (kind == DG_PRECOND_MLP && (!h->mlp.packed || h->mlp.nb != dg_nb(h->asm_k)))
         return dg_fail(h, DG_ERR_STATE, "MLP preconditioner: dg_mlp_init / dg_mlp_set_weights for this degree first");
     h->bj_ok = false;
+    h->ras_ok = false;
     dg_status s = dg_launch_bj_setup(h);
     if (s == DG_OK) h->bj_ok = true;
+    if (s == DG_OK && kind == DG_PRECOND_SCHWARZ) {
+        if (!h->A64) return dg_fail(h, DG_ERR_STATE, "the Schwarz preconditioner needs the f64 blocks");
+        s = ras_setup(h);
+        if (s == DG_OK) h->ras_ok = true;
+    }
     return s;
 }
 
@@ -260,6 +391,27 @@ extern "C" dg_status dg_precond_apply(dg_handle* h, int dtype, const void* r, vo
     if (!h->bj_ok) return dg_fail(h, DG_ERR_STATE, "preconditioner not set up");
     if (!dg_aligned16(r) || !dg_aligned16(z)) return dg_fail(h, DG_ERR_INVALID_ARG, "r and z must be 16-byte aligned");
     if (dtype != DG_F64 && dtype != DG_F32 && dtype != DG_BF16) return dg_fail(h, DG_ERR_INVALID_ARG, "dtype");
+    if (h->p.precond == DG_PRECOND_SCHWARZ) {
+        if (!h->ras_ok) return dg_fail(h, DG_ERR_STATE, "Schwarz preconditioner not set up");
+        const unsigned grid = (unsigned)((h->ne + 255) / 256);
+        const int nb = dg_nb(h->asm_k);
+#define DG_RAS_APPLY(NBV)                                                                                         \
+        if (nb == NBV) {                                                                                          \
+            if (dtype == DG_F64)                                                                                  \
+                k_apply<NBV, double, double, double><<<grid, 256, 0, h->stream>>>(                                \
+                    h->G64, h->nbr, (const double*)r, (double*)z, h->ne, dctl_none(), vsel_fixed(), vsel_fixed()); \
+            else                                                                                                  \
+                k_apply<NBV, float, float, float><<<grid, 256, 0, h->stream>>>(                                   \
+                    h->G32, h->nbr, (const float*)r, (float*)z, h->ne, dctl_none(), vsel_fixed(), vsel_fixed());  \
+        }
+        DG_RAS_APPLY(3)
+        DG_RAS_APPLY(6)
+        DG_RAS_APPLY(10)
+#undef DG_RAS_APPLY
+        h->nlaunch += 1;
+        DG_LAUNCH_CK(h);
+        return DG_OK;
+    }
     dg_status s = dg_launch_bj_apply(h, dtype == DG_F64 ? DG_F64 : DG_F32, r, z, nullptr);
     if (s != DG_OK || h->p.precond != DG_PRECOND_MLP || !h->mlp.packed) return s;
     const int one = 1;

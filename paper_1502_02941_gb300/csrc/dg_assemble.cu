@@ -447,6 +447,7 @@ extern "C" dg_status dg_assemble(dg_handle* h, const dg_coeffs* c) {
     double fac = h->p.sigma_bdry_factor > 0.0 ? h->p.sigma_bdry_factor : 2.0;
     h->assembled = false;
     h->bj_ok = false;
+    h->ras_ok = false;
     if ((s = dg_launch_assemble(h, c, kappa, sig, fac * sig)) != DG_OK) return s;
     h->assembled = true;
     h->asm_k = k;

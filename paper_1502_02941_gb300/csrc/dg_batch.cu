@@ -614,6 +614,7 @@ extern "C" dg_status dg_batch_setup(dg_handle* h, int n_inst, const int* elem_st
     h->b_inst_active = true;
     h->assembled = false;
     h->bj_ok = false;
+    h->ras_ok = false;
     if (h->b_graph) {
         cudaGraphExecDestroy(h->b_graph);
         h->b_graph = nullptr;
@@ -927,6 +928,8 @@ extern "C" dg_status dg_batch_solve(dg_handle* h, int inner_dtype, int inner_m, 
     if (inner_dtype == DG_BF16 && !h->A16) return dg_fail(h, DG_ERR_STATE, "bf16 blocks not stored");
     if (inner_dtype != DG_F64 && inner_dtype != DG_F32 && inner_dtype != DG_BF16)
         return dg_fail(h, DG_ERR_INVALID_ARG, "inner_dtype");
+    if (h->p.precond == DG_PRECOND_SCHWARZ)
+        return dg_fail(h, DG_ERR_INVALID_ARG, "the batched solver takes block Jacobi, the learned correction or none");
     if (h->p.precond != DG_PRECOND_NONE && !h->bj_ok) {
         dg_status s = dg_precond_setup(h, DG_PRECOND_BLOCK_JACOBI);
         if (s != DG_OK) return s;

@@ -518,7 +518,7 @@ static void launch_bj(dg_handle* h, const TB* B, const TV* r, TV* z, DevCtl ctl,
 // Returns the number of kernels enqueued.
 template <int NB, typename TA, typename TB, typename TV>
 static int enqueue_cycle(dg_handle* h, GmresWork& W, const TA* A, const TB* B, const TV* F, TV* x, bool flex,
-                         const TA* Ah) {
+                         const TA* Ah, const TV* G) {
     TV* V = (TV*)W.V;
     TV* Z = (TV*)W.Z;
     TV* R = (TV*)W.R;
@@ -542,6 +542,10 @@ static int enqueue_cycle(dg_handle* h, GmresWork& W, const TA* A, const TB* B, c
             dg_mlp_correct<TV>(h, V, Zb, step, vj, zj, nullptr);
             launch_apply<NB, TA, TV>(h, A, Zb, V, step_noscale, zj, vj1);
             ++extra;
+        } else if (G) {
+            // Schwarz: Z = s_j G V_j, V_{j+1} = A Z (two applies)
+            launch_apply<NB, TV, TV>(h, G, V, Z, step, vj, vsel_fixed());
+            launch_apply<NB, TA, TV>(h, A, Z, V, step_noscale, vsel_fixed(), vj1);
         } else if (Ah) {
             // V_{j+1} = s_j (A M^-1) V_j: one apply of the precomputed operator
             launch_apply<NB, TA, TV>(h, Ah, V, V + ld, step, vj, vj);
@@ -562,7 +566,8 @@ static int enqueue_cycle(dg_handle* h, GmresWork& W, const TA* A, const TB* B, c
         k_gm_axpy<TV><<<gx, 256, 0, h->stream>>>(x, R, n, st);
     } else {
         k_gm_combine<TV><<<gx, 256, 0, h->stream>>>(V, ld, nvec, st, R);
-        launch_bj<NB, TB, TV>(h, B, R, Z, pend, vsel_fixed(), vsel_fixed());
+        if (G) launch_apply<NB, TV, TV>(h, G, R, Z, pend, vsel_fixed(), vsel_fixed());
+        else launch_bj<NB, TB, TV>(h, B, R, Z, pend, vsel_fixed(), vsel_fixed());
         k_gm_axpy<TV><<<gx, 256, 0, h->stream>>>(x, Z, n, st);
     }
     launch_apply<NB, TA, TV>(h, A, x, R, pend, vsel_fixed(), vsel_fixed());
@@ -631,7 +636,8 @@ static const T* ahat_of(const dg_handle* h) {
 // given (block Jacobi), each Arnoldi step is one apply of Ah.
 template <int NB, typename TA, typename TB, typename TV>
 static dg_status gmres_run(dg_handle* h, GmresWork& W, const TA* A, const TB* B, const TV* F, TV* x, int m,
-                           double tol, int max_it, dg_solve_info* info, bool flex = false, const TA* Ah = nullptr) {
+                           double tol, int max_it, dg_solve_info* info, bool flex = false, const TA* Ah = nullptr,
+                           const TV* G = nullptr) {
     const long n = (long)h->ne * NB;
     dg_status s = ensure_workspace(h, W, n, m, sizeof(TV));
     if (s != DG_OK) return s;
@@ -644,9 +650,11 @@ static dg_status gmres_run(dg_handle* h, GmresWork& W, const TA* A, const TB* B,
     DG_LAUNCH_CK(h);
     DG_CK(h, cudaMemcpyAsync(W.st_host, W.st, GM_HDR, cudaMemcpyDeviceToHost, h->stream));
     DG_CK(h, cudaStreamSynchronize(h->stream));
-    if (flex || !B) Ah = nullptr;
-    const uintptr_t key[7] = {(uintptr_t)x, (uintptr_t)F, (uintptr_t)A, (uintptr_t)B,
-                              (uintptr_t)m | ((uintptr_t)flex << 20), (uintptr_t)h->stream, (uintptr_t)Ah};
+    if (flex || !B || G) Ah = nullptr;
+    if (flex) G = nullptr;
+    const uintptr_t key[8] = {(uintptr_t)x, (uintptr_t)F, (uintptr_t)A, (uintptr_t)B,
+                              (uintptr_t)m | ((uintptr_t)flex << 20), (uintptr_t)h->stream, (uintptr_t)Ah,
+                              (uintptr_t)G};
     if (W.graph && memcmp(key, W.key, sizeof(key)) != 0) {
         cudaGraphExecDestroy(W.graph);
         W.graph = nullptr;
@@ -655,7 +663,7 @@ static dg_status gmres_run(dg_handle* h, GmresWork& W, const TA* A, const TB* B,
     if (use_graph && !W.graph && !W.st_host->done) {
         cudaGraph_t g;
         DG_CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-        W.nodes = enqueue_cycle<NB, TA, TB, TV>(h, W, A, B, F, x, flex, Ah);
+        W.nodes = enqueue_cycle<NB, TA, TB, TV>(h, W, A, B, F, x, flex, Ah, G);
         DG_CK(h, cudaStreamEndCapture(h->stream, &g));
         cudaError_t e = cudaGraphInstantiate(&W.graph, g, 0);
         cudaGraphDestroy(g);
@@ -670,7 +678,7 @@ static dg_status gmres_run(dg_handle* h, GmresWork& W, const TA* A, const TB* B,
             DG_CK(h, cudaGraphLaunch(W.graph, h->stream));
             h->nlaunch += W.nodes;
         } else {
-            h->nlaunch += enqueue_cycle<NB, TA, TB, TV>(h, W, A, B, F, x, flex, Ah);
+            h->nlaunch += enqueue_cycle<NB, TA, TB, TV>(h, W, A, B, F, x, flex, Ah, G);
         }
         DG_LAUNCH_CK(h);
         DG_CK(h, cudaStreamSynchronize(h->stream));
@@ -710,8 +718,9 @@ static dg_status gmres_f64(dg_handle* h, const double* F, double* x, dg_solve_in
         const int one = 1;
         DG_CK(h, cudaMemcpyAsync(h->mlp.on, &one, sizeof(int), cudaMemcpyHostToDevice, h->stream));
     }
+    const double* G = h->p.precond == DG_PRECOND_SCHWARZ ? h->G64 : nullptr;
     const dg_status s = gmres_run<NB, double, double, double>(h, h->gw[0], h->A64, B, F, x, h->p.gmres_m, h->p.tol,
-                                                              h->p.max_it, info, mlp, h->Ah64);
+                                                              h->p.max_it, info, mlp, h->Ah64, G);
     if (h->gw[0].V) {
         h->basis = (const double*)h->gw[0].V;
         h->basis_ld = h->gw[0].ld;
@@ -725,8 +734,9 @@ extern "C" dg_status dg_gmres_solve(dg_handle* h, const double* F, double* x, dg
     h->basis = nullptr;
     if (!h->assembled) return dg_fail(h, DG_ERR_STATE, "not assembled");
     if (!h->A64) return dg_fail(h, DG_ERR_STATE, "f64 blocks not stored");
-    if (h->p.precond != DG_PRECOND_NONE && !h->bj_ok) {
-        dg_status s = dg_precond_setup(h, DG_PRECOND_BLOCK_JACOBI);
+    if (h->p.precond != DG_PRECOND_NONE && (!h->bj_ok || (h->p.precond == DG_PRECOND_SCHWARZ && !h->ras_ok))) {
+        dg_status s = dg_precond_setup(h, h->p.precond == DG_PRECOND_SCHWARZ ? DG_PRECOND_SCHWARZ
+                                                                             : DG_PRECOND_BLOCK_JACOBI);
         if (s != DG_OK) return s;
     }
     if (h->p.precond == DG_PRECOND_MLP && (!h->mlp.packed || h->mlp.nb != dg_nb(h->asm_k)))
@@ -810,7 +820,9 @@ static dg_status mixed_run(dg_handle* h, const TA* Alo, const double* F, double*
     DG_CK(h, cudaMemcpyAsync(ms, &init, sizeof(MixState), cudaMemcpyHostToDevice, h->stream));
     DG_CK(h, cudaMemsetAsync(x, 0, sizeof(double) * n, h->stream));
     const bool lo16 = sizeof(TA) == 2;
-    const float* B32 = h->p.precond == DG_PRECOND_BLOCK_JACOBI ? (lo16 ? h->Binv16 : h->Binv32) : nullptr;
+    const float* B32 = (h->p.precond == DG_PRECOND_BLOCK_JACOBI || h->p.precond == DG_PRECOND_SCHWARZ)
+                           ? (lo16 ? h->Binv16 : h->Binv32)
+                           : nullptr;
     int inner_total = 0, outer = 0;
     const int gx = W.gx;
     bool converged = false;
@@ -833,7 +845,7 @@ static dg_status mixed_run(dg_handle* h, const TA* Alo, const double* F, double*
         // and a fresh f64 residual serves better than more inner steps
         const int cap = std::min(h->p.max_it - inner_total, DG_INNER_CYCLES * inner_m);
         s = gmres_run<NB, TA, float, float>(h, h->gw[1], Alo, B32, r32, d32, inner_m, inner_tol, cap, &in, false,
-                                                ahat_of<TA>(h));
+                                                ahat_of<TA>(h), h->p.precond == DG_PRECOND_SCHWARZ ? h->G32 : nullptr);
         if (s != DG_OK && s != DG_NOT_CONVERGED) return s;
         inner_total += in.iterations;
         k_mx_update<<<gx, 256, 0, h->stream>>>(x, d32, n, ms);
@@ -866,6 +878,10 @@ extern "C" dg_status dg_mixed_solve(dg_handle* h, int inner_dtype, int inner_m, 
         return dg_fail(h, DG_ERR_INVALID_ARG, "inner_m / inner_tol / max_outer");
     if (h->p.precond == DG_PRECOND_BLOCK_JACOBI && !h->bj_ok) {
         dg_status s = dg_precond_setup(h, DG_PRECOND_BLOCK_JACOBI);
+        if (s != DG_OK) return s;
+    }
+    if (h->p.precond == DG_PRECOND_SCHWARZ && !h->ras_ok) {
+        dg_status s = dg_precond_setup(h, DG_PRECOND_SCHWARZ);
         if (s != DG_OK) return s;
     }
     DG_CK(h, cudaSetDevice(h->device));
@@ -922,7 +938,9 @@ static dg_status gmres_ir_run(dg_handle* h, const TA* Alo, const double* F, doub
     float* d32 = r32 + ld;
     DG_CK(h, cudaMemsetAsync(h->mx_buf, 0, need, h->stream));
     const bool lo16 = sizeof(TA) == 2;
-    const float* B32 = h->p.precond == DG_PRECOND_BLOCK_JACOBI ? (lo16 ? h->Binv16 : h->Binv32) : nullptr;
+    const float* B32 = (h->p.precond == DG_PRECOND_BLOCK_JACOBI || h->p.precond == DG_PRECOND_SCHWARZ)
+                           ? (lo16 ? h->Binv16 : h->Binv32)
+                           : nullptr;
     double* V = (double*)W.V;
     double* Zb = (double*)W.Zb;
     double* R = (double*)W.R;
@@ -948,7 +966,7 @@ static dg_status gmres_ir_run(dg_handle* h, const TA* Alo, const double* F, doub
             dg_solve_info in{};
             const int cap = std::min(h->p.max_it - inner_total, DG_INNER_CYCLES * inner_m);
             s = gmres_run<NB, TA, float, float>(h, h->gw[1], Alo, B32, r32, d32, inner_m, inner_tol, cap, &in, false,
-                                                ahat_of<TA>(h));
+                                                ahat_of<TA>(h), h->p.precond == DG_PRECOND_SCHWARZ ? h->G32 : nullptr);
             if (s != DG_OK && s != DG_NOT_CONVERGED) return s;
             inner_total += in.iterations;
             k_ir_up<<<gx, 256, 0, h->stream>>>(d32, Zb + (size_t)j * ld, n, st->scale + j);
@@ -1001,9 +1019,14 @@ extern "C" dg_status dg_gmres_ir_solve(dg_handle* h, int inner_dtype, int inner_
     if (inner_dtype == DG_BF16 && !h->A16) return dg_fail(h, DG_ERR_STATE, "bf16 blocks not stored");
     if (inner_m < 1 || inner_m > DG_MAXM || !(inner_tol > 0.0 && inner_tol < 1.0) || max_outer < 1)
         return dg_fail(h, DG_ERR_INVALID_ARG, "inner_m / inner_tol / max_outer");
-    if (h->p.precond == DG_PRECOND_MLP) return dg_fail(h, DG_ERR_INVALID_ARG, "the inner solve takes block Jacobi or none");
+    if (h->p.precond == DG_PRECOND_MLP)
+        return dg_fail(h, DG_ERR_INVALID_ARG, "the inner solve takes block Jacobi, Schwarz or none");
     if (h->p.precond == DG_PRECOND_BLOCK_JACOBI && !h->bj_ok) {
         dg_status s = dg_precond_setup(h, DG_PRECOND_BLOCK_JACOBI);
+        if (s != DG_OK) return s;
+    }
+    if (h->p.precond == DG_PRECOND_SCHWARZ && !h->ras_ok) {
+        dg_status s = dg_precond_setup(h, DG_PRECOND_SCHWARZ);
         if (s != DG_OK) return s;
     }
     DG_CK(h, cudaSetDevice(h->device));

@@ -55,7 +55,7 @@ dg_status dg_scratch(dg_handle* h, size_t bytes) {
 static void free_all(dg_handle* h) {
     void* ptrs[] = {h->nodes, h->elems, h->geo, h->nbr, h->nface, h->ftype, h->bidx, h->bedge, h->tab,
                     h->A64, h->A32, h->A16, h->F, h->Binv64, h->Binv32, h->Binv16, h->scratch, h->dflag, h->mx_buf,
-                    h->Ah64, h->Ah32};
+                    h->Ah64, h->Ah32, h->G64, h->G32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (GmresWork& w : h->gw) dg_gmres_free(&w);
@@ -155,11 +155,13 @@ extern "C" dg_status dg_set_params(dg_handle* h, const dg_params* p) {
     if ((p->store & 7) == 0 || (p->store & ~7)) return dg_fail(h, DG_ERR_INVALID_ARG, "store mask");
     if (p->gmres_m < 1 || p->gmres_m > DG_MAXM) return dg_fail(h, DG_ERR_INVALID_ARG, "gmres_m must be 1..64");
     if (!(p->tol > 0.0) || p->max_it < 1) return dg_fail(h, DG_ERR_INVALID_ARG, "tol/max_it");
-    if (p->precond != DG_PRECOND_NONE && p->precond != DG_PRECOND_BLOCK_JACOBI && p->precond != DG_PRECOND_MLP)
+    if (p->precond != DG_PRECOND_NONE && p->precond != DG_PRECOND_BLOCK_JACOBI && p->precond != DG_PRECOND_MLP &&
+        p->precond != DG_PRECOND_SCHWARZ)
         return dg_fail(h, DG_ERR_INVALID_ARG, "precond");
     if (p->degree != h->p.degree || p->store != h->p.store) {
         h->assembled = false;
         h->bj_ok = false;
+        h->ras_ok = false;
     }
     h->p = *p;
     h->params_set = true;
@@ -409,6 +411,7 @@ extern "C" dg_status dg_mesh_upload(dg_handle* h, const double* nodes, int nv, c
     h->mesh_ok = false;
     h->assembled = false;
     h->bj_ok = false;
+    h->ras_ok = false;
     dg_status s;
     if ((s = dg_ensure(h, (void**)&h->nodes, &h->cap_nodes, sizeof(double) * 2 * nv)) != DG_OK) return s;
     if ((s = dg_ensure(h, (void**)&h->elems, &h->cap_elems, sizeof(int) * 3 * (size_t)ne)) != DG_OK) return s;

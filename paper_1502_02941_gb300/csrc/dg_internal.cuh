@@ -103,7 +103,7 @@ struct GmresWork {
     GmresState* st = nullptr;      // device state
     GmresState* st_host = nullptr; // pinned mirror of the state header
     cudaGraphExec_t graph = nullptr;
-    uintptr_t key[7] = {0, 0, 0, 0, 0, 0};
+    uintptr_t key[8] = {0, 0, 0, 0, 0, 0};
     int nodes = 0;
     int gx = 0;    // grid of the 1-D vector kernels (4 blocks of 256 per SM)
     int gsm = 0;   // grid of the multi-dot kernel (one 1024-thread block per SM)
@@ -155,6 +155,13 @@ struct dg_handle {
     double* Ah64 = nullptr;
     float* Ah32 = nullptr;
     size_t Ah_bytes[2] = {0, 0};
+    // one-layer-overlap restricted additive Schwarz (DG_PRECOND_SCHWARZ): row
+    // block K of the patch inverses, z_K = sum_s G_{K,s} r_{L_s} over the same
+    // 4 slots as A (block-ELL), f64 and f32 copies
+    bool ras_ok = false;
+    double* G64 = nullptr;
+    float* G32 = nullptr;
+    size_t G_bytes[2] = {0, 0};
 
     // GMRES workspaces: [0] the f64 solver, [1] the f32 inner solver of the
     // mixed-precision refinement

@@ -26,7 +26,7 @@ DG_ERR_STATE, DG_ERR_NOMEM = 8, 9
 DG_NIPG, DG_SIPG, DG_IIPG = 1, 2, 3
 DG_F64, DG_F32, DG_BF16 = 0, 1, 2
 DG_STORE_F64, DG_STORE_F32, DG_STORE_BF16 = 1, 2, 4
-DG_PRECOND_NONE, DG_PRECOND_BLOCK_JACOBI, DG_PRECOND_MLP = 0, 1, 2
+DG_PRECOND_NONE, DG_PRECOND_BLOCK_JACOBI, DG_PRECOND_MLP, DG_PRECOND_SCHWARZ = 0, 1, 2, 3
 DG_POINTS_VOLUME, DG_POINTS_BOUNDARY, DG_POINTS_ERROR = 0, 1, 2
 DG_PROF_DOTS, DG_PROF_UPDATE = 1, 2
 
