@@ -3,6 +3,7 @@
     python -m paper_1502_02941_gb300.cli --config 2 --N 256 --method 2 --solver gmres
     python -m paper_1502_02941_gb300.cli --config 3 --N 64 --solver mixed-bf16
     python -m paper_1502_02941_gb300.cli --config 3 --solver gmres-ir-f32 --max-it 400000
+    python -m paper_1502_02941_gb300.cli --config 3 --solver gmres-ir-f32 --precond schwarz
 
 Prints one JSON line with sizes, iterations, relative residual, L2 error (when
 the workload has an exact solution) and wall time of the solve.
@@ -21,6 +22,7 @@ def main(argv=None):
     ap.add_argument("--method", type=int, default=None, help="1 NIPG, 2 SIPG, 3 IIPG")
     ap.add_argument("--solver", default="gmres",
                     choices=["gmres", "dense", "mixed-bf16", "mixed-f32", "gmres-ir-bf16", "gmres-ir-f32"])
+    ap.add_argument("--precond", default="block-jacobi", choices=["block-jacobi", "schwarz", "none"])
     ap.add_argument("--m", type=int, default=50)
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--max-it", type=int, default=20000)
@@ -49,8 +51,10 @@ def main(argv=None):
     elif a.solver.endswith("f32"):
         store |= D.DG_STORE_F32
     h = D.DG(0)
-    problem.setup(h, cfg, store=store, gmres_m=a.m, tol=a.tol, max_it=a.max_it)
-    h.precond_setup()
+    pc = {"block-jacobi": D.DG_PRECOND_BLOCK_JACOBI, "schwarz": D.DG_PRECOND_SCHWARZ,
+          "none": D.DG_PRECOND_NONE}[a.precond]
+    problem.setup(h, cfg, store=store, gmres_m=a.m, tol=a.tol, max_it=a.max_it, precond=pc)
+    h.precond_setup(pc)
     info = h.info()
     out = {}
     for _ in range(a.repeat):
@@ -77,7 +81,7 @@ def main(argv=None):
         l2, hmax = h.l2_error(x, problem.exact_at_error_points(h, cfg.problem))
         out.update(l2_error=l2, h_max=hmax)
     out.update(config=a.config, N=cfg.N, k=cfg.k, method=cfg.method, ne=info.ne, dofs=info.dofs,
-               solver=a.solver)
+               solver=a.solver, precond=a.precond)
     print(json.dumps(out))
     h.close()
 
