@@ -388,7 +388,7 @@ def main():
     # ---- mixed precision on the same workload: plain f64 refinement around f32
     # inner GMRES, and f64 FGMRES around f32 / bf16 inner GMRES (GMRES-based
     # refinement; plain refinement around bf16 stalls on this workload)
-    def mixed_steps(kind, inner):
+    def mixed_steps(kind, inner, pc=D.DG_PRECOND_BLOCK_JACOBI):
         store = D.DG_STORE_F64 | (D.DG_STORE_BF16 if inner == D.DG_BF16 else D.DG_STORE_F32)
         # inner GMRES(32) to 1e-3 (f32) / 1e-2 (bf16): the fastest setting of a sweep
         # of restart lengths 16..64 and tolerances 1e-3..1e-6 on this workload
@@ -397,9 +397,9 @@ def main():
         for method in METHODS:
             h.mesh_upload(ma.nodes, ma.elems, ma.dirichlet, ma.neumann)
             h.set_params(method=method, degree=DEGREE, sigma_int=0.0, store=store, gmres_m=50, tol=1e-10,
-                         max_it=20000)
+                         max_it=20000, precond=pc)
             h.assemble(p.eps, p.alpha, p.b, f, gD, gN)
-            h.precond_setup()
+            h.precond_setup(pc)
             if kind == "ir":
                 _, si = h.mixed_solve(inner, inner_m=INNER_M, inner_tol=tol_in, max_outer=60, x=x,
                                       raise_on_nonconv=False)
@@ -410,18 +410,21 @@ def main():
         return res
 
     mixed = {}
-    for name, kind, inner in (("f32", "ir", D.DG_F32), ("f32_gmres_ir", "gir", D.DG_F32),
-                              ("bf16_gmres_ir", "gir", D.DG_BF16)):
-        mixed_steps(kind, inner)   # warm-up (graph capture, workspaces)
+    for name, kind, inner, pc in (("f32", "ir", D.DG_F32, D.DG_PRECOND_BLOCK_JACOBI),
+                                  ("f32_gmres_ir", "gir", D.DG_F32, D.DG_PRECOND_BLOCK_JACOBI),
+                                  ("bf16_gmres_ir", "gir", D.DG_BF16, D.DG_PRECOND_BLOCK_JACOBI),
+                                  ("f32_schwarz", "ir", D.DG_F32, D.DG_PRECOND_SCHWARZ)):
+        mixed_steps(kind, inner, pc)   # warm-up (graph capture, workspaces)
         torch.cuda.synchronize()
         m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         m0.record(stream)
         for _ in range(args.steps):
-            res = mixed_steps(kind, inner)
+            res = mixed_steps(kind, inner, pc)
         m1.record(stream)
         torch.cuda.synchronize()
         mms = m0.elapsed_time(m1)
         mixed[name] = {"refinement": "f64 residual correction" if kind == "ir" else "f64 FGMRES outer",
+                       "preconditioner": "schwarz" if pc == D.DG_PRECOND_SCHWARZ else "block-jacobi",
                        "inner": f"GMRES({INNER_M}) to {1e-2 if inner == D.DG_BF16 else 1e-3:g} or 8 cycles",
                        "solves_per_s": len(METHODS) * args.steps / (mms / 1e3),
                        "ms_per_solve": mms / (len(METHODS) * args.steps),
@@ -433,7 +436,8 @@ def main():
 
     # ---- kernel timings with CUDA events on the launching stream
     h.mesh_upload(ma.nodes, ma.elems, ma.dirichlet, ma.neumann)
-    h.set_params(method=2, degree=DEGREE, sigma_int=0.0, store=D.DG_STORE_F64 | D.DG_STORE_F32 | D.DG_STORE_BF16,
+    h.set_params(method=2, degree=DEGREE, sigma_int=0.0, precond=D.DG_PRECOND_BLOCK_JACOBI,
+                 store=D.DG_STORE_F64 | D.DG_STORE_F32 | D.DG_STORE_BF16,
                  gmres_m=50, tol=1e-10, max_it=20000)
     h.assemble(p.eps, p.alpha, p.b, f, gD, gN)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
