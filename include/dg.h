@@ -367,7 +367,9 @@ dg_status dg_batch_set_tile(dg_handle* h, int tile);
  * per-instance reductions, Hessenberg/Givens and convergence.  DG_F32 /
  * DG_BF16: per-instance f64 iterative refinement (as dg_mixed_solve) around a
  * batched GMRES(inner_m) on f32 vectors with the f32 / bf16 block copy.
- * Each instance stops when its own ||F_i - A_i x_i|| / ||F_i|| <= params.tol.
+ * The preconditioner is params.precond (block Jacobi, Schwarz, the learned
+ * correction or none).  Each instance stops when its own
+ * ||F_i - A_i x_i|| / ||F_i|| <= params.tol.
  *   F device [dofs] f64 or NULL (assembled F); x device [dofs] f64 output;
  *   its, relres, status: host [n_inst] or NULL -- Arnoldi steps (inner steps
  *   summed over corrections), final f64 relative residual, DG_OK /

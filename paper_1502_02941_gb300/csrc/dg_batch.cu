@@ -689,7 +689,7 @@ struct BatchRun {
 
 template <int NB, typename TA, typename TB, typename TV>
 static int b_enqueue_cycle(dg_handle* h, const BatchRun& Rn, const TA* A, const TB* Binv, const TV* F, TV* x,
-                           const TA* Ah) {
+                           const TA* Ah, const TV* G) {
     const BatchDev& B = Rn.B;
     TV* V = (TV*)Rn.V;
     TV* Z = (TV*)Rn.Z;
@@ -710,6 +710,12 @@ static int b_enqueue_cycle(dg_handle* h, const BatchRun& Rn, const TA* A, const 
                                                               DevCtl{nullptr, nullptr, h->b_inst, B.iactive, nullptr},
                                                               zj, vj1);
             ++n;
+        } else if (G) {
+            // Schwarz: Z = s_j G V_j (per-instance scales), V_{j+1} = A Z
+            k_apply<NB, TV, TV, TV><<<ge, 256, 0, h->stream>>>(G, h->nbr, V, Z, h->ne, step, vj, vsel_fixed());
+            k_apply<NB, TA, TV, TV><<<ge, 256, 0, h->stream>>>(A, h->nbr, Z, V, h->ne,
+                                                              DevCtl{nullptr, nullptr, h->b_inst, B.iactive, nullptr},
+                                                              vsel_fixed(), vj1);
         } else if (Ah) {
             // V_{j+1} = s_j (A M^-1) V_j with the precomputed operator
             k_apply<NB, TA, TV, TV><<<ge, 256, 0, h->stream>>>(Ah, h->nbr, V, V + Rn.ld, h->ne, step, vj, vj);
@@ -734,7 +740,10 @@ static int b_enqueue_cycle(dg_handle* h, const BatchRun& Rn, const TA* A, const 
         --n;
     } else {
         k_b_combine<TV><<<Rn.gx, 256, 0, h->stream>>>(V, Rn.ld, B, R);
-        k_bj_apply<NB, TB, TV, TV><<<ge, 256, 0, h->stream>>>(Binv, R, Z, h->ne, pend, vsel_fixed(), vsel_fixed());
+        if (G)
+            k_apply<NB, TV, TV, TV><<<ge, 256, 0, h->stream>>>(G, h->nbr, R, Z, h->ne, pend, vsel_fixed(), vsel_fixed());
+        else
+            k_bj_apply<NB, TB, TV, TV><<<ge, 256, 0, h->stream>>>(Binv, R, Z, h->ne, pend, vsel_fixed(), vsel_fixed());
         k_b_axpy<TV><<<Rn.gx, 256, 0, h->stream>>>(x, Z, B);
     }
     k_apply<NB, TA, TV, TV><<<ge, 256, 0, h->stream>>>(A, h->nbr, x, R, h->ne, pend, vsel_fixed(), vsel_fixed());
@@ -746,9 +755,14 @@ static int b_enqueue_cycle(dg_handle* h, const BatchRun& Rn, const TA* A, const 
 template <int NB, typename TA, typename TB, typename TV>
 static dg_status b_gmres(dg_handle* h, BatchRun& Rn, const TA* A, const TB* Binv, const TV* F, TV* x, double tol,
                          int max_it, int* counters_host) {
-    // A M^-1 precomputed by the block-Jacobi set-up (f64 / f32 copies)
+    // A M^-1 precomputed by the block-Jacobi set-up (f64 / f32 copies), or
+    // the Schwarz rows in the precision of the vectors
     const TA* Ah = nullptr;
-    if (Binv && Rn.B.iuse == nullptr) {
+    const TV* G = nullptr;
+    if (h->p.precond == DG_PRECOND_SCHWARZ) {
+        if constexpr (sizeof(TV) == 8) G = h->G64;
+        else G = h->G32;
+    } else if (Binv && Rn.B.iuse == nullptr) {
         if constexpr (sizeof(TA) == 8) Ah = h->Ah64;
         else if constexpr (sizeof(TA) == 4) Ah = h->Ah32;
     }
@@ -758,10 +772,10 @@ static dg_status b_gmres(dg_handle* h, BatchRun& Rn, const TA* A, const TB* Binv
     k_b_cycle_end<<<1, 1024, 0, h->stream>>>(B);
     h->nlaunch += 2;
     DG_LAUNCH_CK(h);
-    const uintptr_t key[9] = {(uintptr_t)A, (uintptr_t)Binv, (uintptr_t)F, (uintptr_t)x, (uintptr_t)Rn.V,
-                              (uintptr_t)B.bst,
-                              (uintptr_t)Rn.m | ((uintptr_t)sizeof(TV) << 16) | ((uintptr_t)(B.iuse != nullptr) << 24),
-                              (uintptr_t)h->stream, (uintptr_t)Ah};
+    const uintptr_t key[10] = {(uintptr_t)A, (uintptr_t)Binv, (uintptr_t)F, (uintptr_t)x, (uintptr_t)Rn.V,
+                               (uintptr_t)B.bst,
+                               (uintptr_t)Rn.m | ((uintptr_t)sizeof(TV) << 16) | ((uintptr_t)(B.iuse != nullptr) << 24),
+                               (uintptr_t)h->stream, (uintptr_t)Ah, (uintptr_t)G};
     if (h->b_graph && memcmp(key, h->b_key, sizeof(key)) != 0) {
         cudaGraphExecDestroy(h->b_graph);
         h->b_graph = nullptr;
@@ -770,7 +784,7 @@ static dg_status b_gmres(dg_handle* h, BatchRun& Rn, const TA* A, const TB* Binv
     if (use_graph && !h->b_graph) {
         cudaGraph_t g;
         DG_CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-        h->b_nodes = b_enqueue_cycle<NB, TA, TB, TV>(h, Rn, A, Binv, F, x, Ah);
+        h->b_nodes = b_enqueue_cycle<NB, TA, TB, TV>(h, Rn, A, Binv, F, x, Ah, G);
         cudaMemcpyAsync(counters_host, B.counters, sizeof(int) * 4, cudaMemcpyDeviceToHost, h->stream);
         DG_CK(h, cudaStreamEndCapture(h->stream, &g));
         cudaError_t e = cudaGraphInstantiate(&h->b_graph, g, 0);
@@ -786,7 +800,7 @@ static dg_status b_gmres(dg_handle* h, BatchRun& Rn, const TA* A, const TB* Binv
             DG_CK(h, cudaGraphLaunch(h->b_graph, h->stream));
             h->nlaunch += h->b_nodes;
         } else {
-            h->nlaunch += b_enqueue_cycle<NB, TA, TB, TV>(h, Rn, A, Binv, F, x, Ah);
+            h->nlaunch += b_enqueue_cycle<NB, TA, TB, TV>(h, Rn, A, Binv, F, x, Ah, G);
             DG_CK(h, cudaMemcpyAsync(counters_host, B.counters, sizeof(int) * 4, cudaMemcpyDeviceToHost, h->stream));
         }
         DG_LAUNCH_CK(h);
@@ -928,10 +942,9 @@ extern "C" dg_status dg_batch_solve(dg_handle* h, int inner_dtype, int inner_m, 
     if (inner_dtype == DG_BF16 && !h->A16) return dg_fail(h, DG_ERR_STATE, "bf16 blocks not stored");
     if (inner_dtype != DG_F64 && inner_dtype != DG_F32 && inner_dtype != DG_BF16)
         return dg_fail(h, DG_ERR_INVALID_ARG, "inner_dtype");
-    if (h->p.precond == DG_PRECOND_SCHWARZ)
-        return dg_fail(h, DG_ERR_INVALID_ARG, "the batched solver takes block Jacobi, the learned correction or none");
-    if (h->p.precond != DG_PRECOND_NONE && !h->bj_ok) {
-        dg_status s = dg_precond_setup(h, DG_PRECOND_BLOCK_JACOBI);
+    if (h->p.precond != DG_PRECOND_NONE && (!h->bj_ok || (h->p.precond == DG_PRECOND_SCHWARZ && !h->ras_ok))) {
+        dg_status s = dg_precond_setup(h, h->p.precond == DG_PRECOND_SCHWARZ ? DG_PRECOND_SCHWARZ
+                                                                             : DG_PRECOND_BLOCK_JACOBI);
         if (s != DG_OK) return s;
     }
     if (h->p.precond == DG_PRECOND_MLP && (!h->mlp.packed || h->mlp.nb != dg_nb(h->asm_k)))

@@ -192,7 +192,7 @@ struct dg_handle {
     size_t cap_bhost = 0;
     int b_tile = 0;                // dofs per work item (autotuned)
     cudaGraphExec_t b_graph = nullptr;
-    uintptr_t b_key[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    uintptr_t b_key[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     int b_nodes = 0;
 
     MlpState mlp;
