@@ -161,7 +161,9 @@ def batched_section(local, stream, n_inst):
     out = {"workload": f"{n_inst} instances of the batched workload: N in [16,128], k in {{1,2}}, eps log-uniform "
                        "[1e-6,1e-1], |b| U[0,1], alpha U[0,1], 4-Gaussian f; SIPG, homogeneous Dirichlet",
            "instances": n_inst, "ne": info.ne, "dofs": info.dofs, "tile": tile}
-    for name, dt in (("f32_refined", D.DG_F32), ("f64", D.DG_F64)):
+    for name, dt, pc in (("f32_refined", D.DG_F32, D.DG_PRECOND_BLOCK_JACOBI), ("f64", D.DG_F64, D.DG_PRECOND_BLOCK_JACOBI),
+                         ("f32_refined_schwarz", D.DG_F32, D.DG_PRECOND_SCHWARZ)):
+        h.set_params(precond=pc)
         sec, (x, its, rr, st) = _events_time(stream, lambda: h.batch_solve(
             dt, inner_m=50, inner_tol=1e-4, max_outer=60, raise_on_nonconv=False))
         conv = int((st == 0).sum())
