@@ -25,7 +25,7 @@
  * Basis: scaled monomials ((x-xc)/hK)^a ((y-yc)/hK)^b, a+b <= k, on each
  * element (the paper's "Equation.base = 1" option, Sec. 4 set_parameter).
  *
- * Readings of the paper taken here (each is also listed in the design doc):
+ * Readings of the paper taken here (where it is silent, ambiguous or garbled):
  *   A-1  RHS Dirichlet consistency term is  +kappa*eps*grad(v).n*gD  (equal to
  *        the printed -eps*grad(v).n*gD for SIPG); flag `literal_rhs` restores
  *        the printed sign for every method.
