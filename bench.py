@@ -145,33 +145,60 @@ def _events_time(stream, fn):
     return e0.elapsed_time(e1) / 1e3, out
 
 
+BATCH_RUNS = (
+    # name, inner precision, preconditioner, solver
+    ("f32_refined", "f32", "bj", "refine"),
+    ("f64", "f64", "bj", "refine"),
+    ("f32_refined_schwarz", "f32", "schwarz", "refine"),
+    ("f32_gmres_ir", "f32", "bj", "gmres_ir"),
+    ("f32_gmres_ir_schwarz", "f32", "schwarz", "gmres_ir"),
+)
+
+
 def batched_section(local, stream, n_inst):
     """Instances 0..n_inst-1 of the batched workload (N uniform in [16,128], P1
-    or P2, random coefficients): one batched solve with f32 inner GMRES and f64
-    refinement, and one plain f64 batched GMRES, both to rel-res 1e-10."""
+    or P2, random coefficients), one batch per degree, each solved to rel-res
+    1e-10 per instance: f32 inner GMRES with f64 refinement (plain residual
+    correction and GMRES-based), plain f64 batched GMRES, with block Jacobi or
+    the Schwarz preconditioner."""
     import numpy as np
     from paper_1502_02941_gb300 import dg as D, problem, workloads as W
-    cfgs, ma, starts, coeffs = W.batch(4, n_inst)
-    h = D.DG(local)
-    problem.setup_batch(h, cfgs, ma, starts, coeffs, store=D.DG_STORE_F64 | D.DG_STORE_F32, gmres_m=50,
-                        tol=1e-10, max_it=20000)
-    h.precond_setup()
-    info = h.info()
-    tile = h.batch_autotune()
-    out = {"workload": f"{n_inst} instances of the batched workload: N in [16,128], k in {{1,2}}, eps log-uniform "
-                       "[1e-6,1e-1], |b| U[0,1], alpha U[0,1], 4-Gaussian f; SIPG, homogeneous Dirichlet",
-           "instances": n_inst, "ne": info.ne, "dofs": info.dofs, "tile": tile}
-    for name, dt, pc in (("f32_refined", D.DG_F32, D.DG_PRECOND_BLOCK_JACOBI), ("f64", D.DG_F64, D.DG_PRECOND_BLOCK_JACOBI),
-                         ("f32_refined_schwarz", D.DG_F32, D.DG_PRECOND_SCHWARZ)):
-        h.set_params(precond=pc)
-        sec, (x, its, rr, st) = _events_time(stream, lambda: h.batch_solve(
-            dt, inner_m=50, inner_tol=1e-4, max_outer=60, raise_on_nonconv=False))
-        conv = int((st == 0).sum())
-        out[name] = {"seconds": sec, "solves_per_s": n_inst / sec, "converged": conv,
-                     "converged_per_s": conv / sec, "its_median": int(np.median(its)), "its_max": int(its.max()),
-                     "relres_max_converged": float(rr[st == 0].max()) if conv else None}
+    groups = W.batch_by_degree(4, n_inst)
+    out = {"workload": f"{n_inst} instances of the batched workload: N in [16,128], k in {{1,2}} (one batch per "
+                       "degree), eps log-uniform [1e-6,1e-1], |b| U[0,1], alpha U[0,1], 4-Gaussian f; SIPG, "
+                       "homogeneous Dirichlet",
+           "instances": n_inst, "batches": {}}
+    res = {name: {"seconds": 0.0, "converged": 0, "its": []} for name, *_ in BATCH_RUNS}
+    for k, (cfgs, ma, starts, coeffs) in groups.items():
+        h = D.DG(local)
+        problem.setup_batch(h, cfgs, ma, starts, coeffs, store=D.DG_STORE_F64 | D.DG_STORE_F32, gmres_m=50,
+                            tol=1e-10, max_it=20000)
+        h.precond_setup()
+        info = h.info()
+        tile = h.batch_autotune()
+        out["batches"][f"P{k}"] = {"instances": len(cfgs), "ne": info.ne, "dofs": info.dofs, "tile": tile}
+        for name, inner, pc, solver in BATCH_RUNS:
+            h.set_params(precond=D.DG_PRECOND_SCHWARZ if pc == "schwarz" else D.DG_PRECOND_BLOCK_JACOBI)
+            dt = D.DG_F64 if inner == "f64" else D.DG_F32
+            if solver == "refine":
+                fn = lambda: h.batch_solve(dt, inner_m=50, inner_tol=1e-4, max_outer=60, raise_on_nonconv=False)
+            else:
+                fn = lambda: h.batch_gmres_ir_solve(dt, inner_m=32, inner_tol=1e-3, max_outer=1000,
+                                                    raise_on_nonconv=False)
+            sec, (x, its, rr, st) = _events_time(stream, fn)
+            r = res[name]
+            r["seconds"] += sec
+            r["converged"] += int((st == 0).sum())
+            r["its"] += [int(v) for v in its]
+            if (st == 0).any():
+                r["relres_max_converged"] = max(r.get("relres_max_converged", 0.0), float(rr[st == 0].max()))
+        h.close()
+    for name, r in res.items():
+        its = np.array(r.pop("its"))
+        out[name] = {"seconds": r["seconds"], "solves_per_s": n_inst / r["seconds"], "converged": r["converged"],
+                     "converged_per_s": r["converged"] / r["seconds"], "its_median": int(np.median(its)),
+                     "its_max": int(its.max()), "relres_max_converged": r.get("relres_max_converged")}
     out["speedup_f32_vs_f64"] = out["f64"]["seconds"] / out["f32_refined"]["seconds"]
-    h.close()
     return out
 
 

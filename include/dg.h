@@ -379,6 +379,24 @@ dg_status dg_batch_set_tile(dg_handle* h, int tile);
 dg_status dg_batch_solve(dg_handle* h, int inner_dtype, int inner_m, double inner_tol, int max_outer,
                          const double* F, double* x, int* its, double* relres, int* status);
 
+/*
+ * GMRES-based refinement of every instance of the batch (the batched form of
+ * dg_gmres_ir_solve): per instance, f64 flexible GMRES(params.gmres_m) on the
+ * f64 operator whose preconditioner is the low-precision inner solve
+ * z = A_lo^-1 v, a batched GMRES(inner_m) on f32 vectors with the f32 / bf16
+ * block copy and params.precond (block Jacobi, Schwarz or none), stopped at
+ * inner_tol or after 8 restart cycles.  All instances that take outer step j
+ * run their inner solves together; each instance stops when its own
+ * ||F_i - A_i x_i|| / ||F_i|| <= params.tol, after max_outer outer steps, or
+ * once it has spent params.max_it inner steps.  Converges where plain
+ * refinement stalls (restarted inner GMRES stagnating on diffusion-dominated
+ * instances).  inner_dtype DG_F32 or DG_BF16; arguments as dg_batch_solve,
+ * its = inner Arnoldi steps per instance.  DG_ERR_INVALID_ARG for
+ * DG_PRECOND_MLP.  Synchronises.
+ */
+dg_status dg_batch_gmres_ir_solve(dg_handle* h, int inner_dtype, int inner_m, double inner_tol, int max_outer,
+                                  const double* F, double* x, int* its, double* relres, int* status);
+
 /* ------------------------------------------------------------------------ */
 /* learned right preconditioner (not in the paper; layered on its method)    */
 /* ------------------------------------------------------------------------ */

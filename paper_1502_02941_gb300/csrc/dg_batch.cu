@@ -537,14 +537,68 @@ __global__ void __launch_bounds__(256) k_bo_update(double* __restrict__ x, const
 }
 
 // ---------------------------------------------------------------------------
+// GMRES-based refinement kernels: the outer f64 flexible GMRES lives in state
+// set Bo, the inner batched low-precision GMRES in set B, over the same items
+// ---------------------------------------------------------------------------
+// r = s_j V_j in f32 on the instances taking outer step j (s_j their current
+// basis scale); exactly those instances take part in the inner solve.
+__global__ void __launch_bounds__(256) k_bir_down(const double* __restrict__ Vj, float* __restrict__ r, BatchDev Bo,
+                                                   BatchDev B) {
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < Bo.nI; i += blockDim.x) B.iparticipate[i] = Bo.iactive[i];
+    for (int it = blockIdx.x; it < Bo.nit; it += gridDim.x) {
+        const int inst = Bo.item_inst[it];
+        if (!Bo.iactive[inst]) continue;
+        const double s = Bo.iscale[inst];
+        for (int l = Bo.item_lo[it] + threadIdx.x; l < Bo.item_hi[it]; l += blockDim.x) r[l] = (float)(s * Vj[l]);
+    }
+}
+
+// Z_j = d, the inner solution for s_j V_j, in f64
+__global__ void __launch_bounds__(256) k_bir_up(const float* __restrict__ d, double* __restrict__ Zj, BatchDev Bo) {
+    for (int it = blockIdx.x; it < Bo.nit; it += gridDim.x) {
+        const int inst = Bo.item_inst[it];
+        if (!Bo.iactive[inst]) continue;
+        for (int l = Bo.item_lo[it] + threadIdx.x; l < Bo.item_hi[it]; l += blockDim.x) Zj[l] = (double)d[l];
+    }
+}
+
+// Inner steps per instance; an instance that has spent max_it inner steps
+// makes the current outer step its last (its restart then ends it).
+__global__ void k_bir_tally(BatchDev Bo, BatchDev B, int max_it) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Bo.nI; i += gridDim.x * blockDim.x) {
+        if (!Bo.iactive[i]) continue;
+        BOuter* o = Bo.bo + i;
+        o->used += B.bst[i].its;
+        if (o->used >= max_it) Bo.bst[i].max_it = Bo.bst[i].its + 1;
+    }
+}
+
+// number of instances still taking Arnoldi steps (mid-cycle)
+__global__ void k_b_count(BatchDev B) {
+    __shared__ double sh[32];
+    double c = 0.0;
+    for (int i = threadIdx.x; i < B.nI; i += blockDim.x) c += B.iactive[i];
+    c = dg_block_sum(c, sh);
+    if (threadIdx.x == 0) B.counters[0] = (int)c;
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
+// Item tables (shared) and one or two solver-state sets: the inner batched
+// GMRES uses set 0; the GMRES-based refinement keeps its outer flexible GMRES
+// in set 1 over the same items.
+struct BatchSetOffsets {
+    size_t bst, bo, iactive, ipending, ipart, iouter, iscale, partials, jglob, counters, iuse;
+};
 struct BatchHostLayout {
-    size_t off_bst, off_bo, off_iactive, off_ipending, off_ipart, off_iouter, off_iscale, off_item_inst, off_item_lo,
-        off_item_hi, off_iilo, off_iihi, off_partials, off_jglob, off_counters, off_iuse, total;
+    size_t item_inst, item_lo, item_hi, iilo, iihi;
+    BatchSetOffsets set[2];
+    size_t total;
 };
 
-static BatchHostLayout batch_layout(int nI, int nit) {
+static BatchHostLayout batch_layout(int nI, int nit, int nsets) {
     BatchHostLayout L{};
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -552,22 +606,25 @@ static BatchHostLayout batch_layout(int nI, int nit) {
         o = (o + bytes + 255) & ~(size_t)255;
         return r;
     };
-    L.off_bst = take(sizeof(BState) * nI);
-    L.off_bo = take(sizeof(BOuter) * nI);
-    L.off_iactive = take(sizeof(int) * nI);
-    L.off_ipending = take(sizeof(int) * nI);
-    L.off_ipart = take(sizeof(int) * nI);
-    L.off_iouter = take(sizeof(int) * nI);
-    L.off_iscale = take(sizeof(double) * nI);
-    L.off_item_inst = take(sizeof(int) * nit);
-    L.off_item_lo = take(sizeof(int) * nit);
-    L.off_item_hi = take(sizeof(int) * nit);
-    L.off_iilo = take(sizeof(int) * nI);
-    L.off_iihi = take(sizeof(int) * nI);
-    L.off_partials = take(sizeof(double) * (size_t)nit * (DG_MAXM + 2));
-    L.off_jglob = take(sizeof(int));
-    L.off_counters = take(sizeof(int) * 4);
-    L.off_iuse = take(sizeof(int) * nI);
+    L.item_inst = take(sizeof(int) * nit);
+    L.item_lo = take(sizeof(int) * nit);
+    L.item_hi = take(sizeof(int) * nit);
+    L.iilo = take(sizeof(int) * nI);
+    L.iihi = take(sizeof(int) * nI);
+    for (int k = 0; k < nsets; ++k) {
+        BatchSetOffsets& S = L.set[k];
+        S.bst = take(sizeof(BState) * nI);
+        S.bo = take(sizeof(BOuter) * nI);
+        S.iactive = take(sizeof(int) * nI);
+        S.ipending = take(sizeof(int) * nI);
+        S.ipart = take(sizeof(int) * nI);
+        S.iouter = take(sizeof(int) * nI);
+        S.iscale = take(sizeof(double) * nI);
+        S.partials = take(sizeof(double) * (size_t)nit * (DG_MAXM + 2));
+        S.jglob = take(sizeof(int));
+        S.counters = take(sizeof(int) * 4);
+        S.iuse = take(sizeof(int) * nI);
+    }
     L.total = o;
     return L;
 }
@@ -630,8 +687,10 @@ extern "C" dg_status dg_batch_clear(dg_handle* h) {
     return DG_OK;
 }
 
-// Build the item list for degree nb and tile size; returns the layout.
-static dg_status batch_tables(dg_handle* h, int nb, int tile, BatchDev& B, BatchHostLayout& L) {
+// Build the item list for degree nb and tile size and bind the state set(s):
+// B gets set 0; B2, if given, set 1 over the same items.
+static dg_status batch_tables(dg_handle* h, int nb, int tile, BatchDev& B, BatchHostLayout& L,
+                              BatchDev* B2 = nullptr) {
     std::vector<int> iinst, ilo, ihi, iilo(h->b_n), iihi(h->b_n);
     for (int i = 0; i < h->b_n; ++i) {
         const long lo = (long)h->b_elem_start[i] * nb, hi = (long)h->b_elem_start[i + 1] * nb;
@@ -644,28 +703,32 @@ static dg_status batch_tables(dg_handle* h, int nb, int tile, BatchDev& B, Batch
         iihi[i] = (int)iinst.size();
     }
     const int nit = (int)iinst.size();
-    L = batch_layout(h->b_n, nit);
+    L = batch_layout(h->b_n, nit, B2 ? 2 : 1);
     dg_status s;
     if ((s = dg_ensure(h, &h->b_dev, &h->cap_bdev, L.total)) != DG_OK) return s;
     char* base = (char*)h->b_dev;
-    B.bst = (BState*)(base + L.off_bst);
-    B.bo = (BOuter*)(base + L.off_bo);
-    B.iactive = (int*)(base + L.off_iactive);
-    B.ipending = (int*)(base + L.off_ipending);
-    B.iparticipate = (int*)(base + L.off_ipart);
-    B.iouter = (int*)(base + L.off_iouter);
-    B.iscale = (double*)(base + L.off_iscale);
-    B.item_inst = (int*)(base + L.off_item_inst);
-    B.item_lo = (int*)(base + L.off_item_lo);
-    B.item_hi = (int*)(base + L.off_item_hi);
-    B.inst_item_lo = (int*)(base + L.off_iilo);
-    B.inst_item_hi = (int*)(base + L.off_iihi);
-    B.partials = (double*)(base + L.off_partials);
-    B.jglob = (int*)(base + L.off_jglob);
-    B.counters = (int*)(base + L.off_counters);
-    B.iuse = nullptr;
-    B.nI = h->b_n;
-    B.nit = nit;
+    auto bind = [&](BatchDev& D, const BatchSetOffsets& S) {
+        D.bst = (BState*)(base + S.bst);
+        D.bo = (BOuter*)(base + S.bo);
+        D.iactive = (int*)(base + S.iactive);
+        D.ipending = (int*)(base + S.ipending);
+        D.iparticipate = (int*)(base + S.ipart);
+        D.iouter = (int*)(base + S.iouter);
+        D.iscale = (double*)(base + S.iscale);
+        D.item_inst = (int*)(base + L.item_inst);
+        D.item_lo = (int*)(base + L.item_lo);
+        D.item_hi = (int*)(base + L.item_hi);
+        D.inst_item_lo = (int*)(base + L.iilo);
+        D.inst_item_hi = (int*)(base + L.iihi);
+        D.partials = (double*)(base + S.partials);
+        D.jglob = (int*)(base + S.jglob);
+        D.counters = (int*)(base + S.counters);
+        D.iuse = nullptr;
+        D.nI = h->b_n;
+        D.nit = nit;
+    };
+    bind(B, L.set[0]);
+    if (B2) bind(*B2, L.set[1]);
     DG_CK(h, cudaMemsetAsync(h->b_dev, 0, L.total, h->stream));
     DG_CK(h, cudaMemcpyAsync(B.item_inst, iinst.data(), sizeof(int) * nit, cudaMemcpyHostToDevice, h->stream));
     DG_CK(h, cudaMemcpyAsync(B.item_lo, ilo.data(), sizeof(int) * nit, cudaMemcpyHostToDevice, h->stream));
@@ -840,7 +903,7 @@ static dg_status batch_solve_t(dg_handle* h, int inner_dtype, const TA* Alo, con
     Rn.Zb = f64 ? (void*)r64 : (void*)(din + ld);
     DG_CK(h, cudaMemsetAsync(h->mx_buf, 0, vbytes, h->stream));
     if (flex) {
-        Rn.B.iuse = (int*)((char*)h->b_dev + L.off_iuse);
+        Rn.B.iuse = (int*)((char*)h->b_dev + L.set[0].iuse);
         std::vector<int> ones(h->b_n, 1);
         DG_CK(h, cudaMemcpyAsync(Rn.B.iuse, ones.data(), sizeof(int) * h->b_n, cudaMemcpyHostToDevice, h->stream));
         const int one = 1;
@@ -968,6 +1031,165 @@ extern "C" dg_status dg_batch_solve(dg_handle* h, int inner_dtype, int inner_m, 
     DG_BATCH(6)
     DG_BATCH(10)
 #undef DG_BATCH
+    return dg_fail(h, DG_ERR_INVALID_ARG, "degree");
+}
+
+// GMRES-based refinement of every instance: f64 flexible GMRES(params.gmres_m)
+// on A64 (state set 1) whose preconditioner is the batched low-precision
+// GMRES(inner_m) (state set 0), run for all instances taking outer step j at
+// once.  The outer loop is driven from the host, one outer step at a time;
+// each inner solve is the captured cycle graph of b_gmres.
+template <int NB, typename TA, typename TB>
+static dg_status batch_ir_t(dg_handle* h, const TA* Alo, const TB* Binv, int inner_m, double inner_tol,
+                            int max_outer, const double* F, double* x, int* its_out, double* relres_out,
+                            int* status_out) {
+    const long n = (long)h->ne * NB;
+    const long ld = (n + 63) / 64 * 64;
+    const int mo = h->p.gmres_m;
+    BatchRun Rn{};
+    BatchDev Bo{};
+    BatchHostLayout L;
+    const int tile = h->b_tile > 0 ? h->b_tile : 4096;
+    dg_status s = batch_tables(h, NB, tile, Rn.B, L, &Bo);
+    if (s != DG_OK) return s;
+    // outer (f64): V (mo+2) x ld, Z (mo+1) x ld, R; inner (f32): V (inner_m+2) x ld, Z, R, r, d
+    const size_t b64 = ((size_t)(mo + 2) * ld + (size_t)(mo + 1) * ld + (size_t)ld) * sizeof(double);
+    const size_t b32 = ((size_t)(inner_m + 2) * ld + 4 * (size_t)ld) * sizeof(float);
+    const size_t vbytes = b64 + b32 + 1024;
+    if ((s = dg_ensure(h, &h->mx_buf, &h->cap_mx, vbytes)) != DG_OK) return s;
+    double* Vo = (double*)h->mx_buf;
+    double* Zo = Vo + (size_t)(mo + 2) * ld;
+    double* Ro = Zo + (size_t)(mo + 1) * ld;
+    float* v32 = (float*)(Ro + ld);
+    Rn.V = v32;
+    Rn.Z = v32 + (size_t)(inner_m + 2) * ld;
+    Rn.R = (float*)Rn.Z + ld;
+    float* r32 = (float*)Rn.R + ld;
+    float* d32 = r32 + ld;
+    Rn.Zb = nullptr;
+    Rn.ld = ld;
+    Rn.m = inner_m;
+    DG_CK(h, cudaMemsetAsync(h->mx_buf, 0, vbytes, h->stream));
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    Rn.gsm = sms;
+    Rn.gx = 4 * sms;
+    if (!h->b_host) {
+        DG_CK(h, cudaMallocHost(&h->b_host, 64));
+        h->cap_bhost = 64;
+    }
+    int* cnt = (int*)h->b_host;   // [0..3] inner counters, [8..11] outer counters (pinned)
+    int* ocnt = cnt + 8;
+    std::vector<int> one(h->b_n, 1);
+    DG_CK(h, cudaMemcpyAsync(Bo.iparticipate, one.data(), sizeof(int) * h->b_n, cudaMemcpyHostToDevice, h->stream));
+    k_b_init<double><<<Rn.gx, 256, 0, h->stream>>>(F, x, Vo, Bo, mo, max_outer, h->p.tol);
+    DG_CK(h, cudaMemsetAsync(Bo.jglob, 0, sizeof(int), h->stream));
+    k_b_cycle_end<<<1, 1024, 0, h->stream>>>(Bo);
+    h->nlaunch += 2;
+    DG_LAUNCH_CK(h);
+    DG_CK(h, cudaMemcpyAsync(ocnt, Bo.counters, sizeof(int) * 4, cudaMemcpyDeviceToHost, h->stream));
+    DG_CK(h, cudaStreamSynchronize(h->stream));
+    const int cap = std::min(h->p.max_it, DG_INNER_CYCLES * inner_m);
+    const unsigned ge = (unsigned)((h->ne + 255) / 256);
+    const unsigned gi = (unsigned)((h->b_n + 255) / 256);
+    const DevCtl oact{nullptr, nullptr, h->b_inst, Bo.iactive, nullptr};
+    const DevCtl opend{nullptr, nullptr, h->b_inst, Bo.ipending, nullptr};
+    dg_status result = DG_OK;
+    for (int cycle = 0; ocnt[0] > 0 && cycle <= max_outer + 1; ++cycle) {
+        for (int j = 0; j < mo && ocnt[0] > 0; ++j) {
+            // Z_j = A_lo^-1 s_j V_j (batched inner solve), V_{j+1} = A64 Z_j,
+            // Gram-Schmidt and Givens step per instance
+            k_bir_down<<<Rn.gx, 256, 0, h->stream>>>(Vo + (size_t)j * ld, r32, Bo, Rn.B);
+            h->nlaunch += 1;
+            s = b_gmres<NB, TA, TB, float>(h, Rn, Alo, Binv, r32, d32, inner_tol, cap, cnt);
+            if (s != DG_OK) {
+                result = s;
+                break;
+            }
+            k_bir_up<<<Rn.gx, 256, 0, h->stream>>>(d32, Zo + (size_t)j * ld, Bo);
+            k_bir_tally<<<gi, 256, 0, h->stream>>>(Bo, Rn.B, h->p.max_it);
+            k_apply<NB, double, double, double><<<ge, 256, 0, h->stream>>>(
+                h->A64, h->nbr, Zo + (size_t)j * ld, Vo + (size_t)(j + 1) * ld, h->ne, oact, vsel_fixed(),
+                vsel_fixed());
+            for (int pass = 1; pass <= 2; ++pass) {
+                k_b_dots<double><<<Rn.gsm, dim3(B_TX, B_TY), 0, h->stream>>>(Vo, ld, Bo, pass);
+                k_b_update<double><<<Rn.gx, 256, 0, h->stream>>>(Vo, ld, Bo, pass);
+            }
+            k_b_step<<<1, 32, 0, h->stream>>>(Bo);
+            k_b_count<<<1, 1024, 0, h->stream>>>(Bo);
+            h->nlaunch += 10;
+            DG_LAUNCH_CK(h);
+            DG_CK(h, cudaMemcpyAsync(ocnt, Bo.counters, sizeof(int) * 4, cudaMemcpyDeviceToHost, h->stream));
+            DG_CK(h, cudaStreamSynchronize(h->stream));
+        }
+        if (result != DG_OK) break;
+        // x += Z y; true f64 residual; restart or stop per instance
+        k_b_solve<<<h->b_n, 256, 0, h->stream>>>(Bo, 1);
+        k_b_combine<double><<<Rn.gx, 256, 0, h->stream>>>(Zo, ld, Bo, Ro);
+        k_b_axpy<double><<<Rn.gx, 256, 0, h->stream>>>(x, Ro, Bo);
+        k_apply<NB, double, double, double><<<ge, 256, 0, h->stream>>>(h->A64, h->nbr, x, Ro, h->ne, opend,
+                                                                       vsel_fixed(), vsel_fixed());
+        k_b_resid<double><<<Rn.gx, 256, 0, h->stream>>>(F, Ro, Vo, Bo);
+        k_b_cycle_end<<<1, 1024, 0, h->stream>>>(Bo);
+        h->nlaunch += 6;
+        DG_LAUNCH_CK(h);
+        DG_CK(h, cudaMemcpyAsync(ocnt, Bo.counters, sizeof(int) * 4, cudaMemcpyDeviceToHost, h->stream));
+        DG_CK(h, cudaStreamSynchronize(h->stream));
+    }
+    std::vector<BState> hst(h->b_n);
+    std::vector<BOuter> hbo(h->b_n);
+    DG_CK(h, cudaMemcpyAsync(hst.data(), Bo.bst, sizeof(BState) * h->b_n, cudaMemcpyDeviceToHost, h->stream));
+    DG_CK(h, cudaMemcpyAsync(hbo.data(), Bo.bo, sizeof(BOuter) * h->b_n, cudaMemcpyDeviceToHost, h->stream));
+    DG_CK(h, cudaStreamSynchronize(h->stream));
+    int nconv = 0;
+    for (int i = 0; i < h->b_n; ++i) {
+        const bool ok = hst[i].converged && hst[i].relres <= h->p.tol;
+        nconv += ok;
+        if (its_out) its_out[i] = hbo[i].used;
+        if (relres_out) relres_out[i] = hst[i].relres;
+        if (status_out) status_out[i] = ok ? DG_OK : DG_NOT_CONVERGED;
+    }
+    if (result != DG_OK) return result;
+    if (ocnt[1] > 0) return dg_fail(h, DG_ERR_NONFINITE, "NaN/Inf in the batched outer FGMRES");
+    if (nconv < h->b_n)
+        return dg_fail(h, DG_NOT_CONVERGED, std::to_string(h->b_n - nconv) + " instances did not converge");
+    return DG_OK;
+}
+
+extern "C" dg_status dg_batch_gmres_ir_solve(dg_handle* h, int inner_dtype, int inner_m, double inner_tol,
+                                             int max_outer, const double* F, double* x, int* its, double* relres,
+                                             int* status) {
+    if (!h || !x) return DG_ERR_INVALID_ARG;
+    h->basis = nullptr;
+    if (!h->b_inst_active || h->b_n < 1) return dg_fail(h, DG_ERR_STATE, "no batch set up");
+    if (!h->assembled) return dg_fail(h, DG_ERR_STATE, "not assembled");
+    if (!h->A64) return dg_fail(h, DG_ERR_STATE, "the f64 blocks are needed for the outer FGMRES");
+    if (inner_dtype != DG_F32 && inner_dtype != DG_BF16) return dg_fail(h, DG_ERR_INVALID_ARG, "inner_dtype");
+    if (inner_dtype == DG_F32 && !h->A32) return dg_fail(h, DG_ERR_STATE, "f32 blocks not stored");
+    if (inner_dtype == DG_BF16 && !h->A16) return dg_fail(h, DG_ERR_STATE, "bf16 blocks not stored");
+    if (inner_m < 1 || inner_m > DG_MAXM || !(inner_tol > 0.0 && inner_tol < 1.0) || max_outer < 1)
+        return dg_fail(h, DG_ERR_INVALID_ARG, "inner_m / inner_tol / max_outer");
+    if (h->p.precond == DG_PRECOND_MLP)
+        return dg_fail(h, DG_ERR_INVALID_ARG, "the inner solve takes block Jacobi, Schwarz or none");
+    if (h->p.precond != DG_PRECOND_NONE && (!h->bj_ok || (h->p.precond == DG_PRECOND_SCHWARZ && !h->ras_ok))) {
+        dg_status s = dg_precond_setup(h, h->p.precond);
+        if (s != DG_OK) return s;
+    }
+    DG_CK(h, cudaSetDevice(h->device));
+    if (!F) F = h->F;
+    const bool pj = h->p.precond != DG_PRECOND_NONE;
+    const int nb = dg_nb(h->asm_k);
+#define DG_BIR(NBV)                                                                                           \
+    if (nb == NBV)                                                                                            \
+        return inner_dtype == DG_F32                                                                          \
+                   ? batch_ir_t<NBV, float, float>(h, h->A32, pj ? h->Binv32 : nullptr, inner_m, inner_tol,   \
+                                                   max_outer, F, x, its, relres, status)                      \
+                   : batch_ir_t<NBV, __nv_bfloat16, float>(h, h->A16, pj ? h->Binv16 : nullptr, inner_m,      \
+                                                           inner_tol, max_outer, F, x, its, relres, status);
+    DG_BIR(3)
+    DG_BIR(6)
+    DG_BIR(10)
+#undef DG_BIR
     return dg_fail(h, DG_ERR_INVALID_ARG, "degree");
 }
 

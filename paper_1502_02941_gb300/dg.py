@@ -99,6 +99,8 @@ _SIGS = {
     "dg_batch_set_tile": (ctypes.c_int, [c_void_p, ctypes.c_int]),
     "dg_batch_solve": (ctypes.c_int, [c_void_p, ctypes.c_int, ctypes.c_int, c_double, ctypes.c_int, c_void_p,
                                       c_void_p, c_void_p, c_void_p, c_void_p]),
+    "dg_batch_gmres_ir_solve": (ctypes.c_int, [c_void_p, ctypes.c_int, ctypes.c_int, c_double, ctypes.c_int,
+                                               c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "dg_mlp_num_params": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(c_int64)]),
     "dg_mlp_init": (ctypes.c_int, [c_void_p, ctypes.c_uint64]),
     "dg_mlp_set_weights": (ctypes.c_int, [c_void_p, c_void_p, c_int64]),
@@ -330,6 +332,12 @@ def dg_batch_set_tile(h, tile):
 def dg_batch_solve(h, inner_dtype, inner_m, inner_tol, max_outer, F, x, its=None, relres=None, status=None):
     return load().dg_batch_solve(h, int(inner_dtype), int(inner_m), float(inner_tol), int(max_outer), _ptr(F),
                                  _ptr(x), _ptr(its), _ptr(relres), _ptr(status))
+
+
+def dg_batch_gmres_ir_solve(h, inner_dtype, inner_m, inner_tol, max_outer, F, x, its=None, relres=None,
+                            status=None):
+    return load().dg_batch_gmres_ir_solve(h, int(inner_dtype), int(inner_m), float(inner_tol), int(max_outer),
+                                          _ptr(F), _ptr(x), _ptr(its), _ptr(relres), _ptr(status))
 
 
 def dg_mlp_num_params(degree):
@@ -594,6 +602,17 @@ class DG:
         n = self.batch_n
         its = np.zeros(n, np.int32); rr = np.zeros(n); st = np.zeros(n, np.int32)
         s = dg_batch_solve(self.h, inner_dtype, inner_m, inner_tol, max_outer, F, x, its, rr, st)
+        if s != DG_OK and not (s == DG_NOT_CONVERGED and not raise_on_nonconv):
+            self.check(s)
+        return x, its, rr, st
+
+    def batch_gmres_ir_solve(self, inner_dtype=DG_F32, inner_m=32, inner_tol=1e-3, max_outer=500, F=None, x=None,
+                             raise_on_nonconv=True):
+        i = self.info()
+        x = self._empty((i.dofs,)) if x is None else x
+        n = self.batch_n
+        its = np.zeros(n, np.int32); rr = np.zeros(n); st = np.zeros(n, np.int32)
+        s = dg_batch_gmres_ir_solve(self.h, inner_dtype, inner_m, inner_tol, max_outer, F, x, its, rr, st)
         if s != DG_OK and not (s == DG_NOT_CONVERGED and not raise_on_nonconv):
             self.check(s)
         return x, its, rr, st

@@ -45,8 +45,10 @@ def setup_batch(h: D.DG, cfgs, ma: W.MeshArrays, elem_start, coeffs, store=D.DG_
     instance's f at its own volume points (gD = gN = 0: homogeneous Dirichlet
     data on every instance) and assemble all instances in one pass."""
     torch = h.torch
-    h.mesh_upload(ma.nodes, ma.elems, ma.dirichlet, ma.neumann)
     k = cfgs[0].k
+    if any(c.k != k for c in cfgs) or any(c.method != cfgs[0].method for c in cfgs):
+        raise ValueError("the instances of one batch share the degree and the method")
+    h.mesh_upload(ma.nodes, ma.elems, ma.dirichlet, ma.neumann)
     h.set_params(method=cfgs[0].method, degree=k, sigma_int=0.0, store=store, **params)
     h.batch_setup(elem_start, coeffs)
     xq = h.quad_points(D.DG_POINTS_VOLUME)

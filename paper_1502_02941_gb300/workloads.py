@@ -269,6 +269,23 @@ def random_instance(config_id: int, instance: int, N_range=(16, 128), k_choices=
     return Config(f"cfg{config_id}_inst{instance}", N, k, 2, prob)
 
 
+def batch_by_degree(config_id: int, n_inst: int, N_range=(16, 128)):
+    """Instances 0..n_inst-1 of the batched workload grouped by their degree:
+    {k: (cfgs, mesh, elem_start, coeffs)}, one batch per degree (a batch shares
+    k), each instance keeping its own draw."""
+    groups: dict[int, list] = {}
+    for i in range(n_inst):
+        c = random_instance(config_id, i, N_range=N_range)
+        groups.setdefault(c.k, []).append(c)
+    out = {}
+    for k in sorted(groups):
+        cfgs = groups[k]
+        ma, starts = concat_meshes([structured_mesh(c.N) for c in cfgs])
+        coeffs = np.array([[c.problem.eps, c.problem.alpha, *c.problem.b] for c in cfgs])
+        out[k] = (cfgs, ma, starts, coeffs)
+    return out
+
+
 def concat_meshes(meshes):
     """Concatenate independent meshes into one (node and element ids offset);
     returns the MeshArrays and elem_start [len+1] (instance i owns elements
