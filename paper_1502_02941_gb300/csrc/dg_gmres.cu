@@ -229,6 +229,8 @@ __device__ void gm_finish_column(GmresState* st, double wn, const double* hc, co
 template <typename TV>
 __global__ void __launch_bounds__(GM_TX* GM_TY) k_gm_dots(const TV* __restrict__ V, long ld, long nvec,
                                                          GmresState* st, double* partials, int pass) {
+    dg_grid_release();
+    dg_grid_wait();
     if (!st->active || (pass == 2 && !st->reorth)) return;
     using VT = typename Vec<TV>::T;
     constexpr int W = Vec<TV>::W;
@@ -349,6 +351,8 @@ __global__ void __launch_bounds__(GM_TX* GM_TY) k_gm_dots(const TV* __restrict__
 // update does not need it; the next step does).
 template <typename TV>
 __global__ void __launch_bounds__(256) k_gm_update(TV* V, long ld, long nvec, GmresState* st, int pass) {
+    dg_grid_release();
+    dg_grid_wait();
     if (blockIdx.x == 0) {
         __shared__ double hc[DG_MAXM + 2], css[DG_MAXM], sns[DG_MAXM];
         if (!st->colready) return;
@@ -504,14 +508,17 @@ __global__ void __launch_bounds__(256) k_gm_resid(const TV* __restrict__ F, cons
 // host side
 // ---------------------------------------------------------------------------
 template <int NB, typename TA, typename TV>
-static void launch_apply(dg_handle* h, const TA* A, const TV* x, TV* y, DevCtl ctl, VecSel sx, VecSel sy) {
+static void launch_apply(dg_handle* h, const TA* A, const TV* x, TV* y, DevCtl ctl, VecSel sx, VecSel sy,
+                         bool pdl = false) {
     const unsigned grid = (unsigned)((h->ne + 255) / 256);
-    k_apply<NB, TA, TV, TV><<<grid, 256, 0, h->stream>>>(A, h->nbr, x, y, h->ne, ctl, sx, sy);
+    dg_launch(h, pdl, k_apply<NB, TA, TV, TV>, dim3(grid), dim3(256), A, (const int*)h->nbr, x, y, h->ne, ctl, sx,
+              sy);
 }
 template <int NB, typename TB, typename TV>
-static void launch_bj(dg_handle* h, const TB* B, const TV* r, TV* z, DevCtl ctl, VecSel sr, VecSel sz) {
+static void launch_bj(dg_handle* h, const TB* B, const TV* r, TV* z, DevCtl ctl, VecSel sr, VecSel sz,
+                      bool pdl = false) {
     const unsigned grid = (unsigned)((h->ne + 255) / 256);
-    k_bj_apply<NB, TB, TV, TV><<<grid, 256, 0, h->stream>>>(B, r, z, h->ne, ctl, sr, sz);
+    dg_launch(h, pdl, k_bj_apply<NB, TB, TV, TV>, dim3(grid), dim3(256), B, r, z, h->ne, ctl, sr, sz);
 }
 
 // One restart cycle: m Arnoldi steps, the correction and the true residual.
@@ -533,30 +540,34 @@ static int enqueue_cycle(dg_handle* h, GmresWork& W, const TA* A, const TB* B, c
     DevCtl step{&st->active, st->scale};
     DevCtl step_noscale{&st->active, nullptr};
     VecSel vj{&st->j, 0, ld}, vj1{&st->j, 1, ld};
+    // the Arnoldi-step kernels are launched programmatically dependent on their
+    // predecessor (each waits for it before reading), so launch latency and the
+    // predecessor's tail overlap
+    const bool pdl = h->pdl && h->stream != nullptr;
     int extra = 0;
     for (int it = 0; it < W.m; ++it) {
         if (flex) {
             // Z_j = s_j M_BJ^-1 V_j + MLP correction, kept for the update of x
             VecSel zj{&st->j, 0, ld};
-            launch_bj<NB, TB, TV>(h, B, V, Zb, step, vj, zj);
+            launch_bj<NB, TB, TV>(h, B, V, Zb, step, vj, zj, pdl);
             dg_mlp_correct<TV>(h, V, Zb, step, vj, zj, nullptr);
-            launch_apply<NB, TA, TV>(h, A, Zb, V, step_noscale, zj, vj1);
+            launch_apply<NB, TA, TV>(h, A, Zb, V, step_noscale, zj, vj1, pdl);
             ++extra;
         } else if (G) {
             // Schwarz: Z = s_j G V_j, V_{j+1} = A Z (two applies)
-            launch_apply<NB, TV, TV>(h, G, V, Z, step, vj, vsel_fixed());
-            launch_apply<NB, TA, TV>(h, A, Z, V, step_noscale, vsel_fixed(), vj1);
+            launch_apply<NB, TV, TV>(h, G, V, Z, step, vj, vsel_fixed(), pdl);
+            launch_apply<NB, TA, TV>(h, A, Z, V, step_noscale, vsel_fixed(), vj1, pdl);
         } else if (Ah) {
             // V_{j+1} = s_j (A M^-1) V_j: one apply of the precomputed operator
-            launch_apply<NB, TA, TV>(h, Ah, V, V + ld, step, vj, vj);
+            launch_apply<NB, TA, TV>(h, Ah, V, V + ld, step, vj, vj, pdl);
             --extra;
         } else {
-            launch_bj<NB, TB, TV>(h, B, V, Z, step, vj, vsel_fixed());
-            launch_apply<NB, TA, TV>(h, A, Z, V, step_noscale, vsel_fixed(), vj1);
+            launch_bj<NB, TB, TV>(h, B, V, Z, step, vj, vsel_fixed(), pdl);
+            launch_apply<NB, TA, TV>(h, A, Z, V, step_noscale, vsel_fixed(), vj1, pdl);
         }
         for (int pass = 1; pass <= 2; ++pass) {
-            k_gm_dots<TV><<<gdots, bdots, 0, h->stream>>>(V, ld, nvec, st, W.partials, pass);
-            k_gm_update<TV><<<gx + 1, 256, 0, h->stream>>>(V, ld, nvec, st, pass);
+            dg_launch(h, pdl, k_gm_dots<TV>, dim3(gdots), bdots, (const TV*)V, ld, nvec, st, W.partials, pass);
+            dg_launch(h, pdl, k_gm_update<TV>, dim3(gx + 1), dim3(256), V, ld, nvec, st, pass);
         }
     }
     DevCtl pend{&st->pending, nullptr};

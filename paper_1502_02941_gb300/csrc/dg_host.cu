@@ -3,6 +3,7 @@
 // copies out of the handle.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <string>
@@ -117,6 +118,8 @@ extern "C" dg_status dg_create(dg_handle** out, int device, void* stream) {
     dg_handle* h = new dg_handle();
     h->device = device;
     h->stream = (cudaStream_t)stream;
+    const char* pdl = getenv("DG_PDL");
+    h->pdl = !(pdl && pdl[0] == '0');
     dg_params_default(&h->p);
     if (dg_realloc(h, (void**)&h->dflag, 64) != DG_OK) {
         delete h;

@@ -197,6 +197,7 @@ struct dg_handle {
 
     MlpState mlp;
     bool mlp_fallback = false;     // the last flexible solve switched the MLP off
+    bool pdl = true;               // programmatic dependent launch of the Arnoldi-step kernels
     // Krylov basis of the last f64 solve (dg_gmres_solve / dg_batch_solve with
     // DG_F64): basis_n vectors of leading dimension basis_ld (f64, unnormalised);
     // cleared when another solve starts
@@ -242,9 +243,34 @@ dg_status dg_launch_bj_setup(dg_handle* h);
 dg_status dg_launch_bj_apply(dg_handle* h, int dtype, const void* r, void* z, const double* scale);
 void dg_gmres_free(GmresWork* w);
 
+// Launch on h->stream; with `pdl` the kernel carries the programmatic
+// stream-serialisation attribute, so it may be scheduled while its predecessor
+// still runs.  Such a kernel calls dg_grid_release() and then dg_grid_wait()
+// before it reads anything an earlier kernel wrote, on every path.
+template <typename... KArgs, typename... Args>
+static inline void dg_launch(dg_handle* h, bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block,
+                             Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = h->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // ---------------------------------------------------------------------------
 // device helpers
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch (no-ops for a kernel launched without the
+// attribute): release lets the next kernel in the stream be scheduled; wait
+// returns once the preceding kernel has completed and its writes are visible.
+__device__ __forceinline__ void dg_grid_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void dg_grid_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ double dg_warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
