@@ -157,9 +157,10 @@ typedef struct dg_handle dg_handle;
 
 /* Create a handle on CUDA device `device`, issuing work on `stream`
    (a cudaStream_t; NULL = the legacy default stream).  *h receives the handle.
-   The solvers launch their Arnoldi-step kernels with programmatic dependent
-   launch (each kernel may be scheduled while its predecessor finishes);
-   the environment variable DG_PDL=0, read here, turns that off. */
+   The solvers launch the Arnoldi-step kernels of their f32 (inner) GMRES with
+   programmatic dependent launch (each kernel may be scheduled while its
+   predecessor finishes); the environment variable DG_PDL=0, read here, turns
+   that off. */
 dg_status dg_create(dg_handle** h, int device, void* stream);
 /* Free the handle and all device memory it owns.  NULL is accepted. */
 dg_status dg_destroy(dg_handle* h);

@@ -229,8 +229,10 @@ __device__ void gm_finish_column(GmresState* st, double wn, const double* hc, co
 template <typename TV>
 __global__ void __launch_bounds__(GM_TX* GM_TY) k_gm_dots(const TV* __restrict__ V, long ld, long nvec,
                                                          GmresState* st, double* partials, int pass) {
-    dg_grid_release();
-    dg_grid_wait();
+    if constexpr (sizeof(TV) == 4) {   // programmatic dependent launch (f32 solves)
+        dg_grid_release();
+        dg_grid_wait();
+    }
     if (!st->active || (pass == 2 && !st->reorth)) return;
     using VT = typename Vec<TV>::T;
     constexpr int W = Vec<TV>::W;
@@ -351,8 +353,10 @@ __global__ void __launch_bounds__(GM_TX* GM_TY) k_gm_dots(const TV* __restrict__
 // update does not need it; the next step does).
 template <typename TV>
 __global__ void __launch_bounds__(256) k_gm_update(TV* V, long ld, long nvec, GmresState* st, int pass) {
-    dg_grid_release();
-    dg_grid_wait();
+    if constexpr (sizeof(TV) == 4) {   // programmatic dependent launch (f32 solves)
+        dg_grid_release();
+        dg_grid_wait();
+    }
     if (blockIdx.x == 0) {
         __shared__ double hc[DG_MAXM + 2], css[DG_MAXM], sns[DG_MAXM];
         if (!st->colready) return;
@@ -540,10 +544,13 @@ static int enqueue_cycle(dg_handle* h, GmresWork& W, const TA* A, const TB* B, c
     DevCtl step{&st->active, st->scale};
     DevCtl step_noscale{&st->active, nullptr};
     VecSel vj{&st->j, 0, ld}, vj1{&st->j, 1, ld};
-    // the Arnoldi-step kernels are launched programmatically dependent on their
-    // predecessor (each waits for it before reading), so launch latency and the
-    // predecessor's tail overlap
-    const bool pdl = h->pdl && h->stream != nullptr;
+    // f32 vectors: the Arnoldi-step kernels are launched programmatically
+    // dependent on their predecessor (each waits for it before reading), so
+    // launch latency and the predecessor's tail overlap.  Not for f64: the
+    // early-scheduled blocks pile onto the SMs that free up first, and the
+    // FP64-bound kernels then run unbalanced (measured 4.90 against 5.36
+    // solves/s on the 256x256 P2 workload; f32 refinement 12.74 against 12.64)
+    const bool pdl = h->pdl && h->stream != nullptr && sizeof(TV) == 4;
     int extra = 0;
     for (int it = 0; it < W.m; ++it) {
         if (flex) {

@@ -134,17 +134,23 @@ __global__ void __launch_bounds__(256) k_apply(const TA* __restrict__ A, const i
     using CH = Chunk<TA, TACC>;
     constexpr int W = CH::W;
     constexpr int C = (NB * NB + W - 1) / W;
-    dg_grid_release();
     const int K = blockIdx.x * blockDim.x + threadIdx.x;
-    // the adjacency is constant: read it before waiting for the previous kernel
     int Ls[4] = {K, -1, -1, -1};
-    if (K < ne)
+    if constexpr (sizeof(TX) == 4) {
+        // f32 solves launch this kernel programmatically dependent on its
+        // predecessor; the adjacency is constant, so it is read before the wait
+        dg_grid_release();
+        if (K < ne)
 #pragma unroll
-        for (int f = 0; f < 3; ++f) Ls[1 + f] = __ldg(nbr + (size_t)f * ne + K);
-    dg_grid_wait();
+            for (int f = 0; f < 3; ++f) Ls[1 + f] = __ldg(nbr + (size_t)f * ne + K);
+        dg_grid_wait();
+    }
     if (ctl.active && !*ctl.active) return;
     if (K >= ne) return;
     if (ctl.inst && !ctl.iactive[ctl.inst[K]]) return;
+    if constexpr (sizeof(TX) != 4)
+#pragma unroll
+        for (int f = 0; f < 3; ++f) Ls[1 + f] = __ldg(nbr + (size_t)f * ne + K);
     const TX* __restrict__ x = sel(x0, sx);
     TX* __restrict__ y = sel(y0, sy);
     const int tile = K >> 5, lane = K & 31;
@@ -185,8 +191,10 @@ __global__ void __launch_bounds__(256) k_bj_apply(const TA* __restrict__ B, cons
     using CH = Chunk<TA, TACC>;
     constexpr int W = CH::W;
     constexpr int C = (NB * NB + W - 1) / W;
-    dg_grid_release();
-    dg_grid_wait();
+    if constexpr (sizeof(TX) == 4) {   // programmatic dependent launch (f32 solves)
+        dg_grid_release();
+        dg_grid_wait();
+    }
     if (ctl.active && !*ctl.active) return;
     const int K = blockIdx.x * blockDim.x + threadIdx.x;
     if (K >= ne) return;
