@@ -253,25 +253,22 @@ static dg_status ras_setup(dg_handle* h) {
 // ---------------------------------------------------------------------------
 template <int NB>
 static dg_status apply_nb(dg_handle* h, int dtype, const void* x, void* y) {
-    const unsigned grid = (unsigned)((h->ne + 255) / 256);
+    const ElemShape es = elem_shape(h);
     switch (dtype) {
         case DG_F64:
             if (!h->A64) return dg_fail(h, DG_ERR_STATE, "f64 blocks not stored");
-            k_apply<NB, double, double, double><<<grid, 256, 0, h->stream>>>(h->A64, h->nbr, (const double*)x,
-                                                                             (double*)y, h->ne, dctl_none(),
-                                                                             vsel_fixed(), vsel_fixed());
+            k_apply<NB, double, double, double><<<es.grid, es.block, 0, h->stream>>>(
+                h->A64, h->nbr, (const double*)x, (double*)y, h->ne, dctl_none(), vsel_fixed(), vsel_fixed());
             break;
         case DG_F32:
             if (!h->A32) return dg_fail(h, DG_ERR_STATE, "f32 blocks not stored");
-            k_apply<NB, float, float, float><<<grid, 256, 0, h->stream>>>(h->A32, h->nbr, (const float*)x, (float*)y,
-                                                                          h->ne, dctl_none(), vsel_fixed(),
-                                                                          vsel_fixed());
+            k_apply<NB, float, float, float><<<es.grid, es.block, 0, h->stream>>>(
+                h->A32, h->nbr, (const float*)x, (float*)y, h->ne, dctl_none(), vsel_fixed(), vsel_fixed());
             break;
         case DG_BF16:
             if (!h->A16) return dg_fail(h, DG_ERR_STATE, "bf16 blocks not stored");
-            k_apply<NB, __nv_bfloat16, float, float><<<grid, 256, 0, h->stream>>>(h->A16, h->nbr, (const float*)x,
-                                                                                  (float*)y, h->ne, dctl_none(),
-                                                                                  vsel_fixed(), vsel_fixed());
+            k_apply<NB, __nv_bfloat16, float, float><<<es.grid, es.block, 0, h->stream>>>(
+                h->A16, h->nbr, (const float*)x, (float*)y, h->ne, dctl_none(), vsel_fixed(), vsel_fixed());
             break;
         default:
             return dg_fail(h, DG_ERR_INVALID_ARG, "dtype");

@@ -383,8 +383,11 @@ __global__ void __launch_bounds__(256) k_gm_update(TV* V, long ld, long nvec, Gm
     for (int d = threadIdx.x; d <= j; d += blockDim.x) c[d] = (TV)st->coef[d];
     __syncthreads();
     VT* w = reinterpret_cast<VT*>(V + (long)(j + 1) * ld);   // aliases V: no __restrict__
-    const long nthr = (long)(gridDim.x - 1) * blockDim.x;   // block 0 is the control block
-    for (long q = (long)(blockIdx.x - 1) * blockDim.x + threadIdx.x; q < nvec; q += nthr) {
+    // block 0 is the control block; data block b takes the contiguous range
+    // [nvec b / nd, nvec (b+1) / nd), so every SM gets the same number of rows
+    const long nd = gridDim.x - 1, b = blockIdx.x - 1;
+    const long q1 = nvec * (b + 1) / nd;
+    for (long q = nvec * b / nd + threadIdx.x; q < q1; q += blockDim.x) {
         VT acc = w[q];
         int d = 0;
         for (; d + 4 <= j + 1; d += 4) {
@@ -514,9 +517,9 @@ __global__ void __launch_bounds__(256) k_gm_resid(const TV* __restrict__ F, cons
 template <int NB, typename TA, typename TV>
 static void launch_apply(dg_handle* h, const TA* A, const TV* x, TV* y, DevCtl ctl, VecSel sx, VecSel sy,
                          bool pdl = false) {
-    const unsigned grid = (unsigned)((h->ne + 255) / 256);
-    dg_launch(h, pdl, k_apply<NB, TA, TV, TV>, dim3(grid), dim3(256), A, (const int*)h->nbr, x, y, h->ne, ctl, sx,
-              sy);
+    const ElemShape es = elem_shape(h);
+    dg_launch(h, pdl, k_apply<NB, TA, TV, TV>, dim3(es.grid), dim3(es.block), A, (const int*)h->nbr, x, y, h->ne,
+              ctl, sx, sy);
 }
 template <int NB, typename TB, typename TV>
 static void launch_bj(dg_handle* h, const TB* B, const TV* r, TV* z, DevCtl ctl, VecSel sr, VecSel sz,

@@ -120,6 +120,10 @@ extern "C" dg_status dg_create(dg_handle** out, int device, void* stream) {
     h->stream = (cudaStream_t)stream;
     const char* pdl = getenv("DG_PDL");
     h->pdl = !(pdl && pdl[0] == '0');
+    if (cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        delete h;
+        return DG_ERR_CUDA;
+    }
     dg_params_default(&h->p);
     if (dg_realloc(h, (void**)&h->dflag, 64) != DG_OK) {
         delete h;

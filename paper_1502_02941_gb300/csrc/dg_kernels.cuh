@@ -30,6 +30,20 @@ struct DevCtl {
 };
 static inline DevCtl dctl_none() { return DevCtl{nullptr, nullptr}; }
 
+// Launch shape of the one-thread-per-element kernels: one warp per block when
+// all of the kernel's warps can be resident at once (at most 32 blocks per
+// SM), so that the blocks spread over the SMs to within one warp; 256-thread
+// blocks otherwise.  A one-wave grid of 256-thread blocks leaves some SMs a
+// whole extra block, which an FP64-bound kernel pays in full.
+struct ElemShape {
+    unsigned grid, block;
+};
+static inline ElemShape elem_shape(const dg_handle* h) {
+    const long warps = ((long)h->ne + 31) / 32;
+    if (h->nsm > 0 && warps <= 32L * h->nsm) return ElemShape{(unsigned)warps, 32u};
+    return ElemShape{(unsigned)(((long)h->ne + 255) / 256), 256u};
+}
+
 // ---------------------------------------------------------------------------
 // typed 16-byte chunk loads
 // ---------------------------------------------------------------------------
