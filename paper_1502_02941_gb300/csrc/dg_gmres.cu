@@ -383,11 +383,8 @@ __global__ void __launch_bounds__(256) k_gm_update(TV* V, long ld, long nvec, Gm
     for (int d = threadIdx.x; d <= j; d += blockDim.x) c[d] = (TV)st->coef[d];
     __syncthreads();
     VT* w = reinterpret_cast<VT*>(V + (long)(j + 1) * ld);   // aliases V: no __restrict__
-    // block 0 is the control block; data block b takes the contiguous range
-    // [nvec b / nd, nvec (b+1) / nd), so every SM gets the same number of rows
-    const long nd = gridDim.x - 1, b = blockIdx.x - 1;
-    const long q1 = nvec * (b + 1) / nd;
-    for (long q = nvec * b / nd + threadIdx.x; q < q1; q += blockDim.x) {
+    const long nthr = (long)(gridDim.x - 1) * blockDim.x;   // block 0 is the control block
+    for (long q = (long)(blockIdx.x - 1) * blockDim.x + threadIdx.x; q < nvec; q += nthr) {
         VT acc = w[q];
         int d = 0;
         for (; d + 4 <= j + 1; d += 4) {
