@@ -314,6 +314,26 @@ def reference_arm(args, rank):
 
 
 # ---------------------------------------------------------------------------
+# multi-rank timing (replicas: one independent solve stream per GPU, no
+# collective on the data path; the only collectives are these)
+# ---------------------------------------------------------------------------
+def max_over_ranks(ms, world, device=None):
+    """The slowest rank's time in ms; every rank takes part and gets it."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_rank, world, ms_max):
+    """Units all ranks processed per second of the slowest rank's time."""
+    return units_per_rank * world / (ms_max / 1e3)
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def main():
@@ -399,19 +419,14 @@ def main():
         torch.cuda.nvtx.range_pop()
         barrier()
         clocks = sampler.stop() if sampler else None
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
         return ms, h.launch_count() - n0, clocks
 
     sampler = ClockSampler(local)
     ms, launches, clocks = timed(False, sampler)
     ms_e2e, _, _ = timed(True)
-    solves = len(METHODS) * args.steps * world
-    value = solves / (ms / 1e3)
-    e2e_value = solves / (ms_e2e / 1e3)
+    value = whole_job_value(len(METHODS) * args.steps, world, ms)
+    e2e_value = whole_job_value(len(METHODS) * args.steps, world, ms_e2e)
     its = [last[m][0] for m in METHODS]
 
     # ---- mixed precision on the same workload: plain f64 refinement around f32

@@ -1,0 +1,61 @@
+"""Multi-rank host logic of the benchmark on CPU: world_size-2 gloo ranks.
+
+The solve path does not shard (replicas only): each rank solves its own
+copy of the workload, and the only collectives are the barrier and the
+max-over-ranks timing.  These tests run that timing logic and the
+reference arm's rank handling on gloo, without a GPU."""
+import io
+import contextlib
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+import bench  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ms_local = 100.0 + 50.0 * rank          # rank 1 is the slower one
+        ms = bench.max_over_ranks(ms_local, world)
+        value = bench.whole_job_value(2 * 3, world, ms)   # 2 solves x 3 steps per rank
+        # the reference arm: rank 0 alone runs and prints; other ranks return at once
+        buf = io.StringIO()
+        if rank != 0:
+            with contextlib.redirect_stdout(buf):
+                bench.reference_arm(None, rank)
+        dist.barrier()
+        out[rank] = (ms, value, buf.getvalue())
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_whole_job_value_on_two_gloo_ranks():
+    world = 2
+    with mp.Manager() as mgr:
+        out = mgr.dict()
+        mp.start_processes(_rank_main, args=(world, _free_port(), out), nprocs=world, join=True,
+                           start_method="spawn")
+        res = dict(out)
+    for rank in range(world):
+        ms, value, printed = res[rank]
+        assert ms == 150.0                       # every rank sees the slowest rank's time
+        assert value == pytest.approx(2 * 3 * world / 0.150)
+        assert printed == ""                     # no reference line from rank 1 (nor work)
+
+
+def test_single_rank_needs_no_process_group():
+    assert bench.max_over_ranks(123.0, 1) == 123.0
+    assert bench.whole_job_value(2, 1, 500.0) == pytest.approx(4.0)
