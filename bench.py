@@ -30,7 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "solves/s to rel-res 1e-10, learned+mixed vs plain FP64 GMRES; apply HBM GB/s"
-WORKLOAD = "cfg2: 256x256 split squares (131072 triangles), P2 (786432 dofs), NIPG+SIPG, eps=1e-6, " \
+WORKLOAD = "boundary layer: 256x256 split squares (131072 triangles), P2 (786432 dofs), NIPG+SIPG, eps=1e-6, " \
            "b=(1,0), alpha=1, boundary-layer u, all Dirichlet, GMRES(50)+block-Jacobi f64 to rel-res 1e-10"
 N_MESH, DEGREE = 256, 2
 METHODS = (1, 2)   # NIPG, SIPG
@@ -163,7 +163,7 @@ def batched_section(local, stream, n_inst):
     the Schwarz preconditioner."""
     import numpy as np
     from paper_1502_02941_gb300 import dg as D, problem, workloads as W
-    groups = W.batch_by_degree(4, n_inst)
+    groups = W.batch_by_degree("batched", n_inst)
     out = {"workload": f"{n_inst} instances of the batched workload: N in [16,128], k in {{1,2}} (one batch per "
                        "degree), eps log-uniform [1e-6,1e-1], |b| U[0,1], alpha U[0,1], 4-Gaussian f; SIPG, "
                        "homogeneous Dirichlet",
@@ -252,7 +252,7 @@ def oracle_sample(gpu_its, iters=50):
     total = 0.0
     detail = []
     for method, its in zip(METHODS, gpu_its):
-        cfg = W.config2(method=method, N=N_MESH)
+        cfg = W.boundary_layer_p2(method=method, N=N_MESH)
         ma = W.structured_mesh(cfg.N)
         p = cfg.problem
         t0 = time.perf_counter()
@@ -275,10 +275,10 @@ def oracle_sample(gpu_its, iters=50):
 
 
 def oracle_iteration_counts():
-    p = os.path.join(ROOT, "oracle", "cfg2_oracle_solves.json")
+    p = os.path.join(ROOT, "oracle", "layer256_p2_oracle_solves.json")
     if os.path.exists(p):
         d = json.load(open(p))
-        return [s["iterations"] for s in d["solves"]], "oracle full solves (oracle/cfg2_oracle_solves.json)"
+        return [s["iterations"] for s in d["solves"]], "oracle full solves (oracle/layer256_p2_oracle_solves.json)"
     return None, None
 
 
@@ -361,15 +361,15 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     h = D.DG(local)
-    cfg0 = W.config2(method=METHODS[0], N=N_MESH)
+    layer = W.boundary_layer_p2(method=METHODS[0], N=N_MESH)
     ma = W.structured_mesh(N_MESH)
     # problem data at the quadrature points (identical for both methods)
-    problem.setup(h, cfg0, mesh=ma, assemble=False)
-    f, gD, gN = problem.problem_data(h, cfg0.problem)
+    problem.setup(h, layer, mesh=ma, assemble=False)
+    f, gD, gN = problem.problem_data(h, layer.problem)
     info = h.info()
     dofs = info.dofs
     x = torch.empty(dofs, dtype=torch.float64, device=dev)
-    p = cfg0.problem
+    p = layer.problem
     f_h = f.cpu().pin_memory(); gD_h = gD.cpu().pin_memory(); gN_h = gN.cpu().pin_memory()
     x_h = torch.empty(dofs, dtype=torch.float64).pin_memory()
     h2d = (f_h.numel() + gD_h.numel() + gN_h.numel()) * 8 * len(METHODS) \
@@ -536,8 +536,8 @@ def main():
     # the same kernels on the 512x512 P3 operator (5.24 M unknowns), large enough
     # that launch and tail latency no longer hide the bandwidth
     h3 = D.DG(local)
-    cfg3 = W.config3(N=512)
-    problem.setup(h3, cfg3, store=D.DG_STORE_F64 | D.DG_STORE_F32 | D.DG_STORE_BF16)
+    bump = W.gaussian_bump_p3(N=512)
+    problem.setup(h3, bump, store=D.DG_STORE_F64 | D.DG_STORE_F32 | D.DG_STORE_BF16)
     i3 = h3.info()
     apply_p3 = {}
     for name, dt, sa, sx in (("f64", D.DG_F64, 8, 8), ("f32", D.DG_F32, 4, 4), ("bf16", D.DG_BF16, 2, 4)):
@@ -570,7 +570,7 @@ def main():
                                           "share of the f64 GMRES step)",
                 "achieved": dots_flops / (dots_ms / 1e3) / 1e12, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
                 "frac": dots_flops / (dots_ms / 1e3) / 1e12 / fp64_peak_tflops,
-                "traffic": profile_traffic("k_gm_dots_f64_cfg2"),
+                "traffic": profile_traffic("k_gm_dots_f64_layer256_p2"),
                 "algorithmic_flops": dots_flops, "algorithmic_bytes": 8.0 * (jmid + 2) * dofs,
                 "avg_launch_ms": dots_ms,
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (f64 FMA probe measured "

@@ -1,6 +1,6 @@
 """Run the oracle's full FP64 GMRES(50) + block-Jacobi solves of the 256x256
 P2 boundary-layer workload (NIPG and SIPG, rel-res 1e-10) and record the
-iteration counts and timings in oracle/cfg2_oracle_solves.json.
+iteration counts and timings in oracle/layer256_p2_oracle_solves.json.
 
 The benchmark's CPU-baseline legs time a bounded slice of the same oracle solve
 (assembly, block inverses and a fixed number of iterations) and scale the
@@ -22,7 +22,7 @@ from paper_1502_02941_gb300 import workloads as W  # noqa: E402
 
 
 def run(method, N=256):
-    cfg = W.config2(method=method, N=N)
+    cfg = W.boundary_layer_p2(method=method, N=N)
     ma = W.structured_mesh(cfg.N)
     m = O.make_mesh(ma.nodes, ma.elems, ma.dirichlet, ma.neumann)
     s, kap = O.set_parameter(cfg.method, cfg.k)
@@ -43,7 +43,7 @@ if __name__ == "__main__":
     out = {"workload": "256x256 split squares, P2, eps=1e-6, b=(1,0), alpha=1, boundary-layer u, "
                        "GMRES(50)+block-Jacobi, rel-res 1e-10",
            "host": os.uname().machine, "solves": [run(1), run(2)]}
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "cfg2_oracle_solves.json")
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "layer256_p2_oracle_solves.json")
     with open(path, "w") as fh:
         json.dump(out, fh, indent=1)
     print(json.dumps(out, indent=1))

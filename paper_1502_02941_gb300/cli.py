@@ -1,9 +1,13 @@
 """Command-line solve of one workload through libdg.
 
-    python -m paper_1502_02941_gb300.cli --config 2 --N 256 --method 2 --solver gmres
-    python -m paper_1502_02941_gb300.cli --config 3 --N 64 --solver mixed-bf16
-    python -m paper_1502_02941_gb300.cli --config 3 --solver gmres-ir-f32 --max-it 400000
-    python -m paper_1502_02941_gb300.cli --config 3 --solver gmres-ir-f32 --precond schwarz
+    python -m paper_1502_02941_gb300.cli --workload layer --N 256 --method 2 --solver gmres
+    python -m paper_1502_02941_gb300.cli --workload bump --N 64 --solver mixed-bf16
+    python -m paper_1502_02941_gb300.cli --workload bump --solver gmres-ir-f32 --max-it 400000
+    python -m paper_1502_02941_gb300.cli --workload bump --solver gmres-ir-f32 --precond schwarz
+
+Workloads: sine (8x8 split squares, P1 SIPG, u = sin(pi x) sin(pi y)), layer
+(256x256, P2, eps = 1e-6 boundary layer), bump (512x512, P3, rotating flow,
+Gaussian bump, Neumann right/top); --N changes the mesh size.
 
 Prints one JSON line with sizes, iterations, relative residual, L2 error (when
 the workload has an exact solution) and wall time of the solve.
@@ -17,7 +21,7 @@ import time
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3])
+    ap.add_argument("--workload", default="layer", choices=["sine", "layer", "bump"])
     ap.add_argument("--N", type=int, default=None)
     ap.add_argument("--method", type=int, default=None, help="1 NIPG, 2 SIPG, 3 IIPG")
     ap.add_argument("--solver", default="gmres",
@@ -35,13 +39,13 @@ def main(argv=None):
     from . import problem
     from . import workloads as W
 
-    if a.config == 1:
-        cfg = W.config1()
-    elif a.config == 2:
-        cfg = W.config2(method=a.method or 2, N=a.N or 256)
+    if a.workload == "sine":
+        cfg = W.sine_8x8()
+    elif a.workload == "layer":
+        cfg = W.boundary_layer_p2(method=a.method or 2, N=a.N or 256)
     else:
-        cfg = W.config3(N=a.N or 512)
-    if a.N and a.config == 1:
+        cfg = W.gaussian_bump_p3(N=a.N or 512)
+    if a.N and a.workload == "sine":
         cfg.N = a.N
     if a.method:
         cfg.method = a.method
@@ -80,7 +84,7 @@ def main(argv=None):
     if cfg.problem.exact is not None:
         l2, hmax = h.l2_error(x, problem.exact_at_error_points(h, cfg.problem))
         out.update(l2_error=l2, h_max=hmax)
-    out.update(config=a.config, N=cfg.N, k=cfg.k, method=cfg.method, ne=info.ne, dofs=info.dofs,
+    out.update(workload=a.workload, N=cfg.N, k=cfg.k, method=cfg.method, ne=info.ne, dofs=info.dofs,
                solver=a.solver, precond=a.precond)
     print(json.dumps(out))
     h.close()

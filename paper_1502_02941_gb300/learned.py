@@ -17,14 +17,14 @@ from . import dg as D
 from . import problem
 from . import workloads as W
 
-TRAIN_CONFIG_ID = 5
+TRAIN_FAMILY = "learned"
 
 
 def make_batch(h: D.DG, n_inst: int, N: int, first: int = 0, k: int = 2, store=D.DG_STORE_F64, **params):
     """Instances first .. first+n_inst-1 of the learned workload's draw."""
     cfgs, i = [], first
     while len(cfgs) < n_inst:
-        c = W.random_instance(TRAIN_CONFIG_ID, i, N_fixed=N, k_fixed=k)
+        c = W.random_instance(TRAIN_FAMILY, i, N_fixed=N, k_fixed=k)
         i += 1
         cfgs.append(c)
     ma, starts = W.concat_meshes([W.structured_mesh(c.N) for c in cfgs])

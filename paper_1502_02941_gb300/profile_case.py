@@ -35,7 +35,7 @@ def main(argv=None):
     from . import problem
     from . import workloads as W
 
-    cfg = W.config2(method=2, N=a.N)
+    cfg = W.boundary_layer_p2(method=2, N=a.N)
     h = D.DG(0)
     if a.kernel == "step":
         ma = W.structured_mesh(a.N)

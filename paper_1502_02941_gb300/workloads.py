@@ -207,7 +207,8 @@ def gaussians_source(centres, widths, amp=1.0):
 
 
 # ---------------------------------------------------------------------------
-# the five workload configurations
+# the workloads: sine 8x8 P1, boundary layer P2, Gaussian bump P3, and the
+# random families of the batched and learned solves
 # ---------------------------------------------------------------------------
 
 @dataclass
@@ -220,42 +221,46 @@ class Config:
     sigma: float | None = None   # interior penalty override; boundary = 2 sigma
 
 
-def config1() -> Config:
+def sine_8x8() -> Config:
     """8x8 split squares (128 triangles), P1, SIPG sigma = 6k^2, eps=1, b=0,
     alpha=0, all Dirichlet, u = sin(pi x) sin(pi y); direct solve."""
-    return Config("cfg1_sipg_p1_n8", 8, 1, 2, Problem("sinsin", 1.0, 0.0, (0, 0, 0, 0, 0, 0), sinsin),
+    return Config("sine_sipg_p1_n8", 8, 1, 2, Problem("sinsin", 1.0, 0.0, (0, 0, 0, 0, 0, 0), sinsin),
                   sigma=6.0)
 
 
-def config2(method: int = 2, N: int = 256) -> Config:
+def boundary_layer_p2(method: int = 2, N: int = 256) -> Config:
     """256x256 split squares (131072 triangles), P2, NIPG or SIPG, eps=1e-6,
     b=(1,0), alpha=1, boundary-layer solution, all Dirichlet; GMRES(50)+BJ."""
     eps = 1e-6
-    return Config(f"cfg2_{'nipg' if method == 1 else 'sipg'}_p2_n{N}", N, 2, method,
+    return Config(f"layer_{'nipg' if method == 1 else 'sipg'}_p2_n{N}", N, 2, method,
                   Problem("boundary_layer", eps, 1.0, (1.0, 0, 0, 0, 0, 0), boundary_layer(eps)))
 
 
-def config3(N: int = 512) -> Config:
+def gaussian_bump_p3(N: int = 512) -> Config:
     """512x512 split squares (524288 triangles), P3, SIPG, eps=1e-3,
     b=(0.5-y, x-0.5), alpha=0.1, Gaussian-bump solution; Dirichlet on
     left/bottom, Neumann on right/top; mixed precision."""
-    return Config(f"cfg3_sipg_p3_n{N}", N, 3, 2,
+    return Config(f"bump_sipg_p3_n{N}", N, 3, 2,
                   Problem("gaussian", 1e-3, 0.1, (0.5, 0.0, -1.0, -0.5, 1.0, 0.0), gaussian_bump,
                           neumann_sides=("right", "top")))
 
 
-def instance_seed(config_id: int, instance: int) -> int:
-    return 20260000 + 1000 * config_id + instance
+# seed of instance i of a random family: SEED_BASE[family] + i
+SEED_BASE = {"batched": 20264000, "learned": 20265000}
 
 
-def random_instance(config_id: int, instance: int, N_range=(16, 128), k_choices=(1, 2),
+def instance_seed(family: str, instance: int) -> int:
+    return SEED_BASE[family] + instance
+
+
+def random_instance(family: str, instance: int, N_range=(16, 128), k_choices=(1, 2),
                     N_fixed: int | None = None, k_fixed: int | None = None) -> Config:
     """Per-instance draw for the batched and learned workloads: N uniform in
     N_range, k from k_choices, eps log-uniform on [1e-6,1e-1], b = U[0,1] times
     a unit vector at a U[0,2pi) angle, alpha ~ U[0,1], f a sum of 4 Gaussians
     (centres U[0,1]^2, widths U[0.05,0.2], amplitude 1); SIPG, homogeneous
     Dirichlet data on all sides."""
-    rng = np.random.default_rng(instance_seed(config_id, instance))
+    rng = np.random.default_rng(instance_seed(family, instance))
     N = int(rng.integers(N_range[0], N_range[1] + 1)) if N_fixed is None else N_fixed
     k = int(rng.choice(k_choices)) if k_fixed is None else k_fixed
     eps = float(10 ** rng.uniform(-6, -1))
@@ -266,16 +271,16 @@ def random_instance(config_id: int, instance: int, N_range=(16, 128), k_choices=
     widths = rng.uniform(0.05, 0.2, size=4)
     prob = Problem("gaussians", eps, alpha, (s * np.cos(theta), 0, 0, s * np.sin(theta), 0, 0),
                    None, gaussians_source([tuple(c) for c in centres], list(widths)))
-    return Config(f"cfg{config_id}_inst{instance}", N, k, 2, prob)
+    return Config(f"{family}_inst{instance}", N, k, 2, prob)
 
 
-def batch_by_degree(config_id: int, n_inst: int, N_range=(16, 128)):
+def batch_by_degree(family: str, n_inst: int, N_range=(16, 128)):
     """Instances 0..n_inst-1 of the batched workload grouped by their degree:
     {k: (cfgs, mesh, elem_start, coeffs)}, one batch per degree (a batch shares
     k), each instance keeping its own draw."""
     groups: dict[int, list] = {}
     for i in range(n_inst):
-        c = random_instance(config_id, i, N_range=N_range)
+        c = random_instance(family, i, N_range=N_range)
         groups.setdefault(c.k, []).append(c)
     out = {}
     for k in sorted(groups):
@@ -305,13 +310,13 @@ def concat_meshes(meshes):
             np.array(starts, np.int32))
 
 
-def batch(config_id: int, n_inst: int, k: int | None = None, N_fixed: int | None = None, N_range=(16, 128)):
-    """Instances of the batched (config_id 4) or learned (config_id 5) workload
+def batch(family: str, n_inst: int, k: int | None = None, N_fixed: int | None = None, N_range=(16, 128)):
+    """Instances of the batched ("batched") or learned ("learned") workload
     with degree k (instances of the other degree are skipped, so that one batch
     shares k), their concatenated mesh, elem_start and coefficient table."""
     cfgs, i = [], 0
     while len(cfgs) < n_inst:
-        c = random_instance(config_id, i, N_range=N_range, N_fixed=N_fixed)
+        c = random_instance(family, i, N_range=N_range, N_fixed=N_fixed)
         i += 1
         if k is not None and c.k != k:
             continue

@@ -21,7 +21,7 @@ def _np(t):
 @pytest.mark.parametrize("k", [1, 2])
 @pytest.mark.parametrize("inner", ["f64", "f32"])
 def test_batch_matches_single_instance_solves(k, inner):
-    cfgs, ma, starts, coeffs = W.batch(4, 5, k=k, N_range=(3, 7))
+    cfgs, ma, starts, coeffs = W.batch("batched", 5, k=k, N_range=(3, 7))
     h = D.DG(0)
     store = D.DG_STORE_F64 | (D.DG_STORE_F32 if inner == "f32" else 0)
     problem.setup_batch(h, cfgs, ma, starts, coeffs, store=store, tol=1e-11, gmres_m=20)
@@ -49,7 +49,7 @@ def test_batch_matches_single_instance_solves(k, inner):
 
 
 def test_batch_autotune_and_rejects_touching_instances():
-    cfgs, ma, starts, coeffs = W.batch(4, 4, k=1, N_range=(3, 5))
+    cfgs, ma, starts, coeffs = W.batch("batched", 4, k=1, N_range=(3, 5))
     h = D.DG(0)
     problem.setup_batch(h, cfgs, ma, starts, coeffs)
     tile = h.batch_autotune()
@@ -70,7 +70,7 @@ def test_batch_with_schwarz_matches_oracle(inner):
     """Batched solve with the Schwarz preconditioner: every instance reaches
     1e-10 measured by the oracle's operator, in no more Arnoldi steps than with
     block Jacobi."""
-    cfgs, ma, starts, coeffs = W.batch(4, 5, k=2, N_range=(4, 8))
+    cfgs, ma, starts, coeffs = W.batch("batched", 5, k=2, N_range=(4, 8))
     h = D.DG(0)
     store = D.DG_STORE_F64 | (D.DG_STORE_F32 if inner == "f32" else 0)
     problem.setup_batch(h, cfgs, ma, starts, coeffs, store=store, tol=1e-11, gmres_m=20)
@@ -98,7 +98,7 @@ def test_batch_gmres_refinement_matches_oracle(inner, pc):
     batched low-precision inner solve): every instance reaches 1e-11 in its own
     f64 residual and 1e-10 measured by the oracle's operator, and agrees with
     the single-instance GMRES-based refinement of the same instance."""
-    cfgs, ma, starts, coeffs = W.batch(4, 5, k=2, N_range=(4, 8))
+    cfgs, ma, starts, coeffs = W.batch("batched", 5, k=2, N_range=(4, 8))
     h = D.DG(0)
     store = D.DG_STORE_F64 | (D.DG_STORE_F32 if inner == "f32" else D.DG_STORE_BF16)
     prec = D.DG_PRECOND_SCHWARZ if pc == "schwarz" else D.DG_PRECOND_BLOCK_JACOBI
@@ -134,7 +134,7 @@ def test_batch_gmres_refinement_matches_oracle(inner, pc):
 
 
 def test_batch_rejects_mixed_degrees():
-    cfgs, ma, starts, coeffs = W.batch(4, 6)
+    cfgs, ma, starts, coeffs = W.batch("batched", 6)
     assert len({c.k for c in cfgs}) == 2
     h = D.DG(0)
     with pytest.raises(ValueError):

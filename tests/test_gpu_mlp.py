@@ -18,7 +18,7 @@ def _np(t):
 
 
 def _handle(k=2, N=6):
-    cfg = W.config2(method=2, N=N)
+    cfg = W.boundary_layer_p2(method=2, N=N)
     cfg.k = k
     h = D.DG(0)
     problem.setup(h, cfg, tol=1e-11, gmres_m=30)

@@ -253,8 +253,8 @@ def test_singular_block_reported():
 # ----------------------------------------------------------------------------
 
 
-def test_config1_dense_solve_and_l2():
-    cfg = W.config1()
+def test_sine_8x8_dense_solve_and_l2():
+    cfg = W.sine_8x8()
     ma = W.structured_mesh(cfg.N)
     h = gpu_setup(ma, cfg.k, cfg.method, cfg.problem, sigma=cfg.sigma)
     xg = h.dense_solve()
@@ -272,7 +272,7 @@ def test_config1_dense_solve_and_l2():
 
 @pytest.mark.parametrize("method", [1, 2])
 def test_gmres_matches_oracle(method):
-    cfg = W.config2(method=method, N=12)
+    cfg = W.boundary_layer_p2(method=method, N=12)
     ma = W.structured_mesh(cfg.N)
     h = gpu_setup(ma, cfg.k, cfg.method, cfg.problem, tol=1e-12, gmres_m=20)
     xg, info = h.gmres_solve()
@@ -317,7 +317,7 @@ def test_eval_matches_oracle():
 
 
 def test_nonfinite_data_reported():
-    cfg = W.config2(N=4)
+    cfg = W.boundary_layer_p2(N=4)
     ma = W.structured_mesh(cfg.N)
     h = D.DG(0)
     problem.setup(h, cfg, mesh=ma, assemble=False)
@@ -340,7 +340,7 @@ def test_nonfinite_data_reported():
 def test_mixed_refinement_reaches_f64_tolerance(inner):
     """bf16/f32 inner solves with f64 refinement reach rel-res 1e-10, measured
     by the oracle's own f64 operator (reading A-12)."""
-    cfg = W.config3(N=12)
+    cfg = W.gaussian_bump_p3(N=12)
     ma = W.structured_mesh(cfg.N, cfg.problem.neumann_sides)
     store = D.DG_STORE_F64 | (D.DG_STORE_F32 if inner == "f32" else D.DG_STORE_BF16)
     h = gpu_setup(ma, cfg.k, cfg.method, cfg.problem, store=store, tol=1e-10)
@@ -361,7 +361,7 @@ def test_mixed_refinement_reaches_f64_tolerance(inner):
 def test_gmres_refinement_reaches_f64_tolerance(inner):
     """Outer f64 FGMRES with the low-precision solve as preconditioner reaches
     rel-res 1e-10, measured by the oracle's own f64 operator (reading A-12)."""
-    cfg = W.config3(N=12)
+    cfg = W.gaussian_bump_p3(N=12)
     ma = W.structured_mesh(cfg.N, cfg.problem.neumann_sides)
     store = D.DG_STORE_F64 | (D.DG_STORE_F32 if inner == "f32" else D.DG_STORE_BF16)
     h = gpu_setup(ma, cfg.k, cfg.method, cfg.problem, store=store, tol=1e-10)
@@ -379,7 +379,7 @@ def test_gmres_refinement_converges_where_bf16_refinement_stalls():
     refinement around bf16 inner solves stalls (cond(A) u_bf16 > 1); the f64
     FGMRES outer loop around the same inner solves reaches 1e-10.  The final
     residual is re-measured here with the f64 apply."""
-    cfg = W.config2(method=2, N=256)
+    cfg = W.boundary_layer_p2(method=2, N=256)
     ma = W.structured_mesh(cfg.N)
     h = gpu_setup(ma, cfg.k, cfg.method, cfg.problem, store=D.DG_STORE_F64 | D.DG_STORE_BF16, tol=1e-10,
                   max_it=4000)
@@ -451,7 +451,7 @@ def test_schwarz_gmres_reaches_tolerance_in_fewer_steps():
     (32x32, P2, NIPG): relres <= 1e-10 measured by the oracle's operator, in
     fewer Arnoldi steps than with block Jacobi; mixed refinement around f32
     Schwarz-preconditioned inner solves also reaches 1e-10."""
-    cfg = W.config2(method=1, N=32)
+    cfg = W.boundary_layer_p2(method=1, N=32)
     ma = W.structured_mesh(cfg.N)
     h = gpu_setup(ma, cfg.k, cfg.method, cfg.problem, store=D.DG_STORE_F64 | D.DG_STORE_F32, tol=1e-10,
                   gmres_m=50)

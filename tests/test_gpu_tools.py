@@ -17,14 +17,14 @@ def _run(*args):
 
 
 def test_cli_dense_solve_of_the_8x8_workload():
-    out = _run("paper_1502_02941_gb300.cli", "--config", "1", "--solver", "dense")
+    out = _run("paper_1502_02941_gb300.cli", "--workload", "sine", "--solver", "dense")
     assert out["ne"] == 128 and out["dofs"] == 384
     assert 0 < out["l2_error"] < 5e-2
 
 
 @pytest.mark.parametrize("solver", ["gmres", "mixed-f32", "gmres-ir-bf16"])
 def test_cli_iterative_solvers(solver):
-    out = _run("paper_1502_02941_gb300.cli", "--config", "2", "--N", "16", "--solver", solver)
+    out = _run("paper_1502_02941_gb300.cli", "--workload", "layer", "--N", "16", "--solver", solver)
     assert out["status"] == "DG_OK" and out["relres"] <= 1e-10
 
 

@@ -63,7 +63,7 @@ def _triangle_set(nodes, elems):
     return out
 
 
-def test_two_refinements_give_config1_mesh():
+def test_two_refinements_give_the_8x8_mesh():
     """Two uniform refinements of the printed 8-triangle mesh give the 8x8 "/"
     split mesh of 128 triangles (Sec. 2.1 refinement loop)."""
     nodes, elems, dr, ne = W.FIXTURE_NODES, W.FIXTURE_ELEMS, W.FIXTURE_DIRICHLET, np.zeros((0, 2), np.int32)
@@ -245,8 +245,8 @@ def test_pure_transport_reproduction():
 # ----------------------------------------------------------------------------
 
 
-def test_sipg_symmetric_positive_definite_config1():
-    c = W.config1()
+def test_sipg_symmetric_positive_definite_sine_8x8():
+    c = W.sine_8x8()
     ma = W.structured_mesh(c.N)
     run = oracle_system(ma, c.k, c.method, c.problem, sigma=c.sigma)
     A = O.dense_matrix(run.mesh, run.system.A_diag, run.system.A_off)
@@ -391,7 +391,7 @@ def test_dense_solve_matches_numpy():
 
 @pytest.mark.parametrize("method", [1, 2])
 def test_gmres_matches_direct(method):
-    c = W.config2(method=method, N=8)
+    c = W.boundary_layer_p2(method=method, N=8)
     run = oracle_system(W.structured_mesh(c.N), c.k, c.method, c.problem)
     x, its, relres, ok = O.gmres(run.mesh, run.system.A_diag, run.system.A_off, run.system.F, m=20, tol=1e-12)
     assert ok and relres <= 1e-12 and its > 0

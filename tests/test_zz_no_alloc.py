@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 
 
 def test_l2_error_noalloc_matches_regular_entry_point():
-    cfg = W.config2(method=2, N=24)          # 1152 triangles, P2
+    cfg = W.boundary_layer_p2(method=2, N=24)          # 1152 triangles, P2
     h = D.DG(0)
     problem.setup(h, cfg, tol=1e-12)
     x, _ = h.gmres_solve()
