@@ -835,10 +835,12 @@ static dg_status b_gmres(dg_handle* h, BatchRun& Rn, const TA* A, const TB* Binv
     k_b_cycle_end<<<1, 1024, 0, h->stream>>>(B);
     h->nlaunch += 2;
     DG_LAUNCH_CK(h);
-    const uintptr_t key[10] = {(uintptr_t)A, (uintptr_t)Binv, (uintptr_t)F, (uintptr_t)x, (uintptr_t)Rn.V,
+    // the captured cycle holds pointers, sizes, the degree and the item count
+    const uintptr_t key[12] = {(uintptr_t)A, (uintptr_t)Binv, (uintptr_t)F, (uintptr_t)x, (uintptr_t)Rn.V,
                                (uintptr_t)B.bst,
                                (uintptr_t)Rn.m | ((uintptr_t)sizeof(TV) << 16) | ((uintptr_t)(B.iuse != nullptr) << 24),
-                               (uintptr_t)h->stream, (uintptr_t)Ah, (uintptr_t)G};
+                               (uintptr_t)h->stream, (uintptr_t)Ah, (uintptr_t)G,
+                               (uintptr_t)(unsigned)h->ne | ((uintptr_t)NB << 32), (uintptr_t)(unsigned)B.nit};
     if (h->b_graph && memcmp(key, h->b_key, sizeof(key)) != 0) {
         cudaGraphExecDestroy(h->b_graph);
         h->b_graph = nullptr;

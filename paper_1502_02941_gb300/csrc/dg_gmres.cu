@@ -670,9 +670,11 @@ static dg_status gmres_run(dg_handle* h, GmresWork& W, const TA* A, const TB* B,
     DG_CK(h, cudaStreamSynchronize(h->stream));
     if (flex || !B || G) Ah = nullptr;
     if (flex) G = nullptr;
-    const uintptr_t key[8] = {(uintptr_t)x, (uintptr_t)F, (uintptr_t)A, (uintptr_t)B,
+    // the captured cycle holds pointers, sizes and the degree: a new mesh of
+    // the same size reuses it, anything else captures again
+    const uintptr_t key[9] = {(uintptr_t)x, (uintptr_t)F, (uintptr_t)A, (uintptr_t)B,
                               (uintptr_t)m | ((uintptr_t)flex << 20), (uintptr_t)h->stream, (uintptr_t)Ah,
-                              (uintptr_t)G};
+                              (uintptr_t)G, (uintptr_t)(unsigned)h->ne | ((uintptr_t)NB << 32)};
     if (W.graph && memcmp(key, W.key, sizeof(key)) != 0) {
         cudaGraphExecDestroy(W.graph);
         W.graph = nullptr;

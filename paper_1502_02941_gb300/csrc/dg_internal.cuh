@@ -103,7 +103,7 @@ struct GmresWork {
     GmresState* st = nullptr;      // device state
     GmresState* st_host = nullptr; // pinned mirror of the state header
     cudaGraphExec_t graph = nullptr;
-    uintptr_t key[8] = {0, 0, 0, 0, 0, 0};
+    uintptr_t key[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     int nodes = 0;
     int gx = 0;    // grid of the 1-D vector kernels (4 blocks of 256 per SM)
     int gsm = 0;   // grid of the multi-dot kernel (one 1024-thread block per SM)
@@ -192,7 +192,7 @@ struct dg_handle {
     size_t cap_bhost = 0;
     int b_tile = 0;                // dofs per work item (autotuned)
     cudaGraphExec_t b_graph = nullptr;
-    uintptr_t b_key[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    uintptr_t b_key[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     int b_nodes = 0;
 
     MlpState mlp;

@@ -270,6 +270,33 @@ def test_sine_8x8_dense_solve_and_l2():
     h.close()
 
 
+def test_captured_cycle_is_not_reused_across_degree_or_size():
+    """The restart cycle captured as a CUDA graph bakes in the element count and
+    the degree.  A P1 mesh and a P2 mesh with the same number of unknowns (384),
+    solved in turn on one handle into the same output buffer, give the results
+    of fresh handles."""
+    m8 = W.structured_mesh(8)                                              # 128 triangles, P1
+    m44, _ = W.concat_meshes([W.structured_mesh(4), W.structured_mesh(4)])   # 64 triangles, P2
+    cases = [(W.sine_8x8(), m8), (W.boundary_layer_p2(method=2, N=4), m44)]
+    h = D.DG(0)
+    x = torch.empty(384, dtype=torch.float64, device="cuda")
+    got = []
+    for c, m in cases + cases:
+        problem.setup(h, c, mesh=m, tol=1e-11, gmres_m=20)
+        assert h.info().dofs == 384
+        h.gmres_solve(x=x)
+        got.append(_np(x).copy())
+    h.close()
+    for i, (c, m) in enumerate(cases):
+        hf = D.DG(0)
+        problem.setup(hf, c, mesh=m, tol=1e-11, gmres_m=20)
+        xf, _ = hf.gmres_solve()
+        xf = _np(xf)
+        for g in (got[i], got[i + 2]):
+            assert np.abs(g - xf).max() <= 1e-12 * np.abs(xf).max()
+        hf.close()
+
+
 @pytest.mark.parametrize("method", [1, 2])
 def test_gmres_matches_oracle(method):
     cfg = W.boundary_layer_p2(method=method, N=12)
