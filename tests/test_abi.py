@@ -95,3 +95,29 @@ def test_reference_rules(lib, k):
 def test_invalid_arguments(lib):
     with pytest.raises(D.DGError):
         D.dg_reference_basis(7, np.zeros((1, 2)))
+
+
+def _declared_arity():
+    """Parameter count of every entry point in include/dg.h (comments removed)."""
+    import re
+    txt = open(D.HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    txt = re.sub(r"//[^\n]*", "", txt)
+    out = {}
+    for m in re.finditer(r"(dg_status|const char\s*\*|size_t)\s+(dg_\w+)\s*\(([^)]*)\)\s*;", txt):
+        args = m.group(3).strip()
+        out[m.group(2)] = (m.group(1).replace(" ", ""), 0 if args in ("", "void") else args.count(",") + 1)
+    return out
+
+
+def test_binding_signatures_match_the_header(lib):
+    """The binding passes exactly as many arguments as each declaration takes,
+    and declares the same result kind (status int, string or size)."""
+    import ctypes
+    kinds = {"dg_status": ctypes.c_int, "constchar*": ctypes.c_char_p, "size_t": ctypes.c_size_t}
+    arity = _declared_arity()
+    assert set(arity) == set(D.header_symbols())
+    for name, (ret, n) in arity.items():
+        res, args = D._SIGS[name]
+        assert len(args) == n, (name, len(args), n)
+        assert res is kinds[ret], (name, res, ret)
