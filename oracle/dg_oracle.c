@@ -20,7 +20,9 @@
  *   - y = (D+C+R) x, a block-Jacobi preconditioned restarted GMRES(m)
  *     (Saad & Schultz 1986, modified Gram-Schmidt Arnoldi, Givens rotations),
  *     a dense LU solve with partial pivoting (the "Stiff\F" of Sec. 2.3);
- *   - the L2 error and h_max reported by the paper's dg_error (Sec. 2.4).
+ *   - the L2 error and h_max reported by the paper's dg_error (Sec. 2.4);
+ *   - the non-linear reaction vector H(v) and its Jacobian HJ(v) of Sec. 3
+ *     (Eq. (nonlinsystem), (newton)) for r(u) = c u^p.
  *
  * Basis: scaled monomials ((x-xc)/hK)^a ((y-yc)/hK)^b, a+b <= k, on each
  * element (the paper's "Equation.base = 1" option, Sec. 4 set_parameter).
@@ -779,6 +781,43 @@ int orc_gmres(int nb, int ne, int ned, const int* edges, const double* diag, con
 done:
     free(V); free(w); free(z); free(H); free(cs); free(sn); free(gvec); free(yv);
     return converged ? 0 : 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Non-linear reaction (Sec. 3, Eq. (nonlin)): the vector H and its Jacobian  */
+/* HJ of Eq. (nonlinsystem)/(newton) for r(u) = c u^p,                       */
+/*   H_i(v)  = int_K r(u_h) phi_i,     u_h = sum_j v_j phi_j on K,           */
+/*   HJ_ij(v) = dH_i/dv_j = int_K r'(u_h) phi_j phi_i   (element-diagonal),  */
+/* with the volume rule of the assembly ((k+2)^2 Duffy points).             */
+/* H [ne*nb], HJ [ne][nb][nb] (row i = test function, column j = trial).    */
+/* ------------------------------------------------------------------------ */
+void orc_nonlinear(int k, const double* nodes, int ne, const int* elems, const double* coef,
+                   int p, double c, double* H, double* HJ)
+{
+    int n = k + 2, nb = nbasis(k);
+    double r[ORC_MAXQ * ORC_MAXQ], s[ORC_MAXQ * ORC_MAXQ], w[ORC_MAXQ * ORC_MAXQ];
+    duffy_rule(n, r, s, w);
+    double phi[ORC_MAXNB], d1[ORC_MAXNB], d2[ORC_MAXNB];
+    memset(H, 0, sizeof(double) * (size_t)ne * nb);
+    memset(HJ, 0, sizeof(double) * (size_t)ne * nb * nb);
+    for (int K = 0; K < ne; ++K) {
+        elem_geo g; element_geometry(nodes, elems, K, &g);
+        double detJ = 2.0 * g.area;
+        for (int q = 0; q < n * n; ++q) {
+            double x, y; ref_to_phys(&g, r[q], s[q], &x, &y);
+            monomial_basis(&g, k, x, y, phi, d1, d2);
+            double uh = 0.0;
+            for (int j = 0; j < nb; ++j) uh += coef[(size_t)K * nb + j] * phi[j];
+            double rv = c * ipow(uh, p);                       /* r(u_h)  */
+            double dr = p >= 1 ? c * p * ipow(uh, p - 1) : 0.0; /* r'(u_h) */
+            double wq = w[q] * detJ;
+            for (int i = 0; i < nb; ++i) {
+                H[(size_t)K * nb + i] += wq * rv * phi[i];
+                for (int j = 0; j < nb; ++j)
+                    HJ[((size_t)K * nb + i) * nb + j] += wq * dr * phi[j] * phi[i];
+            }
+        }
+    }
 }
 
 /* ------------------------------------------------------------------------ */

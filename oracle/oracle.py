@@ -313,6 +313,44 @@ def dense_matrix(mesh: Mesh, diag, off):
     return to_sparse(mesh, diag, off).toarray()
 
 
+def nonlinear(mesh: Mesh, k: int, coef, p: int, c: float):
+    """The paper's nonlinear_global (Sec. 3): H(v) and HJ(v) of Eq. (newton)
+    for r(u) = c u^p.  Returns H [ne*nb] and HJ [ne, nb, nb] (element-diagonal
+    blocks of the Jacobian of H)."""
+    lib = _load()
+    nb = nbasis(k)
+    coef = np.ascontiguousarray(coef, dtype=np.float64).reshape(-1)
+    H = np.zeros(mesh.ne * nb)
+    HJ = np.zeros((mesh.ne, nb, nb))
+    lib.orc_nonlinear(k, _d(mesh.nodes), mesh.ne, _i(mesh.elems), _d(coef), int(p), ctypes.c_double(c),
+                      _d(H), _d(HJ))
+    return H, HJ
+
+
+def newton(mesh: Mesh, system: System, p: int, c: float, tol: float = 1e-10, max_newton: int = 50):
+    """Newton's method of Eq. (newton) for D v + C v + R v + H(v) = F:
+    v^0 = 0; Res^k = A v^k + H(v^k) - F; J^k = A + HJ(v^k); J^k w^k = -Res^k
+    (sparse LU); v^{k+1} = v^k + w^k.  Stops when ||Res^k|| <= tol ||F||
+    (reading of the paper's test on the linear residual) or after max_newton
+    corrections.  Returns (v, corrections, [||Res^0||/||F||, ...])."""
+    import scipy.sparse.linalg as spla
+    k = system.k
+    A = to_sparse(mesh, system.A_diag, system.A_off)
+    F = system.F
+    nF = np.linalg.norm(F)
+    v = np.zeros_like(F)
+    hist = []
+    for it in range(max_newton + 1):
+        H, HJ = nonlinear(mesh, k, v, p, c)
+        res = A @ v + H - F
+        hist.append(np.linalg.norm(res) / nF)
+        if hist[-1] <= tol or it == max_newton:
+            return v, it, hist
+        J = to_sparse(mesh, system.A_diag + HJ, system.A_off)
+        v = v + spla.spsolve(J.tocsc(), -res)
+    return v, max_newton, hist
+
+
 def l2_error(mesh: Mesh, k: int, coef, uex_q):
     """The paper's dg_error (Sec. 2.4): (||u_h - u||_L2, h_max); uex_q at
     quad_points(ERROR)."""

@@ -95,8 +95,10 @@ def perturbed_mesh(N: int, seed: int, amount: float = 0.2, neumann_sides=()) -> 
 
 @dataclass
 class Problem:
-    """alpha u - eps Lap u + b.grad u = f with eps, alpha constant and
-    b(x,y) = (b0 + b1 x + b2 y, b3 + b4 x + b5 y) (Eq. (1))."""
+    """alpha u - eps Lap u + b.grad u (+ r(u)) = f with eps, alpha constant and
+    b(x,y) = (b0 + b1 x + b2 y, b3 + b4 x + b5 y) (Eq. (1)); with reaction =
+    (p, c) the non-linear reaction r(u) = c u^p of Sec. 3 is part of the
+    model (Eq. (nonlin))."""
     name: str
     eps: float
     alpha: float
@@ -105,6 +107,7 @@ class Problem:
     source: object = None         # callable(xp, x, y) -> f, when there is no exact solution
     neumann_sides: tuple = ()
     meta: dict = field(default_factory=dict)
+    reaction: tuple = ()          # (p, c): r(u) = c u^p
 
     def bvec(self, xp, x, y):
         b = self.b
@@ -116,7 +119,11 @@ class Problem:
             return self.source(xp, x, y)
         u, ux, uy, lap = self.exact(xp, x, y)
         bx, by = self.bvec(xp, x, y)
-        return self.alpha * u - self.eps * lap + bx * ux + by * uy
+        f = self.alpha * u - self.eps * lap + bx * ux + by * uy
+        if self.reaction:
+            p, c = self.reaction
+            f = f + c * u ** p
+        return f
 
     def u(self, xp, x, y):
         if self.exact is None:
@@ -243,6 +250,18 @@ def gaussian_bump_p3(N: int = 512) -> Config:
     return Config(f"bump_sipg_p3_n{N}", N, 3, 2,
                   Problem("gaussian", 1e-3, 0.1, (0.5, 0.0, -1.0, -0.5, 1.0, 0.0), gaussian_bump,
                           neumann_sides=("right", "top")))
+
+
+def tanh_nonlinear(N: int = 8, k: int = 1, method: int = 2) -> Config:
+    """The paper's non-linear example (Sec. 3 and its Main_Nonlinear listing):
+    the initial mesh refined twice (8x8 split squares, 128 triangles), SIPG P1,
+    eps = 1e-6, b = (1, 2)/sqrt(5), alpha = 1, r(u) = u^2, Dirichlet data on all
+    sides from u = (1 - tanh((2x - y - 0.25)/sqrt(5 eps)))/2."""
+    eps = 1e-6
+    s5 = 1.0 / math.sqrt(5.0)
+    return Config(f"tanh_nl_{'nipg' if method == 1 else ('sipg' if method == 2 else 'iipg')}_p{k}_n{N}", N, k,
+                  method, Problem("tanh_layer_u2", eps, 1.0, (s5, 0, 0, 2 * s5, 0, 0), tanh_layer(eps),
+                                  reaction=(2, 1.0)))
 
 
 # seed of instance i of a random family: SEED_BASE[family] + i

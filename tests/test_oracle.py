@@ -521,3 +521,92 @@ def test_bf16_rounding():
     import torch
     a = np.random.default_rng(2).standard_normal(1000) * 10
     np.testing.assert_array_equal(M.bf16_round(a), torch.tensor(a, dtype=torch.float32).to(torch.bfloat16).double().numpy())
+
+
+# ----------------------------------------------------------------------------
+# non-linear reaction r(u) = c u^p and Newton's method (Sec. 3)
+# ----------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+@pytest.mark.parametrize("p", [2, 3])
+def test_nonlinear_jacobian_is_the_derivative_of_H(k, p):
+    """HJ(v) is the Jacobian of H(v) (Eq. (newton)): central differences of H
+    in each coefficient.  H is element-local, so perturbing coefficient j of
+    every element at once gives column j of every diagonal block, and nothing
+    outside them."""
+    ma = W.perturbed_mesh(3, seed=5)
+    m = O.make_mesh(ma.nodes, ma.elems, ma.dirichlet, ma.neumann)
+    nb = O.nbasis(k)
+    rng = np.random.default_rng(10 * k + p)
+    v = rng.normal(size=m.ne * nb)
+    H, HJ = O.nonlinear(m, k, v, p, 0.7)
+    h = 1e-5
+    for j in range(nb):
+        e = np.zeros((m.ne, nb)); e[:, j] = h
+        Hp, _ = O.nonlinear(m, k, v + e.ravel(), p, 0.7)
+        Hm, _ = O.nonlinear(m, k, v - e.ravel(), p, 0.7)
+        fd = ((Hp - Hm) / (2 * h)).reshape(m.ne, nb)
+        np.testing.assert_allclose(fd, HJ[:, :, j], rtol=0, atol=1e-8 * np.abs(HJ).max())
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_nonlinear_H_against_adaptive_quadrature(k):
+    """H_i = int_K c u_h^2 phi_i on single elements, by scipy's adaptive dblquad
+    over the triangle: the assembly's (k+2)^2 Duffy rule is exact for this
+    degree-3k integrand when 3k <= 2k+2."""
+    from scipy.integrate import dblquad
+    ma = W.perturbed_mesh(2, seed=11)
+    m = O.make_mesh(ma.nodes, ma.elems, ma.dirichlet, ma.neumann)
+    nb = O.nbasis(k)
+    rng = np.random.default_rng(k)
+    v = rng.normal(size=m.ne * nb)
+    H, _ = O.nonlinear(m, k, v, 2, 1.3)
+    for K in (0, 5):
+        P = ma.nodes[ma.elems[K]]
+
+        def integrand(s, r, i):
+            xy = P[0] + r * (P[1] - P[0]) + s * (P[2] - P[0])
+            u, phi = O.evaluate(m, k, v, [K], xy[None, :], want_basis=True)
+            return 1.3 * u[0] ** 2 * phi[0, i]
+        e1, e2 = P[1] - P[0], P[2] - P[0]
+        det = abs(e1[0] * e2[1] - e1[1] * e2[0])
+        for i in range(nb):
+            val, _ = dblquad(integrand, 0.0, 1.0, 0.0, lambda r: 1.0 - r, args=(i,), epsabs=1e-13, epsrel=1e-13)
+            assert abs(val * det - H[K * nb + i]) <= 1e-11 * max(1.0, abs(H[K * nb + i]))
+
+
+@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("method", [1, 2, 3])
+def test_newton_reproduces_polynomial_solutions(k, method):
+    """With r(u) = c u^2 and u in P_k, the exact solution solves the discrete
+    non-linear system (consistency; the volume rule integrates u^2 phi exactly
+    for k <= 2), so Newton from v = 0 reaches it."""
+    a, bb = {1: (1, 0), 2: (1, 1)}[k]
+    prob = W.Problem("poly_u2", 0.3, 0.7, (0.4, 0.3, -0.2, -0.6, 0.1, 0.5), W.polynomial(a, bb),
+                     neumann_sides=("right", "top"), reaction=(2, 1.5))
+    ma = W.perturbed_mesh(4, seed=7, neumann_sides=prob.neumann_sides)
+    run = oracle_system(ma, k, method, prob)
+    v, steps, hist = O.newton(run.mesh, run.system, 2, 1.5, tol=1e-13)
+    assert hist[-1] <= 1e-13 and steps <= 8
+    err, _ = oracle_l2(run, v, prob)
+    assert err < 1e-11
+
+
+def test_newton_converges_quadratically_on_the_papers_example():
+    """The paper's non-linear example (tanh layer, r(u) = u^2, SIPG P1 on the
+    twice-refined initial mesh): Newton's residual falls quadratically once it
+    is small, and the iterate solves the discrete system to 1e-12."""
+    c = W.tanh_nonlinear()
+    ma = W.structured_mesh(c.N)
+    run = oracle_system(ma, c.k, c.method, c.problem)
+    v, steps, hist = O.newton(run.mesh, run.system, 2, 1.0, tol=1e-12)
+    assert hist[-1] <= 1e-12 and steps <= 12
+    tail = [(a, b) for a, b in zip(hist, hist[1:]) if a < 1e-3]
+    assert tail and all(b <= 10.0 * a * a for a, b in tail)
+    # r(u) = 0 recovers the linear system's solution
+    lin = W.Problem("tanh_layer", c.problem.eps, 1.0, c.problem.b, c.problem.exact)
+    run0 = oracle_system(ma, c.k, c.method, lin)
+    v0, steps0, _ = O.newton(run0.mesh, run0.system, 2, 0.0, tol=1e-13)
+    np.testing.assert_allclose(v0, oracle_direct(run0), rtol=0, atol=1e-10 * np.abs(v0).max())
+    assert steps0 == 1
