@@ -202,6 +202,34 @@ def batched_section(local, stream, n_inst):
     return out
 
 
+def nonlinear_section(local, stream):
+    """The paper's non-linear example (tanh layer, eps = 1e-6, b = (1,2)/sqrt(5),
+    alpha = 1, r(u) = u^2, SIPG) on 256x256 split squares with P2: Newton to
+    ||Res|| <= 1e-10 ||F||, each correction by GMRES(50) + block Jacobi on the
+    Jacobian to 1e-8; and the H / HJ kernel alone."""
+    import torch
+    from paper_1502_02941_gb300 import dg as D, problem, workloads as W
+    c = W.tanh_nonlinear(N=256, k=2)
+    h = D.DG(local)
+    problem.setup(h, c, mesh=W.structured_mesh(c.N), gmres_m=50, tol=1e-10, max_it=20000)
+    info = h.info()
+    h.newton_solve(p=2, c=1.0, max_newton=20, lin_tol=1e-8)            # warm-up
+    sec, (x, ni) = _events_time(stream, lambda: h.newton_solve(p=2, c=1.0, max_newton=20, lin_tol=1e-8))
+    l2, _ = h.l2_error(x, problem.exact_at_error_points(h, c.problem))
+    H = torch.empty(info.dofs, dtype=torch.float64, device=x.device)
+    HJ = torch.empty((info.ne, 6, 6), dtype=torch.float64, device=x.device)
+    reps = 20
+    for _ in range(3):
+        D.dg_nonlinear_global(h.h, 2, 1.0, x, H, HJ)
+    ksec, _ = _events_time(stream, lambda: [D.dg_nonlinear_global(h.h, 2, 1.0, x, H, HJ) for _ in range(reps)])
+    h.close()
+    return {"workload": "the paper's non-linear example (tanh layer, r(u) = u^2, eps = 1e-6, b = (1,2)/sqrt(5), "
+                        "alpha = 1, SIPG) on 256x256 split squares (131072 triangles), P2 (786432 dofs)",
+            "seconds": sec, "newton_steps": ni.outer, "gmres_steps": ni.iterations, "relres": ni.relres,
+            "converged": ni.status == 0, "l2_error": l2,
+            "k_nonlin_ms": ksec / reps * 1e3, "k_nonlin_elements_per_s": info.ne * reps / ksec}
+
+
 def learned_section(local, stream, n_inst, steps):
     """Learned preconditioner on the learned workload (64x64 split squares, P2,
     batched-workload coefficients): collect rows from the f64 solves of n_inst
@@ -594,6 +622,7 @@ def main():
     if not args.no_extras:
         line["batched"] = batched_section(local, stream, args.batch_instances)
         line["learned"] = learned_section(local, stream, args.learned_instances, args.learned_steps)
+        line["nonlinear"] = nonlinear_section(local, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ref_its, _ = oracle_iteration_counts()
         scale_its = ref_its if ref_its else its

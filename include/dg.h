@@ -402,6 +402,39 @@ dg_status dg_batch_gmres_ir_solve(dg_handle* h, int inner_dtype, int inner_m, do
                                   const double* F, double* x, int* its, double* relres, int* status);
 
 /* ------------------------------------------------------------------------ */
+/* non-linear reaction (Sec. 3)                                               */
+/* ------------------------------------------------------------------------ */
+/*
+ * The paper's nonlinear_global (Sec. 3, Eq. (nonlinsystem), (newton)) for
+ * r(u) = c u^p (p = 1..4; the paper's example is u^2): at the coefficients x
+ * (device [dofs] f64, the layout of dg_gmres_solve's x),
+ *   H  device [dofs] f64:           H_i = int_K r(u_h) phi_i,
+ *   HJ device [ne][nb][nb] f64 or NULL: HJ_K(i, j) = int_K r'(u_h) phi_j phi_i,
+ * the element-diagonal blocks of dH/dx (row i test, column j trial), with
+ * the volume rule of the assembly.  Needs an f64 assembly of the same
+ * degree; not in batch mode.  Asynchronous on the handle's stream.
+ */
+dg_status dg_nonlinear_global(dg_handle* h, int p, double c, const double* x, double* H, double* HJ);
+
+/*
+ * Solve alpha u - eps Lap u + b.grad u + c u^p = f (Eq. (nonlin)), i.e.
+ * A v + H(v) = F with A = D + C + R assembled by dg_assemble, by Newton's
+ * method (Eq. (newton)): v^0 = 0; Res^k = A v^k + H(v^k) - F;
+ * J^k = A + HJ(v^k); J^k w = -Res^k by restarted GMRES(params.gmres_m) with
+ * params.precond (block Jacobi, Schwarz or none) set up on J^k, to relative
+ * residual lin_tol; v^{k+1} = v^k + w.  Stops when ||Res^k|| <= params.tol
+ * ||F|| (DG_OK) or after max_newton corrections (DG_NOT_CONVERGED).
+ *   F device [dofs] f64 or NULL (assembled F); x device [dofs] f64 output.
+ *   info: outer = Newton corrections, iterations = GMRES steps summed,
+ *         relres = final ||Res|| / ||F||.
+ * DG_ERR_INVALID_ARG for p outside 1..4, max_newton < 1, lin_tol outside
+ * (0,1) or DG_PRECOND_MLP.  The preconditioner is left set up on the last
+ * Jacobian and is rebuilt by the next solve.  Synchronises.
+ */
+dg_status dg_newton_solve(dg_handle* h, int p, double c, int max_newton, double lin_tol, const double* F, double* x,
+                          dg_solve_info* info);
+
+/* ------------------------------------------------------------------------ */
 /* learned right preconditioner (not in the paper; layered on its method)    */
 /* ------------------------------------------------------------------------ */
 /*

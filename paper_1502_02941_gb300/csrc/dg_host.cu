@@ -56,7 +56,7 @@ dg_status dg_scratch(dg_handle* h, size_t bytes) {
 static void free_all(dg_handle* h) {
     void* ptrs[] = {h->nodes, h->elems, h->geo, h->nbr, h->nface, h->ftype, h->bidx, h->bedge, h->tab,
                     h->A64, h->A32, h->A16, h->F, h->Binv64, h->Binv32, h->Binv16, h->scratch, h->dflag, h->mx_buf,
-                    h->Ah64, h->Ah32, h->G64, h->G32};
+                    h->Ah64, h->Ah32, h->G64, h->G32, h->J64, h->nl_buf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (GmresWork& w : h->gw) dg_gmres_free(&w);

@@ -209,6 +209,13 @@ struct dg_handle {
     // mixed-precision refinement buffers (r64, A x, r32, d32, state)
     void* mx_buf = nullptr;
     size_t cap_mx = 0;
+
+    // Newton's method for the non-linear reaction (dg_nonlin.cu): the Jacobian
+    // J = A + HJ in the f64 block layout, and the vectors rhs, A v, H, w
+    double* J64 = nullptr;
+    size_t cap_J64 = 0;
+    double* nl_buf = nullptr;
+    size_t cap_nl = 0;
 };
 
 // error helpers (dg_host.cu)

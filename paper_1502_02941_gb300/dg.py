@@ -101,6 +101,9 @@ _SIGS = {
                                       c_void_p, c_void_p, c_void_p, c_void_p]),
     "dg_batch_gmres_ir_solve": (ctypes.c_int, [c_void_p, ctypes.c_int, ctypes.c_int, c_double, ctypes.c_int,
                                                c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "dg_nonlinear_global": (ctypes.c_int, [c_void_p, ctypes.c_int, c_double, c_void_p, c_void_p, c_void_p]),
+    "dg_newton_solve": (ctypes.c_int, [c_void_p, ctypes.c_int, c_double, ctypes.c_int, c_double, c_void_p,
+                                       c_void_p, ctypes.POINTER(dg_solve_info)]),
     "dg_mlp_num_params": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(c_int64)]),
     "dg_mlp_init": (ctypes.c_int, [c_void_p, ctypes.c_uint64]),
     "dg_mlp_set_weights": (ctypes.c_int, [c_void_p, c_void_p, c_int64]),
@@ -340,6 +343,15 @@ def dg_batch_gmres_ir_solve(h, inner_dtype, inner_m, inner_tol, max_outer, F, x,
                                           _ptr(F), _ptr(x), _ptr(its), _ptr(relres), _ptr(status))
 
 
+def dg_nonlinear_global(h, p, c, x, H, HJ=None):
+    return load().dg_nonlinear_global(h, int(p), float(c), _ptr(x), _ptr(H), _ptr(HJ))
+
+
+def dg_newton_solve(h, p, c, max_newton, lin_tol, F, x, info):
+    return load().dg_newton_solve(h, int(p), float(c), int(max_newton), float(lin_tol), _ptr(F), _ptr(x),
+                                  ctypes.byref(info))
+
+
 def dg_mlp_num_params(degree):
     n = c_int64()
     s = load().dg_mlp_num_params(int(degree), ctypes.byref(n))
@@ -563,6 +575,24 @@ class DG:
         x = self._empty((i.dofs,)) if x is None else x
         info = dg_solve_info()
         s = dg_gmres_ir_solve(self.h, inner_dtype, inner_m, inner_tol, max_outer, F, x, info)
+        if s != DG_OK and not (s == DG_NOT_CONVERGED and not raise_on_nonconv):
+            self.check(s)
+        return x, info
+
+    def nonlinear_global(self, x, p=2, c=1.0, want_jacobian=True):
+        """H(x) [dofs] and, if asked, the element blocks of its Jacobian [ne, nb, nb]."""
+        i = self.info()
+        nb = i.dofs // i.ne
+        H = self._empty((i.dofs,))
+        HJ = self._empty((i.ne, nb, nb)) if want_jacobian else None
+        self.check(dg_nonlinear_global(self.h, p, c, x, H, HJ))
+        return H, HJ
+
+    def newton_solve(self, p=2, c=1.0, max_newton=50, lin_tol=1e-12, F=None, x=None, raise_on_nonconv=True):
+        i = self.info()
+        x = self._empty((i.dofs,)) if x is None else x
+        info = dg_solve_info()
+        s = dg_newton_solve(self.h, p, c, max_newton, lin_tol, F, x, info)
         if s != DG_OK and not (s == DG_NOT_CONVERGED and not raise_on_nonconv):
             self.check(s)
         return x, info
