@@ -4,10 +4,13 @@
     python -m paper_1502_02941_gb300.cli --workload bump --N 64 --solver mixed-bf16
     python -m paper_1502_02941_gb300.cli --workload bump --solver gmres-ir-f32 --max-it 400000
     python -m paper_1502_02941_gb300.cli --workload bump --solver gmres-ir-f32 --precond schwarz
+    python -m paper_1502_02941_gb300.cli --workload tanh-u2 --solver newton
 
 Workloads: sine (8x8 split squares, P1 SIPG, u = sin(pi x) sin(pi y)), layer
 (256x256, P2, eps = 1e-6 boundary layer), bump (512x512, P3, rotating flow,
-Gaussian bump, Neumann right/top); --N changes the mesh size.
+Gaussian bump, Neumann right/top), tanh-u2 (the paper's non-linear example:
+8x8, P1, tanh layer with r(u) = u^2; --k sets the degree); --N changes the mesh
+size.  The newton solver applies to tanh-u2.
 
 Prints one JSON line with sizes, iterations, relative residual, L2 error (when
 the workload has an exact solution) and wall time of the solve.
@@ -21,11 +24,13 @@ import time
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="layer", choices=["sine", "layer", "bump"])
+    ap.add_argument("--workload", default="layer", choices=["sine", "layer", "bump", "tanh-u2"])
+    ap.add_argument("--k", type=int, default=None, help="degree (tanh-u2)")
     ap.add_argument("--N", type=int, default=None)
     ap.add_argument("--method", type=int, default=None, help="1 NIPG, 2 SIPG, 3 IIPG")
     ap.add_argument("--solver", default="gmres",
-                    choices=["gmres", "dense", "mixed-bf16", "mixed-f32", "gmres-ir-bf16", "gmres-ir-f32"])
+                    choices=["gmres", "dense", "mixed-bf16", "mixed-f32", "gmres-ir-bf16", "gmres-ir-f32",
+                             "newton"])
     ap.add_argument("--precond", default="block-jacobi", choices=["block-jacobi", "schwarz", "none"])
     ap.add_argument("--m", type=int, default=50)
     ap.add_argument("--tol", type=float, default=1e-10)
@@ -43,8 +48,12 @@ def main(argv=None):
         cfg = W.sine_8x8()
     elif a.workload == "layer":
         cfg = W.boundary_layer_p2(method=a.method or 2, N=a.N or 256)
+    elif a.workload == "tanh-u2":
+        cfg = W.tanh_nonlinear(N=a.N or 8, k=a.k or 1, method=a.method or 2)
     else:
         cfg = W.gaussian_bump_p3(N=a.N or 512)
+    if (a.solver == "newton") != bool(cfg.problem.reaction):
+        ap.error("--solver newton goes with the non-linear workload tanh-u2, and only there")
     if a.N and a.workload == "sine":
         cfg.N = a.N
     if a.method:
@@ -69,6 +78,9 @@ def main(argv=None):
             si = None
         elif a.solver == "gmres":
             x, si = h.gmres_solve(raise_on_nonconv=False)
+        elif a.solver == "newton":
+            p, c = cfg.problem.reaction
+            x, si = h.newton_solve(p=p, c=c, max_newton=50, lin_tol=min(1e-2, 100 * a.tol), raise_on_nonconv=False)
         elif a.solver.startswith("mixed"):
             dt = D.DG_BF16 if a.solver == "mixed-bf16" else D.DG_F32
             x, si = h.mixed_solve(dt, inner_m=a.m, inner_tol=1e-2 if dt == D.DG_BF16 else 1e-4, max_outer=60,

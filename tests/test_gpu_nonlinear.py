@@ -69,6 +69,13 @@ def test_newton_on_the_papers_example_matches_oracle(method):
     assert _oracle_nonlinear_residual(run, xo, 2, 1.0) <= 1e-10
     vo, steps, _ = O.newton(run.mesh, run.system, 2, 1.0, tol=1e-12)
     np.testing.assert_allclose(xo, vo, rtol=0, atol=1e-7 * np.abs(vo).max())
+    # the paper's driver prints DoFs, h_max, L2 error and Newton steps
+    from paper_1502_02941_gb300 import problem
+    from helpers import oracle_l2
+    l2g, hmax = h.l2_error(x, problem.exact_at_error_points(h, c.problem))
+    l2o, hmo = oracle_l2(run, vo, c.problem)
+    assert abs(l2g - l2o) <= 1e-8 * l2o and abs(hmax - hmo) <= 1e-15
+    assert abs(info.outer - steps) <= 1
     h.close()
 
 

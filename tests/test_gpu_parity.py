@@ -270,6 +270,28 @@ def test_sine_8x8_dense_solve_and_l2():
     h.close()
 
 
+@pytest.mark.parametrize("method", [1, 2, 3])
+def test_papers_linear_example(method):
+    """The paper's linear example (Sec. 2: tanh internal layer, eps = 1e-6,
+    b = (1,2)/sqrt(5), alpha = 1, P1 on the twice-refined initial mesh): the
+    dense and the GMRES solve equal the oracle's direct solve as functions, and
+    the L2 error and h_max its dg_error."""
+    c = W.tanh_nonlinear(method=method)
+    prob = W.Problem("tanh_layer", c.problem.eps, c.problem.alpha, c.problem.b, c.problem.exact)
+    ma = W.structured_mesh(c.N)
+    h = gpu_setup(ma, c.k, method, prob, tol=1e-12, gmres_m=50)
+    run = oracle_run(ma, c.k, method, prob)
+    xo = oracle_direct(run)
+    T = basis_change(run, ma, c.k)
+    for xg, tol in ((h.gmres_solve()[0], 1e-8), (h.dense_solve(), 1e-10)):
+        np.testing.assert_allclose(x_to_oracle(T, _np(xg)), xo, rtol=0, atol=tol * np.abs(xo).max())
+    xe = O.quad_points(run.mesh, c.k, O.ERROR)
+    l2o, hmo = O.l2_error(run.mesh, c.k, xo, prob.u(np, xe[..., 0], xe[..., 1]))
+    l2g, hmax = h.l2_error(xg, problem.exact_at_error_points(h, prob))
+    assert abs(l2g - l2o) <= 1e-9 * l2o and abs(hmax - hmo) <= 1e-15
+    h.close()
+
+
 def test_captured_cycle_is_not_reused_across_degree_or_size():
     """The restart cycle captured as a CUDA graph bakes in the element count and
     the degree.  A P1 mesh and a P2 mesh with the same number of unknowns (384),

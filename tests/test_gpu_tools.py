@@ -28,6 +28,20 @@ def test_cli_iterative_solvers(solver):
     assert out["status"] == "DG_OK" and out["relres"] <= 1e-10
 
 
+def test_cli_newton_on_the_papers_nonlinear_example():
+    out = _run("paper_1502_02941_gb300.cli", "--workload", "tanh-u2", "--solver", "newton")
+    assert out["status"] == "DG_OK" and out["relres"] <= 1e-10 and 1 <= out["outer"] <= 15
+    # L2 error and h_max of the paper's driver, against the oracle's Newton solve
+    import oracle as O
+    from paper_1502_02941_gb300 import workloads as W
+    from helpers import oracle_l2, oracle_system
+    c = W.tanh_nonlinear()
+    run = oracle_system(W.structured_mesh(c.N), c.k, c.method, c.problem)
+    v, _, _ = O.newton(run.mesh, run.system, 2, 1.0, tol=1e-12)
+    l2o, hmo = oracle_l2(run, v, c.problem)
+    assert out["ne"] == 128 and abs(out["l2_error"] - l2o) <= 1e-5 * l2o and abs(out["h_max"] - hmo) <= 1e-15
+
+
 @pytest.mark.parametrize("kernel", ["dots", "update", "apply32", "assemble"])
 def test_profile_case_kernels(kernel):
     out = _run("paper_1502_02941_gb300.profile_case", "--kernel", kernel, "--N", "32", "--reps", "2")
