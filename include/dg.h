@@ -199,6 +199,25 @@ dg_status dg_params_default(dg_params* p);
 dg_status dg_mesh_upload(dg_handle* h, const double* nodes, int nv, const int* elems, int ne,
                          const int* dirichlet, int nd, const int* neumann, int nn);
 
+/*
+ * Uniform (red) refinement, the paper's uniformrefine (Sec. 2.1): every
+ * triangle is cut into four by its edge midpoints and every boundary edge into
+ * two.  Host arrays in (as dg_mesh_upload), caller-allocated host arrays out;
+ * no GPU is used and no handle is needed.  With nodes_out == NULL only the
+ * sizes are written: *nv_out = nv + (number of distinct edges), *ne_out = 4 ne,
+ * *nd_out = 2 nd, *nn_out = 2 nn.  Otherwise nodes_out [*nv_out][2] keeps the
+ * old nodes first and then the edge midpoints, numbered in the order their
+ * edges are first met (elements in order, local edges (0,1), (1,2), (2,0));
+ * element (a, b, c) with midpoints m_ab, m_bc, m_ca becomes (a, m_ab, m_ca),
+ * (m_ab, b, m_bc), (m_ca, m_bc, c), (m_ab, m_bc, m_ca) in elems_out
+ * [4 ne][3], counter-clockwise when the parent is; boundary edge (s, e)
+ * becomes (s, m), (m, e).  DG_ERR_MESH for a node index out of range or a
+ * boundary edge that is not an element edge.
+ */
+dg_status dg_mesh_refine(const double* nodes, int nv, const int* elems, int ne, const int* dirichlet, int nd,
+                         const int* neumann, int nn, double* nodes_out, int* nv_out, int* elems_out, int* ne_out,
+                         int* dirichlet_out, int* nd_out, int* neumann_out, int* nn_out);
+
 /* Set method and solver parameters (the paper's set_parameter).  A change of
    degree invalidates assembled data. */
 dg_status dg_set_params(dg_handle* h, const dg_params* p);

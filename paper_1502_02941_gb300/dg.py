@@ -101,6 +101,10 @@ _SIGS = {
                                       c_void_p, c_void_p, c_void_p, c_void_p]),
     "dg_batch_gmres_ir_solve": (ctypes.c_int, [c_void_p, ctypes.c_int, ctypes.c_int, c_double, ctypes.c_int,
                                                c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "dg_mesh_refine": (ctypes.c_int, [c_void_p, ctypes.c_int, c_void_p, ctypes.c_int, c_void_p, ctypes.c_int,
+                                      c_void_p, ctypes.c_int, c_void_p, ctypes.POINTER(ctypes.c_int), c_void_p,
+                                      ctypes.POINTER(ctypes.c_int), c_void_p, ctypes.POINTER(ctypes.c_int),
+                                      c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "dg_nonlinear_global": (ctypes.c_int, [c_void_p, ctypes.c_int, c_double, c_void_p, c_void_p, c_void_p]),
     "dg_newton_solve": (ctypes.c_int, [c_void_p, ctypes.c_int, c_double, ctypes.c_int, c_double, c_void_p,
                                        c_void_p, ctypes.POINTER(dg_solve_info)]),
@@ -341,6 +345,30 @@ def dg_batch_gmres_ir_solve(h, inner_dtype, inner_m, inner_tol, max_outer, F, x,
                             status=None):
     return load().dg_batch_gmres_ir_solve(h, int(inner_dtype), int(inner_m), float(inner_tol), int(max_outer),
                                           _ptr(F), _ptr(x), _ptr(its), _ptr(relres), _ptr(status))
+
+
+def dg_mesh_refine(nodes, elems, dirichlet, neumann):
+    """The paper's uniformrefine (Sec. 2.1) through libdg: one red refinement of
+    host arrays; returns (nodes, elems, dirichlet, neumann) as numpy arrays."""
+    lib = load()
+    nodes = np.ascontiguousarray(nodes, dtype=np.float64).reshape(-1, 2)
+    elems = np.ascontiguousarray(elems, dtype=np.int32).reshape(-1, 3)
+    dirichlet = np.ascontiguousarray(dirichlet, dtype=np.int32).reshape(-1, 2)
+    neumann = np.ascontiguousarray(neumann, dtype=np.int32).reshape(-1, 2)
+    sizes = [ctypes.c_int() for _ in range(4)]
+    args = (_ptr(nodes), nodes.shape[0], _ptr(elems), elems.shape[0], _ptr(dirichlet), dirichlet.shape[0],
+            _ptr(neumann), neumann.shape[0])
+    s = lib.dg_mesh_refine(*args, None, ctypes.byref(sizes[0]), None, ctypes.byref(sizes[1]), None,
+                           ctypes.byref(sizes[2]), None, ctypes.byref(sizes[3]))
+    if s != DG_OK:
+        raise DGError(s, "dg_mesh_refine")
+    nv, ne, nd, nn = (v.value for v in sizes)
+    out = (np.zeros((nv, 2)), np.zeros((ne, 3), np.int32), np.zeros((nd, 2), np.int32), np.zeros((nn, 2), np.int32))
+    s = lib.dg_mesh_refine(*args, _ptr(out[0]), ctypes.byref(sizes[0]), _ptr(out[1]), ctypes.byref(sizes[1]),
+                           _ptr(out[2]), ctypes.byref(sizes[2]), _ptr(out[3]), ctypes.byref(sizes[3]))
+    if s != DG_OK:
+        raise DGError(s, "dg_mesh_refine")
+    return out
 
 
 def dg_nonlinear_global(h, p, c, x, H, HJ=None):

@@ -77,6 +77,26 @@ def structured_mesh(N: int, neumann_sides=(), x0=0.0, y0=0.0, L=1.0) -> MeshArra
     return MeshArrays(nodes, elems, dirichlet, neumann)
 
 
+def lshape_mesh() -> MeshArrays:
+    """An L-shaped polygon: the unit square without its upper-right quarter, as
+    six triangles of the 2x2 split-square mesh.  Dirichlet on the edges that
+    touch x = 0 or y = 0, Neumann on the rest; boundary edges counter-clockwise."""
+    m = structured_mesh(2)
+    keep = [K for K in range(m.ne) if not (m.nodes[m.elems[K]].mean(0) > 0.5).all()]
+    elems = m.elems[keep].astype(np.int32)
+    count: dict = {}
+    for t in elems:
+        for f in range(3):
+            e = tuple(sorted((int(t[f]), int(t[(f + 1) % 3]))))
+            count[e] = count.get(e, 0) + 1
+    bnd = [(int(t[f]), int(t[(f + 1) % 3])) for t in elems for f in range(3)
+           if count[tuple(sorted((int(t[f]), int(t[(f + 1) % 3]))))] == 1]
+    on_axis = lambda e: (m.nodes[list(e)] == 0.0).any()   # noqa: E731
+    dirichlet = np.array([e for e in bnd if on_axis(e)], np.int32).reshape(-1, 2)
+    neumann = np.array([e for e in bnd if not on_axis(e)], np.int32).reshape(-1, 2)
+    return MeshArrays(m.nodes, elems, dirichlet, neumann)
+
+
 def perturbed_mesh(N: int, seed: int, amount: float = 0.2, neumann_sides=()) -> MeshArrays:
     """structured_mesh with interior nodes moved by up to amount*h (seeded):
     a general unstructured-looking triangulation that stays valid."""

@@ -292,6 +292,30 @@ def test_papers_linear_example(method):
     h.close()
 
 
+@pytest.mark.parametrize("k", [1, 2])
+def test_solve_on_a_refined_polygonal_mesh(k):
+    """uniformrefine (Sec. 2.1) of an L-shaped domain with Dirichlet and Neumann
+    parts, three times (384 triangles), then the GPU solve: a P_k polynomial is
+    reproduced, and the solution equals the oracle's direct solve on the same
+    mesh as a function."""
+    m = W.lshape_mesh()
+    arrays = (m.nodes, m.elems, m.dirichlet, m.neumann)
+    for _ in range(3):
+        arrays = D.dg_mesh_refine(*arrays)
+    ma = W.MeshArrays(*arrays)
+    a, bb = {1: (1, 0), 2: (1, 1)}[k]
+    prob = W.Problem("poly", 0.3, 0.7, (0.4, 0.3, -0.2, -0.6, 0.1, 0.5), W.polynomial(a, bb))
+    h = gpu_setup(ma, k, 2, prob, tol=1e-12, gmres_m=50)
+    x, _ = h.gmres_solve()
+    l2, _ = h.l2_error(x, problem.exact_at_error_points(h, prob))
+    assert l2 < 1e-9
+    run = oracle_run(ma, k, 2, prob)
+    xo = oracle_direct(run)
+    T = basis_change(run, ma, k)
+    np.testing.assert_allclose(x_to_oracle(T, _np(x)), xo, rtol=0, atol=1e-8 * np.abs(xo).max())
+    h.close()
+
+
 def test_captured_cycle_is_not_reused_across_degree_or_size():
     """The restart cycle captured as a CUDA graph bakes in the element count and
     the degree.  A P1 mesh and a P2 mesh with the same number of unknowns (384),
