@@ -171,6 +171,47 @@ def test_mass_matrix_exact(k):
     np.testing.assert_allclose(run.system.R_diag[0], M, rtol=1e-13, atol=1e-15)
 
 
+@pytest.mark.parametrize("k", [2, 3])
+def test_stiffness_matrix_exact(k):
+    """The volume diffusion block eps int grad(phi_j).grad(phi_i) for P2 and P3
+    against exact integrals of the monomial derivatives (a one-element mesh
+    with Neumann edges only, where D has no edge terms, Sec. 1 / Eq. (ds))."""
+    v = [[0.1, 0.2], [0.9, 0.35], [0.3, 0.8]]
+    eps = 0.37
+    ma = _one_element(v)
+    ma = W.MeshArrays(ma.nodes, ma.elems, np.zeros((0, 2), np.int32), ma.dirichlet)
+    run = oracle_system(ma, k, 2, W.Problem("z", eps, 0.0, (0,) * 6, None, lambda xp, x, y: 0 * x))
+    V = np.array(v)
+    xc, yc = V.mean(0)
+    h = max(np.linalg.norm(V[(i + 1) % 3] - V[i]) for i in range(3))
+    exps = [(a, d - a) for d in range(k + 1) for a in range(d, -1, -1)]
+
+    def I(a, b):
+        return _exact_monomial_integral(v, a, b, xc, yc, h) if a >= 0 and b >= 0 else 0.0
+    S = np.array([[(ai * aj * I(ai + aj - 2, bi + bj) + bi * bj * I(ai + aj, bi + bj - 2)) / h ** 2
+                   for (aj, bj) in exps] for (ai, bi) in exps])
+    np.testing.assert_allclose(run.system.D_diag[0], eps * S, rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_convection_matrix_exact(k):
+    """Volume convection int (b.grad phi_j) phi_i with the radial field
+    b = (x - xc, y - yc): by Euler's theorem b.grad phi_j = deg_j phi_j for the
+    scaled monomials, so C = M diag(deg).  b.n > 0 on every edge (the centroid
+    is inside), so no upwind edge term enters C (reading A-5/A-6)."""
+    v = [[0.1, 0.2], [0.9, 0.35], [0.3, 0.8]]
+    V = np.array(v)
+    xc, yc = V.mean(0)
+    b = (-xc, 1.0, 0.0, -yc, 0.0, 1.0)
+    run = oracle_system(_one_element(v), k, 2, W.Problem("z", 0.0, 0.0, b, None, lambda xp, x, y: 0 * x))
+    h = max(np.linalg.norm(V[(i + 1) % 3] - V[i]) for i in range(3))
+    exps = [(a, d - a) for d in range(k + 1) for a in range(d, -1, -1)]
+    M = np.array([[_exact_monomial_integral(v, ai + aj, bi + bj, xc, yc, h) for (aj, bj) in exps]
+                  for (ai, bi) in exps])
+    deg = np.array([a + bb for a, bb in exps], dtype=float)
+    np.testing.assert_allclose(run.system.C_diag[0], M * deg[None, :], rtol=1e-12, atol=1e-15)
+
+
 def test_p1_stiffness_and_mass_closed_form():
     """P1 element matrices in the barycentric (hat) basis, textbook forms:
     stiffness |K| grad(lambda_i).grad(lambda_j) = (e_i . e_j)/(4|K|) with e_i
