@@ -19,7 +19,9 @@
 // refinement, r = F - A64 x, inner batched GMRES on f32 vectors for
 // A_lo d = r/||r||, x += ||r|| d; instances whose f64 relative residual meets
 // the tolerance leave the refinement.  inner_dtype DG_F64: one batched f64
-// GMRES on A64 x = F.
+// GMRES on A64 x = F.  GMRES-based refinement (dg_batch_gmres_ir_solve): a
+// per-instance f64 flexible GMRES on A64 whose preconditioner is the batched
+// inner solve; its state is a second solver-state set over the same items.
 #include <math.h>
 #include <string.h>
 

@@ -3,19 +3,25 @@
 //
 // Every step of the iteration runs in kernels on the handle's stream; the
 // host launches one captured CUDA graph per restart cycle and reads a small
-// status header when the cycle ends.  One Arnoldi step j is 4 kernels:
-//   1. Z       = s_j M^-1 V_j                       (block-Jacobi apply)
-//   2. V_{j+1} = A Z                                (operator apply)
-//   3. r_d     = <V_d, V_{j+1}>, d <= j+1           (one multi-dot pass; d = j+1
-//                                                    is ||V_{j+1}||^2)
-//   4. V_{j+1} -= sum_d s_d^2 r_d V_d, ||V_{j+1}||^2 (one update pass)
-// plus, only when the norm fell below 0.7 of its value before the update, a
-// second classical Gram-Schmidt pass (kernels 3-4 again; otherwise they exit at
-// once).  Reductions finish inside the reducing kernel: the last block to
-// arrive (threadfence + arrival counter, no waiting) sums the per-block
-// partials in a fixed order and runs the control step -- Hessenberg column,
-// Givens rotations, residual estimate, convergence / re-orthogonalisation
-// decisions -- so results are deterministic.  Basis vectors are stored
+// status header when the cycle ends.  One Arnoldi step j is 3 kernels:
+//   1. V_{j+1} = s_j (A M^-1) V_j                   (one apply of the operator
+//                                                    preconditioned once at
+//                                                    set-up; with Schwarz or
+//                                                    the learned correction the
+//                                                    preconditioner is applied
+//                                                    first, then A)
+//   2. r_d = <V_d, V_{j+1}>, d <= j+1               (one multi-dot pass; d = j+1
+//                                                    is ||w||^2)
+//   3. V_{j+1} -= sum_d s_d^2 r_d V_d               (one update pass)
+// The norm of the orthogonalised vector comes from the same reduction as
+// ||w||^2 - sum_d h_d^2 (single-reduction classical Gram-Schmidt).  When that
+// leaves less than 0.49 ||w||^2 a second Gram-Schmidt pass runs (kernels 2-3
+// again, which otherwise exit at once) and its own self-dot gives the norm.
+// The multi-dot finishes its reduction in the last block to arrive
+// (threadfence + arrival counter, no waiting), which sums the per-block
+// partials in a fixed order, so results are deterministic; block 0 of the
+// update kernel then takes the Hessenberg / Givens step and the convergence
+// decision while the other blocks stream.  Basis vectors are stored
 // unnormalised with s_i = 1/||V_i||.  Hessenberg and Givens arithmetic is f64.
 // End of a cycle: y = H^-1 g, U = sum y_i s_i V_i, x += M^-1 U, r = F - A x,
 // and the true residual decides convergence.
@@ -184,8 +190,9 @@ __global__ void __launch_bounds__(256) k_gm_init(const TV* __restrict__ F, TV* _
     st->g[0] = bn;
     st->scale[0] = 1.0 / bn;
 }
-// Givens / Hessenberg step for column j; runs in thread 0 of the last block
-// with the column and the previous rotations staged in shared memory.
+// Givens / Hessenberg step for column j; runs in thread 0 of the update
+// kernel's block 0 with the column and the previous rotations staged in
+// shared memory.
 __device__ void gm_finish_column(GmresState* st, double wn, const double* hc, const double* cs, const double* sn) {
     // state read up front: the stores into H below may alias it for the compiler
     const int j = st->j, m = st->m, its = st->its + 1, max_it = st->max_it;
