@@ -161,7 +161,9 @@ def status_name(s):
 
 
 def _ptr(x):
-    """Device/host pointer of a torch tensor, numpy array, int or None."""
+    """Pointer of a numpy array (host data), a torch tensor (device data: the
+    kernels dereference it, so a host tensor is refused here rather than left
+    to fault on the GPU), an int or None."""
     if x is None:
         return None
     if isinstance(x, int):
@@ -173,6 +175,8 @@ def _ptr(x):
     if hasattr(x, "data_ptr"):
         if not x.is_contiguous():
             raise ValueError("tensor must be contiguous")
+        if not x.is_cuda:
+            raise ValueError("a device (CUDA) tensor is expected here; host data goes in numpy arrays")
         return x.data_ptr()
     raise TypeError(f"cannot take a pointer of {type(x)}")
 

@@ -121,3 +121,15 @@ def test_binding_signatures_match_the_header(lib):
         res, args = D._SIGS[name]
         assert len(args) == n, (name, len(args), n)
         assert res is kinds[ret], (name, res, ret)
+
+
+def test_binding_refuses_host_tensors_for_device_arguments():
+    """Torch tensors are passed to the kernels as device pointers; a host tensor
+    is refused in the binding before any call (numpy arrays are the host path)."""
+    import torch
+    with pytest.raises(ValueError):
+        D._ptr(torch.zeros(4, dtype=torch.float64))
+    with pytest.raises(ValueError):
+        D._ptr(np.zeros((4, 2))[:, 0])          # not contiguous
+    a = np.zeros(3)
+    assert D._ptr(a) == a.ctypes.data and D._ptr(None) is None and D._ptr(7) == 7
