@@ -31,7 +31,9 @@
  *   A-1  RHS Dirichlet consistency term is  +kappa*eps*grad(v).n*gD  (equal to
  *        the printed -eps*grad(v).n*gD for SIPG); flag `literal_rhs` restores
  *        the printed sign for every method.
- *   A-3  h_e = |e| (edge length), superpenalisation exponent b0 = 1.
+ *   A-3  h_e = |e| (edge length), raised to the superpenalisation exponent b0
+ *        of set_parameter (Sec. 4; the paper's default b0 = 1): the penalty
+ *        terms carry sigma eps / |e|^b0.
  *   A-5  upwind decision taken pointwise at each edge quadrature point with the
  *        strict inequality b.n < 0 (weight min(b.n,0)).
  *   A-6  the inflow-boundary terms are applied on every boundary edge where
@@ -370,6 +372,7 @@ typedef struct {
     double kappa, sigma_int, sigma_bdry, eps, alpha;
     double b[6];
     int literal_rhs;
+    double b0;        /* superpenalisation exponent: penalty sigma eps / |e|^b0 */
 } orc_coeffs;
 
 static void advection(const orc_coeffs* c, double x, double y, double* bx, double* by)
@@ -389,14 +392,14 @@ static void advection(const orc_coeffs* c, double x, double y, double* bx, doubl
 void orc_assemble(int k, const double* nodes, int ne, const int* elems,
                   int ned, const int* edges, const int* elem_edges,
                   double kappa, double sigma_int, double sigma_bdry,
-                  double eps, double alpha, const double* b_affine, int literal_rhs,
+                  double eps, double alpha, const double* b_affine, int literal_rhs, double b0,
                   const double* f_q, const double* gD_q, const double* gN_q,
                   double* D_diag, double* D_off, double* C_diag, double* C_off,
                   double* R_diag, double* R_off, double* F)
 {
     orc_coeffs cf;
     cf.kappa = kappa; cf.sigma_int = sigma_int; cf.sigma_bdry = sigma_bdry;
-    cf.eps = eps; cf.alpha = alpha; cf.literal_rhs = literal_rhs;
+    cf.eps = eps; cf.alpha = alpha; cf.literal_rhs = literal_rhs; cf.b0 = b0;
     for (int i = 0; i < 6; ++i) cf.b[i] = b_affine[i];
     const int nb = nbasis(k);
     const size_t nb2 = (size_t)nb * nb;
@@ -451,7 +454,7 @@ void orc_assemble(int k, const double* nodes, int ne, const int* elems,
             double dx = bpt[0] - a[0], dy = bpt[1] - a[1];
             double len = sqrt(dx * dx + dy * dy);
             double ne_x = dy / len, ne_y = -dx / len;   /* n_e: outward of Ki */
-            double he = len;                              /* A-3 */
+            double he = pow(len, cf.b0);                  /* A-3: h_e = |e|, raised to b0 */
             int type = E[4];
             int bidx = -1;
             if (E[3] < 0) bidx = (int)(ib++);

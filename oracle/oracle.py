@@ -208,10 +208,12 @@ class System:
 
 def assemble(mesh: Mesh, k: int, kappa: float, sigma_int: float, sigma_bdry: float,
              eps: float, alpha: float, b_affine, f_q, gD_q, gN_q,
-             literal_rhs: bool = False, split: bool = True) -> System:
+             literal_rhs: bool = False, split: bool = True, b0: float = 1.0) -> System:
     """The paper's global_system (Sec. 2.3): D, C, R and F of Eq. (system).
 
-    b_affine = (b0..b5): b(x,y) = (b0 + b1 x + b2 y, b3 + b4 x + b5 y).
+    b_affine = (c0..c5): b(x,y) = (c0 + c1 x + c2 y, c3 + c4 x + c5 y).
+    b0: the superpenalisation exponent of set_parameter (Sec. 4): the penalty
+    terms carry sigma eps / |e|^b0 (reading A-3; the paper's default is 1).
     f_q at quad_points(VOLUME); gD_q, gN_q at quad_points(BOUNDARY) (gD is read
     on Dirichlet edges and on the inflow part of every boundary edge, reading
     A-6; gN on Neumann edges).  With split=False only A = D+C+R is stored (in
@@ -235,7 +237,7 @@ def assemble(mesh: Mesh, k: int, kappa: float, sigma_int: float, sigma_bdry: flo
     F = np.zeros((ne, nb))
     lib.orc_assemble(k, _d(mesh.nodes), ne, _i(mesh.elems), ned, _i(mesh.edges), _i(mesh.elem_edges),
                      ctypes.c_double(kappa), ctypes.c_double(sigma_int), ctypes.c_double(sigma_bdry),
-                     ctypes.c_double(eps), ctypes.c_double(alpha), _d(b), ctypes.c_int(int(literal_rhs)),
+                     ctypes.c_double(eps), ctypes.c_double(alpha), _d(b), ctypes.c_int(int(literal_rhs)), ctypes.c_double(b0),
                      _d(f_q), _d(gD_q), _d(gN_q), _d(Dd), _d(Do), _d(Cd), _d(Co), _d(Rd), _d(Ro), _d(F))
     if not split:
         z_d, z_o = np.zeros_like(Dd), np.zeros_like(Do)

@@ -35,7 +35,7 @@ class OracleRun:
 
 
 def oracle_system(ma: W.MeshArrays, k: int, method: int, prob: W.Problem, sigma=None,
-                  literal_rhs=False, split=True) -> OracleRun:
+                  literal_rhs=False, split=True, b0=1.0) -> OracleRun:
     m = O.make_mesh(ma.nodes, ma.elems, ma.dirichlet, ma.neumann)
     s, kap = O.set_parameter(method, k)
     if sigma is not None:
@@ -47,7 +47,7 @@ def oracle_system(ma: W.MeshArrays, k: int, method: int, prob: W.Problem, sigma=
     gD = prob.gD(np, xb[..., 0], xb[..., 1])
     gN = prob.gN(np, xb[..., 0], xb[..., 1], nrm[:, None, 0], nrm[:, None, 1])
     sysm = O.assemble(m, k, kap, s, 2 * s, prob.eps, prob.alpha, prob.b, f, gD, gN,
-                      literal_rhs=literal_rhs, split=split)
+                      literal_rhs=literal_rhs, split=split, b0=b0)
     return OracleRun(m, k, sysm, kap, s)
 
 

@@ -651,3 +651,37 @@ def test_newton_converges_quadratically_on_the_papers_example():
     v0, steps0, _ = O.newton(run0.mesh, run0.system, 2, 0.0, tol=1e-13)
     np.testing.assert_allclose(v0, oracle_direct(run0), rtol=0, atol=1e-10 * np.abs(v0).max())
     assert steps0 == 1
+
+
+# ----------------------------------------------------------------------------
+# superpenalisation b0 (Sec. 4 set_parameter; reading A-3)
+# ----------------------------------------------------------------------------
+
+
+def test_penalty_scales_as_edge_length_to_minus_b0():
+    """On an equilateral element with side L, the penalty part of D (D with
+    sigma minus D with sigma = 0) for exponent b0 is D_pen(b0) = D_pen(1) L^(1-b0):
+    the penalty is sigma eps / |e|^b0 on every edge."""
+    L = 0.37
+    v = [[0.1, 0.2], [0.1 + L, 0.2], [0.1 + L / 2, 0.2 + L * math.sqrt(3) / 2]]
+    prob = W.Problem("z", 0.6, 0.0, (0,) * 6, None, lambda xp, x, y: 0 * x)
+    ma = _one_element(v)
+    pen = {}
+    for b0 in (1.0, 2.0, 3.0):
+        d1 = oracle_system(ma, 2, 2, prob, sigma=5.0, b0=b0).system.D_diag[0]
+        d0 = oracle_system(ma, 2, 2, prob, sigma=0.0, b0=b0).system.D_diag[0]
+        pen[b0] = d1 - d0
+    for b0 in (2.0, 3.0):
+        np.testing.assert_allclose(pen[b0], pen[1.0] * L ** (1 - b0), rtol=1e-12, atol=1e-14 * np.abs(pen[b0]).max())
+
+
+@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("method", [1, 2, 3])
+def test_superpenalisation_keeps_polynomial_reproduction(k, method):
+    """The penalty terms vanish on continuous data, so with b0 = 3 every method
+    still reproduces P_k solutions (consistency)."""
+    prob = _poly_problem(k)
+    ma = W.perturbed_mesh(4, seed=7, neumann_sides=prob.neumann_sides)
+    run = oracle_system(ma, k, method, prob, b0=3.0)
+    err, _ = oracle_l2(run, oracle_direct(run), prob)
+    assert err < 1e-10
