@@ -98,7 +98,9 @@ typedef struct {
                                   paper's rule: 3k(k+1) for SIPG/IIPG, 1 for NIPG */
     double  sigma_bdry_factor; /* boundary-edge penalty = factor * sigma_int
                                   (paper: 2); <= 0 selects 2 */
-    double  b0;                /* superpenalisation exponent of h_e; only 1 */
+    double  b0;                /* superpenalisation exponent (Sec. 4 set_parameter):
+                                  the penalty terms carry sigma eps / |e|^b0;
+                                  1 (the paper's default) .. 8 */
     int32_t store;             /* DG_STORE_* mask of block copies to keep */
     int32_t gmres_m;           /* GMRES restart length, 1..64 (default 50) */
     double  tol;               /* relative residual target ||F-Ax||/||F|| */

@@ -34,6 +34,7 @@ struct AsmArgs {
     TabLayout L;
     int ne;
     double eps, alpha, kappa, sig_int, sig_bdry;
+    double b0;        // superpenalisation: the penalty terms carry sigma eps / |e|^b0
     double b[6];
     double* A64;
     float* A32;
@@ -140,7 +141,9 @@ __global__ void __launch_bounds__(256) k_asm_factors(const AsmArgs a, double* __
                 const double tx = j00 * dV[f][0] + j01 * dV[f][1];
                 const double ty = j10 * dV[f][0] + j11 * dV[f][1];
                 const double len = sqrt(tx * tx + ty * ty);
-                const double nx = ty / len, ny = -tx / len;   // h_e = |e|, b0 = 1
+                const double nx = ty / len, ny = -tx / len;
+                // penalty sigma eps / h_e^b0 with h_e = |e|, integrated over |e|
+                const double pfac = a.b0 == 1.0 ? 1.0 : pow(len, 1.0 - a.b0);
                 const double nu_r = i00 * nx + i01 * ny, nu_s = i10 * nx + i11 * ny;
                 const double fac1 = type == 0 ? -0.5 : (type == 1 ? -1.0 : 0.0);
                 const double fac2 = type == 0 ? 0.5 : (type == 1 ? 1.0 : 0.0);
@@ -150,7 +153,7 @@ __global__ void __launch_bounds__(256) k_asm_factors(const AsmArgs a, double* __
                 cf[1 * sne] = fac1 * eps * len * nu_s;
                 cf[2 * sne] = fac2 * a.kappa * eps * len * nu_r;
                 cf[3 * sne] = fac2 * a.kappa * eps * len * nu_s;
-                cf[4 * sne] = sig * eps;
+                cf[4 * sne] = sig * eps * pfac;
                 double lnr = 0.0, lns = 0.0;
                 if (type == 0) {
                     const double li00 = gload(a.geo, G_I00, ne, Ln), li01 = gload(a.geo, G_I01, ne, Ln);
@@ -163,7 +166,7 @@ __global__ void __launch_bounds__(256) k_asm_factors(const AsmArgs a, double* __
                 cf[6 * sne] = -0.5 * in * eps * len * lns;
                 cf[7 * sne] = -0.5 * in * a.kappa * eps * len * nu_r;
                 cf[8 * sne] = -0.5 * in * a.kappa * eps * len * nu_s;
-                cf[9 * sne] = -in * sig_int * eps;
+                cf[9 * sne] = -in * sig_int * eps * pfac;
                 cf[10 * sne] = in;
 #pragma unroll
                 for (int q = 0; q < NQ; ++q) {
@@ -329,7 +332,7 @@ __global__ void __launch_bounds__(256) k_rhs(const AsmArgs a) {
         const double ty = j10 * dV[f][0] + j11 * dV[f][1];
         const double len = sqrt(tx * tx + ty * ty);
         const double nx = ty / len, ny = -tx / len;
-        const double he = len;
+        const double he = a.b0 == 1.0 ? len : pow(len, a.b0);   // h_e^b0, h_e = |e|
         for (int q = 0; q < NQ; ++q) {
             const double w = sm[L.face_w + q] * len;
             const int o = (f * NQ + q) * NB + i;
@@ -367,6 +370,7 @@ dg_status dg_launch_assemble(dg_handle* h, const dg_coeffs* c, double kappa, dou
     a.eps = c->eps;
     a.alpha = c->alpha;
     a.kappa = kappa;
+    a.b0 = h->p.b0;
     a.sig_int = sig_int;
     a.sig_bdry = sig_bdry;
     for (int t = 0; t < 6; ++t) a.b[t] = c->b[t];

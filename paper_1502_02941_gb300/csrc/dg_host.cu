@@ -158,7 +158,7 @@ extern "C" dg_status dg_set_params(dg_handle* h, const dg_params* p) {
     if (!h || !p) return DG_ERR_INVALID_ARG;
     if (p->method < DG_NIPG || p->method > DG_IIPG) return dg_fail(h, DG_ERR_INVALID_ARG, "method must be 1..3");
     if (p->degree < 1 || p->degree > DG_MAXK) return dg_fail(h, DG_ERR_INVALID_ARG, "degree must be 1..3");
-    if (p->b0 != 1.0) return dg_fail(h, DG_ERR_INVALID_ARG, "only b0 = 1 is supported");
+    if (!(p->b0 >= 1.0 && p->b0 <= 8.0)) return dg_fail(h, DG_ERR_INVALID_ARG, "b0 must be in [1, 8]");
     if ((p->store & 7) == 0 || (p->store & ~7)) return dg_fail(h, DG_ERR_INVALID_ARG, "store mask");
     if (p->gmres_m < 1 || p->gmres_m > DG_MAXM) return dg_fail(h, DG_ERR_INVALID_ARG, "gmres_m must be 1..64");
     if (!(p->tol > 0.0) || p->max_it < 1) return dg_fail(h, DG_ERR_INVALID_ARG, "tol/max_it");

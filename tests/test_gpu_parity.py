@@ -18,7 +18,7 @@ from paper_1502_02941_gb300 import problem
 from paper_1502_02941_gb300 import workloads as W
 from gpu_helpers import (basis_change, gpu_setup, oracle_blocks, oracle_run, rel_residual_oracle, to_gpu_basis,
                          x_to_oracle)
-from helpers import oracle_direct
+from helpers import oracle_direct, oracle_system
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -151,6 +151,27 @@ def test_assembly_parity(k, method):
     _rel_close(_np(Ag), Ao_g, 1e-11)
     Fo_g = np.einsum("kmi,km->ki", T, run.system.F.reshape(ma.ne, -1)).reshape(-1)
     _rel_close(Fg, Fo_g, 1e-11)
+    h.close()
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+@pytest.mark.parametrize("method", [1, 2])
+def test_superpenalised_assembly_parity(k, method):
+    """Superpenalisation b0 = 2.5 (penalty sigma eps / |e|^b0): blocks and F
+    equal the oracle's, and b0 outside [1, 8] is refused."""
+    prob = _bumpy_problem()
+    ma = W.perturbed_mesh(5, seed=11, neumann_sides=prob.neumann_sides)
+    h = gpu_setup(ma, k, method, prob, b0=2.5)
+    Ag, _ = h.blocks()
+    Fg = _np(h.rhs())
+    run = oracle_system(ma, k, method, prob, b0=2.5)
+    T = basis_change(run, ma, k)
+    Ao, nbr = oracle_blocks(run, ma)
+    _rel_close(_np(Ag), to_gpu_basis(T, Ao, nbr), 1e-11)
+    _rel_close(Fg, np.einsum("kmi,km->ki", T, run.system.F.reshape(ma.ne, -1)).reshape(-1), 1e-11)
+    with pytest.raises(D.DGError) as e:
+        h.set_params(b0=0.5)
+    assert e.value.status == D.DG_ERR_INVALID_ARG
     h.close()
 
 
