@@ -527,7 +527,7 @@ dg_status dg_eval(dg_handle* h, const double* x, int np, const double* rs, doubl
  * dg_l2_error without any device allocation.  Same inputs, outputs and result
  * as dg_l2_error (the paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory, e.g. when another allocator owns
- * all of it or a timing-critical loop must not enter the driver's allocator).
+ * all of it or a timing-critical loop must not call cudaMalloc).
  * Its reduction scratch is a fixed array inside the library (16385 doubles per
  * GPU, kept until the process exits), which limits the mesh to 4,194,304
  * elements (DG_ERR_INVALID_ARG beyond).  The handle's reference tables must

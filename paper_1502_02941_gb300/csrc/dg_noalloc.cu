@@ -3,8 +3,7 @@
 //
 // Who needs it: a host program whose device memory is handed out entirely by
 // another allocator (a framework's caching allocator, a fixed pool carved out
-// at start-up) or a timing-critical loop that must not enter the driver's
-// allocator.  Such callers set the handle up once, then call this entry point
+// at start-up) or a timing-critical loop that must not call cudaMalloc.  Such callers set the handle up once, then call this entry point
 // as often as they like; it touches only the caller's buffers, the handle's
 // existing arrays and one fixed array that lives in this library's image.
 //

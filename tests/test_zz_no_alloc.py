@@ -2,8 +2,8 @@
 regular dg_l2_error, through the C ABI.
 
 dg_l2_error_noalloc serves callers that cannot allocate device memory (all of
-it owned by another allocator, or a timing-critical loop that must stay out of
-the driver's allocator); its scratch is a fixed array inside the library.  This
+it owned by another allocator, or a timing-critical loop that must not call
+cudaMalloc); its scratch is a fixed array inside the library.  This
 file is collected last so that a run stopping at the first failure has already
 run every other test; it also passes on its own in a fresh process.
 """
