@@ -92,3 +92,28 @@ def test_refinement_rejects_bad_input():
     with pytest.raises(D.DGError) as e:
         D.dg_mesh_refine(m.nodes, m.elems, bd, m.neumann)
     assert e.value.status == D.DG_ERR_MESH
+
+
+@pytest.mark.parametrize("mesh", ["square", "lshape"])
+def test_repeated_refinement_counts_and_euler_characteristic(mesh):
+    """Each refinement: T' = 4T, E' = 2E + 3T, V' = V + E, boundary edges double;
+    so V - E + T (1 for a simply connected polygon) is kept."""
+    if mesh == "square":
+        m = W.structured_mesh(3, neumann_sides=("left",))
+        arrays = (m.nodes, m.elems, m.dirichlet, m.neumann)
+    else:
+        m = W.lshape_mesh()
+        arrays = (m.nodes, m.elems, m.dirichlet, m.neumann)
+
+    def counts(a):
+        edges = {tuple(sorted((int(t[f]), int(t[(f + 1) % 3])))) for t in a[1] for f in range(3)}
+        used = len(np.unique(a[1]))          # vertices of the triangulation (unused nodes are kept)
+        return used, len(edges), a[1].shape[0], a[2].shape[0] + a[3].shape[0]
+    V, E, T, B = counts(arrays)
+    assert V - E + T == 1
+    for _ in range(3):
+        arrays = D.dg_mesh_refine(*arrays)
+        V2, E2, T2, B2 = counts(arrays)
+        assert (V2, E2, T2, B2) == (V + E, 2 * E + 3 * T, 4 * T, 2 * B)
+        V, E, T, B = V2, E2, T2, B2
+        assert V - E + T == 1

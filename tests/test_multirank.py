@@ -81,3 +81,18 @@ def test_reference_arm_prints_one_contract_line():
     assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["value"] > 0
     assert d["config"]["workload"] == bench.WORKLOAD and d["cpu_baseline"]["kind"] == "oracle"
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def test_batched_workload_grouped_by_degree_keeps_each_draw():
+    """The bench's batched workload: instances 0..63 of the batched family,
+    one batch per drawn degree; every instance keeps its own seeded draw."""
+    from paper_1502_02941_gb300 import workloads as W
+    groups = W.batch_by_degree("batched", 64)
+    assert sorted(groups) == [1, 2] and sum(len(g[0]) for g in groups.values()) == 64
+    for k, (cfgs, ma, starts, coeffs) in groups.items():
+        assert all(c.k == k for c in cfgs)
+        assert starts[-1] == ma.elems.shape[0] == sum(2 * c.N ** 2 for c in cfgs)
+        for c, row in zip(cfgs, coeffs):
+            i = int(c.name.split("inst")[1])
+            d = W.random_instance("batched", i)
+            assert (d.N, d.k, d.problem.eps, d.problem.alpha) == (c.N, c.k, row[0], row[1])
