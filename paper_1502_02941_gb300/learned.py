@@ -9,6 +9,8 @@ patch correction.
 """
 from __future__ import annotations
 
+import json
+import struct
 import time
 
 import numpy as np
@@ -84,3 +86,52 @@ def evaluate(h: D.DG, max_it=20000, tol=1e-10):
                      "converged": int((st == 0).sum())}
     h.set_params(precond=D.DG_PRECOND_BLOCK_JACOBI)
     return out
+
+
+# ---------------------------------------------------------------------------
+# checkpoints of the trained network
+# ---------------------------------------------------------------------------
+# File layout (little-endian): 8-byte magic b"DGMLPW1\0", uint32 header length
+# L, L bytes of UTF-8 JSON {"degree", "n_params", "dtype": "float32", "seed",
+# "config"}, then n_params float32 values (the flat vector of
+# dg_mlp_set_weights / dg_mlp_get_weights).
+_MAGIC = b"DGMLPW1\0"
+
+
+def save_weights(path, theta, degree: int, seed: int = 0, config: dict | None = None) -> None:
+    """Write the network's flat parameter vector with a header (degree, size,
+    training seed and settings) to a file path or a binary file object."""
+    theta = np.ascontiguousarray(theta, dtype="<f4").reshape(-1)
+    n = D.dg_mlp_num_params(degree)
+    if theta.size != n:
+        raise ValueError(f"{theta.size} parameters given, degree {degree} has {n}")
+    head = json.dumps({"degree": int(degree), "n_params": int(n), "dtype": "float32", "seed": int(seed),
+                       "config": config or {}}, sort_keys=True).encode()
+    blob = _MAGIC + struct.pack("<I", len(head)) + head + theta.tobytes()
+    if hasattr(path, "write"):
+        path.write(blob)
+    else:
+        with open(path, "wb") as fh:
+            fh.write(blob)
+
+
+def load_weights(path):
+    """Read a checkpoint written by save_weights (a file path or a binary file
+    object); returns (theta float32, header).  Raises ValueError for a foreign
+    or truncated file or a size that does not match the degree."""
+    if hasattr(path, "read"):
+        data = path.read()
+    else:
+        with open(path, "rb") as fh:
+            data = fh.read()
+    if len(data) < 12 or data[:8] != _MAGIC:
+        raise ValueError("not a network checkpoint")
+    (hl,) = struct.unpack("<I", data[8:12])
+    if len(data) < 12 + hl:
+        raise ValueError("truncated header")
+    head = json.loads(data[12:12 + hl].decode())
+    n = D.dg_mlp_num_params(head["degree"])
+    if head.get("dtype") != "float32" or head.get("n_params") != n or len(data) != 12 + hl + 4 * n:
+        raise ValueError("checkpoint size does not match its degree")
+    theta = np.frombuffer(data, dtype="<f4", count=n, offset=12 + hl).astype(np.float32)
+    return theta, head

@@ -133,3 +133,25 @@ def test_binding_refuses_host_tensors_for_device_arguments():
         D._ptr(np.zeros((4, 2))[:, 0])          # not contiguous
     a = np.zeros(3)
     assert D._ptr(a) == a.ctypes.data and D._ptr(None) is None and D._ptr(7) == 7
+
+
+def test_network_checkpoint_round_trip():
+    """Trained weights are saved with a header (degree, size, seed, settings)
+    and read back bit for bit; foreign, truncated or mismatched files are
+    refused (in memory: the format is the same for files)."""
+    import io
+    from paper_1502_02941_gb300 import learned as L
+    n = D.dg_mlp_num_params(2)
+    theta = np.random.default_rng(0).standard_normal(n).astype(np.float32)
+    buf = io.BytesIO()
+    L.save_weights(buf, theta, 2, seed=7, config={"steps": 4000})
+    raw = buf.getvalue()
+    back, head = L.load_weights(io.BytesIO(raw))
+    np.testing.assert_array_equal(back, theta)
+    assert head["degree"] == 2 and head["seed"] == 7 and head["config"] == {"steps": 4000}
+    assert raw[:8] == b"DGMLPW1\0" and len(raw) == 12 + int.from_bytes(raw[8:12], "little") + 4 * n
+    with pytest.raises(ValueError):
+        L.save_weights(io.BytesIO(), theta[:-1], 2)
+    for bad in (b"X" + raw[1:], raw[:-4]):
+        with pytest.raises(ValueError):
+            L.load_weights(io.BytesIO(bad))
