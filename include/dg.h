@@ -46,7 +46,7 @@ typedef int dg_status;
 #define DG_ERR_INVALID_ARG     1  /* a pointer, size or enum is out of range */
 #define DG_ERR_CUDA            2  /* a CUDA runtime call failed */
 #define DG_NOT_CONVERGED       3  /* solver hit its iteration cap; info still filled */
-#define DG_ERR_TIMEOUT         4  /* a bounded device-side wait expired (reserved: no kernel of this library waits on the device) */
+#define DG_ERR_TIMEOUT         4  /* a bounded device-side wait expired (reserved: no kernel of this library spins on a flag) */
 #define DG_ERR_NONFINITE       5  /* NaN/Inf met in data or in a residual */
 #define DG_ERR_SINGULAR_BLOCK  6  /* a diagonal block could not be inverted */
 #define DG_ERR_MESH            7  /* invalid mesh: clockwise element, edge shared by
