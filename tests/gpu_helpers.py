@@ -62,14 +62,13 @@ def oracle_blocks(run, ma: W.MeshArrays):
 
 def to_gpu_basis(T, blocks, nbr):
     """T_K^T B(K, L) T_L for every stored block."""
-    ne = blocks.shape[0]
     out = np.zeros_like(blocks)
-    out[:, 0] = np.einsum("kmi,kmn,knj->kij", T, blocks[:, 0], T)
+    Tt = np.transpose(T, (0, 2, 1))
+    out[:, 0] = Tt @ blocks[:, 0] @ T
     for f in range(3):
         L = nbr[:, f]
         ok = L >= 0
-        TL = T[np.where(ok, L, 0)]
-        out[ok, 1 + f] = np.einsum("kmi,kmn,knj->kij", T[ok], blocks[ok, 1 + f], TL[ok])
+        out[ok, 1 + f] = Tt[ok] @ blocks[ok, 1 + f] @ T[L[ok]]
     return out
 
 
