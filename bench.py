@@ -269,37 +269,99 @@ def learned_section(local, stream, n_inst, steps):
 # ---------------------------------------------------------------------------
 # CPU baseline (the oracle), bounded sample
 # ---------------------------------------------------------------------------
-def oracle_sample(gpu_its, iters=50):
+ORACLE_ITERS = 50   # one full GMRES(50) restart cycle per method: the MGS cost averaged over j = 0..49
+
+
+def cpu_info():
+    """Host cores visible to this process and the CPU model name."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    if not model:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.strip().lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    import platform
+    return {"nproc": cores, "cpu_model": model or platform.processor() or platform.machine()}
+
+
+def oracle_sample(gpu_its, iters=ORACLE_ITERS, omp=False):
     """Time the oracle's assembly + block inverses + `iters` GMRES iterations of
     each method and scale the per-iteration time to `gpu_its` (iterations the
-    same algorithm needs) -> estimated oracle solves/s."""
+    same algorithm needs) -> estimated oracle solves/s.  omp: the oracle's
+    all-cores timing build (OpenMP loops), else the serial build.  Returns
+    (solves/s, per-method detail, threads used)."""
     import numpy as np
 
     import oracle as O
     from paper_1502_02941_gb300 import workloads as W
-    total = 0.0
-    detail = []
-    for method, its in zip(METHODS, gpu_its):
-        cfg = W.boundary_layer_p2(method=method, N=N_MESH)
-        ma = W.structured_mesh(cfg.N)
-        p = cfg.problem
-        t0 = time.perf_counter()
-        m = O.make_mesh(ma.nodes, ma.elems, ma.dirichlet, ma.neumann)
-        s, kap = O.set_parameter(cfg.method, cfg.k)
-        xq = O.quad_points(m, cfg.k, O.VOLUME)
-        xb = O.quad_points(m, cfg.k, O.BOUNDARY)
-        sysm = O.assemble(m, cfg.k, kap, s, 2 * s, p.eps, p.alpha, p.b, p.f(np, xq[..., 0], xq[..., 1]),
-                          p.gD(np, xb[..., 0], xb[..., 1]), None, split=False)
-        t1 = time.perf_counter()
-        _, done, _, _ = O.gmres(m, sysm.A_diag, sysm.A_off, sysm.F, m=50, tol=1e-10, max_it=iters)
-        t2 = time.perf_counter()
-        per_it = (t2 - t1) / max(done, 1)
-        est = (t1 - t0) + per_it * its
-        total += est
-        detail.append({"method": "NIPG" if method == 1 else "SIPG", "setup_s": round(t1 - t0, 3),
-                       "per_iteration_ms": round(per_it * 1e3, 3), "iterations_scaled_to": its,
-                       "est_solve_s": round(est, 3)})
-    return len(METHODS) / total, detail
+    O.set_openmp(omp)
+    try:
+        threads = O.num_threads()
+        total = 0.0
+        detail = []
+        for method, its in zip(METHODS, gpu_its):
+            cfg = W.boundary_layer_p2(method=method, N=N_MESH)
+            ma = W.structured_mesh(cfg.N)
+            p = cfg.problem
+            t0 = time.perf_counter()
+            m = O.make_mesh(ma.nodes, ma.elems, ma.dirichlet, ma.neumann)
+            s, kap = O.set_parameter(cfg.method, cfg.k)
+            xq = O.quad_points(m, cfg.k, O.VOLUME)
+            xb = O.quad_points(m, cfg.k, O.BOUNDARY)
+            sysm = O.assemble(m, cfg.k, kap, s, 2 * s, p.eps, p.alpha, p.b, p.f(np, xq[..., 0], xq[..., 1]),
+                              p.gD(np, xb[..., 0], xb[..., 1]), None, split=False)
+            t1 = time.perf_counter()
+            _, done, _, _ = O.gmres(m, sysm.A_diag, sysm.A_off, sysm.F, m=50, tol=1e-10, max_it=iters)
+            t2 = time.perf_counter()
+            per_it = (t2 - t1) / max(done, 1)
+            est = (t1 - t0) + per_it * its
+            total += est
+            detail.append({"method": "NIPG" if method == 1 else "SIPG", "setup_s": round(t1 - t0, 3),
+                           "iterations_timed": done, "per_iteration_ms": round(per_it * 1e3, 3),
+                           "iterations_scaled_to": its, "est_solve_s": round(est, 3)})
+    finally:
+        O.set_openmp(False)
+    return len(METHODS) / total, detail, threads
+
+
+def oracle_all_cores(scale_its):
+    """The same sample on the oracle's all-cores build; None if that build is
+    unavailable on this host."""
+    import oracle as O
+    try:
+        O.build(openmp=True)
+    except Exception as e:   # no OpenMP runtime for this compiler
+        return {"unavailable": f"oracle OpenMP build failed: {type(e).__name__}"}
+    v, detail, threads = oracle_sample(scale_its, omp=True)
+    return {"value": v, "unit": "solves/s", "cores": threads, "kind": "oracle (OpenMP loops, timing build)",
+            "sample": f"per method: oracle assembly (serial) + block inverses + {ORACLE_ITERS} GMRES(50) "
+                      f"iterations on {threads} threads; per-iteration time scaled to {scale_its} iterations",
+            "detail": detail}
+
+
+def workload_config(world):
+    """The `config` both arms report (sizes of the step's workload; no measured values)."""
+    ne = 2 * N_MESH * N_MESH
+    nb = (DEGREE + 1) * (DEGREE + 2) // 2
+    return {"workload": WORKLOAD, "N": N_MESH, "k": DEGREE, "ne": ne, "dofs": ne * nb, "methods": ["NIPG", "SIPG"],
+            "gmres_m": 50, "tol": 1e-10,
+            "l2_policy": "working set > L2 (blocks 151 MB + Krylov basis 321 MB per solve)",
+            "parallelism": f"replicas x{world}"}
 
 
 def oracle_iteration_counts():
@@ -320,23 +382,26 @@ def reference_arm(args, rank):
     if its is None:
         its, src = [2000, 2000], "assumed 2000 iterations per solve (no oracle record)"
     for _ in range(args.warmup):
-        oracle_sample(its, iters=10)
+        oracle_sample(its, iters=1)          # untimed: loads the library and pages the inputs in
     vals = []
     t0 = time.perf_counter()
-    details = None
+    details, threads = None, 1
     for _ in range(args.steps):
-        v, details = oracle_sample(its, iters=20)
+        v, details, threads = oracle_sample(its)
         vals.append(v)
     wall = time.perf_counter() - t0
     value = statistics.mean(vals)
+    host = cpu_info()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD},
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                             "sample": "per step and method: oracle assembly + block inverses + 20 GMRES "
-                                       f"iterations, per-iteration time scaled to {its} iterations ({src})",
-                             "detail": details},
+            "data": "synthetic", "config": workload_config(world),
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": threads, "kind": "oracle",
+                             "sample": f"per step and method: oracle assembly + block inverses + {ORACLE_ITERS} "
+                                       f"GMRES(50) iterations (one restart cycle), per-iteration time scaled to "
+                                       f"{its} iterations ({src})",
+                             "host": host, "detail": details},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -610,12 +675,9 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "N": N_MESH, "k": DEGREE, "ne": info.ne, "dofs": dofs,
-                       "methods": ["NIPG", "SIPG"], "gmres_m": 50, "tol": 1e-10,
-                       "iterations": {"NIPG": its[0], "SIPG": its[1]},
-                       "relres": {"NIPG": last[1][1], "SIPG": last[2][1]},
-                       "l2_policy": "working set > L2 (blocks 151 MB + Krylov basis 321 MB per solve)",
-                       "parallelism": f"replicas x{world}"},
+            "config": workload_config(world),
+            "solve": {"iterations": {"NIPG": its[0], "SIPG": its[1]},
+                      "relres": {"NIPG": last[1][1], "SIPG": last[2][1]}},
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
             "mixed": mixed, "assembly": assembly, "kernels": kernels, "hbm_peak_GBps": peak}
@@ -626,11 +688,13 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ref_its, _ = oracle_iteration_counts()
         scale_its = ref_its if ref_its else its
-        cpu_val, detail = oracle_sample(scale_its, iters=50)
-        line["cpu_baseline"] = {"value": cpu_val, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                                "sample": "per method: oracle assembly + block inverses + 50 GMRES(50) iterations; "
-                                          f"per-iteration time scaled to {scale_its} iterations",
-                                "detail": detail}
+        cpu_val, detail, threads = oracle_sample(scale_its)
+        line["cpu_baseline"] = {"value": cpu_val, "unit": "solves/s", "cores": threads, "kind": "oracle",
+                                "sample": f"per method: oracle assembly + block inverses + {ORACLE_ITERS} GMRES(50) "
+                                          f"iterations (one restart cycle); per-iteration time scaled to "
+                                          f"{scale_its} iterations",
+                                "host": cpu_info(), "detail": detail,
+                                "all_cores": oracle_all_cores(scale_its)}
     if rank == 0:
         print(json.dumps(line))
     h.close()

@@ -52,6 +52,30 @@
 #include <stdlib.h>
 #include <string.h>
 
+/*
+ * Timing build only: compiled with -DORC_OPENMP -fopenmp (liboracle_omp.so)
+ * the element, edge and vector loops of the apply, the block-Jacobi apply
+ * and GMRES run on all host cores (edge contributions added atomically, dot
+ * products as OpenMP reductions, so the last bits of the rounding differ).
+ * The build the tests use has no such pragmas: it is the plain serial code.
+ */
+#ifdef ORC_OPENMP
+#include <omp.h>
+#define ORC_PAR(x) _Pragma(x)
+#else
+#define ORC_PAR(x)
+#endif
+
+/* Threads the loops above run on (1 in the serial build). */
+int orc_num_threads(void)
+{
+#ifdef ORC_OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
 #define ORC_MAXK 4
 #define ORC_MAXNB 15   /* (k+1)(k+2)/2 for k = 4 */
 #define ORC_MAXQ 16    /* Gauss points per direction */
@@ -598,12 +622,14 @@ void orc_assemble(int k, const double* nodes, int ne, const int* elems,
 void orc_apply(int nb, int ne, int ned, const int* edges,
                const double* diag, const double* off, const double* x, double* y)
 {
+    ORC_PAR("omp parallel for schedule(static)")
     for (int K = 0; K < ne; ++K)
         for (int i = 0; i < nb; ++i) {
             double s = 0.0;
             for (int j = 0; j < nb; ++j) s += BLK(diag, K, nb)[i * nb + j] * x[K * nb + j];
             y[K * nb + i] = s;
         }
+    ORC_PAR("omp parallel for schedule(static)")
     for (int e = 0; e < ned; ++e) {
         int Ki = edges[5 * e + 2], Kj = edges[5 * e + 3];
         if (Kj < 0) continue;
@@ -613,7 +639,9 @@ void orc_apply(int nb, int ne, int ned, const int* edges,
                 s0 += BLK(off, 2 * e + 0, nb)[i * nb + j] * x[Kj * nb + j];
                 s1 += BLK(off, 2 * e + 1, nb)[i * nb + j] * x[Ki * nb + j];
             }
+            ORC_PAR("omp atomic")
             y[Ki * nb + i] += s0;
+            ORC_PAR("omp atomic")
             y[Kj * nb + i] += s1;
         }
     }
@@ -693,11 +721,15 @@ int orc_block_jacobi(int nb, int ne, const double* diag, double* inv)
 /* ------------------------------------------------------------------------ */
 static double dotv(size_t n, const double* a, const double* b)
 {
-    double s = 0.0; for (size_t i = 0; i < n; ++i) s += a[i] * b[i]; return s;
+    double s = 0.0;
+    ORC_PAR("omp parallel for reduction(+:s) schedule(static)")
+    for (size_t i = 0; i < n; ++i) s += a[i] * b[i];
+    return s;
 }
 
 static void bj_apply(int nb, int ne, const double* inv, const double* r, double* z)
 {
+    ORC_PAR("omp parallel for schedule(static)")
     for (int K = 0; K < ne; ++K)
         for (int i = 0; i < nb; ++i) {
             double s = 0.0;
@@ -734,11 +766,13 @@ int orc_gmres(int nb, int ne, int ned, const int* edges, const double* diag, con
     for (;;) {
         /* r = b - A x */
         orc_apply(nb, ne, ned, edges, diag, off, x, w);
+        ORC_PAR("omp parallel for schedule(static)")
         for (size_t i = 0; i < n; ++i) w[i] = b[i] - w[i];
         double beta = sqrt(dotv(n, w, w));
         relres = beta / bnorm;
         if (relres <= tol) { converged = 1; break; }
         if (its >= max_it) break;
+        ORC_PAR("omp parallel for schedule(static)")
         for (size_t i = 0; i < n; ++i) V[i] = w[i] / beta;
         memset(gvec, 0, sizeof(double) * (m + 1));
         gvec[0] = beta;
@@ -751,11 +785,15 @@ int orc_gmres(int nb, int ne, int ned, const int* edges, const double* diag, con
             for (int i = 0; i <= j; ++i) {                     /* modified Gram-Schmidt */
                 double h = dotv(n, w, V + (size_t)i * n);
                 H[i * m + j] = h;
+                ORC_PAR("omp parallel for schedule(static)")
                 for (size_t l = 0; l < n; ++l) w[l] -= h * V[(size_t)i * n + l];
             }
             double hn = sqrt(dotv(n, w, w));
             H[(j + 1) * m + j] = hn;
-            if (hn != 0.0) for (size_t l = 0; l < n; ++l) V[(size_t)(j + 1) * n + l] = w[l] / hn;
+            if (hn != 0.0) {
+                ORC_PAR("omp parallel for schedule(static)")
+                for (size_t l = 0; l < n; ++l) V[(size_t)(j + 1) * n + l] = w[l] / hn;
+            }
             for (int i = 0; i < j; ++i) {                      /* previous rotations */
                 double t1 = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
                 double t2 = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
@@ -775,9 +813,12 @@ int orc_gmres(int nb, int ne, int ned, const int* edges, const double* diag, con
             yv[i] = s / H[i * m + i];
         }
         memset(w, 0, sizeof(double) * n);
-        for (int i = 0; i < j; ++i)
+        for (int i = 0; i < j; ++i) {
+            ORC_PAR("omp parallel for schedule(static)")
             for (size_t l = 0; l < n; ++l) w[l] += yv[i] * V[(size_t)i * n + l];
+        }
         if (inv) bj_apply(nb, ne, inv, w, z); else memcpy(z, w, sizeof(double) * n);
+        ORC_PAR("omp parallel for schedule(static)")
         for (size_t l = 0; l < n; ++l) x[l] += z[l];
     }
     info[0] = its; info[1] = relres;

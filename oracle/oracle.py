@@ -22,27 +22,45 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "dg_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
-_lib = None
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
+_libs = {}
+_use_omp = False
 
 NIPG, SIPG, IIPG = 1, 2, 3   # the paper's `method` numbering (Sec. 2.2)
 
 
-def build(force: bool = False) -> str:
-    """Compile dg_oracle.c into liboracle.so with gcc (portable flags only)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared",
-               "-o", _LIB + ".tmp", _SRC, "-lm"]
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile dg_oracle.c into liboracle.so with gcc (portable flags only).
+    openmp=True builds liboracle_omp.so, the same source with its OpenMP loops
+    switched on, used only to time the oracle on all host cores."""
+    lib = _LIB_OMP if openmp else _LIB
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
+        extra = ["-DORC_OPENMP", "-fopenmp"] if openmp else []
+        cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared", *extra,
+               "-o", lib + ".tmp", _SRC, "-lm"]
         subprocess.check_call(cmd)
-        os.replace(_LIB + ".tmp", _LIB)
-    return _LIB
+        os.replace(lib + ".tmp", lib)
+    return lib
+
+
+def set_openmp(on: bool) -> None:
+    """Route later oracle calls to the all-cores timing build (True) or the
+    serial build (False, the default and what every test uses)."""
+    global _use_omp
+    _use_omp = bool(on)
+
+
+def num_threads() -> int:
+    """Host threads the current build's loops run on."""
+    return int(_load().orc_num_threads())
 
 
 def _load():
-    global _lib
-    if _lib is None:
-        build()
-        _lib = ctypes.CDLL(_LIB)
-    return _lib
+    key = "omp" if _use_omp else "serial"
+    if key not in _libs:
+        path = build(openmp=_use_omp)
+        _libs[key] = ctypes.CDLL(path)
+    return _libs[key]
 
 
 def _p(a, ctype):
