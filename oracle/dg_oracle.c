@@ -349,6 +349,8 @@ static void monomial_basis(const elem_geo* g, int k, double x, double y,
  * which = 1: boundary-edge points, [n boundary edges, in edge order][k+2][2],
  *            each edge traversed from va to vb (counter-clockwise for Ki)
  * which = 2: L2-error points, [ne][(k+4)^2][2]
+ * which = 3: points of every edge, [ned][k+2][2], in edge order, each edge
+ *            traversed from va to vb (where a variable eps is evaluated)
  */
 void orc_quad_points(int which, int k, const double* nodes, int ne, const int* elems,
                      int ned, const int* edges, double* out)
@@ -369,7 +371,7 @@ void orc_quad_points(int which, int k, const double* nodes, int ne, const int* e
         orc_gauss_legendre01(n, t, tw);
         size_t ib = 0;
         for (int e = 0; e < ned; ++e) {
-            if (edges[5 * e + 3] >= 0) continue;
+            if (which == 1 && edges[5 * e + 3] >= 0) continue;
             const double* a = nodes + 2 * edges[5 * e];
             const double* b = nodes + 2 * edges[5 * e + 1];
             for (int q = 0; q < n; ++q) {
@@ -412,12 +414,19 @@ static void advection(const orc_coeffs* c, double x, double y, double* bx, doubl
  * (zeroed here); pass C_* or R_* equal to D_* to accumulate into one matrix.
  * f_q: [ne][(k+2)^2] at the volume points; gD_q, gN_q: [nbe][k+2] at the
  * boundary-edge points (orc_quad_points order).  F: [ne][nb].
+ * Diffusion: the constant eps, or, when eps_vol is given, the values of the
+ * paper's fdiff(x, y) (Sec. 2.2) at the quadrature points: eps_vol
+ * [ne][(k+2)^2] at the volume points (orc_quad_points 0) for the volume term,
+ * eps_edge [ned][k+2] at the edge points (orc_quad_points 3) for the face
+ * terms {eps grad u}, {eps grad v}, the penalty sigma eps / h_e and the RHS
+ * Dirichlet terms (reading A-4: eps taken pointwise at each quadrature point).
  */
 void orc_assemble(int k, const double* nodes, int ne, const int* elems,
                   int ned, const int* edges, const int* elem_edges,
                   double kappa, double sigma_int, double sigma_bdry,
                   double eps, double alpha, const double* b_affine, int literal_rhs, double b0,
                   const double* f_q, const double* gD_q, const double* gN_q,
+                  const double* eps_vol, const double* eps_edge,
                   double* D_diag, double* D_off, double* C_diag, double* C_off,
                   double* R_diag, double* R_off, double* F)
 {
@@ -450,10 +459,11 @@ void orc_assemble(int k, const double* nodes, int ne, const int* elems,
                 double bx, by; advection(&cf, x, y, &bx, &by);
                 monomial_basis(&g, k, x, y, phi, px, py);
                 double fval = f_q[(size_t)K * n * n + q];
+                double epsq = eps_vol ? eps_vol[(size_t)K * n * n + q] : cf.eps;
                 for (int i = 0; i < nb; ++i) {          /* test  v = phi_i */
                     for (int j = 0; j < nb; ++j) {      /* trial u = phi_j */
                         /* D: eps grad u . grad v */
-                        BLK(D_diag, K, nb)[i * nb + j] += wq * cf.eps * (px[j] * px[i] + py[j] * py[i]);
+                        BLK(D_diag, K, nb)[i * nb + j] += wq * epsq * (px[j] * px[i] + py[j] * py[i]);
                         /* C: (b . grad u) v */
                         BLK(C_diag, K, nb)[i * nb + j] += wq * (bx * px[j] + by * py[j]) * phi[i];
                         /* R: alpha u v */
@@ -490,6 +500,7 @@ void orc_assemble(int k, const double* nodes, int ne, const int* elems,
             for (int q = 0; q < nq; ++q) {
                 double x = a[0] + t[q] * dx, y = a[1] + t[q] * dy;
                 double wq = tw[q] * len;
+                double epsq = eps_vol ? eps_edge[(size_t)e * nq + q] : cf.eps;
                 double phi_i[ORC_MAXNB], pxi[ORC_MAXNB], pyi[ORC_MAXNB];
                 double phi_j[ORC_MAXNB], pxj[ORC_MAXNB], pyj[ORC_MAXNB];
                 monomial_basis(&gi, k, x, y, phi_i, pxi, pyi);
@@ -521,11 +532,11 @@ void orc_assemble(int k, const double* nodes, int ne, const int* elems,
                                 /* [v] (vector) and {eps grad v}, {eps grad u} */
                                 double jv_x = sgn_v * pv[i] * ne_x, jv_y = sgn_v * pv[i] * ne_y;
                                 double ju_x = sgn_u * pu[j] * ne_x, ju_y = sgn_u * pu[j] * ne_y;
-                                double agv_x = avgw * cf.eps * pvx[i], agv_y = avgw * cf.eps * pvy[i];
-                                double agu_x = avgw * cf.eps * pux[j], agu_y = avgw * cf.eps * puy[j];
+                                double agv_x = avgw * epsq * pvx[i], agv_y = avgw * epsq * pvy[i];
+                                double agu_x = avgw * epsq * pux[j], agu_y = avgw * epsq * puy[j];
                                 double val = -(agu_x * jv_x + agu_y * jv_y)
                                              + cf.kappa * (agv_x * ju_x + agv_y * ju_y)
-                                             + sigma * cf.eps / he * (ju_x * jv_x + ju_y * jv_y);
+                                             + sigma * epsq / he * (ju_x * jv_x + ju_y * jv_y);
                                 blk[i * nb + j] += wq * val;
                             }
                     }
@@ -535,8 +546,8 @@ void orc_assemble(int k, const double* nodes, int ne, const int* elems,
                     double g = gD_q[(size_t)bidx * nq + q];
                     double cons = cf.literal_rhs ? -1.0 : cf.kappa;
                     for (int i = 0; i < nb; ++i)
-                        F[E[2] * nb + i] += wq * g * (sigma * cf.eps / he * phi_i[i]
-                                          + cons * cf.eps * (pxi[i] * ne_x + pyi[i] * ne_y));
+                        F[E[2] * nb + i] += wq * g * (sigma * epsq / he * phi_i[i]
+                                          + cons * epsq * (pxi[i] * ne_x + pyi[i] * ne_y));
                 }
             }
         }

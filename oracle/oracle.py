@@ -172,18 +172,22 @@ def refine(nodes, elems, dirichlet, neumann):
     return nodes_out[:nv_new].copy(), elems_out, dir_out, neu_out
 
 
-VOLUME, BOUNDARY, ERROR = 0, 1, 2
+VOLUME, BOUNDARY, ERROR, EDGES = 0, 1, 2, 3
 
 
 def quad_points(mesh: Mesh, k: int, which: int) -> np.ndarray:
     """Physical quadrature points (reading A-8): VOLUME [ne,(k+2)^2,2],
     BOUNDARY [n_bedges,k+2,2] (boundary edges in edge-table order, each run
-    counter-clockwise for its element), ERROR [ne,(k+4)^2,2]."""
+    counter-clockwise for its element), ERROR [ne,(k+4)^2,2], EDGES
+    [ned,k+2,2] (every edge in edge-table order, run from its first to its
+    second node)."""
     lib = _load()
     if which == VOLUME:
         shape = (mesh.ne, (k + 2) ** 2, 2)
     elif which == BOUNDARY:
         shape = (mesh.n_bedges, k + 2, 2)
+    elif which == EDGES:
+        shape = (mesh.ned, k + 2, 2)
     else:
         shape = (mesh.ne, (k + 4) ** 2, 2)
     out = np.zeros(shape)
@@ -226,7 +230,8 @@ class System:
 
 def assemble(mesh: Mesh, k: int, kappa: float, sigma_int: float, sigma_bdry: float,
              eps: float, alpha: float, b_affine, f_q, gD_q, gN_q,
-             literal_rhs: bool = False, split: bool = True, b0: float = 1.0) -> System:
+             literal_rhs: bool = False, split: bool = True, b0: float = 1.0,
+             eps_vol=None, eps_edge=None) -> System:
     """The paper's global_system (Sec. 2.3): D, C, R and F of Eq. (system).
 
     b_affine = (c0..c5): b(x,y) = (c0 + c1 x + c2 y, c3 + c4 x + c5 y).
@@ -236,6 +241,9 @@ def assemble(mesh: Mesh, k: int, kappa: float, sigma_int: float, sigma_bdry: flo
     on Dirichlet edges and on the inflow part of every boundary edge, reading
     A-6; gN on Neumann edges).  With split=False only A = D+C+R is stored (in
     D_*; C_* and R_* alias it).
+    eps_vol / eps_edge: a variable diffusion coefficient (the paper's fdiff,
+    Sec. 2.2) given at quad_points(VOLUME) [ne][(k+2)^2] and at
+    quad_points(EDGES) [ned][k+2]; both or neither (then eps is the constant).
     """
     lib = _load()
     nb = nbasis(k)
@@ -245,6 +253,11 @@ def assemble(mesh: Mesh, k: int, kappa: float, sigma_int: float, sigma_bdry: flo
     nbe = mesh.n_bedges
     gD_q = np.ascontiguousarray(gD_q if gD_q is not None else np.zeros((nbe, k + 2)), dtype=np.float64).reshape(nbe, k + 2)
     gN_q = np.ascontiguousarray(gN_q if gN_q is not None else np.zeros((nbe, k + 2)), dtype=np.float64).reshape(nbe, k + 2)
+    if (eps_vol is None) != (eps_edge is None):
+        raise ValueError("eps_vol and eps_edge are given together")
+    if eps_vol is not None:
+        eps_vol = np.ascontiguousarray(eps_vol, dtype=np.float64).reshape(ne, (k + 2) ** 2)
+        eps_edge = np.ascontiguousarray(eps_edge, dtype=np.float64).reshape(ned, k + 2)
     Dd = np.zeros((ne, nb, nb))
     Do = np.zeros((ned, 2, nb, nb))
     if split:
@@ -256,7 +269,8 @@ def assemble(mesh: Mesh, k: int, kappa: float, sigma_int: float, sigma_bdry: flo
     lib.orc_assemble(k, _d(mesh.nodes), ne, _i(mesh.elems), ned, _i(mesh.edges), _i(mesh.elem_edges),
                      ctypes.c_double(kappa), ctypes.c_double(sigma_int), ctypes.c_double(sigma_bdry),
                      ctypes.c_double(eps), ctypes.c_double(alpha), _d(b), ctypes.c_int(int(literal_rhs)), ctypes.c_double(b0),
-                     _d(f_q), _d(gD_q), _d(gN_q), _d(Dd), _d(Do), _d(Cd), _d(Co), _d(Rd), _d(Ro), _d(F))
+                     _d(f_q), _d(gD_q), _d(gN_q), _d(eps_vol), _d(eps_edge),
+                     _d(Dd), _d(Do), _d(Cd), _d(Co), _d(Rd), _d(Ro), _d(F))
     if not split:
         z_d, z_o = np.zeros_like(Dd), np.zeros_like(Do)
         return System(k, Dd, Do, z_d, z_o, z_d, z_o, F.reshape(-1))

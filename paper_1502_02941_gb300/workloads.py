@@ -128,6 +128,15 @@ class Problem:
     neumann_sides: tuple = ()
     meta: dict = field(default_factory=dict)
     reaction: tuple = ()          # (p, c): r(u) = c u^p
+    # variable diffusion coefficient, the paper's fdiff(x, y) (Sec. 2.2):
+    # callable(xp, x, y) -> (eps, eps_x, eps_y); None = the constant eps
+    eps_fn: object = None
+
+    def eps_at(self, xp, x, y):
+        """The diffusion coefficient at points (the constant, or eps_fn)."""
+        if self.eps_fn is None:
+            return self.eps + 0.0 * x
+        return self.eps_fn(xp, x, y)[0]
 
     def bvec(self, xp, x, y):
         b = self.b
@@ -139,7 +148,11 @@ class Problem:
             return self.source(xp, x, y)
         u, ux, uy, lap = self.exact(xp, x, y)
         bx, by = self.bvec(xp, x, y)
-        f = self.alpha * u - self.eps * lap + bx * ux + by * uy
+        if self.eps_fn is None:
+            f = self.alpha * u - self.eps * lap + bx * ux + by * uy
+        else:   # -div(eps grad u) = -eps Lap u - grad eps . grad u
+            e, ex_, ey_ = self.eps_fn(xp, x, y)
+            f = self.alpha * u - e * lap - (ex_ * ux + ey_ * uy) + bx * ux + by * uy
         if self.reaction:
             p, c = self.reaction
             f = f + c * u ** p
@@ -161,7 +174,7 @@ class Problem:
         if self.exact is None:
             return 0.0 * x
         _, ux, uy, _ = self.exact(xp, x, y)
-        return self.eps * (ux * nx + uy * ny)
+        return self.eps_at(xp, x, y) * (ux * nx + uy * ny)
 
 
 def sinsin(xp, x, y):
@@ -221,6 +234,25 @@ def polynomial(a: int, bexp: int, c0=0.3):
         uyy = bexp * (bexp - 1) * x ** a * y ** (bexp - 2) if bexp > 1 else 0.0 * x
         return u, ux, uy, uxx + uyy
     return ex
+
+
+def affine_eps(e0, e1, e2):
+    """eps(x, y) = e0 + e1 x + e2 y (with its gradient)."""
+    def fn(xp, x, y):
+        return e0 + e1 * x + e2 * y, e1 + 0.0 * x, e2 + 0.0 * x
+    return fn
+
+
+def wavy_eps(e0=1.0, amp=0.5):
+    """eps(x, y) = e0 + amp sin(2 pi x) cos(pi y) (with its gradient); positive
+    for amp < e0."""
+    pi = math.pi
+
+    def fn(xp, x, y):
+        s2, c2 = xp.sin(2 * pi * x), xp.cos(2 * pi * x)
+        cy, sy = xp.cos(pi * y), xp.sin(pi * y)
+        return e0 + amp * s2 * cy, amp * 2 * pi * c2 * cy, -amp * pi * s2 * sy
+    return fn
 
 
 def gaussians_source(centres, widths, amp=1.0):

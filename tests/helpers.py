@@ -46,8 +46,13 @@ def oracle_system(ma: W.MeshArrays, k: int, method: int, prob: W.Problem, sigma=
     f = prob.f(np, xq[..., 0], xq[..., 1])
     gD = prob.gD(np, xb[..., 0], xb[..., 1])
     gN = prob.gN(np, xb[..., 0], xb[..., 1], nrm[:, None, 0], nrm[:, None, 1])
+    ev = ee = None
+    if prob.eps_fn is not None:   # variable diffusion: eps at the volume and edge points
+        ev = prob.eps_at(np, xq[..., 0], xq[..., 1])
+        xe = O.quad_points(m, k, O.EDGES)
+        ee = prob.eps_at(np, xe[..., 0], xe[..., 1])
     sysm = O.assemble(m, k, kap, s, 2 * s, prob.eps, prob.alpha, prob.b, f, gD, gN,
-                      literal_rhs=literal_rhs, split=split, b0=b0)
+                      literal_rhs=literal_rhs, split=split, b0=b0, eps_vol=ev, eps_edge=ee)
     return OracleRun(m, k, sysm, kap, s)
 
 
