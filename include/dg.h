@@ -83,6 +83,7 @@ typedef int dg_status;
 #define DG_POINTS_VOLUME   0  /* [ne][(k+2)^2]: Duffy-collapsed Gauss-Legendre */
 #define DG_POINTS_BOUNDARY 1  /* [n_bedges][k+2]: Gauss-Legendre on boundary edges */
 #define DG_POINTS_ERROR    2  /* [ne][(k+4)^2]: the L2-error rule */
+#define DG_POINTS_FACE     3  /* [ne][3][k+2]: Gauss-Legendre on the three faces of every element */
 
 /* ------------------------------------------------------------------------ */
 /* parameters                                                                */
@@ -109,7 +110,7 @@ typedef struct {
 } dg_params;
 
 /*
- * Problem data (Eq. (1)).  eps and alpha are constants; the advection field is
+ * Problem data (Eq. (1)).  alpha is a constant; the advection field is
  * affine, b(x,y) = (b[0] + b[1] x + b[2] y, b[3] + b[4] x + b[5] y).  The data
  * f, gD, gN are given at the library's quadrature points (dg_quad_points), the
  * way the paper's vectorised sub-functions fsource / DBCexact / NBCexact are
@@ -119,6 +120,18 @@ typedef struct {
  *        and on the inflow part (b.n < 0) of EVERY boundary edge, Neumann ones
  *        included (the inflow term of Eq. (ds) runs over all of Gamma^-)
  *   gN : device [n_bedges][k+2]   at DG_POINTS_BOUNDARY; read on Neumann edges
+ * The diffusion coefficient is the constant eps, or, when eps_q is given, the
+ * paper's fdiff(x, y) (Sec. 2.2) evaluated at the points:
+ *   eps_q : device [ne][(k+2)^2]  at DG_POINTS_VOLUME (the volume term)
+ *   eps_f : device [ne][3][k+2]   at DG_POINTS_FACE (the face terms
+ *           {eps grad u}, {eps grad v}, the penalty sigma eps / h_e and the
+ *           Dirichlet RHS terms); on an interior edge the mean of the two
+ *           elements' values at each point is used, which is eps(x) itself
+ *           for a continuous eps
+ * eps_q and eps_f are given together (DG_ERR_INVALID_ARG otherwise), need the
+ * f64 block copy in params.store, and are not read in batch mode
+ * (DG_ERR_INVALID_ARG).  All terms of Eq. (ds) are linear in eps, so the
+ * library assembles the eps = 0 operator and adds the pointwise-eps terms.
  */
 typedef struct {
     double eps;
@@ -127,6 +140,8 @@ typedef struct {
     const double* f;   double f_const;
     const double* gD;  double gD_const;
     const double* gN;  double gN_const;
+    const double* eps_q;   /* NULL: constant eps */
+    const double* eps_f;
 } dg_coeffs;
 
 /* Sizes of the uploaded mesh for the current degree. */
@@ -172,6 +187,60 @@ dg_status dg_destroy(dg_handle* h);
    the solver's CUDA graphs. */
 dg_status dg_stream_create(int device, void** stream);
 dg_status dg_stream_destroy(void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* device memory of a handle                                                 */
+/* ------------------------------------------------------------------------ */
+/*
+ * (Runtime; the paper, a MATLAB code, has no counterpart.)
+ * A handle keeps its mesh, assembled operator, preconditioner and solver
+ * workspaces in device memory it allocates as the calls need it (arrays grow
+ * when a larger mesh or degree needs more, and are kept for reuse).  By
+ * default that memory comes from cudaMalloc.  A caller that owns the device's
+ * memory (a framework's caching allocator, a pool sized at start-up) can
+ * supply it instead, in one of two ways, right after dg_create and before any
+ * other call that allocates:
+ *   - dg_set_allocator: the handle calls alloc(ctx, bytes, device, stream)
+ *     for every array and free(ctx, ptr, bytes, device, stream) when it
+ *     releases one (stream = the handle's stream at that moment).  alloc must
+ *     return memory on the handle's device, aligned to 256 bytes, or NULL
+ *     (the call then fails with DG_ERR_NOMEM).
+ *   - dg_set_arena: the handle carves every array out of the caller's device
+ *     buffer [base, base + bytes) (base aligned to 256 bytes; first fit with
+ *     256-byte granules); DG_ERR_NOMEM when the arena has no free range large
+ *     enough.  The caller keeps the buffer alive until dg_destroy.
+ * Either call moves the handle's 64-byte flag block to the new source and
+ * fails with DG_ERR_STATE if the handle already holds any other device memory.
+ * dg_destroy releases everything through the source in use.  Small pinned
+ * HOST buffers for solver status words still come from cudaMallocHost, and
+ * CUDA graph instantiation may allocate inside the driver.
+ * Ownership: the handle owns the memory it obtained until it releases it.
+ */
+typedef void* (*dg_alloc_fn)(void* ctx, size_t bytes, int device, void* stream);
+typedef void (*dg_free_fn)(void* ctx, void* ptr, size_t bytes, int device, void* stream);
+dg_status dg_set_allocator(dg_handle* h, dg_alloc_fn alloc_fn, dg_free_fn free_fn, void* ctx);
+dg_status dg_set_arena(dg_handle* h, void* base, size_t bytes);
+
+/* Categories of the handle's device memory for dg_workspace_size. */
+#define DG_WS_TOTAL     0  /* everything the handle holds now */
+#define DG_WS_MESH      1  /* mesh arrays, geometry, adjacency, reference tables */
+#define DG_WS_OPERATOR  2  /* assembled block copies (params.store) and F */
+#define DG_WS_PRECOND   3  /* block-Jacobi inverses, A M^-1, Schwarz rows */
+#define DG_WS_SOLVER    4  /* Krylov bases, solver states, refinement, batch and Newton buffers */
+#define DG_WS_LEARNED   5  /* network weights, training rows and training workspace */
+#define DG_WS_SCRATCH   6  /* shared scratch (assembly factors, reductions, dense LU) and flags */
+#define DG_WS_PEAK      7  /* largest DG_WS_TOTAL since dg_create or the last dg_set_allocator / dg_set_arena */
+/*
+ * Bytes of device memory the handle holds in category `what` (DG_WS_*), as
+ * requested from its memory source (an arena rounds each array up to 256
+ * bytes on top of this).  DG_WS_PEAK sizes an arena for a later handle that
+ * runs the same sequence of calls on the same sizes: with first fit,
+ * arrays re-allocated as they grow can fragment the arena, so leave headroom
+ * (a quarter more covers the library's own call sequences).  Returns 0 for a
+ * NULL handle or an unknown category.  Host-side bookkeeping, no
+ * synchronisation.
+ */
+size_t dg_workspace_size(const dg_handle* h, int what);
 
 /* Change the stream later calls issue work on. */
 dg_status dg_set_stream(dg_handle* h, void* stream);
@@ -422,6 +491,31 @@ dg_status dg_batch_solve(dg_handle* h, int inner_dtype, int inner_m, double inne
 dg_status dg_batch_gmres_ir_solve(dg_handle* h, int inner_dtype, int inner_m, double inner_tol, int max_outer,
                                   const double* F, double* x, int* its, double* relres, int* status);
 
+/*
+ * A group of batches solved in one call: hs [nh] distinct handles, each set up
+ * with dg_batch_setup (typically one batch per degree, since a handle's
+ * kernels are specialised on its degree, when the instances of a workload
+ * differ in degree).  Every batch is solved as by dg_batch_solve /
+ * dg_batch_gmres_ir_solve with the shared arguments, each from its own host
+ * thread on its handle's stream, so that the batches' launch sequences run on
+ * the GPU at the same time; the call returns when all have finished.  Give
+ * the handles different non-default streams to let them overlap (one stream
+ * serialises them; the results are the same).
+ *   F [nh] (or NULL: every batch's assembled F; an entry may be NULL), x [nh],
+ *   its / relres / status [nh] (or NULL; an entry may be NULL): the per-batch
+ *   arguments of the single-batch calls, all as there.
+ * Returns the first error of a batch other than DG_NOT_CONVERGED, else
+ * DG_NOT_CONVERGED if any instance of any batch missed the tolerance, else
+ * DG_OK; each handle's dg_last_error describes its own batch.  Synchronises.
+ * (Runtime; the paper has no counterpart.)
+ */
+dg_status dg_batch_group_solve(dg_handle* const* hs, int nh, int inner_dtype, int inner_m, double inner_tol,
+                               int max_outer, const double* const* F, double* const* x, int* const* its,
+                               double* const* relres, int* const* status);
+dg_status dg_batch_group_gmres_ir_solve(dg_handle* const* hs, int nh, int inner_dtype, int inner_m,
+                                        double inner_tol, int max_outer, const double* const* F, double* const* x,
+                                        int* const* its, double* const* relres, int* const* status);
+
 /* ------------------------------------------------------------------------ */
 /* non-linear reaction (Sec. 3)                                               */
 /* ------------------------------------------------------------------------ */
@@ -532,9 +626,15 @@ dg_status dg_eval(dg_handle* h, const double* x, int np, const double* rs, doubl
  * GPU, kept until the process exits), which limits the mesh to 4,194,304
  * elements (DG_ERR_INVALID_ARG beyond).  The handle's reference tables must
  * already exist: call dg_quad_points, dg_boundary_info or dg_assemble once
- * for the current degree first (DG_ERR_STATE otherwise).  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  All calls
+ * for the current degree first (DG_ERR_STATE otherwise).  dg_create looks up
+ * the array's device address (cudaGetSymbolAddress, with the handle's device
+ * current); that lookup makes the CUDA runtime load the module holding the
+ * array, so the array's device memory is allocated when the first handle is
+ * created on a device, not in a dg_l2_error_noalloc call.  If the current
+ * CUDA context has changed since (device reset, primary context released and
+ * created again), the call looks the address up anew before launching,
+ * which loads the module into the new context; make calls after such a
+ * change, like the first handle creation, outside any stream capture.  All calls
  * share the array: calls whose GPU work overlaps (other streams or handles on
  * the same device) race on it and must be serialised by the caller.
  * Synchronises the handle's stream.

@@ -364,6 +364,7 @@ dg_status dg_launch_bj_setup(dg_handle* h) {
 }
 
 extern "C" dg_status dg_precond_setup(dg_handle* h, int kind) {
+    DG_WS_SCOPE(h, DG_WS_PRECOND);
     if (!h) return DG_ERR_INVALID_ARG;
     if (!h->assembled) return dg_fail(h, DG_ERR_STATE, "not assembled");
     if (kind == DG_PRECOND_NONE) return DG_OK;

@@ -355,6 +355,156 @@ __global__ void __launch_bounds__(256) k_rhs(const AsmArgs a) {
     a.F[(size_t)K * NB + i] = acc;
 }
 
+// ---------------------------------------------------------------------------
+// variable diffusion eps(x, y) (the paper's fdiff, evaluated at the points)
+// ---------------------------------------------------------------------------
+// Every term of Eq. (ds) that holds eps is linear in it, so with a pointwise
+// eps the operator is the eps = 0 assembly plus the terms below, which this
+// kernel adds into the f64 blocks and F by quadrature with eps at each point:
+//   volume  (K,K)   += int eps grad phi_j . grad phi_i
+//   interior(K,K)   += int eps [-1/2 (grad phi_j.n) phi_i + kappa/2 (grad phi_i.n) phi_j
+//                               + sigma/h_e^b0 phi_j phi_i]
+//           (K,L)   += int eps [-1/2 (grad psi_j.n) phi_i - kappa/2 (grad phi_i.n) psi_j
+//                               - sigma/h_e^b0 psi_j phi_i]
+//   Dirichlet (K,K) += int eps [-(grad phi_j.n) phi_i + kappa (grad phi_i.n) phi_j
+//                               + sigma_b/h_e^b0 phi_j phi_i]
+//   Dirichlet F_i   += int gD eps (sigma_b/h_e^b0 phi_i + kappa grad phi_i.n)
+// (the jump/average form of the constant-eps kernels above, A-1 sign).  One
+// CTA per 32-element tile: lanes are elements, warps run over the entries
+// (i, j) of the four blocks and then over F_i.  On an interior edge eps at a
+// point is the mean of the two elements' values there.
+template <int K_DEG>
+__global__ void __launch_bounds__(256) k_diff_var(const AsmArgs a, const double* __restrict__ eps_q,
+                                                  const double* __restrict__ eps_f) {
+    constexpr int NB = dg_nb(K_DEG);
+    constexpr int NQ = K_DEG + 2;
+    constexpr int QK = NQ * NQ;
+    constexpr int NB2 = NB * NB;
+    extern __shared__ double sm[];
+    const TabLayout& L = a.L;
+    double* se = sm + L.err_w;          // eps at the tile's volume points [QK][32]
+    double* sf = se + QK * 32;          // eps on the tile's faces [3][NQ][32]
+    for (int t = threadIdx.x; t < L.err_w; t += blockDim.x) sm[t] = a.tab[t];
+    const int ne = a.ne;
+    const int tile = blockIdx.x;
+    for (int t = threadIdx.x; t < QK * 32; t += blockDim.x) {
+        const int q = t >> 5, K = tile * 32 + (t & 31);
+        se[t] = K < ne ? eps_q[(size_t)K * QK + q] : 0.0;
+    }
+    for (int t = threadIdx.x; t < 3 * NQ * 32; t += blockDim.x) {
+        const int fq = t >> 5, K = tile * 32 + (t & 31);
+        const int f = fq / NQ, q = fq - f * NQ;
+        double v = 0.0;
+        if (K < ne) {
+            v = eps_f[((size_t)K * 3 + f) * NQ + q];
+            if (__ldg(a.ftype + (size_t)f * ne + K) == 0) {
+                const int Ln = __ldg(a.nbr + (size_t)f * ne + K), nf = __ldg(a.nface + (size_t)f * ne + K);
+                v = 0.5 * (v + eps_f[((size_t)Ln * 3 + nf) * NQ + (NQ - 1 - q)]);
+            }
+        }
+        sf[t] = v;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int K = tile * 32 + lane;
+    if (K >= ne) return;
+    const double j00 = gload(a.geo, G_J00, ne, K), j01 = gload(a.geo, G_J01, ne, K);
+    const double j10 = gload(a.geo, G_J10, ne, K), j11 = gload(a.geo, G_J11, ne, K);
+    const double i00 = gload(a.geo, G_I00, ne, K), i01 = gload(a.geo, G_I01, ne, K);
+    const double i10 = gload(a.geo, G_I10, ne, K), i11 = gload(a.geo, G_I11, ne, K);
+    const double det = gload(a.geo, G_DET, ne, K);
+    const double grr = i00 * i00 + i01 * i01, grs = i00 * i10 + i01 * i11, gss = i10 * i10 + i11 * i11;
+    const double* vw = sm + L.vol_w;
+    const double* vdr = sm + L.vol_dr;
+    const double* vds = sm + L.vol_ds;
+    const double* fw = sm + L.face_w;
+    const double* fphi = sm + L.face_phi;
+    const double* fdr = sm + L.face_dr;
+    const double* fds = sm + L.face_ds;
+    const double dV[3][2] = {{1.0, 0.0}, {-1.0, 1.0}, {0.0, -1.0}};
+    for (int m = warp; m < NB2 + NB; m += 8) {
+        const bool rhs = m >= NB2;
+        const int i = rhs ? m - NB2 : m / NB, j = rhs ? 0 : m - (m / NB) * NB;
+        double out[4] = {0.0, 0.0, 0.0, 0.0};
+        if (!rhs) {
+            for (int q = 0; q < QK; ++q) {
+                const double dri = vdr[q * NB + i], dsi = vds[q * NB + i];
+                const double drj = vdr[q * NB + j], dsj = vds[q * NB + j];
+                const double g = grr * drj * dri + grs * (drj * dsi + dsj * dri) + gss * dsj * dsi;
+                out[0] = fma(vw[q] * det * se[q * 32 + lane], g, out[0]);
+            }
+        }
+        for (int f = 0; f < 3; ++f) {
+            const int type = __ldg(a.ftype + (size_t)f * ne + K);
+            if (type == 2 || (rhs && type != 1)) continue;
+            const double tx = j00 * dV[f][0] + j01 * dV[f][1];
+            const double ty = j10 * dV[f][0] + j11 * dV[f][1];
+            const double len = sqrt(tx * tx + ty * ty);
+            const double nx = ty / len, ny = -tx / len;
+            const double ph = a.b0 == 1.0 ? 1.0 / len : pow(len, -a.b0);   // 1 / h_e^b0
+            const double sig = type == 0 ? a.sig_int : a.sig_bdry;
+            int Ln = -1, nf = 0;
+            double l00 = 0.0, l01 = 0.0, l10 = 0.0, l11 = 0.0;
+            if (type == 0) {
+                Ln = __ldg(a.nbr + (size_t)f * ne + K);
+                nf = __ldg(a.nface + (size_t)f * ne + K);
+                l00 = gload(a.geo, G_I00, ne, Ln);
+                l01 = gload(a.geo, G_I01, ne, Ln);
+                l10 = gload(a.geo, G_I10, ne, Ln);
+                l11 = gload(a.geo, G_I11, ne, Ln);
+            }
+            const int b = rhs ? __ldg(a.bidx + (size_t)f * ne + K) : -1;
+            double kk = 0.0, kl = 0.0;
+            for (int q = 0; q < NQ; ++q) {
+                const double w = fw[q] * len * sf[(f * NQ + q) * 32 + lane];
+                const int oi = (f * NQ + q) * NB + i;
+                const double pi = fphi[oi];
+                const double gi = (i00 * fdr[oi] + i10 * fds[oi]) * nx + (i01 * fdr[oi] + i11 * fds[oi]) * ny;
+                if (rhs) {
+                    const double gD = a.gD ? __ldg(a.gD + (size_t)b * NQ + q) : a.gD_const;
+                    kk = fma(w * gD, sig * ph * pi + a.kappa * gi, kk);
+                    continue;
+                }
+                const int oj = (f * NQ + q) * NB + j;
+                const double pj = fphi[oj];
+                const double gj = (i00 * fdr[oj] + i10 * fds[oj]) * nx + (i01 * fdr[oj] + i11 * fds[oj]) * ny;
+                if (type == 0) {
+                    kk = fma(w, -0.5 * gj * pi + 0.5 * a.kappa * gi * pj + sig * ph * pj * pi, kk);
+                    const int ol = (nf * NQ + NQ - 1 - q) * NB + j;
+                    const double psj = fphi[ol];
+                    const double gl = (l00 * fdr[ol] + l10 * fds[ol]) * nx + (l01 * fdr[ol] + l11 * fds[ol]) * ny;
+                    kl = fma(w, -0.5 * gl * pi - 0.5 * a.kappa * gi * psj - sig * ph * psj * pi, kl);
+                } else {
+                    kk = fma(w, -gj * pi + a.kappa * gi * pj + sig * ph * pj * pi, kk);
+                }
+            }
+            out[0] += kk;
+            if (!rhs && type == 0) out[1 + f] = kl;
+        }
+        if (rhs) {
+            a.F[(size_t)K * NB + i] += out[0];
+        } else {
+            a.A64[dg_blk_index<double>(K, 0, m, NB, 4)] += out[0];
+            for (int f = 0; f < 3; ++f)
+                if (out[1 + f] != 0.0) a.A64[dg_blk_index<double>(K, 1 + f, m, NB, 4)] += out[1 + f];
+        }
+    }
+}
+
+// The f32 / bf16 block copies rounded from the f64 blocks (after k_diff_var).
+template <int NB>
+__global__ void __launch_bounds__(256) k_round_copies(const double* __restrict__ A64, float* A32, __nv_bfloat16* A16,
+                                                      int ne) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)ne * 4 * NB * NB) return;
+    const int K = (int)(t / (4 * NB * NB));
+    const int r = (int)(t - (long)K * 4 * NB * NB);
+    const int s = r / (NB * NB), m = r - s * NB * NB;
+    const double v = A64[dg_blk_index<double>(K, s, m, NB, 4)];
+    if (A32) A32[dg_blk_index<float>(K, s, m, NB, 4)] = (float)v;
+    if (A16) A16[dg_blk_index<__nv_bfloat16>(K, s, m, NB, 4)] = __double2bfloat16(v);
+}
+
 dg_status dg_launch_assemble(dg_handle* h, const dg_coeffs* c, double kappa, double sig_int, double sig_bdry) {
     const int k = h->p.degree;
     const int nb = dg_nb(k);
@@ -420,13 +570,49 @@ dg_status dg_launch_assemble(dg_handle* h, const dg_coeffs* c, double kappa, dou
     }
     h->nlaunch += 3;
     DG_LAUNCH_CK(h);
+    if (c->eps_q) {
+        // pointwise eps: the kernels above ran with eps = 0 (the caller's copy
+        // of the coefficients); add the eps terms, then round the copies
+        const size_t dsmem = sizeof(double) * ((size_t)h->tl.err_w + 32 * (size_t)(h->tl.qk + 3 * h->tl.nq));
+        const long nent = (long)h->ne * 4 * nb * nb;
+        const unsigned gc = (unsigned)((nent + 255) / 256);
+        switch (k) {
+            case 1:
+                DG_CK(h, cudaFuncSetAttribute(k_diff_var<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
+                k_diff_var<1><<<ga, 256, dsmem, h->stream>>>(a, c->eps_q, c->eps_f);
+                if (a.A32 || a.A16) k_round_copies<3><<<gc, 256, 0, h->stream>>>(a.A64, a.A32, a.A16, h->ne);
+                break;
+            case 2:
+                DG_CK(h, cudaFuncSetAttribute(k_diff_var<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
+                k_diff_var<2><<<ga, 256, dsmem, h->stream>>>(a, c->eps_q, c->eps_f);
+                if (a.A32 || a.A16) k_round_copies<6><<<gc, 256, 0, h->stream>>>(a.A64, a.A32, a.A16, h->ne);
+                break;
+            case 3:
+                DG_CK(h, cudaFuncSetAttribute(k_diff_var<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
+                k_diff_var<3><<<ga, 256, dsmem, h->stream>>>(a, c->eps_q, c->eps_f);
+                if (a.A32 || a.A16) k_round_copies<10><<<gc, 256, 0, h->stream>>>(a.A64, a.A32, a.A16, h->ne);
+                break;
+        }
+        h->nlaunch += (a.A32 || a.A16) ? 2 : 1;
+        DG_LAUNCH_CK(h);
+    }
     return DG_OK;
 }
 
 extern "C" dg_status dg_assemble(dg_handle* h, const dg_coeffs* c) {
+    DG_WS_SCOPE(h, DG_WS_OPERATOR);
     if (!h || !c) return DG_ERR_INVALID_ARG;
     if (!h->mesh_ok) return dg_fail(h, DG_ERR_STATE, "no mesh uploaded");
     if (!(c->eps >= 0.0) || !(c->alpha == c->alpha)) return dg_fail(h, DG_ERR_INVALID_ARG, "eps must be >= 0");
+    if ((c->eps_q == nullptr) != (c->eps_f == nullptr))
+        return dg_fail(h, DG_ERR_INVALID_ARG, "eps_q and eps_f are given together");
+    if (c->eps_q && h->b_inst_active)
+        return dg_fail(h, DG_ERR_INVALID_ARG, "a pointwise eps is not read in batch mode");
+    if (c->eps_q && !(h->p.store & DG_STORE_F64))
+        return dg_fail(h, DG_ERR_INVALID_ARG, "a pointwise eps needs the f64 block copy (params.store)");
+    dg_coeffs cv = *c;
+    if (c->eps_q) cv.eps = 0.0;   // the eps terms are added pointwise after the eps = 0 assembly
+    c = &cv;
     DG_CK(h, cudaSetDevice(h->device));
     const int k = h->p.degree;
     const int nb = dg_nb(k);

@@ -26,6 +26,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -632,6 +633,7 @@ static BatchHostLayout batch_layout(int nI, int nit, int nsets) {
 }
 
 extern "C" dg_status dg_batch_setup(dg_handle* h, int n_inst, const int* elem_start, const double* coeffs) {
+    DG_WS_SCOPE(h, DG_WS_SOLVER);
     if (!h || n_inst < 1 || !elem_start || !coeffs) return DG_ERR_INVALID_ARG;
     if (!h->mesh_ok) return dg_fail(h, DG_ERR_STATE, "upload the concatenated mesh first");
     if (elem_start[0] != 0 || elem_start[n_inst] != h->ne)
@@ -998,6 +1000,7 @@ static dg_status batch_solve_t(dg_handle* h, int inner_dtype, const TA* Alo, con
 
 extern "C" dg_status dg_batch_solve(dg_handle* h, int inner_dtype, int inner_m, double inner_tol, int max_outer,
                                     const double* F, double* x, int* its, double* relres, int* status) {
+    DG_WS_SCOPE(h, DG_WS_SOLVER);
     if (!h || !x) return DG_ERR_INVALID_ARG;
     h->basis = nullptr;
     if (!h->b_inst_active || h->b_n < 1) return dg_fail(h, DG_ERR_STATE, "no batch set up");
@@ -1163,6 +1166,7 @@ static dg_status batch_ir_t(dg_handle* h, const TA* Alo, const TB* Binv, int inn
 extern "C" dg_status dg_batch_gmres_ir_solve(dg_handle* h, int inner_dtype, int inner_m, double inner_tol,
                                              int max_outer, const double* F, double* x, int* its, double* relres,
                                              int* status) {
+    DG_WS_SCOPE(h, DG_WS_SOLVER);
     if (!h || !x) return DG_ERR_INVALID_ARG;
     h->basis = nullptr;
     if (!h->b_inst_active || h->b_n < 1) return dg_fail(h, DG_ERR_STATE, "no batch set up");
@@ -1197,6 +1201,82 @@ extern "C" dg_status dg_batch_gmres_ir_solve(dg_handle* h, int inner_dtype, int 
     return dg_fail(h, DG_ERR_INVALID_ARG, "degree");
 }
 
+// ---------------------------------------------------------------------------
+// groups of batches solved in one call
+// ---------------------------------------------------------------------------
+// A workload whose instances differ in degree is uploaded as one batch per
+// degree (each on its own handle, with kernels specialised on the unknowns per
+// element).  The group call drives every batch's solve from its own host
+// thread on its handle's stream, so the batches' launch sequences run on the
+// GPU at the same time and the call returns when the slowest has finished.
+struct GroupJob {
+    dg_handle* h;
+    const double* F;
+    double* x;
+    int *its, *status;
+    double* relres;
+    dg_status result;
+};
+
+static dg_status group_run(dg_handle* const* hs, int nh, const double* const* F, double* const* x, int* const* its,
+                           double* const* relres, int* const* status,
+                           dg_status (*solve)(GroupJob&, const void*), const void* args) {
+    if (!hs || nh < 1 || nh > 64 || !x) return DG_ERR_INVALID_ARG;
+    for (int i = 0; i < nh; ++i) {
+        if (!hs[i] || !x[i]) return DG_ERR_INVALID_ARG;
+        for (int l = 0; l < i; ++l)
+            if (hs[l] == hs[i]) return dg_fail(hs[i], DG_ERR_INVALID_ARG, "a handle appears twice in the group");
+    }
+    std::vector<GroupJob> jobs(nh);
+    for (int i = 0; i < nh; ++i)
+        jobs[i] = GroupJob{hs[i], F ? F[i] : nullptr, x[i], its ? its[i] : nullptr, status ? status[i] : nullptr,
+                           relres ? relres[i] : nullptr, DG_OK};
+    std::vector<std::thread> th;
+    th.reserve(nh - 1);
+    for (int i = 1; i < nh; ++i) th.emplace_back([&jobs, i, solve, args] { jobs[i].result = solve(jobs[i], args); });
+    jobs[0].result = solve(jobs[0], args);
+    for (auto& t : th) t.join();
+    // the first error other than non-convergence, else non-convergence, else OK
+    dg_status res = DG_OK;
+    for (const GroupJob& j : jobs)
+        if (j.result != DG_OK && j.result != DG_NOT_CONVERGED) return j.result;
+    for (const GroupJob& j : jobs)
+        if (j.result == DG_NOT_CONVERGED) res = DG_NOT_CONVERGED;
+    return res;
+}
+
+struct GroupArgs {
+    int inner_dtype, inner_m, max_outer;
+    double inner_tol;
+};
+
+static dg_status group_solve_one(GroupJob& j, const void* a) {
+    const GroupArgs& g = *(const GroupArgs*)a;
+    return dg_batch_solve(j.h, g.inner_dtype, g.inner_m, g.inner_tol, g.max_outer, j.F, j.x, j.its, j.relres,
+                          j.status);
+}
+
+static dg_status group_ir_one(GroupJob& j, const void* a) {
+    const GroupArgs& g = *(const GroupArgs*)a;
+    return dg_batch_gmres_ir_solve(j.h, g.inner_dtype, g.inner_m, g.inner_tol, g.max_outer, j.F, j.x, j.its,
+                                   j.relres, j.status);
+}
+
+extern "C" dg_status dg_batch_group_solve(dg_handle* const* hs, int nh, int inner_dtype, int inner_m,
+                                          double inner_tol, int max_outer, const double* const* F, double* const* x,
+                                          int* const* its, double* const* relres, int* const* status) {
+    const GroupArgs g{inner_dtype, inner_m, max_outer, inner_tol};
+    return group_run(hs, nh, F, x, its, relres, status, group_solve_one, &g);
+}
+
+extern "C" dg_status dg_batch_group_gmres_ir_solve(dg_handle* const* hs, int nh, int inner_dtype, int inner_m,
+                                                   double inner_tol, int max_outer, const double* const* F,
+                                                   double* const* x, int* const* its, double* const* relres,
+                                                   int* const* status) {
+    const GroupArgs g{inner_dtype, inner_m, max_outer, inner_tol};
+    return group_run(hs, nh, F, x, its, relres, status, group_ir_one, &g);
+}
+
 extern "C" dg_status dg_batch_set_tile(dg_handle* h, int tile) {
     if (!h || tile < 0 || (tile > 0 && (tile < 256 || tile > (1 << 20)))) return DG_ERR_INVALID_ARG;
     h->b_tile = tile;
@@ -1227,6 +1307,7 @@ __global__ void k_b_prof_state(BatchDev B, int j) {
 // timing the batched multi-dot on this batch for each candidate; the result is
 // kept in the handle and returned through *tile.
 extern "C" dg_status dg_batch_autotune(dg_handle* h, int* tile) {
+    DG_WS_SCOPE(h, DG_WS_SOLVER);
     if (!h || !tile) return DG_ERR_INVALID_ARG;
     h->basis = nullptr;
     if (!h->b_inst_active || !h->assembled) return dg_fail(h, DG_ERR_STATE, "set up and assemble a batch first");

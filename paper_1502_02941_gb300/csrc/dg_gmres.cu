@@ -354,6 +354,27 @@ __global__ void __launch_bounds__(GM_TX* GM_TY) k_gm_dots(const TV* __restrict__
     st->colready = 1;
 }
 
+// Block 0 of the update kernels: the Givens step of the column the multi-dot
+// tail marked ready, with the column and the previous rotations staged in
+// shared memory.
+__device__ void gm_control_block(GmresState* st) {
+    __shared__ double hc[DG_MAXM + 2], css[DG_MAXM], sns[DG_MAXM];
+    if (!st->colready) return;
+    const int jc = st->jw;
+    for (int i = threadIdx.x; i <= jc; i += blockDim.x) {
+        hc[i] = st->hcol[i];
+        if (i < jc) {
+            css[i] = st->cs[i];
+            sns[i] = st->sn[i];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st->colready = 0;
+        gm_finish_column(st, st->wn_fin, hc, css, sns);
+    }
+}
+
 // V_{j+1} -= sum_{d<=j} coef_d V_d for the column j = jw the multi-dot kernel
 // prepared.  Block 0 (dispatched first) takes the Givens step of the column
 // when the multi-dot tail marked it ready, in parallel with the update (the
@@ -365,21 +386,7 @@ __global__ void __launch_bounds__(256) k_gm_update(TV* V, long ld, long nvec, Gm
         dg_grid_wait();
     }
     if (blockIdx.x == 0) {
-        __shared__ double hc[DG_MAXM + 2], css[DG_MAXM], sns[DG_MAXM];
-        if (!st->colready) return;
-        const int jc = st->jw;
-        for (int i = threadIdx.x; i <= jc; i += blockDim.x) {
-            hc[i] = st->hcol[i];
-            if (i < jc) {
-                css[i] = st->cs[i];
-                sns[i] = st->sn[i];
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            st->colready = 0;
-            gm_finish_column(st, st->wn_fin, hc, css, sns);
-        }
+        gm_control_block(st);
         return;
     }
     if (!st->active || (pass == 2 && !st->reorth)) return;
@@ -410,6 +417,204 @@ __global__ void __launch_bounds__(256) k_gm_update(TV* V, long ld, long nvec, Gm
             for (int i = 0; i < W; ++i) Vec<TV>::set(acc, i, ::fma(-c[d], Vec<TV>::get(v, i), Vec<TV>::get(acc, i)));
         }
         w[q] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// f32 Arnoldi kernels (the inner GMRES of the mixed-precision solvers)
+// ---------------------------------------------------------------------------
+// Sum of two two-float numbers (hi, lo): Knuth's TwoSum of the high parts,
+// the low parts added to its error, renormalised (Dekker's fast TwoSum).  The
+// compiler keeps the order of these additions (no fast-math flags).
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) {
+    const float s = a.x + b.x;
+    const float bp = s - a.x;
+    float e = (a.x - (s - bp)) + (b.x - bp);
+    e += a.y + b.y;
+    const float hi = s + e;
+    return make_float2(hi, e - (hi - s));
+}
+
+#define GM32_THREADS 512
+#define GM32_WARPS (GM32_THREADS / 32)
+#define GM32_G 16   // dots per warp group
+
+// f32 multi-dot r_d = <V_d, V_{j+1}>, d <= j+1 (pass 1 and pass 2 alike; d = j+1
+// is ||w||^2).  The ncol = j+2 dots are cut into ngroups groups of equal size
+// (at most GM32_G); the warps of a block are split into (group, row
+// partition) pairs and every partition strides over the 512-byte row chunks,
+// so all resident warps stream at every step j: per chunk a warp loads w once
+// and the chunk of each vector of its group.  (Fewer blocks that each take an
+// equal run of chunks measured slower: the kernel is latency-bound, and
+// resident warps matter more than balance.)  Each lane sums its few products
+// in f32, the warp in an f32 tree (32 terms); the warps of a block and then
+// the blocks are summed in two-float arithmetic (f2_add), and the last block
+// to arrive turns each total into one f64 value: no per-warp f64 work, which
+// on this GPU's FP64 pipe would cost as much as the streaming.  The tail then
+// follows the f64 kernel: h_d = s_d r_d, the update coefficients, and the norm
+// ||w||^2 - sum h_d^2 or a request for a second pass.
+__global__ void __launch_bounds__(GM32_THREADS, 2) k_gm_dots32(const float* __restrict__ V, long ld, long nvec,
+                                                               GmresState* st, float2* partials, int pass) {
+    dg_grid_release();   // programmatic dependent launch
+    dg_grid_wait();
+    if (!st->active || (pass == 2 && !st->reorth)) return;
+    const int j = st->j;
+    const int ncol = j + 2;
+    const int ngroups = (ncol + GM32_G - 1) / GM32_G;   // <= 5 (ncol <= DG_MAXM + 2)
+    const int gsize = (ncol + ngroups - 1) / ngroups;
+    const int pb = GM32_WARPS / ngroups;                 // row partitions per block
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = wid % ngroups, part = wid / ngroups;
+    const int d0 = g * gsize;
+    const int dn = part < pb ? max(0, min(gsize, ncol - d0)) : 0;
+    __shared__ float red[GM32_WARPS][GM32_G];
+    float acc[GM32_G];
+#pragma unroll
+    for (int i = 0; i < GM32_G; ++i) acc[i] = 0.f;
+    if (dn > 0) {
+        const long nchunk = (nvec + 31) / 32;
+        const long P = (long)gridDim.x * pb;
+        const long ld4 = ld / 4;
+        const float4* __restrict__ w = reinterpret_cast<const float4*>(V + (long)(j + 1) * ld);
+        const float4* __restrict__ vg = reinterpret_cast<const float4*>(V + (long)d0 * ld);
+        for (long c = (long)blockIdx.x * pb + part; c < nchunk; c += P) {
+            const long q = c * 32 + lane;
+            if (q >= nvec) continue;
+            const float4 wv = w[q];
+#pragma unroll
+            for (int d = 0; d < GM32_G; ++d) {
+                if (d < dn) {
+                    const float4 v = vg[(long)d * ld4 + q];
+                    acc[d] = fmaf(v.x, wv.x, acc[d]);
+                    acc[d] = fmaf(v.y, wv.y, acc[d]);
+                    acc[d] = fmaf(v.z, wv.z, acc[d]);
+                    acc[d] = fmaf(v.w, wv.w, acc[d]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < GM32_G; ++d) {
+        if (d < gsize) {   // block-uniform
+            float v = acc[d];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) red[wid][d] = d < dn ? v : 0.f;
+        }
+    }
+    __syncthreads();
+    const int gx = gridDim.x;
+    for (int d = threadIdx.x; d < ncol; d += blockDim.x) {
+        const int gg = d / gsize, dd = d - gg * gsize;
+        float2 s = make_float2(0.f, 0.f);
+        for (int p = 0; p < pb; ++p) s = f2_add(s, make_float2(red[p * ngroups + gg][dd], 0.f));
+        partials[(long)d * gx + blockIdx.x] = s;
+    }
+    if (!last_block(&st->arrive)) return;
+    __shared__ float2 tot[DG_MAXM + 2];
+    for (int d = wid; d < ncol; d += GM32_WARPS) {
+        float2 s = make_float2(0.f, 0.f);
+        for (int b = lane; b < gx; b += 32) s = f2_add(s, __ldcg(partials + (long)d * gx + b));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float2 t;
+            t.x = __shfl_xor_sync(0xffffffffu, s.x, o);
+            t.y = __shfl_xor_sync(0xffffffffu, s.y, o);
+            s = f2_add(s, t);
+        }
+        if (lane == 0) tot[d] = s;
+    }
+    __syncthreads();
+    __shared__ double hp[DG_MAXM + 2];
+    for (int d = threadIdx.x; d < ncol; d += blockDim.x) {
+        const double r = (double)tot[d].x + (double)tot[d].y;
+        if (d == j + 1) {
+            hp[d] = r;   // ||w||^2
+        } else {
+            const double hd = st->scale[d] * r;
+            hp[d] = hd;
+            st->hcol[d] = pass == 1 ? hd : st->hcol[d] + hd;
+            st->coef[d] = hd * st->scale[d];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x >= 32) return;
+    double s2 = 0.0;
+    for (int d = threadIdx.x; d <= j; d += 32) s2 = fma(hp[d], hp[d], s2);
+    s2 = dg_warp_sum(s2);
+    if (threadIdx.x != 0) return;
+    const double w2 = hp[j + 1];
+    const double rest = w2 - s2;
+    st->jw = j;
+    if (pass == 1) {
+        const bool again = !(rest >= 0.49 * w2);
+        st->reorth = again ? 1 : 0;
+        if (again) return;
+    }
+    st->wn_fin = sqrt(rest > 0.0 ? rest : 0.0);
+    st->colready = 1;
+}
+
+// f32 Gram-Schmidt update V_{j+1} -= sum_{d<=j} coef_d V_d (j = jw): block 0
+// takes the Givens step; every other thread streams one 16-byte column slice
+// through the basis, GM32_U vectors per round so that that many loads are in
+// flight per thread.
+#define GM32_U 8
+__global__ void __launch_bounds__(256) k_gm_update32(float* V, long ld, long nvec, GmresState* st, int pass) {
+    dg_grid_release();   // programmatic dependent launch
+    dg_grid_wait();
+    if (blockIdx.x == 0) {
+        gm_control_block(st);
+        return;
+    }
+    if (!st->active || (pass == 2 && !st->reorth)) return;
+    __shared__ float c[DG_MAXM + 2];
+    const int j = st->jw;
+    for (int d = threadIdx.x; d <= j; d += blockDim.x) c[d] = (float)st->coef[d];
+    __syncthreads();
+    const long ld4 = ld / 4;
+    float4* w = reinterpret_cast<float4*>(V + (long)(j + 1) * ld);   // aliases V: no __restrict__
+    const float4* v0 = reinterpret_cast<const float4*>(V);
+    const long nthr = (long)(gridDim.x - 1) * blockDim.x;
+    for (long q = (long)(blockIdx.x - 1) * blockDim.x + threadIdx.x; q < nvec; q += nthr) {
+        float4 acc = w[q];
+        int d = 0;
+        for (; d + GM32_U <= j + 1; d += GM32_U) {
+            float4 v[GM32_U];
+#pragma unroll
+            for (int u = 0; u < GM32_U; ++u) v[u] = v0[(long)(d + u) * ld4 + q];
+#pragma unroll
+            for (int u = 0; u < GM32_U; ++u) {
+                const float cc = -c[d + u];
+                acc.x = fmaf(cc, v[u].x, acc.x);
+                acc.y = fmaf(cc, v[u].y, acc.y);
+                acc.z = fmaf(cc, v[u].z, acc.z);
+                acc.w = fmaf(cc, v[u].w, acc.w);
+            }
+        }
+        for (; d <= j; ++d) {
+            const float4 v = v0[(long)d * ld4 + q];
+            const float cc = -c[d];
+            acc.x = fmaf(cc, v.x, acc.x);
+            acc.y = fmaf(cc, v.y, acc.y);
+            acc.z = fmaf(cc, v.z, acc.z);
+            acc.w = fmaf(cc, v.w, acc.w);
+        }
+        w[q] = acc;
+    }
+}
+
+// Launch the multi-dot + update pair of Gram-Schmidt pass `pass`.
+template <typename TV>
+static void launch_gs_pass(dg_handle* h, GmresWork& W, TV* V, long ld, long nvec, bool pdl, int pass) {
+    if constexpr (sizeof(TV) == 4) {
+        dg_launch(h, pdl, k_gm_dots32, dim3(W.gd32), dim3(GM32_THREADS), (const float*)V, ld, nvec, W.st,
+                  (float2*)W.partials, pass);
+        dg_launch(h, pdl, k_gm_update32, dim3(W.gu32 + 1), dim3(256), (float*)V, ld, nvec, W.st, pass);
+    } else {
+        dg_launch(h, pdl, k_gm_dots<TV>, dim3(W.gsm), dim3(GM_TX, GM_TY), (const TV*)V, ld, nvec, W.st, W.partials,
+                  pass);
+        dg_launch(h, pdl, k_gm_update<TV>, dim3(W.gx + 1), dim3(256), V, ld, nvec, W.st, pass);
     }
 }
 
@@ -546,8 +751,6 @@ static int enqueue_cycle(dg_handle* h, GmresWork& W, const TA* A, const TB* B, c
     const long ld = (long)W.ld;
     const long nvec = ld / Vec<TV>::W;
     const int gx = W.gx;
-    const dim3 bdots(GM_TX, GM_TY);
-    const int gdots = W.gsm;
     DevCtl step{&st->active, st->scale};
     DevCtl step_noscale{&st->active, nullptr};
     VecSel vj{&st->j, 0, ld}, vj1{&st->j, 1, ld};
@@ -579,10 +782,7 @@ static int enqueue_cycle(dg_handle* h, GmresWork& W, const TA* A, const TB* B, c
             launch_bj<NB, TB, TV>(h, B, V, Z, step, vj, vsel_fixed(), pdl);
             launch_apply<NB, TA, TV>(h, A, Z, V, step_noscale, vsel_fixed(), vj1, pdl);
         }
-        for (int pass = 1; pass <= 2; ++pass) {
-            dg_launch(h, pdl, k_gm_dots<TV>, dim3(gdots), bdots, (const TV*)V, ld, nvec, st, W.partials, pass);
-            dg_launch(h, pdl, k_gm_update<TV>, dim3(gx + 1), dim3(256), V, ld, nvec, st, pass);
-        }
+        for (int pass = 1; pass <= 2; ++pass) launch_gs_pass<TV>(h, W, V, ld, nvec, pdl, pass);
     }
     DevCtl pend{&st->pending, nullptr};
     k_gm_solve<<<1, 256, 0, h->stream>>>(st, flex ? 1 : 0);
@@ -601,10 +801,9 @@ static int enqueue_cycle(dg_handle* h, GmresWork& W, const TA* A, const TB* B, c
     return 6 * W.m + 6 + extra - (flex ? 1 : 0);
 }
 
-void dg_gmres_free(GmresWork* w) {
+void dg_gmres_free(dg_handle* h, GmresWork* w) {
     void* ptrs[] = {w->V, w->Z, w->R, w->Zb, w->partials, w->st};
-    for (void* p : ptrs)
-        if (p) cudaFree(p);
+    for (void* p : ptrs) dg_dev_free(h, p);
     if (w->st_host) cudaFreeHost(w->st_host);
     if (w->graph) cudaGraphExecDestroy(w->graph);
     *w = GmresWork();
@@ -622,7 +821,7 @@ static dg_status ensure_workspace(dg_handle* h, GmresWork& W, long n, int m, siz
         DG_CK(h, cudaMemsetAsync(W.Z, 0, ld * elem, h->stream));
         DG_CK(h, cudaMemsetAsync(W.R, 0, ld * elem, h->stream));
         if (W.Zb) {
-            cudaFree(W.Zb);
+            dg_dev_free(h, W.Zb);
             W.Zb = nullptr;
         }
         W.ld = ld;
@@ -639,6 +838,16 @@ static dg_status ensure_workspace(dg_handle* h, GmresWork& W, long n, int m, siz
     long want = 4L * sms, cap = (n + 255) / 256;
     W.gx = (int)(want < cap ? want : (cap < 1 ? 1 : cap));
     W.gsm = (int)((long)sms < (n + 1023) / 1024 ? sms : ((n + 1023) / 1024 < 1 ? 1 : (n + 1023) / 1024));
+    {
+        // f32 kernels: 16-byte slices of 4 entries; two multi-dot blocks per SM
+        // (one 512-byte chunk per warp at least), five update blocks per SM (44
+        // registers a thread: all resident at once)
+        const long nvec4 = (long)(((size_t)n + 63) / 64 * 64) / 4;
+        const long want_d = 2L * sms, cap_d = (nvec4 + 32 * GM32_WARPS - 1) / (32 * GM32_WARPS);
+        W.gd32 = (int)std::max(1L, std::min(want_d, cap_d));
+        const long want_u = 5L * sms - 1, cap_u = (nvec4 + 255) / 256;   // + the control block: 5 per SM
+        W.gu32 = (int)std::max(1L, std::min(want_u, cap_u));
+    }
     if (!W.partials)
         if ((s = dg_realloc(h, (void**)&W.partials, sizeof(double) * (DG_MAXM + 2) * 4096)) != DG_OK) return s;
     if (!W.st) {
@@ -757,6 +966,7 @@ static dg_status gmres_f64(dg_handle* h, const double* F, double* x, dg_solve_in
 }
 
 extern "C" dg_status dg_gmres_solve(dg_handle* h, const double* F, double* x, dg_solve_info* info) {
+    DG_WS_SCOPE(h, DG_WS_SOLVER);
     if (!h || !x) return DG_ERR_INVALID_ARG;
     h->basis = nullptr;
     if (!h->assembled) return dg_fail(h, DG_ERR_STATE, "not assembled");
@@ -894,6 +1104,7 @@ static dg_status mixed_run(dg_handle* h, const TA* Alo, const double* F, double*
 
 extern "C" dg_status dg_mixed_solve(dg_handle* h, int inner_dtype, int inner_m, double inner_tol, int max_outer,
                                     const double* F, double* x, dg_solve_info* info) {
+    DG_WS_SCOPE(h, DG_WS_SOLVER);
     if (!h || !x) return DG_ERR_INVALID_ARG;
     h->basis = nullptr;
     if (!h->assembled) return dg_fail(h, DG_ERR_STATE, "not assembled");
@@ -1037,6 +1248,7 @@ static dg_status gmres_ir_run(dg_handle* h, const TA* Alo, const double* F, doub
 
 extern "C" dg_status dg_gmres_ir_solve(dg_handle* h, int inner_dtype, int inner_m, double inner_tol, int max_outer,
                                        const double* F, double* x, dg_solve_info* info) {
+    DG_WS_SCOPE(h, DG_WS_SOLVER);
     if (!h || !x) return DG_ERR_INVALID_ARG;
     h->basis = nullptr;
     if (!h->assembled) return dg_fail(h, DG_ERR_STATE, "not assembled");
@@ -1124,11 +1336,19 @@ static dg_status profile_arnoldi(dg_handle* h, int which, int j, int reps, doubl
         k_prof_state<<<1, 32, 0, h->stream>>>(W.st, j, m);
         DG_CK(h, cudaEventRecord(e0, h->stream));
         const long nvec = (long)W.ld / Vec<TV>::W;
-        if (which == DG_PROF_DOTS)
-            k_gm_dots<TV><<<W.gsm, dim3(GM_TX, GM_TY), 0, h->stream>>>((const TV*)W.V, (long)W.ld, nvec, W.st,
-                                                                         W.partials, 1);
-        else
-            k_gm_update<TV><<<W.gx + 1, 256, 0, h->stream>>>((TV*)W.V, (long)W.ld, nvec, W.st, 1);
+        if constexpr (sizeof(TV) == 4) {
+            if (which == DG_PROF_DOTS)
+                k_gm_dots32<<<W.gd32, GM32_THREADS, 0, h->stream>>>((const float*)W.V, (long)W.ld, nvec, W.st,
+                                                                  (float2*)W.partials, 1);
+            else
+                k_gm_update32<<<W.gu32 + 1, 256, 0, h->stream>>>((float*)W.V, (long)W.ld, nvec, W.st, 1);
+        } else {
+            if (which == DG_PROF_DOTS)
+                k_gm_dots<TV><<<W.gsm, dim3(GM_TX, GM_TY), 0, h->stream>>>((const TV*)W.V, (long)W.ld, nvec, W.st,
+                                                                             W.partials, 1);
+            else
+                k_gm_update<TV><<<W.gx + 1, 256, 0, h->stream>>>((TV*)W.V, (long)W.ld, nvec, W.st, 1);
+        }
         DG_CK(h, cudaEventRecord(e1, h->stream));
         DG_CK(h, cudaEventSynchronize(e1));
         float ms = 0.f;
@@ -1143,6 +1363,7 @@ static dg_status profile_arnoldi(dg_handle* h, int which, int j, int reps, doubl
 }
 
 extern "C" dg_status dg_profile_kernel(dg_handle* h, int which, int dtype, int param, int reps, double* avg_ms) {
+    DG_WS_SCOPE(h, DG_WS_SOLVER);
     if (!h || !avg_ms || reps < 1) return DG_ERR_INVALID_ARG;
     if (!h->assembled) return dg_fail(h, DG_ERR_STATE, "not assembled");
     if (which != DG_PROF_DOTS && which != DG_PROF_UPDATE) return dg_fail(h, DG_ERR_INVALID_ARG, "which");

@@ -25,18 +25,98 @@ dg_status dg_cuda_fail(dg_handle* h, cudaError_t e, const char* what) {
     return DG_ERR_CUDA;
 }
 
+// ---------------------------------------------------------------------------
+// device memory: cudaMalloc, the caller's allocator or a caller arena
+// ---------------------------------------------------------------------------
+static const size_t kGranule = 256;
+
+void* DgArena::take(size_t bytes) {
+    const size_t need = (bytes + kGranule - 1) / kGranule * kGranule;
+    for (auto it = free_ranges.begin(); it != free_ranges.end(); ++it) {
+        if (it->second < need) continue;
+        const size_t off = it->first, len = it->second;
+        free_ranges.erase(it);
+        if (len > need) free_ranges[off + need] = len - need;
+        used[off] = need;
+        return (void*)(base + off);
+    }
+    return nullptr;
+}
+
+bool DgArena::give_back(void* p) {
+    const size_t off = (size_t)((uintptr_t)p - base);
+    auto u = used.find(off);
+    if (u == used.end()) return false;
+    size_t start = off, len = u->second;
+    used.erase(u);
+    auto nx = free_ranges.lower_bound(start);
+    if (nx != free_ranges.end() && nx->first == start + len) {   // merge with the next free range
+        len += nx->second;
+        nx = free_ranges.erase(nx);
+    }
+    if (nx != free_ranges.begin()) {                              // and with the previous one
+        auto pv = std::prev(nx);
+        if (pv->first + pv->second == start) {
+            start = pv->first;
+            len += pv->second;
+            free_ranges.erase(pv);
+        }
+    }
+    free_ranges[start] = len;
+    return true;
+}
+
+dg_status dg_dev_alloc(dg_handle* h, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) return DG_OK;
+    if (h->arena) {
+        *p = h->arena->take(bytes);
+        if (!*p) return dg_fail(h, DG_ERR_NOMEM, "the caller's arena has no free range of " + std::to_string(bytes) +
+                                                     " bytes (dg_workspace_size(DG_WS_PEAK) sizes it)");
+    } else if (h->ualloc) {
+        *p = h->ualloc(h->uctx, bytes, h->device, (void*)h->stream);
+        if (!*p) return dg_fail(h, DG_ERR_NOMEM, "the caller's allocator returned NULL");
+        if (((uintptr_t)*p & (kGranule - 1)) != 0) {
+            h->ufree(h->uctx, *p, bytes, h->device, (void*)h->stream);
+            *p = nullptr;
+            return dg_fail(h, DG_ERR_INVALID_ARG, "the caller's allocator returned memory not aligned to 256 bytes");
+        }
+    } else {
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e != cudaSuccess) {
+            *p = nullptr;
+            return dg_cuda_fail(h, e, "cudaMalloc");
+        }
+    }
+    const int cat = (h->ws_cat > 0 && h->ws_cat < DG_WS_PEAK) ? h->ws_cat : DG_WS_SCRATCH;
+    h->held[*p] = DgMemRec{bytes, cat};
+    h->held_bytes[cat] += bytes;
+    h->held_bytes[DG_WS_TOTAL] += bytes;
+    if (h->held_bytes[DG_WS_TOTAL] > h->peak_bytes) h->peak_bytes = h->held_bytes[DG_WS_TOTAL];
+    return DG_OK;
+}
+
+void dg_dev_free(dg_handle* h, void* p) {
+    if (!p) return;
+    auto it = h->held.find(p);
+    size_t bytes = 0;
+    if (it != h->held.end()) {
+        bytes = it->second.bytes;
+        h->held_bytes[it->second.cat] -= bytes;
+        h->held_bytes[DG_WS_TOTAL] -= bytes;
+        h->held.erase(it);
+    }
+    if (h->arena) h->arena->give_back(p);
+    else if (h->ufree) h->ufree(h->uctx, p, bytes, h->device, (void*)h->stream);
+    else cudaFree(p);
+}
+
 dg_status dg_realloc(dg_handle* h, void** p, size_t bytes) {
     if (*p) {
-        cudaFree(*p);
+        dg_dev_free(h, *p);
         *p = nullptr;
     }
-    if (bytes == 0) return DG_OK;
-    cudaError_t e = cudaMalloc(p, bytes);
-    if (e != cudaSuccess) {
-        *p = nullptr;
-        return dg_cuda_fail(h, e, "cudaMalloc");
-    }
-    return DG_OK;
+    return dg_dev_alloc(h, p, bytes);
 }
 
 dg_status dg_ensure(dg_handle* h, void** p, size_t* cap, size_t bytes) {
@@ -48,29 +128,86 @@ dg_status dg_ensure(dg_handle* h, void** p, size_t* cap, size_t bytes) {
 
 dg_status dg_scratch(dg_handle* h, size_t bytes) {
     if (h->scratch_bytes >= bytes) return DG_OK;
+    DG_WS_SCOPE(h, DG_WS_SCRATCH);
     dg_status s = dg_realloc(h, (void**)&h->scratch, bytes);
     h->scratch_bytes = s == DG_OK ? bytes : 0;
     return s;
+}
+
+// Switch the memory source of a fresh handle: only the flag block may be held.
+static dg_status switch_source(dg_handle* h, dg_alloc_fn a, dg_free_fn f, void* ctx, DgArena* arena) {
+    if (h->held.size() > 1 || (h->held.size() == 1 && h->held.begin()->first != (void*)h->dflag)) {
+        delete arena;
+        return dg_fail(h, DG_ERR_STATE, "the memory source can only be set right after dg_create, before any call "
+                                        "that allocates");
+    }
+    DG_CK(h, cudaSetDevice(h->device));
+    if (h->stream) DG_CK(h, cudaStreamSynchronize(h->stream));
+    dg_dev_free(h, h->dflag);
+    h->dflag = nullptr;
+    delete h->arena;
+    h->arena = arena;
+    h->ualloc = a;
+    h->ufree = f;
+    h->uctx = ctx;
+    h->peak_bytes = 0;
+    DG_WS_SCOPE(h, DG_WS_SCRATCH);
+    dg_status s = dg_dev_alloc(h, (void**)&h->dflag, 64);
+    if (s != DG_OK) return s;
+    DG_CK(h, cudaMemsetAsync(h->dflag, 0, 64, h->stream));
+    return DG_OK;
+}
+
+extern "C" dg_status dg_set_allocator(dg_handle* h, dg_alloc_fn alloc_fn, dg_free_fn free_fn, void* ctx) {
+    if (!h) return DG_ERR_INVALID_ARG;
+    if ((alloc_fn == nullptr) != (free_fn == nullptr))
+        return dg_fail(h, DG_ERR_INVALID_ARG, "alloc_fn and free_fn are given together (both NULL: cudaMalloc)");
+    return switch_source(h, alloc_fn, free_fn, ctx, nullptr);
+}
+
+extern "C" dg_status dg_set_arena(dg_handle* h, void* base, size_t bytes) {
+    if (!h) return DG_ERR_INVALID_ARG;
+    if (!base || ((uintptr_t)base & (kGranule - 1)) != 0 || bytes < kGranule)
+        return dg_fail(h, DG_ERR_INVALID_ARG, "the arena needs a base aligned to 256 bytes and at least 256 bytes");
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, base) != cudaSuccess || at.type != cudaMemoryTypeDevice ||
+        at.device != h->device) {
+        cudaGetLastError();
+        return dg_fail(h, DG_ERR_INVALID_ARG, "the arena must be device memory on the handle's device");
+    }
+    DgArena* a = new DgArena();
+    a->base = (uintptr_t)base;
+    a->size = bytes / kGranule * kGranule;
+    a->free_ranges[0] = a->size;
+    return switch_source(h, nullptr, nullptr, nullptr, a);
+}
+
+extern "C" size_t dg_workspace_size(const dg_handle* h, int what) {
+    if (!h || what < 0 || what > DG_WS_PEAK) return 0;
+    if (what == DG_WS_PEAK) return h->peak_bytes;
+    return h->held_bytes[what];
 }
 
 static void free_all(dg_handle* h) {
     void* ptrs[] = {h->nodes, h->elems, h->geo, h->nbr, h->nface, h->ftype, h->bidx, h->bedge, h->tab,
                     h->A64, h->A32, h->A16, h->F, h->Binv64, h->Binv32, h->Binv16, h->scratch, h->dflag, h->mx_buf,
                     h->Ah64, h->Ah32, h->G64, h->G32, h->J64, h->nl_buf};
-    for (void* p : ptrs)
-        if (p) cudaFree(p);
-    for (GmresWork& w : h->gw) dg_gmres_free(&w);
+    for (void* p : ptrs) dg_dev_free(h, p);
+    for (GmresWork& w : h->gw) dg_gmres_free(h, &w);
     {
         MlpState& S = h->mlp;
         for (void* p : {(void*)S.theta, (void*)S.wr, (void*)S.m, (void*)S.v, (void*)S.grad, (void*)S.wbf,
                         (void*)S.bias, (void*)S.X, (void*)S.T, (void*)S.ws, (void*)S.on})
-            if (p) cudaFree(p);
+            dg_dev_free(h, p);
     }
-    for (void* p : {(void*)h->b_inst, (void*)h->b_icoef, h->b_dev})
-        if (p) cudaFree(p);
+    for (void* p : {(void*)h->b_inst, (void*)h->b_icoef, h->b_dev}) dg_dev_free(h, p);
     if (h->b_host) cudaFreeHost(h->b_host);
     if (h->b_graph) cudaGraphExecDestroy(h->b_graph);
     free(h->b_elem_start);
+    // anything left (none expected) goes back to the source too
+    while (!h->held.empty()) dg_dev_free(h, h->held.begin()->first);
+    delete h->arena;
+    h->arena = nullptr;
 }
 
 extern "C" const char* dg_status_string(dg_status s) {
@@ -128,6 +265,12 @@ extern "C" dg_status dg_create(dg_handle** out, int device, void* stream) {
     if (dg_realloc(h, (void**)&h->dflag, 64) != DG_OK) {
         delete h;
         return DG_ERR_NOMEM;
+    }
+    // the allocation-free entry point's scratch address (dg_noalloc.cu)
+    if (dg_noalloc_prepare(h) != DG_OK) {
+        cudaFree(h->dflag);
+        delete h;
+        return DG_ERR_CUDA;
     }
     *out = h;
     return DG_OK;
@@ -410,6 +553,7 @@ static std::string mesh_flag_text(int f) {
 
 extern "C" dg_status dg_mesh_upload(dg_handle* h, const double* nodes, int nv, const int* elems, int ne,
                                     const int* dirichlet, int nd, const int* neumann, int nn) {
+    DG_WS_SCOPE(h, DG_WS_MESH);
     if (!h) return DG_ERR_INVALID_ARG;
     if (!nodes || !elems || nv < 3 || ne < 1 || nd < 0 || nn < 0 || (nd > 0 && !dirichlet) ||
         (nn > 0 && !neumann) || ne > (1 << 27))
@@ -544,6 +688,18 @@ __global__ void k_points_elem(const double* __restrict__ geo, int ne, const doub
     xy[2 * g + 1] = y0 + geo[G_J10 * (size_t)ne + K] * rr + geo[G_J11 * (size_t)ne + K] * ss;
 }
 
+// Points of every element face: (K, f, q) at ((K*3 + f)*nq + q), each face run
+// from local vertex f to f+1 (counter-clockwise around K).
+__global__ void k_points_face(const double* __restrict__ geo, int ne, const double* __restrict__ fr,
+                              const double* __restrict__ fs, int nq, double* xy) {
+    long g = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= (long)ne * 3 * nq) return;
+    int K = (int)(g / (3 * nq)), fq = (int)(g - (long)K * 3 * nq);
+    double rr = fr[fq], ss = fs[fq];
+    xy[2 * g] = geo[G_X0 * (size_t)ne + K] + geo[G_J00 * (size_t)ne + K] * rr + geo[G_J01 * (size_t)ne + K] * ss;
+    xy[2 * g + 1] = geo[G_Y0 * (size_t)ne + K] + geo[G_J10 * (size_t)ne + K] * rr + geo[G_J11 * (size_t)ne + K] * ss;
+}
+
 __global__ void k_points_bdry(const double* __restrict__ geo, int ne, const int* __restrict__ bedge, int nbe,
                               const double* __restrict__ fr, const double* __restrict__ fs, int nq, double* xy,
                               double* normals, int* type, const int* __restrict__ ftype) {
@@ -572,6 +728,7 @@ __global__ void k_points_bdry(const double* __restrict__ geo, int ne, const int*
 }
 
 extern "C" dg_status dg_quad_points(dg_handle* h, int which, double* xy) {
+    DG_WS_SCOPE(h, DG_WS_MESH);
     if (!h || !xy) return DG_ERR_INVALID_ARG;
     if (!h->mesh_ok) return dg_fail(h, DG_ERR_STATE, "no mesh uploaded");
     dg_status s = dg_ensure_tables(h, h->p.degree);
@@ -590,6 +747,10 @@ extern "C" dg_status dg_quad_points(dg_handle* h, int which, double* xy) {
             k_points_bdry<<<(unsigned)((n + T - 1) / T), T, 0, h->stream>>>(
                 h->geo, h->ne, h->bedge, h->nbe, h->tab + L.face_r, h->tab + L.face_s, L.nq, xy, nullptr, nullptr,
                 h->ftype);
+    } else if (which == DG_POINTS_FACE) {
+        long n = (long)h->ne * 3 * L.nq;
+        k_points_face<<<(unsigned)((n + T - 1) / T), T, 0, h->stream>>>(h->geo, h->ne, h->tab + L.face_r,
+                                                                         h->tab + L.face_s, L.nq, xy);
     } else {
         return dg_fail(h, DG_ERR_INVALID_ARG, "which");
     }
@@ -599,6 +760,7 @@ extern "C" dg_status dg_quad_points(dg_handle* h, int which, double* xy) {
 }
 
 extern "C" dg_status dg_boundary_info(dg_handle* h, double* normals, int* type) {
+    DG_WS_SCOPE(h, DG_WS_MESH);
     if (!h || (!normals && !type)) return DG_ERR_INVALID_ARG;
     if (!h->mesh_ok) return dg_fail(h, DG_ERR_STATE, "no mesh uploaded");
     dg_status s = dg_ensure_tables(h, h->p.degree);

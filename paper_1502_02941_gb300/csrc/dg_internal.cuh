@@ -22,7 +22,10 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
+
+#include <map>
 #include <string>
+#include <unordered_map>
 
 #include "dg.h"
 
@@ -107,6 +110,26 @@ struct GmresWork {
     int nodes = 0;
     int gx = 0;    // grid of the 1-D vector kernels (4 blocks of 256 per SM)
     int gsm = 0;   // grid of the multi-dot kernel (one 1024-thread block per SM)
+    int gd32 = 0;  // grid of the f32 multi-dot (two 512-thread blocks per SM)
+    int gu32 = 0;  // streaming blocks of the f32 update (plus its control block)
+};
+
+// A caller-supplied device buffer that the handle carves its arrays from
+// (dg_set_arena): first fit over a list of free ranges, 256-byte granules,
+// neighbouring free ranges merged on release.
+struct DgArena {
+    uintptr_t base = 0;
+    size_t size = 0;
+    std::map<size_t, size_t> free_ranges;         // offset -> length
+    std::unordered_map<size_t, size_t> used;      // offset -> length
+    void* take(size_t bytes);
+    bool give_back(void* p);
+};
+
+// One live device allocation of a handle.
+struct DgMemRec {
+    size_t bytes;
+    int cat;       // DG_WS_* category
 };
 
 struct dg_handle {
@@ -216,7 +239,32 @@ struct dg_handle {
     size_t cap_J64 = 0;
     double* nl_buf = nullptr;
     size_t cap_nl = 0;
+
+    // device memory source and bookkeeping (dg_host.cu): cudaMalloc by
+    // default, else the caller's allocator (dg_set_allocator) or a caller
+    // arena (dg_set_arena); every live allocation with its size and category
+    dg_alloc_fn ualloc = nullptr;
+    dg_free_fn ufree = nullptr;
+    void* uctx = nullptr;
+    DgArena* arena = nullptr;
+    std::unordered_map<void*, DgMemRec> held;
+    size_t held_bytes[DG_WS_PEAK] = {0, 0, 0, 0, 0, 0, 0};   // [0] = total
+    size_t peak_bytes = 0;
+    int ws_cat = DG_WS_SCRATCH;    // category of allocations made now
 };
+
+// Category of the allocations made while a scope object lives (restored on exit).
+struct DgWsScope {
+    dg_handle* h;
+    int prev;
+    DgWsScope(dg_handle* hh, int cat) : h(hh), prev(hh ? hh->ws_cat : 0) {
+        if (h) h->ws_cat = cat;
+    }
+    ~DgWsScope() {
+        if (h) h->ws_cat = prev;
+    }
+};
+#define DG_WS_SCOPE(h, cat) DgWsScope dg_ws_scope__((h), (cat))
 
 // error helpers (dg_host.cu)
 dg_status dg_fail(dg_handle* h, dg_status s, const std::string& msg);
@@ -231,9 +279,15 @@ dg_status dg_cuda_fail(dg_handle* h, cudaError_t e, const char* what);
 // vector arguments are read with 16-byte loads
 static inline bool dg_aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
+// Device memory of a handle, from its memory source, tagged with h->ws_cat.
+dg_status dg_dev_alloc(dg_handle* h, void** p, size_t bytes);
+void dg_dev_free(dg_handle* h, void* p);   // NULL is accepted
 // allocation helper: frees *p (if any) and allocates bytes
 dg_status dg_realloc(dg_handle* h, void** p, size_t bytes);
 dg_status dg_scratch(dg_handle* h, size_t bytes);   // ensure h->scratch >= bytes
+// device address of the allocation-free entry point's scratch array, looked
+// up at handle creation (dg_noalloc.cu)
+dg_status dg_noalloc_prepare(dg_handle* h);
 // keep *p if its capacity *cap already holds bytes, else reallocate
 dg_status dg_ensure(dg_handle* h, void** p, size_t* cap, size_t bytes);
 
@@ -249,7 +303,7 @@ dg_status dg_launch_assemble(dg_handle* h, const dg_coeffs* c, double kappa, dou
 dg_status dg_launch_apply(dg_handle* h, int dtype, const void* x, void* y);
 dg_status dg_launch_bj_setup(dg_handle* h);
 dg_status dg_launch_bj_apply(dg_handle* h, int dtype, const void* r, void* z, const double* scale);
-void dg_gmres_free(GmresWork* w);
+void dg_gmres_free(dg_handle* h, GmresWork* w);
 
 // Launch on h->stream; with `pdl` the kernel carries the programmatic
 // stream-serialisation attribute, so it may be scheduled while its predecessor

@@ -741,6 +741,7 @@ static dg_status mlp_refresh(dg_handle* h) {
 }
 
 extern "C" dg_status dg_mlp_init(dg_handle* h, uint64_t seed) {
+    DG_WS_SCOPE(h, DG_WS_LEARNED);
     if (!h) return DG_ERR_INVALID_ARG;
     DG_CK(h, cudaSetDevice(h->device));
     const int nb = dg_nb(h->p.degree);
@@ -758,6 +759,7 @@ extern "C" dg_status dg_mlp_init(dg_handle* h, uint64_t seed) {
 }
 
 extern "C" dg_status dg_mlp_set_weights(dg_handle* h, const float* theta, int64_t n) {
+    DG_WS_SCOPE(h, DG_WS_LEARNED);
     if (!h || !theta) return DG_ERR_INVALID_ARG;
     DG_CK(h, cudaSetDevice(h->device));
     const int nb = dg_nb(h->p.degree);
@@ -804,18 +806,19 @@ static dg_status mlp_rows_from(dg_handle* h, const double* r, double* e) {
         long cap = S.cap ? S.cap : 65536;
         while (cap < need) cap *= 2;
         float *X = nullptr, *T = nullptr;
-        if (cudaMalloc(&X, sizeof(float) * cap * S.din) != cudaSuccess) return dg_fail(h, DG_ERR_NOMEM, "rows");
-        if (cudaMalloc(&T, sizeof(float) * cap * nb) != cudaSuccess) {
-            cudaFree(X);
-            return dg_fail(h, DG_ERR_NOMEM, "rows");
+        dg_status s = dg_dev_alloc(h, (void**)&X, sizeof(float) * cap * S.din);
+        if (s != DG_OK) return s;
+        if ((s = dg_dev_alloc(h, (void**)&T, sizeof(float) * cap * nb)) != DG_OK) {
+            dg_dev_free(h, X);
+            return s;
         }
         if (S.rows) {
             DG_CK(h, cudaMemcpyAsync(X, S.X, sizeof(float) * S.rows * S.din, cudaMemcpyDeviceToDevice, h->stream));
             DG_CK(h, cudaMemcpyAsync(T, S.T, sizeof(float) * S.rows * nb, cudaMemcpyDeviceToDevice, h->stream));
         }
         DG_CK(h, cudaStreamSynchronize(h->stream));
-        cudaFree(S.X);
-        cudaFree(S.T);
+        dg_dev_free(h, S.X);
+        dg_dev_free(h, S.T);
         S.X = X;
         S.T = T;
         S.cap = cap;
@@ -846,6 +849,7 @@ static dg_status mlp_rows_from(dg_handle* h, const double* r, double* e) {
 }
 
 extern "C" dg_status dg_mlp_collect(dg_handle* h, const double* F, const double* xk) {
+    DG_WS_SCOPE(h, DG_WS_LEARNED);
     if (!h || !xk) return DG_ERR_INVALID_ARG;
     dg_status s = mlp_check_collect(h);
     if (s != DG_OK) return s;
@@ -864,6 +868,7 @@ extern "C" dg_status dg_mlp_collect(dg_handle* h, const double* F, const double*
 }
 
 extern "C" dg_status dg_mlp_collect_basis(dg_handle* h, int nvec) {
+    DG_WS_SCOPE(h, DG_WS_LEARNED);
     if (!h || nvec < 1) return DG_ERR_INVALID_ARG;
     dg_status s = mlp_check_collect(h);
     if (s != DG_OK) return s;
@@ -893,6 +898,7 @@ static dg_status mlp_ws(dg_handle* h, int B) {
 }
 
 extern "C" dg_status dg_mlp_train(dg_handle* h, int steps, int batch_rows, float lr, uint64_t seed, float* loss) {
+    DG_WS_SCOPE(h, DG_WS_LEARNED);
     if (!h || steps < 1 || batch_rows < 1 || !(lr > 0.f)) return DG_ERR_INVALID_ARG;
     MlpState& S = h->mlp;
     if (!S.ready) return dg_fail(h, DG_ERR_STATE, "dg_mlp_init first");
@@ -936,6 +942,7 @@ extern "C" dg_status dg_mlp_train(dg_handle* h, int steps, int batch_rows, float
 // T [rows][nb] f32); host outputs.
 extern "C" dg_status dg_mlp_loss_grad(dg_handle* h, const float* X, const float* T, int rows, double* loss,
                                       float* grad) {
+    DG_WS_SCOPE(h, DG_WS_LEARNED);
     if (!h || !X || !T || rows < 1) return DG_ERR_INVALID_ARG;
     MlpState& S = h->mlp;
     if (!S.ready) return dg_fail(h, DG_ERR_STATE, "dg_mlp_init first");
@@ -958,6 +965,7 @@ extern "C" dg_status dg_mlp_loss_grad(dg_handle* h, const float* X, const float*
 
 // Tensor-core forward on caller feature rows: Y [rows][nb] (device f32).
 extern "C" dg_status dg_mlp_forward(dg_handle* h, const float* X, int rows, float* Y) {
+    DG_WS_SCOPE(h, DG_WS_LEARNED);
     if (!h || !X || !Y || rows < 1) return DG_ERR_INVALID_ARG;
     MlpState& S = h->mlp;
     if (!S.packed) return dg_fail(h, DG_ERR_STATE, "dg_mlp_init first");

@@ -28,23 +28,69 @@
 
 static __device__ __align__(256) double dg_noalloc_scratch[DG_NOALLOC_PARTIALS + 1];
 
-// Device address of the array for each device ordinal, looked up once per
-// device (in host code the symbol name is only a host-side stand-in).
+// Device address of the array for each device ordinal, with the id of the
+// CUDA context it was looked up in (in host code the symbol name is only a
+// host-side stand-in).  The address is looked up when a handle is created on
+// the device (dg_create calls dg_noalloc_prepare with the device current),
+// which also makes the runtime load this file's module, and so allocate the
+// array, at that point rather than in the first dg_l2_error_noalloc call.  A
+// call whose current context differs from the one of the cached address (the
+// device was reset, or its primary context released and created anew) looks
+// the address up again before launching anything.
 static std::mutex g_noalloc_mu;
 static double* g_noalloc_addr[DG_NOALLOC_MAX_DEVICES];
+static unsigned long long g_noalloc_ctx[DG_NOALLOC_MAX_DEVICES];
 
+// Id of the current CUDA context through the driver entry points the runtime
+// exposes (no link against the driver library); false if unavailable.
+static bool current_context_id(unsigned long long* id) {
+    typedef int (*ctx_current_fn)(void**);
+    typedef int (*ctx_id_fn)(void*, unsigned long long*);
+    static ctx_current_fn get_current = nullptr;
+    static ctx_id_fn get_id = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q2 == cudaDriverEntryPointSuccess) {
+            get_current = (ctx_current_fn)f1;
+            get_id = (ctx_id_fn)f2;
+        }
+    }
+    if (!get_current || !get_id) return false;
+    void* ctx = nullptr;
+    if (get_current(&ctx) != 0 || !ctx) return false;
+    return get_id(ctx, id) == 0;
+}
+
+// Look the array's address up for h->device (current) unless the cached one
+// belongs to the current context.
 static dg_status noalloc_scratch(dg_handle* h, double** out) {
     if (h->device < 0 || h->device >= DG_NOALLOC_MAX_DEVICES)
         return dg_fail(h, DG_ERR_INVALID_ARG, "device ordinal too large for the allocation-free entry point");
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[h->device]) {
+    unsigned long long ctx = 0;
+    const bool known = current_context_id(&ctx);
+    if (!g_noalloc_addr[h->device] || !known || g_noalloc_ctx[h->device] != ctx) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, dg_noalloc_scratch);   // h->device is current
         if (e != cudaSuccess) return dg_cuda_fail(h, e, "cudaGetSymbolAddress(dg_noalloc_scratch)");
         g_noalloc_addr[h->device] = (double*)p;
+        g_noalloc_ctx[h->device] = known ? ctx : 0;
     }
     *out = g_noalloc_addr[h->device];
     return DG_OK;
+}
+
+// Set-up at handle creation (h->device current): resolve the address once.
+dg_status dg_noalloc_prepare(dg_handle* h) {
+    double* p = nullptr;
+    return noalloc_scratch(h, &p);
 }
 
 // One element per thread: block b writes sum over its elements of

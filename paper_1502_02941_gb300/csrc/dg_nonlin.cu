@@ -157,6 +157,7 @@ static dg_status nonlin_checks(dg_handle* h, int p, double c) {
 }
 
 extern "C" dg_status dg_nonlinear_global(dg_handle* h, int p, double c, const double* x, double* H, double* HJ) {
+    DG_WS_SCOPE(h, DG_WS_SOLVER);
     if (!h || !x || !H) return DG_ERR_INVALID_ARG;
     dg_status s = nonlin_checks(h, p, c);
     if (s != DG_OK) return s;
@@ -182,6 +183,7 @@ struct OperatorSwap {
 
 extern "C" dg_status dg_newton_solve(dg_handle* h, int p, double c, int max_newton, double lin_tol, const double* F,
                                      double* x, dg_solve_info* info) {
+    DG_WS_SCOPE(h, DG_WS_SOLVER);
     if (!h || !x) return DG_ERR_INVALID_ARG;
     h->basis = nullptr;
     dg_status s = nonlin_checks(h, p, c);

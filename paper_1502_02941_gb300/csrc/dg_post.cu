@@ -203,6 +203,7 @@ __global__ void __launch_bounds__(1024) k_dense_lu_solve(double* M, double* b, i
 }
 
 extern "C" dg_status dg_dense_solve(dg_handle* h, const double* F, double* x) {
+    DG_WS_SCOPE(h, DG_WS_SOLVER);
     if (!h || !x) return DG_ERR_INVALID_ARG;
     if (!h->assembled || !h->A64) return dg_fail(h, DG_ERR_STATE, "not assembled with f64 blocks");
     DG_CK(h, cudaSetDevice(h->device));

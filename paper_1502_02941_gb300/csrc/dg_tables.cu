@@ -234,6 +234,7 @@ void dg_build_tables(int k, double* T) {
 }
 
 dg_status dg_ensure_tables(dg_handle* h, int k) {
+    DG_WS_SCOPE(h, DG_WS_MESH);
     if (h->tab_k == k && h->tab) return DG_OK;
     TabLayout L = dg_table_layout(k);
     std::vector<double> host(L.total);

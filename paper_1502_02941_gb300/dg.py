@@ -27,8 +27,9 @@ DG_NIPG, DG_SIPG, DG_IIPG = 1, 2, 3
 DG_F64, DG_F32, DG_BF16 = 0, 1, 2
 DG_STORE_F64, DG_STORE_F32, DG_STORE_BF16 = 1, 2, 4
 DG_PRECOND_NONE, DG_PRECOND_BLOCK_JACOBI, DG_PRECOND_MLP, DG_PRECOND_SCHWARZ = 0, 1, 2, 3
-DG_POINTS_VOLUME, DG_POINTS_BOUNDARY, DG_POINTS_ERROR = 0, 1, 2
+DG_POINTS_VOLUME, DG_POINTS_BOUNDARY, DG_POINTS_ERROR, DG_POINTS_FACE = 0, 1, 2, 3
 DG_PROF_DOTS, DG_PROF_UPDATE = 1, 2
+DG_WS_TOTAL, DG_WS_MESH, DG_WS_OPERATOR, DG_WS_PRECOND, DG_WS_SOLVER, DG_WS_LEARNED, DG_WS_SCRATCH, DG_WS_PEAK = range(8)
 
 c_int32, c_int64, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
 
@@ -43,7 +44,8 @@ class dg_coeffs(ctypes.Structure):
     _fields_ = [("eps", c_double), ("alpha", c_double), ("b", c_double * 6),
                 ("f", c_void_p), ("f_const", c_double),
                 ("gD", c_void_p), ("gD_const", c_double),
-                ("gN", c_void_p), ("gN_const", c_double)]
+                ("gN", c_void_p), ("gN_const", c_double),
+                ("eps_q", c_void_p), ("eps_f", c_void_p)]
 
 
 class dg_info(ctypes.Structure):
@@ -57,9 +59,16 @@ class dg_solve_info(ctypes.Structure):
                 ("status", c_int32), ("relres", c_double)]
 
 
+# dg_alloc_fn / dg_free_fn of include/dg.h
+DG_ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, c_void_p, ctypes.c_size_t, ctypes.c_int, c_void_p)
+DG_FREE_FN = ctypes.CFUNCTYPE(None, c_void_p, c_void_p, ctypes.c_size_t, ctypes.c_int, c_void_p)
+
 _lib = None
 
 _SIGS = {
+    "dg_set_allocator": (ctypes.c_int, [c_void_p, DG_ALLOC_FN, DG_FREE_FN, c_void_p]),
+    "dg_set_arena": (ctypes.c_int, [c_void_p, c_void_p, ctypes.c_size_t]),
+    "dg_workspace_size": (ctypes.c_size_t, [c_void_p, ctypes.c_int]),
     "dg_create": (ctypes.c_int, [ctypes.POINTER(c_void_p), ctypes.c_int, c_void_p]),
     "dg_destroy": (ctypes.c_int, [c_void_p]),
     "dg_set_stream": (ctypes.c_int, [c_void_p, c_void_p]),
@@ -101,6 +110,11 @@ _SIGS = {
                                       c_void_p, c_void_p, c_void_p, c_void_p]),
     "dg_batch_gmres_ir_solve": (ctypes.c_int, [c_void_p, ctypes.c_int, ctypes.c_int, c_double, ctypes.c_int,
                                                c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "dg_batch_group_solve": (ctypes.c_int, [c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, c_double,
+                                            ctypes.c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "dg_batch_group_gmres_ir_solve": (ctypes.c_int, [c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, c_double,
+                                                     ctypes.c_int, c_void_p, c_void_p, c_void_p, c_void_p,
+                                                     c_void_p]),
     "dg_mesh_refine": (ctypes.c_int, [c_void_p, ctypes.c_int, c_void_p, ctypes.c_int, c_void_p, ctypes.c_int,
                                       c_void_p, ctypes.c_int, c_void_p, ctypes.POINTER(ctypes.c_int), c_void_p,
                                       ctypes.POINTER(ctypes.c_int), c_void_p, ctypes.POINTER(ctypes.c_int),
@@ -160,25 +174,74 @@ def status_name(s):
     return load().dg_status_string(int(s)).decode()
 
 
-def _ptr(x):
-    """Pointer of a numpy array (host data), a torch tensor (device data: the
-    kernels dereference it, so a host tensor is refused here rather than left
-    to fault on the GPU), an int or None."""
-    if x is None:
-        return None
-    if isinstance(x, int):
+_TORCH_DTYPES = {"f64": "torch.float64", "f32": "torch.float32", "bf16": "torch.bfloat16", "i32": "torch.int32"}
+_NP_DTYPES = {"f64": np.float64, "f32": np.float32, "i32": np.int32}
+
+
+def _host(x, n=None, dtype=None, what="host argument"):
+    """Pointer of HOST data: a C-contiguous numpy array (or a contiguous CPU
+    torch tensor), an integer address (passed through unchecked) or None.  A
+    CUDA tensor is refused: the library reads or writes this memory from the
+    CPU.  n: least number of elements; dtype: "f64" / "f32" / "i32"."""
+    if x is None or isinstance(x, int):
         return x
     if isinstance(x, np.ndarray):
         if not x.flags["C_CONTIGUOUS"]:
-            raise ValueError("array must be C-contiguous")
+            raise ValueError(f"{what}: array must be C-contiguous")
+        if dtype is not None and x.dtype != _NP_DTYPES[dtype]:
+            raise ValueError(f"{what}: numpy dtype {_NP_DTYPES[dtype].__name__} expected, got {x.dtype}")
+        if n is not None and x.size < n:
+            raise ValueError(f"{what}: {n} elements needed, the array has {x.size}")
         return x.ctypes.data
     if hasattr(x, "data_ptr"):
+        if x.is_cuda:
+            raise ValueError(f"{what}: host memory is expected here (a numpy array), not a CUDA tensor")
         if not x.is_contiguous():
-            raise ValueError("tensor must be contiguous")
-        if not x.is_cuda:
-            raise ValueError("a device (CUDA) tensor is expected here; host data goes in numpy arrays")
+            raise ValueError(f"{what}: tensor must be contiguous")
+        if dtype is not None and str(x.dtype) != _TORCH_DTYPES[dtype]:
+            raise ValueError(f"{what}: {_TORCH_DTYPES[dtype]} expected, got {x.dtype}")
+        if n is not None and x.numel() < n:
+            raise ValueError(f"{what}: {n} elements needed, the tensor has {x.numel()}")
         return x.data_ptr()
-    raise TypeError(f"cannot take a pointer of {type(x)}")
+    raise TypeError(f"{what}: cannot take a pointer of {type(x)}")
+
+
+def _dev(x, n=None, dtype=None, what="device argument"):
+    """Pointer of DEVICE data: a contiguous CUDA torch tensor, an integer
+    address (a raw device pointer, passed through unchecked) or None.  numpy
+    arrays and CPU tensors are refused here, because the kernels would
+    dereference their host addresses.  n: least number of elements; dtype:
+    "f64" / "f32" / "bf16" / "i32" (a tuple allows several)."""
+    if x is None or isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        raise ValueError(f"{what}: device memory is expected here (a CUDA tensor), not a numpy array")
+    if hasattr(x, "data_ptr"):
+        if not x.is_cuda:
+            raise ValueError(f"{what}: a device (CUDA) tensor is expected here; host data goes in numpy arrays")
+        if not x.is_contiguous():
+            raise ValueError(f"{what}: tensor must be contiguous")
+        if dtype is not None:
+            allowed = (dtype,) if isinstance(dtype, str) else dtype
+            if str(x.dtype) not in [_TORCH_DTYPES[d] for d in allowed]:
+                raise ValueError(f"{what}: {' or '.join(_TORCH_DTYPES[d] for d in allowed)} expected, got {x.dtype}")
+        if n is not None and x.numel() < n:
+            raise ValueError(f"{what}: {n} elements needed, the tensor has {x.numel()}")
+        return x.data_ptr()
+    raise TypeError(f"{what}: cannot take a pointer of {type(x)}")
+
+
+def _sizes(h):
+    """Mesh sizes of handle h under its current parameters, or None when the
+    library has none yet (it then reports the call-order error itself)."""
+    i = dg_info()
+    if load().dg_get_info(h, ctypes.byref(i)) != DG_OK:
+        return None
+    return i
+
+
+def _vec_dtype(dtype):
+    return "f64" if int(dtype) == DG_F64 else "f32"
 
 
 # ---------------------------------------------------------------------------
@@ -231,13 +294,28 @@ def dg_mesh_upload(h, nodes, elems, dirichlet, neumann):
     elems = np.ascontiguousarray(elems, dtype=np.int32).reshape(-1, 3)
     dirichlet = np.ascontiguousarray(dirichlet, dtype=np.int32).reshape(-1, 2)
     neumann = np.ascontiguousarray(neumann, dtype=np.int32).reshape(-1, 2)
-    return load().dg_mesh_upload(h, _ptr(nodes), nodes.shape[0], _ptr(elems), elems.shape[0],
-                                 _ptr(dirichlet) if len(dirichlet) else None, dirichlet.shape[0],
-                                 _ptr(neumann) if len(neumann) else None, neumann.shape[0])
+    return load().dg_mesh_upload(h, _host(nodes), nodes.shape[0], _host(elems), elems.shape[0],
+                                 _host(dirichlet) if len(dirichlet) else None, dirichlet.shape[0],
+                                 _host(neumann) if len(neumann) else None, neumann.shape[0])
 
 
 def dg_set_params(h, p):
     return load().dg_set_params(h, ctypes.byref(p))
+
+
+def dg_set_allocator(h, alloc_fn, free_fn, ctx=None):
+    """alloc_fn / free_fn: DG_ALLOC_FN / DG_FREE_FN objects (the caller keeps
+    them alive as long as the handle), or None for both (cudaMalloc)."""
+    return load().dg_set_allocator(h, alloc_fn if alloc_fn is not None else DG_ALLOC_FN(),
+                                   free_fn if free_fn is not None else DG_FREE_FN(), ctx)
+
+
+def dg_set_arena(h, base, nbytes):
+    return load().dg_set_arena(h, _dev(base, None, None, "arena"), int(nbytes))
+
+
+def dg_workspace_size(h, what):
+    return int(load().dg_workspace_size(h, int(what)))
 
 
 def dg_get_info(h):
@@ -246,28 +324,60 @@ def dg_get_info(h):
     return s, i
 
 
+def _points_count(i, which):
+    return {DG_POINTS_VOLUME: i.ne * i.q_volume, DG_POINTS_BOUNDARY: i.n_bedges * i.q_edge,
+            DG_POINTS_ERROR: i.ne * i.q_error, DG_POINTS_FACE: i.ne * 3 * i.q_edge}.get(int(which))
+
+
 def dg_quad_points(h, which, xy):
-    return load().dg_quad_points(h, int(which), _ptr(xy))
+    i = _sizes(h)
+    n = None if i is None or _points_count(i, which) is None else 2 * _points_count(i, which)
+    return load().dg_quad_points(h, int(which), _dev(xy, n, "f64", "xy"))
 
 
 def dg_boundary_info(h, normals, types=None):
-    return load().dg_boundary_info(h, _ptr(normals), _ptr(types))
+    i = _sizes(h)
+    nbe = None if i is None else i.n_bedges
+    return load().dg_boundary_info(h, _dev(normals, None if nbe is None else 2 * nbe, "f64", "normals"),
+                                   _dev(types, nbe, "i32", "type"))
+
+
+def dg_coeffs_data(h, c, f=None, gD=None, gN=None, eps_q=None, eps_f=None):
+    """Fill the device pointers of a dg_coeffs from tensors (checked against
+    the handle's point counts)."""
+    i = _sizes(h)
+    nv = None if i is None else i.ne * i.q_volume
+    ne_ = None if i is None else i.n_bedges * i.q_edge
+    nf = None if i is None else i.ne * 3 * i.q_edge
+    c.f, c.gD, c.gN = _dev(f, nv, "f64", "f"), _dev(gD, ne_, "f64", "gD"), _dev(gN, ne_, "f64", "gN")
+    c.eps_q, c.eps_f = _dev(eps_q, nv, "f64", "eps_q"), _dev(eps_f, nf, "f64", "eps_f")
+    return c
 
 
 def dg_assemble(h, c):
     return load().dg_assemble(h, ctypes.byref(c))
 
 
+def _dofs(h):
+    i = _sizes(h)
+    return None if i is None else i.dofs
+
+
 def dg_get_rhs(h, F):
-    return load().dg_get_rhs(h, _ptr(F))
+    return load().dg_get_rhs(h, _dev(F, _dofs(h), "f64", "F"))
 
 
 def dg_get_blocks(h, dtype, out, nbr=None):
-    return load().dg_get_blocks(h, int(dtype), _ptr(out), _ptr(nbr))
+    i = _sizes(h)
+    n = None if i is None else i.ne * 4 * i.nb * i.nb
+    kinds = {DG_F64: "f64", DG_F32: "f32", DG_BF16: "bf16"}.get(int(dtype))
+    return load().dg_get_blocks(h, int(dtype), _dev(out, n, kinds, "out"),
+                                _dev(nbr, None if i is None else 3 * i.ne, "i32", "nbr"))
 
 
 def dg_apply(h, dtype, x, y):
-    return load().dg_apply(h, int(dtype), _ptr(x), _ptr(y))
+    n, t = _dofs(h), _vec_dtype(dtype)
+    return load().dg_apply(h, int(dtype), _dev(x, n, t, "x"), _dev(y, n, t, "y"))
 
 
 def dg_precond_setup(h, kind):
@@ -275,43 +385,61 @@ def dg_precond_setup(h, kind):
 
 
 def dg_precond_apply(h, dtype, r, z):
-    return load().dg_precond_apply(h, int(dtype), _ptr(r), _ptr(z))
+    n, t = _dofs(h), _vec_dtype(dtype)
+    return load().dg_precond_apply(h, int(dtype), _dev(r, n, t, "r"), _dev(z, n, t, "z"))
+
+
+def _solve_vectors(h, F, x):
+    n = _dofs(h)
+    return _dev(F, n, "f64", "F"), _dev(x, n, "f64", "x")
 
 
 def dg_gmres_solve(h, F, x, info=None):
-    return load().dg_gmres_solve(h, _ptr(F), _ptr(x), ctypes.byref(info) if info is not None else None)
+    Fp, xp = _solve_vectors(h, F, x)
+    return load().dg_gmres_solve(h, Fp, xp, ctypes.byref(info) if info is not None else None)
 
 
 def dg_mixed_solve(h, inner_dtype, inner_m, inner_tol, max_outer, F, x, info=None):
-    return load().dg_mixed_solve(h, int(inner_dtype), int(inner_m), float(inner_tol), int(max_outer), _ptr(F),
-                                 _ptr(x), ctypes.byref(info) if info is not None else None)
+    Fp, xp = _solve_vectors(h, F, x)
+    return load().dg_mixed_solve(h, int(inner_dtype), int(inner_m), float(inner_tol), int(max_outer), Fp, xp,
+                                 ctypes.byref(info) if info is not None else None)
 
 
 def dg_gmres_ir_solve(h, inner_dtype, inner_m, inner_tol, max_outer, F, x, info=None):
-    return load().dg_gmres_ir_solve(h, int(inner_dtype), int(inner_m), float(inner_tol), int(max_outer), _ptr(F),
-                                    _ptr(x), ctypes.byref(info) if info is not None else None)
+    Fp, xp = _solve_vectors(h, F, x)
+    return load().dg_gmres_ir_solve(h, int(inner_dtype), int(inner_m), float(inner_tol), int(max_outer), Fp, xp,
+                                    ctypes.byref(info) if info is not None else None)
 
 
 def dg_dense_solve(h, F, x):
-    return load().dg_dense_solve(h, _ptr(F), _ptr(x))
+    Fp, xp = _solve_vectors(h, F, x)
+    return load().dg_dense_solve(h, Fp, xp)
+
+
+def _l2_args(h, x, uex_q):
+    i = _sizes(h)
+    return (_dev(x, None if i is None else i.dofs, "f64", "x"),
+            _dev(uex_q, None if i is None else i.ne * i.q_error, "f64", "uex_q"))
 
 
 def dg_l2_error(h, x, uex_q):
     l2, hmax = c_double(), c_double()
-    s = load().dg_l2_error(h, _ptr(x), _ptr(uex_q), ctypes.byref(l2), ctypes.byref(hmax))
+    s = load().dg_l2_error(h, *_l2_args(h, x, uex_q), ctypes.byref(l2), ctypes.byref(hmax))
     return s, l2.value, hmax.value
 
 
 def dg_l2_error_noalloc(h, x, uex_q):
     """dg_l2_error through the allocation-free entry point (see include/dg.h)."""
     l2, hmax = c_double(), c_double()
-    s = load().dg_l2_error_noalloc(h, _ptr(x), _ptr(uex_q), ctypes.byref(l2), ctypes.byref(hmax))
+    s = load().dg_l2_error_noalloc(h, *_l2_args(h, x, uex_q), ctypes.byref(l2), ctypes.byref(hmax))
     return s, l2.value, hmax.value
 
 
 def dg_eval(h, x, rs, out):
     rs = np.ascontiguousarray(rs, dtype=np.float64).reshape(-1, 2)
-    return load().dg_eval(h, _ptr(x), rs.shape[0], _ptr(rs), _ptr(out))
+    i = _sizes(h)
+    return load().dg_eval(h, _dev(x, None if i is None else i.dofs, "f64", "x"), rs.shape[0], _host(rs),
+                          _dev(out, None if i is None else i.ne * rs.shape[0], "f64", "out"))
 
 
 def dg_profile_kernel(h, which, dtype, param, reps):
@@ -323,7 +451,9 @@ def dg_profile_kernel(h, which, dtype, param, reps):
 def dg_batch_setup(h, elem_start, coeffs):
     elem_start = np.ascontiguousarray(elem_start, dtype=np.int32).reshape(-1)
     coeffs = np.ascontiguousarray(coeffs, dtype=np.float64).reshape(-1, 8)
-    return load().dg_batch_setup(h, elem_start.shape[0] - 1, _ptr(elem_start), _ptr(coeffs))
+    if coeffs.shape[0] != elem_start.shape[0] - 1:
+        raise ValueError("coeffs needs one row of 8 per instance")
+    return load().dg_batch_setup(h, elem_start.shape[0] - 1, _host(elem_start), _host(coeffs))
 
 
 def dg_batch_clear(h):
@@ -340,15 +470,77 @@ def dg_batch_set_tile(h, tile):
     return load().dg_batch_set_tile(h, int(tile))
 
 
-def dg_batch_solve(h, inner_dtype, inner_m, inner_tol, max_outer, F, x, its=None, relres=None, status=None):
-    return load().dg_batch_solve(h, int(inner_dtype), int(inner_m), float(inner_tol), int(max_outer), _ptr(F),
-                                 _ptr(x), _ptr(its), _ptr(relres), _ptr(status))
+def _batch_outputs(its, relres, status, n_inst):
+    return (_host(its, n_inst, "i32", "its"), _host(relres, n_inst, "f64", "relres"),
+            _host(status, n_inst, "i32", "status"))
+
+
+def dg_batch_solve(h, inner_dtype, inner_m, inner_tol, max_outer, F, x, its=None, relres=None, status=None,
+                   n_inst=None):
+    Fp, xp = _solve_vectors(h, F, x)
+    return load().dg_batch_solve(h, int(inner_dtype), int(inner_m), float(inner_tol), int(max_outer), Fp, xp,
+                                 *_batch_outputs(its, relres, status, n_inst))
 
 
 def dg_batch_gmres_ir_solve(h, inner_dtype, inner_m, inner_tol, max_outer, F, x, its=None, relres=None,
-                            status=None):
-    return load().dg_batch_gmres_ir_solve(h, int(inner_dtype), int(inner_m), float(inner_tol), int(max_outer),
-                                          _ptr(F), _ptr(x), _ptr(its), _ptr(relres), _ptr(status))
+                            status=None, n_inst=None):
+    Fp, xp = _solve_vectors(h, F, x)
+    return load().dg_batch_gmres_ir_solve(h, int(inner_dtype), int(inner_m), float(inner_tol), int(max_outer), Fp,
+                                          xp, *_batch_outputs(its, relres, status, n_inst))
+
+
+def _group_args(hs, F, xs, its, relres, status):
+    """Pointer arrays of a group call: handles, and per batch F (device, may be
+    None), x (device), its / relres / status (host numpy, may be None)."""
+    nh = len(hs)
+    P = c_void_p * nh
+    harr = P(*[h.value if isinstance(h, c_void_p) else h for h in hs])
+    keep = []
+
+    def arr(vals, conv):
+        if vals is None:
+            return None
+        a = P(*[conv(v, i) for i, v in enumerate(vals)])
+        keep.append(a)
+        return ctypes.cast(a, c_void_p)
+
+    sizes = [_sizes(h) for h in hs]
+    dof = lambda i: None if sizes[i] is None else sizes[i].dofs
+    Fa = arr(F, lambda v, i: _dev(v, dof(i), "f64", "F"))
+    xa = arr(xs, lambda v, i: _dev(v, dof(i), "f64", "x"))
+    ia = arr(its, lambda v, i: _host(v, None, "i32", "its"))
+    ra = arr(relres, lambda v, i: _host(v, None, "f64", "relres"))
+    sa = arr(status, lambda v, i: _host(v, None, "i32", "status"))
+    return harr, nh, Fa, xa, ia, ra, sa, keep
+
+
+def dg_batch_group_solve(hs, inner_dtype, inner_m, inner_tol, max_outer, F, xs, its=None, relres=None, status=None):
+    harr, nh, Fa, xa, ia, ra, sa, _keep = _group_args(hs, F, xs, its, relres, status)
+    return load().dg_batch_group_solve(ctypes.cast(harr, c_void_p), nh, int(inner_dtype), int(inner_m),
+                                       float(inner_tol), int(max_outer), Fa, xa, ia, ra, sa)
+
+
+def dg_batch_group_gmres_ir_solve(hs, inner_dtype, inner_m, inner_tol, max_outer, F, xs, its=None, relres=None,
+                                  status=None):
+    harr, nh, Fa, xa, ia, ra, sa, _keep = _group_args(hs, F, xs, its, relres, status)
+    return load().dg_batch_group_gmres_ir_solve(ctypes.cast(harr, c_void_p), nh, int(inner_dtype), int(inner_m),
+                                                float(inner_tol), int(max_outer), Fa, xa, ia, ra, sa)
+
+
+def batch_group(dgs, solver="gmres_ir", inner_dtype=DG_F32, inner_m=32, inner_tol=1e-3, max_outer=500,
+                raise_on_nonconv=True):
+    """Solve the batches of several DG objects (e.g. one per degree) in one
+    group call; returns per batch (x, its, relres, status)."""
+    xs = [d._empty((d.info().dofs,)) for d in dgs]
+    its = [np.zeros(d.batch_n, np.int32) for d in dgs]
+    rr = [np.zeros(d.batch_n) for d in dgs]
+    st = [np.zeros(d.batch_n, np.int32) for d in dgs]
+    fn = dg_batch_group_gmres_ir_solve if solver == "gmres_ir" else dg_batch_group_solve
+    s = fn([d.h for d in dgs], inner_dtype, inner_m, inner_tol, max_outer, None, xs, its, rr, st)
+    if s != DG_OK and not (s == DG_NOT_CONVERGED and not raise_on_nonconv):
+        msgs = "; ".join(dg_last_error(d.h) for d in dgs)
+        raise DGError(s, msgs)
+    return [(xs[i], its[i], rr[i], st[i]) for i in range(len(dgs))]
 
 
 def dg_mesh_refine(nodes, elems, dirichlet, neumann):
@@ -360,27 +552,31 @@ def dg_mesh_refine(nodes, elems, dirichlet, neumann):
     dirichlet = np.ascontiguousarray(dirichlet, dtype=np.int32).reshape(-1, 2)
     neumann = np.ascontiguousarray(neumann, dtype=np.int32).reshape(-1, 2)
     sizes = [ctypes.c_int() for _ in range(4)]
-    args = (_ptr(nodes), nodes.shape[0], _ptr(elems), elems.shape[0], _ptr(dirichlet), dirichlet.shape[0],
-            _ptr(neumann), neumann.shape[0])
+    args = (_host(nodes), nodes.shape[0], _host(elems), elems.shape[0], _host(dirichlet), dirichlet.shape[0],
+            _host(neumann), neumann.shape[0])
     s = lib.dg_mesh_refine(*args, None, ctypes.byref(sizes[0]), None, ctypes.byref(sizes[1]), None,
                            ctypes.byref(sizes[2]), None, ctypes.byref(sizes[3]))
     if s != DG_OK:
         raise DGError(s, "dg_mesh_refine")
     nv, ne, nd, nn = (v.value for v in sizes)
     out = (np.zeros((nv, 2)), np.zeros((ne, 3), np.int32), np.zeros((nd, 2), np.int32), np.zeros((nn, 2), np.int32))
-    s = lib.dg_mesh_refine(*args, _ptr(out[0]), ctypes.byref(sizes[0]), _ptr(out[1]), ctypes.byref(sizes[1]),
-                           _ptr(out[2]), ctypes.byref(sizes[2]), _ptr(out[3]), ctypes.byref(sizes[3]))
+    s = lib.dg_mesh_refine(*args, _host(out[0]), ctypes.byref(sizes[0]), _host(out[1]), ctypes.byref(sizes[1]),
+                           _host(out[2]), ctypes.byref(sizes[2]), _host(out[3]), ctypes.byref(sizes[3]))
     if s != DG_OK:
         raise DGError(s, "dg_mesh_refine")
     return out
 
 
 def dg_nonlinear_global(h, p, c, x, H, HJ=None):
-    return load().dg_nonlinear_global(h, int(p), float(c), _ptr(x), _ptr(H), _ptr(HJ))
+    i = _sizes(h)
+    n = None if i is None else i.dofs
+    return load().dg_nonlinear_global(h, int(p), float(c), _dev(x, n, "f64", "x"), _dev(H, n, "f64", "H"),
+                                      _dev(HJ, None if i is None else i.ne * i.nb * i.nb, "f64", "HJ"))
 
 
 def dg_newton_solve(h, p, c, max_newton, lin_tol, F, x, info):
-    return load().dg_newton_solve(h, int(p), float(c), int(max_newton), float(lin_tol), _ptr(F), _ptr(x),
+    Fp, xp = _solve_vectors(h, F, x)
+    return load().dg_newton_solve(h, int(p), float(c), int(max_newton), float(lin_tol), Fp, xp,
                                   ctypes.byref(info))
 
 
@@ -398,17 +594,18 @@ def dg_mlp_init(h, seed):
 
 def dg_mlp_set_weights(h, theta):
     theta = np.ascontiguousarray(theta, dtype=np.float32)
-    return load().dg_mlp_set_weights(h, _ptr(theta), theta.size)
+    return load().dg_mlp_set_weights(h, _host(theta), theta.size)
 
 
 def dg_mlp_get_weights(h, n):
     out = np.zeros(n, np.float32)
-    s = load().dg_mlp_get_weights(h, _ptr(out), n)
+    s = load().dg_mlp_get_weights(h, _host(out), n)
     return s, out
 
 
 def dg_mlp_collect(h, F, xk):
-    return load().dg_mlp_collect(h, _ptr(F), _ptr(xk))
+    Fp, xp = _solve_vectors(h, F, xk)
+    return load().dg_mlp_collect(h, Fp, xp)
 
 
 def dg_mlp_collect_basis(h, nvec):
@@ -421,8 +618,16 @@ def dg_mlp_num_rows(h):
     return s, n.value
 
 
+def _mlp_widths(h):
+    i = _sizes(h)
+    return (None, None) if i is None else (4 * i.nb + 8, i.nb)
+
+
 def dg_mlp_get_rows(h, X, T, max_rows):
-    return load().dg_mlp_get_rows(h, _ptr(X), _ptr(T), int(max_rows))
+    din, nb = _mlp_widths(h)
+    m = int(max_rows)
+    return load().dg_mlp_get_rows(h, _host(X, None if din is None else m * din, "f32", "X"),
+                                  _host(T, None if nb is None else m * nb, "f32", "T"), m)
 
 
 def dg_mlp_clear_data(h):
@@ -430,17 +635,25 @@ def dg_mlp_clear_data(h):
 
 
 def dg_mlp_train(h, steps, batch_rows, lr, seed, loss=None):
-    return load().dg_mlp_train(h, int(steps), int(batch_rows), float(lr), int(seed), _ptr(loss))
+    return load().dg_mlp_train(h, int(steps), int(batch_rows), float(lr), int(seed),
+                               _host(loss, int(steps), "f32", "loss"))
 
 
 def dg_mlp_loss_grad(h, X, T, rows, grad=None):
     loss = c_double()
-    s = load().dg_mlp_loss_grad(h, _ptr(X), _ptr(T), int(rows), ctypes.byref(loss), _ptr(grad))
+    din, nb = _mlp_widths(h)
+    r = int(rows)
+    s = load().dg_mlp_loss_grad(h, _dev(X, None if din is None else r * din, "f32", "X"),
+                                _dev(T, None if nb is None else r * nb, "f32", "T"), r, ctypes.byref(loss),
+                                _host(grad, None, "f32", "grad"))
     return s, loss.value
 
 
 def dg_mlp_forward(h, X, rows, Y):
-    return load().dg_mlp_forward(h, _ptr(X), int(rows), _ptr(Y))
+    din, nb = _mlp_widths(h)
+    r = int(rows)
+    return load().dg_mlp_forward(h, _dev(X, None if din is None else r * din, "f32", "X"), r,
+                                 _dev(Y, None if nb is None else r * nb, "f32", "Y"))
 
 
 def dg_get_launch_count(h):
@@ -453,7 +666,7 @@ def dg_reference_basis(degree, rs):
     rs = np.ascontiguousarray(rs, dtype=np.float64).reshape(-1, 2)
     nb = (degree + 1) * (degree + 2) // 2
     phi = np.zeros((rs.shape[0], nb)); dr = np.zeros_like(phi); ds = np.zeros_like(phi)
-    s = load().dg_reference_basis(int(degree), rs.shape[0], _ptr(rs), _ptr(phi), _ptr(dr), _ptr(ds))
+    s = load().dg_reference_basis(int(degree), rs.shape[0], _host(rs), _host(phi), _host(dr), _host(ds))
     if s != DG_OK:
         raise DGError(s, "dg_reference_basis")
     return phi, dr, ds
@@ -463,7 +676,7 @@ def dg_reference_rule(which, degree):
     n = ctypes.c_int()
     load().dg_reference_rule(int(which), int(degree), None, None, ctypes.byref(n))
     rs = np.zeros((n.value, 2)); w = np.zeros(n.value)
-    s = load().dg_reference_rule(int(which), int(degree), _ptr(rs), _ptr(w), ctypes.byref(n))
+    s = load().dg_reference_rule(int(which), int(degree), _host(rs), _host(w), ctypes.byref(n))
     if s != DG_OK:
         raise DGError(s, "dg_reference_rule")
     return rs, w
@@ -491,11 +704,13 @@ class DG:
                 stream = cur.cuda_stream
         self.h = dg_create(device, stream)
         self.params = dg_params_default()
+        self._memory_source = None
 
     def close(self):
         if self.h is not None:
             dg_destroy(self.h)
             self.h = None
+        self._memory_source = None
         if self._own_stream is not None:
             dg_stream_destroy(self._own_stream)
             self._own_stream = None
@@ -509,6 +724,31 @@ class DG:
     def check(self, s):
         if s != DG_OK:
             raise DGError(s, dg_last_error(self.h))
+
+    # -- device memory --------------------------------------------------------
+    def set_arena(self, buf):
+        """Carve the handle's device memory out of `buf` (a CUDA tensor the
+        object keeps alive); right after construction only."""
+        self.check(dg_set_arena(self.h, buf, buf.numel() * buf.element_size()))
+        self._memory_source = buf
+
+    def use_torch_allocator(self):
+        """Take the handle's device memory from torch's caching allocator
+        (counted by torch.cuda.memory_allocated); right after construction only."""
+        torch = self.torch
+
+        def alloc(ctx, nbytes, device, stream):
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device=int(device), stream=int(stream or 0))
+
+        def free(ctx, ptr, nbytes, device, stream):
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+        fns = (DG_ALLOC_FN(alloc), DG_FREE_FN(free))
+        self.check(dg_set_allocator(self.h, *fns))
+        self._memory_source = fns
+
+    def workspace_size(self, what=DG_WS_TOTAL):
+        return dg_workspace_size(self.h, what)
 
     # -- set-up -------------------------------------------------------------
     def mesh_upload(self, nodes, elems, dirichlet, neumann):
@@ -530,7 +770,7 @@ class DG:
     def quad_points(self, which):
         i = self.info()
         shape = {DG_POINTS_VOLUME: (i.ne, i.q_volume, 2), DG_POINTS_BOUNDARY: (i.n_bedges, i.q_edge, 2),
-                 DG_POINTS_ERROR: (i.ne, i.q_error, 2)}[which]
+                 DG_POINTS_ERROR: (i.ne, i.q_error, 2), DG_POINTS_FACE: (i.ne, 3, i.q_edge, 2)}[which]
         out = self._empty(shape)
         self.check(dg_quad_points(self.h, which, out))
         return out
@@ -542,13 +782,16 @@ class DG:
         self.check(dg_boundary_info(self.h, n, t))
         return n, t
 
-    def assemble(self, eps, alpha, b, f=None, gD=None, gN=None, f_const=0.0, gD_const=0.0, gN_const=0.0):
+    def assemble(self, eps, alpha, b, f=None, gD=None, gN=None, f_const=0.0, gD_const=0.0, gN_const=0.0,
+                 eps_q=None, eps_f=None):
+        """eps_q / eps_f: a pointwise diffusion coefficient at DG_POINTS_VOLUME
+        and DG_POINTS_FACE (then eps is not used), or None for the constant eps."""
         c = dg_coeffs()
         c.eps, c.alpha = float(eps), float(alpha)
         for t in range(6):
             c.b[t] = float(b[t])
-        self._keep = (f, gD, gN)
-        c.f, c.gD, c.gN = _ptr(f), _ptr(gD), _ptr(gN)
+        self._keep = (f, gD, gN, eps_q, eps_f)
+        dg_coeffs_data(self.h, c, f, gD, gN, eps_q, eps_f)
         c.f_const, c.gD_const, c.gN_const = float(f_const), float(gD_const), float(gN_const)
         self.check(dg_assemble(self.h, c))
 
@@ -663,7 +906,7 @@ class DG:
         x = self._empty((i.dofs,)) if x is None else x
         n = self.batch_n
         its = np.zeros(n, np.int32); rr = np.zeros(n); st = np.zeros(n, np.int32)
-        s = dg_batch_solve(self.h, inner_dtype, inner_m, inner_tol, max_outer, F, x, its, rr, st)
+        s = dg_batch_solve(self.h, inner_dtype, inner_m, inner_tol, max_outer, F, x, its, rr, st, n_inst=n)
         if s != DG_OK and not (s == DG_NOT_CONVERGED and not raise_on_nonconv):
             self.check(s)
         return x, its, rr, st
@@ -674,7 +917,8 @@ class DG:
         x = self._empty((i.dofs,)) if x is None else x
         n = self.batch_n
         its = np.zeros(n, np.int32); rr = np.zeros(n); st = np.zeros(n, np.int32)
-        s = dg_batch_gmres_ir_solve(self.h, inner_dtype, inner_m, inner_tol, max_outer, F, x, its, rr, st)
+        s = dg_batch_gmres_ir_solve(self.h, inner_dtype, inner_m, inner_tol, max_outer, F, x, its, rr, st,
+                                    n_inst=n)
         if s != DG_OK and not (s == DG_NOT_CONVERGED and not raise_on_nonconv):
             self.check(s)
         return x, its, rr, st

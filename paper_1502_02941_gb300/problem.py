@@ -28,6 +28,18 @@ def problem_data(h: D.DG, prob: W.Problem):
     return f, gD, gN
 
 
+def eps_data(h: D.DG, prob: W.Problem):
+    """A variable diffusion coefficient (the paper's fdiff) at the volume and
+    face points (device tensors), or (None, None) for a constant eps."""
+    if prob.eps_fn is None:
+        return None, None
+    torch = h.torch
+    xq = h.quad_points(D.DG_POINTS_VOLUME)
+    xf = h.quad_points(D.DG_POINTS_FACE)
+    return (prob.eps_at(torch, xq[..., 0], xq[..., 1]).contiguous(),
+            prob.eps_at(torch, xf[..., 0], xf[..., 1]).contiguous())
+
+
 def setup(h: D.DG, cfg: W.Config, store=D.DG_STORE_F64, mesh: W.MeshArrays | None = None,
           assemble: bool = True, **params):
     ma = mesh if mesh is not None else mesh_for(cfg)
@@ -36,7 +48,8 @@ def setup(h: D.DG, cfg: W.Config, store=D.DG_STORE_F64, mesh: W.MeshArrays | Non
     data = problem_data(h, cfg.problem)
     if assemble:
         p = cfg.problem
-        h.assemble(p.eps, p.alpha, p.b, *data)
+        eq, ef = eps_data(h, p)
+        h.assemble(p.eps, p.alpha, p.b, *data, eps_q=eq, eps_f=ef)
     return ma, data
 
 

@@ -124,15 +124,38 @@ def test_binding_signatures_match_the_header(lib):
 
 
 def test_binding_refuses_host_tensors_for_device_arguments():
-    """Torch tensors are passed to the kernels as device pointers; a host tensor
-    is refused in the binding before any call (numpy arrays are the host path)."""
+    """Every pointer argument is marked host or device in the binding.  Device
+    arguments take CUDA tensors (or raw integer addresses); a numpy array or a
+    CPU tensor there is refused before any library call, because the kernels
+    would dereference its host address.  Host arguments take numpy arrays (or
+    CPU tensors).  Sizes and dtypes are checked against what the call needs."""
     import torch
     with pytest.raises(ValueError):
-        D._ptr(torch.zeros(4, dtype=torch.float64))
+        D._dev(torch.zeros(4, dtype=torch.float64))          # CPU tensor as device memory
     with pytest.raises(ValueError):
-        D._ptr(np.zeros((4, 2))[:, 0])          # not contiguous
+        D._dev(np.zeros(4))                                  # numpy array as device memory
+    with pytest.raises(ValueError):
+        D._host(np.zeros((4, 2))[:, 0])                      # not contiguous
+    with pytest.raises(ValueError):
+        D._host(np.zeros(3), n=4)                            # too few elements
+    with pytest.raises(ValueError):
+        D._host(np.zeros(3, np.float32), dtype="f64")        # wrong dtype
     a = np.zeros(3)
-    assert D._ptr(a) == a.ctypes.data and D._ptr(None) is None and D._ptr(7) == 7
+    assert D._host(a) == a.ctypes.data and D._host(None) is None and D._host(7) == 7
+    assert D._dev(None) is None and D._dev(7) == 7
+    t = torch.zeros(3, dtype=torch.float64)
+    assert D._host(t) == t.data_ptr()
+    # the wrappers refuse host memory for device arguments before calling the
+    # library (no handle is needed for the refusal)
+    for fn in (D.dg_l2_error_noalloc, D.dg_l2_error):
+        with pytest.raises(ValueError):
+            fn(None, np.zeros(3), np.zeros(3))
+        with pytest.raises(ValueError):
+            fn(None, torch.zeros(3, dtype=torch.float64), torch.zeros(3, dtype=torch.float64))
+    with pytest.raises(ValueError):
+        D.dg_apply(None, D.DG_F64, np.zeros(3), np.zeros(3))
+    with pytest.raises(ValueError):
+        D.dg_gmres_solve(None, None, np.zeros(3))
 
 
 def test_network_checkpoint_round_trip():

@@ -140,3 +140,46 @@ def test_batch_rejects_mixed_degrees():
     with pytest.raises(ValueError):
         problem.setup_batch(h, cfgs, ma, starts, coeffs)
     h.close()
+
+
+@pytest.mark.parametrize("solver", ["gmres_ir", "refine"])
+def test_group_solve_of_a_mixed_degree_batch(solver):
+    """Instances of the batched workload with both drawn degrees: one batch per
+    degree, solved in one group call whose batches run concurrently on their
+    own streams.  Every instance meets 1e-10 with the oracle's operator, and
+    each batch's result equals its own single-batch solve."""
+    groups = W.batch_by_degree("batched", 8, N_range=(4, 9))
+    assert sorted(groups) == [1, 2]
+    dgs, setups = [], []
+    for k, (cfgs, ma, starts, coeffs) in groups.items():
+        h = D.DG(0)
+        problem.setup_batch(h, cfgs, ma, starts, coeffs, store=D.DG_STORE_F64 | D.DG_STORE_F32, tol=1e-11,
+                            gmres_m=20, precond=D.DG_PRECOND_SCHWARZ)
+        h.precond_setup(D.DG_PRECOND_SCHWARZ)
+        dgs.append(h)
+        setups.append((cfgs, starts))
+    if solver == "gmres_ir":
+        res = D.batch_group(dgs, "gmres_ir", D.DG_F32, inner_m=16, inner_tol=1e-3, max_outer=300)
+    else:
+        res = D.batch_group(dgs, "refine", D.DG_F32, inner_m=20, inner_tol=1e-5, max_outer=30)
+    for h, (cfgs, starts), (x, its, rr, st) in zip(dgs, setups, res):
+        assert (st == 0).all() and (rr <= 1e-11).all()
+        if solver == "gmres_ir":
+            xs, _, _, _ = h.batch_gmres_ir_solve(D.DG_F32, inner_m=16, inner_tol=1e-3, max_outer=300)
+        else:
+            xs, _, _, _ = h.batch_solve(D.DG_F32, inner_m=20, inner_tol=1e-5, max_outer=30)
+        np.testing.assert_allclose(_np(x), _np(xs), rtol=0, atol=1e-12 * np.abs(_np(xs)).max())
+        xb = _np(x)
+        nb = O.nbasis(cfgs[0].k)
+        for i, c in enumerate(cfgs):
+            a, b = starts[i] * nb, starts[i + 1] * nb
+            mi = W.structured_mesh(c.N)
+            run = oracle_system(mi, c.k, c.method, c.problem)
+            T = basis_change(run, mi, c.k)
+            assert rel_residual_oracle(run, T, xb[a:b]) <= 1e-10
+    # a handle twice is refused
+    s = D.dg_batch_group_solve([dgs[0].h, dgs[0].h], D.DG_F32, 20, 1e-5, 30, None,
+                               [res[0][0], res[0][0]])
+    assert s == D.DG_ERR_INVALID_ARG
+    for h in dgs:
+        h.close()

@@ -38,6 +38,24 @@ def test_l2_error_noalloc_matches_regular_entry_point():
     h.close()
 
 
+def test_l2_error_noalloc_binding_checks_sizes_and_memory_kind():
+    cfg = W.boundary_layer_p2(method=2, N=4)
+    h = D.DG(0)
+    problem.setup(h, cfg)
+    info = h.info()
+    uex = problem.exact_at_error_points(h, cfg.problem)
+    x = torch.zeros(info.dofs, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        D.dg_l2_error_noalloc(h.h, x.cpu().numpy(), uex)            # host array as device memory
+    with pytest.raises(ValueError):
+        D.dg_l2_error_noalloc(h.h, x[:-1], uex)                      # one entry short
+    with pytest.raises(ValueError):
+        D.dg_l2_error_noalloc(h.h, x.float(), uex)                   # f32 where f64 is read
+    s, l2, _ = D.dg_l2_error_noalloc(h.h, x, uex)
+    assert s == D.DG_OK and l2 > 0
+    h.close()
+
+
 def test_l2_error_noalloc_rejects_oversized_mesh():
     ma = W.structured_mesh(1449)             # 4,199,202 triangles > 4,194,304
     h = D.DG(0)
@@ -45,7 +63,10 @@ def test_l2_error_noalloc_rejects_oversized_mesh():
     h.set_params(degree=1)
     h.boundary_info()                        # builds the reference tables
     dummy = torch.zeros(16, dtype=torch.float64, device="cuda")
-    s, _, _ = D.dg_l2_error_noalloc(h.h, dummy, dummy)
+    # the binding would refuse a 16-entry buffer for this mesh; raw addresses
+    # reach the library, whose own size bound must reject the call before any
+    # launch (nothing is read from the buffer)
+    s, _, _ = D.dg_l2_error_noalloc(h.h, dummy.data_ptr(), dummy.data_ptr())
     assert s == D.DG_ERR_INVALID_ARG
     assert "4194304" in D.dg_last_error(h.h)
     h.close()
