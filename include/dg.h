@@ -179,6 +179,11 @@ typedef struct dg_handle dg_handle;
    predecessor finishes); the environment variable DG_PDL=0, read here, turns
    that off. */
 dg_status dg_create(dg_handle** h, int device, void* stream);
+/* (Test hook: with the environment variable DG_FAIL_CUDA_CALL=n set when the
+   handle is created, the n-th CUDA runtime call the handle checks reports a
+   failure after the real call has succeeded: the call in progress returns
+   DG_ERR_CUDA with dg_last_error naming the injected failure, and later
+   calls behave normally.  No GPU fault is involved.) */
 /* Free the handle and all device memory it owns.  NULL is accepted. */
 dg_status dg_destroy(dg_handle* h);
 /* Create / destroy a CUDA stream that is ordered with the legacy default
@@ -210,7 +215,9 @@ dg_status dg_stream_destroy(void* stream);
  *     256-byte granules); DG_ERR_NOMEM when the arena has no free range large
  *     enough.  The caller keeps the buffer alive until dg_destroy.
  * Either call moves the handle's 64-byte flag block to the new source and
- * fails with DG_ERR_STATE if the handle already holds any other device memory.
+ * fails with DG_ERR_STATE if the handle already holds any other device memory
+ * (if the new source cannot give the flag block, the call returns
+ * DG_ERR_NOMEM and the handle stays on cudaMalloc).
  * dg_destroy releases everything through the source in use.  Small pinned
  * HOST buffers for solver status words still come from cudaMallocHost, and
  * CUDA graph instantiation may allocate inside the driver.

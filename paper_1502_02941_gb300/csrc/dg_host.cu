@@ -153,7 +153,19 @@ static dg_status switch_source(dg_handle* h, dg_alloc_fn a, dg_free_fn f, void* 
     h->peak_bytes = 0;
     DG_WS_SCOPE(h, DG_WS_SCRATCH);
     dg_status s = dg_dev_alloc(h, (void**)&h->dflag, 64);
-    if (s != DG_OK) return s;
+    if (s != DG_OK) {
+        // the new source cannot give even the flag block: stay on cudaMalloc
+        const std::string msg = h->err;
+        delete h->arena;
+        h->arena = nullptr;
+        h->ualloc = nullptr;
+        h->ufree = nullptr;
+        h->uctx = nullptr;
+        if (dg_dev_alloc(h, (void**)&h->dflag, 64) != DG_OK) return DG_ERR_NOMEM;
+        DG_CK(h, cudaMemsetAsync(h->dflag, 0, 64, h->stream));
+        h->err = msg + "; the handle keeps cudaMalloc";
+        return s;
+    }
     DG_CK(h, cudaMemsetAsync(h->dflag, 0, 64, h->stream));
     return DG_OK;
 }
@@ -257,6 +269,8 @@ extern "C" dg_status dg_create(dg_handle** out, int device, void* stream) {
     h->stream = (cudaStream_t)stream;
     const char* pdl = getenv("DG_PDL");
     h->pdl = !(pdl && pdl[0] == '0');
+    const char* inj = getenv("DG_FAIL_CUDA_CALL");   // test hook, see DG_CK
+    h->fail_cuda_in = inj ? atol(inj) : 0;
     if (cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
         delete h;
         return DG_ERR_CUDA;

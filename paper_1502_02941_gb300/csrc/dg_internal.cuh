@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <map>
 #include <string>
@@ -251,6 +252,7 @@ struct dg_handle {
     size_t held_bytes[DG_WS_PEAK] = {0, 0, 0, 0, 0, 0, 0};   // [0] = total
     size_t peak_bytes = 0;
     int ws_cat = DG_WS_SCRATCH;    // category of allocations made now
+    long fail_cuda_in = 0;         // test hook: > 0 fails the n-th checked CUDA call (DG_CK)
 };
 
 // Category of the allocations made while a scope object lives (restored on exit).
@@ -269,10 +271,20 @@ struct DgWsScope {
 // error helpers (dg_host.cu)
 dg_status dg_fail(dg_handle* h, dg_status s, const std::string& msg);
 dg_status dg_cuda_fail(dg_handle* h, cudaError_t e, const char* what);
-#define DG_CK(h, call)                                                 \
-    do {                                                               \
-        cudaError_t e__ = (call);                                      \
-        if (e__ != cudaSuccess) return dg_cuda_fail((h), e__, #call);  \
+// Checked CUDA runtime call.  Host-side fault injection for tests: with
+// DG_FAIL_CUDA_CALL=n in the environment at dg_create, the handle's n-th
+// checked call reports a failure (after the real call has run and
+// succeeded), so that the error path runs without any GPU fault.  Calls that
+// begin or end a stream capture are not counted: failing there would leave
+// the stream capturing.
+static inline bool dg_injectable(const char* what) { return strstr(what, "Capture") == nullptr; }
+#define DG_CK(h, call)                                                                               \
+    do {                                                                                             \
+        cudaError_t e__ = (call);                                                                    \
+        if (e__ == cudaSuccess && (h)->fail_cuda_in > 0 && dg_injectable(#call) &&                   \
+            --(h)->fail_cuda_in == 0)                                                                \
+            return dg_cuda_fail((h), cudaErrorUnknown, "injected failure (DG_FAIL_CUDA_CALL) of " #call); \
+        if (e__ != cudaSuccess) return dg_cuda_fail((h), e__, #call);                                \
     } while (0)
 #define DG_LAUNCH_CK(h) DG_CK(h, cudaGetLastError())
 

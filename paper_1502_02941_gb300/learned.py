@@ -129,8 +129,16 @@ def load_weights(path):
     (hl,) = struct.unpack("<I", data[8:12])
     if len(data) < 12 + hl:
         raise ValueError("truncated header")
-    head = json.loads(data[12:12 + hl].decode())
-    n = D.dg_mlp_num_params(head["degree"])
+    try:
+        head = json.loads(data[12:12 + hl].decode())
+    except (UnicodeDecodeError, ValueError) as e:
+        raise ValueError(f"unreadable checkpoint header: {e}") from None
+    if not isinstance(head, dict):
+        raise ValueError("checkpoint header is not a JSON object")
+    deg = head.get("degree")
+    if not isinstance(deg, int) or isinstance(deg, bool) or not 1 <= deg <= 3:
+        raise ValueError(f"checkpoint header has no valid degree (1..3): {deg!r}")
+    n = D.dg_mlp_num_params(deg)
     if head.get("dtype") != "float32" or head.get("n_params") != n or len(data) != 12 + hl + 4 * n:
         raise ValueError("checkpoint size does not match its degree")
     theta = np.frombuffer(data, dtype="<f4", count=n, offset=12 + hl).astype(np.float32)

@@ -178,3 +178,16 @@ def test_network_checkpoint_round_trip():
     for bad in (b"X" + raw[1:], raw[:-4]):
         with pytest.raises(ValueError):
             L.load_weights(io.BytesIO(bad))
+    # headers that are not an object with an integer degree in 1..3 are refused
+    # with ValueError too (not KeyError / AttributeError / DGError)
+    import json
+    import struct
+    for h in ({"n_params": n, "dtype": "float32"}, {"degree": 7, "n_params": n, "dtype": "float32"},
+              {"degree": "2", "n_params": n, "dtype": "float32"}, [2, n], "x"):
+        hb = json.dumps(h).encode()
+        blob = raw[:8] + struct.pack("<I", len(hb)) + hb + theta.tobytes()
+        with pytest.raises(ValueError):
+            L.load_weights(io.BytesIO(blob))
+    hb = b"\xff\xfe{"
+    with pytest.raises(ValueError):
+        L.load_weights(io.BytesIO(raw[:8] + struct.pack("<I", len(hb)) + hb))

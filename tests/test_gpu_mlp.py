@@ -142,12 +142,15 @@ def test_training_reduces_loss():
     h.close()
 
 
-def test_trained_network_gains_over_block_jacobi_on_unseen_instances():
-    """What training buys: on instances not seen in training, the trained
-    network's preconditioner is at least twice as close (in the residual-space
-    loss) to the one-layer-overlap Schwarz correction as block Jacobi alone
-    (the untrained output y = 0); and flexible GMRES with it still reaches the
-    tolerance in f64 on every instance."""
+def test_trained_network_fits_the_patch_correction_on_unseen_instances():
+    """What training buys in the quantity it is trained on: on instances not
+    seen in training, the trained network's preconditioner is at least twice as
+    close (in the residual-space loss) to the one-layer-overlap Schwarz
+    correction as block Jacobi alone (the untrained output y = 0); flexible
+    GMRES with it still reaches the tolerance in f64 on every instance.  This
+    is not a gain in Arnoldi steps or time: the test prints the measured step
+    ratio, and the benchmark's learned section reports steps and time against
+    block Jacobi and Schwarz."""
     from paper_1502_02941_gb300 import learned as L
     h = D.DG(0)
     L.make_batch(h, 16, 16, first=0, gmres_m=30)
@@ -177,5 +180,7 @@ def test_trained_network_gains_over_block_jacobi_on_unseen_instances():
     res = L.evaluate(he, max_it=20000)
     assert res["mlp"]["converged"] == 6 and res["bj"]["converged"] == 6
     assert np.all(res["mlp"]["relres"] <= 1e-10)
+    print(f"mean Arnoldi steps: network {np.mean(res['mlp']['its']):.1f}, block Jacobi "
+          f"{np.mean(res['bj']['its']):.1f} (ratio {np.mean(res['mlp']['its']) / np.mean(res['bj']['its']):.3f})")
     h.close()
     he.close()

@@ -486,6 +486,32 @@ def test_mlp_gradient_matches_finite_differences():
         assert abs(fd - g[i]) <= 1e-6 * (1 + abs(g[i]))
 
 
+def test_mlp_forward_by_hand():
+    """A network with a handful of non-zero weights, evaluated by hand: layer
+    order (weights, then bias, then ReLU), a ReLU after each hidden layer and
+    none after the last.  Input 1: x0 = 2 gives h1 = (2.5, 0), h2 = (4, 1),
+    a3 = (-1, 3) -> h3 = (0, 3), y = (6.25, -3, 1).  Input 2: x0 = -1 gives
+    h1 = (0, 1.5), h2 = (0, 5.5), a3 = (-27.5, 5.5) -> h3 = (0, 5.5),
+    y = (11.25, -5.5, 1).  A missing third ReLU would give y0 = -3.75 on
+    input 1; a ReLU on the output would give y1 = 0."""
+    from oracle import mlp as M
+    nb = 3
+    W1, b1, W2, b2, W3, b3, W4, b4 = [np.zeros(s) for s in M.sizes(nb)]
+    W1[0, 0], W1[1, 0] = 1.0, -1.0
+    b1[0], b1[1] = 0.5, 0.5
+    W2[0, 0], W2[1, 1] = 2.0, 3.0
+    b2[0], b2[1] = -1.0, 1.0
+    W3[0, 0], W3[0, 1], W3[1, 0], W3[1, 1] = 1.0, -5.0, 0.5, 1.0
+    W4[0, 0], W4[0, 1], W4[1, 1], W4[2, 2] = 10.0, 2.0, -1.0, 7.0
+    b4[:] = (0.25, 0.0, 1.0)
+    theta = np.concatenate([a.ravel() for a in (W1, b1, W2, b2, W3, b3, W4, b4)] + [np.ones(1)])
+    assert theta.size == M.n_params(nb)
+    X = np.zeros((2, M.din_of(nb)))
+    X[0, 0], X[1, 0] = 2.0, -1.0
+    y, _ = M.forward(theta, X, nb)
+    np.testing.assert_array_equal(y, [[6.25, -3.0, 1.0], [11.25, -5.5, 1.0]])
+
+
 def test_mlp_adam_step_by_hand():
     from oracle import mlp as M
     th = np.array([1.0, -2.0]); g = np.array([0.5, -0.25])
