@@ -576,7 +576,8 @@ dg_status dg_newton_solve(dg_handle* h, int p, double c, int max_newton, double 
  * switched off and block Jacobi finishes the solve (info.outer = -1 then).
  * Parameters: one flat f32 vector W1 [128][din], b1, W2 [128][128], b2, W3,
  * b3, W4 [nb][128], b4 (row-major), sigma; inference uses them rounded to bf16 on the
- * tensor cores with f32 accumulation, training uses the same bf16-rounded
+ * tensor cores (tcgen05, f32 accumulation in tensor memory; the features, the
+ * output scaling and A_KK^-1 in f32), training uses the same bf16-rounded
  * values in f32 GEMMs and updates f32 master weights with Adam.
  */
 dg_status dg_mlp_num_params(int degree, int64_t* n);
@@ -605,7 +606,10 @@ dg_status dg_mlp_train(dg_handle* h, int steps, int batch_rows, float lr, uint64
 /* Loss (mean 0.5|y-t|^2) and gradient at the current weights on caller rows
    X device [rows][din], T device [rows][nb] (f32); loss, grad host. */
 dg_status dg_mlp_loss_grad(dg_handle* h, const float* X, const float* T, int rows, double* loss, float* grad);
-/* Tensor-core forward pass y on caller feature rows: X device [rows][din], Y device [rows][nb] (f32). */
+/* Tensor-core forward pass y on caller feature rows: X device [rows][din], Y device [rows][nb] (f32).
+   The inference kernel (tcgen05 MMAs with accumulators in tensor memory)
+   bounds its waits on the MMAs: DG_ERR_TIMEOUT if one ran out, here and in the
+   flexible solves that apply the network.  Synchronises. */
 dg_status dg_mlp_forward(dg_handle* h, const float* X, int rows, float* Y);
 
 /* ------------------------------------------------------------------------ */

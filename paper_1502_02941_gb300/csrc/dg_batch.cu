@@ -977,6 +977,7 @@ static dg_status batch_solve_t(dg_handle* h, int inner_dtype, const TA* Alo, con
             ++outer;
         }
     }
+    if (flex && result == DG_OK) result = dg_mlp_check_timeout(h);
     // per-instance results
     hst.resize(h->b_n);
     hbo.resize(h->b_n);

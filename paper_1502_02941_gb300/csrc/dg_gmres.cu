@@ -955,8 +955,12 @@ static dg_status gmres_f64(dg_handle* h, const double* F, double* x, dg_solve_in
         DG_CK(h, cudaMemcpyAsync(h->mlp.on, &one, sizeof(int), cudaMemcpyHostToDevice, h->stream));
     }
     const double* G = h->p.precond == DG_PRECOND_SCHWARZ ? h->G64 : nullptr;
-    const dg_status s = gmres_run<NB, double, double, double>(h, h->gw[0], h->A64, B, F, x, h->p.gmres_m, h->p.tol,
-                                                              h->p.max_it, info, mlp, h->Ah64, G);
+    dg_status s = gmres_run<NB, double, double, double>(h, h->gw[0], h->A64, B, F, x, h->p.gmres_m, h->p.tol,
+                                                        h->p.max_it, info, mlp, h->Ah64, G);
+    if (mlp) {
+        const dg_status t = dg_mlp_check_timeout(h);
+        if (t != DG_OK) s = t;
+    }
     if (h->gw[0].V) {
         h->basis = (const double*)h->gw[0].V;
         h->basis_ld = h->gw[0].ld;

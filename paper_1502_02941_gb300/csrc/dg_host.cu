@@ -280,6 +280,11 @@ extern "C" dg_status dg_create(dg_handle** out, int device, void* stream) {
         delete h;
         return DG_ERR_NOMEM;
     }
+    if (cudaMemset(h->dflag, 0, 64) != cudaSuccess) {
+        cudaFree(h->dflag);
+        delete h;
+        return DG_ERR_CUDA;
+    }
     // the allocation-free entry point's scratch address (dg_noalloc.cu)
     if (dg_noalloc_prepare(h) != DG_OK) {
         cudaFree(h->dflag);

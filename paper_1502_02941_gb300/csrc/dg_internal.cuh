@@ -69,6 +69,7 @@ struct GmresState;   // device-side solver state (dg_gmres.cu)
 #define DG_MLP_WIDTH 128
 #define DG_MLP_NOUTP 16      // output rows of the packed last layer (nb <= 10, zero padded)
 #define DG_MLP_NFEAT 8       // per-element features after the 4 nb residual entries
+#define DG_FLAG_MLP_TIMEOUT 8   // int slot of h->dflag: an inference kernel gave up waiting for its MMAs
 
 // Element-local MLP right preconditioner (dg_mlp.cu).
 struct MlpState {
@@ -300,6 +301,9 @@ dg_status dg_scratch(dg_handle* h, size_t bytes);   // ensure h->scratch >= byte
 // device address of the allocation-free entry point's scratch array, looked
 // up at handle creation (dg_noalloc.cu)
 dg_status dg_noalloc_prepare(dg_handle* h);
+// DG_ERR_TIMEOUT if the learned preconditioner's kernel gave up a bounded wait
+// since the last check (dg_mlp.cu); synchronises
+dg_status dg_mlp_check_timeout(dg_handle* h);
 // keep *p if its capacity *cap already holds bytes, else reallocate
 dg_status dg_ensure(dg_handle* h, void** p, size_t* cap, size_t bytes);
 

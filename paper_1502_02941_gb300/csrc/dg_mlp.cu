@@ -442,67 +442,115 @@ __global__ void k_mlp_pack(const float* __restrict__ theta, MlpOff o, MlpPack pk
 }
 
 // ---------------------------------------------------------------------------
-// fused tensor-core inference
+// fused tensor-core inference (tcgen05: accumulators in tensor memory)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint32_t* b) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<const uint32_t*>(&v);
-}
-
-// One warp: rows r0..r0+15 of act [rows][ACT_LD] (bf16) times W [N][K] (bf16,
-// row stride K): acc[nt][4] for N/8 n-tiles.
-template <int NT, int KSTEPS>
-__device__ __forceinline__ void warp_layer(const __nv_bfloat16* act, int act_ld, int r0, const __nv_bfloat16* W,
-                                           int wld, float (*acc)[4]) {
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-#pragma unroll
-    for (int nt = 0; nt < NT; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
-#pragma unroll
-    for (int ks = 0; ks < KSTEPS; ++ks) {
-        const int k0 = ks * 16;
-        uint32_t a[4];
-        a[0] = *reinterpret_cast<const uint32_t*>(act + (r0 + g) * act_ld + k0 + 2 * t);
-        a[1] = *reinterpret_cast<const uint32_t*>(act + (r0 + g + 8) * act_ld + k0 + 2 * t);
-        a[2] = *reinterpret_cast<const uint32_t*>(act + (r0 + g) * act_ld + k0 + 2 * t + 8);
-        a[3] = *reinterpret_cast<const uint32_t*>(act + (r0 + g + 8) * act_ld + k0 + 2 * t + 8);
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt) {
-            uint32_t b[2];
-            b[0] = *reinterpret_cast<const uint32_t*>(W + (nt * 8 + g) * wld + k0 + 2 * t);
-            b[1] = *reinterpret_cast<const uint32_t*>(W + (nt * 8 + g) * wld + k0 + 2 * t + 8);
-            mma_bf16(acc[nt], a, b);
-        }
-    }
-}
-
-// bias + relu, write back as bf16 into the warp's rows of act
-template <int NT>
-__device__ __forceinline__ void warp_store_relu(__nv_bfloat16* act, int act_ld, int r0, const float* b,
-                                                float (*acc)[4]) {
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    __syncwarp();
-#pragma unroll
-    for (int nt = 0; nt < NT; ++nt) {
-        const int c = nt * 8 + 2 * t;
-        const float b0 = b[c], b1 = b[c + 1];
-        *reinterpret_cast<uint32_t*>(act + (r0 + g) * act_ld + c) =
-            pack_bf16(fmaxf(acc[nt][0] + b0, 0.f), fmaxf(acc[nt][1] + b1, 0.f));
-        *reinterpret_cast<uint32_t*>(act + (r0 + g + 8) * act_ld + c) =
-            pack_bf16(fmaxf(acc[nt][2] + b0, 0.f), fmaxf(acc[nt][3] + b1, 0.f));
-    }
-    __syncwarp();
-}
-
+// One CTA of 128 threads per SM walks 128-row tiles (row = element).  Thread t
+// owns row t: it builds the row's features, and after each layer reads row t
+// of the accumulator (TMEM lane t).  Thread 0 issues the tcgen05.mma
+// instructions of a layer (M = 128, N = 128 or 16, K = 16 each, bf16 operands
+// from shared memory, f32 accumulation in TMEM) and commits them to an
+// mbarrier that all threads wait on.  Operands use the K-major layout without
+// swizzle: 8-row x 16-byte core matrices, LBO = 128 bytes between the core
+// matrices along K, SBO between 8-row groups (K/8 * 128 bytes).
 #define MLP_ROWS 128
-#define MLP_ACT_LD (MW + 8)    // padded row stride (bf16) of the activation tile
+#define MLP_THREADS 128
+#define MLP_ACT_SBO 2048                  // activation tile: 128 columns -> 16 core matrices per 8-row group
+#define MLP_WAIT_LIMIT (1u << 26)         // mbarrier polls before the kernel gives up (error flag)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// 64-bit shared-memory matrix descriptor: start address, leading and stride
+// byte offsets (each >> 4), descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::f16: f32 accumulator, bf16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void smem_fence_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 16 consecutive f32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Wait for phase `parity` of the mbarrier, at most MLP_WAIT_LIMIT polls;
+// false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    for (uint32_t it = 0; it < MLP_WAIT_LIMIT; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// Byte offset of element (row, k) in a K-major core-matrix tile whose 8-row
+// groups are sbo bytes apart.
+__device__ __forceinline__ uint32_t cm_off(int row, int k, uint32_t sbo) {
+    return (uint32_t)(row >> 3) * sbo + (uint32_t)(k >> 3) * 128u + (uint32_t)(row & 7) * 16u + (uint32_t)(k & 7) * 2u;
+}
+
+// 8 f32 values as 8 bf16 (one 16-byte unit of a core matrix row)
+__device__ __forceinline__ uint4 pack8_bf16(const float* v) {
+    uint4 u;
+    u.x = __bfloat16_as_ushort(__float2bfloat16_rn(v[0])) | ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[1])) << 16);
+    u.y = __bfloat16_as_ushort(__float2bfloat16_rn(v[2])) | ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[3])) << 16);
+    u.z = __bfloat16_as_ushort(__float2bfloat16_rn(v[4])) | ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[5])) << 16);
+    u.w = __bfloat16_as_ushort(__float2bfloat16_rn(v[6])) | ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[7])) << 16);
+    return u;
+}
+
+// The coefficient and shape features of elem_coef in f32 (they are rounded to
+// bf16 for the network).
+__device__ __forceinline__ void elem_coef32(int K, int ne, const double* __restrict__ geo, const int* inst,
+                                            const double* icoef, const double* scoef, float* out) {
+    const double* c = inst ? icoef + (size_t)DG_ICOEF * inst[K] : scoef;
+    const float j00 = (float)geo[G_J00 * (size_t)ne + K], j01 = (float)geo[G_J01 * (size_t)ne + K];
+    const float j10 = (float)geo[G_J10 * (size_t)ne + K], j11 = (float)geo[G_J11 * (size_t)ne + K];
+    const float x = (float)geo[G_X0 * (size_t)ne + K] + (j00 + j01) * (1.f / 3.f);
+    const float y = (float)geo[G_Y0 * (size_t)ne + K] + (j10 + j11) * (1.f / 3.f);
+    out[0] = log10f(fmaxf((float)c[0], 1e-12f)) * (1.f / 6.f) + 1.f;
+    out[1] = (float)c[2] + (float)c[3] * x + (float)c[4] * y;
+    out[2] = (float)c[5] + (float)c[6] * x + (float)c[7] * y;
+    out[3] = (float)c[1];
+    const float hs = rsqrtf((float)geo[G_DET * (size_t)ne + K]);
+    out[4] = j00 * hs;
+    out[5] = j01 * hs;
+    out[6] = j10 * hs;
+    out[7] = j11 * hs;
+}
 
 struct MlpRun {
     const __nv_bfloat16* wbf;
@@ -511,142 +559,211 @@ struct MlpRun {
     CoefSrc cs;
     const int* on;            // global enable flag (NULL = on)
     const int* iuse;          // per-instance enable flags (batch) or NULL
-    const double* B64;        // block-Jacobi inverses A_KK^-1 (f64 vectors)
-    const float* B32;         // (f32 vectors)
+    const float* B32;         // block-Jacobi inverses A_KK^-1 (f32 copy)
+    int* err;                 // device flag: an mbarrier wait ran out
 };
 
-// z_K += A_KK^-1 (scale * s_K * sigma * y_K) for every element (r, z vectors of type TV, selected
-// through the solver control exactly like the block-Jacobi apply).  Also used
-// with Xin != NULL: y for precomputed feature rows (parity tests).
+// Shared-memory layout of k_mlp_tc (byte offsets, 1024-aligned operand tiles).
+struct MlpSmem {
+    uint32_t w1, w2, w3, w4, act, bias, s, k, bar, slot, total;
+};
+__host__ __device__ inline MlpSmem mlp_smem_layout(int dinp) {
+    MlpSmem L;
+    uint32_t o = 0;
+    L.w1 = o; o += (uint32_t)MW * dinp * 2;
+    o = (o + 1023u) & ~1023u;
+    L.w2 = o; o += MW * MW * 2;
+    L.w3 = o; o += MW * MW * 2;
+    L.w4 = o; o += DG_MLP_NOUTP * MW * 2;
+    o = (o + 1023u) & ~1023u;
+    L.act = o; o += MLP_ROWS * MW * 2;
+    L.bias = o; o += sizeof(float) * (3 * MW + DG_MLP_NOUTP + 4);
+    L.s = o; o += sizeof(float) * MLP_ROWS;
+    L.k = o; o += sizeof(int) * MLP_ROWS;
+    o = (o + 15u) & ~15u;
+    L.bar = o; o += 16;
+    L.slot = o; o += 16;
+    L.total = o + 1024;   // slack to align the dynamic base to 1024 bytes
+    return L;
+}
+
+// Copy a row-major [N][K] bf16 matrix into the core-matrix layout (16 bytes
+// per thread and step).
+__device__ __forceinline__ void stage_cm(const __nv_bfloat16* __restrict__ src, int N, int K, unsigned char* dst) {
+    const int units = N * (K / 8);
+    for (int u = threadIdx.x; u < units; u += blockDim.x) {
+        const int n = u / (K / 8), k8 = u - n * (K / 8);
+        *reinterpret_cast<uint4*>(dst + cm_off(n, k8 * 8, (uint32_t)K * 16u)) =
+            *reinterpret_cast<const uint4*>(src + (size_t)n * K + k8 * 8);
+    }
+}
+
+// z_K += A_KK^-1 (scale * s_K * sigma * y_K) for every element (r, z vectors of
+// type TV, selected through the solver control exactly like the block-Jacobi
+// apply); with Xin != NULL: y for precomputed feature rows (parity tests).
 template <int NB, typename TV>
-__global__ void __launch_bounds__(256, 1) k_mlp_apply(const TV* __restrict__ r0p, TV* __restrict__ z0p,
-                                                       const int* __restrict__ nbr, int ne, MlpRun R, DevCtl ctl,
-                                                       VecSel sr, VecSel sz, const float* __restrict__ Xin,
-                                                       float* __restrict__ Yout) {
+__global__ void __launch_bounds__(MLP_THREADS, 1) k_mlp_tc(const TV* __restrict__ r0p, TV* __restrict__ z0p,
+                                                            const int* __restrict__ nbr, int ne, MlpRun R, DevCtl ctl,
+                                                            VecSel sr, VecSel sz, const float* __restrict__ Xin,
+                                                            float* __restrict__ Yout) {
     if (ctl.active && !*ctl.active) return;
     if (R.on && !*R.on) return;
-    extern __shared__ __align__(16) unsigned char smraw[];
+    extern __shared__ unsigned char smraw[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smraw + 1023u) & ~(uintptr_t)1023u);
     constexpr int DIN = 4 * NB + DG_MLP_NFEAT;
-    const int dinp = R.pk.dinp;
-    __nv_bfloat16* sW = reinterpret_cast<__nv_bfloat16*>(smraw);
-    float* sb = reinterpret_cast<float*>(smraw + sizeof(__nv_bfloat16) * R.pk.total);
-    __nv_bfloat16* act = reinterpret_cast<__nv_bfloat16*>(sb + 3 * MW + DG_MLP_NOUTP + 4);
-    float* ss = reinterpret_cast<float*>(act + MLP_ROWS * MLP_ACT_LD);
-    int* sk = reinterpret_cast<int*>(ss + MLP_ROWS);
-    // weights and biases once per CTA (persistent grid)
-    {
-        const uint4* src = reinterpret_cast<const uint4*>(R.wbf);
-        uint4* dst = reinterpret_cast<uint4*>(sW);
-        for (long i = threadIdx.x; i < R.pk.total / 8; i += blockDim.x) dst[i] = src[i];
-        for (int i = threadIdx.x; i < 3 * MW + DG_MLP_NOUTP + 1; i += blockDim.x) sb[i] = R.bias[i];
+    constexpr int DINP = (DIN + 15) / 16 * 16;   // = R.pk.dinp (checked by the launcher)
+    const MlpSmem SL = mlp_smem_layout(DINP);
+    float* sb = reinterpret_cast<float*>(sm + SL.bias);
+    float* ss = reinterpret_cast<float*>(sm + SL.s);
+    int* sk = reinterpret_cast<int*>(sm + SL.k);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + SL.bar);
+    uint32_t* slot = reinterpret_cast<uint32_t*>(sm + SL.slot);
+    unsigned char* act = sm + SL.act;
+    const int t = threadIdx.x, warp = t >> 5;
+    // weights (core-matrix layout) and biases once per CTA
+    stage_cm(R.wbf + R.pk.W1, MW, DINP, sm + SL.w1);
+    stage_cm(R.wbf + R.pk.W2, MW, MW, sm + SL.w2);
+    stage_cm(R.wbf + R.pk.W3, MW, MW, sm + SL.w3);
+    stage_cm(R.wbf + R.pk.W4, DG_MLP_NOUTP, MW, sm + SL.w4);
+    for (int i = t; i < 3 * MW + DG_MLP_NOUTP + 1; i += blockDim.x) sb[i] = R.bias[i];
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                     "r"(MW)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *slot;
+    const uint32_t tlane = tmem + ((uint32_t)(warp * 32) << 16);   // this warp's 32 TMEM lanes
+    const uint32_t s_act = smem_u32(act);
+    const uint32_t s_w[4] = {smem_u32(sm + SL.w1), smem_u32(sm + SL.w2), smem_u32(sm + SL.w3), smem_u32(sm + SL.w4)};
+    const int kdim[4] = {DINP, MW, MW, MW};
     const TV* __restrict__ r = Xin ? nullptr : sel(r0p, sr);
     TV* __restrict__ z = Xin ? nullptr : sel(z0p, sz);
     const int ntile = (ne + MLP_ROWS - 1) / MLP_ROWS;
-    const int warp = threadIdx.x >> 5;
-    for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
-        __syncthreads();
-        // ---- features (one thread per element)
-        if (threadIdx.x < MLP_ROWS) {
-            const int row = threadIdx.x;
-            const int K = tile * MLP_ROWS + row;
-            __nv_bfloat16* x = act + row * MLP_ACT_LD;
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < ntile && ok; tile += gridDim.x) {
+        // ---- features of row t (f32), written as bf16 in the core-matrix layout
+        {
+            const int K = tile * MLP_ROWS + t;
             bool live = K < ne;
             if (live && ctl.inst) live = ctl.iactive[ctl.inst[K]] && (!R.iuse || R.iuse[ctl.inst[K]]);
-            float s = 0.f;
+            float xv[DINP];
+#pragma unroll
+            for (int c = 0; c < DINP; ++c) xv[c] = 0.f;
+            float sc_row = 0.f;
             if (live && Xin) {
-                for (int c = 0; c < dinp; ++c) x[c] = __float2bfloat16_rn(c < DIN ? Xin[(size_t)K * DIN + c] : 0.f);
-                s = 1.f;
+                for (int c = 0; c < DIN; ++c) xv[c] = Xin[(size_t)K * DIN + c];
+                sc_row = 1.f;
             } else if (live) {
-                double p[4][NB];
-                double sq = 0.0;
+                float sq = 0.f;
 #pragma unroll
                 for (int sl = 0; sl < 4; ++sl) {
                     const int L = sl == 0 ? K : nbr[(size_t)(sl - 1) * ne + K];
 #pragma unroll
                     for (int i = 0; i < NB; ++i) {
-                        p[sl][i] = L >= 0 ? (double)r[(size_t)L * NB + i] : 0.0;
-                        sq += p[sl][i] * p[sl][i];
+                        const float v = L >= 0 ? (float)r[(size_t)L * NB + i] : 0.f;
+                        xv[sl * NB + i] = v;
+                        sq = fmaf(v, v, sq);
                     }
                 }
-                const double sd = sqrt(sq / (4 * NB)) + 1e-30;
+                const float sd = sqrtf(sq * (1.f / (4 * NB))) + 1e-30f;
+                const float inv = 1.f / sd;
 #pragma unroll
-                for (int sl = 0; sl < 4; ++sl)
-#pragma unroll
-                    for (int i = 0; i < NB; ++i) x[sl * NB + i] = __float2bfloat16_rn((float)(p[sl][i] / sd));
-                float cf[DG_MLP_NFEAT];
-                elem_coef(K, ne, R.cs.geo, R.cs.inst, R.cs.icoef, R.cs.scoef, cf);
-                for (int c = 0; c < DG_MLP_NFEAT; ++c) x[4 * NB + c] = __float2bfloat16_rn(cf[c]);
-                for (int c = DIN; c < dinp; ++c) x[c] = __float2bfloat16_rn(0.f);
+                for (int c = 0; c < 4 * NB; ++c) xv[c] *= inv;
+                elem_coef32(K, ne, R.cs.geo, R.cs.inst, R.cs.icoef, R.cs.scoef, xv + 4 * NB);
                 double sc = 1.0;
                 if (ctl.inst) sc = ctl.iscale ? ctl.iscale[ctl.inst[K]] : 1.0;
                 else if (ctl.scale) sc = ctl.scale[sr.j ? *sr.j + sr.add : 0];
-                s = (float)(sd * sc);
-            } else {
-                for (int c = 0; c < dinp; ++c) x[c] = __float2bfloat16_rn(0.f);
+                sc_row = sd * (float)sc;
             }
-            ss[row] = s;
-            sk[row] = live ? K : -1;
+#pragma unroll
+            for (int k8 = 0; k8 < DINP / 8; ++k8)
+                *reinterpret_cast<uint4*>(act + cm_off(t, k8 * 8, MLP_ACT_SBO)) = pack8_bf16(xv + k8 * 8);
+            ss[t] = sc_row;
+            sk[t] = live ? K : -1;
         }
-        __syncthreads();
-        // ---- four layers, warp w owns rows 16w .. 16w+15
-        const int r0 = warp * 16;
-        float acc[16][4];
-        if (dinp == 16) warp_layer<16, 1>(act, MLP_ACT_LD, r0, sW + R.pk.W1, dinp, acc);
-        else if (dinp == 32) warp_layer<16, 2>(act, MLP_ACT_LD, r0, sW + R.pk.W1, dinp, acc);
-        else warp_layer<16, 3>(act, MLP_ACT_LD, r0, sW + R.pk.W1, dinp, acc);
-        warp_store_relu<16>(act, MLP_ACT_LD, r0, sb, acc);
-        warp_layer<16, 8>(act, MLP_ACT_LD, r0, sW + R.pk.W2, MW, acc);
-        warp_store_relu<16>(act, MLP_ACT_LD, r0, sb + MW, acc);
-        warp_layer<16, 8>(act, MLP_ACT_LD, r0, sW + R.pk.W3, MW, acc);
-        warp_store_relu<16>(act, MLP_ACT_LD, r0, sb + 2 * MW, acc);
-        float out[2][4];
-        warp_layer<2, 8>(act, MLP_ACT_LD, r0, sW + R.pk.W4, MW, out);
-        // ---- u_K = s sigma y_K, staged as f32 in the warp's own activation rows
-        const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-        const float sig = sb[3 * MW + DG_MLP_NOUTP];
-        __syncwarp();
-#pragma unroll
-        for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-            for (int hrow = 0; hrow < 2; ++hrow)
-#pragma unroll
-                for (int cc = 0; cc < 2; ++cc) {
-                    const int row = r0 + g + 8 * hrow;
-                    const int col = nt * 8 + 2 * t + cc;
-                    const int K = sk[row];
-                    if (K < 0 || col >= NB) continue;
-                    const float y = out[nt][2 * hrow + cc] + sb[3 * MW + col];
-                    if (Yout) Yout[(size_t)K * NB + col] = y;
-                    else reinterpret_cast<float*>(act + row * MLP_ACT_LD)[col] = ss[row] * sig * y;
+        // ---- four layers; D (TMEM, 128 lanes x 128 f32 columns) is reused
+        for (int layer = 0; layer < 4 && ok; ++layer) {
+            smem_fence_async();   // this thread's shared-memory writes -> the tensor core's (async) proxy
+            tc_fence_before();
+            __syncthreads();
+            if (t == 0) {
+                tc_fence_after();
+                const int N = layer == 3 ? DG_MLP_NOUTP : MW;
+                const uint32_t idesc = layer == 3 ? tc_idesc(128, DG_MLP_NOUTP) : tc_idesc(128, MW);
+                const uint32_t wsbo = (uint32_t)kdim[layer] * 16u;
+                for (int ks = 0; ks < kdim[layer] / 16; ++ks)
+                    tc_mma(tmem, tc_desc(s_act + ks * 256u, 128u, MLP_ACT_SBO), tc_desc(s_w[layer] + ks * 256u, 128u, wsbo),
+                           idesc, ks > 0 ? 1u : 0u);
+                tc_commit(bar);
+                (void)N;
+            }
+            // the give-up decision is block-uniform, so every thread takes the same barriers
+            if (__syncthreads_or(mbar_wait(bar, phase) ? 0 : 1)) {
+                ok = false;
+                if (t == 0) {
+                    if (R.err) atomicExch(R.err, 1);
+                    mbar_wait(bar, phase);   // one more bounded wait for the MMAs in flight
                 }
-        __syncwarp();
-        // ---- z_K += A_KK^-1 u_K (one lane per row of the warp)
-        if (!Yout && lane < 16) {
-            const int row = r0 + lane;
-            const int K = sk[row];
-            if (K >= 0) {
-                const float* u = reinterpret_cast<const float*>(act + row * MLP_ACT_LD);
+                break;
+            }
+            phase ^= 1u;
+            tc_fence_after();
+            if (layer < 3) {
+                // bias + relu of row t, written back as the next layer's A operand
+                const float* b = sb + layer * MW;
+#pragma unroll 1
+                for (int c0 = 0; c0 < MW; c0 += 16) {
+                    float v[16];
+                    tc_ld16(tlane + (uint32_t)c0, v);
 #pragma unroll
-                for (int i = 0; i < NB; ++i) {
-                    double a = 0.0;
+                    for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i] + b[c0 + i], 0.f);
+                    *reinterpret_cast<uint4*>(act + cm_off(t, c0, MLP_ACT_SBO)) = pack8_bf16(v);
+                    *reinterpret_cast<uint4*>(act + cm_off(t, c0 + 8, MLP_ACT_SBO)) = pack8_bf16(v + 8);
+                }
+            } else {
+                // y = D + b4; z_K += A_KK^-1 (s sigma y) in f32, added to z in TV
+                float v[16];
+                tc_ld16(tlane, v);
+                const int K = sk[t];
+                const float sig = sb[3 * MW + DG_MLP_NOUTP];
+                if (K >= 0) {
+                    float u[NB];
 #pragma unroll
-                    for (int j = 0; j < NB; ++j) {
-                        if constexpr (sizeof(TV) == 8)
-                            a = fma(R.B64[dg_blk_index<double>(K, 0, i * NB + j, NB, 1)], (double)u[j], a);
-                        else
-                            a = fma((double)R.B32[dg_blk_index<float>(K, 0, i * NB + j, NB, 1)], (double)u[j], a);
+                    for (int i = 0; i < NB; ++i) u[i] = v[i] + sb[3 * MW + i];
+                    if (Yout) {
+#pragma unroll
+                        for (int i = 0; i < NB; ++i) Yout[(size_t)K * NB + i] = u[i];
+                    } else {
+                        const float s = ss[t] * sig;
+#pragma unroll
+                        for (int i = 0; i < NB; ++i) u[i] *= s;
+#pragma unroll
+                        for (int i = 0; i < NB; ++i) {
+                            float a = 0.f;
+#pragma unroll
+                            for (int j = 0; j < NB; ++j) a = fmaf(R.B32[dg_blk_index<float>(K, 0, i * NB + j, NB, 1)], u[j], a);
+                            z[(size_t)K * NB + i] = (TV)((double)z[(size_t)K * NB + i] + (double)a);
+                        }
                     }
-                    z[(size_t)K * NB + i] = (TV)((double)z[(size_t)K * NB + i] + a);
                 }
             }
         }
     }
-}
-
-static size_t mlp_smem(const MlpPack& pk) {
-    return sizeof(__nv_bfloat16) * pk.total + sizeof(float) * (3 * MW + DG_MLP_NOUTP + 4) +
-           sizeof(__nv_bfloat16) * MLP_ROWS * MLP_ACT_LD + sizeof(float) * MLP_ROWS + sizeof(int) * MLP_ROWS;
+    // free the tensor memory: every thread's loads have completed (wait::ld)
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(MW) : "memory");
 }
 
 template <int NB, typename TV>
@@ -663,20 +780,22 @@ static dg_status launch_mlp(dg_handle* h, const TV* r, TV* z, DevCtl ctl, VecSel
     for (int t = 0; t < 8; ++t) R.cs.scoef[t] = S.coef[t];
     R.on = Xin ? nullptr : S.on;
     R.iuse = iuse;
-    R.B64 = h->Binv64;
     R.B32 = h->Binv32;
-    const size_t smem = mlp_smem(R.pk);
+    R.err = h->dflag + DG_FLAG_MLP_TIMEOUT;
+    if (!Xin && !R.B32) return dg_fail(h, DG_ERR_STATE, "the learned correction needs the block-Jacobi set-up");
+    if (R.pk.dinp != (4 * NB + DG_MLP_NFEAT + 15) / 16 * 16) return dg_fail(h, DG_ERR_STATE, "MLP input width");
+    const size_t smem = mlp_smem_layout(R.pk.dinp).total;
     static thread_local int configured[DG_MAXK + 1][2] = {};
     int& cfg = configured[dg_nb(1) == NB ? 1 : (dg_nb(2) == NB ? 2 : 3)][sizeof(TV) == 8 ? 1 : 0];
     if (!cfg) {
-        DG_CK(h, cudaFuncSetAttribute(k_mlp_apply<NB, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        DG_CK(h, cudaFuncSetAttribute(k_mlp_tc<NB, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         cfg = 1;
     }
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
     const int ntile = (ne + MLP_ROWS - 1) / MLP_ROWS;
     const int grid = ntile < sms ? ntile : sms;
-    k_mlp_apply<NB, TV><<<grid, 256, smem, h->stream>>>(r, z, h->nbr, ne, R, ctl, sr, sz, Xin, Yout);
+    k_mlp_tc<NB, TV><<<grid, MLP_THREADS, smem, h->stream>>>(r, z, h->nbr, ne, R, ctl, sr, sz, Xin, Yout);
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(h->stream, &cap);
     if (cap == cudaStreamCaptureStatusNone) h->nlaunch += 1;   // captured launches are counted per graph launch
@@ -979,7 +1098,18 @@ extern "C" dg_status dg_mlp_forward(dg_handle* h, const float* X, int rows, floa
     }
     if (s != DG_OK) return s;
     DG_LAUNCH_CK(h);
-    return DG_OK;
+    return dg_mlp_check_timeout(h);
+}
+
+// The inference kernel's bounded waits: DG_ERR_TIMEOUT (and the flag cleared)
+// if a launch since the last check gave up waiting for its MMAs.  Synchronises.
+dg_status dg_mlp_check_timeout(dg_handle* h) {
+    int f = 0;
+    DG_CK(h, cudaMemcpyAsync(&f, h->dflag + DG_FLAG_MLP_TIMEOUT, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    DG_CK(h, cudaStreamSynchronize(h->stream));
+    if (!f) return DG_OK;
+    DG_CK(h, cudaMemsetAsync(h->dflag + DG_FLAG_MLP_TIMEOUT, 0, sizeof(int), h->stream));
+    return dg_fail(h, DG_ERR_TIMEOUT, "the learned preconditioner's tensor-core kernel gave up waiting for its MMAs");
 }
 
 // Copy collected rows to the host (first `max_rows`).
