@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and learned sections")
     ap.add_argument("--batch-instances", type=int, default=1024)
-    ap.add_argument("--learned-instances", type=int, default=16)
+    ap.add_argument("--learned-instances", type=int, default=16, help="training instances")
+    ap.add_argument("--learned-eval", type=int, default=1024, help="unseen instances evaluated")
     ap.add_argument("--learned-steps", type=int, default=4000)
     return ap.parse_args()
 
@@ -211,6 +212,38 @@ def batched_section(local, stream, n_inst, runs=BATCH_RUNS):
     return out
 
 
+def bump512_section(local, stream, inner_m=50, inner_tol=1e-4):
+    """The mixed-precision workload of the 512x512 split squares (524288
+    triangles), P3 (5.24 M unknowns): SIPG, eps = 1e-3, rotating b, alpha = 0.1,
+    Gaussian-bump solution, Dirichlet left/bottom and Neumann right/top; one
+    solve to rel-res 1e-10 by f64 FGMRES(50) around f32 GMRES inner solves with
+    the Schwarz preconditioner (GMRES-based refinement), timed after an untimed
+    set-up; the relative residual is re-measured with the f64 apply."""
+    import torch
+    from paper_1502_02941_gb300 import dg as D, problem, workloads as W
+    c = W.gaussian_bump_p3(N=512)
+    h = D.DG(local)
+    t0 = time.perf_counter()
+    problem.setup(h, c, store=D.DG_STORE_F64 | D.DG_STORE_F32, gmres_m=50, tol=1e-10, max_it=400000,
+                  precond=D.DG_PRECOND_SCHWARZ)
+    h.precond_setup(D.DG_PRECOND_SCHWARZ)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    info = h.info()
+    sec, (x, si) = _events_time(stream, lambda: h.gmres_ir_solve(D.DG_F32, inner_m=inner_m, inner_tol=inner_tol,
+                                                                 max_outer=5000, raise_on_nonconv=False))
+    F = h.rhs()
+    rr = (torch.linalg.norm(F - h.apply(x)) / torch.linalg.norm(F)).item()
+    l2, _ = h.l2_error(x, problem.exact_at_error_points(h, c.problem))
+    h.close()
+    return {"workload": "512x512 split squares (524288 triangles), P3 (5242880 dofs), SIPG, eps=1e-3, rotating b, "
+                        "alpha=0.1, Gaussian bump, Dirichlet left/bottom, Neumann right/top",
+            "solver": f"f64 FGMRES(50) around f32 GMRES({inner_m}) inner solves to {inner_tol:g} or 8 cycles, "
+                      "Schwarz preconditioner", "setup_s": setup_s, "seconds": sec, "solves_per_s": 1.0 / sec,
+            "inner_iterations": si.iterations, "outer": si.outer, "relres": si.relres, "relres_check": rr,
+            "converged": si.status == 0, "l2_error": l2, "dofs": info.dofs}
+
+
 def nonlinear_section(local, stream):
     """The paper's non-linear example (tanh layer, eps = 1e-6, b = (1,2)/sqrt(5),
     alpha = 1, r(u) = u^2, SIPG) on 256x256 split squares with P2: Newton to
@@ -239,39 +272,64 @@ def nonlinear_section(local, stream):
             "k_nonlin_ms": ksec / reps * 1e3, "k_nonlin_elements_per_s": info.ne * reps / ksec}
 
 
-def learned_section(local, stream, n_inst, steps):
+LEARNED_RUNS = (
+    # name, preconditioner, inner precision (f64: batched f64 GMRES(50); f32: f32 inner solves + f64 refinement)
+    ("bj_f64", "bj", "f64"), ("schwarz_f64", "schwarz", "f64"), ("mlp_f64", "mlp", "f64"),
+    ("bj_f32_refined", "bj", "f32"), ("schwarz_f32_refined", "schwarz", "f32"), ("mlp_f32_refined", "mlp", "f32"),
+)
+
+
+def learned_section(local, stream, n_train, steps, n_eval, chunk=1024, runs=LEARNED_RUNS):
     """Learned preconditioner on the learned workload (64x64 split squares, P2,
-    batched-workload coefficients): collect rows from the f64 solves of n_inst
-    training instances, train on the GPU, then solve n_inst unseen instances
-    with block Jacobi and with the network (flexible GMRES), in f64 and with
-    f32 inner solves + f64 refinement."""
+    batched-workload coefficients): collect rows from the f64 solves of n_train
+    training instances, train on the GPU, then solve n_eval unseen instances
+    (in batches of at most `chunk`) with block Jacobi, with the Schwarz
+    preconditioner and with the network (flexible GMRES), in f64 and with f32
+    inner solves + f64 refinement; steps and time per instance and the ratios
+    of the network against both."""
     import numpy as np
     from paper_1502_02941_gb300 import dg as D, learned as L
+    pcs = {"bj": D.DG_PRECOND_BLOCK_JACOBI, "schwarz": D.DG_PRECOND_SCHWARZ, "mlp": D.DG_PRECOND_MLP}
     h = D.DG(local)
-    t_col, _ = _events_time(stream, lambda: (L.make_batch(h, n_inst, 64, first=0, gmres_m=50),
+    t_col, _ = _events_time(stream, lambda: (L.make_batch(h, n_train, 64, first=0, gmres_m=50),
                                              h.mlp_init(seed=7), L.collect(h)))
     rows = h.mlp_rows()
     t_train, (loss, _) = _events_time(stream, lambda: L.train(h, steps=steps))
     theta = h.mlp_get_weights()
     h.close()
-    he = D.DG(local)
-    L.make_batch(he, n_inst, 64, first=1000, gmres_m=50, store=D.DG_STORE_F64 | D.DG_STORE_F32)
-    he.mlp_set_weights(theta)
-    out = {"workload": f"{n_inst} training + {n_inst} unseen instances, 64x64 split squares (8192 triangles), P2",
-           "train_rows": rows, "collect_s": t_col, "train_steps": steps, "train_s": t_train,
-           "loss_first": float(loss[0]), "loss_last": float(loss[-1])}
-    for name, pc, dt in (("bj_f64", D.DG_PRECOND_BLOCK_JACOBI, D.DG_F64), ("mlp_f64", D.DG_PRECOND_MLP, D.DG_F64),
-                         ("bj_f32_refined", D.DG_PRECOND_BLOCK_JACOBI, D.DG_F32),
-                         ("mlp_f32_refined", D.DG_PRECOND_MLP, D.DG_F32)):
-        he.set_params(precond=pc, tol=1e-10, max_it=20000)
-        he.batch_solve(dt, inner_m=50, inner_tol=1e-4, max_outer=60, raise_on_nonconv=False)   # warm-up
-        sec, (x, its, rr, st) = _events_time(stream, lambda: he.batch_solve(
-            dt, inner_m=50, inner_tol=1e-4, max_outer=60, raise_on_nonconv=False))
-        out[name] = {"seconds": sec, "solves_per_s": n_inst / sec, "converged": int((st == 0).sum()),
+    out = {"workload": f"{n_train} training + {n_eval} unseen instances (from instance 1000 on), 64x64 split squares "
+                       f"(8192 triangles), P2, solved in batches of at most {chunk} instances",
+           "train_instances": n_train, "eval_instances": n_eval, "train_rows": rows, "collect_s": t_col,
+           "train_steps": steps, "train_s": t_train, "loss_first": float(loss[0]), "loss_last": float(loss[-1])}
+    acc = {name: {"seconds": 0.0, "its": [], "converged": 0} for name, _, _ in runs}
+    for first in range(0, n_eval, chunk):
+        n = min(chunk, n_eval - first)
+        he = D.DG(local)
+        L.make_batch(he, n, 64, first=1000 + first, gmres_m=50, store=D.DG_STORE_F64 | D.DG_STORE_F32)
+        he.precond_setup(D.DG_PRECOND_SCHWARZ)
+        he.mlp_set_weights(theta)
+        for name, pc, inner in runs:
+            dt = D.DG_F64 if inner == "f64" else D.DG_F32
+            he.set_params(precond=pcs[pc], tol=1e-10, max_it=20000)
+            if first == 0:
+                he.batch_solve(dt, inner_m=50, inner_tol=1e-4, max_outer=60, raise_on_nonconv=False)   # warm-up
+            sec, (x, its, rr, st) = _events_time(stream, lambda: he.batch_solve(
+                dt, inner_m=50, inner_tol=1e-4, max_outer=60, raise_on_nonconv=False))
+            a = acc[name]
+            a["seconds"] += sec
+            a["its"] += [int(v) for v in its]
+            a["converged"] += int((st == 0).sum())
+        he.close()
+    for name, a in acc.items():
+        its = np.array(a["its"])
+        out[name] = {"seconds": a["seconds"], "solves_per_s": n_eval / a["seconds"], "converged": a["converged"],
                      "its_median": int(np.median(its)), "its_mean": float(its.mean()), "its_max": int(its.max())}
-    out["its_ratio_mlp_vs_bj_f64"] = out["mlp_f64"]["its_mean"] / out["bj_f64"]["its_mean"]
-    out["time_ratio_mlp_vs_bj_f64"] = out["mlp_f64"]["seconds"] / out["bj_f64"]["seconds"]
-    he.close()
+    for base in ("bj", "schwarz"):
+        for inner in ("f64", "f32_refined"):
+            m, b = out.get(f"mlp_{inner}"), out.get(f"{base}_{inner}")
+            if m and b:
+                out[f"its_ratio_mlp_vs_{base}_{inner}"] = m["its_mean"] / b["its_mean"]
+                out[f"time_ratio_mlp_vs_{base}_{inner}"] = m["seconds"] / b["seconds"]
     return out
 
 
@@ -692,8 +750,10 @@ def main():
             "mixed": mixed, "assembly": assembly, "kernels": kernels, "hbm_peak_GBps": peak}
     if not args.no_extras:
         line["batched"] = batched_section(local, stream, args.batch_instances)
-        line["learned"] = learned_section(local, stream, args.learned_instances, args.learned_steps)
+        line["learned"] = learned_section(local, stream, args.learned_instances, args.learned_steps,
+                                          args.learned_eval)
         line["nonlinear"] = nonlinear_section(local, stream)
+        line["bump512_p3"] = bump512_section(local, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ref_its, _ = oracle_iteration_counts()
         scale_its = ref_its if ref_its else its

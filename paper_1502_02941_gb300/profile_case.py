@@ -6,7 +6,11 @@ profilers (a small, self-contained case: ~0.6 GB on the device).
     python -m paper_1502_02941_gb300.profile_case --kernel step --reps 1
 
 dots / update: the Arnoldi multi-dot / update kernel of f64 (or --f32) GMRES at
-step j on a synthetic basis (dg_profile_kernel); apply64 / apply32 / apply16:
+step j on a synthetic basis (dg_profile_kernel); mlp: the learned
+preconditioner's tensor-core inference (dg_mlp_forward) on one feature row
+per element (131072 rows); bsolve: one batched f32 GMRES-based refinement
+(Schwarz) of the P2 instances among the first --batch instances of the
+batched workload; apply64 / apply32 / apply16:
 the block-sparse operator apply on the f64 / f32 / bf16 block copy; assemble:
 one assembly; step: the benchmark's step (mesh upload, assembly, block-Jacobi
 set-up and f64 GMRES(50) to 1e-10 for NIPG and SIPG) after one untimed step,
@@ -22,7 +26,9 @@ import json
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--kernel", required=True,
-                    choices=["dots", "update", "apply64", "apply32", "apply16", "assemble", "step"])
+                    choices=["dots", "update", "apply64", "apply32", "apply16", "assemble", "step", "mlp",
+                             "bsolve"])
+    ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--j", type=int, default=25)
     ap.add_argument("--f32", action="store_true", help="f32 Arnoldi kernels (dots / update)")
     ap.add_argument("--reps", type=int, default=3)
@@ -37,6 +43,24 @@ def main(argv=None):
 
     cfg = W.boundary_layer_p2(method=2, N=a.N)
     h = D.DG(0)
+    if a.kernel == "bsolve":
+        cfgs, ma, starts, coeffs = W.batch_by_degree("batched", a.batch)[2]
+        problem.setup_batch(h, cfgs, ma, starts, coeffs, store=D.DG_STORE_F64 | D.DG_STORE_F32, gmres_m=50,
+                            tol=1e-10, max_it=20000, precond=D.DG_PRECOND_SCHWARZ)
+        h.precond_setup(D.DG_PRECOND_SCHWARZ)
+        tile = h.batch_autotune()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        for _ in range(a.reps):
+            e0.record()
+            _, its, _, st = h.batch_gmres_ir_solve(D.DG_F32, inner_m=32, inner_tol=1e-3, max_outer=1000)
+            e1.record()
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        print(json.dumps({"kernel": "bsolve", "instances": len(cfgs), "dofs": h.info().dofs, "tile": tile,
+                          "ms": tot / a.reps, "its_max": int(its.max()), "converged": int((st == 0).sum())}))
+        h.close()
+        return
     if a.kernel == "step":
         ma = W.structured_mesh(a.N)
         problem.setup(h, cfg, mesh=ma, assemble=False)
@@ -81,6 +105,24 @@ def main(argv=None):
             e1.synchronize()
             tot += e0.elapsed_time(e1)
         out["ms"] = tot / a.reps
+    elif a.kernel == "mlp":
+        h.mlp_init(seed=3)
+        rows = info.ne
+        din = 4 * info.nb + 8
+        X = torch.randn((rows, din), dtype=torch.float32, device="cuda")
+        Y = torch.empty((rows, info.nb), dtype=torch.float32, device="cuda")
+        h.check(D.dg_mlp_forward(h.h, X, rows, Y))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        for _ in range(a.reps):
+            e0.record()
+            h.check(D.dg_mlp_forward(h.h, X, rows, Y))
+            e1.record()
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        out["ms"] = tot / a.reps
+        out["rows"] = rows
+        out["tflops"] = 2.0 * rows * (32 * 128 + 2 * 128 * 128 + 128 * 16) / (out["ms"] / 1e3) / 1e12
     elif a.kernel in ("dots", "update"):
         which = D.DG_PROF_DOTS if a.kernel == "dots" else D.DG_PROF_UPDATE
         out["j"] = a.j
