@@ -301,11 +301,15 @@ __global__ void __launch_bounds__(GM_TX* GM_TY) k_gm_dots(const TV* __restrict__
             partials[(long)t0 * gx + blockIdx.x] = r;
         }
     } else {
+        // only the accumulators that hold a dot are reduced (warp-uniform test):
+        // every f64 instruction here costs time on this GPU's FP64 pipe
 #pragma unroll
         for (int k = 0; k < GM_DPT; ++k) {
             const int d = ty + GM_TY * k;
-            const double v = dg_warp_sum(acc[k].get());
-            if (tx == 0 && d <= dlast) partials[(long)d * gx + blockIdx.x] = v;
+            if (d <= dlast) {
+                const double v = dg_warp_sum(acc[k].get());
+                if (tx == 0) partials[(long)d * gx + blockIdx.x] = v;
+            }
         }
     }
     if (!last_block(&st->arrive)) return;
@@ -423,18 +427,6 @@ __global__ void __launch_bounds__(256) k_gm_update(TV* V, long ld, long nvec, Gm
 // ---------------------------------------------------------------------------
 // f32 Arnoldi kernels (the inner GMRES of the mixed-precision solvers)
 // ---------------------------------------------------------------------------
-// Sum of two two-float numbers (hi, lo): Knuth's TwoSum of the high parts,
-// the low parts added to its error, renormalised (Dekker's fast TwoSum).  The
-// compiler keeps the order of these additions (no fast-math flags).
-__device__ __forceinline__ float2 f2_add(float2 a, float2 b) {
-    const float s = a.x + b.x;
-    const float bp = s - a.x;
-    float e = (a.x - (s - bp)) + (b.x - bp);
-    e += a.y + b.y;
-    const float hi = s + e;
-    return make_float2(hi, e - (hi - s));
-}
-
 #define GM32_THREADS 512
 #define GM32_WARPS (GM32_THREADS / 32)
 #define GM32_G 16   // dots per warp group

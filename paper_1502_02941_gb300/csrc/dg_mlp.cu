@@ -444,7 +444,8 @@ __global__ void k_mlp_pack(const float* __restrict__ theta, MlpOff o, MlpPack pk
 // ---------------------------------------------------------------------------
 // fused tensor-core inference (tcgen05: accumulators in tensor memory)
 // ---------------------------------------------------------------------------
-// One CTA of 128 threads per SM walks 128-row tiles (row = element).  Thread t
+// CTAs of 128 threads (two per SM where the shared memory fits) walk 128-row
+// tiles (row = element).  Thread t
 // owns row t: it builds the row's features, and after each layer reads row t
 // of the accumulator (TMEM lane t).  Thread 0 issues the tcgen05.mma
 // instructions of a layer (M = 128, N = 128 or 16, K = 16 each, bf16 operands
@@ -602,7 +603,7 @@ __device__ __forceinline__ void stage_cm(const __nv_bfloat16* __restrict__ src, 
 // type TV, selected through the solver control exactly like the block-Jacobi
 // apply); with Xin != NULL: y for precomputed feature rows (parity tests).
 template <int NB, typename TV>
-__global__ void __launch_bounds__(MLP_THREADS, 1) k_mlp_tc(const TV* __restrict__ r0p, TV* __restrict__ z0p,
+__global__ void __launch_bounds__(MLP_THREADS, 2) k_mlp_tc(const TV* __restrict__ r0p, TV* __restrict__ z0p,
                                                             const int* __restrict__ nbr, int ne, MlpRun R, DevCtl ctl,
                                                             VecSel sr, VecSel sz, const float* __restrict__ Xin,
                                                             float* __restrict__ Yout) {
@@ -791,10 +792,15 @@ static dg_status launch_mlp(dg_handle* h, const TV* r, TV* z, DevCtl ctl, VecSel
         DG_CK(h, cudaFuncSetAttribute(k_mlp_tc<NB, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         cfg = 1;
     }
-    int sms = 0;
+    // as many CTAs per SM as the shared memory holds (two for P1 / P2, whose
+    // weights and activation tile take 112 KB; one for P3): one CTA's feature
+    // gathers and epilogues then overlap the other's MMAs
+    int sms = 0, per_sm = 1;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_tc<NB, TV>, MLP_THREADS, smem);
+    per_sm = per_sm < 1 ? 1 : (per_sm > 2 ? 2 : per_sm);
     const int ntile = (ne + MLP_ROWS - 1) / MLP_ROWS;
-    const int grid = ntile < sms ? ntile : sms;
+    const int grid = ntile < per_sm * sms ? ntile : per_sm * sms;
     k_mlp_tc<NB, TV><<<grid, MLP_THREADS, smem, h->stream>>>(r, z, h->nbr, ne, R, ctl, sr, sz, Xin, Yout);
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(h->stream, &cap);

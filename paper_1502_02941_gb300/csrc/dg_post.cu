@@ -129,14 +129,23 @@ __global__ void k_densify(const double* __restrict__ A, const int* __restrict__ 
     M[((long)K * nb + i) * n + (long)L * nb + j] = A[dg_blk_index<double>(K, s, m, nb, 4)];
 }
 
-// LU with partial pivoting in one CTA (1024 threads); matrix in global memory.
-__global__ void __launch_bounds__(1024) k_dense_lu_solve(double* M, double* b, int n, int* flag) {
+// Dense LU with partial pivoting, blocked and right-looking (panels of LU_B
+// columns), on the row-major n x n matrix M in global memory; the row swaps
+// are applied to whole rows of M and to b, so that at the end P M = L U with
+// the unit lower L below the diagonal, U on and above it, and b = P b.
+#define LU_B 32
+
+// Factor the panel of columns [k0, k0 + bw) over rows k0..n-1 (one CTA):
+// per column the pivot (largest |M[r][c]|, lowest index on ties), the swap of
+// rows c and p across all n columns and in b, the multipliers below the
+// diagonal, and the rank-1 update of the panel's remaining columns.  A zero
+// pivot sets *flag (the factors are then meaningless; no access leaves M).
+__global__ void __launch_bounds__(1024) k_lu_panel(double* M, double* b, int n, int k0, int bw, int* flag) {
     __shared__ double sv[32];
     __shared__ int si[32];
     __shared__ int piv;
     const int t = threadIdx.x, nt = blockDim.x, lane = t & 31, wid = t >> 5;
-    for (int c = 0; c < n; ++c) {
-        // pivot: argmax |M[r][c]|, r >= c
+    for (int c = k0; c < k0 + bw; ++c) {
         double best = -1.0;
         int bi = c;
         for (int r = c + t; r < n; r += nt) {
@@ -174,32 +183,82 @@ __global__ void __launch_bounds__(1024) k_dense_lu_solve(double* M, double* b, i
         }
         __syncthreads();
         const double d = M[(long)c * n + c];
-        if (d == 0.0) return;  // singular: flag already set
-        for (int r = c + 1 + t; r < n; r += nt) M[(long)r * n + c] /= d;
+        const double inv = d != 0.0 ? 1.0 / d : 0.0;
+        for (int r = c + 1 + t; r < n; r += nt) M[(long)r * n + c] *= inv;
         __syncthreads();
-        // trailing update, one row per warp, columns across lanes
-        for (int r = c + 1 + wid; r < n; r += nt / 32) {
-            const double l = M[(long)r * n + c];
-            if (l != 0.0)
-                for (int j = c + 1 + lane; j < n; j += 32) M[(long)r * n + j] -= l * M[(long)c * n + j];
-            if (lane == 0) b[r] -= l * b[c];
+        const int w = k0 + bw - c - 1;   // panel columns right of c
+        if (w > 0) {
+            const long cnt = (long)(n - c - 1) * w;
+            for (long e = t; e < cnt; e += nt) {
+                const int r = c + 1 + (int)(e / w), j = c + 1 + (int)(e % w);
+                M[(long)r * n + j] -= M[(long)r * n + c] * M[(long)c * n + j];
+            }
         }
         __syncthreads();
     }
-    // back substitution: x stored in b
-    for (int r = n - 1; r >= 0; --r) {
-        double s = 0.0;
-        for (int j = r + 1 + t; j < n; j += nt) s += M[(long)r * n + j] * b[j];
-        s = dg_warp_sum(s);
-        if (lane == 0) sv[wid] = s;
-        __syncthreads();
-        if (t == 0) {
-            double tot = 0.0;
-            for (int w = 0; w < nt / 32; ++w) tot += sv[w];
-            b[r] = (b[r] - tot) / M[(long)r * n + r];
-        }
+}
+
+// U12 = L11^-1 A12: rows k0..k0+bw-1, columns k0+bw..n-1, unit lower L11; one
+// thread per column.
+__global__ void __launch_bounds__(256) k_lu_trsm(double* M, int n, int k0, int bw) {
+    const int j = k0 + bw + blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    for (int i = 1; i < bw; ++i) {
+        double s = M[(long)(k0 + i) * n + j];
+        for (int l = 0; l < i; ++l) s -= M[(long)(k0 + i) * n + k0 + l] * M[(long)(k0 + l) * n + j];
+        M[(long)(k0 + i) * n + j] = s;
+    }
+}
+
+// A22 -= L21 U12 over rows and columns k0+bw..n-1 (inner dimension bw <=
+// LU_B): 32 x 32 output tiles, 256 threads with 4 outputs each, the tile's L21
+// rows and U12 columns staged in shared memory.
+__global__ void __launch_bounds__(256) k_lu_gemm(double* M, int n, int k0, int bw) {
+    __shared__ double Ls[32][LU_B + 1], Us[LU_B][32 + 1];
+    const int r0 = k0 + bw + blockIdx.y * 32, c0 = k0 + bw + blockIdx.x * 32;
+    const int t = threadIdx.x;
+    for (int e = t; e < 32 * LU_B; e += 256) {
+        const int rr = e / LU_B, kk = e % LU_B;
+        Ls[rr][kk] = (r0 + rr < n && kk < bw) ? M[(long)(r0 + rr) * n + k0 + kk] : 0.0;
+        const int k2 = e / 32, cc = e % 32;
+        Us[k2][cc] = (c0 + cc < n && k2 < bw) ? M[(long)(k0 + k2) * n + c0 + cc] : 0.0;
+    }
+    __syncthreads();
+    const int cc = t & 31, rq = t >> 5;   // rows rq, rq + 8, rq + 16, rq + 24
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int k = 0; k < bw; ++k) {
+        const double u = Us[k][cc];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] = fma(Ls[rq + 8 * q][k], u, acc[q]);
+    }
+    if (c0 + cc >= n) return;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int r = r0 + rq + 8 * q;
+        if (r < n) M[(long)r * n + c0 + cc] -= acc[q];
+    }
+}
+
+// L y = b (unit lower), then U x = y, column-oriented with b in shared memory
+// (n <= 4096); x overwrites b.
+__global__ void __launch_bounds__(1024) k_lu_trisolve(const double* M, double* b, int n) {
+    extern __shared__ double sb[];
+    const int t = threadIdx.x, nt = blockDim.x;
+    for (int i = t; i < n; i += nt) sb[i] = b[i];
+    __syncthreads();
+    for (int j = 0; j < n; ++j) {          // forward: b_i -= L_ij y_j, i > j
+        const double yj = sb[j];
+        for (int i = j + 1 + t; i < n; i += nt) sb[i] -= M[(long)i * n + j] * yj;
         __syncthreads();
     }
+    for (int j = n - 1; j >= 0; --j) {     // backward: x_j = y_j / U_jj, then b_i -= U_ij x_j, i < j
+        const double xj = sb[j] / M[(long)j * n + j];
+        __syncthreads();
+        if (t == 0) sb[j] = xj;
+        for (int i = t; i < j; i += nt) sb[i] -= M[(long)i * n + j] * xj;
+        __syncthreads();
+    }
+    for (int i = t; i < n; i += nt) b[i] = sb[i];
 }
 
 extern "C" dg_status dg_dense_solve(dg_handle* h, const double* F, double* x) {
@@ -218,8 +277,24 @@ extern "C" dg_status dg_dense_solve(dg_handle* h, const double* F, double* x) {
     long tot = (long)h->ne * 4 * nb * nb;
     k_densify<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(h->A64, h->nbr, h->ne, nb, M, n);
     DG_CK(h, cudaMemcpyAsync(x, F ? F : h->F, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
-    k_dense_lu_solve<<<1, 1024, 0, h->stream>>>(M, x, (int)n, h->dflag);
-    h->nlaunch += 2;
+    const int nn = (int)n;
+    int launches = 1;
+    for (int k0 = 0; k0 < nn; k0 += LU_B) {
+        const int bw = nn - k0 < LU_B ? nn - k0 : LU_B;
+        k_lu_panel<<<1, 1024, 0, h->stream>>>(M, x, nn, k0, bw, h->dflag);
+        ++launches;
+        const int rest = nn - k0 - bw;
+        if (rest > 0) {
+            k_lu_trsm<<<(unsigned)((rest + 255) / 256), 256, 0, h->stream>>>(M, nn, k0, bw);
+            const unsigned gt = (unsigned)((rest + 31) / 32);
+            k_lu_gemm<<<dim3(gt, gt), 256, 0, h->stream>>>(M, nn, k0, bw);
+            launches += 2;
+        }
+    }
+    DG_CK(h, cudaFuncSetAttribute(k_lu_trisolve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(sizeof(double) * n)));
+    k_lu_trisolve<<<1, 1024, sizeof(double) * n, h->stream>>>(M, x, nn);
+    h->nlaunch += launches + 1;
     DG_LAUNCH_CK(h);
     int flag = 0;
     DG_CK(h, cudaMemcpyAsync(&flag, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));

@@ -561,3 +561,27 @@ def test_schwarz_gmres_reaches_tolerance_in_fewer_steps():
     assert im.status == D.DG_OK and rel_residual_oracle(run, T, _np(xm)) <= 1e-10 * 1.5
     print(f"Arnoldi steps: block Jacobi {ib.iterations}, Schwarz {iS.iterations}")
     h.close()
+
+
+@pytest.mark.parametrize("N,k", [(10, 2), (13, 3)])
+def test_blocked_dense_lu_matches_oracle(N, k):
+    """The blocked LU of the dense solve (32-column panels, the last one ragged:
+    1200 and 3380 unknowns) equals the oracle's direct solve as a function,
+    and an all-zero operator is reported as singular."""
+    prob = W.Problem("gauss", 0.05, 0.4, (0.5, 0.0, -1.0, -0.5, 1.0, 0.0), W.gaussian_bump,
+                     neumann_sides=("right", "top"))
+    ma = W.perturbed_mesh(N, seed=3, neumann_sides=prob.neumann_sides)
+    h = gpu_setup(ma, k, 1, prob)
+    n = h.info().dofs
+    assert n % 32 != 0
+    xg = h.dense_solve()
+    run = oracle_run(ma, k, 1, prob)
+    xo = oracle_direct(run)
+    T = basis_change(run, ma, k)
+    assert np.abs(x_to_oracle(T, _np(xg)) - xo).max() <= 1e-10 * np.abs(xo).max()
+    h.close()
+    hz = gpu_setup(W.structured_mesh(3), 1, 2, W.Problem("z", 0.0, 0.0, (0,) * 6, W.sinsin))
+    with pytest.raises(D.DGError) as e:
+        hz.dense_solve()
+    assert e.value.status == D.DG_ERR_SINGULAR_BLOCK
+    hz.close()
