@@ -263,11 +263,14 @@ __global__ void __launch_bounds__(B_TX* B_TY) k_b_dots(const TV* __restrict__ V,
             }
             __syncthreads();
         } else {
+            // only the accumulators that hold a dot are reduced (warp-uniform test)
 #pragma unroll
             for (int k = 0; k < B_DPT; ++k) {
                 const int d = ty + B_TY * k;
-                const double v = dg_warp_sum(acc[k].get());
-                if (tx == 0 && d <= dlast) B.partials[(long)it * (DG_MAXM + 2) + d] = v;
+                if (d <= dlast) {
+                    const double v = dg_warp_sum(acc[k].get());
+                    if (tx == 0) B.partials[(long)it * (DG_MAXM + 2) + d] = v;
+                }
             }
         }
         if (!inst_last(&st->arrive, B.inst_item_hi[inst] - B.inst_item_lo[inst])) continue;
@@ -291,6 +294,130 @@ __global__ void __launch_bounds__(B_TX* B_TY) k_b_dots(const TV* __restrict__ V,
                     hc[d] = h;
                     st->coef[d] = hd * st->scale[d];
                 }
+            }
+        }
+        for (int i = t; i < j; i += B_TX * B_TY) {
+            css[i] = st->cs[i];
+            sns[i] = st->sn[i];
+        }
+        __syncthreads();
+        if (t == 0) {
+            const double w2 = hp[j + 1];
+            double s2 = 0.0;
+            for (int d = 0; d <= j; ++d) s2 = ::fma(hp[d], hp[d], s2);
+            const double rest = w2 - s2;
+            bool ready = true;
+            if (pass == 1) {
+                const bool again = !(rest >= 0.49 * w2);
+                st->reorth = again ? 1 : 0;
+                ready = !again;
+            }
+            if (ready) b_finish_column(B, inst, j, sqrt(rest > 0.0 ? rest : 0.0), hc, css, sns);
+        }
+        __syncthreads();
+    }
+}
+
+// The f32 segmented multi-dot (the batched inner solves): per item the ncol
+// = j+2 dots are cut into equal groups of at most 16, and the 32 warps of the
+// block into (group, row partition) pairs, so every warp streams at every step
+// j; lanes sum their products in f32, each warp in an f32 tree, the warps of
+// a group in two-float arithmetic into the item's partial (a float2 in the
+// partial's 8 bytes).  The instance's last item to arrive sums its items'
+// partials in two-float and turns each dot into one f64 value: no per-warp f64
+// work, which on this GPU's FP64 pipe would cost as much as the streaming.
+// The tail is that of k_b_dots.
+__global__ void __launch_bounds__(B_TX* B_TY) k_b_dots32(const float* __restrict__ V, long ld, BatchDev B, int pass) {
+    const int j = *B.jglob;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int t = ty * B_TX + tx;
+    __shared__ double hp[DG_MAXM + 2], hc[DG_MAXM + 2], css[DG_MAXM], sns[DG_MAXM];
+    __shared__ float red[B_TY][16];
+    __shared__ float2 tot[DG_MAXM + 2];
+    const int ncol = j + 2;
+    const int ngroups = (ncol + 15) / 16;
+    const int gsize = (ncol + ngroups - 1) / ngroups;
+    const int pb = B_TY / ngroups;
+    const int g = ty % ngroups, part = ty / ngroups;
+    const int d0 = g * gsize;
+    const int dn = part < pb ? max(0, min(gsize, ncol - d0)) : 0;
+    float2* P2 = reinterpret_cast<float2*>(B.partials);
+    for (int it = blockIdx.x; it < B.nit; it += gridDim.x) {
+        const int inst = B.item_inst[it];
+        BState* st = B.bst + inst;
+        if (!B.iactive[inst] || (pass == 2 && !st->reorth)) continue;
+        const float* __restrict__ w = V + (long)(j + 1) * ld;
+        const float* __restrict__ vg = V + (long)d0 * ld;
+        const int lo = B.item_lo[it], hi = B.item_hi[it];
+        float acc[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) acc[i] = 0.f;
+        if (dn > 0) {
+            if (((lo | hi) & 1) == 0) {
+                // even bounds (always for the split-square workloads): 8-byte slices
+                for (int l = lo + 2 * (part * B_TX + tx); l < hi; l += 2 * pb * B_TX) {
+                    const float2 wl = *reinterpret_cast<const float2*>(w + l);
+#pragma unroll
+                    for (int d = 0; d < 16; ++d)
+                        if (d < dn) {
+                            const float2 v = *reinterpret_cast<const float2*>(vg + (long)d * ld + l);
+                            acc[d] = fmaf(v.x, wl.x, fmaf(v.y, wl.y, acc[d]));
+                        }
+                }
+            } else {
+                for (int l = lo + part * B_TX + tx; l < hi; l += pb * B_TX) {
+                    const float wl = w[l];
+#pragma unroll
+                    for (int d = 0; d < 16; ++d)
+                        if (d < dn) acc[d] = fmaf(vg[(long)d * ld + l], wl, acc[d]);
+                }
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < 16; ++d) {
+            if (d < gsize) {   // block-uniform
+                float v = acc[d];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (tx == 0) red[ty][d] = d < dn ? v : 0.f;
+            }
+        }
+        __syncthreads();
+        if (t < ncol) {
+            const int gg = t / gsize, dd = t - gg * gsize;
+            float2 sacc = make_float2(0.f, 0.f);
+            for (int p = 0; p < pb; ++p) sacc = f2_add(sacc, make_float2(red[p * ngroups + gg][dd], 0.f));
+            P2[(long)it * (DG_MAXM + 2) + t] = sacc;
+        }
+        __syncthreads();
+        if (!inst_last(&st->arrive, B.inst_item_hi[inst] - B.inst_item_lo[inst])) continue;
+        // one warp per dot over the instance's items, two-float
+        const int ilo = B.inst_item_lo[inst], ihi = B.inst_item_hi[inst];
+        for (int d = ty; d < ncol; d += B_TY) {
+            float2 sacc = make_float2(0.f, 0.f);
+            for (int i2 = ilo + tx; i2 < ihi; i2 += B_TX) sacc = f2_add(sacc, __ldcg(P2 + (long)i2 * (DG_MAXM + 2) + d));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                float2 q;
+                q.x = __shfl_xor_sync(0xffffffffu, sacc.x, o);
+                q.y = __shfl_xor_sync(0xffffffffu, sacc.y, o);
+                sacc = f2_add(sacc, q);
+            }
+            if (tx == 0) tot[d] = sacc;
+        }
+        __syncthreads();
+        if (t < ncol) {
+            const int d = t;
+            const double r = (double)tot[d].x + (double)tot[d].y;
+            if (d == j + 1) {
+                hp[d] = r;
+            } else {
+                const double hd = st->scale[d] * r;
+                hp[d] = hd;
+                const double h = pass == 1 ? hd : st->hcol[d] + hd;
+                st->hcol[d] = h;
+                hc[d] = h;
+                st->coef[d] = hd * st->scale[d];
             }
         }
         for (int i = t; i < j; i += B_TX * B_TY) {
@@ -342,6 +469,59 @@ __global__ void __launch_bounds__(256) k_b_update(TV* V, long ld, BatchDev B, in
             }
             for (; d <= j; ++d) acc = ::fma(-c[d], V[(long)d * ld + l], acc);
             w[l] = acc;
+        }
+    }
+}
+
+// The f32 segmented update: as k_b_update, eight basis vectors in flight per
+// thread and 8-byte slices where the item's bounds are even.
+__global__ void __launch_bounds__(256) k_b_update32(float* V, long ld, BatchDev B, int pass) {
+    const int j = *B.jglob;
+    __shared__ float c[DG_MAXM + 2];
+    for (int it = blockIdx.x; it < B.nit; it += gridDim.x) {
+        const int inst = B.item_inst[it];
+        BState* st = B.bst + inst;
+        if (!B.iactive[inst] || (pass == 2 && !st->reorth)) continue;
+        __syncthreads();
+        for (int d = threadIdx.x; d <= j; d += blockDim.x) c[d] = (float)st->coef[d];
+        __syncthreads();
+        float* w = V + (long)(j + 1) * ld;   // aliases V: no __restrict__
+        const int lo = B.item_lo[it], hi = B.item_hi[it];
+        if (((lo | hi) & 1) == 0) {
+            for (int l = lo + 2 * threadIdx.x; l < hi; l += 2 * blockDim.x) {
+                float2 acc = *reinterpret_cast<const float2*>(w + l);
+                int d = 0;
+                for (; d + 8 <= j + 1; d += 8) {
+                    float2 v[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) v[u] = *reinterpret_cast<const float2*>(V + (long)(d + u) * ld + l);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        acc.x = fmaf(-c[d + u], v[u].x, acc.x);
+                        acc.y = fmaf(-c[d + u], v[u].y, acc.y);
+                    }
+                }
+                for (; d <= j; ++d) {
+                    const float2 v = *reinterpret_cast<const float2*>(V + (long)d * ld + l);
+                    acc.x = fmaf(-c[d], v.x, acc.x);
+                    acc.y = fmaf(-c[d], v.y, acc.y);
+                }
+                *reinterpret_cast<float2*>(w + l) = acc;
+            }
+        } else {
+            for (int l = lo + threadIdx.x; l < hi; l += blockDim.x) {
+                float acc = w[l];
+                int d = 0;
+                for (; d + 8 <= j + 1; d += 8) {
+                    float v[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) v[u] = V[(long)(d + u) * ld + l];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) acc = fmaf(-c[d + u], v[u], acc);
+                }
+                for (; d <= j; ++d) acc = fmaf(-c[d], V[(long)d * ld + l], acc);
+                w[l] = acc;
+            }
         }
     }
 }
@@ -794,8 +974,13 @@ static int b_enqueue_cycle(dg_handle* h, const BatchRun& Rn, const TA* A, const 
                                                               vsel_fixed(), vj1);
         }
         for (int pass = 1; pass <= 2; ++pass) {
-            k_b_dots<TV><<<Rn.gsm, dim3(B_TX, B_TY), 0, h->stream>>>(V, Rn.ld, B, pass);
-            k_b_update<TV><<<Rn.gx, 256, 0, h->stream>>>(V, Rn.ld, B, pass);
+            if constexpr (sizeof(TV) == 4) {
+                k_b_dots32<<<Rn.gsm, dim3(B_TX, B_TY), 0, h->stream>>>((const float*)V, Rn.ld, B, pass);
+                k_b_update32<<<Rn.gx, 256, 0, h->stream>>>((float*)V, Rn.ld, B, pass);
+            } else {
+                k_b_dots<TV><<<Rn.gsm, dim3(B_TX, B_TY), 0, h->stream>>>(V, Rn.ld, B, pass);
+                k_b_update<TV><<<Rn.gx, 256, 0, h->stream>>>(V, Rn.ld, B, pass);
+            }
         }
         k_b_step<<<1, 32, 0, h->stream>>>(B);
         n += 7;
@@ -1337,7 +1522,7 @@ extern "C" dg_status dg_batch_autotune(dg_handle* h, int* tile) {
         for (int r = 0; r < 4; ++r) {
             k_b_prof_state<<<(h->b_n + 255) / 256, 256, 0, h->stream>>>(B, j);
             DG_CK(h, cudaEventRecord(e0, h->stream));
-            k_b_dots<float><<<sms, dim3(B_TX, B_TY), 0, h->stream>>>((const float*)h->mx_buf, ld, B, 1);
+            k_b_dots32<<<sms, dim3(B_TX, B_TY), 0, h->stream>>>((const float*)h->mx_buf, ld, B, 1);
             DG_CK(h, cudaEventRecord(e1, h->stream));
             DG_CK(h, cudaEventSynchronize(e1));
             float ms = 0.f;

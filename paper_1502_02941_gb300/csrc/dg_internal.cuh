@@ -375,6 +375,19 @@ __device__ __forceinline__ double dg_block_sum(double v, double* sh) {
     return r;
 }
 
+// Sum of two two-float numbers (hi, lo): Knuth's TwoSum of the high parts,
+// the low parts added to its error, renormalised (Dekker's fast TwoSum).  The
+// compiler keeps the order of these additions (no fast-math flags).  The f32
+// Krylov reductions use it across warps and blocks.
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) {
+    const float s = a.x + b.x;
+    const float bp = s - a.x;
+    float e = (a.x - (s - bp)) + (b.x - bp);
+    e += a.y + b.y;
+    const float hi = s + e;
+    return make_float2(hi, e - (hi - s));
+}
+
 // Index of entry (K, slot s, m) in a tile-interleaved block array of type T
 // with `slots` slots per element.
 template <typename T>

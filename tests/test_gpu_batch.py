@@ -183,3 +183,48 @@ def test_group_solve_of_a_mixed_degree_batch(solver):
     assert s == D.DG_ERR_INVALID_ARG
     for h in dgs:
         h.close()
+
+
+def _pentagon():
+    """Five triangles around a centre node (an odd element count), all
+    boundary edges Dirichlet."""
+    ang = np.pi / 2 + 2 * np.pi * np.arange(5) / 5
+    nodes = np.vstack([[0.5, 0.5], np.column_stack([0.5 + 0.4 * np.cos(ang), 0.5 + 0.4 * np.sin(ang)])])
+    elems = np.array([[0, 1 + i, 1 + (i + 1) % 5] for i in range(5)], np.int32)
+    dirichlet = np.array([[1 + i, 1 + (i + 1) % 5] for i in range(5)], np.int32)
+    return W.MeshArrays(nodes, elems, dirichlet, np.zeros((0, 2), np.int32))
+
+
+@pytest.mark.parametrize("solver", ["refine", "gmres_ir"])
+def test_batch_with_odd_unknown_offsets(solver):
+    """P1 instances of 5, 20 and 5 triangles: the unknown offsets of the second
+    and third instance are odd, so the f32 batched kernels take their scalar
+    paths; each instance equals its single-instance solve."""
+    p5 = _pentagon()
+    p20 = W.MeshArrays(*D.dg_mesh_refine(p5.nodes, p5.elems, p5.dirichlet, p5.neumann))
+    meshes = [p5, p20, p5]
+    ma, starts = W.concat_meshes(meshes)
+    assert (starts[1] * 3) % 2 == 1
+    probs = [W.Problem("g", e, a, b, None, W.gaussians_source([(0.4, 0.6)], [0.15]))
+             for e, a, b in ((0.05, 0.3, (0.6, 0, 0, -0.2, 0, 0)), (1e-3, 0.8, (0.1, 0, 0, 0.7, 0, 0)),
+                             (0.2, 0.0, (-0.4, 0, 0, 0.1, 0, 0)))]
+    cfgs = [W.Config(f"p{i}", 0, 1, 2, p) for i, p in enumerate(probs)]
+    coeffs = np.array([[p.eps, p.alpha, *p.b] for p in probs])
+    h = D.DG(0)
+    store = D.DG_STORE_F64 | D.DG_STORE_F32
+    problem.setup_batch(h, cfgs, ma, starts, coeffs, store=store, tol=1e-11, gmres_m=20)
+    h.precond_setup()
+    if solver == "refine":
+        x, its, rr, st = h.batch_solve(D.DG_F32, inner_m=20, inner_tol=1e-5, max_outer=30)
+    else:
+        x, its, rr, st = h.batch_gmres_ir_solve(D.DG_F32, inner_m=16, inner_tol=1e-3, max_outer=300)
+    assert (st == 0).all() and (rr <= 1e-11).all()
+    xb = _np(x)
+    for i, (c, mi) in enumerate(zip(cfgs, meshes)):
+        a, b = starts[i] * 3, starts[i + 1] * 3
+        hs = D.DG(0)
+        problem.setup(hs, c, mesh=mi, tol=1e-12, gmres_m=20)
+        xs = _np(hs.gmres_solve()[0])
+        assert np.abs(xs - xb[a:b]).max() <= 1e-8 * np.abs(xs).max(), i
+        hs.close()
+    h.close()
