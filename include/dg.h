@@ -660,11 +660,19 @@ dg_status dg_l2_error_noalloc(dg_handle* h, const double* x, const double* uex_q
  * kernel run in isolation on the handle's GMRES workspace, for roofline
  * accounting: which = DG_PROF_DOTS (the multi-dot of an Arnoldi step) or
  * DG_PROF_UPDATE (its Gram-Schmidt update), at step `param` = j (0 <= j <
- * gmres_m), for dtype DG_F64 (f64 vectors) or DG_F32 (f32 vectors), averaged
- * over reps launches.  Overwrites the workspace.  Synchronises.
+ * gmres_m), for dtype DG_F64 (f64 vectors) or DG_F32 (f32 vectors); or
+ * which = DG_PROF_APPLY, the operator apply of Sec. 2.3 (dg_apply) with the
+ * block copy dtype = DG_F64, DG_F32 or DG_BF16 (param ignored; f32 vectors
+ * for the low-precision copies), the rest of the workspace read before each
+ * launch so that the operator is not left in L2 when the basis is larger
+ * than L2.
+ * Averaged over reps launches.  Overwrites the workspace.  Synchronises.
+ * Errors: DG_ERR_STATE (not assembled, or the requested block copy not
+ * stored), DG_ERR_INVALID_ARG (which, dtype, param).
  */
 #define DG_PROF_DOTS   1
 #define DG_PROF_UPDATE 2
+#define DG_PROF_APPLY  3
 dg_status dg_profile_kernel(dg_handle* h, int which, int dtype, int param, int reps, double* avg_ms);
 
 /* Number of CUDA kernels this handle has launched so far (a graph launch

@@ -221,7 +221,8 @@ __device__ void b_finish_column(BatchDev& B, int inst, int j, double wn, const d
 // Segmented multi-dot: per item, r_d = <V_d, V_{j+1}> over the item's range,
 // d = 0..j+1 (the last one is ||w||^2).  Last item of an instance: h_d, the
 // norm ||w||^2 - sum h_d^2 and either the Givens step or a request for a
-// second Gram-Schmidt pass (less than 0.49 ||w||^2 left), as in dg_gmres.cu.
+// second Gram-Schmidt pass (less than DG_REORTH_FRAC ||w||^2 left), as in
+// dg_gmres.cu.
 template <typename TV>
 __global__ void __launch_bounds__(B_TX* B_TY) k_b_dots(const TV* __restrict__ V, long ld, BatchDev B, int pass) {
     const int j = *B.jglob;
@@ -308,7 +309,7 @@ __global__ void __launch_bounds__(B_TX* B_TY) k_b_dots(const TV* __restrict__ V,
             const double rest = w2 - s2;
             bool ready = true;
             if (pass == 1) {
-                const bool again = !(rest >= 0.49 * w2);
+                const bool again = !(rest >= DG_REORTH_FRAC * w2);
                 st->reorth = again ? 1 : 0;
                 ready = !again;
             }
@@ -432,7 +433,7 @@ __global__ void __launch_bounds__(B_TX* B_TY) k_b_dots32(const float* __restrict
             const double rest = w2 - s2;
             bool ready = true;
             if (pass == 1) {
-                const bool again = !(rest >= 0.49 * w2);
+                const bool again = !(rest >= DG_REORTH_FRAC * w2);
                 st->reorth = again ? 1 : 0;
                 ready = !again;
             }

@@ -15,7 +15,7 @@
 //   3. V_{j+1} -= sum_d s_d^2 r_d V_d               (one update pass)
 // The norm of the orthogonalised vector comes from the same reduction as
 // ||w||^2 - sum_d h_d^2 (single-reduction classical Gram-Schmidt).  When that
-// leaves less than 0.49 ||w||^2 a second Gram-Schmidt pass runs (kernels 2-3
+// leaves less than DG_REORTH_FRAC ||w||^2 a second Gram-Schmidt pass runs (kernels 2-3
 // again, which otherwise exit at once) and its own self-dot gives the norm.
 // The multi-dot finishes its reduction in the last block to arrive
 // (threadfence + arrival counter, no waiting), which sums the per-block
@@ -339,9 +339,9 @@ __global__ void __launch_bounds__(GM_TX* GM_TY) k_gm_dots(const TV* __restrict__
     __syncthreads();
     if (t >= 32) return;
     // norm of w - sum h_d v_d without another pass: ||w||^2 - sum h_d^2 (the
-    // v_d are orthonormal).  Accepted when at least 0.49 ||w||^2 remains (at
-    // most a factor 2 of cancellation); otherwise a second Gram-Schmidt pass
-    // runs and its own self-dot gives the norm exactly.
+    // v_d are orthonormal).  Accepted when at least DG_REORTH_FRAC ||w||^2
+    // remains (at most a factor 2 of cancellation in the norm); otherwise a
+    // second Gram-Schmidt pass runs and its own self-dot gives the norm exactly.
     double s2 = 0.0;
     for (int d = t; d <= j; d += 32) s2 = fma(hp[d], hp[d], s2);
     s2 = dg_warp_sum(s2);
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(GM_TX* GM_TY) k_gm_dots(const TV* __restrict__
     const double rest = w2 - s2;
     st->jw = j;
     if (pass == 1) {
-        const bool again = !(rest >= 0.49 * w2);
+        const bool again = !(rest >= DG_REORTH_FRAC * w2);
         st->reorth = again ? 1 : 0;
         if (again) return;
     }
@@ -539,7 +539,7 @@ __global__ void __launch_bounds__(GM32_THREADS, 2) k_gm_dots32(const float* __re
     const double rest = w2 - s2;
     st->jw = j;
     if (pass == 1) {
-        const bool again = !(rest >= 0.49 * w2);
+        const bool again = !(rest >= DG_REORTH_FRAC * w2);
         st->reorth = again ? 1 : 0;
         if (again) return;
     }
@@ -594,6 +594,147 @@ __global__ void __launch_bounds__(256) k_gm_update32(float* V, long ld, long nve
         }
         w[q] = acc;
     }
+}
+
+// The apply of an f32 Arnoldi step fused with its multi-dot (pass 1):
+//   w = V_{j+1} = s A x   (x = V_j with s = s_j, or x = xfix with s = 1),
+//   r_d = <V_d, w> for d <= j and r_{j+1} = ||w||^2,
+// then the tail of k_gm_dots32 (h_d, the update coefficients, the norm or a
+// request for a second pass).  One warp per 32-element tile (lane = element)
+// computes the tile's rows of w as k_apply does, keeps them in registers and
+// takes the dots with the tile's rows of V_0..V_j (32 * NB consecutive entries
+// of each, eight vectors per round of loads); lanes sum in f32, the warp in an
+// f32 tree, the block's warps and then the blocks in two-float arithmetic.  This
+// saves the multi-dot kernel's launch, ramp and tail and its re-read of w.
+#define AD_WARPS 8
+template <int NB, typename TA>
+__global__ void __launch_bounds__(AD_WARPS * 32) k_apply_dots32(const TA* __restrict__ A, const int* __restrict__ nbr,
+                                                                float* V, long ld, const float* xfix, int ne,
+                                                                GmresState* st, float2* partials) {
+    using CH = Chunk<TA, float>;
+    constexpr int W = CH::W;
+    constexpr int C = (NB * NB + W - 1) / W;
+    dg_grid_release();   // programmatic dependent launch
+    dg_grid_wait();
+    if (!st->active) return;
+    const int j = st->j;
+    const int ncol = j + 2;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ float red[AD_WARPS][DG_MAXM + 2];
+    __shared__ float2 tot[DG_MAXM + 2];
+    __shared__ double hp[DG_MAXM + 2];
+    for (int d = lane; d < ncol; d += 32) red[warp][d] = 0.f;
+    const float* __restrict__ x = xfix ? xfix : V + (long)j * ld;
+    const float sc = xfix ? 1.f : (float)st->scale[j];
+    float* w = V + (long)(j + 1) * ld;
+    const int ntiles = (ne + 31) / 32;
+    for (int tile = blockIdx.x * AD_WARPS + warp; tile < ntiles; tile += gridDim.x * AD_WARPS) {
+        const int K = tile * 32 + lane;
+        const bool live = K < ne;
+        float acc[NB];
+#pragma unroll
+        for (int r = 0; r < NB; ++r) acc[r] = 0.f;
+        if (live) {
+            int Ls[4] = {K, -1, -1, -1};
+#pragma unroll
+            for (int f = 0; f < 3; ++f) Ls[1 + f] = __ldg(nbr + (size_t)f * ne + K);
+#pragma unroll
+            for (int sl = 0; sl < 4; ++sl) {
+                const int Ln = Ls[sl];
+                if (Ln < 0) continue;
+                float xv[NB];
+                load_x<NB, float, float>(x, Ln, xv);
+                const TA* base = A + (((size_t)tile * 4 + sl) * C * 32 + lane) * W;
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    float v[W];
+                    CH::load(base + (size_t)c * 32 * W, v);
+#pragma unroll
+                    for (int q = 0; q < W; ++q) {
+                        const int m = c * W + q;
+                        if (m < NB * NB) acc[m / NB] = fmaf(v[q], xv[m % NB], acc[m / NB]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < NB; ++r) acc[r] *= sc;
+            store_y<NB, float, float>(w, K, acc);
+        }
+        // dots of the tile's rows: eight basis vectors per round of loads
+        for (int d0 = 0; d0 <= j; d0 += 8) {
+            float p[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                p[u] = 0.f;
+                if (live && d0 + u <= j) {
+                    float vr[NB];
+                    load_x<NB, float, float>(V + (long)(d0 + u) * ld, K, vr);
+#pragma unroll
+                    for (int r = 0; r < NB; ++r) p[u] = fmaf(vr[r], acc[r], p[u]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (d0 + u > j) break;   // warp-uniform
+                float v = p[u];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) red[warp][d0 + u] += v;
+            }
+        }
+        float pw = 0.f;
+#pragma unroll
+        for (int r = 0; r < NB; ++r) pw = fmaf(acc[r], acc[r], pw);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) pw += __shfl_xor_sync(0xffffffffu, pw, o);
+        if (lane == 0) red[warp][j + 1] += pw;
+    }
+    __syncthreads();
+    const int gx = gridDim.x;
+    for (int d = threadIdx.x; d < ncol; d += blockDim.x) {
+        float2 sacc = make_float2(0.f, 0.f);
+        for (int q = 0; q < AD_WARPS; ++q) sacc = f2_add(sacc, make_float2(red[q][d], 0.f));
+        partials[(long)d * gx + blockIdx.x] = sacc;
+    }
+    if (!last_block(&st->arrive)) return;
+    for (int d = warp; d < ncol; d += AD_WARPS) {
+        float2 sacc = make_float2(0.f, 0.f);
+        for (int b = lane; b < gx; b += 32) sacc = f2_add(sacc, __ldcg(partials + (long)d * gx + b));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float2 t;
+            t.x = __shfl_xor_sync(0xffffffffu, sacc.x, o);
+            t.y = __shfl_xor_sync(0xffffffffu, sacc.y, o);
+            sacc = f2_add(sacc, t);
+        }
+        if (lane == 0) tot[d] = sacc;
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < ncol; d += blockDim.x) {
+        const double r = (double)tot[d].x + (double)tot[d].y;
+        if (d == j + 1) {
+            hp[d] = r;
+        } else {
+            const double hd = st->scale[d] * r;
+            hp[d] = hd;
+            st->hcol[d] = hd;
+            st->coef[d] = hd * st->scale[d];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x >= 32) return;
+    double s2 = 0.0;
+    for (int d = threadIdx.x; d <= j; d += 32) s2 = fma(hp[d], hp[d], s2);
+    s2 = dg_warp_sum(s2);
+    if (threadIdx.x != 0) return;
+    const double w2 = hp[j + 1];
+    const double rest = w2 - s2;
+    st->jw = j;
+    const bool again = !(rest >= DG_REORTH_FRAC * w2);
+    st->reorth = again ? 1 : 0;
+    if (again) return;
+    st->wn_fin = sqrt(rest > 0.0 ? rest : 0.0);
+    st->colready = 1;
 }
 
 // Launch the multi-dot + update pair of Gram-Schmidt pass `pass`.
@@ -754,7 +895,34 @@ static int enqueue_cycle(dg_handle* h, GmresWork& W, const TA* A, const TB* B, c
     // solves/s on the 256x256 P2 workload; f32 refinement 12.74 against 12.64)
     const bool pdl = h->pdl && h->stream != nullptr && sizeof(TV) == 4;
     int extra = 0;
-    for (int it = 0; it < W.m; ++it) {
+    // f32 vectors without the learned correction: the step's (last) apply and
+    // its multi-dot are one kernel (k_apply_dots32), then the update and the
+    // conditional second Gram-Schmidt pass
+    if constexpr (sizeof(TV) == 4) {
+        if (!flex) {
+            const unsigned ntiles = (unsigned)((h->ne + 31) / 32);
+            const unsigned gad = std::min((ntiles + AD_WARPS - 1) / AD_WARPS, 4096u);
+            for (int it = 0; it < W.m; ++it) {
+                const float* xfix = nullptr;
+                const TA* Aop = A;
+                if (G) {
+                    launch_apply<NB, TV, TV>(h, G, V, Z, step, vj, vsel_fixed(), pdl);   // Z = s_j G V_j
+                    xfix = (const float*)Z;
+                } else if (Ah) {
+                    Aop = Ah;                                                             // (A M^-1) s_j V_j
+                } else {
+                    launch_bj<NB, TB, TV>(h, B, V, Z, step, vj, vsel_fixed(), pdl);      // Z = s_j M^-1 V_j
+                    xfix = (const float*)Z;
+                }
+                dg_launch(h, pdl, k_apply_dots32<NB, TA>, dim3(gad), dim3(AD_WARPS * 32), Aop, (const int*)h->nbr,
+                          (float*)V, ld, xfix, h->ne, st, (float2*)W.partials);
+                dg_launch(h, pdl, k_gm_update32, dim3(W.gu32 + 1), dim3(256), (float*)V, ld, nvec, st, 1);
+                launch_gs_pass<TV>(h, W, V, ld, nvec, pdl, 2);
+                extra += (G || !Ah) ? -1 : -2;   // 5 kernels a step (4 with A M^-1) instead of 6
+            }
+        }
+    }
+    for (int it = 0; it < W.m && !(sizeof(TV) == 4 && !flex); ++it) {
         if (flex) {
             // Z_j = s_j M_BJ^-1 V_j + MLP correction, kept for the update of x
             VecSel zj{&st->j, 0, ld};
@@ -1358,10 +1526,63 @@ static dg_status profile_arnoldi(dg_handle* h, int which, int j, int reps, doubl
     return DG_OK;
 }
 
+// Reads the first cnt entries of V (clean lines through L2); the store never
+// happens for the positive fill pattern but keeps the loads.
+template <typename TV>
+__global__ void k_prof_read(const TV* __restrict__ V, size_t cnt, TV* sink) {
+    TV s = (TV)0;
+    for (size_t l = (size_t)blockIdx.x * blockDim.x + threadIdx.x; l < cnt; l += (size_t)gridDim.x * blockDim.x)
+        s += V[l];
+    if (s < (TV)0) *sink = s;
+}
+
+// One operator apply y = A x (block copy `dtype`) between CUDA events, with
+// x = V_0 and y = V_1 of the GMRES workspace (filled once).  Before each launch
+// the rest of the basis is read, which evicts A from L2 when the basis is
+// larger than L2 and, being reads, leaves no dirty lines whose write-back
+// would be charged to the apply.
+template <typename TV>
+static dg_status profile_apply(dg_handle* h, int dtype, int reps, double* avg_ms) {
+    GmresWork& W = h->gw[sizeof(TV) == 8 ? 0 : 1];
+    const long n = (long)h->ne * dg_nb(h->asm_k);
+    const int m = h->p.gmres_m;
+    dg_status s = ensure_workspace(h, W, n, m, sizeof(TV));
+    if (s != DG_OK) return s;
+    cudaEvent_t e0, e1;
+    DG_CK(h, cudaEventCreate(&e0));
+    DG_CK(h, cudaEventCreate(&e1));
+    double tot = 0.0;
+    TV* V = (TV*)W.V;
+    k_prof_fill<TV><<<1024, 256, 0, h->stream>>>(V, (size_t)(m + 2), (size_t)n, W.ld);
+    h->nlaunch += 1;
+    for (int r = 0; r < reps && s == DG_OK; ++r) {
+        k_prof_read<TV><<<1024, 256, 0, h->stream>>>(V + 2 * W.ld, (size_t)m * W.ld, (TV*)W.partials);
+        h->nlaunch += 1;
+        DG_CK(h, cudaEventRecord(e0, h->stream));
+        s = dg_launch_apply(h, dtype, V, V + W.ld);
+        DG_CK(h, cudaEventRecord(e1, h->stream));
+        DG_CK(h, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        DG_CK(h, cudaEventElapsedTime(&ms, e0, e1));
+        tot += ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != DG_OK) return s;
+    *avg_ms = tot / reps;
+    return DG_OK;
+}
+
 extern "C" dg_status dg_profile_kernel(dg_handle* h, int which, int dtype, int param, int reps, double* avg_ms) {
     DG_WS_SCOPE(h, DG_WS_SOLVER);
     if (!h || !avg_ms || reps < 1) return DG_ERR_INVALID_ARG;
     if (!h->assembled) return dg_fail(h, DG_ERR_STATE, "not assembled");
+    if (which == DG_PROF_APPLY) {
+        if (dtype != DG_F64 && dtype != DG_F32 && dtype != DG_BF16) return dg_fail(h, DG_ERR_INVALID_ARG, "dtype");
+        DG_CK(h, cudaSetDevice(h->device));
+        return dtype == DG_F64 ? profile_apply<double>(h, dtype, reps, avg_ms)
+                               : profile_apply<float>(h, dtype, reps, avg_ms);
+    }
     if (which != DG_PROF_DOTS && which != DG_PROF_UPDATE) return dg_fail(h, DG_ERR_INVALID_ARG, "which");
     if (dtype != DG_F64 && dtype != DG_F32) return dg_fail(h, DG_ERR_INVALID_ARG, "dtype");
     DG_CK(h, cudaSetDevice(h->device));

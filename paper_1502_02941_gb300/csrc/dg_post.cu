@@ -129,91 +129,200 @@ __global__ void k_densify(const double* __restrict__ A, const int* __restrict__ 
     M[((long)K * nb + i) * n + (long)L * nb + j] = A[dg_blk_index<double>(K, s, m, nb, 4)];
 }
 
-// Dense LU with partial pivoting, blocked and right-looking (panels of LU_B
-// columns), on the row-major n x n matrix M in global memory; the row swaps
-// are applied to whole rows of M and to b, so that at the end P M = L U with
-// the unit lower L below the diagonal, U on and above it, and b = P b.
-#define LU_B 32
+// Dense LU with partial pivoting, blocked and right-looking, on the row-major
+// n x n matrix M in global memory: P M = L U with the unit lower L below the
+// diagonal and U on and above it; b is permuted with the rows.  Each panel of
+// bw <= LU_B columns is factored in shared memory (k_lu_panel), its row swaps
+// are applied to the other columns and U12 = L11^-1 A12 is formed
+// (k_lu_swap_trsm), and A22 -= L21 U12 (k_lu_gemm).  The kernels are launched
+// programmatically dependent on their predecessor (each waits for it before
+// touching memory).
+//
+// Widest panel: 16 columns.  The panel's rank-1 updates (about R bw^2 / 2
+// FMAs per panel) run on one SM, whose FP64 pipe does two FMAs a clock on this
+// GPU; the trailing update takes the rest of the GPU.
+#define LU_B 16
+#define LU_SMEM (216 * 1024)   // shared memory of the panel kernel
+#define LU_PERM (2 * LU_B)     // rows a panel's swaps can touch
 
-// Factor the panel of columns [k0, k0 + bw) over rows k0..n-1 (one CTA):
-// per column the pivot (largest |M[r][c]|, lowest index on ties), the swap of
-// rows c and p across all n columns and in b, the multipliers below the
-// diagonal, and the rank-1 update of the panel's remaining columns.  A zero
-// pivot sets *flag (the factors are then meaningless; no access leaves M).
-__global__ void __launch_bounds__(1024) k_lu_panel(double* M, double* b, int n, int k0, int bw, int* flag) {
-    __shared__ double sv[32];
-    __shared__ int si[32];
-    __shared__ int piv;
-    const int t = threadIdx.x, nt = blockDim.x, lane = t & 31, wid = t >> 5;
-    for (int c = k0; c < k0 + bw; ++c) {
-        double best = -1.0;
-        int bi = c;
-        for (int r = c + t; r < n; r += nt) {
-            const double v = fabs(M[(long)r * n + c]);
-            if (v > best) { best = v; bi = r; }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            const double ov = __shfl_xor_sync(0xffffffffu, best, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-        }
-        if (lane == 0) { sv[wid] = best; si[wid] = bi; }
-        __syncthreads();
-        if (t == 0) {
-            double bb = -1.0;
-            int ii = c;
-            for (int w = 0; w < nt / 32; ++w)
-                if (sv[w] > bb || (sv[w] == bb && si[w] < ii)) { bb = sv[w]; ii = si[w]; }
-            piv = ii;
-            if (!(bb > 0.0)) *flag = 1;
-        }
-        __syncthreads();
-        const int p = piv;
-        if (p != c) {
-            for (int j = t; j < n; j += nt) {
-                const double a = M[(long)c * n + j];
-                M[(long)c * n + j] = M[(long)p * n + j];
-                M[(long)p * n + j] = a;
-            }
-            if (t == 0) {
-                const double a = b[c];
-                b[c] = b[p];
-                b[p] = a;
-            }
-        }
-        __syncthreads();
-        const double d = M[(long)c * n + c];
-        const double inv = d != 0.0 ? 1.0 / d : 0.0;
-        for (int r = c + 1 + t; r < n; r += nt) M[(long)r * n + c] *= inv;
-        __syncthreads();
-        const int w = k0 + bw - c - 1;   // panel columns right of c
-        if (w > 0) {
-            const long cnt = (long)(n - c - 1) * w;
-            for (long e = t; e < cnt; e += nt) {
-                const int r = c + 1 + (int)(e / w), j = c + 1 + (int)(e % w);
-                M[(long)r * n + j] -= M[(long)r * n + c] * M[(long)c * n + j];
-            }
-        }
-        __syncthreads();
+// Panel width for R = n - k0 remaining rows: the largest power of two <= LU_B
+// whose column-major panel (column stride R | 1) fits in LU_SMEM.
+static int lu_panel_width(int R) {
+    int bw = LU_B;
+    while (bw > 1 && (size_t)(R | 1) * bw * sizeof(double) > LU_SMEM) bw >>= 1;
+    return bw;
+}
+
+// Block argmax of (|value|, row) pairs, the lowest row on ties; every thread
+// gets the winner.  One pair per warp is staged in sv / si.
+__device__ __forceinline__ void lu_argmax(double& best, int& bi, double* sv, int* si) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (lane == 0) { sv[wid] = best; si[wid] = bi; }
+    __syncthreads();
+    best = lane < nw ? sv[lane] : -1.0;
+    bi = lane < nw ? si[lane] : 0x7fffffff;
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
     }
 }
 
-// U12 = L11^-1 A12: rows k0..k0+bw-1, columns k0+bw..n-1, unit lower L11; one
-// thread per column.
-__global__ void __launch_bounds__(256) k_lu_trsm(double* M, int n, int k0, int bw) {
-    const int j = k0 + bw + blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    for (int i = 1; i < bw; ++i) {
-        double s = M[(long)(k0 + i) * n + j];
-        for (int l = 0; l < i; ++l) s -= M[(long)(k0 + i) * n + k0 + l] * M[(long)(k0 + l) * n + j];
-        M[(long)(k0 + i) * n + j] = s;
+// Factor the panel of columns [k0, k0 + bw) over rows k0..n-1 in shared memory
+// (one CTA, a multiple of 32 threads): per column the pivot (largest |entry|,
+// lowest row on ties), the swap of the two rows within the panel, the
+// multipliers below the diagonal and the rank-1 update of the panel's later
+// columns, which also finds the next column's pivot candidates.  Then the
+// panel's swaps, in order, composed into one permutation of the rows they touch:
+// perm = {count, rows[LU_PERM], src[LU_PERM]}, row rows[q] receiving the content
+// of row src[q]; b is permuted with it.  A zero pivot sets *flag (the factors
+// are then meaningless; no access leaves M).
+__global__ void __launch_bounds__(1024) k_lu_panel(double* M, double* b, int* perm, int n, int k0, int bw,
+                                                   int* flag) {
+    dg_grid_release();
+    dg_grid_wait();
+    extern __shared__ double P[];   // P[j * Rp + i] = M[k0 + i][k0 + j]
+    __shared__ double sv[32];
+    __shared__ int si[32];
+    __shared__ int sp[LU_B];
+    __shared__ int prow[LU_PERM], psrc[LU_PERM];
+    __shared__ int pcount;
+    const int R = n - k0, Rp = R | 1;
+    const int t = threadIdx.x, nt = blockDim.x;
+    for (int e = t; e < R * bw; e += nt) {
+        const int i = e / bw, j = e - i * bw;
+        P[j * Rp + i] = M[(long)(k0 + i) * n + k0 + j];
     }
+    __syncthreads();
+    double best = -1.0;
+    int bi = 0x7fffffff;
+    for (int i = t; i < R; i += nt) {
+        const double v = fabs(P[i]);
+        if (v > best) { best = v; bi = i; }
+    }
+    for (int c = 0; c < bw; ++c) {
+        lu_argmax(best, bi, sv, si);
+        // no candidate wins when the column holds only NaNs: keep row c
+        const int p = (bi >= c && bi < R) ? bi : c;
+        if (t == 0) {
+            sp[c] = p;
+            if (!(best > 0.0)) *flag = 1;
+        }
+        if (p != c && t < bw) {
+            const double a = P[t * Rp + c];
+            P[t * Rp + c] = P[t * Rp + p];
+            P[t * Rp + p] = a;
+        }
+        __syncthreads();
+        const double d = P[c * Rp + c];
+        const double inv = d != 0.0 ? 1.0 / d : 0.0;
+        best = -1.0;
+        bi = 0x7fffffff;
+        for (int i = c + 1 + t; i < R; i += nt) {
+            const double l = P[c * Rp + i] * inv;
+            P[c * Rp + i] = l;
+            for (int j = c + 1; j < bw; ++j) P[j * Rp + i] = fma(-l, P[j * Rp + c], P[j * Rp + i]);
+            if (c + 1 < bw) {
+                const double v = fabs(P[(c + 1) * Rp + i]);
+                if (v > best) { best = v; bi = i; }
+            }
+        }
+    }
+    if (t == 0) {   // compose the swaps (local row indices)
+        int cnt = 0;
+        for (int c = 0; c < bw; ++c) {
+            const int r1 = c, r2 = sp[c];
+            if (r1 == r2) continue;
+            int q1 = -1, q2 = -1;
+            for (int q = 0; q < cnt; ++q) {
+                if (prow[q] == r1) q1 = q;
+                if (prow[q] == r2) q2 = q;
+            }
+            if (q1 < 0) { q1 = cnt; prow[cnt] = r1; psrc[cnt] = r1; ++cnt; }
+            if (q2 < 0) { q2 = cnt; prow[cnt] = r2; psrc[cnt] = r2; ++cnt; }
+            const int a = psrc[q1];
+            psrc[q1] = psrc[q2];
+            psrc[q2] = a;
+        }
+        pcount = cnt;
+        perm[0] = cnt;
+        for (int q = 0; q < cnt; ++q) {
+            perm[1 + q] = k0 + prow[q];
+            perm[1 + LU_PERM + q] = k0 + psrc[q];
+        }
+    }
+    __syncthreads();
+    for (int e = t; e < R * bw; e += nt) {
+        const int i = e / bw, j = e - i * bw;
+        M[(long)(k0 + i) * n + k0 + j] = P[j * Rp + i];
+    }
+    const int cnt = pcount;
+    double bv = 0.0;
+    if (t < cnt) bv = b[k0 + psrc[t]];
+    __syncthreads();
+    if (t < cnt) b[k0 + prow[t]] = bv;
+}
+
+// The panel's row permutation on every column outside it (one thread per
+// column: all the touched entries loaded, then stored), then U12 = L11^-1 A12
+// on the columns right of it (unit lower L11 staged in shared memory).  One
+// warp per block, so that the FP64 work of the triangular solves spreads over
+// many SMs.
+__global__ void __launch_bounds__(32) k_lu_swap_trsm(double* M, const int* perm, int n, int k0, int bw) {
+    dg_grid_release();
+    dg_grid_wait();
+    __shared__ double L[LU_B][LU_B + 1];
+    __shared__ int prow[LU_PERM], psrc[LU_PERM];
+    const int t = threadIdx.x;
+    for (int e = t; e < bw * bw; e += blockDim.x) {
+        const int i = e / bw, l = e - i * bw;
+        L[i][l] = M[(long)(k0 + i) * n + k0 + l];
+    }
+    const int cnt = perm[0];
+    for (int q = t; q < cnt; q += blockDim.x) {
+        prow[q] = perm[1 + q];
+        psrc[q] = perm[1 + LU_PERM + q];
+    }
+    __syncthreads();
+    const int q0 = blockIdx.x * blockDim.x + t;   // over the n - bw columns outside the panel
+    if (q0 >= n - bw) return;
+    const int j = q0 < k0 ? q0 : q0 + bw;
+    double v[LU_PERM];
+#pragma unroll
+    for (int q = 0; q < LU_PERM; ++q)
+        if (q < cnt) v[q] = M[(long)psrc[q] * n + j];
+#pragma unroll
+    for (int q = 0; q < LU_PERM; ++q)
+        if (q < cnt) M[(long)prow[q] * n + j] = v[q];
+    if (j < k0 + bw) return;
+    double u[LU_B];
+#pragma unroll
+    for (int i = 0; i < LU_B; ++i) u[i] = i < bw ? M[(long)(k0 + i) * n + j] : 0.0;
+#pragma unroll
+    for (int i = 1; i < LU_B; ++i) {
+        if (i < bw) {
+            double s = u[i];
+#pragma unroll
+            for (int l = 0; l < i; ++l) s = fma(-L[i][l], u[l], s);
+            u[i] = s;
+        }
+    }
+#pragma unroll
+    for (int i = 1; i < LU_B; ++i)
+        if (i < bw) M[(long)(k0 + i) * n + j] = u[i];
 }
 
 // A22 -= L21 U12 over rows and columns k0+bw..n-1 (inner dimension bw <=
 // LU_B): 32 x 32 output tiles, 256 threads with 4 outputs each, the tile's L21
 // rows and U12 columns staged in shared memory.
 __global__ void __launch_bounds__(256) k_lu_gemm(double* M, int n, int k0, int bw) {
+    dg_grid_release();
+    dg_grid_wait();
     __shared__ double Ls[32][LU_B + 1], Us[LU_B][32 + 1];
     const int r0 = k0 + bw + blockIdx.y * 32, c0 = k0 + bw + blockIdx.x * 32;
     const int t = threadIdx.x;
@@ -239,23 +348,59 @@ __global__ void __launch_bounds__(256) k_lu_gemm(double* M, int n, int k0, int b
     }
 }
 
-// L y = b (unit lower), then U x = y, column-oriented with b in shared memory
-// (n <= 4096); x overwrites b.
+// L y = b (unit lower), then U x = y, in blocks of 32 rows with b in shared
+// memory (n <= 4096); x overwrites b.  Per block, warp 0 solves the diagonal
+// block (lane = row, the solved entries passed by shuffles), then one warp per
+// remaining row subtracts the block's contribution (lane = column: coalesced
+// 256-byte reads of M).
 __global__ void __launch_bounds__(1024) k_lu_trisolve(const double* M, double* b, int n) {
+    dg_grid_release();
+    dg_grid_wait();
     extern __shared__ double sb[];
-    const int t = threadIdx.x, nt = blockDim.x;
+    __shared__ double D[32][33];
+    const int t = threadIdx.x, nt = blockDim.x, lane = t & 31, wid = t >> 5, nw = nt >> 5;
     for (int i = t; i < n; i += nt) sb[i] = b[i];
-    __syncthreads();
-    for (int j = 0; j < n; ++j) {          // forward: b_i -= L_ij y_j, i > j
-        const double yj = sb[j];
-        for (int i = j + 1 + t; i < n; i += nt) sb[i] -= M[(long)i * n + j] * yj;
+    for (int j0 = 0; j0 < n; j0 += 32) {   // forward
+        const int w = min(32, n - j0);
+        for (int e = t; e < w * w; e += nt) D[e / w][e % w] = M[(long)(j0 + e / w) * n + j0 + e % w];
+        __syncthreads();
+        if (wid == 0) {
+            double y = lane < w ? sb[j0 + lane] : 0.0;
+            for (int c = 0; c < w - 1; ++c) {
+                const double yc = __shfl_sync(0xffffffffu, y, c);
+                if (lane > c && lane < w) y = fma(-D[lane][c], yc, y);
+            }
+            if (lane < w) sb[j0 + lane] = y;
+        }
+        __syncthreads();
+        const double yl = lane < w ? sb[j0 + lane] : 0.0;
+        for (int i = j0 + w + wid; i < n; i += nw) {
+            double v = lane < w ? M[(long)i * n + j0 + lane] * yl : 0.0;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) sb[i] -= v;
+        }
         __syncthreads();
     }
-    for (int j = n - 1; j >= 0; --j) {     // backward: x_j = y_j / U_jj, then b_i -= U_ij x_j, i < j
-        const double xj = sb[j] / M[(long)j * n + j];
+    for (int j1 = n; j1 > 0; j1 -= 32) {   // backward
+        const int j0 = max(0, j1 - 32), w = j1 - j0;
+        for (int e = t; e < w * w; e += nt) D[e / w][e % w] = M[(long)(j0 + e / w) * n + j0 + e % w];
         __syncthreads();
-        if (t == 0) sb[j] = xj;
-        for (int i = t; i < j; i += nt) sb[i] -= M[(long)i * n + j] * xj;
+        if (wid == 0) {
+            double y = lane < w ? sb[j0 + lane] : 0.0;
+            for (int c = w - 1; c >= 0; --c) {
+                if (lane == c) y = y / D[c][c];
+                const double xc = __shfl_sync(0xffffffffu, y, c);
+                if (lane < c) y = fma(-D[lane][c], xc, y);
+            }
+            if (lane < w) sb[j0 + lane] = y;
+        }
+        __syncthreads();
+        const double xl = lane < w ? sb[j0 + lane] : 0.0;
+        for (int i = wid; i < j0; i += nw) {
+            double v = lane < w ? M[(long)i * n + j0 + lane] * xl : 0.0;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) sb[i] -= v;
+        }
         __syncthreads();
     }
     for (int i = t; i < n; i += nt) b[i] = sb[i];
@@ -269,31 +414,44 @@ extern "C" dg_status dg_dense_solve(dg_handle* h, const double* F, double* x) {
     const int nb = dg_nb(h->asm_k);
     const long n = (long)h->ne * nb;
     if (n > 4096) return dg_fail(h, DG_ERR_INVALID_ARG, "dense solve is limited to 4096 unknowns");
-    dg_status s = dg_scratch(h, sizeof(double) * (size_t)n * n + 64);
+    const size_t mbytes = (sizeof(double) * (size_t)n * n + 255) / 256 * 256;
+    dg_status s = dg_scratch(h, mbytes + sizeof(int) * (1 + 2 * LU_PERM));
     if (s != DG_OK) return s;
     double* M = h->scratch;
+    int* perm = reinterpret_cast<int*>(reinterpret_cast<char*>(h->scratch) + mbytes);
     DG_CK(h, cudaMemsetAsync(M, 0, sizeof(double) * (size_t)n * n, h->stream));
     DG_CK(h, cudaMemsetAsync(h->dflag, 0, sizeof(int), h->stream));
     long tot = (long)h->ne * 4 * nb * nb;
     k_densify<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(h->A64, h->nbr, h->ne, nb, M, n);
     DG_CK(h, cudaMemcpyAsync(x, F ? F : h->F, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
-    const int nn = (int)n;
-    int launches = 1;
-    for (int k0 = 0; k0 < nn; k0 += LU_B) {
-        const int bw = nn - k0 < LU_B ? nn - k0 : LU_B;
-        k_lu_panel<<<1, 1024, 0, h->stream>>>(M, x, nn, k0, bw, h->dflag);
-        ++launches;
-        const int rest = nn - k0 - bw;
-        if (rest > 0) {
-            k_lu_trsm<<<(unsigned)((rest + 255) / 256), 256, 0, h->stream>>>(M, nn, k0, bw);
-            const unsigned gt = (unsigned)((rest + 31) / 32);
-            k_lu_gemm<<<dim3(gt, gt), 256, 0, h->stream>>>(M, nn, k0, bw);
-            launches += 2;
-        }
-    }
+    DG_CK(h, cudaFuncSetAttribute(k_lu_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, LU_SMEM));
     DG_CK(h, cudaFuncSetAttribute(k_lu_trisolve, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)(sizeof(double) * n)));
-    k_lu_trisolve<<<1, 1024, sizeof(double) * n, h->stream>>>(M, x, nn);
+    const bool pdl = h->pdl && h->stream != nullptr;
+    const int nn = (int)n;
+    int launches = 1;
+    for (int k0 = 0; k0 < nn;) {
+        const int R = nn - k0;
+        const int bw = std::min(lu_panel_width(R), R);
+        // about four rows a thread: fewer warps make the per-column barriers cheaper
+        const int nt = std::min(1024, std::max(32, ((R + 3) / 4 + 31) / 32 * 32));
+        const size_t sm = sizeof(double) * (size_t)(R | 1) * bw;
+        dg_launch_smem(h, pdl, sm, k_lu_panel, dim3(1), dim3(nt), M, x, perm, nn, k0, bw, h->dflag);
+        ++launches;
+        if (nn > bw) {
+            dg_launch(h, pdl, k_lu_swap_trsm, dim3((unsigned)((nn - bw + 31) / 32)), dim3(32), M, (const int*)perm,
+                      nn, k0, bw);
+            ++launches;
+        }
+        const int rest = R - bw;
+        if (rest > 0) {
+            const unsigned gt = (unsigned)((rest + 31) / 32);
+            dg_launch(h, pdl, k_lu_gemm, dim3(gt, gt), dim3(256), M, nn, k0, bw);
+            ++launches;
+        }
+        k0 += bw;
+    }
+    dg_launch_smem(h, pdl, sizeof(double) * n, k_lu_trisolve, dim3(1), dim3(1024), (const double*)M, x, nn);
     h->nlaunch += launches + 1;
     DG_LAUNCH_CK(h);
     int flag = 0;

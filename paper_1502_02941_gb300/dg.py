@@ -28,7 +28,7 @@ DG_F64, DG_F32, DG_BF16 = 0, 1, 2
 DG_STORE_F64, DG_STORE_F32, DG_STORE_BF16 = 1, 2, 4
 DG_PRECOND_NONE, DG_PRECOND_BLOCK_JACOBI, DG_PRECOND_MLP, DG_PRECOND_SCHWARZ = 0, 1, 2, 3
 DG_POINTS_VOLUME, DG_POINTS_BOUNDARY, DG_POINTS_ERROR, DG_POINTS_FACE = 0, 1, 2, 3
-DG_PROF_DOTS, DG_PROF_UPDATE = 1, 2
+DG_PROF_DOTS, DG_PROF_UPDATE, DG_PROF_APPLY = 1, 2, 3
 DG_WS_TOTAL, DG_WS_MESH, DG_WS_OPERATOR, DG_WS_PRECOND, DG_WS_SOLVER, DG_WS_LEARNED, DG_WS_SCRATCH, DG_WS_PEAK = range(8)
 
 c_int32, c_int64, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p

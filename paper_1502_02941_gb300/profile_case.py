@@ -1,5 +1,6 @@
-"""Launch one hot kernel of the solver on the 256x256 P2 workload, for
-profilers (a small, self-contained case: ~0.6 GB on the device).
+"""Launch one hot kernel of the solver on the 256x256 P2 workload (or, with
+--p3, the P3 Gaussian bump; --N 512 holds ~3 GB), for profilers (a small,
+self-contained case: ~0.6 GB on the device).
 
     python -m paper_1502_02941_gb300.profile_case --kernel dots --j 25 --reps 3
     python -m paper_1502_02941_gb300.profile_case --kernel apply64 --reps 3
@@ -11,7 +12,8 @@ preconditioner's tensor-core inference (dg_mlp_forward) on one feature row
 per element (131072 rows); bsolve: one batched f32 GMRES-based refinement
 (Schwarz) of the P2 instances among the first --batch instances of the
 batched workload; apply64 / apply32 / apply16:
-the block-sparse operator apply on the f64 / f32 / bf16 block copy; assemble:
+the block-sparse operator apply on the f64 / f32 / bf16 block copy (timed by
+dg_profile_kernel around the bare launch, L2 flushed by reads before each); assemble:
 one assembly; step: the benchmark's step (mesh upload, assembly, block-Jacobi
 set-up and f64 GMRES(50) to 1e-10 for NIPG and SIPG) after one untimed step,
 inside an NVTX range "timed_steps".  Prints the average CUDA-event time per
@@ -33,6 +35,8 @@ def main(argv=None):
     ap.add_argument("--f32", action="store_true", help="f32 Arnoldi kernels (dots / update)")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--N", type=int, default=256)
+    ap.add_argument("--p3", action="store_true",
+                    help="the P3 Gaussian-bump workload on N x N split squares instead of the P2 boundary layer")
     a = ap.parse_args(argv)
 
     import torch
@@ -41,7 +45,7 @@ def main(argv=None):
     from . import problem
     from . import workloads as W
 
-    cfg = W.boundary_layer_p2(method=2, N=a.N)
+    cfg = W.gaussian_bump_p3(N=a.N) if a.p3 else W.boundary_layer_p2(method=2, N=a.N)
     h = D.DG(0)
     if a.kernel == "bsolve":
         cfgs, ma, starts, coeffs = W.batch_by_degree("batched", a.batch)[2]
@@ -128,19 +132,9 @@ def main(argv=None):
         out["j"] = a.j
         out["ms"] = h.profile_kernel(which, D.DG_F32 if a.f32 else D.DG_F64, a.j, reps=a.reps)
     else:
+        # the bare launch between CUDA events inside the library, L2 flushed by reads before each
         dt = {"apply64": D.DG_F64, "apply32": D.DG_F32, "apply16": D.DG_BF16}[a.kernel]
-        td = torch.float64 if dt == D.DG_F64 else torch.float32
-        x = torch.randn(info.dofs, dtype=td, device="cuda")
-        y = torch.empty_like(x)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        tot = 0.0
-        for _ in range(a.reps):
-            e0.record()
-            h.apply(x, dt, y)
-            e1.record()
-            e1.synchronize()
-            tot += e0.elapsed_time(e1)
-        out["ms"] = tot / a.reps
+        out["ms"] = h.profile_kernel(D.DG_PROF_APPLY, dt, 0, reps=a.reps)
     print(json.dumps(out))
     h.close()
 

@@ -565,9 +565,12 @@ def test_schwarz_gmres_reaches_tolerance_in_fewer_steps():
 
 @pytest.mark.parametrize("N,k", [(10, 2), (13, 3)])
 def test_blocked_dense_lu_matches_oracle(N, k):
-    """The blocked LU of the dense solve (32-column panels, the last one ragged:
-    1200 and 3380 unknowns) equals the oracle's direct solve as a function,
-    and an all-zero operator is reported as singular."""
+    """The blocked LU of the dense solve equals the oracle's direct solve as a
+    function, and an all-zero operator is reported as singular.  1200 and 3380
+    unknowns: panels of 16 (8, then 16) columns, as wide as the shared-memory
+    panel allows for the rows left, the last one ragged; the 1200-unknown
+    operator takes 490 row swaps under partial pivoting (LAPACK's getrf on
+    the same matrix), so the pivoting path is exercised."""
     prob = W.Problem("gauss", 0.05, 0.4, (0.5, 0.0, -1.0, -0.5, 1.0, 0.0), W.gaussian_bump,
                      neumann_sides=("right", "top"))
     ma = W.perturbed_mesh(N, seed=3, neumann_sides=prob.neumann_sides)

@@ -42,7 +42,24 @@ def test_cli_newton_on_the_papers_nonlinear_example():
     assert out["ne"] == 128 and abs(out["l2_error"] - l2o) <= 1e-5 * l2o and abs(out["h_max"] - hmo) <= 1e-15
 
 
-@pytest.mark.parametrize("kernel", ["dots", "update", "apply32", "assemble", "mlp"])
+@pytest.mark.parametrize("kernel", ["dots", "update", "apply32", "apply16", "assemble", "mlp"])
 def test_profile_case_kernels(kernel):
     out = _run("paper_1502_02941_gb300.profile_case", "--kernel", kernel, "--N", "32", "--reps", "2")
     assert out["ms"] > 0
+
+
+def test_profile_hook_times_the_apply_of_each_stored_copy():
+    """DG_PROF_APPLY times one bare apply per stored block copy; a copy that is
+    not stored is a state error, an unknown dtype an argument error."""
+    from paper_1502_02941_gb300 import dg as D
+    from paper_1502_02941_gb300 import problem
+    from paper_1502_02941_gb300 import workloads as W
+    h = D.DG(0)
+    problem.setup(h, W.boundary_layer_p2(N=16), store=D.DG_STORE_F64 | D.DG_STORE_F32, gmres_m=20)
+    for dt in (D.DG_F64, D.DG_F32):
+        assert h.profile_kernel(D.DG_PROF_APPLY, dt, 0, reps=2) > 0
+    for dt, st in ((D.DG_BF16, D.DG_ERR_STATE), (7, D.DG_ERR_INVALID_ARG)):
+        with pytest.raises(D.DGError) as e:
+            h.profile_kernel(D.DG_PROF_APPLY, dt, 0, reps=2)
+        assert e.value.status == st
+    h.close()
