@@ -430,9 +430,16 @@ dg_status dg_gmres_ir_solve(dg_handle* h, int inner_dtype, int inner_m, double i
                             const double* F, double* x, dg_solve_info* info);
 
 /*
- * Direct solve Stiff x = F (the paper's coef = Stiff\F) by dense LU with
- * partial pivoting on the device, f64.  For small systems: dofs <= 4096.
- * F device or NULL (assembled F); x device output.  Synchronises.
+ * Direct solve Stiff x = F (the paper's coef = Stiff\F, Sec. 2.3) by dense LU
+ * with partial pivoting on the device.  For small systems: dofs <= 4096.
+ * The matrix is factored in f32 and the solution refined in f64 (residual
+ * F - Stiff x with the f64 blocks, correction from the f32 factors) until
+ * ||F - Stiff x||_inf <= sqrt(dofs) eps_f64 ||Stiff||_inf ||x||_inf, at most 10
+ * steps; when that does not converge, or the f32 factorization meets a zero
+ * pivot, the matrix is factored in f64 instead (also when the environment
+ * variable DG_DENSE_F64=1 was set at dg_create).  F device or NULL (assembled
+ * F; may equal x); x device output.  DG_ERR_SINGULAR_BLOCK when the f64
+ * factorization meets a zero pivot.  Synchronises.
  */
 dg_status dg_dense_solve(dg_handle* h, const double* F, double* x);
 

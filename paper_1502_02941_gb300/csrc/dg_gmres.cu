@@ -596,147 +596,6 @@ __global__ void __launch_bounds__(256) k_gm_update32(float* V, long ld, long nve
     }
 }
 
-// The apply of an f32 Arnoldi step fused with its multi-dot (pass 1):
-//   w = V_{j+1} = s A x   (x = V_j with s = s_j, or x = xfix with s = 1),
-//   r_d = <V_d, w> for d <= j and r_{j+1} = ||w||^2,
-// then the tail of k_gm_dots32 (h_d, the update coefficients, the norm or a
-// request for a second pass).  One warp per 32-element tile (lane = element)
-// computes the tile's rows of w as k_apply does, keeps them in registers and
-// takes the dots with the tile's rows of V_0..V_j (32 * NB consecutive entries
-// of each, eight vectors per round of loads); lanes sum in f32, the warp in an
-// f32 tree, the block's warps and then the blocks in two-float arithmetic.  This
-// saves the multi-dot kernel's launch, ramp and tail and its re-read of w.
-#define AD_WARPS 8
-template <int NB, typename TA>
-__global__ void __launch_bounds__(AD_WARPS * 32) k_apply_dots32(const TA* __restrict__ A, const int* __restrict__ nbr,
-                                                                float* V, long ld, const float* xfix, int ne,
-                                                                GmresState* st, float2* partials) {
-    using CH = Chunk<TA, float>;
-    constexpr int W = CH::W;
-    constexpr int C = (NB * NB + W - 1) / W;
-    dg_grid_release();   // programmatic dependent launch
-    dg_grid_wait();
-    if (!st->active) return;
-    const int j = st->j;
-    const int ncol = j + 2;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __shared__ float red[AD_WARPS][DG_MAXM + 2];
-    __shared__ float2 tot[DG_MAXM + 2];
-    __shared__ double hp[DG_MAXM + 2];
-    for (int d = lane; d < ncol; d += 32) red[warp][d] = 0.f;
-    const float* __restrict__ x = xfix ? xfix : V + (long)j * ld;
-    const float sc = xfix ? 1.f : (float)st->scale[j];
-    float* w = V + (long)(j + 1) * ld;
-    const int ntiles = (ne + 31) / 32;
-    for (int tile = blockIdx.x * AD_WARPS + warp; tile < ntiles; tile += gridDim.x * AD_WARPS) {
-        const int K = tile * 32 + lane;
-        const bool live = K < ne;
-        float acc[NB];
-#pragma unroll
-        for (int r = 0; r < NB; ++r) acc[r] = 0.f;
-        if (live) {
-            int Ls[4] = {K, -1, -1, -1};
-#pragma unroll
-            for (int f = 0; f < 3; ++f) Ls[1 + f] = __ldg(nbr + (size_t)f * ne + K);
-#pragma unroll
-            for (int sl = 0; sl < 4; ++sl) {
-                const int Ln = Ls[sl];
-                if (Ln < 0) continue;
-                float xv[NB];
-                load_x<NB, float, float>(x, Ln, xv);
-                const TA* base = A + (((size_t)tile * 4 + sl) * C * 32 + lane) * W;
-#pragma unroll
-                for (int c = 0; c < C; ++c) {
-                    float v[W];
-                    CH::load(base + (size_t)c * 32 * W, v);
-#pragma unroll
-                    for (int q = 0; q < W; ++q) {
-                        const int m = c * W + q;
-                        if (m < NB * NB) acc[m / NB] = fmaf(v[q], xv[m % NB], acc[m / NB]);
-                    }
-                }
-            }
-#pragma unroll
-            for (int r = 0; r < NB; ++r) acc[r] *= sc;
-            store_y<NB, float, float>(w, K, acc);
-        }
-        // dots of the tile's rows: eight basis vectors per round of loads
-        for (int d0 = 0; d0 <= j; d0 += 8) {
-            float p[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                p[u] = 0.f;
-                if (live && d0 + u <= j) {
-                    float vr[NB];
-                    load_x<NB, float, float>(V + (long)(d0 + u) * ld, K, vr);
-#pragma unroll
-                    for (int r = 0; r < NB; ++r) p[u] = fmaf(vr[r], acc[r], p[u]);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                if (d0 + u > j) break;   // warp-uniform
-                float v = p[u];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (lane == 0) red[warp][d0 + u] += v;
-            }
-        }
-        float pw = 0.f;
-#pragma unroll
-        for (int r = 0; r < NB; ++r) pw = fmaf(acc[r], acc[r], pw);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) pw += __shfl_xor_sync(0xffffffffu, pw, o);
-        if (lane == 0) red[warp][j + 1] += pw;
-    }
-    __syncthreads();
-    const int gx = gridDim.x;
-    for (int d = threadIdx.x; d < ncol; d += blockDim.x) {
-        float2 sacc = make_float2(0.f, 0.f);
-        for (int q = 0; q < AD_WARPS; ++q) sacc = f2_add(sacc, make_float2(red[q][d], 0.f));
-        partials[(long)d * gx + blockIdx.x] = sacc;
-    }
-    if (!last_block(&st->arrive)) return;
-    for (int d = warp; d < ncol; d += AD_WARPS) {
-        float2 sacc = make_float2(0.f, 0.f);
-        for (int b = lane; b < gx; b += 32) sacc = f2_add(sacc, __ldcg(partials + (long)d * gx + b));
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            float2 t;
-            t.x = __shfl_xor_sync(0xffffffffu, sacc.x, o);
-            t.y = __shfl_xor_sync(0xffffffffu, sacc.y, o);
-            sacc = f2_add(sacc, t);
-        }
-        if (lane == 0) tot[d] = sacc;
-    }
-    __syncthreads();
-    for (int d = threadIdx.x; d < ncol; d += blockDim.x) {
-        const double r = (double)tot[d].x + (double)tot[d].y;
-        if (d == j + 1) {
-            hp[d] = r;
-        } else {
-            const double hd = st->scale[d] * r;
-            hp[d] = hd;
-            st->hcol[d] = hd;
-            st->coef[d] = hd * st->scale[d];
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x >= 32) return;
-    double s2 = 0.0;
-    for (int d = threadIdx.x; d <= j; d += 32) s2 = fma(hp[d], hp[d], s2);
-    s2 = dg_warp_sum(s2);
-    if (threadIdx.x != 0) return;
-    const double w2 = hp[j + 1];
-    const double rest = w2 - s2;
-    st->jw = j;
-    const bool again = !(rest >= DG_REORTH_FRAC * w2);
-    st->reorth = again ? 1 : 0;
-    if (again) return;
-    st->wn_fin = sqrt(rest > 0.0 ? rest : 0.0);
-    st->colready = 1;
-}
-
 // Launch the multi-dot + update pair of Gram-Schmidt pass `pass`.
 template <typename TV>
 static void launch_gs_pass(dg_handle* h, GmresWork& W, TV* V, long ld, long nvec, bool pdl, int pass) {
@@ -895,34 +754,7 @@ static int enqueue_cycle(dg_handle* h, GmresWork& W, const TA* A, const TB* B, c
     // solves/s on the 256x256 P2 workload; f32 refinement 12.74 against 12.64)
     const bool pdl = h->pdl && h->stream != nullptr && sizeof(TV) == 4;
     int extra = 0;
-    // f32 vectors without the learned correction: the step's (last) apply and
-    // its multi-dot are one kernel (k_apply_dots32), then the update and the
-    // conditional second Gram-Schmidt pass
-    if constexpr (sizeof(TV) == 4) {
-        if (!flex) {
-            const unsigned ntiles = (unsigned)((h->ne + 31) / 32);
-            const unsigned gad = std::min((ntiles + AD_WARPS - 1) / AD_WARPS, 4096u);
-            for (int it = 0; it < W.m; ++it) {
-                const float* xfix = nullptr;
-                const TA* Aop = A;
-                if (G) {
-                    launch_apply<NB, TV, TV>(h, G, V, Z, step, vj, vsel_fixed(), pdl);   // Z = s_j G V_j
-                    xfix = (const float*)Z;
-                } else if (Ah) {
-                    Aop = Ah;                                                             // (A M^-1) s_j V_j
-                } else {
-                    launch_bj<NB, TB, TV>(h, B, V, Z, step, vj, vsel_fixed(), pdl);      // Z = s_j M^-1 V_j
-                    xfix = (const float*)Z;
-                }
-                dg_launch(h, pdl, k_apply_dots32<NB, TA>, dim3(gad), dim3(AD_WARPS * 32), Aop, (const int*)h->nbr,
-                          (float*)V, ld, xfix, h->ne, st, (float2*)W.partials);
-                dg_launch(h, pdl, k_gm_update32, dim3(W.gu32 + 1), dim3(256), (float*)V, ld, nvec, st, 1);
-                launch_gs_pass<TV>(h, W, V, ld, nvec, pdl, 2);
-                extra += (G || !Ah) ? -1 : -2;   // 5 kernels a step (4 with A M^-1) instead of 6
-            }
-        }
-    }
-    for (int it = 0; it < W.m && !(sizeof(TV) == 4 && !flex); ++it) {
+    for (int it = 0; it < W.m; ++it) {
         if (flex) {
             // Z_j = s_j M_BJ^-1 V_j + MLP correction, kept for the update of x
             VecSel zj{&st->j, 0, ld};

@@ -588,3 +588,34 @@ def test_blocked_dense_lu_matches_oracle(N, k):
         hz.dense_solve()
     assert e.value.status == D.DG_ERR_SINGULAR_BLOCK
     hz.close()
+
+
+@pytest.mark.parametrize("N,k", [(8, 1), (10, 2)])
+def test_dense_solve_refined_f32_factors_and_f64_factors_agree(N, k, monkeypatch):
+    """The dense solve's two paths: f32 factors with f64 refinement (the
+    default) and f64 factors (DG_DENSE_F64=1 at dg_create) both equal the
+    oracle's direct solve, their true residuals are at f64 rounding level, and
+    F may be the output vector itself."""
+    prob = W.Problem("gauss", 0.05, 0.4, (0.5, 0.0, -1.0, -0.5, 1.0, 0.0), W.gaussian_bump,
+                     neumann_sides=("right", "top"))
+    ma = W.perturbed_mesh(N, seed=5, neumann_sides=prob.neumann_sides)
+    run = oracle_run(ma, k, 2, prob)
+    xo = oracle_direct(run)
+    T = basis_change(run, ma, k)
+    xs = []
+    for f64 in (False, True):
+        if f64:
+            monkeypatch.setenv("DG_DENSE_F64", "1")
+        h = gpu_setup(ma, k, 2, prob)
+        monkeypatch.delenv("DG_DENSE_F64", raising=False)
+        xg = h.dense_solve()
+        F = h.rhs()
+        rr = (torch.linalg.norm(F - h.apply(xg)) / torch.linalg.norm(F)).item()
+        assert rr <= 1e-13, (f64, rr)
+        assert np.abs(x_to_oracle(T, _np(xg)) - xo).max() <= 1e-10 * np.abs(xo).max()
+        xa = F.clone()
+        h.check(D.dg_dense_solve(h.h, xa, xa))   # F and x the same vector
+        assert torch.equal(xa, xg)
+        xs.append(_np(xg))
+        h.close()
+    assert np.abs(xs[0] - xs[1]).max() <= 1e-11 * np.abs(xs[1]).max()
