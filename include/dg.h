@@ -608,10 +608,18 @@ dg_status dg_mlp_num_rows(dg_handle* h, int64_t* rows);
 dg_status dg_mlp_get_rows(dg_handle* h, float* X, float* T, int64_t max_rows);   /* host outputs */
 dg_status dg_mlp_clear_data(dg_handle* h);
 /* Adam on random mini-batches of the collected rows: `steps` updates of
-   batch_rows rows each, learning rate lr; loss host [steps] or NULL.  Synchronises. */
+   batch_rows rows each, learning rate lr; loss host [steps] or NULL.  The
+   forward and backward GEMMs of each step run on the tcgen05 tensor cores
+   (bf16 operands, f32 accumulation in tensor memory; the weight gradients'
+   sums over the rows split over CTAs and reduced in a fixed order).
+   DG_ERR_TIMEOUT when a tensor-core kernel gave up waiting for its MMAs.
+   Synchronises. */
 dg_status dg_mlp_train(dg_handle* h, int steps, int batch_rows, float lr, uint64_t seed, float* loss);
 /* Loss (mean 0.5|y-t|^2) and gradient at the current weights on caller rows
-   X device [rows][din], T device [rows][nb] (f32); loss, grad host. */
+   X device [rows][din], T device [rows][nb] (f32); loss, grad host.  The GEMMs
+   run in f32 on the CUDA cores; with the environment variable DG_MLP_GRAD_TC=1
+   set at dg_create they run on the tensor cores as in dg_mlp_train (then
+   DG_ERR_TIMEOUT as there).  Synchronises. */
 dg_status dg_mlp_loss_grad(dg_handle* h, const float* X, const float* T, int rows, double* loss, float* grad);
 /* Tensor-core forward pass y on caller feature rows: X device [rows][din], Y device [rows][nb] (f32).
    The inference kernel (tcgen05 MMAs with accumulators in tensor memory)

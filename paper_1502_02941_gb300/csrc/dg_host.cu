@@ -271,6 +271,8 @@ extern "C" dg_status dg_create(dg_handle** out, int device, void* stream) {
     h->pdl = !(pdl && pdl[0] == '0');
     const char* d64 = getenv("DG_DENSE_F64");
     h->dense_f64 = d64 && d64[0] == '1';
+    const char* gtc = getenv("DG_MLP_GRAD_TC");
+    h->mlp_grad_tc = gtc && gtc[0] == '1';
     const char* inj = getenv("DG_FAIL_CUDA_CALL");   // test hook, see DG_CK
     h->fail_cuda_in = inj ? atol(inj) : 0;
     if (cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {

@@ -232,6 +232,7 @@ struct dg_handle {
     bool mlp_fallback = false;     // the last flexible solve switched the MLP off
     bool pdl = true;               // programmatic dependent launch of the f32 Arnoldi-step kernels
     bool dense_f64 = false;        // dense solve: f64 factorization only (no f32 factors + refinement)
+    bool mlp_grad_tc = false;      // dg_mlp_loss_grad on the tensor cores (as training), not the f32 GEMMs
     int nsm = 0;                   // SMs on the device
     // Krylov basis of the last f64 solve (dg_gmres_solve / dg_batch_solve with
     // DG_F64): basis_n vectors of leading dimension basis_ld (f64, unnormalised);

@@ -209,8 +209,33 @@ __global__ void k_mlp_gather(const float* __restrict__ X, const float* __restric
 
 // Loss and gradient of the network (weights wr) on rows Xb/Tb (device).  ws
 // holds H1,H2,H3 [B][128], Y/D [B][nb], dH [B][128] x 2.
+template <bool TA, bool TB>
+static int tcgemm(cudaStream_t s, int nsm, int M, int N, int K, const float* A, int lda, const float* B, int ldb,
+                  float* C, int ldc, const float* bias, int relu, const float* mask, int ldm, float* part, int* err);
+
+// Where the GEMMs of a training step run: the f32 CUDA-core tiles (k_sgemm) or
+// the tensor cores with bf16 operands and f32 accumulation (tcgemm).
+struct GemmSel {
+    bool tc;
+    int nsm;
+    float* part;
+    int* err;
+    int launches;   // kernels launched so far
+};
+template <bool TA, bool TB>
+static void gemm_sel(GemmSel& g, cudaStream_t s, int M, int N, int K, const float* A, int lda, const float* B,
+                     int ldb, float* C, int ldc, const float* bias = nullptr, int relu = 0,
+                     const float* mask = nullptr, int ldm = 0) {
+    if (g.tc) {
+        g.launches += tcgemm<TA, TB>(s, g.nsm, M, N, K, A, lda, B, ldb, C, ldc, bias, relu, mask, ldm, g.part, g.err);
+    } else {
+        sgemm<TA, TB>(s, M, N, K, A, lda, B, ldb, C, ldc, bias, relu, mask, ldm);
+        ++g.launches;
+    }
+}
+
 static void mlp_loss_grad(cudaStream_t st, const MlpState& S, const MlpOff& o, const float* Xb, const float* Tb,
-                          int B, float* ws, float* grad, double* loss_dev) {
+                          int B, float* ws, float* grad, double* loss_dev, GemmSel& gs) {
     const int din = S.din, nb = S.nb;
     const float* W = S.wr;
     float* H1 = ws;
@@ -221,22 +246,22 @@ static void mlp_loss_grad(cudaStream_t st, const MlpState& S, const MlpOff& o, c
     float* G1 = D + (long)B * 16;
     float* G2 = G1 + (long)B * MW;
     // forward
-    sgemm<false, true>(st, B, MW, din, Xb, din, W + o.W1, din, H1, MW, W + o.b1, 1);
-    sgemm<false, true>(st, B, MW, MW, H1, MW, W + o.W2, MW, H2, MW, W + o.b2, 1);
-    sgemm<false, true>(st, B, MW, MW, H2, MW, W + o.W3, MW, H3, MW, W + o.b3, 1);
-    sgemm<false, true>(st, B, nb, MW, H3, MW, W + o.W4, MW, Y, nb, W + o.b4, 0);
+    gemm_sel<false, true>(gs, st, B, MW, din, Xb, din, W + o.W1, din, H1, MW, W + o.b1, 1);
+    gemm_sel<false, true>(gs, st, B, MW, MW, H1, MW, W + o.W2, MW, H2, MW, W + o.b2, 1);
+    gemm_sel<false, true>(gs, st, B, MW, MW, H2, MW, W + o.W3, MW, H3, MW, W + o.b3, 1);
+    gemm_sel<false, true>(gs, st, B, nb, MW, H3, MW, W + o.W4, MW, Y, nb, W + o.b4, 0);
     k_mlp_lossd<<<64, 256, 0, st>>>(Y, Tb, D, (long)B * nb, B, loss_dev);
     // backward
-    sgemm<true, false>(st, nb, MW, B, D, nb, H3, MW, grad + o.W4, MW);          // gW4 = D^T H3
+    gemm_sel<true, false>(gs, st, nb, MW, B, D, nb, H3, MW, grad + o.W4, MW);          // gW4 = D^T H3
     k_colsum<<<nb, 256, 0, st>>>(D, B, nb, grad + o.b4);
-    sgemm<false, false>(st, B, MW, nb, D, nb, W + o.W4, MW, G1, MW, nullptr, 0, H3, MW);   // dH3
-    sgemm<true, false>(st, MW, MW, B, G1, MW, H2, MW, grad + o.W3, MW);          // gW3 = dH3^T H2
+    gemm_sel<false, false>(gs, st, B, MW, nb, D, nb, W + o.W4, MW, G1, MW, nullptr, 0, H3, MW);   // dH3
+    gemm_sel<true, false>(gs, st, MW, MW, B, G1, MW, H2, MW, grad + o.W3, MW);          // gW3 = dH3^T H2
     k_colsum<<<MW, 256, 0, st>>>(G1, B, MW, grad + o.b3);
-    sgemm<false, false>(st, B, MW, MW, G1, MW, W + o.W3, MW, G2, MW, nullptr, 0, H2, MW);  // dH2
-    sgemm<true, false>(st, MW, MW, B, G2, MW, H1, MW, grad + o.W2, MW);          // gW2
+    gemm_sel<false, false>(gs, st, B, MW, MW, G1, MW, W + o.W3, MW, G2, MW, nullptr, 0, H2, MW);  // dH2
+    gemm_sel<true, false>(gs, st, MW, MW, B, G2, MW, H1, MW, grad + o.W2, MW);          // gW2
     k_colsum<<<MW, 256, 0, st>>>(G2, B, MW, grad + o.b2);
-    sgemm<false, false>(st, B, MW, MW, G2, MW, W + o.W2, MW, G1, MW, nullptr, 0, H1, MW);  // dH1
-    sgemm<true, false>(st, MW, din, B, G1, MW, Xb, din, grad + o.W1, din);       // gW1
+    gemm_sel<false, false>(gs, st, B, MW, MW, G2, MW, W + o.W2, MW, G1, MW, nullptr, 0, H1, MW);  // dH1
+    gemm_sel<true, false>(gs, st, MW, din, B, G1, MW, Xb, din, grad + o.W1, din);       // gW1
     k_colsum<<<MW, 256, 0, st>>>(G1, B, MW, grad + o.b1);
 }
 
@@ -767,6 +792,199 @@ __global__ void __launch_bounds__(MLP_THREADS, 2) k_mlp_tc(const TV* __restrict_
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(MW) : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// tensor-core GEMM for training (tcgen05, accumulators in tensor memory)
+// ---------------------------------------------------------------------------
+// C[M x N] = op(A)[M x K] op(B)[K x N] with the epilogue of k_sgemm (bias[n],
+// relu, mask), N <= 128: op(A)[m][k] = TA ? A[k lda + m] : A[m lda + k] and
+// op(B)[k][n] = TB ? B[n ldb + k] : B[k ldb + n], f32 in global memory.  One
+// CTA of 128 threads per 128-row tile of C and K split (blockIdx.y) over
+// `splits` equal ranges of whole 64-column chunks.  Per chunk the threads
+// gather op(A) (128 x 64) and op(B)^T (Np x 64, Np = N rounded up to 16),
+// round them to bf16 into the K-major core-matrix layout (as k_mlp_tc), and
+// thread 0 issues four tcgen05.mma (M = 128, N = Np, K = 16; f32 accumulation
+// in TMEM) and commits them to an mbarrier.  Thread t then reads row t of the
+// accumulator: with one split it applies the epilogue and stores C, otherwise
+// it stores its split's partial P[split][m][n] for k_tc_gemm_reduce.
+#define TCG_KC 64                          // K columns per staged chunk
+#define TCG_SBO (TCG_KC / 8 * 128)         // bytes between 8-row groups of a chunk tile
+#define TCG_TILE (128 * TCG_KC * 2)        // bytes of one 128-row bf16 chunk tile
+#define TCG_SMEM (3 * TCG_TILE + 1024)     // A and B tiles + slack: at most four CTAs per SM (512 TMEM columns)
+
+template <bool T_, bool ROWK>
+__device__ __forceinline__ float tcg_elem(const float* __restrict__ X, int ld, int r, int k) {
+    // ROWK: element (r, k) at X[r ld + k]; else at X[k ld + r]
+    return ROWK ? X[(long)r * ld + k] : X[(long)k * ld + r];
+}
+
+// Gather rows [r0, r0 + rows) x chunk columns [k0, k0 + TCG_KC) of an operand
+// whose element (r, k) sits at X[r ld + k] (ROWK) or X[k ld + r], as bf16 core
+// matrices.  Entries outside R x K are zero.
+template <bool ROWK>
+__device__ __forceinline__ void tcg_stage(const float* __restrict__ X, int ld, int R, int K, int r0, int k0, int rows,
+                                          unsigned char* dst) {
+    const int units = rows * (TCG_KC / 8);
+    for (int u = threadIdx.x; u < units; u += blockDim.x) {
+        // ROWK: consecutive threads take consecutive 8-column pieces of a row
+        // (contiguous); else consecutive rows of one piece (contiguous along r)
+        const int r = ROWK ? u / (TCG_KC / 8) : u % rows;
+        const int k8 = ROWK ? u % (TCG_KC / 8) : u / rows;
+        float v[8];
+        const int gr = r0 + r;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int gk = k0 + k8 * 8 + i;
+            v[i] = (gr < R && gk < K) ? tcg_elem<false, ROWK>(X, ld, gr, gk) : 0.f;
+        }
+        *reinterpret_cast<uint4*>(dst + cm_off(r, k8 * 8, TCG_SBO)) = pack8_bf16(v);
+    }
+}
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(128) k_tc_gemm(int M, int N, int K, const float* __restrict__ A, int lda,
+                                                 const float* __restrict__ B, int ldb, float* __restrict__ C, int ldc,
+                                                 const float* __restrict__ bias, int relu,
+                                                 const float* __restrict__ mask, int ldm, int kchunks,
+                                                 float* __restrict__ part, int* err) {
+    extern __shared__ unsigned char smraw[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smraw + 1023u) & ~(uintptr_t)1023u);
+    unsigned char* sa = sm;
+    unsigned char* sbt = sm + TCG_TILE;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * TCG_TILE);
+    uint32_t* slot = reinterpret_cast<uint32_t*>(sm + 2 * TCG_TILE + 16);
+    const int t = threadIdx.x, warp = t >> 5;
+    const int m0 = blockIdx.x * 128;
+    const int Np = (N + 15) / 16 * 16;
+    const int kbeg = blockIdx.y * kchunks * TCG_KC;
+    const int kend = min(K, kbeg + kchunks * TCG_KC);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(128)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *slot;
+    const uint32_t idesc = tc_idesc(128, Np);
+    uint32_t phase = 0;
+    bool ok = true;
+    int nchunk = 0;
+    for (int k0 = kbeg; k0 < kend && ok; k0 += TCG_KC, ++nchunk) {
+        // op(A) row m, col k: A[m lda + k] unless TA; op(B)^T row n, col k: B[n ldb + k] when TB
+        tcg_stage<!TA>(A, lda, M, K, m0, k0, 128, sa);
+        tcg_stage<TB>(B, ldb, N, K, 0, k0, Np, sbt);
+        smem_fence_async();   // the staged tiles -> the tensor core's (async) proxy
+        tc_fence_before();
+        __syncthreads();
+        if (t == 0) {
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(sa), b0 = smem_u32(sbt);
+#pragma unroll
+            for (int ks = 0; ks < TCG_KC / 16; ++ks)
+                tc_mma(tmem, tc_desc(a0 + ks * 256u, 128u, TCG_SBO), tc_desc(b0 + ks * 256u, 128u, TCG_SBO), idesc,
+                       (nchunk > 0 || ks > 0) ? 1u : 0u);
+            tc_commit(bar);
+        }
+        // the give-up decision is block-uniform, so every thread takes the same barriers
+        if (__syncthreads_or(mbar_wait(bar, phase) ? 0 : 1)) {
+            ok = false;
+            if (t == 0) {
+                if (err) atomicExch(err, 1);
+                mbar_wait(bar, phase);   // one more bounded wait for the MMAs in flight
+            }
+        }
+        phase ^= 1u;
+        tc_fence_after();
+    }
+    const int m = m0 + t;
+    if (ok && nchunk > 0) {
+        const uint32_t tlane = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int c0 = 0; c0 < Np; c0 += 16) {
+            float v[16];
+            tc_ld16(tlane + (uint32_t)c0, v);   // every thread of the warp takes part
+            if (m >= M) continue;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int n = c0 + i;
+                if (n >= N) break;
+                if (gridDim.y > 1) {
+                    part[((size_t)blockIdx.y * M + m) * N + n] = v[i];
+                } else {
+                    float c = v[i];
+                    if (bias) c += bias[n];
+                    if (relu) c = fmaxf(c, 0.f);
+                    if (mask && !(mask[(long)m * ldm + n] > 0.f)) c = 0.f;
+                    C[(long)m * ldc + n] = c;
+                }
+            }
+        }
+    } else if (!ok || nchunk == 0) {   // an empty split (or a failed wait) contributes zeros
+        if (m < M)
+            for (int n = 0; n < N; ++n) {
+                if (gridDim.y > 1) part[((size_t)blockIdx.y * M + m) * N + n] = 0.f;
+                else C[(long)m * ldc + n] = 0.f;
+            }
+    }
+    // free the tensor memory: every thread's loads have completed (wait::ld)
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128) : "memory");
+}
+
+// C = sum of the splits' partials in split order, then the epilogue.
+__global__ void k_tc_gemm_reduce(int M, int N, int splits, const float* __restrict__ part, float* __restrict__ C,
+                                 int ldc, const float* __restrict__ bias, int relu, const float* __restrict__ mask,
+                                 int ldm) {
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long)M * N) return;
+    const int m = (int)(e / N), n = (int)(e - (long)m * N);
+    float c = 0.f;
+    for (int s = 0; s < splits; ++s) c += part[(size_t)s * M * N + e];
+    if (bias) c += bias[n];
+    if (relu) c = fmaxf(c, 0.f);
+    if (mask && !(mask[(long)m * ldm + n] > 0.f)) c = 0.f;
+    C[(long)m * ldc + n] = c;
+}
+
+#define TCG_MAX_SPLITS 64
+#define TCG_PART_FLOATS ((size_t)TCG_MAX_SPLITS * 128 * 128)   // split-K partials of a <= 128 x 128 product
+
+// C = op(A) op(B) (+ epilogue) on the tensor cores, N <= 128 (k_tc_gemm).  K is
+// split when there are fewer 128-row tiles than SMs (the weight gradients,
+// whose K is the batch of rows), into at most TCG_MAX_SPLITS ranges of whole
+// chunks; `part` holds TCG_PART_FLOATS floats.  Returns the kernels launched.
+template <bool TA, bool TB>
+static int tcgemm(cudaStream_t s, int nsm, int M, int N, int K, const float* A, int lda, const float* B, int ldb,
+                  float* C, int ldc, const float* bias, int relu, const float* mask, int ldm, float* part, int* err) {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_tc_gemm<TA, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, TCG_SMEM);
+        attr = true;
+    }
+    const int mt = (M + 127) / 128;
+    const int chunks = (K + TCG_KC - 1) / TCG_KC;
+    int splits = 1;
+    if (mt < nsm && chunks > 1) {
+        splits = std::min(chunks, std::max(1, 2 * nsm / mt));
+        splits = std::min(splits, (int)(TCG_PART_FLOATS / ((size_t)M * N)));
+        splits = std::max(1, std::min(splits, TCG_MAX_SPLITS));
+    }
+    const int kch = (chunks + splits - 1) / splits;
+    splits = (chunks + kch - 1) / kch;
+    k_tc_gemm<TA, TB><<<dim3(mt, splits), 128, TCG_SMEM, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, relu, mask, ldm,
+                                                               kch, part, err);
+    if (splits > 1)
+        k_tc_gemm_reduce<<<(unsigned)(((long)M * N + 255) / 256), 256, 0, s>>>(M, N, splits, part, C, ldc, bias, relu,
+                                                                               mask, ldm);
+    return splits > 1 ? 2 : 1;
+}
+
 template <int NB, typename TV>
 static dg_status launch_mlp(dg_handle* h, const TV* r, TV* z, DevCtl ctl, VecSel sr, VecSel sz, const int* iuse,
                             const float* Xin, float* Yout, int ne) {
@@ -1013,9 +1231,15 @@ extern "C" dg_status dg_mlp_num_rows(dg_handle* h, int64_t* rows) {
     return DG_OK;
 }
 
+// Training workspace: activations and gradients of B rows, a batch of rows,
+// the loss accumulator, and the split-K partials of the tensor-core GEMMs.
+static size_t mlp_ws_part_offset(const MlpState& S, int B) {
+    const size_t f = mlp_ws_floats(B) + (size_t)B * (S.din + S.nb) + 2 * sizeof(double) / sizeof(float) + 8;
+    return (f + 63) / 64 * 64;   // floats, 256-byte aligned
+}
 static dg_status mlp_ws(dg_handle* h, int B) {
     MlpState& S = h->mlp;
-    const size_t need = sizeof(float) * (mlp_ws_floats(B) + (size_t)B * (S.din + S.nb)) + sizeof(double) * 4;
+    const size_t need = sizeof(float) * (mlp_ws_part_offset(S, B) + TCG_PART_FLOATS);
     if (S.ws_cap >= need) return DG_OK;
     dg_status s = dg_realloc(h, (void**)&S.ws, need);
     S.ws_cap = s == DG_OK ? need : 0;
@@ -1045,21 +1269,25 @@ extern "C" dg_status dg_mlp_train(dg_handle* h, int steps, int batch_rows, float
         k_mlp_set_sigma<<<1, 1, 0, h->stream>>>(lossd, S.rows * S.nb, S.theta + o.sig, S.wr + o.sig);
         h->nlaunch += 2;
     }
+    // the GEMMs of training on the tensor cores
+    GemmSel gs{true, h->nsm, ws + mlp_ws_part_offset(S, batch_rows), h->dflag + DG_FLAG_MLP_TIMEOUT, 0};
     for (int it = 0; it < steps; ++it) {
         k_mlp_gather<<<256, 64, 0, h->stream>>>(S.X, S.T, S.din, S.nb, S.rows, batch_rows, seed, S.step + it, Xb, Tb,
                                                 S.theta + o.sig);
         DG_CK(h, cudaMemsetAsync(lossd, 0, sizeof(double), h->stream));
-        mlp_loss_grad(h->stream, S, o, Xb, Tb, batch_rows, ws, S.grad, lossd);
+        mlp_loss_grad(h->stream, S, o, Xb, Tb, batch_rows, ws, S.grad, lossd, gs);
         ++S.step;
         const float c1 = 1.f - powf(0.9f, (float)S.step), c2 = 1.f - powf(0.999f, (float)S.step);
         k_mlp_adam<<<512, 256, 0, h->stream>>>(S.theta, S.grad, S.m, S.v, S.wr, S.P, lr, c1, c2);
-        h->nlaunch += 20;
+        h->nlaunch += 7;   // gather, loss, four column sums, Adam
         if (loss) DG_CK(h, cudaMemcpyAsync(&hl[it], lossd, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     }
     DG_LAUNCH_CK(h);
     DG_CK(h, cudaStreamSynchronize(h->stream));
+    h->nlaunch += gs.launches;
     if (loss)
         for (int it = 0; it < steps; ++it) loss[it] = (float)hl[it];
+    if ((s = dg_mlp_check_timeout(h)) != DG_OK) return s;
     return mlp_refresh(h);
 }
 
@@ -1079,13 +1307,14 @@ extern "C" dg_status dg_mlp_loss_grad(dg_handle* h, const float* X, const float*
     double* lossd = reinterpret_cast<double*>(((uintptr_t)(ws + mlp_ws_floats(rows) + (size_t)rows * (S.din + S.nb)) + 7) &
                                               ~(uintptr_t)7);
     DG_CK(h, cudaMemsetAsync(lossd, 0, sizeof(double), h->stream));
-    mlp_loss_grad(h->stream, S, o, X, T, rows, ws, S.grad, lossd);
-    h->nlaunch += 18;
+    GemmSel gs{h->mlp_grad_tc, h->nsm, ws + mlp_ws_part_offset(S, rows), h->dflag + DG_FLAG_MLP_TIMEOUT, 0};
+    mlp_loss_grad(h->stream, S, o, X, T, rows, ws, S.grad, lossd, gs);
+    h->nlaunch += 5 + gs.launches;   // + the loss and four column sums
     DG_LAUNCH_CK(h);
     if (loss) DG_CK(h, cudaMemcpyAsync(loss, lossd, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     if (grad) DG_CK(h, cudaMemcpyAsync(grad, S.grad, sizeof(float) * S.P, cudaMemcpyDeviceToHost, h->stream));
     DG_CK(h, cudaStreamSynchronize(h->stream));
-    return DG_OK;
+    return h->mlp_grad_tc ? dg_mlp_check_timeout(h) : DG_OK;
 }
 
 // Tensor-core forward on caller feature rows: Y [rows][nb] (device f32).

@@ -9,7 +9,8 @@ self-contained case: ~0.6 GB on the device).
 dots / update: the Arnoldi multi-dot / update kernel of f64 (or --f32) GMRES at
 step j on a synthetic basis (dg_profile_kernel); mlp: the learned
 preconditioner's tensor-core inference (dg_mlp_forward) on one feature row
-per element (131072 rows); bsolve: one batched f32 GMRES-based refinement
+per element (131072 rows); train: Adam steps of the learned preconditioner on
+8192-row batches (ms per step; its GEMMs run on the tensor cores); bsolve: one batched f32 GMRES-based refinement
 (Schwarz) of the P2 instances among the first --batch instances of the
 batched workload; apply64 / apply32 / apply16:
 the block-sparse operator apply on the f64 / f32 / bf16 block copy (timed by
@@ -29,7 +30,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--kernel", required=True,
                     choices=["dots", "update", "apply64", "apply32", "apply16", "assemble", "step", "mlp",
-                             "bsolve"])
+                             "bsolve", "train"])
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--j", type=int, default=25)
     ap.add_argument("--f32", action="store_true", help="f32 Arnoldi kernels (dots / update)")
@@ -127,6 +128,23 @@ def main(argv=None):
         out["ms"] = tot / a.reps
         out["rows"] = rows
         out["tflops"] = 2.0 * rows * (32 * 128 + 2 * 128 * 128 + 128 * 16) / (out["ms"] / 1e3) / 1e12
+    elif a.kernel == "train":
+        # training rows from a short GMRES run, then Adam steps of 8192 rows
+        # (the GEMMs of each step on the tensor cores)
+        h.mlp_init(seed=3)
+        h.set_params(max_it=10)
+        xk, _ = h.gmres_solve(raise_on_nonconv=False)
+        h.mlp_collect(xk)
+        h.mlp_train(2, batch_rows=8192)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        steps = 10 * a.reps
+        e0.record()
+        h.mlp_train(steps, batch_rows=8192)
+        e1.record()
+        e1.synchronize()
+        out["ms"] = e0.elapsed_time(e1) / steps
+        out["batch_rows"] = 8192
     elif a.kernel in ("dots", "update"):
         which = D.DG_PROF_DOTS if a.kernel == "dots" else D.DG_PROF_UPDATE
         out["j"] = a.j

@@ -28,8 +28,9 @@ def _handle(k=2, N=6):
 
 @pytest.mark.parametrize("k", [1, 2])
 def test_loss_and_gradient_match_oracle(k):
-    """GPU loss/gradient (f32 GEMMs, bf16-rounded weights) vs the FP64 oracle
-    backpropagation on the same bf16-rounded weights."""
+    """GPU loss/gradient (dg_mlp_loss_grad's default f32 GEMMs, bf16-rounded
+    weights) vs the FP64 oracle backpropagation on the same bf16-rounded
+    weights."""
     h, _ = _handle(k)
     nb = O.nbasis(k)
     rng = np.random.default_rng(k)
@@ -44,6 +45,64 @@ def test_loss_and_gradient_match_oracle(k):
     lo, go = M.loss_and_grad(M.bf16_round_params(theta), X.astype(np.float64), T.astype(np.float64), nb)
     assert abs(loss - lo) <= 1e-5 * abs(lo)
     assert np.abs(grad - go).max() <= 2e-5 * np.abs(go).max()
+    h.close()
+
+
+def _oracle_loss_grad_bf16_gemms(theta, X, T, nb):
+    """The oracle's backpropagation (oracle/mlp.py loss_and_grad) with the
+    tensor-core path's roundings: every GEMM operand rounded to bf16 (the
+    weights already are), accumulation, masks and bias sums unrounded."""
+    W1, b1, W2, b2, W3, b3, W4, b4 = M.unpack(M.bf16_round_params(theta), nb)
+    r = M.bf16_round
+    a1 = r(X) @ W1.T + b1
+    h1 = np.maximum(a1, 0)
+    a2 = r(h1) @ W2.T + b2
+    h2 = np.maximum(a2, 0)
+    a3 = r(h2) @ W3.T + b3
+    h3 = np.maximum(a3, 0)
+    y = r(h3) @ W4.T + b4
+    n = X.shape[0]
+    d = (y - T) / n
+    loss = 0.5 * ((y - T) ** 2).sum() / n
+    gW4, gb4 = r(d).T @ r(h3), d.sum(0)
+    d3 = (r(d) @ W4) * (a3 > 0)
+    gW3, gb3 = r(d3).T @ r(h2), d3.sum(0)
+    d2 = (r(d3) @ W3) * (a2 > 0)
+    gW2, gb2 = r(d2).T @ r(h1), d2.sum(0)
+    d1 = (r(d2) @ W2) * (a1 > 0)
+    gW1, gb1 = r(d1).T @ r(X), d1.sum(0)
+    g = np.concatenate([a.ravel() for a in (gW1, gb1, gW2, gb2, gW3, gb3, gW4, gb4)] + [np.zeros(1)])
+    return loss, g
+
+
+@pytest.mark.parametrize("k,rows", [(1, 300), (2, 300), (2, 5000), (3, 300)])
+def test_tensor_core_gradient_matches_oracle_with_bf16_operands(k, rows, monkeypatch):
+    """The training GEMMs on the tensor cores (tcgen05, bf16 operands, f32
+    accumulation; DG_MLP_GRAD_TC=1 routes dg_mlp_loss_grad through them, as
+    dg_mlp_train always does) against the oracle's backpropagation with the
+    same operand roundings.  300 rows leave ragged row tiles and K chunks;
+    5000 rows split the weight gradients' K over many CTAs."""
+    monkeypatch.setenv("DG_MLP_GRAD_TC", "1")
+    h, _ = _handle(k)
+    monkeypatch.delenv("DG_MLP_GRAD_TC")
+    nb = O.nbasis(k)
+    rng = np.random.default_rng(10 + k)
+    theta = (rng.standard_normal(M.n_params(nb)) * 0.1).astype(np.float32)
+    h.mlp_set_weights(theta)
+    X = rng.standard_normal((rows, M.din_of(nb))).astype(np.float32)
+    T = rng.standard_normal((rows, nb)).astype(np.float32)
+    grad = np.zeros(M.n_params(nb), np.float32)
+    s, loss = D.dg_mlp_loss_grad(h.h, torch.tensor(X, device="cuda"), torch.tensor(T, device="cuda"), rows, grad)
+    assert s == D.DG_OK
+    lo, go = _oracle_loss_grad_bf16_gemms(theta, X.astype(np.float64), T.astype(np.float64), nb)
+    assert abs(loss - lo) <= 1e-4 * abs(lo)
+    # (an intermediate can round to the neighbouring bf16 value when f32 and
+    # f64 differ in its last bits: a few such entries, each a 2^-8 change of one
+    # term of a long sum)
+    assert np.abs(grad - go).max() <= 1e-3 * np.abs(go).max()
+    # the f32 gradient of the same weights differs by about the bf16 rounding
+    _, gf = M.loss_and_grad(M.bf16_round_params(theta), X.astype(np.float64), T.astype(np.float64), nb)
+    assert np.abs(grad - gf).max() <= 5e-2 * np.abs(gf).max()
     h.close()
 
 

@@ -42,7 +42,7 @@ def test_cli_newton_on_the_papers_nonlinear_example():
     assert out["ne"] == 128 and abs(out["l2_error"] - l2o) <= 1e-5 * l2o and abs(out["h_max"] - hmo) <= 1e-15
 
 
-@pytest.mark.parametrize("kernel", ["dots", "update", "apply32", "apply16", "assemble", "mlp"])
+@pytest.mark.parametrize("kernel", ["dots", "update", "apply32", "apply16", "assemble", "mlp", "train"])
 def test_profile_case_kernels(kernel):
     out = _run("paper_1502_02941_gb300.profile_case", "--kernel", kernel, "--N", "32", "--reps", "2")
     assert out["ms"] > 0
