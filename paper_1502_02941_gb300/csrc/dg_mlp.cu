@@ -962,11 +962,8 @@ __global__ void k_tc_gemm_reduce(int M, int N, int splits, const float* __restri
 template <bool TA, bool TB>
 static int tcgemm(cudaStream_t s, int nsm, int M, int N, int K, const float* A, int lda, const float* B, int ldb,
                   float* C, int ldc, const float* bias, int relu, const float* mask, int ldm, float* part, int* err) {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_tc_gemm<TA, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, TCG_SMEM);
-        attr = true;
-    }
+    // (per call: the attribute belongs to the current device)
+    cudaFuncSetAttribute(k_tc_gemm<TA, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, TCG_SMEM);
     const int mt = (M + 127) / 128;
     const int chunks = (K + TCG_KC - 1) / TCG_KC;
     int splits = 1;
@@ -1004,8 +1001,13 @@ static dg_status launch_mlp(dg_handle* h, const TV* r, TV* z, DevCtl ctl, VecSel
     if (!Xin && !R.B32) return dg_fail(h, DG_ERR_STATE, "the learned correction needs the block-Jacobi set-up");
     if (R.pk.dinp != (4 * NB + DG_MLP_NFEAT + 15) / 16 * 16) return dg_fail(h, DG_ERR_STATE, "MLP input width");
     const size_t smem = mlp_smem_layout(R.pk.dinp).total;
-    static thread_local int configured[DG_MAXK + 1][2] = {};
-    int& cfg = configured[dg_nb(1) == NB ? 1 : (dg_nb(2) == NB ? 2 : 3)][sizeof(TV) == 8 ? 1 : 0];
+    // the attribute belongs to a device: set once per (thread, device), every call
+    // beyond 64 devices
+    static thread_local int configured[64][DG_MAXK + 1][2] = {};
+    int dummy = 0;
+    int& cfg = h->device >= 0 && h->device < 64
+                   ? configured[h->device][dg_nb(1) == NB ? 1 : (dg_nb(2) == NB ? 2 : 3)][sizeof(TV) == 8 ? 1 : 0]
+                   : dummy;
     if (!cfg) {
         DG_CK(h, cudaFuncSetAttribute(k_mlp_tc<NB, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         cfg = 1;
