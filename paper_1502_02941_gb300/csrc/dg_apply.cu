@@ -67,16 +67,18 @@ __global__ void __launch_bounds__(128) k_bj_setup(const TA* __restrict__ A, int 
         }
 }
 
-// Block (K, slot s) of A M^-1: A_{K,s} Binv_L with L = K (s = 0) or the
-// neighbour across face s-1, in f64; zero for a missing neighbour.  One thread
-// per (element, slot); writes the f64 and / or f32 copy.
+// Block (K, slot s) of A M^-1: A_{K,s} Binv_L with L the neighbour across face
+// s-1, in f64; zero for a missing neighbour.  Slot 0, A_KK A_KK^-1 = I, is not
+// formed: the applies of A M^-1 take it as the identity (k_apply, UNIT).  One
+// thread per (element, slot); writes the f64 and / or f32 copy.
 template <int NB>
 __global__ void __launch_bounds__(128) k_ahat_setup(const double* __restrict__ A, const double* __restrict__ Binv,
                                                      const int* __restrict__ nbr, int ne, double* Ah64, float* Ah32) {
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 4L * ne) return;
     const int K = (int)(t >> 2), s = (int)(t & 3);
-    const int L = s == 0 ? K : __ldg(nbr + (size_t)(s - 1) * ne + K);
+    if (s == 0) return;
+    const int L = __ldg(nbr + (size_t)(s - 1) * ne + K);
     double a[NB][NB], b[NB][NB];
     for (int i = 0; i < NB; ++i)
         for (int j = 0; j < NB; ++j) {

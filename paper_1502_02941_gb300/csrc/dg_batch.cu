@@ -966,7 +966,8 @@ static int b_enqueue_cycle(dg_handle* h, const BatchRun& Rn, const TA* A, const 
                                                               vsel_fixed(), vj1);
         } else if (Ah) {
             // V_{j+1} = s_j (A M^-1) V_j with the precomputed operator
-            k_apply<NB, TA, TV, TV><<<ge, 256, 0, h->stream>>>(Ah, h->nbr, V, V + Rn.ld, h->ne, step, vj, vj);
+            k_apply<NB, TA, TV, TV, true><<<ge, 256, 0, h->stream>>>(Ah, h->nbr, V, V + Rn.ld, h->ne, step, vj,
+                                                                    vj);   // unit diagonal blocks
             --n;
         } else {
             k_bj_apply<NB, TB, TV, TV><<<ge, 256, 0, h->stream>>>(Binv, V, Z, h->ne, step, vj, vsel_fixed());

@@ -715,12 +715,12 @@ __global__ void __launch_bounds__(256) k_gm_resid(const TV* __restrict__ F, cons
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-template <int NB, typename TA, typename TV>
+template <int NB, typename TA, typename TV, bool UNIT = false>
 static void launch_apply(dg_handle* h, const TA* A, const TV* x, TV* y, DevCtl ctl, VecSel sx, VecSel sy,
                          bool pdl = false) {
     const ElemShape es = elem_shape(h);
-    dg_launch(h, pdl, k_apply<NB, TA, TV, TV>, dim3(es.grid), dim3(es.block), A, (const int*)h->nbr, x, y, h->ne,
-              ctl, sx, sy);
+    dg_launch(h, pdl, k_apply<NB, TA, TV, TV, UNIT>, dim3(es.grid), dim3(es.block), A, (const int*)h->nbr, x, y,
+              h->ne, ctl, sx, sy);
 }
 template <int NB, typename TB, typename TV>
 static void launch_bj(dg_handle* h, const TB* B, const TV* r, TV* z, DevCtl ctl, VecSel sr, VecSel sz,
@@ -768,7 +768,7 @@ static int enqueue_cycle(dg_handle* h, GmresWork& W, const TA* A, const TB* B, c
             launch_apply<NB, TA, TV>(h, A, Z, V, step_noscale, vsel_fixed(), vj1, pdl);
         } else if (Ah) {
             // V_{j+1} = s_j (A M^-1) V_j: one apply of the precomputed operator
-            launch_apply<NB, TA, TV>(h, Ah, V, V + ld, step, vj, vj, pdl);
+            launch_apply<NB, TA, TV, true>(h, Ah, V, V + ld, step, vj, vj, pdl);   // unit diagonal blocks
             --extra;
         } else {
             launch_bj<NB, TB, TV>(h, B, V, Z, step, vj, vsel_fixed(), pdl);

@@ -141,7 +141,9 @@ __device__ __forceinline__ void store_y(TX* __restrict__ y, int K, const TACC* v
 // picked from the Krylov basis by the device-side step counter; with
 // ctl.scale set, y is multiplied by the scale factor of the selected x (the
 // lazily normalised basis vector; per instance through ctl.iscale in a batch).
-template <int NB, typename TA, typename TX, typename TACC>
+// UNIT: slot 0 is the identity and is not read (the block-Jacobi-preconditioned
+// operator A M^-1, whose diagonal blocks are A_KK A_KK^-1 = I).
+template <int NB, typename TA, typename TX, typename TACC, bool UNIT = false>
 __global__ void __launch_bounds__(256) k_apply(const TA* __restrict__ A, const int* __restrict__ nbr,
                                                 const TX* __restrict__ x0, TX* __restrict__ y0, int ne,
                                                 DevCtl ctl, VecSel sx, VecSel sy) {
@@ -177,6 +179,11 @@ __global__ void __launch_bounds__(256) k_apply(const TA* __restrict__ A, const i
         if (Ln < 0) continue;
         TACC xv[NB];
         load_x<NB, TX, TACC>(x, Ln, xv);
+        if (UNIT && s == 0) {
+#pragma unroll
+            for (int r = 0; r < NB; ++r) acc[r] += xv[r];
+            continue;
+        }
         const TA* base = A + (((size_t)tile * 4 + s) * C * 32 + lane) * W;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
