@@ -445,19 +445,33 @@ __global__ void __launch_bounds__(B_TX* B_TY) k_b_dots32(const float* __restrict
 
 // Segmented update: V_{j+1} -= sum_d coef_d V_d on each item (the multi-dot
 // kernel already took the Givens step or asked for a second pass).
+// Slice `sub` of S of work item [lo0, hi0): equal lengths rounded up to even,
+// so even item bounds keep even slice bounds; the last slices may be empty.
+// The updates split items into slices so that small batches (fewer items than
+// resident blocks) still spread over the SMs, and otherwise launch a block per
+// item, which the block scheduler balances.
+__device__ __forceinline__ void b_slice(int lo0, int hi0, int S, int sub, int& lo, int& hi) {
+    const int len = ((hi0 - lo0 + S - 1) / S + 1) & ~1;
+    lo = min(hi0, lo0 + sub * len);
+    hi = min(hi0, lo + len);
+}
+
 template <typename TV>
-__global__ void __launch_bounds__(256) k_b_update(TV* V, long ld, BatchDev B, int pass) {
+__global__ void __launch_bounds__(256) k_b_update(TV* V, long ld, BatchDev B, int pass, int S) {
     const int j = *B.jglob;
     __shared__ TV c[DG_MAXM + 2];
-    for (int it = blockIdx.x; it < B.nit; it += gridDim.x) {
+    for (int q = blockIdx.x; q < B.nit * S; q += gridDim.x) {
+        const int it = q / S;
+        int lo, hi;
+        b_slice(B.item_lo[it], B.item_hi[it], S, q - it * S, lo, hi);
         const int inst = B.item_inst[it];
         BState* st = B.bst + inst;
-        if (!B.iactive[inst] || (pass == 2 && !st->reorth)) continue;
+        if (lo >= hi || !B.iactive[inst] || (pass == 2 && !st->reorth)) continue;
         __syncthreads();
         for (int d = threadIdx.x; d <= j; d += blockDim.x) c[d] = (TV)st->coef[d];
         __syncthreads();
         TV* w = V + (long)(j + 1) * ld;
-        for (int l = B.item_lo[it] + threadIdx.x; l < B.item_hi[it]; l += blockDim.x) {
+        for (int l = lo + threadIdx.x; l < hi; l += blockDim.x) {
             TV acc = w[l];
             int d = 0;
             for (; d + 4 <= j + 1; d += 4) {
@@ -476,18 +490,20 @@ __global__ void __launch_bounds__(256) k_b_update(TV* V, long ld, BatchDev B, in
 
 // The f32 segmented update: as k_b_update, eight basis vectors in flight per
 // thread and 8-byte slices where the item's bounds are even.
-__global__ void __launch_bounds__(256) k_b_update32(float* V, long ld, BatchDev B, int pass) {
+__global__ void __launch_bounds__(256) k_b_update32(float* V, long ld, BatchDev B, int pass, int S) {
     const int j = *B.jglob;
     __shared__ float c[DG_MAXM + 2];
-    for (int it = blockIdx.x; it < B.nit; it += gridDim.x) {
+    for (int q = blockIdx.x; q < B.nit * S; q += gridDim.x) {
+        const int it = q / S;
+        int lo, hi;
+        b_slice(B.item_lo[it], B.item_hi[it], S, q - it * S, lo, hi);
         const int inst = B.item_inst[it];
         BState* st = B.bst + inst;
-        if (!B.iactive[inst] || (pass == 2 && !st->reorth)) continue;
+        if (lo >= hi || !B.iactive[inst] || (pass == 2 && !st->reorth)) continue;
         __syncthreads();
         for (int d = threadIdx.x; d <= j; d += blockDim.x) c[d] = (float)st->coef[d];
         __syncthreads();
         float* w = V + (long)(j + 1) * ld;   // aliases V: no __restrict__
-        const int lo = B.item_lo[it], hi = B.item_hi[it];
         if (((lo | hi) & 1) == 0) {
             for (int l = lo + 2 * threadIdx.x; l < hi; l += 2 * blockDim.x) {
                 float2 acc = *reinterpret_cast<const float2*>(w + l);
@@ -935,6 +951,17 @@ struct BatchRun {
     int gsm, gx;
 };
 
+// Launch shape of the segmented updates: S slices per item so that there are
+// at least two blocks per resident update block (4 per SM), one block per slice.
+struct UpdShape {
+    unsigned grid;
+    int S;
+};
+static UpdShape upd_shape(int nit, int gx) {
+    const int S = std::max(1, std::min(16, (2 * gx + nit - 1) / std::max(1, nit)));
+    return UpdShape{(unsigned)std::min(std::max(1L, (long)nit * S), 65535L), S};
+}
+
 template <int NB, typename TA, typename TB, typename TV>
 static int b_enqueue_cycle(dg_handle* h, const BatchRun& Rn, const TA* A, const TB* Binv, const TV* F, TV* x,
                            const TA* Ah, const TV* G) {
@@ -948,6 +975,7 @@ static int b_enqueue_cycle(dg_handle* h, const BatchRun& Rn, const TA* A, const 
     DevCtl step{nullptr, nullptr, h->b_inst, B.iactive, B.iscale};
     DevCtl pend{nullptr, nullptr, h->b_inst, B.ipending, nullptr};
     VecSel vj{B.jglob, 0, Rn.ld}, vj1{B.jglob, 1, Rn.ld};
+    const UpdShape us = upd_shape(B.nit, Rn.gx);
     int n = 0;
     for (int it = 0; it < Rn.m; ++it) {
         if (flex) {
@@ -978,10 +1006,10 @@ static int b_enqueue_cycle(dg_handle* h, const BatchRun& Rn, const TA* A, const 
         for (int pass = 1; pass <= 2; ++pass) {
             if constexpr (sizeof(TV) == 4) {
                 k_b_dots32<<<Rn.gsm, dim3(B_TX, B_TY), 0, h->stream>>>((const float*)V, Rn.ld, B, pass);
-                k_b_update32<<<Rn.gx, 256, 0, h->stream>>>((float*)V, Rn.ld, B, pass);
+                k_b_update32<<<us.grid, 256, 0, h->stream>>>((float*)V, Rn.ld, B, pass, us.S);
             } else {
                 k_b_dots<TV><<<Rn.gsm, dim3(B_TX, B_TY), 0, h->stream>>>(V, Rn.ld, B, pass);
-                k_b_update<TV><<<Rn.gx, 256, 0, h->stream>>>(V, Rn.ld, B, pass);
+                k_b_update<TV><<<us.grid, 256, 0, h->stream>>>(V, Rn.ld, B, pass, us.S);
             }
         }
         k_b_step<<<1, 32, 0, h->stream>>>(B);
@@ -1288,6 +1316,7 @@ static dg_status batch_ir_t(dg_handle* h, const TA* Alo, const TB* Binv, int inn
     const unsigned ge = (unsigned)((h->ne + 255) / 256);
     const unsigned gi = (unsigned)((h->b_n + 255) / 256);
     const DevCtl oact{nullptr, nullptr, h->b_inst, Bo.iactive, nullptr};
+    const UpdShape uo = upd_shape(Bo.nit, Rn.gx);
     const DevCtl opend{nullptr, nullptr, h->b_inst, Bo.ipending, nullptr};
     dg_status result = DG_OK;
     for (int cycle = 0; ocnt[0] > 0 && cycle <= max_outer + 1; ++cycle) {
@@ -1308,7 +1337,7 @@ static dg_status batch_ir_t(dg_handle* h, const TA* Alo, const TB* Binv, int inn
                 vsel_fixed());
             for (int pass = 1; pass <= 2; ++pass) {
                 k_b_dots<double><<<Rn.gsm, dim3(B_TX, B_TY), 0, h->stream>>>(Vo, ld, Bo, pass);
-                k_b_update<double><<<Rn.gx, 256, 0, h->stream>>>(Vo, ld, Bo, pass);
+                k_b_update<double><<<uo.grid, 256, 0, h->stream>>>(Vo, ld, Bo, pass, uo.S);
             }
             k_b_step<<<1, 32, 0, h->stream>>>(Bo);
             k_b_count<<<1, 1024, 0, h->stream>>>(Bo);
