@@ -69,7 +69,7 @@ struct BatchDev {
     int* item_hi;         // [nit] one past the last unknown
     int* inst_item_lo;    // [nI]
     int* inst_item_hi;    // [nI]
-    double* partials;     // [nit][DG_MAXM+2]
+    double* partials;     // [nit * dots_slices][DG_MAXM+2]: per item, or per multi-dot slice
     int* jglob;           // current Arnoldi step of all active instances
     int* counters;        // [4]: active instances, nonfinite, outer-active
     int* iuse;            // [nI] learned correction still on (flexible mode), else NULL
@@ -79,6 +79,7 @@ struct BatchDev {
 #define B_TX 32
 #define B_TY 32
 #define B_DPT ((DG_MAXM + 2 + B_TY - 1) / B_TY)
+#define B_DOTS_SMAX 16   // most slices per work item in the multi-dots (partials per slice)
 
 template <typename TV>
 struct BAcc {
@@ -112,6 +113,16 @@ __device__ __forceinline__ bool inst_last(unsigned int* counter, int nitems) {
     }
     __syncthreads();
     return amlast != 0;
+}
+
+// Slice `sub` of S of work item [lo0, hi0): equal lengths rounded up to even,
+// so even item bounds keep even slice bounds; the last slices may be empty.
+// The updates and multi-dots split items into slices (see upd_shape and
+// dots_shape) so that the blocks get even shares of the work.
+__device__ __forceinline__ void b_slice(int lo0, int hi0, int S, int sub, int& lo, int& hi) {
+    const int len = ((hi0 - lo0 + S - 1) / S + 1) & ~1;
+    lo = min(hi0, lo0 + sub * len);
+    hi = min(hi0, lo + len);
 }
 
 __device__ __forceinline__ double block_sum_1d(double v, double* sh) { return dg_block_sum(v, sh); }
@@ -224,19 +235,22 @@ __device__ void b_finish_column(BatchDev& B, int inst, int j, double wn, const d
 // second Gram-Schmidt pass (less than DG_REORTH_FRAC ||w||^2 left), as in
 // dg_gmres.cu.
 template <typename TV>
-__global__ void __launch_bounds__(B_TX* B_TY) k_b_dots(const TV* __restrict__ V, long ld, BatchDev B, int pass) {
+__global__ void __launch_bounds__(B_TX* B_TY) k_b_dots(const TV* __restrict__ V, long ld, BatchDev B, int pass,
+                                                         int S) {
     const int j = *B.jglob;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int t = ty * B_TX + tx;
     __shared__ double hp[DG_MAXM + 2], hc[DG_MAXM + 2], css[DG_MAXM], sns[DG_MAXM];
-    for (int it = blockIdx.x; it < B.nit; it += gridDim.x) {
+    for (int q = blockIdx.x; q < B.nit * S; q += gridDim.x) {
+        const int it = q / S;   // item; slice q - it * S of it
         const int inst = B.item_inst[it];
         BState* st = B.bst + inst;
         if (!B.iactive[inst] || (pass == 2 && !st->reorth)) continue;
         const int dlast = j + 1;
         const TV* __restrict__ w = V + (long)(j + 1) * ld;
         BAcc<TV> acc[B_DPT];
-        const int lo = B.item_lo[it], hi = B.item_hi[it];
+        int lo, hi;
+        b_slice(B.item_lo[it], B.item_hi[it], S, q - it * S, lo, hi);
         // f64: with at most 16 dots, nsub = 32 / ncol warps share each dot (on
         // the batched workload this cut the f64 solve from 37.4 to 33.7 s, while
         // the f32 inner solves were faster without it: 12.9 against 15.7 s)
@@ -260,7 +274,7 @@ __global__ void __launch_bounds__(B_TX* B_TY) k_b_dots(const TV* __restrict__ V,
             if (t < ncol) {
                 double r = 0.0;
                 for (int u = 0; u < nsub; ++u) r += hp[t + u * ncol];
-                B.partials[(long)it * (DG_MAXM + 2) + t] = r;
+                B.partials[(long)q * (DG_MAXM + 2) + t] = r;
             }
             __syncthreads();
         } else {
@@ -270,13 +284,13 @@ __global__ void __launch_bounds__(B_TX* B_TY) k_b_dots(const TV* __restrict__ V,
                 const int d = ty + B_TY * k;
                 if (d <= dlast) {
                     const double v = dg_warp_sum(acc[k].get());
-                    if (tx == 0) B.partials[(long)it * (DG_MAXM + 2) + d] = v;
+                    if (tx == 0) B.partials[(long)q * (DG_MAXM + 2) + d] = v;
                 }
             }
         }
-        if (!inst_last(&st->arrive, B.inst_item_hi[inst] - B.inst_item_lo[inst])) continue;
+        if (!inst_last(&st->arrive, (B.inst_item_hi[inst] - B.inst_item_lo[inst]) * S)) continue;
         // 16 threads per dot over the instance's items
-        const int ilo = B.inst_item_lo[inst], ihi = B.inst_item_hi[inst];
+        const int ilo = B.inst_item_lo[inst] * S, ihi = B.inst_item_hi[inst] * S;   // its slices
         for (int d0 = 0; d0 <= dlast; d0 += (B_TX * B_TY) / 16) {
             const int d = d0 + t / 16;
             double r = 0.0;
@@ -328,7 +342,8 @@ __global__ void __launch_bounds__(B_TX* B_TY) k_b_dots(const TV* __restrict__ V,
 // partials in two-float and turns each dot into one f64 value: no per-warp f64
 // work, which on this GPU's FP64 pipe would cost as much as the streaming.
 // The tail is that of k_b_dots.
-__global__ void __launch_bounds__(B_TX* B_TY) k_b_dots32(const float* __restrict__ V, long ld, BatchDev B, int pass) {
+__global__ void __launch_bounds__(B_TX* B_TY) k_b_dots32(const float* __restrict__ V, long ld, BatchDev B, int pass,
+                                                          int S) {
     const int j = *B.jglob;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int t = ty * B_TX + tx;
@@ -343,13 +358,15 @@ __global__ void __launch_bounds__(B_TX* B_TY) k_b_dots32(const float* __restrict
     const int d0 = g * gsize;
     const int dn = part < pb ? max(0, min(gsize, ncol - d0)) : 0;
     float2* P2 = reinterpret_cast<float2*>(B.partials);
-    for (int it = blockIdx.x; it < B.nit; it += gridDim.x) {
+    for (int q = blockIdx.x; q < B.nit * S; q += gridDim.x) {
+        const int it = q / S;   // item; slice q - it * S of it
         const int inst = B.item_inst[it];
         BState* st = B.bst + inst;
         if (!B.iactive[inst] || (pass == 2 && !st->reorth)) continue;
         const float* __restrict__ w = V + (long)(j + 1) * ld;
         const float* __restrict__ vg = V + (long)d0 * ld;
-        const int lo = B.item_lo[it], hi = B.item_hi[it];
+        int lo, hi;
+        b_slice(B.item_lo[it], B.item_hi[it], S, q - it * S, lo, hi);
         float acc[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) acc[i] = 0.f;
@@ -388,12 +405,12 @@ __global__ void __launch_bounds__(B_TX* B_TY) k_b_dots32(const float* __restrict
             const int gg = t / gsize, dd = t - gg * gsize;
             float2 sacc = make_float2(0.f, 0.f);
             for (int p = 0; p < pb; ++p) sacc = f2_add(sacc, make_float2(red[p * ngroups + gg][dd], 0.f));
-            P2[(long)it * (DG_MAXM + 2) + t] = sacc;
+            P2[(long)q * (DG_MAXM + 2) + t] = sacc;
         }
         __syncthreads();
-        if (!inst_last(&st->arrive, B.inst_item_hi[inst] - B.inst_item_lo[inst])) continue;
+        if (!inst_last(&st->arrive, (B.inst_item_hi[inst] - B.inst_item_lo[inst]) * S)) continue;
         // one warp per dot over the instance's items, two-float
-        const int ilo = B.inst_item_lo[inst], ihi = B.inst_item_hi[inst];
+        const int ilo = B.inst_item_lo[inst] * S, ihi = B.inst_item_hi[inst] * S;   // its slices
         for (int d = ty; d < ncol; d += B_TY) {
             float2 sacc = make_float2(0.f, 0.f);
             for (int i2 = ilo + tx; i2 < ihi; i2 += B_TX) sacc = f2_add(sacc, __ldcg(P2 + (long)i2 * (DG_MAXM + 2) + d));
@@ -445,16 +462,6 @@ __global__ void __launch_bounds__(B_TX* B_TY) k_b_dots32(const float* __restrict
 
 // Segmented update: V_{j+1} -= sum_d coef_d V_d on each item (the multi-dot
 // kernel already took the Givens step or asked for a second pass).
-// Slice `sub` of S of work item [lo0, hi0): equal lengths rounded up to even,
-// so even item bounds keep even slice bounds; the last slices may be empty.
-// The updates split items into slices so that small batches (fewer items than
-// resident blocks) still spread over the SMs, and otherwise launch a block per
-// item, which the block scheduler balances.
-__device__ __forceinline__ void b_slice(int lo0, int hi0, int S, int sub, int& lo, int& hi) {
-    const int len = ((hi0 - lo0 + S - 1) / S + 1) & ~1;
-    lo = min(hi0, lo0 + sub * len);
-    hi = min(hi0, lo + len);
-}
 
 template <typename TV>
 __global__ void __launch_bounds__(256) k_b_update(TV* V, long ld, BatchDev B, int pass, int S) {
@@ -798,7 +805,13 @@ struct BatchHostLayout {
     size_t total;
 };
 
-static BatchHostLayout batch_layout(int nI, int nit, int nsets) {
+// Slices per item of the multi-dots (grid: one block per SM walks them): about
+// 32 slices per block, so the last round of a block is a small share.
+static int dots_slices(int nit, int gsm) {
+    return std::max(1, std::min(B_DOTS_SMAX, (32 * gsm + nit - 1) / std::max(1, nit)));
+}
+
+static BatchHostLayout batch_layout(int nI, int nit, int nsets, int dsl) {
     BatchHostLayout L{};
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -820,7 +833,7 @@ static BatchHostLayout batch_layout(int nI, int nit, int nsets) {
         S.ipart = take(sizeof(int) * nI);
         S.iouter = take(sizeof(int) * nI);
         S.iscale = take(sizeof(double) * nI);
-        S.partials = take(sizeof(double) * (size_t)nit * (DG_MAXM + 2));
+        S.partials = take(sizeof(double) * (size_t)nit * dsl * (DG_MAXM + 2));   // per multi-dot slice
         S.jglob = take(sizeof(int));
         S.counters = take(sizeof(int) * 4);
         S.iuse = take(sizeof(int) * nI);
@@ -904,7 +917,7 @@ static dg_status batch_tables(dg_handle* h, int nb, int tile, BatchDev& B, Batch
         iihi[i] = (int)iinst.size();
     }
     const int nit = (int)iinst.size();
-    L = batch_layout(h->b_n, nit, B2 ? 2 : 1);
+    L = batch_layout(h->b_n, nit, B2 ? 2 : 1, dots_slices(nit, h->nsm));   // h->nsm: the multi-dots' grid
     dg_status s;
     if ((s = dg_ensure(h, &h->b_dev, &h->cap_bdev, L.total)) != DG_OK) return s;
     char* base = (char*)h->b_dev;
@@ -976,6 +989,7 @@ static int b_enqueue_cycle(dg_handle* h, const BatchRun& Rn, const TA* A, const 
     DevCtl pend{nullptr, nullptr, h->b_inst, B.ipending, nullptr};
     VecSel vj{B.jglob, 0, Rn.ld}, vj1{B.jglob, 1, Rn.ld};
     const UpdShape us = upd_shape(B.nit, Rn.gx);
+    const int dsl = dots_slices(B.nit, Rn.gsm);
     int n = 0;
     for (int it = 0; it < Rn.m; ++it) {
         if (flex) {
@@ -1005,10 +1019,10 @@ static int b_enqueue_cycle(dg_handle* h, const BatchRun& Rn, const TA* A, const 
         }
         for (int pass = 1; pass <= 2; ++pass) {
             if constexpr (sizeof(TV) == 4) {
-                k_b_dots32<<<Rn.gsm, dim3(B_TX, B_TY), 0, h->stream>>>((const float*)V, Rn.ld, B, pass);
+                k_b_dots32<<<Rn.gsm, dim3(B_TX, B_TY), 0, h->stream>>>((const float*)V, Rn.ld, B, pass, dsl);
                 k_b_update32<<<us.grid, 256, 0, h->stream>>>((float*)V, Rn.ld, B, pass, us.S);
             } else {
-                k_b_dots<TV><<<Rn.gsm, dim3(B_TX, B_TY), 0, h->stream>>>(V, Rn.ld, B, pass);
+                k_b_dots<TV><<<Rn.gsm, dim3(B_TX, B_TY), 0, h->stream>>>(V, Rn.ld, B, pass, dsl);
                 k_b_update<TV><<<us.grid, 256, 0, h->stream>>>(V, Rn.ld, B, pass, us.S);
             }
         }
@@ -1317,6 +1331,7 @@ static dg_status batch_ir_t(dg_handle* h, const TA* Alo, const TB* Binv, int inn
     const unsigned gi = (unsigned)((h->b_n + 255) / 256);
     const DevCtl oact{nullptr, nullptr, h->b_inst, Bo.iactive, nullptr};
     const UpdShape uo = upd_shape(Bo.nit, Rn.gx);
+    const int dslo = dots_slices(Bo.nit, Rn.gsm);
     const DevCtl opend{nullptr, nullptr, h->b_inst, Bo.ipending, nullptr};
     dg_status result = DG_OK;
     for (int cycle = 0; ocnt[0] > 0 && cycle <= max_outer + 1; ++cycle) {
@@ -1336,7 +1351,7 @@ static dg_status batch_ir_t(dg_handle* h, const TA* Alo, const TB* Binv, int inn
                 h->A64, h->nbr, Zo + (size_t)j * ld, Vo + (size_t)(j + 1) * ld, h->ne, oact, vsel_fixed(),
                 vsel_fixed());
             for (int pass = 1; pass <= 2; ++pass) {
-                k_b_dots<double><<<Rn.gsm, dim3(B_TX, B_TY), 0, h->stream>>>(Vo, ld, Bo, pass);
+                k_b_dots<double><<<Rn.gsm, dim3(B_TX, B_TY), 0, h->stream>>>(Vo, ld, Bo, pass, dslo);
                 k_b_update<double><<<uo.grid, 256, 0, h->stream>>>(Vo, ld, Bo, pass, uo.S);
             }
             k_b_step<<<1, 32, 0, h->stream>>>(Bo);
@@ -1553,7 +1568,8 @@ extern "C" dg_status dg_batch_autotune(dg_handle* h, int* tile) {
         for (int r = 0; r < 4; ++r) {
             k_b_prof_state<<<(h->b_n + 255) / 256, 256, 0, h->stream>>>(B, j);
             DG_CK(h, cudaEventRecord(e0, h->stream));
-            k_b_dots32<<<sms, dim3(B_TX, B_TY), 0, h->stream>>>((const float*)h->mx_buf, ld, B, 1);
+            k_b_dots32<<<sms, dim3(B_TX, B_TY), 0, h->stream>>>((const float*)h->mx_buf, ld, B, 1,
+                                                                dots_slices(B.nit, sms));
             DG_CK(h, cudaEventRecord(e1, h->stream));
             DG_CK(h, cudaEventSynchronize(e1));
             float ms = 0.f;
